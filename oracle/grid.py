@@ -1,0 +1,44 @@
+"""Finite-difference spatial operator A_h (test infrastructure only).
+
+The paper's experiments use P1 finite elements (Sec. 4); the workloads here use the
+standard finite-difference Dirichlet Laplacian on the unit interval / unit square,
+interior points only, h = 1/(M_x + 1):
+
+* 1D: (A_h u)_i = (2 u_i - u_{i-1} - u_{i+1}) / h^2, u_0 = u_{M+1} = 0.
+* 2D: 5-point stencil, A_h = I_y (x) T_x + T_y (x) I_x with the grid flattened as
+  index = y * M_x + x (x fastest).
+
+A_h is symmetric positive definite, i.e. it satisfies the coercivity assumption of
+eq. (1.2). Its eigenvectors are the sampled sine modes sin(p pi x_i) with eigenvalues
+lambda_p = (4/h^2) sin^2(p pi h / 2) -- the textbook closed form used by the pins.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def lap1d(m: int) -> sp.csr_matrix:
+    h = 1.0 / (m + 1)
+    e = np.ones(m)
+    return sp.diags([-e[1:], 2 * e, -e[1:]], [-1, 0, 1], format="csr") / (h * h)
+
+
+def laplacian(mx: int, my: int = 1, dim: int = 1) -> sp.csr_matrix:
+    if dim == 1:
+        return lap1d(mx)
+    tx = lap1d(mx)
+    ty = lap1d(my)
+    return (sp.kron(sp.identity(my), tx) + sp.kron(ty, sp.identity(mx))).tocsr()
+
+
+def sine_eigenvalues(m: int) -> np.ndarray:
+    """lambda_p = (4/h^2) sin^2(p pi h / 2), p = 1..m."""
+    h = 1.0 / (m + 1)
+    p = np.arange(1, m + 1)
+    return 4.0 / (h * h) * np.sin(p * np.pi * h / 2) ** 2
+
+
+def sine_mode(m: int, p: int) -> np.ndarray:
+    x = np.arange(1, m + 1) / (m + 1)
+    return np.sin(p * np.pi * x)

@@ -1,0 +1,203 @@
+"""Seeded synthetic inputs for the solver and for its oracle.
+
+This module only draws random numbers and samples the problem data (initial value v,
+source f and its time derivatives at t = 0) on the grid. It holds none of the method's
+arithmetic; both the CUDA path's tests/benchmark and the CPU oracle take their inputs
+from here.
+
+The paper's experiments (Sec. 4) use P1 finite elements with specific analytic data and
+publish no timings; these synthetic problems stand in for them at the paper's scale
+(h ~ 1e-3 in 1D, N = 100..1000), on the finite-difference Dirichlet grid of the unit
+interval / square with interior points x_i = i h, h = 1/(M_x + 1), flattened index
+y * M_x + x, and uniform time levels t_n = n T / N, n = 1..N.
+
+Random draws use ``numpy.random.default_rng(seed).standard_normal``:
+
+* 1D sine series: v(x) = sum_{n<=P} c_n sin(n pi x), c_n = z_n / n^2, z drawn with shape (P,).
+* 2D sine series: v(x, y) = sum_{m,n<=P} c_mn sin(m pi x) sin(n pi y), c_mn = z_mn/(m^2+n^2),
+  z drawn with shape (P, P), first index the x-mode.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Problem:
+    name: str
+    dim: int
+    mx: int
+    my: int
+    N: int
+    k: int
+    alpha: float
+    kappa: float
+    T: float
+    v: np.ndarray                       # [M]
+    f_time: np.ndarray                  # [N] g(t_n), n = 1..N   (f = g(t) phi(x))
+    f_space: np.ndarray                 # [M] phi(x)
+    f_derivs0: np.ndarray               # [k-1] d^l g/dt^l (0), l = 0..k-2
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def M(self) -> int:
+        return self.mx * self.my
+
+    @property
+    def tau(self) -> float:
+        return self.T / self.N
+
+    @property
+    def dof(self) -> int:
+        return self.M * self.N
+
+    def f(self) -> np.ndarray:
+        """[N, M] samples f(t_n, x), n = 1..N."""
+        return np.outer(self.f_time, self.f_space)
+
+    def fderiv(self) -> np.ndarray:
+        """[k-1, M]: row l is d_t^l f(0, x), l = 0..k-2 (row 0 = f(0))."""
+        return np.outer(self.f_derivs0, self.f_space).reshape(max(self.k - 1, 0), self.M)
+
+
+def grid_points(m: int) -> np.ndarray:
+    return np.arange(1, m + 1) / (m + 1)
+
+
+def sine_series_1d(m: int, coef: np.ndarray) -> np.ndarray:
+    x = grid_points(m)
+    n = np.arange(1, len(coef) + 1)
+    return np.sin(np.pi * np.outer(x, n)) @ coef
+
+
+def sine_series_2d(mx: int, my: int, coef: np.ndarray) -> np.ndarray:
+    """coef[m-1, n-1] multiplies sin(m pi x) sin(n pi y); returns [my * mx] (x fastest)."""
+    sx = np.sin(np.pi * np.outer(grid_points(mx), np.arange(1, coef.shape[0] + 1)))  # [mx, P]
+    sy = np.sin(np.pi * np.outer(grid_points(my), np.arange(1, coef.shape[1] + 1)))  # [my, P]
+    return (sy @ coef.T @ sx.T).reshape(-1)  # [my, mx]
+
+
+def random_v(dim: int, mx: int, my: int, modes: int, rng) -> np.ndarray:
+    if dim == 1:
+        z = rng.standard_normal(modes)
+        return sine_series_1d(mx, z / np.arange(1, modes + 1) ** 2)
+    z = rng.standard_normal((modes, modes))
+    m = np.arange(1, modes + 1)
+    return sine_series_2d(mx, my, z / (m[:, None] ** 2 + m[None, :] ** 2))
+
+
+def mode_field(dim: int, mx: int, my: int, px: int = 1, py: int = 2) -> np.ndarray:
+    if dim == 1:
+        return np.sin(px * np.pi * grid_points(mx))
+    return np.outer(np.sin(py * np.pi * grid_points(my)), np.sin(px * np.pi * grid_points(mx))).reshape(-1)
+
+
+def _exp_decay(N, T, k):
+    t = np.arange(1, N + 1) * (T / N)
+    return np.exp(-t), np.array([(-1.0) ** l for l in range(max(k - 1, 0))])
+
+
+def make_problem(name, dim, mx, my, N, k, alpha, kappa, T, v, time_kind, f_space):
+    t = np.arange(1, N + 1) * (T / N)
+    if time_kind == "zero":
+        g, d = np.zeros(N), np.zeros(max(k - 1, 0))
+    elif time_kind == "exp":          # g(t) = e^{-t}: d^l g(0) = (-1)^l
+        g, d = _exp_decay(N, T, k)
+    elif time_kind == "linear":       # g(t) = t: g(0) = 0, g'(0) = 1
+        g = t.copy()
+        d = np.zeros(max(k - 1, 0))
+        if k - 1 >= 2:
+            d[1] = 1.0
+    elif time_kind == "exp_growth":   # g(t) = e^{t}: d^l g(0) = 1
+        g, d = np.exp(t), np.ones(max(k - 1, 0))
+    else:
+        raise ValueError(time_kind)
+    return Problem(name, dim, mx, my if dim == 2 else 1, N, k, alpha, kappa, T, v,
+                   g, f_space, d, meta={"time_kind": time_kind})
+
+
+# ---------------------------------------------------------------------------
+# The five workloads
+# ---------------------------------------------------------------------------
+
+
+def c1_heat1d() -> Problem:
+    """1D heat, M = 63, N = 64, T = 1, BDF2, kappa = 0.1, f = 0, v = 16-mode sine series (seed 0)."""
+    rng = np.random.default_rng(0)
+    mx = 63
+    v = random_v(1, mx, 1, 16, rng)
+    return make_problem("heat1d_M63_N64_bdf2", 1, mx, 1, 64, 2, 1.0, 0.1, 1.0, v, "zero",
+                        np.zeros(mx))
+
+
+def c2_heat2d(mx: int = 255, N: int = 256) -> Problem:
+    """2D heat, 255 x 255, N = 256, T = 1, BDF4 with corrections, kappa = 0.05,
+    f = e^{-t} sin(pi x) sin(2 pi y), v = 64 x 64-mode sine series (seed 1)."""
+    rng = np.random.default_rng(1)
+    v = random_v(2, mx, mx, min(64, mx), rng)
+    return make_problem(f"heat2d_{mx}x{mx}_N{N}_bdf4", 2, mx, mx, N, 4, 1.0, 0.05, 1.0, v, "exp",
+                        mode_field(2, mx, mx, 1, 2))
+
+
+def c3_subdiff1d(mx: int = 1023, N: int = 1024) -> Problem:
+    """1D subdiffusion alpha = 0.5, M = 1023, N = 1024, T = 1, CQ-BDF3, kappa = 0.01,
+    f = t sin(pi x), v = 0."""
+    return make_problem(f"subdiff1d_M{mx}_N{N}_cqbdf3_a0.5", 1, mx, 1, N, 3, 0.5, 0.01, 1.0,
+                        np.zeros(mx), "linear", mode_field(1, mx, 1, 1))
+
+
+C4_AXIS = (127, 255, 511)
+C4_N = (64, 256, 1024, 2048)
+C4_ALPHA = (0.3, 0.7, 1.0)
+C4_KAPPA = (0.1, 0.01)
+
+
+def c4_draw(rng, idx: int, axis=C4_AXIS, Ns=C4_N) -> Problem:
+    """One problem of the mixed batch. Field order of the draws: dim, axis size, N, k,
+    alpha, kappa, then the sine-series coefficients of v."""
+    dim = int(rng.integers(1, 3))
+    m = int(axis[rng.integers(0, len(axis))])
+    N = int(Ns[rng.integers(0, len(Ns))])
+    k = int(rng.integers(1, 7))
+    alpha = float(C4_ALPHA[rng.integers(0, len(C4_ALPHA))])
+    kappa = float(C4_KAPPA[rng.integers(0, len(C4_KAPPA))])
+    v = random_v(dim, m, m, 16, rng)
+    return make_problem(f"mix{idx}_{dim}d_{m}_N{N}_k{k}_a{alpha}_kap{kappa}", dim, m, m, N, k,
+                        alpha, kappa, 1.0, v, "exp", mode_field(dim, m, m, 1, 2))
+
+
+def c4_batch(n: int = 64, seed: int = 2, axis=C4_AXIS, Ns=C4_N) -> list[Problem]:
+    """Batched mix: n problems, 1D or 2D, per-axis size from {127, 255, 511}, N from
+    {64, 256, 1024, 2048}, k uniform in 1..6, alpha from {0.3, 0.7, 1.0}, kappa from
+    {0.1, 0.01}; f = e^{-t} sin(pi x) [sin(2 pi y)], v a 16 (x 16)-mode sine series."""
+    rng = np.random.default_rng(seed)
+    return [c4_draw(rng, i, axis, Ns) for i in range(n)]
+
+
+def c5_arrivals(n: int, rate: float = 200.0, seed: int = 3, axis=C4_AXIS, Ns=C4_N):
+    """Poisson arrival stream: (arrival time in s, Problem) pairs, exponential
+    inter-arrival times with mean 1/rate, problems drawn from the batch distribution."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        out.append((t, c4_draw(rng, i, axis, Ns)))
+    return out
+
+
+def small_problem(dim=1, mx=31, N=32, k=2, alpha=1.0, kappa=0.1, T=1.0, seed=7,
+                  time_kind="exp", modes=8, my=None) -> Problem:
+    """Small problems for parity tests (sizes spanning several tiles and ragged tails)."""
+    rng = np.random.default_rng(seed)
+    my = mx if my is None else my
+    v = random_v(dim, mx, my, min(modes, mx, my), rng)
+    if dim == 1:
+        fs = mode_field(1, mx, 1, 1) + 0.3 * mode_field(1, mx, 1, 3)
+    else:
+        fs = mode_field(2, mx, my, 1, 2)
+    p = make_problem(f"small_{dim}d_{mx}x{my}_N{N}_k{k}_a{alpha}", dim, mx, my, N, k, alpha, kappa,
+                     T, v, time_kind, fs)
+    return p
