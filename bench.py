@@ -1,0 +1,371 @@
+"""Benchmark of the parallel-in-time solve on the 2D heat workload.
+
+Workload (one "step" = one whole solve through the hot path): 2D heat on the unit square,
+255 x 255 interior points, N = 256 steps, T = 1, BDF4 with starting-step corrections,
+kappa = 0.05, f = e^{-t} sin(pi x) sin(2 pi y), v a 64 x 64-mode random sine series (seed 1).
+A step forms F_hat from (v, f, d^l f(0)), sets U_0 = v and runs WR sweeps until the
+solver's a-posteriori error estimate is below tol = 1e-9 (relative l2 error <= 1e-8 against
+the sequential FP64 solution is checked at this size by tests/test_gpu_parity.py).
+
+value   = space-time DOF (N * M) per second of the MIXED path, inputs resident in HBM.
+e2e     = the same through host buffers (pinned H2D of v, f, d^l f(0); D2H of U) per step.
+The FP64 diagonalised path (Algorithm 1 in FP64) is timed beside it on the same GPU.
+
+``--impl reference`` times the CPU oracle (sequential FP64 BDF4 with a sparse LU) on a
+bounded sample of the same workload, on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "space-time DOF/s to rel err 1e-8 (mixed vs FP64 diag); p50/p99 solve latency"
+UNIT = "DOF/s"
+TOL = 1e-9
+
+# algorithmic bytes per launch of each kernel, as a function of (N, M); see the design doc
+def algo_bytes(name: str, N: int, M: int) -> float:
+    NM, JM = N * M, (N // 2 + 1) * M
+    table = {
+        "resid_fwd_ff": 16 * NM + 8 * JM,       # read U, F_hat (double-float); write half spectrum
+        "inv_update_ff": 8 * JM + 16 * NM,      # read spectrum; read + write U (double-float)
+        "dst_f32": 16 * JM,                     # read + write spectrum (complex float)
+        "axis_solve_f32": 16 * JM,
+        "rhs_f64": 16 * NM,                     # read f, write F_hat
+        "cvt_d2ff": 16 * NM,
+        "cvt_ff2d": 16 * NM,
+        "initial_guess": 8 * NM,
+        "direct_fwd_f64": 8 * NM + 16 * JM,
+        "direct_inv_f64": 16 * JM + 16 * NM,
+        "dst_f64": 32 * JM,
+        "axis_solve_f64": 32 * JM,
+    }
+    return float(table.get(name, 0.0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def problem_for_rank(rank: int):
+    # weak scaling: every rank solves its own instance (replicas; no exchange step)
+    return workloads.c2_heat2d()
+
+
+def oracle_sample(p, budget_s: float = 15.0):
+    """Time the CPU oracle on the first n_s time levels of the workload (bounded)."""
+    from oracle import grid, sequential
+    A = grid.laplacian(p.mx, p.my, p.dim)
+    f_full = p.f()
+    fd = p.fderiv()
+
+    def run(n_s):
+        t0 = time.perf_counter()
+        sequential.solve_sequential(p.k, p.alpha, p.tau, A, p.v, f_full[:n_s], fd)
+        return time.perf_counter() - t0
+
+    t8 = run(8)
+    per = t8 / 8
+    n_s = int(max(8, min(p.N, budget_s / max(per, 1e-9))))
+    t = run(n_s)
+    return {"value": p.M * n_s / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"sequential FP64 BDF{p.k} (sparse LU, SuperLU single-threaded) over the first "
+                      f"{n_s} of {p.N} time levels of the workload, {t:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    p = problem_for_rank(0)
+    samples = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = oracle_sample(p, budget_s=min(20.0, 150.0 / max(1, args.warmup + args.steps)))
+        if i >= args.warmup:
+            samples.append(info["value"])
+    value = statistics.median(samples)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * p.dof / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": p.name, "dof": p.dof},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    from paper_2007_13125_gb300 import Plan, pint
+    from paper_2007_13125_gb300 import build as pbuild
+    if not pbuild.up_to_date():
+        raise RuntimeError("libpint.so is not built (run __graft_entry__.build())")
+
+    p = problem_for_rank(rank)
+    N, M = p.N, p.M
+    v_h, f_h, fd_h = p.v, p.f(), p.fderiv()
+    v = torch.tensor(v_h, device=dev)
+    f = torch.tensor(f_h, device=dev)
+    fd = torch.tensor(fd_h, device=dev)
+    F = torch.empty((N, M), dtype=torch.float64, device=dev)
+    U = torch.empty((N, M), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    plans = {"mixed": Plan.for_problem(p, "mixed"), "fp64": Plan.for_problem(p, "fp64")}
+    last = {}
+
+    def step(prec):
+        plan = plans[prec]
+        plan.form_rhs(v, f, fd, F, stream)
+        plan.initial_guess(v, U, stream)
+        st, sweeps, upd = plan.solve(F, U, tol=TOL, max_sweeps=30, stream=stream)
+        last[prec] = (sweeps, upd)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(prec, steps, warmup, per_step=False):
+        for _ in range(warmup):
+            step(prec)
+        barrier()
+        lat = []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            if per_step:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            step(prec)
+            if per_step:
+                b.record(stream)
+                lat.append((a, b))
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if pg is not None:
+            t = torch.tensor([ms], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        lats = [a.elapsed_time(b) for a, b in lat]
+        return ms / steps, lats
+
+    # ---- main timed region: MIXED path, per-kernel events on, clocks sampled ----
+    for _ in range(args.warmup):
+        step("mixed")
+    barrier()
+    pint.set_profiling(True)
+    pint.kernel_stats(reset=True)
+    clk = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clk.start()
+    ms_mixed, lat_mixed = timed("mixed", args.steps, 0, per_step=True)
+    clocks = clk.stop()
+    kstats = pint.kernel_stats(reset=True)
+    pint.set_profiling(False)
+    launches = sum(n for n, _ in kstats.values())
+
+    # ---- FP64 diagonalised path, same workload ----
+    ms_fp64, lat_fp64 = timed("fp64", max(2, args.steps // 2), 1, per_step=True)
+
+    # ---- end to end: host buffers, H2D + solve + D2H per step ----
+    v_pin = torch.tensor(v_h).pin_memory()
+    f_pin = torch.tensor(f_h).pin_memory()
+    fd_pin = torch.tensor(fd_h).pin_memory()
+    U_pin = torch.empty((N, M), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        v.copy_(v_pin, non_blocking=True)
+        f.copy_(f_pin, non_blocking=True)
+        fd.copy_(fd_pin, non_blocking=True)
+        step("mixed")
+        U_pin.copy_(U, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ke = max(3, args.steps // 2)
+    e0.record(stream)
+    for _ in range(ke):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / ke
+    h2d = (v_h.size + f_h.size + fd_h.size) * 8
+    d2h = N * M * 8
+
+    # ---- roofline of the dominant kernel ----
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    top = max(kstats.items(), key=lambda kv: kv[1][1]) if kstats else None
+    roofline = None
+    per_kernel = {}
+    for name, (n, tot) in kstats.items():
+        avg_ms = tot / max(n, 1)
+        b = algo_bytes(name, N, M)
+        per_kernel[name] = {"launches": n, "avg_us": round(1e3 * avg_ms, 2),
+                            "share": round(tot / sum(t for _, t in kstats.values()), 3),
+                            "algo_GBps": round(b / (avg_ms * 1e-3) / 1e9, 1) if b else None}
+    if top:
+        name, (n, tot) = top
+        avg_s = tot / n * 1e-3
+        ach = algo_bytes(name, N, M) / avg_s / 1e9
+        roofline = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(ach / hbm_peak, 3), "traffic": None,
+                    "peak_source": peak_src + " hbm_gbs (STREAM-style copy)",
+                    "algo_bytes_per_launch": algo_bytes(name, N, M)}
+
+    n_world = world
+    dof_total = p.dof * n_world
+    value = dof_total / (ms_mixed * 1e-3)
+    lat_sorted = sorted(lat_mixed)
+    p50 = float(np.percentile(lat_sorted, 50)) if lat_sorted else None
+    p99 = float(np.percentile(lat_sorted, 99)) if lat_sorted else None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = oracle_sample(p)
+        except Exception as e:  # never let the baseline break the bench line
+            cpu = {"error": str(e)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
+        "config": {
+            "workload": p.name, "dim": p.dim, "mx": p.mx, "my": p.my, "N": N, "k": p.k,
+            "kappa": p.kappa, "dof_per_gpu": p.dof, "precision": "mixed", "tol": TOL,
+            "sweeps": last["mixed"][0], "final_update": last["mixed"][1],
+            "latency_ms_p50": p50, "latency_ms_p99": p99,
+            "fp64_diag": {"dof_per_s": dof_total / (ms_fp64 * 1e-3), "ms_per_solve": ms_fp64,
+                          "sweeps": last["fp64"][0],
+                          "latency_ms_p50": float(np.percentile(lat_fp64, 50)),
+                          "latency_ms_p99": float(np.percentile(lat_fp64, 99))},
+            "mixed_over_fp64": ms_fp64 / ms_mixed,
+            "l2_policy": "inputs larger than L2 (U, F_hat, f: 133 MB each in FP64)",
+            "parallelism": f"replicas x{world}",
+            "kernels": per_kernel,
+        },
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": dof_total / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for pl in plans.values():
+        pl.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * pint.h -- C ABI of the GB300 parallel-in-time solver for BDF-k (k = 1..6) diffusion and
+ * CQ-BDF-k subdiffusion, after Wu & Zhou, "A parallel-in-time algorithm for high-order BDF
+ * methods for diffusion and subdiffusion equations" (arXiv 2007.13125).
+ *
+ * Problem (Sec. 1, eq. (1.1) and eq. (1.4)):  D_t^alpha u + A u = f on (0, T], u(0) = v, with
+ * D_t^alpha the first derivative (alpha = 1) or the Caputo derivative (0 < alpha < 1), and A the
+ * finite-difference Dirichlet Laplacian on the unit interval (dim = 1) or unit square (dim = 2):
+ * interior points only, h_x = 1/(mx+1), h_y = 1/(my+1), 3-point / 5-point stencil.
+ *
+ * Discretisation: uniform steps t_n = n tau, n = 1..N; corrected BDF-k (Sec. 2.1, eq. (2.1)) or
+ * corrected CQ-BDF-k (Sec. 3.1, eq. (3.7)) with the starting-step constants of Table 1. The
+ * sequential scheme is the all-at-once system K U = F_hat (eq. (2.6)/(3.11) with kappa = 0).
+ *
+ * Parallel-in-time solve: the waveform-relaxation iteration (eq. (2.5) / eq. (3.10)) replaces
+ * the history by kappa-periodic data; each sweep solves P_kappa U_m = F_{m-1} with the
+ * kappa-circulant matrix B_k(kappa) = S D S^-1, S = Lambda(kappa) V (Lemma 2.3 / Lemma 3.3):
+ * a kappa^{n/N}-scaled DFT along time, N independent shifted spatial solves
+ * (g_j tau^-alpha + A) q_j = h_j, g_j the eigenvalues of B_k(kappa), and the inverse DFT and
+ * scaling (Algorithm 1 / Algorithm 2). The exact time-stepping solution is the fixed point.
+ *
+ * Data layout (all solver arrays): FP64, row-major [N][M], row n-1 holds time level t_n, and a
+ * row is the grid flattened as y * mx + x (x fastest), M = mx * my (my = 1 in 1D).
+ *
+ * Memory: every array argument marked "device" is a device pointer owned by the caller (for
+ * example torch.Tensor.data_ptr() of a CUDA tensor) that must stay valid until the stream work
+ * of the call has completed. A plan owns its device workspaces and constant tables.
+ * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *
+ * Errors: every call returns a pint_status and never aborts, throws or traps. A failing call
+ * leaves a message retrievable with pint_last_error() (thread-local). Invalid arguments return
+ * PINT_EINVAL before anything is enqueued. A plan is not thread-safe; use one per host thread.
+ *
+ * Supported sizes: N a power of two, 8 <= N <= 4096 (CQ: N <= 2048); mx + 1 and my + 1 powers
+ * of two, 3 <= mx, my <= 2047 (the sine transforms run as FFTs of length 2(m+1)).
+ */
+#ifndef PINT_H
+#define PINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pint_plan_s* pint_plan;
+
+typedef enum {
+  PINT_OK = 0,
+  PINT_EINVAL = 1,     /* invalid argument or unsupported size */
+  PINT_ENOMEM = 2,     /* device or host allocation failed */
+  PINT_ECUDA = 3,      /* a CUDA runtime call failed (message in pint_last_error) */
+  PINT_ENOTCONV = 4,   /* pint_solve reached max_sweeps above tol */
+  PINT_ETIMEOUT = 5,   /* bounded wait expired (serving API) */
+  PINT_EAGAIN = 6,     /* result not ready yet (serving API) */
+  PINT_EBUDGET = 7,    /* request larger than the serving memory budget */
+  PINT_ENOTFOUND = 8   /* unknown ticket (serving API) */
+} pint_status;
+
+/* Arithmetic of a sweep.
+ * PINT_FP64:  Algorithm 1/2 as printed, every step in FP64 (direct form F_{m-1} of eq. (2.7) /
+ *             eq. (3.12), FP64 DFTs and spatial solves).
+ * PINT_MIXED: residual-correction form U_m = U_{m-1} + P~^-1 (F_hat - K U_{m-1}), algebraically the
+ *             same iteration; the residual in double-float (~48-bit) arithmetic, the kappa-scaled
+ *             DFT and the shifted solves (P~^-1) in FP32 complex, the iterate kept in double-float.
+ * PINT_FP32:  Algorithm 1/2 entirely in FP32 (reports the single-precision floor). */
+typedef enum { PINT_FP64 = 0, PINT_MIXED = 1, PINT_FP32 = 2 } pint_precision;
+
+/* Eigenvalues used for the CQ kappa-circulant (identical for alpha = 1):
+ * TRUNC_DFT:   g_j = sum_{l<N} kappa^{l/N} omega_l e^{-2 pi i j l/N}, the spectrum of B_k(kappa) as
+ *              printed in eq. (3.11) (weights omega_0..omega_{N-1}).
+ * CLOSED_FORM: g_j = delta_k(kappa^{1/N} e^{-2 pi i j/N})^alpha (principal branch). */
+typedef enum { PINT_EIG_TRUNC_DFT = 0, PINT_EIG_CLOSED_FORM = 1 } pint_eig_variant;
+
+typedef struct {
+  int dim;  /* 1 or 2 */
+  int mx;   /* interior points along x */
+  int my;   /* interior points along y (ignored, taken as 1, when dim == 1) */
+} pint_grid;
+
+typedef struct {
+  int k;                  /* BDF order 1..6 */
+  double alpha;           /* 1 (diffusion) or 0 < alpha < 1 (subdiffusion) */
+  double kappa;           /* WR relaxation parameter, 0 < kappa < 1 */
+  double tau;             /* time step T/N > 0 */
+  int N;                  /* time levels */
+  pint_grid grid;
+  pint_precision precision;
+  pint_eig_variant eig;
+} pint_plan_desc;
+
+/* Build a plan: FP64 constant tables (BDF / CQ weights omega_j of eq. (2.2) / eq. (3.2) --
+ * CQ weights by the power-series recursion for delta_k^alpha --, the Table 1 constants, the
+ * time scales kappa^{n/N}, the eigenvalues g_j of Lemma 2.3 / 3.3, the sine-transform
+ * eigenvalues, FFT twiddles) on the host, one upload, and the device workspaces.
+ * Returns PINT_EINVAL for k outside 1..6, alpha outside (0,1], kappa outside (0,1), tau <= 0,
+ * or unsupported N / mx / my; PINT_ENOMEM / PINT_ECUDA on device failure. *out is set only on
+ * success. Synchronous. */
+pint_status pint_plan_create(int k, double alpha, double kappa, double tau, int N,
+                             const pint_grid* grid, pint_precision precision, pint_plan* out);
+pint_status pint_plan_create_desc(const pint_plan_desc* desc, pint_plan* out);
+
+/* Free a plan and its device memory (synchronises the device first). NULL is accepted. */
+pint_status pint_plan_destroy(pint_plan plan);
+
+/* Bytes of device memory the plan holds (tables + workspaces); 0 for NULL. */
+size_t pint_plan_workspace_bytes(pint_plan plan);
+
+/* Right-hand side of the all-at-once system (eq. (2.7) / eq. (3.12) without the kappa term):
+ *   F_hat_n = f(t_n) + a_n^(k) (f(0) - A v) + sum_{l=1}^{k-2} b_{l,n}^(k) tau^l d_t^l f(0)
+ *             + tau^-alpha sum_{j=0}^{n-1} omega_j v,        n = 1..N.
+ * v      [M]      device, initial value on the grid
+ * f      [N][M]   device, f(t_n) on the grid
+ * fderiv [k-1][M] device, row l = d_t^l f(0) (row 0 = f(0)); may be NULL when k = 1
+ * Fhat   [N][M]   device, output (FP64)
+ * Enqueued on `stream`; asynchronous. */
+pint_status pint_form_rhs(pint_plan plan, const double* v, const double* f, const double* fderiv,
+                          double* Fhat, void* stream);
+
+/* Initial guess U_0^n = v for n = 1..N (the starting iterate of Theorem 2.7).
+ * v [M] device; U [N][M] device, output. Asynchronous on `stream`. */
+pint_status pint_initial_guess(pint_plan plan, const double* v, double* U, void* stream);
+
+/* One WR sweep U_next = P_kappa^-1 (F_hat + (P_kappa - K) U_prev) (Algorithm 1 / 2, one iteration
+ * of eq. (2.5) / eq. (3.10); in PINT_MIXED the same iterate in residual-correction form).
+ * Fhat, U_prev, U_next [N][M] device; U_next may equal U_prev.
+ * upd_rel: optional host pointer; when non-NULL the call waits for the stream and stores
+ * ||U_next - U_prev||_2 / ||U_next||_2 (space-time l2). */
+pint_status pint_wr_sweep(pint_plan plan, const double* Fhat, const double* U_prev, double* U_next,
+                          double* upd_rel, void* stream);
+
+/* Iterate sweeps from the initial guess in U until converged (Theorem 2.7 uses U_0^n = v).
+ * After sweep m, upd_m = ||U_m - U_{m-1}|| / ||U_m||; for m >= 2 with q = upd_m / upd_{m-1} < 1 the
+ * error estimate is upd_m q / (1 - q). Stops when that estimate is <= tol (or upd_1 <= tol/100),
+ * or, if the ratio stagnates (q >= 1), when upd_m <= tol. Returns PINT_ENOTCONV after max_sweeps
+ * otherwise (U then holds the last iterate).
+ * Fhat [N][M] device input; U [N][M] device, in: initial guess, out: solution.
+ * sweeps_out, upd_rel_out: optional host pointers. Synchronises `stream` once per sweep to read
+ * two norms (16 bytes). */
+pint_status pint_solve(pint_plan plan, const double* Fhat, double* U, double tol, int max_sweeps,
+                       int* sweeps_out, double* upd_rel_out, void* stream);
+
+/* ---- host-only queries (no GPU needed) ---- */
+
+/* omega_0..omega_{n-1}: BDF-k weights (alpha = 1, zero past k; eq. (2.2)) or the CQ weights,
+ * coefficients of delta_k(xi)^alpha (eq. (3.2)), by the power-series recursion
+ * q_0 = p_0^alpha, q_m = (1/(m p_0)) sum_{i=1}^{min(m,k)} ((alpha+1) i - m) p_i q_{m-i}. */
+pint_status pint_time_weights(int k, double alpha, int n, double* omega);
+
+/* Table 1 constants: a[n-1] = a_n^(k) (n = 1..5), b[(l-1)*5 + (n-1)] = b_{l,n}^(k) (l = 1..4);
+ * zero where the table has no entry. b_{3,1}^(5) is returned as -1/720 (the printed +1/720
+ * contradicts the order conditions that define the table). */
+pint_status pint_correction_coefficients(int k, double* a, double* b);
+
+/* Eigenvalues g_j, j = 0..N-1, of B_k(kappa) for the chosen variant (Lemma 2.3 / 3.3), FP64. */
+pint_status pint_circulant_eigenvalues(int k, double alpha, double kappa, int N, pint_eig_variant eig,
+                                       double* re, double* im);
+
+/* ---- diagnostics ---- */
+const char* pint_last_error(void);
+const char* pint_status_string(pint_status s);
+const char* pint_version(void);
+
+/* Per-kernel timing with CUDA events recorded around every launch on its stream (off by
+ * default). pint_kernel_stats waits for the recorded events, then fills up to `max` entries
+ * (names are static strings) and returns the number of distinct kernels; reset != 0 clears. */
+pint_status pint_set_profiling(int enable);
+int pint_kernel_stats(int max, const char** names, int* launches, double* total_ms, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PINT_H */

@@ -1,0 +1,115 @@
+// Internal declarations shared by the kernel translation units and the host plan code.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace pint {
+
+constexpr int kThreads = 256;   // threads per CTA of every tile kernel
+constexpr int kMaxK = 6;
+
+// ---- time-axis kernels (kernels_time.cu) ----
+
+// MIXED: r = F_hat - K U in double-float, times kappa^{i/N}, real -> half-complex DFT.
+struct ResidFwdArgs {
+  const float* Uhi; const float* Ulo;      // iterate U [N][M] (double-float)
+  const float* Fhi; const float* Flo;      // F_hat [N][M] (double-float)
+  const double* y;                         // CQ: tau^-alpha (L_omega U) [N][M], else null
+  float2* S;                               // half spectrum [(N/2+1)][M]
+  const float* s;                          // kappa^{i/N}, i < N
+  const float2* tw;                        // exp(-2 pi i m / N), m < N
+  int N, M, mx, dim, k, C;
+  float c_hi[kMaxK + 1], c_lo[kMaxK + 1];  // c_0 (incl. stencil centre), c_j = omega_j tau^-alpha
+  float gx_hi, gx_lo, gy_hi, gy_lo;        // 1/hx^2, 1/hy^2
+};
+
+// MIXED: inverse DFT, times 1/(N kappa^{i/N}), U += c (double-float), norms.
+struct InvUpdArgs {
+  const float2* S; float* Uhi; float* Ulo;
+  const float* inv_s; const float2* tw;
+  int N, M, C;
+  double* norms;                           // [0] += sum c^2, [1] += sum U^2
+};
+
+// FP64 / FP32: F_{m-1} = F_hat + (P - K) U_{m-1}, times kappa^{i/N}, DFT.
+template <typename T> struct DirectFwdArgs {
+  const T* F; const T* U;                  // F_hat, U_{m-1} [N][M]
+  const double* z;                         // CQ: kappa tau^-alpha (W' U) [N][M], else null
+  void* S;                                 // half spectrum of T2
+  const T* s; const void* tw;
+  int N, M, C, k;
+  T kw[kMaxK + 1];                         // kappa tau^-alpha omega_j (BDF corner)
+};
+
+template <typename T> struct DirectInvArgs {
+  const void* S; const T* Uold; T* Uout;
+  const T* inv_s; const void* tw;
+  int N, M, C;
+  double* norms;                           // [0] += sum (Unew-Uold)^2, [1] += sum Unew^2
+};
+
+// CQ Toeplitz product z = omega * U (linear convolution along time, 2N-point FFTs).
+struct ToepArgs {
+  const double* Ud; const float* Uhi; const float* Ulo; const float* Uf;
+  int ukind;                               // 0 double, 1 double-float, 2 float
+  double* out;                             // [N][M]
+  const double2* what;                     // FFT_{2N}(omega, zero padded), permuted, pre-scaled
+  const double2* tw;                       // exp(-2 pi i m / 2N)
+  int N, M, C, half;                       // half 0: z_0..z_{N-1}; 1: z_N..z_{2N-1}
+};
+
+// right-hand side F_hat (FP64)
+struct RhsArgs {
+  const double* v; const double* f; const double* fd; double* F;
+  const double* beta;                      // tau^-alpha sum_{j<n} omega_j, n = 1..N
+  int N, M, mx, dim, k;
+  double gx, gy;
+  double a[kMaxK];                         // a_n, n = 1..k-1
+  double bt[kMaxK][kMaxK];                 // b_{l,n} tau^l
+};
+
+// ---- spatial kernels (kernels_space.cu) ----
+// Sine transform / shifted solve along one axis of the half spectrum.
+template <typename T> struct AxisArgs {
+  void* S;                                 // T2 spectrum
+  int n;                                   // points along the axis (interior)
+  int lines;                               // number of lines
+  int mode;                                // 0: lines contiguous (stride 1); 1: stride P
+  int P;                                   // mode 1: lines per j-slice (= mx), stride
+  int op;                                  // 0: transform only; 1: transform, divide, transform
+  const void* sigma;                       // T2 [N/2+1] (op 1)
+  const T* lam_axis;                       // [n] eigenvalues along this axis (op 1)
+  const T* lam_other;                      // mode 1: [P] eigenvalues of the other axis
+  T scale;                                 // op 1 divisor scale
+  int lines_per_j;                         // op 1: j = line / lines_per_j
+  const void* tw;                          // exp(-2 pi i m / L), L = 2(n+1)
+  int C, ld;
+};
+
+size_t resid_fwd_smem(int N, int C);
+size_t inv_upd_smem(int N, int C);
+template <typename T> size_t direct_smem(int N, int C);
+size_t toep_smem(int N, int C);
+template <typename T> size_t axis_smem(int n, int C);
+
+cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st);
+cudaError_t launch_inv_upd(const InvUpdArgs& a, cudaStream_t st);
+template <typename T> cudaError_t launch_direct_fwd(const DirectFwdArgs<T>& a, cudaStream_t st);
+template <typename T> cudaError_t launch_direct_inv(const DirectInvArgs<T>& a, cudaStream_t st);
+cudaError_t launch_toeplitz(const ToepArgs& a, cudaStream_t st);
+cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t st);
+template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t st);
+
+// conversions
+cudaError_t launch_d2ff(const double* x, float* hi, float* lo, size_t n, cudaStream_t st);
+cudaError_t launch_ff2d(const float* hi, const float* lo, double* x, size_t n, cudaStream_t st);
+cudaError_t launch_d2f(const double* x, float* y, size_t n, cudaStream_t st);
+cudaError_t launch_f2d(const float* x, double* y, size_t n, cudaStream_t st);
+cudaError_t launch_bcast_d(const double* v, double* U, int N, int M, cudaStream_t st);
+cudaError_t launch_bcast_d2ff(const double* v, float* hi, float* lo, int N, int M, cudaStream_t st);
+
+// Kernel timing hooks (per-kernel CUDA events when profiling is on).
+void prof_begin(const char* name, cudaStream_t st);
+void prof_end(cudaStream_t st);
+
+}  // namespace pint

@@ -1,0 +1,779 @@
+// Host side of the C ABI: plan construction (FP64 constant tables), workspaces, the sweep
+// and solve drivers, host-only queries, error reporting and per-kernel timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pint.h"
+#include "fft.cuh"
+#include "pint_internal.h"
+
+using cd = std::complex<double>;
+
+namespace pint {
+
+// ---------------------------------------------------------------------------
+// error state
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static pint_status fail(pint_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+static pint_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return PINT_ECUDA;
+}
+#define PINT_CUDA(call)                                        \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call);        \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// per-kernel timing
+// ---------------------------------------------------------------------------
+struct ProfRec { const char* name; cudaEvent_t a, b; };
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof_recs;
+static std::vector<cudaEvent_t> g_prof_pool;
+static thread_local ProfRec g_prof_open = {nullptr, nullptr, nullptr};
+
+static cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_begin(const char* name, cudaStream_t st) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_open.name = name;
+  g_prof_open.a = prof_event();
+  g_prof_open.b = prof_event();
+  cudaEventRecord(g_prof_open.a, st);
+}
+void prof_end(cudaStream_t st) {
+  if (!g_prof_on || !g_prof_open.name) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEventRecord(g_prof_open.b, st);
+  g_prof_recs.push_back(g_prof_open);
+  g_prof_open.name = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 host math: weights, Table 1, eigenvalues
+// ---------------------------------------------------------------------------
+static void bdf_poly(int k, double* w) {  // omega_0..omega_k of sum_l (1 - z)^l / l
+  for (int j = 0; j <= k; ++j) w[j] = 0.0;
+  for (int l = 1; l <= k; ++l) {
+    double binom = 1.0;  // C(l, j)
+    for (int j = 0; j <= l; ++j) {
+      w[j] += ((j & 1) ? -binom : binom) / l;
+      binom = binom * (l - j) / (j + 1);
+    }
+  }
+}
+
+static void time_weights(int k, double alpha, int n, double* out) {
+  double p[kMaxK + 1];
+  bdf_poly(k, p);
+  if (alpha == 1.0) {
+    for (int i = 0; i < n; ++i) out[i] = i <= k ? p[i] : 0.0;
+    return;
+  }
+  if (n <= 0) return;
+  out[0] = std::pow(p[0], alpha);
+  for (int m = 1; m < n; ++m) {
+    double s = 0.0;
+    const int top = std::min(m, k);
+    for (int i = 1; i <= top; ++i) s += ((alpha + 1.0) * i - m) * p[i] * out[m - i];
+    out[m] = s / (m * p[0]);
+  }
+}
+
+// Table 1 (Sec. 2.1), b_{3,1}^(5) = -1/720.
+static void table1(int k, double* a, double (*b)[5]) {
+  static const double A[7][5] = {
+      {0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}, {1.0 / 2, 0, 0, 0, 0},
+      {11.0 / 12, -5.0 / 12, 0, 0, 0},
+      {31.0 / 24, -7.0 / 6, 3.0 / 8, 0, 0},
+      {1181.0 / 720, -177.0 / 80, 341.0 / 240, -251.0 / 720, 0},
+      {2837.0 / 1440, -2543.0 / 720, 17.0 / 5, -1201.0 / 720, 95.0 / 288}};
+  static const double B[7][4][5] = {
+      {}, {}, {},
+      {{1.0 / 12, 0, 0, 0, 0}},
+      {{1.0 / 6, -1.0 / 12, 0, 0, 0}, {0, 0, 0, 0, 0}},
+      {{59.0 / 240, -29.0 / 120, 19.0 / 240, 0, 0}, {1.0 / 240, -1.0 / 240, 0, 0, 0},
+       {-1.0 / 720, 0, 0, 0, 0}},
+      {{77.0 / 240, -7.0 / 15, 73.0 / 240, -3.0 / 40, 0}, {1.0 / 96, -1.0 / 60, 1.0 / 160, 0, 0},
+       {-1.0 / 360, 1.0 / 720, 0, 0, 0}, {0, 0, 0, 0, 0}}};
+  for (int n = 0; n < 5; ++n) a[n] = A[k][n];
+  for (int l = 0; l < 4; ++l)
+    for (int n = 0; n < 5; ++n) b[l][n] = B[k][l][n];
+}
+
+// delta_k(z) = sum_l s^l / l with s = 1 - z supplied directly (no cancellation near z = 1)
+static cd delta_from_s(int k, cd s) {
+  cd out = 0.0, p = 1.0;
+  for (int l = 1; l <= k; ++l) {
+    p *= s;
+    out += p / double(l);
+  }
+  return out;
+}
+
+// exp(-2 pi i m / L) with the angle reduced exactly
+static cd unit_root(long m, long L) {
+  m %= L;
+  if (m < 0) m += L;
+  const double x = 2.0 * double(m) / double(L);  // angle = pi x
+  double s, c;
+  sincospi(x, &s, &c);
+  return cd(c, -s);
+}
+
+static void host_fft(std::vector<cd>& a, bool inverse) {  // natural order, radix-2
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    for (size_t i = 0; i < n; i += len)
+      for (size_t j = 0; j < len / 2; ++j) {
+        cd w = unit_root((long)j, (long)len);
+        if (inverse) w = std::conj(w);
+        cd u = a[i + j], t = a[i + j + len / 2] * w;
+        a[i + j] = u + t;
+        a[i + j + len / 2] = u - t;
+      }
+  }
+}
+
+static void eigenvalues(int k, double alpha, double kappa, int N, pint_eig_variant eig,
+                        const std::vector<double>& omega, std::vector<cd>& g) {
+  g.assign(N, cd(0.0, 0.0));
+  const double lk = std::log(kappa) / N;
+  if (alpha == 1.0 || eig == PINT_EIG_CLOSED_FORM) {
+    // g_j = delta_k(kappa^{1/N} e^{-2 pi i j / N})^alpha, 1 - z = -expm1(ln kappa / N - 2 pi i j / N)
+    const double r = std::exp(lk);           // kappa^{1/N}
+    const double om = -std::expm1(lk);       // 1 - kappa^{1/N}
+    for (int j = 0; j < N; ++j) {
+      // z = r e^{-i t}, t = 2 pi j / N;  1 - z = (1 - r) + r (1 - e^{-i t}),
+      // 1 - e^{-i t} = 2 sin^2(t/2) + i sin t: both parts free of cancellation
+      double sn, cs, sh, ch;
+      sincospi(2.0 * double(j) / double(N), &sn, &cs);
+      sincospi(double(j) / double(N), &sh, &ch);
+      const cd one_minus_e(2.0 * sh * sh, sn);
+      const cd s = om + r * one_minus_e;
+      cd d = delta_from_s(k, s);
+      if (alpha != 1.0) d = std::exp(alpha * std::log(d));
+      g[j] = d;
+    }
+    return;
+  }
+  // truncated kappa-circulant of eq. (3.11): DFT of c_l = kappa^{l/N} omega_l, l < N
+  std::vector<cd> c(N);
+  for (int l = 0; l < N; ++l) c[l] = std::exp(lk * l) * omega[l];
+  host_fft(c, false);
+  g = c;
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+template <typename T> struct DevTables {
+  void* tw_time = nullptr;   // V[N]
+  T* s = nullptr;            // [N]
+  T* inv_s = nullptr;        // [N]
+  void* sigma = nullptr;     // V[N/2+1]
+  void* tw_x = nullptr;      // V[2(mx+1)]
+  void* tw_y = nullptr;      // V[2(my+1)]
+  T* lam_x = nullptr;        // [mx]
+  T* lam_y = nullptr;        // [my]
+};
+
+}  // namespace pint
+
+using namespace pint;
+
+struct pint_plan_s {
+  int k; double alpha, kappa, tau; int N;
+  int dim, mx, my, M;
+  pint_precision prec;
+  pint_eig_variant eig;
+  bool cq;
+  std::vector<double> omega;
+  double a[5];
+  double b[4][5];
+  std::vector<cd> g;
+  double gx, gy;
+  // device
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  DevTables<float> tf;
+  DevTables<double> td;
+  double* beta = nullptr;           // [N]
+  double2* tw_2n = nullptr;         // [2N]
+  double2* what_lo = nullptr;       // [2N] permuted, * tau^-alpha / 2N
+  double2* what_up = nullptr;       // [2N] permuted, * kappa tau^-alpha / 2N
+  float *Uhi = nullptr, *Ulo = nullptr, *Fhi = nullptr, *Flo = nullptr;  // MIXED / FP32 (Uhi, Fhi)
+  void* S = nullptr;                // spectrum
+  double* z = nullptr;              // CQ Toeplitz output [N][M]
+  double* norms = nullptr;          // device [2]
+  double* h_norms = nullptr;        // pinned host [2]
+  // tiles
+  int Ct, Ctd, Cz, Cx, Cy;          // columns per CTA: time (float), time (T), toeplitz, x-axis, y-axis
+};
+
+namespace {
+
+bool pow2(long x) { return x > 0 && (x & (x - 1)) == 0; }
+
+template <typename X> pint_status dalloc(pint_plan p, X** ptr, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(X));
+  if (e != cudaSuccess) return fail(PINT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  p->allocs.push_back(q);
+  p->bytes += count * sizeof(X);
+  *ptr = reinterpret_cast<X*>(q);
+  return PINT_OK;
+}
+
+template <typename X> pint_status upload(pint_plan p, X** ptr, const std::vector<X>& host) {
+  pint_status s = dalloc(p, ptr, host.size());
+  if (s != PINT_OK) return s;
+  PINT_CUDA(cudaMemcpy(*ptr, host.data(), host.size() * sizeof(X), cudaMemcpyHostToDevice));
+  return PINT_OK;
+}
+
+int pick_cols(size_t per_col_bytes, size_t budget, int cmax, int cmin) {
+  int C = cmax;
+  while (C > cmin && per_col_bytes * C > budget) C >>= 1;
+  return C;
+}
+
+template <typename T>
+pint_status build_tables(pint_plan p, DevTables<T>& t) {
+  using V = typename c2<T>::t;
+  const int N = p->N;
+  auto tw_of = [](int L) {
+    std::vector<V> w(L);
+    for (int m = 0; m < L; ++m) {
+      cd r = unit_root(m, L);
+      w[m].x = (T)r.real();
+      w[m].y = (T)r.imag();
+    }
+    return w;
+  };
+  std::vector<V> tw = tw_of(N);
+  pint_status s;
+  V* dtw;
+  if ((s = upload(p, &dtw, tw)) != PINT_OK) return s;
+  t.tw_time = dtw;
+  std::vector<T> sc(N), isc(N);
+  const double lk = std::log(p->kappa) / N;
+  for (int i = 0; i < N; ++i) {
+    sc[i] = (T)std::exp(lk * i);
+    isc[i] = (T)(std::exp(-lk * i) / N);
+  }
+  if ((s = upload(p, &t.s, sc)) != PINT_OK) return s;
+  if ((s = upload(p, &t.inv_s, isc)) != PINT_OK) return s;
+  std::vector<V> sig(N / 2 + 1);
+  const double ta = std::pow(p->tau, -p->alpha);
+  for (int j = 0; j <= N / 2; ++j) {
+    sig[j].x = (T)(p->g[j].real() * ta);
+    sig[j].y = (T)(p->g[j].imag() * ta);
+  }
+  V* dsig;
+  if ((s = upload(p, &dsig, sig)) != PINT_OK) return s;
+  t.sigma = dsig;
+  auto lam_of = [](int m) {
+    std::vector<T> l(m);
+    const double h = 1.0 / (m + 1);
+    for (int q = 1; q <= m; ++q) {
+      double sn, cs;
+      sincospi(0.5 * q * h, &sn, &cs);
+      l[q - 1] = (T)(4.0 / (h * h) * sn * sn);
+    }
+    return l;
+  };
+  std::vector<V> twx = tw_of(2 * (p->mx + 1));
+  V* dtwx;
+  if ((s = upload(p, &dtwx, twx)) != PINT_OK) return s;
+  t.tw_x = dtwx;
+  if ((s = upload(p, &t.lam_x, lam_of(p->mx))) != PINT_OK) return s;
+  if (p->dim == 2) {
+    std::vector<V> twy = tw_of(2 * (p->my + 1));
+    V* dtwy;
+    if ((s = upload(p, &dtwy, twy)) != PINT_OK) return s;
+    t.tw_y = dtwy;
+    if ((s = upload(p, &t.lam_y, lam_of(p->my))) != PINT_OK) return s;
+  }
+  return PINT_OK;
+}
+
+pint_status validate(int k, double alpha, double kappa, double tau, int N, const pint_grid* g) {
+  if (!g) return fail(PINT_EINVAL, "grid is NULL");
+  if (k < 1 || k > kMaxK) return fail(PINT_EINVAL, "k must be in 1..6");
+  if (!(alpha > 0.0 && alpha <= 1.0)) return fail(PINT_EINVAL, "alpha must be in (0, 1]");
+  if (!(kappa > 0.0 && kappa < 1.0)) return fail(PINT_EINVAL, "kappa must be in (0, 1)");
+  if (!(tau > 0.0) || !std::isfinite(tau)) return fail(PINT_EINVAL, "tau must be positive");
+  if (!pow2(N) || N < 8 || N > 4096) return fail(PINT_EINVAL, "N must be a power of two in [8, 4096]");
+  if (alpha != 1.0 && N > 2048) return fail(PINT_EINVAL, "CQ (alpha < 1) supports N <= 2048");
+  if (N <= k) return fail(PINT_EINVAL, "N must exceed k");
+  if (g->dim != 1 && g->dim != 2) return fail(PINT_EINVAL, "grid.dim must be 1 or 2");
+  if (!pow2(g->mx + 1) || g->mx < 3 || g->mx > 2047) return fail(PINT_EINVAL, "mx + 1 must be a power of two, 3 <= mx <= 2047");
+  if (g->dim == 2 && (!pow2(g->my + 1) || g->my < 3 || g->my > 2047))
+    return fail(PINT_EINVAL, "my + 1 must be a power of two, 3 <= my <= 2047");
+  return PINT_OK;
+}
+
+void destroy_plan(pint_plan p) {
+  if (!p) return;
+  for (void* q : p->allocs) cudaFree(q);
+  if (p->h_norms) cudaFreeHost(p->h_norms);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan* out) {
+  if (!d || !out) return fail(PINT_EINVAL, "NULL argument");
+  pint_status s = validate(d->k, d->alpha, d->kappa, d->tau, d->N, &d->grid);
+  if (s != PINT_OK) return s;
+  if (d->precision < PINT_FP64 || d->precision > PINT_FP32) return fail(PINT_EINVAL, "bad precision");
+  if (d->eig != PINT_EIG_TRUNC_DFT && d->eig != PINT_EIG_CLOSED_FORM) return fail(PINT_EINVAL, "bad eig variant");
+  pint_plan p = new pint_plan_s();
+  p->k = d->k; p->alpha = d->alpha; p->kappa = d->kappa; p->tau = d->tau; p->N = d->N;
+  p->dim = d->grid.dim; p->mx = d->grid.mx; p->my = d->grid.dim == 2 ? d->grid.my : 1;
+  p->M = p->mx * p->my;
+  p->prec = d->precision; p->eig = d->eig;
+  p->cq = d->alpha != 1.0;
+  const int N = p->N, M = p->M;
+  p->omega.resize(N);
+  time_weights(p->k, p->alpha, N, p->omega.data());
+  table1(p->k, p->a, p->b);
+  eigenvalues(p->k, p->alpha, p->kappa, N, p->eig, p->omega, p->g);
+  const double hx = 1.0 / (p->mx + 1), hy = 1.0 / (p->my + 1);
+  p->gx = 1.0 / (hx * hx);
+  p->gy = p->dim == 2 ? 1.0 / (hy * hy) : 0.0;
+
+  auto bail = [&](pint_status st) { destroy_plan(p); return st; };
+
+  // tables
+  if (p->prec == PINT_FP64) {
+    if ((s = build_tables(p, p->td)) != PINT_OK) return bail(s);
+  } else {
+    if ((s = build_tables(p, p->tf)) != PINT_OK) return bail(s);
+  }
+  const double ta = std::pow(p->tau, -p->alpha);
+  std::vector<double> beta(N);
+  double cs = 0.0;
+  for (int i = 0; i < N; ++i) {
+    cs += p->omega[i];
+    beta[i] = ta * cs;
+  }
+  if ((s = upload(p, &p->beta, beta)) != PINT_OK) return bail(s);
+  if (p->cq) {
+    const int L = 2 * N;
+    std::vector<double2> tw(L);
+    for (int m = 0; m < L; ++m) {
+      cd r = unit_root(m, L);
+      tw[m] = make_double2(r.real(), r.imag());
+    }
+    if ((s = upload(p, &p->tw_2n, tw)) != PINT_OK) return bail(s);
+    std::vector<cd> w(L, cd(0.0, 0.0));
+    for (int i = 0; i < N; ++i) w[i] = p->omega[i];
+    host_fft(w, false);
+    std::vector<double2> lo(L), up(L);
+    for (int j = 0; j < L; ++j) {
+      const int pos = fft_pos(j, L);
+      const cd vlo = w[j] * (ta / L), vup = w[j] * (p->kappa * ta / L);
+      lo[pos] = make_double2(vlo.real(), vlo.imag());
+      up[pos] = make_double2(vup.real(), vup.imag());
+    }
+    if ((s = upload(p, &p->what_lo, lo)) != PINT_OK) return bail(s);
+    if ((s = upload(p, &p->what_up, up)) != PINT_OK) return bail(s);
+    if ((s = dalloc(p, &p->z, (size_t)N * M)) != PINT_OK) return bail(s);
+  }
+  // workspaces
+  const size_t NM = (size_t)N * M, JM = (size_t)(N / 2 + 1) * M;
+  if (p->prec == PINT_MIXED) {
+    if ((s = dalloc(p, &p->Uhi, NM)) != PINT_OK) return bail(s);
+    if ((s = dalloc(p, &p->Ulo, NM)) != PINT_OK) return bail(s);
+    if ((s = dalloc(p, &p->Fhi, NM)) != PINT_OK) return bail(s);
+    if ((s = dalloc(p, &p->Flo, NM)) != PINT_OK) return bail(s);
+  } else if (p->prec == PINT_FP32) {
+    if ((s = dalloc(p, &p->Uhi, NM)) != PINT_OK) return bail(s);
+    if ((s = dalloc(p, &p->Fhi, NM)) != PINT_OK) return bail(s);
+  }
+  {
+    const size_t esz = p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2);
+    unsigned char* S;
+    if ((s = dalloc(p, &S, JM * esz)) != PINT_OK) return bail(s);
+    p->S = S;
+  }
+  if ((s = dalloc(p, &p->norms, 2)) != PINT_OK) return bail(s);
+  if (cudaMallocHost(&p->h_norms, 2 * sizeof(double)) != cudaSuccess) return bail(fail(PINT_ENOMEM, "cudaMallocHost"));
+
+  // tile widths (columns per CTA), shared-memory budget ~96 KB
+  const size_t budget = 96 * 1024;
+  const int cmin_t = std::max(1, kThreads / N);  // every thread needs >= 1 time level
+  p->Ct = pick_cols((size_t)N * sizeof(float2), budget, 32, cmin_t);
+  p->Ctd = pick_cols((size_t)N * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2)), budget, 32, cmin_t);
+  p->Cz = pick_cols((size_t)2 * N * sizeof(double2), 160 * 1024, 16, 1);
+  const size_t ve = p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2);
+  p->Cx = pick_cols((size_t)2 * (p->mx + 1) * ve, budget, 16, 1);
+  p->Cy = pick_cols((size_t)2 * (p->my + 1) * ve, budget, 16, 1);
+  *out = p;
+  return PINT_OK;
+}
+
+extern "C" pint_status pint_plan_create(int k, double alpha, double kappa, double tau, int N,
+                                        const pint_grid* grid, pint_precision precision, pint_plan* out) {
+  if (!grid) return fail(PINT_EINVAL, "grid is NULL");
+  pint_plan_desc d;
+  d.k = k; d.alpha = alpha; d.kappa = kappa; d.tau = tau; d.N = N; d.grid = *grid;
+  d.precision = precision; d.eig = PINT_EIG_TRUNC_DFT;
+  return pint_plan_create_desc(&d, out);
+}
+
+extern "C" pint_status pint_plan_destroy(pint_plan p) {
+  if (!p) return PINT_OK;
+  cudaDeviceSynchronize();
+  destroy_plan(p);
+  return PINT_OK;
+}
+
+extern "C" size_t pint_plan_workspace_bytes(pint_plan p) { return p ? p->bytes : 0; }
+
+extern "C" pint_status pint_form_rhs(pint_plan p, const double* v, const double* f, const double* fderiv,
+                                     double* Fhat, void* stream) {
+  if (!p || !v || !f || !Fhat) return fail(PINT_EINVAL, "NULL argument");
+  if (p->k >= 2 && !fderiv) return fail(PINT_EINVAL, "fderiv is required for k >= 2");
+  RhsArgs a{};
+  a.v = v; a.f = f; a.fd = fderiv; a.F = Fhat; a.beta = p->beta;
+  a.N = p->N; a.M = p->M; a.mx = p->mx; a.dim = p->dim; a.k = p->k;
+  a.gx = p->gx; a.gy = p->gy;
+  for (int n = 0; n < kMaxK - 1; ++n) {
+    a.a[n] = n < 5 ? p->a[n] : 0.0;
+    for (int l = 1; l <= 4; ++l) a.bt[l][n] = p->b[l - 1][n] * std::pow(p->tau, l);
+  }
+  cudaError_t e = launch_rhs(a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rhs kernel");
+  return PINT_OK;
+}
+
+extern "C" pint_status pint_initial_guess(pint_plan p, const double* v, double* U, void* stream) {
+  if (!p || !v || !U) return fail(PINT_EINVAL, "NULL argument");
+  cudaError_t e = launch_bcast_d(v, U, p->N, p->M, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "initial guess kernel");
+  return PINT_OK;
+}
+
+namespace {
+
+void split_ff(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// spatial step on the half spectrum for T (float: MIXED/FP32, double: FP64)
+template <typename T>
+cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
+  const int J = p->N / 2 + 1;
+  if (p->dim == 1) {
+    AxisArgs<T> a{};
+    a.S = p->S; a.n = p->mx; a.lines = J; a.mode = 0; a.P = 1; a.op = 1;
+    a.sigma = t.sigma; a.lam_axis = t.lam_x; a.lam_other = nullptr;
+    a.scale = (T)(2.0 * (p->mx + 1)); a.lines_per_j = 1; a.tw = t.tw_x;
+    a.C = p->Cx; a.ld = p->Cx + 1;
+    return launch_axis(a, st);
+  }
+  AxisArgs<T> ax{};
+  ax.S = p->S; ax.n = p->mx; ax.lines = J * p->my; ax.mode = 0; ax.P = 1; ax.op = 0;
+  ax.tw = t.tw_x; ax.C = p->Cx; ax.ld = p->Cx + 1;
+  cudaError_t e = launch_axis(ax, st);
+  if (e != cudaSuccess) return e;
+  AxisArgs<T> ay{};
+  ay.S = p->S; ay.n = p->my; ay.lines = J * p->mx; ay.mode = 1; ay.P = p->mx; ay.op = 1;
+  ay.sigma = t.sigma; ay.lam_axis = t.lam_y; ay.lam_other = t.lam_x;
+  ay.scale = (T)(-4.0 * (p->mx + 1) * (double)(p->my + 1)); ay.lines_per_j = p->mx;
+  ay.tw = t.tw_y; ay.C = p->Cy; ay.ld = p->Cy + 1;
+  e = launch_axis(ay, st);
+  if (e != cudaSuccess) return e;
+  return launch_axis(ax, st);
+}
+
+// MIXED sweep on the plan's double-float iterate (Uhi/Ulo) and F_hat (Fhi/Flo)
+pint_status sweep_mixed(pint_plan p, cudaStream_t st) {
+  const int N = p->N, M = p->M;
+  if (p->cq) {
+    ToepArgs ta{};
+    ta.Uhi = p->Uhi; ta.Ulo = p->Ulo; ta.ukind = 1; ta.out = p->z; ta.what = p->what_lo;
+    ta.tw = p->tw_2n; ta.N = N; ta.M = M; ta.C = p->Cz; ta.half = 0;
+    cudaError_t e = launch_toeplitz(ta, st);
+    if (e != cudaSuccess) return cuda_fail(e, "toeplitz kernel");
+  }
+  PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
+  ResidFwdArgs r{};
+  r.Uhi = p->Uhi; r.Ulo = p->Ulo; r.Fhi = p->Fhi; r.Flo = p->Flo;
+  r.y = p->cq ? p->z : nullptr;
+  r.S = reinterpret_cast<float2*>(p->S);
+  r.s = p->tf.s; r.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
+  r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Ct;
+  const double ta = std::pow(p->tau, -p->alpha);
+  double c0 = 2.0 * p->gx + 2.0 * p->gy;
+  if (!p->cq) {
+    r.k = p->k;
+    c0 += p->omega[0] * ta;
+    for (int j = 1; j <= p->k; ++j) split_ff(p->omega[j] * ta, r.c_hi[j], r.c_lo[j]);
+  } else {
+    r.k = 0;
+  }
+  split_ff(c0, r.c_hi[0], r.c_lo[0]);
+  split_ff(p->gx, r.gx_hi, r.gx_lo);
+  split_ff(p->gy, r.gy_hi, r.gy_lo);
+  cudaError_t e = launch_resid_fwd(r, st);
+  if (e != cudaSuccess) return cuda_fail(e, "residual kernel");
+  e = spatial<float>(p, p->tf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "spatial kernel");
+  InvUpdArgs u{};
+  u.S = reinterpret_cast<const float2*>(p->S); u.Uhi = p->Uhi; u.Ulo = p->Ulo;
+  u.inv_s = p->tf.inv_s; u.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
+  u.N = N; u.M = M; u.C = p->Ct; u.norms = p->norms;
+  e = launch_inv_upd(u, st);
+  if (e != cudaSuccess) return cuda_fail(e, "update kernel");
+  return PINT_OK;
+}
+
+// FP64 / FP32 direct-form sweep: Uout = P^-1 (F + (P - K) Uin)
+template <typename T>
+pint_status sweep_direct(pint_plan p, const DevTables<T>& t, const T* F, const T* Uin, T* Uout,
+                         cudaStream_t st) {
+  const int N = p->N, M = p->M;
+  if (p->cq) {
+    ToepArgs ta{};
+    if (sizeof(T) == 8) { ta.Ud = reinterpret_cast<const double*>(Uin); ta.ukind = 0; }
+    else { ta.Uf = reinterpret_cast<const float*>(Uin); ta.ukind = 2; }
+    ta.out = p->z; ta.what = p->what_up; ta.tw = p->tw_2n; ta.N = N; ta.M = M; ta.C = p->Cz; ta.half = 1;
+    cudaError_t e = launch_toeplitz(ta, st);
+    if (e != cudaSuccess) return cuda_fail(e, "toeplitz kernel");
+  }
+  PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
+  DirectFwdArgs<T> f{};
+  f.F = F; f.U = Uin; f.z = p->cq ? p->z : nullptr; f.S = p->S; f.s = t.s; f.tw = t.tw_time;
+  f.N = N; f.M = M; f.C = p->Ctd; f.k = p->cq ? 0 : p->k;
+  const double kt = p->kappa * std::pow(p->tau, -p->alpha);
+  for (int j = 0; j <= p->k; ++j) f.kw[j] = (T)(kt * p->omega[j]);
+  cudaError_t e = launch_direct_fwd(f, st);
+  if (e != cudaSuccess) return cuda_fail(e, "direct fwd kernel");
+  e = spatial<T>(p, t, st);
+  if (e != cudaSuccess) return cuda_fail(e, "spatial kernel");
+  DirectInvArgs<T> iv{};
+  iv.S = p->S; iv.Uold = Uin; iv.Uout = Uout; iv.inv_s = t.inv_s; iv.tw = t.tw_time;
+  iv.N = N; iv.M = M; iv.C = p->Ctd; iv.norms = p->norms;
+  e = launch_direct_inv(iv, st);
+  if (e != cudaSuccess) return cuda_fail(e, "direct inv kernel");
+  return PINT_OK;
+}
+
+pint_status read_norms(pint_plan p, cudaStream_t st, double* upd) {
+  PINT_CUDA(cudaMemcpyAsync(p->h_norms, p->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PINT_CUDA(cudaStreamSynchronize(st));
+  const double c2 = p->h_norms[0], u2 = p->h_norms[1];
+  *upd = u2 > 0.0 ? std::sqrt(c2 / u2) : std::sqrt(c2);
+  return PINT_OK;
+}
+
+// sweep on FP64 user buffers
+pint_status sweep_user(pint_plan p, const double* Fhat, const double* Uin, double* Uout, cudaStream_t st) {
+  const size_t NM = (size_t)p->N * p->M;
+  cudaError_t e;
+  if (p->prec == PINT_FP64) return sweep_direct<double>(p, p->td, Fhat, Uin, Uout, st);
+  if (p->prec == PINT_MIXED) {
+    if ((e = launch_d2ff(Fhat, p->Fhi, p->Flo, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+    if ((e = launch_d2ff(Uin, p->Uhi, p->Ulo, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+    pint_status s = sweep_mixed(p, st);
+    if (s != PINT_OK) return s;
+    if ((e = launch_ff2d(p->Uhi, p->Ulo, Uout, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+    return PINT_OK;
+  }
+  if ((e = launch_d2f(Fhat, p->Fhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+  if ((e = launch_d2f(Uin, p->Uhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+  pint_status s = sweep_direct<float>(p, p->tf, p->Fhi, p->Uhi, p->Uhi, st);
+  if (s != PINT_OK) return s;
+  if ((e = launch_f2d(p->Uhi, Uout, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+  return PINT_OK;
+}
+
+}  // namespace
+
+extern "C" pint_status pint_wr_sweep(pint_plan p, const double* Fhat, const double* U_prev, double* U_next,
+                                     double* upd_rel, void* stream) {
+  if (!p || !Fhat || !U_prev || !U_next) return fail(PINT_EINVAL, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  pint_status s = sweep_user(p, Fhat, U_prev, U_next, st);
+  if (s != PINT_OK) return s;
+  if (upd_rel) return read_norms(p, st, upd_rel);
+  return PINT_OK;
+}
+
+extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, double tol, int max_sweeps,
+                                  int* sweeps_out, double* upd_rel_out, void* stream) {
+  if (!p || !Fhat || !U) return fail(PINT_EINVAL, "NULL argument");
+  if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t NM = (size_t)p->N * p->M;
+  cudaError_t e;
+  if (p->prec == PINT_MIXED) {
+    if ((e = launch_d2ff(Fhat, p->Fhi, p->Flo, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+    if ((e = launch_d2ff(U, p->Uhi, p->Ulo, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+  } else if (p->prec == PINT_FP32) {
+    if ((e = launch_d2f(Fhat, p->Fhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+    if ((e = launch_d2f(U, p->Uhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+  }
+  double prev = -1.0, upd = 0.0;
+  int m = 0;
+  bool done = false;
+  pint_status s = PINT_OK;
+  while (m < max_sweeps && !done) {
+    if (p->prec == PINT_MIXED) s = sweep_mixed(p, st);
+    else if (p->prec == PINT_FP64) s = sweep_direct<double>(p, p->td, Fhat, U, U, st);
+    else s = sweep_direct<float>(p, p->tf, p->Fhi, p->Uhi, p->Uhi, st);
+    if (s != PINT_OK) return s;
+    ++m;
+    if ((s = read_norms(p, st, &upd)) != PINT_OK) return s;
+    if (m == 1) {
+      done = upd <= 0.01 * tol;
+    } else {
+      const double q = prev > 0.0 ? upd / prev : 0.0;
+      if (q < 1.0) done = upd * q / (1.0 - q) <= tol;
+      else done = upd <= tol;
+    }
+    prev = upd;
+  }
+  if (p->prec == PINT_MIXED) {
+    if ((e = launch_ff2d(p->Uhi, p->Ulo, U, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+  } else if (p->prec == PINT_FP32) {
+    if ((e = launch_f2d(p->Uhi, U, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+  }
+  if (sweeps_out) *sweeps_out = m;
+  if (upd_rel_out) *upd_rel_out = upd;
+  if (!done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
+  return PINT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host-only queries and diagnostics
+// ---------------------------------------------------------------------------
+extern "C" pint_status pint_time_weights(int k, double alpha, int n, double* omega) {
+  if (k < 1 || k > kMaxK || !(alpha > 0.0 && alpha <= 1.0) || n < 0 || (!omega && n > 0))
+    return fail(PINT_EINVAL, "bad arguments");
+  time_weights(k, alpha, n, omega);
+  return PINT_OK;
+}
+
+extern "C" pint_status pint_correction_coefficients(int k, double* a, double* b) {
+  if (k < 1 || k > kMaxK || !a || !b) return fail(PINT_EINVAL, "bad arguments");
+  double bb[4][5];
+  table1(k, a, bb);
+  for (int l = 0; l < 4; ++l)
+    for (int n = 0; n < 5; ++n) b[l * 5 + n] = bb[l][n];
+  return PINT_OK;
+}
+
+extern "C" pint_status pint_circulant_eigenvalues(int k, double alpha, double kappa, int N,
+                                                  pint_eig_variant eig, double* re, double* im) {
+  if (k < 1 || k > kMaxK || !(alpha > 0.0 && alpha <= 1.0) || !(kappa > 0.0 && kappa < 1.0) ||
+      !pow2(N) || N <= k || !re || !im)
+    return fail(PINT_EINVAL, "bad arguments");
+  std::vector<double> w(N);
+  time_weights(k, alpha, N, w.data());
+  std::vector<cd> g;
+  eigenvalues(k, alpha, kappa, N, eig, w, g);
+  for (int j = 0; j < N; ++j) {
+    re[j] = g[j].real();
+    im[j] = g[j].imag();
+  }
+  return PINT_OK;
+}
+
+extern "C" const char* pint_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* pint_status_string(pint_status s) {
+  switch (s) {
+    case PINT_OK: return "PINT_OK";
+    case PINT_EINVAL: return "PINT_EINVAL";
+    case PINT_ENOMEM: return "PINT_ENOMEM";
+    case PINT_ECUDA: return "PINT_ECUDA";
+    case PINT_ENOTCONV: return "PINT_ENOTCONV";
+    case PINT_ETIMEOUT: return "PINT_ETIMEOUT";
+    case PINT_EAGAIN: return "PINT_EAGAIN";
+    case PINT_EBUDGET: return "PINT_EBUDGET";
+    case PINT_ENOTFOUND: return "PINT_ENOTFOUND";
+  }
+  return "unknown";
+}
+
+extern "C" const char* pint_version(void) { return "pint-gb300 0.1 (sm_103a)"; }
+
+extern "C" pint_status pint_set_profiling(int enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = enable != 0;
+  return PINT_OK;
+}
+
+extern "C" int pint_kernel_stats(int max, const char** names, int* launches, double* total_ms, int reset) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::vector<const char*> nm;
+  std::vector<int> cnt;
+  std::vector<double> tot;
+  for (const ProfRec& r : g_prof_recs) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    size_t i = 0;
+    for (; i < nm.size(); ++i)
+      if (std::strcmp(nm[i], r.name) == 0) break;
+    if (i == nm.size()) {
+      nm.push_back(r.name);
+      cnt.push_back(0);
+      tot.push_back(0.0);
+    }
+    cnt[i] += 1;
+    tot[i] += ms;
+  }
+  const int n = (int)nm.size();
+  for (int i = 0; i < n && i < max; ++i) {
+    if (names) names[i] = nm[i];
+    if (launches) launches[i] = cnt[i];
+    if (total_ms) total_ms[i] = tot[i];
+  }
+  if (reset) {
+    for (const ProfRec& r : g_prof_recs) {
+      g_prof_pool.push_back(r.a);
+      g_prof_pool.push_back(r.b);
+    }
+    g_prof_recs.clear();
+  }
+  return n;
+}

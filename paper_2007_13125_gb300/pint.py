@@ -1,0 +1,294 @@
+"""ctypes binding of include/pint.h: argument marshalling only.
+
+Every function keeps the C name (without the ``pint_`` prefix where it is a method of
+``Plan``). Device arrays are passed as torch CUDA tensors (float64, contiguous), whose
+``data_ptr()`` goes straight to the library; streams are torch.cuda.Stream objects or
+raw handles. No arithmetic of the method happens in Python.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpint.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "pint.h")
+
+PINT_OK, PINT_EINVAL, PINT_ENOMEM, PINT_ECUDA, PINT_ENOTCONV = 0, 1, 2, 3, 4
+PINT_ETIMEOUT, PINT_EAGAIN, PINT_EBUDGET, PINT_ENOTFOUND = 5, 6, 7, 8
+PINT_FP64, PINT_MIXED, PINT_FP32 = 0, 1, 2
+PINT_EIG_TRUNC_DFT, PINT_EIG_CLOSED_FORM = 0, 1
+PRECISIONS = {"fp64": PINT_FP64, "mixed": PINT_MIXED, "fp32": PINT_FP32}
+
+
+class PintError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("mx", ctypes.c_int), ("my", ctypes.c_int)]
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("alpha", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("tau", ctypes.c_double), ("N", ctypes.c_int), ("grid", _Grid),
+                ("precision", ctypes.c_int), ("eig", ctypes.c_int)]
+
+
+class _Req(ctypes.Structure):
+    _fields_ = [("desc", _Desc), ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("sweeps", ctypes.c_int), ("upd_rel", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+
+
+def lib():
+    """Load libpint.so (raises if it has not been built: there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "pint_plan_create": (_I, [_I, _D, _D, _D, _I, ctypes.POINTER(_Grid), _I, ctypes.POINTER(_P)]),
+        "pint_plan_create_desc": (_I, [ctypes.POINTER(_Desc), ctypes.POINTER(_P)]),
+        "pint_plan_destroy": (_I, [_P]),
+        "pint_plan_workspace_bytes": (ctypes.c_size_t, [_P]),
+        "pint_form_rhs": (_I, [_P, _P, _P, _P, _P, _P]),
+        "pint_initial_guess": (_I, [_P, _P, _P, _P]),
+        "pint_wr_sweep": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D), _P]),
+        "pint_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+        "pint_time_weights": (_I, [_I, _D, _I, ctypes.POINTER(_D)]),
+        "pint_correction_coefficients": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+        "pint_circulant_eigenvalues": (_I, [_I, _D, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+        "pint_last_error": (ctypes.c_char_p, []),
+        "pint_status_string": (ctypes.c_char_p, [_I]),
+        "pint_version": (ctypes.c_char_p, []),
+        "pint_set_profiling": (_I, [_I]),
+        "pint_kernel_stats": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I),
+                                   ctypes.POINTER(_D), _I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    for name, (res, args) in _server_sig().items():
+        if hasattr(L, name):
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def _server_sig():
+    return {
+        "pint_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
+        "pint_server_destroy": (_I, [_P]),
+        "pint_submit": (_I, [_P, ctypes.POINTER(_Req), _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+        "pint_poll": (_I, [_P, ctypes.c_uint64, _I, _P, ctypes.POINTER(_Info)]),
+        "pint_server_stats": (_I, [_P, ctypes.POINTER(_D)]),
+    }
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/pint.h."""
+    text = open(HEADER_PATH).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pint_[a-z0-9_]+)\s*\(", text)))
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().pint_status_string(s).decode()
+    except Exception:  # library not loadable: still format the number
+        return f"status {s}"
+
+
+def last_error() -> str:
+    return lib().pint_last_error().decode()
+
+
+def check(status: int):
+    if status != PINT_OK:
+        raise PintError(status, last_error())
+
+
+def _ptr(t):
+    """data_ptr of a CUDA float64 contiguous tensor (or None)."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ---- host-only queries ----
+def time_weights(k: int, alpha: float, n: int) -> np.ndarray:
+    out = np.zeros(n)
+    check(lib().pint_time_weights(k, alpha, n, out.ctypes.data_as(ctypes.POINTER(_D))))
+    return out
+
+
+def correction_coefficients(k: int):
+    a = np.zeros(5)
+    b = np.zeros(20)
+    check(lib().pint_correction_coefficients(k, a.ctypes.data_as(ctypes.POINTER(_D)),
+                                             b.ctypes.data_as(ctypes.POINTER(_D))))
+    return a, b.reshape(4, 5)
+
+
+def circulant_eigenvalues(k: int, alpha: float, kappa: float, N: int, eig: int = PINT_EIG_TRUNC_DFT):
+    re_, im_ = np.zeros(N), np.zeros(N)
+    check(lib().pint_circulant_eigenvalues(k, alpha, kappa, N, eig,
+                                           re_.ctypes.data_as(ctypes.POINTER(_D)),
+                                           im_.ctypes.data_as(ctypes.POINTER(_D))))
+    return re_ + 1j * im_
+
+
+def set_profiling(on: bool):
+    check(lib().pint_set_profiling(1 if on else 0))
+
+
+def kernel_stats(reset: bool = True) -> dict:
+    n = 64
+    names = (ctypes.c_char_p * n)()
+    launches = (_I * n)()
+    tot = (_D * n)()
+    k = lib().pint_kernel_stats(n, names, launches, tot, 1 if reset else 0)
+    return {names[i].decode(): (launches[i], tot[i]) for i in range(min(k, n))}
+
+
+class Plan:
+    """Owns a pint_plan handle."""
+
+    def __init__(self, k, alpha, kappa, tau, N, dim, mx, my=1, precision="mixed",
+                 eig=PINT_EIG_TRUNC_DFT):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        d = _Desc(k, float(alpha), float(kappa), float(tau), int(N), _Grid(dim, mx, my if dim == 2 else 1),
+                  prec, eig)
+        h = _P()
+        check(lib().pint_plan_create_desc(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.k, self.alpha, self.kappa, self.tau, self.N = k, alpha, kappa, tau, N
+        self.dim, self.mx, self.my = dim, mx, (my if dim == 2 else 1)
+        self.M = self.mx * self.my
+        self.precision = prec
+
+    @classmethod
+    def for_problem(cls, p, precision="mixed", eig=PINT_EIG_TRUNC_DFT):
+        return cls(p.k, p.alpha, p.kappa, p.tau, p.N, p.dim, p.mx, p.my, precision, eig)
+
+    def close(self):
+        if self.handle:
+            lib().pint_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self) -> int:
+        return int(lib().pint_plan_workspace_bytes(self.handle))
+
+    def form_rhs(self, v, f, fderiv, Fhat, stream=None):
+        check(lib().pint_form_rhs(self.handle, _ptr(v), _ptr(f), _ptr(fderiv) if fderiv is not None and fderiv.numel() else None,
+                                  _ptr(Fhat), _stream(stream)))
+
+    def initial_guess(self, v, U, stream=None):
+        check(lib().pint_initial_guess(self.handle, _ptr(v), _ptr(U), _stream(stream)))
+
+    def wr_sweep(self, Fhat, U_prev, U_next, stream=None, want_update=True) -> float | None:
+        upd = _D(0.0)
+        check(lib().pint_wr_sweep(self.handle, _ptr(Fhat), _ptr(U_prev), _ptr(U_next),
+                                  ctypes.byref(upd) if want_update else None, _stream(stream)))
+        return upd.value if want_update else None
+
+    def solve(self, Fhat, U, tol=1e-10, max_sweeps=50, stream=None, raise_on_notconv=True):
+        sweeps = _I(0)
+        upd = _D(0.0)
+        st = lib().pint_solve(self.handle, _ptr(Fhat), _ptr(U), float(tol), int(max_sweeps),
+                              ctypes.byref(sweeps), ctypes.byref(upd), _stream(stream))
+        if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
+            raise PintError(st, last_error())
+        return st, sweeps.value, upd.value
+
+
+class Server:
+    """Owns a pint_server handle (continuous-batching solve server)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 16):
+        h = _P()
+        check(lib().pint_server_create(ctypes.c_size_t(int(hbm_budget_bytes)), int(max_active),
+                                       ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().pint_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, p, v, f, fderiv, tol=1e-8, max_sweeps=50, precision="mixed"):
+        """v, f, fderiv: host float64 numpy arrays (copied at submit)."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        d = _Desc(p.k, float(p.alpha), float(p.kappa), float(p.tau), int(p.N),
+                  _Grid(p.dim, p.mx, p.my if p.dim == 2 else 1), prec, PINT_EIG_TRUNC_DFT)
+        req = _Req(d, float(tol), int(max_sweeps))
+        t = ctypes.c_uint64(0)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        fd = np.ascontiguousarray(fderiv, dtype=np.float64)
+        check(lib().pint_submit(self.handle, ctypes.byref(req), v.ctypes.data_as(_P),
+                                f.ctypes.data_as(_P), fd.ctypes.data_as(_P) if fd.size else None,
+                                ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int, out: np.ndarray | None, timeout_us: int = 0):
+        info = _Info()
+        st = lib().pint_poll(self.handle, ctypes.c_uint64(ticket), int(timeout_us),
+                             out.ctypes.data_as(_P) if out is not None else None, ctypes.byref(info))
+        return st, info
+
+    def stats(self) -> dict:
+        v = (_D * 8)()
+        check(lib().pint_server_stats(self.handle, v))
+        keys = ["completed", "active", "queued", "hbm_in_use", "dof_done", "sweeps_done", "busy_s", "peak_hbm"]
+        return {k: v[i] for i, k in enumerate(keys)}

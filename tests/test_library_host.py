@@ -1,0 +1,68 @@
+"""The C-ABI library without a GPU: it loads, exports every function include/pint.h declares,
+and its host-side constant tables agree with the oracle."""
+import numpy as np
+import pytest
+
+from oracle import bdf
+
+
+@pytest.fixture(scope="module")
+def pint():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2007_13125_gb300 import pint as P
+    return P
+
+
+def test_exports_every_declared_symbol(pint):
+    L = pint.lib()
+    names = pint.header_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing
+
+
+def test_time_weights_match_oracle(pint):
+    for k in range(1, 7):
+        for alpha in (1.0, 0.3, 0.5, 0.7):
+            n = 512
+            got = pint.time_weights(k, alpha, n)
+            ref = bdf.cq_weights(k, alpha, n)
+            assert np.max(np.abs(got - ref)) < 1e-13, (k, alpha)
+
+
+def test_correction_table_matches_oracle(pint):
+    for k in range(1, 7):
+        a, b = pint.correction_coefficients(k)
+        assert np.allclose(a[: k - 1], bdf.correction_a(k), rtol=0, atol=1e-16)
+        assert np.all(a[k - 1:] == 0)
+        if k >= 3:
+            assert np.allclose(b[: k - 2, : k - 1], bdf.correction_b(k), rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("k,alpha,N", [(1, 1.0, 16), (4, 1.0, 64), (6, 1.0, 32), (2, 0.5, 64), (3, 0.3, 128)])
+def test_eigenvalues_match_oracle_definition(pint, k, alpha, N):
+    kappa = 0.05
+    got = pint.circulant_eigenvalues(k, alpha, kappa, N)
+    ref = bdf.circulant_eigenvalues(bdf.cq_weights(k, alpha, N), kappa, N)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_closed_form_eigenvalues(pint):
+    N, kappa = 64, 0.1
+    got = pint.circulant_eigenvalues(3, 0.5, kappa, N, pint.PINT_EIG_CLOSED_FORM)
+    z = kappa ** (1.0 / N) * np.exp(-2j * np.pi * np.arange(N) / N)
+    ref = np.exp(0.5 * np.log(bdf.delta_k(3, z)))
+    assert np.max(np.abs(got - ref)) < 1e-13
+
+
+def test_invalid_plans_rejected_before_device_use(pint):
+    # validation runs before any CUDA call, so these fail cleanly without a GPU
+    for args in [(0, 1.0, 0.1, 0.01, 64, 1, 63), (7, 1.0, 0.1, 0.01, 64, 1, 63),
+                 (2, 0.0, 0.1, 0.01, 64, 1, 63), (2, 1.0, 0.0, 0.01, 64, 1, 63),
+                 (2, 1.0, 0.1, 0.0, 64, 1, 63), (2, 1.0, 0.1, 0.01, 48, 1, 63),
+                 (2, 1.0, 0.1, 0.01, 64, 1, 62), (2, 1.0, 0.1, 0.01, 64, 3, 63)]:
+        with pytest.raises(pint.PintError) as e:
+            pint.Plan(*args)
+        assert e.value.status == pint.PINT_EINVAL
+    assert "status" in pint.status_string(1) or pint.status_string(1) == "PINT_EINVAL"
