@@ -72,6 +72,9 @@ typedef enum { PINT_FP64 = 0, PINT_MIXED = 1, PINT_FP32 = 2 } pint_precision;
  *              printed in eq. (3.11) (weights omega_0..omega_{N-1}).
  * CLOSED_FORM: g_j = delta_k(kappa^{1/N} e^{-2 pi i j/N})^alpha (principal branch). */
 typedef enum { PINT_EIG_TRUNC_DFT = 0, PINT_EIG_CLOSED_FORM = 1 } pint_eig_variant;
+/* CLOSED_FORM with alpha < 1 is accepted only with PINT_MIXED: the residual-correction form has
+ * the sequential solution as its fixed point for any preconditioner, whereas the printed direct
+ * form's kappa-term (eq. (3.12)) belongs to the truncated matrix (PINT_EINVAL otherwise). */
 
 typedef struct {
   int dim;  /* 1 or 2 */
@@ -88,6 +91,9 @@ typedef struct {
   pint_grid grid;
   pint_precision precision;
   pint_eig_variant eig;
+  int ysolve;             /* 2D y-direction solver of the shifted systems: 0 = choose by timing
+                             both at plan creation (cached per shape), 1 = sine transform,
+                             2 = tridiagonal (FP32 inner solves only; FP64 uses 1) */
 } pint_plan_desc;
 
 /* Build a plan: FP64 constant tables (BDF / CQ weights omega_j of eq. (2.2) / eq. (3.2) --

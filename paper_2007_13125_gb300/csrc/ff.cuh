@@ -69,14 +69,47 @@ __device__ __forceinline__ ff ff_add_f(ff x, float c) {
   return r;
 }
 
-// exact split of a double into hi = rn(x), lo = rn(x - hi)
+// Split a double into hi + lo with integer operations only. On GB300 every FP64<->FP32
+// conversion runs at the FP64 rate (~1/70 of FP32), so the bit patterns are taken apart
+// directly: hi = x rounded to 24 significant bits (nearest, ties to even), exact as a float;
+// the remainder x - hi is an integer of at most 29 bits in units of 2^(e-1075), converted to
+// float (rounded: lo keeps 24 of those bits) and scaled: |hi + lo - x| <= 2^-48 |x| for
+// |x| in [2^-74, 2^127). Below 2^-74 lo is dropped (hi stays exact down to 2^-126) and below
+// 2^-126 the result is 0: absolute errors under 1e-37, far below every term of the method.
 __device__ __forceinline__ ff ff_from_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+  const int e = (int)(mag >> 52);
   ff r;
-  r.hi = __double2float_rn(x);
-  r.lo = __double2float_rn(x - (double)r.hi);
+  if (e < 897) { r.hi = 0.f; r.lo = 0.f; return r; }
+  const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
+  // round away the low 29 mantissa bits (nearest-even); a carry moves into the exponent
+  const unsigned long long rm = (mag + 0x0FFFFFFFull + ((mag >> 29) & 1ull)) & ~0x1FFFFFFFull;
+  const unsigned int er = (unsigned int)(rm >> 52);
+  const unsigned int fm = (unsigned int)(rm >> 29) & 0x7FFFFFu;
+  r.hi = __uint_as_float(sgn | ((er - 896u) << 23) | fm);
+  // remainder in units of 2^(e-1075); |d| <= 2^28. Bit-pattern differences equal value
+  // differences in those units even when the rounding carried into the exponent.
+  const int d = (int)((long long)mag - (long long)rm);
+  const int se = e - 948;  // biased float exponent of 2^(e-1075)
+  const float scale = se >= 1 ? __uint_as_float((unsigned int)se << 23) : 0.f;
+  const float lo = __int2float_rn(d) * scale;
+  r.lo = sgn ? -lo : lo;
   return r;
 }
 
-__device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
+// Exact float -> double by bit construction (no FP64 conversion instruction).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int ex = (u >> 23) & 0xFFu;
+  if (ex == 0) return 0.0;  // zero (float subnormals flushed)
+  const unsigned long long hi = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                ((unsigned long long)(ex + 896u) << 52) |
+                                ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)hi);
+}
+
+// hi + lo as a double: two exact bit constructions and one FP64 add.
+__device__ __forceinline__ double ff_to_double(ff x) { return f2d_bits(x.hi) + f2d_bits(x.lo); }
 
 }  // namespace pint

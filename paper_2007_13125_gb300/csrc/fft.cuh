@@ -53,15 +53,19 @@ __host__ __device__ constexpr double cos16(int m) {
 }
 __host__ __device__ constexpr double sin16(int m) { return cos16((m + 12) & 15); }
 
-// v * exp(DIR * 2 pi i m / 16), DIR = -1 (forward) or +1
-template <int DIR, typename V>
-__device__ __forceinline__ V twid16(V v, int m) {
+// v * exp(DIR * 2 pi i M / 16), DIR = -1 (forward) or +1, M a compile-time constant
+template <int M, int DIR, typename V>
+__device__ __forceinline__ V twid16(V v) {
   using T = decltype(v.x);
-  if (m == 0) return v;
-  if (m == 4) return DIR < 0 ? mk(v.y, -v.x) : mk(-v.y, v.x);
-  const T c = (T)cos16(m);
-  const T s = (T)(DIR * sin16(m));
-  return mk(v.x * c - v.y * s, v.x * s + v.y * c);
+  if constexpr (M == 0) {
+    return v;
+  } else if constexpr (M == 4) {
+    return DIR < 0 ? mk(v.y, -v.x) : mk(-v.y, v.x);
+  } else {
+    constexpr T c = (T)cos16(M);
+    constexpr T s = (T)(DIR * sin16(M));
+    return mk(v.x * c - v.y * s, v.x * s + v.y * c);
+  }
 }
 
 __host__ __device__ constexpr int ilog2c(int r) { return r <= 1 ? 0 : 1 + ilog2c(r >> 1); }
@@ -69,124 +73,150 @@ __host__ __device__ constexpr int brev(int i, int bits) {
   return bits == 0 ? 0 : ((i & 1) << (bits - 1)) | brev(i >> 1, bits - 1);
 }
 
-// One radix-2 decimation-in-time stage of butterfly span LEN over a register array;
-// recursion on LEN keeps every index a compile-time constant (the array stays in registers).
-template <int LEN, int R, int DIR, typename V>
-__device__ __forceinline__ void dit_stage(V (&y)[R]) {
-#pragma unroll
-  for (int i = 0; i < R; i += LEN) {
-#pragma unroll
-    for (int j = 0; j < LEN / 2; ++j) {
-      V u = y[i + j];
-      V t = twid16<DIR>(y[i + j + LEN / 2], j * (16 / LEN));
-      y[i + j] = cadd(u, t);
-      y[i + j + LEN / 2] = csub(u, t);
+// Butterflies of one radix-2 decimation-in-time stage of span LEN, block start I, offset J.
+// Template recursion keeps every array index a compile-time constant (registers only).
+template <int LEN, int I, int J, int R, int DIR, typename V>
+__device__ __forceinline__ void dit_bfly(V (&y)[R]) {
+  if constexpr (I < R) {
+    if constexpr (J < LEN / 2) {
+      const V u = y[I + J];
+      const V t = twid16<J * (16 / LEN), DIR>(y[I + J + LEN / 2]);
+      y[I + J] = cadd(u, t);
+      y[I + J + LEN / 2] = csub(u, t);
+      dit_bfly<LEN, I, J + 1, R, DIR>(y);
+    } else {
+      dit_bfly<LEN, I + LEN, 0, R, DIR>(y);
     }
   }
+}
+
+template <int LEN, int R, int DIR, typename V>
+__device__ __forceinline__ void dit_stage(V (&y)[R]) {
+  dit_bfly<LEN, 0, 0, R, DIR>(y);
   if constexpr (LEN < R) dit_stage<LEN * 2, R, DIR>(y);
+}
+
+template <int I, int R, typename V>
+__device__ __forceinline__ void brev_copy(V (&y)[R], const V (&x)[R]) {
+  if constexpr (I < R) {
+    constexpr int J = brev(I, ilog2c(R));
+    y[J] = x[I];
+    brev_copy<I + 1, R>(y, x);
+  }
 }
 
 // y_q = sum_r x_r exp(DIR 2 pi i r q / R), natural order in and out; R <= 16.
 template <int R, int DIR, typename V>
 __device__ __forceinline__ void dft_reg(V (&x)[R]) {
-  constexpr int B = ilog2c(R);
   V y[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) y[brev(i, B)] = x[i];
+  brev_copy<0, R>(y, x);
   if constexpr (R > 1) dit_stage<2, R, DIR>(y);
 #pragma unroll
   for (int i = 0; i < R; ++i) x[i] = y[i];
 }
 
-// Radix schedule: the remainder radix first, then 16s.
+// Radix schedule: np = ceil(log2 L / 4) passes with the bits spread evenly (first passes
+// take the extra bit), each radix in {2, 4, 8, 16}.
 __host__ __device__ inline int fft_npass(int L) {
-  int e = ilog2c(L);
-  return e / 4 + ((e % 4) ? 1 : 0);
+  const int e = ilog2c(L);
+  return (e + 3) / 4;
 }
-__host__ __device__ inline int fft_radix(int L, int pass) {
-  int e = ilog2c(L);
-  int rem = e % 4;
-  if (rem && pass == 0) return 1 << rem;
-  return 16;
+__host__ __device__ inline int fft_logradix(int L, int pass) {
+  const int e = ilog2c(L);
+  const int np = (e + 3) / 4;
+  return e / np + (pass < e % np ? 1 : 0);
 }
+__host__ __device__ inline int fft_radix(int L, int pass) { return 1 << fft_logradix(L, pass); }
 
 // position of frequency j in the output of the forward transform
 __host__ __device__ inline int fft_pos(int j, int L) {
-  int np = fft_npass(L);
-  int p = 0, Ls = L;
+  const int np = fft_npass(L);
+  int p = 0, logLs = ilog2c(L);
   for (int i = 0; i < np; ++i) {
-    int R = fft_radix(L, i);
-    int q = j % R;
-    j /= R;
-    Ls /= R;
-    p += q * Ls;
+    const int lr = fft_logradix(L, i);
+    const int q = j & ((1 << lr) - 1);
+    j >>= lr;
+    logLs -= lr;
+    p += q << logLs;
   }
   return p;
 }
 
-// One pass of radix R at sub-length Ls. DIR < 0: forward (gather natural stride,
-// DFT, twiddle, scatter). DIR > 0: its conjugate transpose.
-template <int R, int DIR, typename V>
-__device__ __forceinline__ void fft_pass(V* X, int ld, int C, int L, int Ls, const V* tw) {
-  const int S = Ls / R;
-  const int items = (L / R) * C;
-  const int tstep = L / Ls;  // W_Ls^e = W_L^{e * tstep}
+// fill perm[j] = fft_pos(j, L), j < L (cooperatively, by the whole block)
+__device__ __forceinline__ void fft_perm_table(unsigned short* perm, int L) {
+  for (int j = threadIdx.x; j < L; j += blockDim.x) perm[j] = (unsigned short)fft_pos(j, L);
+}
+
+// One pass of radix R = 2^LR at sub-length Ls = 2^logLs on a tile of C = 2^logC columns.
+// DIR < 0: forward (gather natural stride, DFT, twiddle, scatter). DIR > 0: its conjugate
+// transpose. All index arithmetic is shifts and masks.
+template <int LR, int DIR, typename V>
+__device__ __forceinline__ void fft_pass(V* X, int ld, int logC, int logL, int logLs, const V* tw) {
+  constexpr int R = 1 << LR;
+  const int logS = logLs - LR;
+  const int Smask = (1 << logS) - 1;
+  const int items = 1 << (logL - LR + logC);
+  const int tshift = logL - logLs;  // W_Ls^e = W_L^{e << tshift}
+  const int Lmask = (1 << logL) - 1;
+  const int Cmask = (1 << logC) - 1;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int c = it % C;
-    const int g = it / C;
-    const int b = g / S;
-    const int n2 = g - b * S;
-    const int base = b * Ls + n2;
+    const int c = it & Cmask;
+    const int g = it >> logC;
+    const int n2 = g & Smask;
+    const int base = ((g >> logS) << logLs) + n2;
     V x[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = X[(base + r * S) * ld + c];
+    for (int r = 0; r < R; ++r) x[r] = X[(base + (r << logS)) * ld + c];
     if (DIR < 0) {
       dft_reg<R, -1>(x);
 #pragma unroll
-      for (int q = 1; q < R; ++q) x[q] = cmul(x[q], tw[(n2 * q * tstep) & (L - 1)]);
+      for (int q = 1; q < R; ++q) x[q] = cmul(x[q], tw[((n2 * q) << tshift) & Lmask]);
     } else {
 #pragma unroll
-      for (int q = 1; q < R; ++q) x[q] = cmulc(x[q], tw[(n2 * q * tstep) & (L - 1)]);
+      for (int q = 1; q < R; ++q) x[q] = cmulc(x[q], tw[((n2 * q) << tshift) & Lmask]);
       dft_reg<R, 1>(x);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) X[(base + r * S) * ld + c] = x[r];
+    for (int r = 0; r < R; ++r) X[(base + (r << logS)) * ld + c] = x[r];
   }
 }
 
 template <int DIR, typename V>
-__device__ __forceinline__ void fft_pass_dispatch(int R, V* X, int ld, int C, int L, int Ls, const V* tw) {
-  switch (R) {
-    case 2: fft_pass<2, DIR>(X, ld, C, L, Ls, tw); break;
-    case 4: fft_pass<4, DIR>(X, ld, C, L, Ls, tw); break;
-    case 8: fft_pass<8, DIR>(X, ld, C, L, Ls, tw); break;
-    default: fft_pass<16, DIR>(X, ld, C, L, Ls, tw); break;
+__device__ __forceinline__ void fft_pass_dispatch(int lr, V* X, int ld, int logC, int logL, int logLs,
+                                                  const V* tw) {
+  switch (lr) {
+    case 1: fft_pass<1, DIR>(X, ld, logC, logL, logLs, tw); break;
+    case 2: fft_pass<2, DIR>(X, ld, logC, logL, logLs, tw); break;
+    case 3: fft_pass<3, DIR>(X, ld, logC, logL, logLs, tw); break;
+    default: fft_pass<4, DIR>(X, ld, logC, logL, logLs, tw); break;
   }
 }
 
 // Forward: natural order in, permuted (fft_pos) order out; exp(-2 pi i n j / L).
-// tw[m] = exp(-2 pi i m / L), m < L, must be visible to all threads.
+// tw[m] = exp(-2 pi i m / L), m < L, must be visible to all threads. C = 2^logC columns.
 template <typename V>
-__device__ void fft_forward(V* X, int ld, int C, int L, const V* tw) {
+__device__ void fft_forward(V* X, int ld, int logC, int L, const V* tw) {
+  const int logL = ilog2c(L);
   const int np = fft_npass(L);
-  int Ls = L;
+  int logLs = logL;
   for (int i = 0; i < np; ++i) {
-    const int R = fft_radix(L, i);
-    fft_pass_dispatch<-1>(R, X, ld, C, L, Ls, tw);
-    Ls /= R;
+    const int lr = fft_logradix(L, i);
+    fft_pass_dispatch<-1>(lr, X, ld, logC, logL, logLs, tw);
+    logLs -= lr;
     __syncthreads();
   }
 }
 
 // Inverse: permuted order in, natural order out, unnormalised: x_n = sum_j X_j exp(+2 pi i n j / L).
 template <typename V>
-__device__ void fft_inverse(V* X, int ld, int C, int L, const V* tw) {
+__device__ void fft_inverse(V* X, int ld, int logC, int L, const V* tw) {
+  const int logL = ilog2c(L);
   const int np = fft_npass(L);
-  int Ls = 1;
+  int logLs = 0;
   for (int i = np - 1; i >= 0; --i) {
-    const int R = fft_radix(L, i);
-    Ls *= R;
-    fft_pass_dispatch<1>(R, X, ld, C, L, Ls, tw);
+    const int lr = fft_logradix(L, i);
+    logLs += lr;
+    fft_pass_dispatch<1>(lr, X, ld, logC, logL, logLs, tw);
     __syncthreads();
   }
 }

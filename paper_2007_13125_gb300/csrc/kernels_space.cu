@@ -3,16 +3,18 @@
 // Dirichlet Laplacian. A_h is diagonalised exactly by the discrete sine transform
 // DST-I, D_{pi} = sin(pi p i / (n+1)), with eigenvalues (4/h^2) sin^2(p pi h / 2).
 //
-// A sine transform of a (complex) line x_1..x_n is taken through its odd extension of
+// k_axis -- a sine transform of a (complex) line x_1..x_n through its odd extension of
 // length L = 2(n+1): the forward FFT of [0, x, 0, -reverse(x)] is -2i D x at frequencies
 // 1..n and keeps the odd symmetry. Dividing that spectrum by a symmetric factor keeps it
 // odd, and the inverse FFT of an odd spectrum Z is 2i D Z. So a shifted solve along one
 // axis is: odd-extend, forward FFT, divide, inverse FFT -- in place, in shared memory,
 // with no permutation (the inverse consumes the forward transform's permuted order).
-//
 // Line layouts: mode 0 -- lines are contiguous rows of n elements (x direction, or the
 // whole 1D grid); mode 1 -- lines run across rows with stride P (y direction in 2D),
 // consecutive lines are consecutive x-modes so loads stay coalesced.
+//
+// k_tri -- the y direction as a tridiagonal solve (after the x sine transform every line
+// (j, p) is a constant-coefficient system): thread per line, data staged in shared memory.
 #include "fft.cuh"
 #include "pint_internal.h"
 
@@ -20,41 +22,54 @@ namespace pint {
 
 template <typename T> size_t axis_smem(int n, int C) {
   const size_t L = 2 * (size_t)(n + 1);
-  return sizeof(typename c2<T>::t) * (L * (C + 1) + L);
+  return sizeof(typename c2<T>::t) * (L * (C + 1) + L) + sizeof(unsigned short) * L + 2 * sizeof(int) * C;
 }
+
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_axis(AxisArgs<T> a) {
   using V = typename c2<T>::t;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int n = a.n, C = a.C, ld = a.ld, L = 2 * (a.n + 1);
+  const int n = a.n, C = a.C, logC = a.logC, ld = a.ld, L = 2 * (a.n + 1);
   V* X = reinterpret_cast<V*>(smraw);
   V* tw = X + (size_t)L * ld;
+  unsigned short* perm = reinterpret_cast<unsigned short*>(tw + L);
+  int* lj = reinterpret_cast<int*>(perm + L + (L & 1));  // line -> j
+  int* lp = lj + C;                                      // line -> position within its slice
   const V* gtw = reinterpret_cast<const V*>(a.tw);
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = gtw[i];
+  fft_perm_table(perm, L);
   V* S = reinterpret_cast<V*>(a.S);
   const int line0 = blockIdx.x * C;
+  const int per = a.mode == 0 ? a.lines_per_j : a.P;
+  for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+    const int line = line0 + cc;
+    lj[cc] = line / per;
+    lp[cc] = line - lj[cc] * per;
+  }
+  __syncthreads();
   const T zero = T(0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
 
   // ---- load with odd extension ----
   if (a.mode == 0) {
-    for (int it = threadIdx.x; it < n * C; it += blockDim.x) {
-      const int cc = it / n, i = it - cc * n;
+    for (int cc = warp; cc < C; cc += nwarp) {
       const int line = line0 + cc;
-      V v = mk(zero, zero);
-      if (line < a.lines) v = S[(size_t)line * n + i];
-      X[(size_t)(i + 1) * ld + cc] = v;
-      X[(size_t)(L - 1 - i) * ld + cc] = mk(-v.x, -v.y);
+      for (int i = lane; i < n; i += 32) {
+        V v = mk(zero, zero);
+        if (line < a.lines) v = S[(size_t)line * n + i];
+        X[(size_t)(i + 1) * ld + cc] = v;
+        X[(size_t)(L - 1 - i) * ld + cc] = mk(-v.x, -v.y);
+      }
     }
   } else {
-    for (int it = threadIdx.x; it < n * C; it += blockDim.x) {
-      const int cc = it % C, i = it / C;
+    for (int it = threadIdx.x; it < (n << logC); it += blockDim.x) {
+      const int cc = it & (C - 1), i = it >> logC;
       const int line = line0 + cc;
       V v = mk(zero, zero);
-      if (line < a.lines) {
-        const int j = line / a.P, p = line - j * a.P;
-        v = S[((size_t)j * n + i) * a.P + p];
-      }
+      if (line < a.lines) v = S[((size_t)lj[cc] * n + i) * a.P + lp[cc]];
       X[(size_t)(i + 1) * ld + cc] = v;
       X[(size_t)(L - 1 - i) * ld + cc] = mk(-v.x, -v.y);
     }
@@ -64,24 +79,21 @@ __global__ void __launch_bounds__(kThreads) k_axis(AxisArgs<T> a) {
     X[(size_t)(n + 1) * ld + cc] = mk(zero, zero);
   }
   __syncthreads();
-  fft_forward(X, ld, C, L, tw);
+  fft_forward(X, ld, logC, L, tw);
 
   if (a.op == 0) {
     // D-transform only: -2i D x at frequencies 1..n, stored in natural order
     if (a.mode == 0) {
-      for (int it = threadIdx.x; it < n * C; it += blockDim.x) {
-        const int cc = it / n, i = it - cc * n;
+      for (int cc = warp; cc < C; cc += nwarp) {
         const int line = line0 + cc;
-        if (line < a.lines) S[(size_t)line * n + i] = X[(size_t)fft_pos(i + 1, L) * ld + cc];
+        if (line >= a.lines) continue;
+        for (int i = lane; i < n; i += 32) S[(size_t)line * n + i] = X[(size_t)perm[i + 1] * ld + cc];
       }
     } else {
-      for (int it = threadIdx.x; it < n * C; it += blockDim.x) {
-        const int cc = it % C, i = it / C;
-        const int line = line0 + cc;
-        if (line < a.lines) {
-          const int j = line / a.P, p = line - j * a.P;
-          S[((size_t)j * n + i) * a.P + p] = X[(size_t)fft_pos(i + 1, L) * ld + cc];
-        }
+      for (int it = threadIdx.x; it < (n << logC); it += blockDim.x) {
+        const int cc = it & (C - 1), i = it >> logC;
+        if (line0 + cc < a.lines)
+          S[((size_t)lj[cc] * n + i) * a.P + lp[cc]] = X[(size_t)perm[i + 1] * ld + cc];
       }
     }
     return;
@@ -89,47 +101,35 @@ __global__ void __launch_bounds__(kThreads) k_axis(AxisArgs<T> a) {
 
   // ---- divide by scale * (sigma_j + lambda_other + lambda_p) at frequencies p and L-p ----
   const V* sigma = reinterpret_cast<const V*>(a.sigma);
-  for (int it = threadIdx.x; it < L * C; it += blockDim.x) {
-    const int cc = it % C, fq = it / C;
-    const int line = line0 + cc;
+  for (int it = threadIdx.x; it < (L << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), fq = it >> logC;
     const int p = fq <= n + 1 ? fq : L - fq;
-    const size_t pos = (size_t)fft_pos(fq, L) * ld + cc;
-    if (p == 0 || p == n + 1 || line >= a.lines) {
+    const size_t pos = (size_t)perm[fq] * ld + cc;
+    if (p == 0 || p == n + 1 || line0 + cc >= a.lines) {
       X[pos] = mk(zero, zero);
       continue;
     }
-    int j, po = 0;
-    if (a.mode == 0) {
-      j = line / a.lines_per_j;
-    } else {
-      j = line / a.P;
-      po = line - j * a.P;
-    }
-    V d = sigma[j];
+    V d = sigma[lj[cc]];
     d.x += a.lam_axis[p - 1];
-    if (a.lam_other) d.x += a.lam_other[po];
+    if (a.lam_other) d.x += a.lam_other[lp[cc]];
     d.x *= a.scale;
     d.y *= a.scale;
-    const T inv = T(1) / (d.x * d.x + d.y * d.y);
+    const T inv = rcp(d.x * d.x + d.y * d.y);
     X[pos] = cmulc(X[pos], mk(d.x * inv, d.y * inv));   // X / d = X conj(d) / |d|^2
   }
   __syncthreads();
-  fft_inverse(X, ld, C, L, tw);
+  fft_inverse(X, ld, logC, L, tw);
 
   if (a.mode == 0) {
-    for (int it = threadIdx.x; it < n * C; it += blockDim.x) {
-      const int cc = it / n, i = it - cc * n;
+    for (int cc = warp; cc < C; cc += nwarp) {
       const int line = line0 + cc;
-      if (line < a.lines) S[(size_t)line * n + i] = X[(size_t)(i + 1) * ld + cc];
+      if (line >= a.lines) continue;
+      for (int i = lane; i < n; i += 32) S[(size_t)line * n + i] = X[(size_t)(i + 1) * ld + cc];
     }
   } else {
-    for (int it = threadIdx.x; it < n * C; it += blockDim.x) {
-      const int cc = it % C, i = it / C;
-      const int line = line0 + cc;
-      if (line < a.lines) {
-        const int j = line / a.P, p = line - j * a.P;
-        S[((size_t)j * n + i) * a.P + p] = X[(size_t)(i + 1) * ld + cc];
-      }
+    for (int it = threadIdx.x; it < (n << logC); it += blockDim.x) {
+      const int cc = it & (C - 1), i = it >> logC;
+      if (line0 + cc < a.lines) S[((size_t)lj[cc] * n + i) * a.P + lp[cc]] = X[(size_t)(i + 1) * ld + cc];
     }
   }
 }
@@ -145,6 +145,126 @@ template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t
                                : (sizeof(T) == 8 ? "axis_solve_f64" : "axis_solve_f32");
   prof_begin(name, st);
   k_axis<T><<<blocks, kThreads, sm, st>>>(a);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Tridiagonal y-solve: d q_y - g (q_{y-1} + q_{y+1}) = b_y, d = sigma_j + lambda_p^x + 2g.
+// With r + 1/r = d/g, |r| < 1 (r = 1 + e/2 - sqrt(e + e^2/4), e = (sigma_j + lambda_p^x)/g,
+// evaluated without cancellation), the matrix is
+//   T = (g/r)(I - rZ)(I - rZ^T) + g r e_0 e_0^T      (Z the down-shift),
+// so T^-1 b = x0 - zeta * (g r x0_0) / (1 + g r zeta_0) with x0 = B^-1 b from two first-order
+// recurrences with the constant factor r, and zeta = B^-1 e_0 in closed form:
+//   zeta_i = (r^{i+1} - r^{2n-i+1}) / (g (1 - r^2)).
+// Pass 1 (forward) also accumulates x0_0 = sum_i r^i w_i, so the correction is known before
+// the backward pass; pass 3 applies it while storing.
+// ---------------------------------------------------------------------------
+size_t tri_smem(int n, int C) { return sizeof(float2) * (size_t)n * C + 2 * sizeof(int) * C; }
+
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {  // a*b + c
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 csqrtf_(float2 z) {
+  const float m = hypotf(z.x, z.y);
+  const float re = sqrtf(fmaxf(0.5f * (m + z.x), 0.f));
+  float im = sqrtf(fmaxf(0.5f * (m - z.x), 0.f));
+  if (z.y < 0.f) im = -im;
+  return make_float2(re, im);
+}
+__device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+  const float inv = __frcp_rn(b.x * b.x + b.y * b.y);
+  return make_float2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
+}
+
+__global__ void __launch_bounds__(kThreads) k_tri(TriArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int n = a.n, C = a.C, logC = a.logC;
+  float2* X = reinterpret_cast<float2*>(smraw);  // [n][C]
+  int* lj = reinterpret_cast<int*>(X + (size_t)n * C);
+  int* lp = lj + C;
+  const int line0 = blockIdx.x * C;
+  for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+    const int line = line0 + cc;
+    lj[cc] = line / a.P;
+    lp[cc] = line - lj[cc] * a.P;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < (n << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), i = it >> logC;
+    float2 v = make_float2(0.f, 0.f);
+    if (line0 + cc < a.lines) v = a.S[((size_t)lj[cc] * n + i) * a.P + lp[cc]];
+    X[(size_t)i * C + cc] = v;
+  }
+  __syncthreads();
+  for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+    if (line0 + cc >= a.lines) continue;
+    const float g = a.g;
+    const float2 sg = a.sigma[lj[cc]];
+    const float ig = 1.f / g;
+    const float2 e = make_float2((sg.x + a.lam_x[lp[cc]]) * ig, sg.y * ig);
+    // r = 1 + e/2 - sqrt(e (1 + e/4)), the root of r + 1/r = 2 + e inside the unit disk
+    const float2 q = make_float2(e.x * (1.f + 0.25f * e.x) - 0.25f * e.y * e.y,
+                                 e.y * (1.f + 0.25f * e.x) + 0.25f * e.x * e.y);
+    const float2 sq = csqrtf_(q);
+    float2 r = make_float2(1.f + 0.5f * e.x - sq.x, 0.5f * e.y - sq.y);
+    if (r.x * r.x + r.y * r.y > 1.f) r = make_float2(1.f + 0.5f * e.x + sq.x, 0.5f * e.y + sq.y);
+    // pass 1: w_i = b_i + r w_{i-1}; x0_0 = sum_i r^i w_i
+    float2 w = make_float2(0.f, 0.f), acc = make_float2(0.f, 0.f), rp = make_float2(1.f, 0.f);
+    for (int i = 0; i < n; ++i) {
+      w = cfma(r, w, X[(size_t)i * C + cc]);
+      X[(size_t)i * C + cc] = w;
+      acc = cfma(rp, w, acc);
+      rp = cfma(rp, r, make_float2(0.f, 0.f));
+    }
+    // pass 2: x0_i = w_i + r x0_{i+1}   (B^-1 b = (r/g) x0)
+    float2 x = make_float2(0.f, 0.f);
+    for (int i = n - 1; i >= 0; --i) {
+      x = cfma(r, x, X[(size_t)i * C + cc]);
+      X[(size_t)i * C + cc] = x;
+    }
+    // correction: gamma = g r X0_0 / (1 + g r zeta_0), X0 = (r/g) x0
+    const float2 r2 = cfma(r, r, make_float2(0.f, 0.f));
+    const float2 one_m_r2 = make_float2(1.f - r2.x, -r2.y);
+    // r^{2n}
+    float2 r2n = make_float2(1.f, 0.f), b = r2;
+    for (int t = n; t > 0; t >>= 1) {
+      if (t & 1) r2n = cfma(r2n, b, make_float2(0.f, 0.f));
+      b = cfma(b, b, make_float2(0.f, 0.f));
+    }
+    // g r zeta_0 = r^2 (1 - r^{2n}) / (1 - r^2)
+    const float2 grz0 = cdiv(cfma(r2, make_float2(-r2n.x, -r2n.y), r2), one_m_r2);
+    const float2 X00 = cfma(r, acc, make_float2(0.f, 0.f));          // r x0_0
+    // gamma * zeta_i = [g r X0_0 / (1 + g r zeta_0)] * (r^{i+1} - r^{2n-i+1}) / (g (1 - r^2))
+    //                = (r/g) K (r^{i+1} - r^{2n+1-i}),  K = r x0_0 / ((1 + g r zeta_0)(1 - r^2))
+    const float2 den = cfma(make_float2(1.f + grz0.x, grz0.y), one_m_r2, make_float2(0.f, 0.f));
+    const float2 K = cdiv(X00, den);
+    // pass 3: q_i = scale * (r/g) (x0_i - K' (r^{i+1} - r^{2n+1-i})),  K' = K (in x0 units)
+    const float2 rg = make_float2(r.x * ig * a.scale, r.y * ig * a.scale);
+    float2 A = r;                                                         // r^{i+1}
+    float2 E = cfma(r2n, r, make_float2(0.f, 0.f));                      // r^{2n+1-i}, i = 0
+    const float2 ir = cdiv(make_float2(1.f, 0.f), r);
+    const size_t col = (size_t)lj[cc] * n * a.P + lp[cc];
+    for (int i = 0; i < n; ++i) {
+      const float2 z = make_float2(A.x - E.x, A.y - E.y);
+      const float2 x0 = X[(size_t)i * C + cc];
+      const float2 xi = cfma(make_float2(-K.x, -K.y), z, x0);
+      a.S[col + (size_t)i * a.P] = cfma(rg, xi, make_float2(0.f, 0.f));
+      A = cfma(A, r, make_float2(0.f, 0.f));
+      E = cfma(E, ir, make_float2(0.f, 0.f));
+    }
+  }
+}
+
+cudaError_t launch_tri(const TriArgs& a, cudaStream_t st) {
+  const size_t sm = tri_smem(a.n, a.C);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  const int blocks = (a.lines + a.C - 1) / a.C;
+  prof_begin("tri_y_f32", st);
+  k_tri<<<blocks, kThreads, sm, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
 }

@@ -6,6 +6,8 @@
 // column c, so one complex N-point FFT transforms two real time series; the half
 // spectra j = 0..N/2 of both are separated afterwards with the conjugate symmetry of
 // real data. Global loads and stores are coalesced over consecutive points.
+// Shared memory per CTA: the [N][C] complex tile, the twiddles and the digit-reversal
+// table of the FFT (fft.cuh).
 #include "ff.cuh"
 #include "fft.cuh"
 #include "pint_internal.h"
@@ -43,22 +45,78 @@ __device__ __forceinline__ void block_reduce_add2(double a, double b, double* ou
   }
 }
 
+// shared-memory carve-up of a time tile: X [N][C] (V), tw [N] (V), perm [N] (u16)
+template <typename V> __host__ __device__ inline size_t time_tile_bytes(int N, int C) {
+  return sizeof(V) * ((size_t)N * C + N) + sizeof(unsigned short) * (size_t)N;
+}
+
+template <typename V>
+__device__ __forceinline__ void time_tile_setup(unsigned char* raw, int N, int C, const V* gtw, V*& X,
+                                                V*& tw, unsigned short*& perm) {
+  X = reinterpret_cast<V*>(raw);
+  tw = X + (size_t)N * C;
+  perm = reinterpret_cast<unsigned short*>(tw + N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = gtw[i];
+  fft_perm_table(perm, N);
+}
+
+// Separate the spectra of the two real columns packed in complex column cc and store the
+// half spectra j = 0..N/2 of points ma (real part) and mb (imaginary part).
+template <typename V>
+__device__ __forceinline__ void store_half_spectrum(const V* X, const unsigned short* perm, V* S, int N,
+                                                    int M, int C, int logC, int m0) {
+  using T = decltype(X[0].x);
+  const int J = N / 2 + 1;
+  const T h = T(0.5);
+  for (int it = threadIdx.x; it < (J << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), j = it >> logC;
+    const V Zj = X[(size_t)perm[j] * C + cc];
+    const V Zn = X[(size_t)perm[(N - j) & (N - 1)] * C + cc];
+    const V A = mk(h * (Zj.x + Zn.x), h * (Zj.y - Zn.y));      // (Z_j + conj Z_{N-j}) / 2
+    const V B = mk(h * (Zj.y + Zn.y), -h * (Zj.x - Zn.x));     // (Z_j - conj Z_{N-j}) / 2i
+    const int ma = m0 + cc, mb = m0 + C + cc;
+    if (ma < M) S[(size_t)j * M + ma] = A;
+    if (mb < M) S[(size_t)j * M + mb] = B;
+  }
+}
+
+// Inverse of store_half_spectrum: Z_j = A_j + i B_j in permuted order (Hermitian symmetry
+// supplies j > N/2).
+template <typename V>
+__device__ __forceinline__ void load_half_spectrum(V* X, const unsigned short* perm, const V* S, int N,
+                                                   int M, int C, int logC, int m0) {
+  const int J = N / 2 + 1;
+  for (int it = threadIdx.x; it < (J << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), j = it >> logC;
+    const int ma = m0 + cc, mb = m0 + C + cc;
+    V A, B;
+    A.x = 0; A.y = 0; B = A;
+    if (ma < M) A = S[(size_t)j * M + ma];
+    if (mb < M) B = S[(size_t)j * M + mb];
+    X[(size_t)perm[j] * C + cc] = mk(A.x - B.y, A.y + B.x);                 // A + iB
+    if (j > 0 && j < N / 2)
+      X[(size_t)perm[N - j] * C + cc] = mk(A.x + B.y, B.x - A.y);           // conj(A) + i conj(B)
+  }
+}
+
 // ---------------------------------------------------------------------------
-// MIXED: residual (double-float) + kappa scaling + forward DFT along time
+// MIXED: residual r = F_hat - K U (double-float) + kappa scaling + forward DFT along time.
+// K U = tau^-alpha sum_{j=0}^{min(n-1,k)} omega_j U^{n-j} + A_h U^n (BDF band, eq. (2.6) with
+// kappa = 0), or, for CQ, the precomputed Toeplitz history y plus A_h U^n.
 // ---------------------------------------------------------------------------
-size_t resid_fwd_smem(int N, int C) { return sizeof(float2) * ((size_t)N * C + N); }
+size_t resid_fwd_smem(int N, int C) { return time_tile_bytes<float2>(N, C); }
 
 __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = a.N, C = a.C, M = a.M;
-  float2* X = reinterpret_cast<float2*>(smraw);
-  float2* tw = X + (size_t)N * C;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  const int N = a.N, C = a.C, M = a.M, logC = a.logC;
+  float2 *X, *tw;
+  unsigned short* perm;
+  time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
 
   const int m0 = blockIdx.x * 2 * C;
-  const int c = threadIdx.x % C;
-  const int nch = blockDim.x / C;
-  const int tc = threadIdx.x / C;
+  const int c = threadIdx.x & (C - 1);
+  const int nch = blockDim.x >> logC;
+  const int tc = threadIdx.x >> logC;
   const int Lc = N / nch;
   const int i0 = tc * Lc;
   const int k = a.k;
@@ -67,117 +125,96 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
   for (int j = 0; j <= kMaxK; ++j) { cw[j].hi = a.c_hi[j]; cw[j].lo = a.c_lo[j]; }
   const ff gx = {a.gx_hi, a.gx_lo}, gy = {a.gy_hi, a.gy_lo};
 
-  for (int half = 0; half < 2; ++half) {
-    const int m = m0 + half * C + c;
-    const bool valid = m < M;
-    const int x = valid ? m % a.mx : 0;
-    ff win[kMaxK];
+  int mm[2];
+  bool valid[2];
+  int xx[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    mm[h] = m0 + h * C + c;
+    valid[h] = mm[h] < M;
+    xx[h] = valid[h] ? mm[h] % a.mx : 0;
+  }
+  ff win[2][kMaxK];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
 #pragma unroll
     for (int j = 0; j < kMaxK; ++j) {
       const int lev = i0 - 1 - j;
-      win[j].hi = 0.f; win[j].lo = 0.f;
-      if (j < k && valid && lev >= 0) win[j] = ldff(a.Uhi, a.Ulo, (size_t)lev * M + m);
+      win[h][j].hi = 0.f;
+      win[h][j].lo = 0.f;
+      if (j < k && valid[h] && lev >= 0) win[h][j] = ldff(a.Uhi, a.Ulo, (size_t)lev * M + mm[h]);
     }
-    for (int i = i0; i < i0 + Lc; ++i) {
-      float r = 0.f;
-      if (valid) {
-        const size_t idx = (size_t)i * M + m;
-        const ff u = ldff(a.Uhi, a.Ulo, idx);
-        ff_acc acc;
-        acc.init(ldff(a.Fhi, a.Flo, idx));
-        if (a.y) acc.sub(ff_from_double(__ldg(a.y + idx)));
-        acc.fma_term(cw[0], u, -1.f);
+#pragma unroll 2
+  for (int i = i0; i < i0 + Lc; ++i) {
+    const float si = __ldg(a.s + i);
+    float r[2];
 #pragma unroll
-        for (int j = 1; j <= kMaxK; ++j)
-          if (j <= k) acc.fma_term(cw[j], win[j - 1], -1.f);
-        if (x > 0) acc.fma_term(gx, ldff(a.Uhi, a.Ulo, idx - 1), 1.f);
-        if (x < a.mx - 1) acc.fma_term(gx, ldff(a.Uhi, a.Ulo, idx + 1), 1.f);
-        if (a.dim == 2) {
-          if (m >= a.mx) acc.fma_term(gy, ldff(a.Uhi, a.Ulo, idx - a.mx), 1.f);
-          if (m + a.mx < M) acc.fma_term(gy, ldff(a.Uhi, a.Ulo, idx + a.mx), 1.f);
-        }
-        r = acc.value() * __ldg(a.s + i);
+    for (int h = 0; h < 2; ++h) {
+      r[h] = 0.f;
+      if (!valid[h]) continue;
+      const int m = mm[h];
+      const size_t idx = (size_t)i * M + m;
+      const ff u = ldff(a.Uhi, a.Ulo, idx);
+      ff_acc acc;
+      acc.init(ff_from_double(__ldg(a.F + idx)));
+      if (a.y) acc.sub(ff_from_double(__ldg(a.y + idx)));
+      acc.fma_term(cw[0], u, -1.f);
 #pragma unroll
-        for (int j = kMaxK - 1; j > 0; --j) win[j] = win[j - 1];
-        win[0] = u;
+      for (int j = 1; j <= kMaxK; ++j)
+        if (j <= k) acc.fma_term(cw[j], win[h][j - 1], -1.f);
+      if (xx[h] > 0) acc.fma_term(gx, ldff(a.Uhi, a.Ulo, idx - 1), 1.f);
+      if (xx[h] < a.mx - 1) acc.fma_term(gx, ldff(a.Uhi, a.Ulo, idx + 1), 1.f);
+      if (a.dim == 2) {
+        if (m >= a.mx) acc.fma_term(gy, ldff(a.Uhi, a.Ulo, idx - a.mx), 1.f);
+        if (m + a.mx < M) acc.fma_term(gy, ldff(a.Uhi, a.Ulo, idx + a.mx), 1.f);
       }
-      if (half == 0) X[(size_t)i * C + c].x = r;
-      else X[(size_t)i * C + c].y = r;
+      r[h] = acc.value() * si;
+#pragma unroll
+      for (int j = kMaxK - 1; j > 0; --j) win[h][j] = win[h][j - 1];
+      win[h][0] = u;
     }
+    X[(size_t)i * C + c] = make_float2(r[0], r[1]);
   }
   __syncthreads();
-  fft_forward(X, C, C, N, tw);
-
-  const int J = N / 2 + 1;
-  for (int it = threadIdx.x; it < J * C; it += blockDim.x) {
-    const int cc = it % C, j = it / C;
-    const float2 Zj = X[(size_t)fft_pos(j, N) * C + cc];
-    const float2 Zn = X[(size_t)fft_pos((N - j) & (N - 1), N) * C + cc];
-    const float2 A = make_float2(0.5f * (Zj.x + Zn.x), 0.5f * (Zj.y - Zn.y));
-    const float2 B = make_float2(0.5f * (Zj.y + Zn.y), -0.5f * (Zj.x - Zn.x));
-    const int ma = m0 + cc, mb = m0 + C + cc;
-    if (ma < M) a.S[(size_t)j * M + ma] = A;
-    if (mb < M) a.S[(size_t)j * M + mb] = B;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Load a half spectrum (two real columns per complex column) into permuted order
-// ---------------------------------------------------------------------------
-template <typename V>
-__device__ __forceinline__ void load_half_spectrum(V* X, const V* S, int N, int M, int C, int m0) {
-  const int J = N / 2 + 1;
-  for (int it = threadIdx.x; it < J * C; it += blockDim.x) {
-    const int cc = it % C, j = it / C;
-    const int ma = m0 + cc, mb = m0 + C + cc;
-    V A, B;
-    A.x = 0; A.y = 0; B = A;
-    if (ma < M) A = S[(size_t)j * M + ma];
-    if (mb < M) B = S[(size_t)j * M + mb];
-    X[(size_t)fft_pos(j, N) * C + cc] = mk(A.x - B.y, A.y + B.x);                 // A + iB
-    if (j > 0 && j < N / 2)
-      X[(size_t)fft_pos(N - j, N) * C + cc] = mk(A.x + B.y, B.x - A.y);           // conj(A) + i conj(B)
-  }
+  fft_forward(X, C, logC, N, tw);
+  store_half_spectrum(X, perm, a.S, N, M, C, logC, m0);
 }
 
 // ---------------------------------------------------------------------------
 // MIXED: inverse DFT + unscale + U += c (double-float) + norms
 // ---------------------------------------------------------------------------
-size_t inv_upd_smem(int N, int C) { return sizeof(float2) * ((size_t)N * C + N); }
+size_t inv_upd_smem(int N, int C) { return time_tile_bytes<float2>(N, C); }
 
 __global__ void __launch_bounds__(kThreads) k_inv_upd(InvUpdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = a.N, C = a.C, M = a.M;
-  float2* X = reinterpret_cast<float2*>(smraw);
-  float2* tw = X + (size_t)N * C;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  const int N = a.N, C = a.C, M = a.M, logC = a.logC;
+  float2 *X, *tw;
+  unsigned short* perm;
+  time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
   const int m0 = blockIdx.x * 2 * C;
-  load_half_spectrum(X, a.S, N, M, C, m0);
   __syncthreads();
-  fft_inverse(X, C, C, N, tw);
+  load_half_spectrum(X, perm, a.S, N, M, C, logC, m0);
+  __syncthreads();
+  fft_inverse(X, C, logC, N, tw);
 
-  const int c = threadIdx.x % C;
-  const int nch = blockDim.x / C;
-  const int tc = threadIdx.x / C;
-  const int Lc = N / nch;
   double sc = 0.0, su = 0.0;
-  for (int half = 0; half < 2; ++half) {
-    const int m = m0 + half * C + c;
-    if (m >= M) continue;
-    float pc = 0.f, pu = 0.f;
-    for (int i = tc * Lc; i < (tc + 1) * Lc; ++i) {
-      const float2 z = X[(size_t)i * C + c];
-      const float cval = (half ? z.y : z.x) * __ldg(a.inv_s + i);
+  for (int it = threadIdx.x; it < (N << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), i = it >> logC;
+    const float2 z = X[(size_t)i * C + cc];
+    const float is = __ldg(a.inv_s + i);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = m0 + h * C + cc;
+      if (m >= M) continue;
+      const float cval = (h ? z.y : z.x) * is;
       const size_t idx = (size_t)i * M + m;
       ff u = {a.Uhi[idx], a.Ulo[idx]};
       u = ff_add_f(u, cval);
       a.Uhi[idx] = u.hi;
       a.Ulo[idx] = u.lo;
-      pc = fmaf(cval, cval, pc);
-      pu = fmaf(u.hi, u.hi, pu);
+      sc += (double)(cval * cval);
+      su += (double)(u.hi * u.hi);
     }
-    sc += pc;
-    su += pu;
   }
   block_reduce_add2(sc, su, a.norms);
 }
@@ -185,22 +222,19 @@ __global__ void __launch_bounds__(kThreads) k_inv_upd(InvUpdArgs a) {
 // ---------------------------------------------------------------------------
 // FP64 / FP32 direct form (Algorithm 1/2 as printed): F_{m-1} -> scale -> DFT
 // ---------------------------------------------------------------------------
-template <typename T> size_t direct_smem(int N, int C) {
-  return sizeof(typename c2<T>::t) * ((size_t)N * C + N);
-}
+template <typename T> size_t direct_smem(int N, int C) { return time_tile_bytes<typename c2<T>::t>(N, C); }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_direct_fwd(DirectFwdArgs<T> a) {
   using V = typename c2<T>::t;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = a.N, C = a.C, M = a.M;
-  V* X = reinterpret_cast<V*>(smraw);
-  V* tw = X + (size_t)N * C;
-  const V* gtw = reinterpret_cast<const V*>(a.tw);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = gtw[i];
+  const int N = a.N, C = a.C, M = a.M, logC = a.logC;
+  V *X, *tw;
+  unsigned short* perm;
+  time_tile_setup(smraw, N, C, reinterpret_cast<const V*>(a.tw), X, tw, perm);
   const int m0 = blockIdx.x * 2 * C;
-  for (int it = threadIdx.x; it < N * C; it += blockDim.x) {
-    const int cc = it % C, i = it / C;
+  for (int it = threadIdx.x; it < (N << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), i = it >> logC;
     T val[2] = {T(0), T(0)};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -211,46 +245,36 @@ __global__ void __launch_bounds__(kThreads) k_direct_fwd(DirectFwdArgs<T> a) {
       if (a.z) {
         f += (T)a.z[idx];
       } else if (i < a.k) {
-        // row n = i+1 <= k: kappa tau^-1 sum_{j=n}^{k} omega_j U^{N+n-j}
-        for (int j = i + 1; j <= a.k; ++j) f += a.kw[j] * a.U[(size_t)(N + i - j) * M + m];
+        // row n = i+1 <= k: kappa tau^-1 sum_{j=n}^{k} omega_j U^{N+n-j}  (eq. (2.7), reading r1)
+#pragma unroll
+        for (int j = 1; j <= kMaxK; ++j)
+          if (j > i && j <= a.k) f += a.kw[j] * a.U[(size_t)(N + i - j) * M + m];
       }
       val[h] = f * a.s[i];
     }
     X[(size_t)i * C + cc] = mk(val[0], val[1]);
   }
   __syncthreads();
-  fft_forward(X, C, C, N, tw);
-  V* S = reinterpret_cast<V*>(a.S);
-  const int J = N / 2 + 1;
-  const T h = T(0.5);
-  for (int it = threadIdx.x; it < J * C; it += blockDim.x) {
-    const int cc = it % C, j = it / C;
-    const V Zj = X[(size_t)fft_pos(j, N) * C + cc];
-    const V Zn = X[(size_t)fft_pos((N - j) & (N - 1), N) * C + cc];
-    const V A = mk(h * (Zj.x + Zn.x), h * (Zj.y - Zn.y));
-    const V B = mk(h * (Zj.y + Zn.y), -h * (Zj.x - Zn.x));
-    const int ma = m0 + cc, mb = m0 + C + cc;
-    if (ma < M) S[(size_t)j * M + ma] = A;
-    if (mb < M) S[(size_t)j * M + mb] = B;
-  }
+  fft_forward(X, C, logC, N, tw);
+  store_half_spectrum(X, perm, reinterpret_cast<V*>(a.S), N, M, C, logC, m0);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_direct_inv(DirectInvArgs<T> a) {
   using V = typename c2<T>::t;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = a.N, C = a.C, M = a.M;
-  V* X = reinterpret_cast<V*>(smraw);
-  V* tw = X + (size_t)N * C;
-  const V* gtw = reinterpret_cast<const V*>(a.tw);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = gtw[i];
+  const int N = a.N, C = a.C, M = a.M, logC = a.logC;
+  V *X, *tw;
+  unsigned short* perm;
+  time_tile_setup(smraw, N, C, reinterpret_cast<const V*>(a.tw), X, tw, perm);
   const int m0 = blockIdx.x * 2 * C;
-  load_half_spectrum(X, reinterpret_cast<const V*>(a.S), N, M, C, m0);
   __syncthreads();
-  fft_inverse(X, C, C, N, tw);
+  load_half_spectrum(X, perm, reinterpret_cast<const V*>(a.S), N, M, C, logC, m0);
+  __syncthreads();
+  fft_inverse(X, C, logC, N, tw);
   double sd = 0.0, su = 0.0;
-  for (int it = threadIdx.x; it < N * C; it += blockDim.x) {
-    const int cc = it % C, i = it / C;
+  for (int it = threadIdx.x; it < (N << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), i = it >> logC;
     const V z = X[(size_t)i * C + cc];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -258,29 +282,30 @@ __global__ void __launch_bounds__(kThreads) k_direct_inv(DirectInvArgs<T> a) {
       if (m >= M) continue;
       const size_t idx = (size_t)i * M + m;
       const T un = (h ? z.y : z.x) * a.inv_s[i];
-      const double d = (double)un - (double)a.Uold[idx];
+      const T d = un - a.Uold[idx];
       a.Uout[idx] = un;
-      sd += d * d;
-      su += (double)un * (double)un;
+      sd += (double)(d * d);
+      su += (double)(un * un);
     }
   }
   block_reduce_add2(sd, su, a.norms);
 }
 
 // ---------------------------------------------------------------------------
-// CQ Toeplitz product along time: z = omega * U (zero-padded 2N-point FFTs, FP64)
+// CQ Toeplitz product along time: z = omega * U (zero-padded 2N-point FFTs, FP64), the
+// circulant embedding of Sec. 3.2 (speedup analysis of Algorithm 2).
 // ---------------------------------------------------------------------------
-size_t toep_smem(int N, int C) { return sizeof(double2) * ((size_t)2 * N * C + 2 * N); }
+size_t toep_smem(int N, int C) { return time_tile_bytes<double2>(2 * N, C); }
 
 __global__ void __launch_bounds__(kThreads) k_toeplitz(ToepArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = a.N, C = a.C, M = a.M, L = 2 * a.N;
-  double2* X = reinterpret_cast<double2*>(smraw);
-  double2* tw = X + (size_t)L * C;
-  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = a.tw[i];
+  const int N = a.N, C = a.C, M = a.M, L = 2 * a.N, logC = a.logC;
+  double2 *X, *tw;
+  unsigned short* perm;
+  time_tile_setup(smraw, L, C, a.tw, X, tw, perm);
   const int m0 = blockIdx.x * 2 * C;
-  for (int it = threadIdx.x; it < L * C; it += blockDim.x) {
-    const int cc = it % C, i = it / C;
+  for (int it = threadIdx.x; it < (L << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), i = it >> logC;
     double val[2] = {0.0, 0.0};
     if (i < N) {
 #pragma unroll
@@ -289,22 +314,22 @@ __global__ void __launch_bounds__(kThreads) k_toeplitz(ToepArgs a) {
         if (m >= M) continue;
         const size_t idx = (size_t)i * M + m;
         if (a.ukind == 0) val[h] = a.Ud[idx];
-        else if (a.ukind == 1) val[h] = (double)a.Uhi[idx] + (double)a.Ulo[idx];
-        else val[h] = (double)a.Uf[idx];
+        else if (a.ukind == 1) val[h] = ff_to_double(ff{a.Uhi[idx], a.Ulo[idx]});
+        else val[h] = f2d_bits(a.Uf[idx]);
       }
     }
     X[(size_t)i * C + cc] = make_double2(val[0], val[1]);
   }
   __syncthreads();
-  fft_forward(X, C, C, L, tw);
-  for (int it = threadIdx.x; it < L * C; it += blockDim.x) {
-    const int cc = it % C, p = it / C;
+  fft_forward(X, C, logC, L, tw);
+  for (int it = threadIdx.x; it < (L << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), p = it >> logC;
     X[(size_t)p * C + cc] = cmul(X[(size_t)p * C + cc], a.what[p]);
   }
   __syncthreads();
-  fft_inverse(X, C, C, L, tw);
-  for (int it = threadIdx.x; it < N * C; it += blockDim.x) {
-    const int cc = it % C, i = it / C;
+  fft_inverse(X, C, logC, L, tw);
+  for (int it = threadIdx.x; it < (N << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), i = it >> logC;
     const double2 z = X[(size_t)(a.half * N + i) * C + cc];
     const int ma = m0 + cc, mb = m0 + C + cc;
     if (ma < M) a.out[(size_t)i * M + ma] = z.x;
@@ -323,7 +348,7 @@ __global__ void k_rhs(RhsArgs a) {
     const int i = (int)(t / a.M);
     const int m = (int)(t - (size_t)i * a.M);
     const double vm = a.v[m];
-    double F = a.f[t] + a.beta[i] * vm;
+    double F = fma(a.beta[i], vm, a.f[t]);
     if (i < a.k - 1) {
       const int x = m % a.mx;
       double Av = 2.0 * a.gx * vm;
@@ -342,7 +367,7 @@ __global__ void k_rhs(RhsArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// conversions
+// conversions (integer bit manipulation; see ff.cuh)
 // ---------------------------------------------------------------------------
 __global__ void k_d2ff(const double* x, float* hi, float* lo, size_t n) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
@@ -366,15 +391,15 @@ __global__ void k_bcast_d(const double* v, double* U, int N, int M) {
 }
 __global__ void k_ff2d(const float* hi, const float* lo, double* x, size_t n) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-    x[t] = (double)hi[t] + (double)lo[t];
+    x[t] = ff_to_double(ff{hi[t], lo[t]});
 }
 __global__ void k_d2f(const double* x, float* y, size_t n) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-    y[t] = (float)x[t];
+    y[t] = ff_from_double(x[t]).hi;
 }
 __global__ void k_f2d(const float* x, double* y, size_t n) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-    y[t] = (double)x[t];
+    y[t] = f2d_bits(x[t]);
 }
 
 // ---------------------------------------------------------------------------

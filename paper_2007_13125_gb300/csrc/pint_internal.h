@@ -13,12 +13,12 @@ constexpr int kMaxK = 6;
 // MIXED: r = F_hat - K U in double-float, times kappa^{i/N}, real -> half-complex DFT.
 struct ResidFwdArgs {
   const float* Uhi; const float* Ulo;      // iterate U [N][M] (double-float)
-  const float* Fhi; const float* Flo;      // F_hat [N][M] (double-float)
+  const double* F;                         // F_hat [N][M] (FP64, split to double-float on load)
   const double* y;                         // CQ: tau^-alpha (L_omega U) [N][M], else null
   float2* S;                               // half spectrum [(N/2+1)][M]
   const float* s;                          // kappa^{i/N}, i < N
   const float2* tw;                        // exp(-2 pi i m / N), m < N
-  int N, M, mx, dim, k, C;
+  int N, M, mx, dim, k, C, logC;
   float c_hi[kMaxK + 1], c_lo[kMaxK + 1];  // c_0 (incl. stencil centre), c_j = omega_j tau^-alpha
   float gx_hi, gx_lo, gy_hi, gy_lo;        // 1/hx^2, 1/hy^2
 };
@@ -27,7 +27,7 @@ struct ResidFwdArgs {
 struct InvUpdArgs {
   const float2* S; float* Uhi; float* Ulo;
   const float* inv_s; const float2* tw;
-  int N, M, C;
+  int N, M, C, logC;
   double* norms;                           // [0] += sum c^2, [1] += sum U^2
 };
 
@@ -37,14 +37,14 @@ template <typename T> struct DirectFwdArgs {
   const double* z;                         // CQ: kappa tau^-alpha (W' U) [N][M], else null
   void* S;                                 // half spectrum of T2
   const T* s; const void* tw;
-  int N, M, C, k;
+  int N, M, C, logC, k;
   T kw[kMaxK + 1];                         // kappa tau^-alpha omega_j (BDF corner)
 };
 
 template <typename T> struct DirectInvArgs {
   const void* S; const T* Uold; T* Uout;
   const T* inv_s; const void* tw;
-  int N, M, C;
+  int N, M, C, logC;
   double* norms;                           // [0] += sum (Unew-Uold)^2, [1] += sum Unew^2
 };
 
@@ -55,7 +55,7 @@ struct ToepArgs {
   double* out;                             // [N][M]
   const double2* what;                     // FFT_{2N}(omega, zero padded), permuted, pre-scaled
   const double2* tw;                       // exp(-2 pi i m / 2N)
-  int N, M, C, half;                       // half 0: z_0..z_{N-1}; 1: z_N..z_{2N-1}
+  int N, M, C, logC, half;                 // half 0: z_0..z_{N-1}; 1: z_N..z_{2N-1}
 };
 
 // right-hand side F_hat (FP64)
@@ -83,7 +83,22 @@ template <typename T> struct AxisArgs {
   T scale;                                 // op 1 divisor scale
   int lines_per_j;                         // op 1: j = line / lines_per_j
   const void* tw;                          // exp(-2 pi i m / L), L = 2(n+1)
-  int C, ld;
+  int C, logC, ld;
+};
+
+// Toeplitz tridiagonal solve along y (2D, after the x sine transform): for each line (j, p),
+// (s_j + lambda_p^x + 2 g) q_y - g (q_{y-1} + q_{y+1}) = b_y, g = 1/h_y^2, through the
+// factorisation T = (g/r)(I - r Z)(I - r Z^T) + g r e_0 e_0^T, r + 1/r = d/g, |r| < 1.
+struct TriArgs {
+  float2* S;                               // spectrum [(N/2+1)][my][mx] (in place)
+  int n;                                   // my
+  int P;                                   // mx (lines per j-slice)
+  int lines;                               // (N/2+1) * mx
+  const float2* sigma;                     // [N/2+1]
+  const float* lam_x;                      // [mx]
+  float g;                                 // 1/h_y^2
+  float scale;                             // result multiplied by this (folds DST-x normalisation)
+  int C, logC;
 };
 
 size_t resid_fwd_smem(int N, int C);
@@ -99,6 +114,8 @@ template <typename T> cudaError_t launch_direct_inv(const DirectInvArgs<T>& a, c
 cudaError_t launch_toeplitz(const ToepArgs& a, cudaStream_t st);
 cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t st);
 template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t st);
+cudaError_t launch_tri(const TriArgs& a, cudaStream_t st);
+size_t tri_smem(int n, int C);
 
 // conversions
 cudaError_t launch_d2ff(const double* x, float* hi, float* lo, size_t n, cudaStream_t st);

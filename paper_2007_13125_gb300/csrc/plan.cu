@@ -234,14 +234,21 @@ struct pint_plan_s {
   double2* tw_2n = nullptr;         // [2N]
   double2* what_lo = nullptr;       // [2N] permuted, * tau^-alpha / 2N
   double2* what_up = nullptr;       // [2N] permuted, * kappa tau^-alpha / 2N
-  float *Uhi = nullptr, *Ulo = nullptr, *Fhi = nullptr, *Flo = nullptr;  // MIXED / FP32 (Uhi, Fhi)
+  float *Uhi = nullptr, *Ulo = nullptr, *Fhi = nullptr;  // MIXED: U double-float; FP32: U, F_hat
   void* S = nullptr;                // spectrum
   double* z = nullptr;              // CQ Toeplitz output [N][M]
   double* norms = nullptr;          // device [2]
   double* h_norms = nullptr;        // pinned host [2]
   // tiles
-  int Ct, Ctd, Cz, Cx, Cy;          // columns per CTA: time (float), time (T), toeplitz, x-axis, y-axis
+  int Ct, Ctd, Cz, Cx, Cy, Ctri;    // columns per CTA: time (float), time (T), toeplitz, x, y, tri
+  int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal
 };
+
+#define PINT_CUDA_B(call)                                      \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return bail(cuda_fail(_e, #call));  \
+  } while (0)
 
 namespace {
 
@@ -355,12 +362,19 @@ void destroy_plan(pint_plan p) {
 
 }  // namespace
 
+namespace {
+pint_status autotune_ysolve(pint_plan p);
+}
+
 extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan* out) {
   if (!d || !out) return fail(PINT_EINVAL, "NULL argument");
   pint_status s = validate(d->k, d->alpha, d->kappa, d->tau, d->N, &d->grid);
   if (s != PINT_OK) return s;
   if (d->precision < PINT_FP64 || d->precision > PINT_FP32) return fail(PINT_EINVAL, "bad precision");
   if (d->eig != PINT_EIG_TRUNC_DFT && d->eig != PINT_EIG_CLOSED_FORM) return fail(PINT_EINVAL, "bad eig variant");
+  if (d->eig == PINT_EIG_CLOSED_FORM && d->alpha != 1.0 && d->precision != PINT_MIXED)
+    return fail(PINT_EINVAL, "CLOSED_FORM eigenvalues with alpha < 1 need the residual form (PINT_MIXED)");
+  if (d->ysolve < 0 || d->ysolve > 2) return fail(PINT_EINVAL, "bad ysolve variant");
   pint_plan p = new pint_plan_s();
   p->k = d->k; p->alpha = d->alpha; p->kappa = d->kappa; p->tau = d->tau; p->N = d->N;
   p->dim = d->grid.dim; p->mx = d->grid.mx; p->my = d->grid.dim == 2 ? d->grid.my : 1;
@@ -419,8 +433,6 @@ extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan*
   if (p->prec == PINT_MIXED) {
     if ((s = dalloc(p, &p->Uhi, NM)) != PINT_OK) return bail(s);
     if ((s = dalloc(p, &p->Ulo, NM)) != PINT_OK) return bail(s);
-    if ((s = dalloc(p, &p->Fhi, NM)) != PINT_OK) return bail(s);
-    if ((s = dalloc(p, &p->Flo, NM)) != PINT_OK) return bail(s);
   } else if (p->prec == PINT_FP32) {
     if ((s = dalloc(p, &p->Uhi, NM)) != PINT_OK) return bail(s);
     if ((s = dalloc(p, &p->Fhi, NM)) != PINT_OK) return bail(s);
@@ -443,6 +455,13 @@ extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan*
   const size_t ve = p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2);
   p->Cx = pick_cols((size_t)2 * (p->mx + 1) * ve, budget, 16, 1);
   p->Cy = pick_cols((size_t)2 * (p->my + 1) * ve, budget, 16, 1);
+  p->Ctri = pick_cols((size_t)p->my * sizeof(float2), 72 * 1024, 32, 1);
+  PINT_CUDA_B(cudaMemset(p->S, 0, JM * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2))));
+  p->ysolve = 1;
+  if (p->dim == 2 && p->prec != PINT_FP64) {
+    if (d->ysolve == 1 || d->ysolve == 2) p->ysolve = d->ysolve;
+    else if ((s = autotune_ysolve(p)) != PINT_OK) return bail(s);
+  }
   *out = p;
   return PINT_OK;
 }
@@ -452,7 +471,7 @@ extern "C" pint_status pint_plan_create(int k, double alpha, double kappa, doubl
   if (!grid) return fail(PINT_EINVAL, "grid is NULL");
   pint_plan_desc d;
   d.k = k; d.alpha = alpha; d.kappa = kappa; d.tau = tau; d.N = N; d.grid = *grid;
-  d.precision = precision; d.eig = PINT_EIG_TRUNC_DFT;
+  d.precision = precision; d.eig = PINT_EIG_TRUNC_DFT; d.ysolve = 0;
   return pint_plan_create_desc(&d, out);
 }
 
@@ -496,6 +515,8 @@ void split_ff(double x, float& hi, float& lo) {
   lo = (float)(x - (double)hi);
 }
 
+template <typename T> bool ysolve_tri(pint_plan p) { return sizeof(T) == 4 && p->ysolve == 2; }
+
 // spatial step on the half spectrum for T (float: MIXED/FP32, double: FP64)
 template <typename T>
 cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
@@ -505,41 +526,96 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
     a.S = p->S; a.n = p->mx; a.lines = J; a.mode = 0; a.P = 1; a.op = 1;
     a.sigma = t.sigma; a.lam_axis = t.lam_x; a.lam_other = nullptr;
     a.scale = (T)(2.0 * (p->mx + 1)); a.lines_per_j = 1; a.tw = t.tw_x;
-    a.C = p->Cx; a.ld = p->Cx + 1;
+    a.C = p->Cx; a.logC = ilog2c(p->Cx); a.ld = p->Cx + 1;
     return launch_axis(a, st);
   }
   AxisArgs<T> ax{};
   ax.S = p->S; ax.n = p->mx; ax.lines = J * p->my; ax.mode = 0; ax.P = 1; ax.op = 0;
-  ax.tw = t.tw_x; ax.C = p->Cx; ax.ld = p->Cx + 1;
+  ax.lines_per_j = p->my; ax.tw = t.tw_x; ax.C = p->Cx; ax.logC = ilog2c(p->Cx); ax.ld = p->Cx + 1;
   cudaError_t e = launch_axis(ax, st);
   if (e != cudaSuccess) return e;
-  AxisArgs<T> ay{};
-  ay.S = p->S; ay.n = p->my; ay.lines = J * p->mx; ay.mode = 1; ay.P = p->mx; ay.op = 1;
-  ay.sigma = t.sigma; ay.lam_axis = t.lam_y; ay.lam_other = t.lam_x;
-  ay.scale = (T)(-4.0 * (p->mx + 1) * (double)(p->my + 1)); ay.lines_per_j = p->mx;
-  ay.tw = t.tw_y; ay.C = p->Cy; ay.ld = p->Cy + 1;
-  e = launch_axis(ay, st);
+  if (ysolve_tri<T>(p)) {
+    TriArgs tr{};
+    tr.S = reinterpret_cast<float2*>(p->S); tr.n = p->my; tr.P = p->mx; tr.lines = J * p->mx;
+    tr.sigma = reinterpret_cast<const float2*>(t.sigma); tr.lam_x = reinterpret_cast<const float*>(t.lam_x);
+    tr.g = (float)p->gy; tr.scale = (float)(-0.5 / (p->mx + 1));
+    tr.C = p->Ctri; tr.logC = ilog2c(p->Ctri);
+    e = launch_tri(tr, st);
+  } else {
+    AxisArgs<T> ay{};
+    ay.S = p->S; ay.n = p->my; ay.lines = J * p->mx; ay.mode = 1; ay.P = p->mx; ay.op = 1;
+    ay.sigma = t.sigma; ay.lam_axis = t.lam_y; ay.lam_other = t.lam_x;
+    ay.scale = (T)(-4.0 * (p->mx + 1) * (double)(p->my + 1)); ay.lines_per_j = p->mx;
+    ay.tw = t.tw_y; ay.C = p->Cy; ay.logC = ilog2c(p->Cy); ay.ld = p->Cy + 1;
+    e = launch_axis(ay, st);
+  }
   if (e != cudaSuccess) return e;
   return launch_axis(ax, st);
 }
 
-// MIXED sweep on the plan's double-float iterate (Uhi/Ulo) and F_hat (Fhi/Flo)
-pint_status sweep_mixed(pint_plan p, cudaStream_t st) {
+// Time the two y-direction solvers (sine transform vs tridiagonal) on this plan's workspace
+// and keep the faster; the choice is cached per (N, mx, my, precision) for the process.
+pint_status autotune_ysolve(pint_plan p) {
+  static std::mutex mu;
+  static std::vector<std::pair<long long, int>> cache;
+  const long long key = (((long long)p->N * 4096 + p->mx) * 4096 + p->my) * 4 + (int)p->prec;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& kv : cache)
+      if (kv.first == key) { p->ysolve = kv.second; return PINT_OK; }
+  }
+  cudaStream_t st;
+  PINT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bestv = 1;
+  const bool prof = g_prof_on;
+  g_prof_on = false;
+  for (int v = 1; v <= 2; ++v) {
+    p->ysolve = v;
+    cudaError_t e = spatial<float>(p, p->tf, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = spatial<float>(p, p->tf, st);
+    cudaEventRecord(e1, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || se != cudaSuccess) {
+      g_prof_on = prof;
+      cudaEventDestroy(e0); cudaEventDestroy(e1); cudaStreamDestroy(st);
+      return cuda_fail(e != cudaSuccess ? e : se, "autotune");
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; bestv = v; }
+  }
+  g_prof_on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  p->ysolve = bestv;
+  std::lock_guard<std::mutex> lk(mu);
+  cache.push_back({key, bestv});
+  return PINT_OK;
+}
+
+// MIXED sweep on the plan's double-float iterate (Uhi/Ulo); F_hat read in FP64
+pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   const int N = p->N, M = p->M;
   if (p->cq) {
     ToepArgs ta{};
     ta.Uhi = p->Uhi; ta.Ulo = p->Ulo; ta.ukind = 1; ta.out = p->z; ta.what = p->what_lo;
-    ta.tw = p->tw_2n; ta.N = N; ta.M = M; ta.C = p->Cz; ta.half = 0;
+    ta.tw = p->tw_2n; ta.N = N; ta.M = M; ta.C = p->Cz; ta.logC = ilog2c(p->Cz); ta.half = 0;
     cudaError_t e = launch_toeplitz(ta, st);
     if (e != cudaSuccess) return cuda_fail(e, "toeplitz kernel");
   }
   PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
   ResidFwdArgs r{};
-  r.Uhi = p->Uhi; r.Ulo = p->Ulo; r.Fhi = p->Fhi; r.Flo = p->Flo;
+  r.Uhi = p->Uhi; r.Ulo = p->Ulo; r.F = Fhat;
   r.y = p->cq ? p->z : nullptr;
   r.S = reinterpret_cast<float2*>(p->S);
   r.s = p->tf.s; r.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
-  r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Ct;
+  r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Ct; r.logC = ilog2c(p->Ct);
   const double ta = std::pow(p->tau, -p->alpha);
   double c0 = 2.0 * p->gx + 2.0 * p->gy;
   if (!p->cq) {
@@ -559,7 +635,7 @@ pint_status sweep_mixed(pint_plan p, cudaStream_t st) {
   InvUpdArgs u{};
   u.S = reinterpret_cast<const float2*>(p->S); u.Uhi = p->Uhi; u.Ulo = p->Ulo;
   u.inv_s = p->tf.inv_s; u.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
-  u.N = N; u.M = M; u.C = p->Ct; u.norms = p->norms;
+  u.N = N; u.M = M; u.C = p->Ct; u.logC = ilog2c(p->Ct); u.norms = p->norms;
   e = launch_inv_upd(u, st);
   if (e != cudaSuccess) return cuda_fail(e, "update kernel");
   return PINT_OK;
@@ -574,14 +650,15 @@ pint_status sweep_direct(pint_plan p, const DevTables<T>& t, const T* F, const T
     ToepArgs ta{};
     if (sizeof(T) == 8) { ta.Ud = reinterpret_cast<const double*>(Uin); ta.ukind = 0; }
     else { ta.Uf = reinterpret_cast<const float*>(Uin); ta.ukind = 2; }
-    ta.out = p->z; ta.what = p->what_up; ta.tw = p->tw_2n; ta.N = N; ta.M = M; ta.C = p->Cz; ta.half = 1;
+    ta.out = p->z; ta.what = p->what_up; ta.tw = p->tw_2n; ta.N = N; ta.M = M; ta.C = p->Cz;
+    ta.logC = ilog2c(p->Cz); ta.half = 1;
     cudaError_t e = launch_toeplitz(ta, st);
     if (e != cudaSuccess) return cuda_fail(e, "toeplitz kernel");
   }
   PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
   DirectFwdArgs<T> f{};
   f.F = F; f.U = Uin; f.z = p->cq ? p->z : nullptr; f.S = p->S; f.s = t.s; f.tw = t.tw_time;
-  f.N = N; f.M = M; f.C = p->Ctd; f.k = p->cq ? 0 : p->k;
+  f.N = N; f.M = M; f.C = p->Ctd; f.logC = ilog2c(p->Ctd); f.k = p->cq ? 0 : p->k;
   const double kt = p->kappa * std::pow(p->tau, -p->alpha);
   for (int j = 0; j <= p->k; ++j) f.kw[j] = (T)(kt * p->omega[j]);
   cudaError_t e = launch_direct_fwd(f, st);
@@ -590,7 +667,7 @@ pint_status sweep_direct(pint_plan p, const DevTables<T>& t, const T* F, const T
   if (e != cudaSuccess) return cuda_fail(e, "spatial kernel");
   DirectInvArgs<T> iv{};
   iv.S = p->S; iv.Uold = Uin; iv.Uout = Uout; iv.inv_s = t.inv_s; iv.tw = t.tw_time;
-  iv.N = N; iv.M = M; iv.C = p->Ctd; iv.norms = p->norms;
+  iv.N = N; iv.M = M; iv.C = p->Ctd; iv.logC = ilog2c(p->Ctd); iv.norms = p->norms;
   e = launch_direct_inv(iv, st);
   if (e != cudaSuccess) return cuda_fail(e, "direct inv kernel");
   return PINT_OK;
@@ -610,9 +687,8 @@ pint_status sweep_user(pint_plan p, const double* Fhat, const double* Uin, doubl
   cudaError_t e;
   if (p->prec == PINT_FP64) return sweep_direct<double>(p, p->td, Fhat, Uin, Uout, st);
   if (p->prec == PINT_MIXED) {
-    if ((e = launch_d2ff(Fhat, p->Fhi, p->Flo, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
     if ((e = launch_d2ff(Uin, p->Uhi, p->Ulo, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
-    pint_status s = sweep_mixed(p, st);
+    pint_status s = sweep_mixed(p, Fhat, st);
     if (s != PINT_OK) return s;
     if ((e = launch_ff2d(p->Uhi, p->Ulo, Uout, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
     return PINT_OK;
@@ -645,7 +721,6 @@ extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, do
   const size_t NM = (size_t)p->N * p->M;
   cudaError_t e;
   if (p->prec == PINT_MIXED) {
-    if ((e = launch_d2ff(Fhat, p->Fhi, p->Flo, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
     if ((e = launch_d2ff(U, p->Uhi, p->Ulo, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
   } else if (p->prec == PINT_FP32) {
     if ((e = launch_d2f(Fhat, p->Fhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
@@ -656,7 +731,7 @@ extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, do
   bool done = false;
   pint_status s = PINT_OK;
   while (m < max_sweeps && !done) {
-    if (p->prec == PINT_MIXED) s = sweep_mixed(p, st);
+    if (p->prec == PINT_MIXED) s = sweep_mixed(p, Fhat, st);
     else if (p->prec == PINT_FP64) s = sweep_direct<double>(p, p->td, Fhat, U, U, st);
     else s = sweep_direct<float>(p, p->tf, p->Fhi, p->Uhi, p->Uhi, st);
     if (s != PINT_OK) return s;

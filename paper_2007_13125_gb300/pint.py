@@ -37,7 +37,7 @@ class _Grid(ctypes.Structure):
 class _Desc(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("alpha", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("tau", ctypes.c_double), ("N", ctypes.c_int), ("grid", _Grid),
-                ("precision", ctypes.c_int), ("eig", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("eig", ctypes.c_int), ("ysolve", ctypes.c_int)]
 
 
 class _Req(ctypes.Structure):
@@ -187,10 +187,10 @@ class Plan:
     """Owns a pint_plan handle."""
 
     def __init__(self, k, alpha, kappa, tau, N, dim, mx, my=1, precision="mixed",
-                 eig=PINT_EIG_TRUNC_DFT):
+                 eig=PINT_EIG_TRUNC_DFT, ysolve=0):
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         d = _Desc(k, float(alpha), float(kappa), float(tau), int(N), _Grid(dim, mx, my if dim == 2 else 1),
-                  prec, eig)
+                  prec, eig, int(ysolve))
         h = _P()
         check(lib().pint_plan_create_desc(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -200,8 +200,8 @@ class Plan:
         self.precision = prec
 
     @classmethod
-    def for_problem(cls, p, precision="mixed", eig=PINT_EIG_TRUNC_DFT):
-        return cls(p.k, p.alpha, p.kappa, p.tau, p.N, p.dim, p.mx, p.my, precision, eig)
+    def for_problem(cls, p, precision="mixed", eig=PINT_EIG_TRUNC_DFT, ysolve=0):
+        return cls(p.k, p.alpha, p.kappa, p.tau, p.N, p.dim, p.mx, p.my, precision, eig, ysolve)
 
     def close(self):
         if self.handle:
@@ -270,7 +270,7 @@ class Server:
         """v, f, fderiv: host float64 numpy arrays (copied at submit)."""
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         d = _Desc(p.k, float(p.alpha), float(p.kappa), float(p.tau), int(p.N),
-                  _Grid(p.dim, p.mx, p.my if p.dim == 2 else 1), prec, PINT_EIG_TRUNC_DFT)
+                  _Grid(p.dim, p.mx, p.my if p.dim == 2 else 1), prec, PINT_EIG_TRUNC_DFT, 0)
         req = _Req(d, float(tol), int(max_sweeps))
         t = ctypes.c_uint64(0)
         v = np.ascontiguousarray(v, dtype=np.float64)

@@ -139,11 +139,32 @@ def test_fp32_floor_reported():
 
 
 def test_closed_form_eigenvalues_converge_to_same_solution():
+    # residual form: the fixed point is K U = F_hat for either preconditioner
     torch = torch_cuda()
     p = _p(1, 63, 64, 3, 0.5, 0.1)
     ref = oracle_solution(p)
-    U, st, sweeps, upd = gpu_solve(p, torch, "fp64", tol=1e-12, eig=1)
-    assert st == 0 and rel_l2(U, ref) <= 1e-10
+    U, st, sweeps, upd = gpu_solve(p, torch, "mixed", tol=1e-11, eig=1)
+    assert st == 0 and rel_l2(U, ref) <= 1e-8
+    from paper_2007_13125_gb300 import Plan, PintError
+    with pytest.raises(PintError):
+        Plan.for_problem(p, "fp64", eig=1)
+
+
+@pytest.mark.parametrize("ysolve", [1, 2])
+@pytest.mark.parametrize("case", [(2, 31, 32, 4, 1.0, 0.05), (2, 63, 16, 2, 0.5, 0.1), (2, 7, 64, 6, 1.0, 0.1)])
+def test_ysolve_variants(case, ysolve):
+    torch = torch_cuda()
+    p = _p(*case)
+    ref = oracle_solution(p)
+    from paper_2007_13125_gb300 import Plan
+    v, f, fd = device_inputs(p, torch)
+    with Plan.for_problem(p, "mixed", ysolve=ysolve) as plan:
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        plan.form_rhs(v, f, fd, F)
+        U = torch.empty_like(F)
+        plan.initial_guess(v, U)
+        st, sweeps, upd = plan.solve(F, U, tol=1e-10)
+    assert rel_l2(U.cpu().numpy(), ref) <= 1e-8, (sweeps, upd)
 
 
 def test_edge_sizes():
