@@ -125,6 +125,11 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
   for (int j = 0; j <= kMaxK; ++j) { cw[j].hi = a.c_hi[j]; cw[j].lo = a.c_lo[j]; }
   const ff gx = {a.gx_hi, a.gx_lo}, gy = {a.gy_hi, a.gy_lo};
 
+  // Lane layout: a warp holds whole groups of C consecutive columns that share one time
+  // chunk, so at every level the x-neighbours of a point sit in adjacent lanes (or in the
+  // other half of the pair): they come from warp shuffles, and only the two tile edges
+  // (points m0 - 1 and m0 + 2C) are loaded from memory. y-neighbours are plain loads.
+  const int lane = threadIdx.x & 31;
   int mm[2];
   bool valid[2];
   int xx[2];
@@ -134,6 +139,8 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
     valid[h] = mm[h] < M;
     xx[h] = valid[h] ? mm[h] % a.mx : 0;
   }
+  const int src_l = c > 0 ? lane - 1 : lane + C - 1;       // left of half 1 when c == 0: half 0, col C-1
+  const int src_r = c < C - 1 ? lane + 1 : lane - (C - 1); // right of half 0 when c == C-1: half 1, col 0
   ff win[2][kMaxK];
 #pragma unroll
   for (int h = 0; h < 2; ++h)
@@ -147,23 +154,52 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
 #pragma unroll 2
   for (int i = i0; i < i0 + Lc; ++i) {
     const float si = __ldg(a.s + i);
+    const size_t row = (size_t)i * M;
+    ff u[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      u[h].hi = 0.f;
+      u[h].lo = 0.f;
+      if (valid[h]) u[h] = ldff(a.Uhi, a.Ulo, row + mm[h]);
+    }
+    // x-neighbours: a shuffle delivers the *sender's* argument, so each shuffle moves one
+    // fixed half and the receiver picks which result it needs.
+    ff lft[2], rgt[2];
+    {
+      const int sl = c > 0 ? lane - 1 : lane + C - 1;
+      const int sr = c < C - 1 ? lane + 1 : lane - (C - 1);
+      ff s1, s2, s3, s4;
+      s1.hi = __shfl_sync(0xffffffffu, u[0].hi, sl);      // c > 0: left of half 0; c == 0: left of half 1
+      s1.lo = __shfl_sync(0xffffffffu, u[0].lo, sl);
+      s2.hi = __shfl_sync(0xffffffffu, u[1].hi, lane - 1); // c > 0: left of half 1
+      s2.lo = __shfl_sync(0xffffffffu, u[1].lo, lane - 1);
+      s3.hi = __shfl_sync(0xffffffffu, u[1].hi, sr);      // c < C-1: right of half 1; c == C-1: right of half 0
+      s3.lo = __shfl_sync(0xffffffffu, u[1].lo, sr);
+      s4.hi = __shfl_sync(0xffffffffu, u[0].hi, lane + 1); // c < C-1: right of half 0
+      s4.lo = __shfl_sync(0xffffffffu, u[0].lo, lane + 1);
+      lft[0] = s1;
+      lft[1] = c > 0 ? s2 : s1;
+      rgt[0] = c < C - 1 ? s4 : s3;
+      rgt[1] = s3;
+    }
+    if (c == 0 && valid[0] && xx[0] > 0) lft[0] = ldff(a.Uhi, a.Ulo, row + mm[0] - 1);
+    if (c == C - 1 && valid[1] && xx[1] < a.mx - 1) rgt[1] = ldff(a.Uhi, a.Ulo, row + mm[1] + 1);
     float r[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       r[h] = 0.f;
       if (!valid[h]) continue;
       const int m = mm[h];
-      const size_t idx = (size_t)i * M + m;
-      const ff u = ldff(a.Uhi, a.Ulo, idx);
+      const size_t idx = row + m;
       ff_acc acc;
       acc.init(ff_from_double(__ldg(a.F + idx)));
       if (a.y) acc.sub(ff_from_double(__ldg(a.y + idx)));
-      acc.fma_term(cw[0], u, -1.f);
+      acc.fma_term(cw[0], u[h], -1.f);
 #pragma unroll
       for (int j = 1; j <= kMaxK; ++j)
         if (j <= k) acc.fma_term(cw[j], win[h][j - 1], -1.f);
-      if (xx[h] > 0) acc.fma_term(gx, ldff(a.Uhi, a.Ulo, idx - 1), 1.f);
-      if (xx[h] < a.mx - 1) acc.fma_term(gx, ldff(a.Uhi, a.Ulo, idx + 1), 1.f);
+      if (xx[h] > 0) acc.fma_term(gx, lft[h], 1.f);
+      if (xx[h] < a.mx - 1) acc.fma_term(gx, rgt[h], 1.f);
       if (a.dim == 2) {
         if (m >= a.mx) acc.fma_term(gy, ldff(a.Uhi, a.Ulo, idx - a.mx), 1.f);
         if (m + a.mx < M) acc.fma_term(gy, ldff(a.Uhi, a.Ulo, idx + a.mx), 1.f);
@@ -171,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
       r[h] = acc.value() * si;
 #pragma unroll
       for (int j = kMaxK - 1; j > 0; --j) win[h][j] = win[h][j - 1];
-      win[h][0] = u;
+      win[h][0] = u[h];
     }
     X[(size_t)i * C + c] = make_float2(r[0], r[1]);
   }
@@ -197,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_inv_upd(InvUpdArgs a) {
   __syncthreads();
   fft_inverse(X, C, logC, N, tw);
 
-  double sc = 0.0, su = 0.0;
+  float sc = 0.f, su = 0.f;  // per-thread partial norms (FP32: the FP64 pipe is ~1/70 rate)
   for (int it = threadIdx.x; it < (N << logC); it += blockDim.x) {
     const int cc = it & (C - 1), i = it >> logC;
     const float2 z = X[(size_t)i * C + cc];
@@ -212,11 +248,11 @@ __global__ void __launch_bounds__(kThreads) k_inv_upd(InvUpdArgs a) {
       u = ff_add_f(u, cval);
       a.Uhi[idx] = u.hi;
       a.Ulo[idx] = u.lo;
-      sc += (double)(cval * cval);
-      su += (double)(u.hi * u.hi);
+      sc = fmaf(cval, cval, sc);
+      su = fmaf(u.hi, u.hi, su);
     }
   }
-  block_reduce_add2(sc, su, a.norms);
+  block_reduce_add2((double)sc, (double)su, a.norms);
 }
 
 // ---------------------------------------------------------------------------

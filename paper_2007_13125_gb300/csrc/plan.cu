@@ -453,8 +453,9 @@ extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan*
   p->Ctd = pick_cols((size_t)N * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2)), budget, 32, cmin_t);
   p->Cz = pick_cols((size_t)2 * N * sizeof(double2), 160 * 1024, 16, 1);
   const size_t ve = p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2);
-  p->Cx = pick_cols((size_t)2 * (p->mx + 1) * ve, budget, 16, 1);
-  p->Cy = pick_cols((size_t)2 * (p->my + 1) * ve, budget, 16, 1);
+  // sine-transform tiles: ~40 KB of lines so that several CTAs share an SM
+  p->Cx = pick_cols((size_t)2 * (p->mx + 1) * ve, 40 * 1024, 16, 1);
+  p->Cy = pick_cols((size_t)2 * (p->my + 1) * ve, 40 * 1024, 16, 1);
   p->Ctri = pick_cols((size_t)p->my * sizeof(float2), 72 * 1024, 32, 1);
   PINT_CUDA_B(cudaMemset(p->S, 0, JM * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2))));
   p->ysolve = 1;
