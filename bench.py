@@ -4,8 +4,9 @@ Workload (one "step" = one whole solve through the hot path): 2D heat on the uni
 255 x 255 interior points, N = 256 steps, T = 1, BDF4 with starting-step corrections,
 kappa = 0.05, f = e^{-t} sin(pi x) sin(2 pi y), v a 64 x 64-mode random sine series (seed 1).
 A step forms F_hat from (v, f, d^l f(0)), sets U_0 = v and runs WR sweeps until the
-solver's a-posteriori error estimate is below tol = 1e-9 (relative l2 error <= 1e-8 against
-the sequential FP64 solution is checked at this size by tests/test_gpu_parity.py).
+solver's a-posteriori error estimate is below tol = 1e-8 (the estimate includes the rounding
+floor of the FP32 inner solves; relative l2 error <= 1e-8 against the sequential FP64 solution
+is checked at this size and tolerance by tests/test_gpu_parity.py).
 
 value   = space-time DOF (N * M) per second of the MIXED path, inputs resident in HBM.
 e2e     = the same through host buffers (pinned H2D of v, f, d^l f(0); D2H of U) per step.
@@ -34,7 +35,7 @@ import workloads  # noqa: E402
 
 METRIC = "space-time DOF/s to rel err 1e-8 (mixed vs FP64 diag); p50/p99 solve latency"
 UNIT = "DOF/s"
-TOL = 1e-9
+TOL = 1e-8
 
 # algorithmic bytes per launch of each kernel, as a function of (N, M); see the design doc
 def algo_bytes(name: str, N: int, M: int) -> float:

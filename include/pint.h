@@ -91,9 +91,11 @@ typedef struct {
   pint_grid grid;
   pint_precision precision;
   pint_eig_variant eig;
-  int ysolve;             /* 2D y-direction solver of the shifted systems: 0 = choose by timing
-                             both at plan creation (cached per shape), 1 = sine transform,
-                             2 = tridiagonal (FP32 inner solves only; FP64 uses 1) */
+  int ysolve;             /* 2D y-direction solver of the shifted systems: 0 or 1 = sine transform
+                             (default), 2 = tridiagonal (FP32 inner solves only; FP64 uses 1),
+                             3 = whichever of 1 and 2 runs faster on this GPU, timed at plan
+                             creation (cached per shape). The sine transform is the default: its
+                             inner solves are more accurate, which saves a sweep (see DESIGN) */
 } pint_plan_desc;
 
 /* Build a plan: FP64 constant tables (BDF / CQ weights omega_j of eq. (2.2) / eq. (3.2) --
@@ -137,10 +139,12 @@ pint_status pint_wr_sweep(pint_plan plan, const double* Fhat, const double* U_pr
                           double* upd_rel, void* stream);
 
 /* Iterate sweeps from the initial guess in U until converged (Theorem 2.7 uses U_0^n = v).
- * After sweep m, upd_m = ||U_m - U_{m-1}|| / ||U_m||; for m >= 2 with q = upd_m / upd_{m-1} < 1 the
- * error estimate is upd_m q / (1 - q). Stops when that estimate is <= tol (or upd_1 <= tol/100),
- * or, if the ratio stagnates (q >= 1), when upd_m <= tol. Returns PINT_ENOTCONV after max_sweeps
- * otherwise (U then holds the last iterate).
+ * After sweep m, upd_m = ||U_m - U_{m-1}|| / ||U_m||. For m >= 2 the contraction is estimated as
+ * q = max(upd_m / upd_{m-1}, q_floor), q_floor = eps * (lambda_max + max_j |g_j| tau^-alpha) /
+ * min_j |g_j tau^-alpha + lambda_min| / kappa the rounding floor of the inner solves (eps = 2^-24
+ * for MIXED/FP32, 2^-53 for FP64), and the error estimate is upd_m q / (1 - q). Stops when that
+ * estimate is <= tol (or upd_1 <= tol/100), or, if q >= 1, when upd_m <= tol. Returns
+ * PINT_ENOTCONV after max_sweeps otherwise (U then holds the last iterate).
  * Fhat [N][M] device input; U [N][M] device, in: initial guess, out: solution.
  * sweeps_out, upd_rel_out: optional host pointers. Synchronises `stream` once per sweep to read
  * two norms (16 bytes). */

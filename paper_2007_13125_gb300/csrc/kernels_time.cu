@@ -86,6 +86,7 @@ template <typename V>
 __device__ __forceinline__ void load_half_spectrum(V* X, const unsigned short* perm, const V* S, int N,
                                                    int M, int C, int logC, int m0) {
   const int J = N / 2 + 1;
+#pragma unroll 4
   for (int it = threadIdx.x; it < (J << logC); it += blockDim.x) {
     const int cc = it & (C - 1), j = it >> logC;
     const int ma = m0 + cc, mb = m0 + C + cc;
@@ -103,115 +104,143 @@ __device__ __forceinline__ void load_half_spectrum(V* X, const unsigned short* p
 // MIXED: residual r = F_hat - K U (double-float) + kappa scaling + forward DFT along time.
 // K U = tau^-alpha sum_{j=0}^{min(n-1,k)} omega_j U^{n-j} + A_h U^n (BDF band, eq. (2.6) with
 // kappa = 0), or, for CQ, the precomputed Toeplitz history y plus A_h U^n.
+//
+// The tile (2C points x all N levels) is processed in chunks of kLK levels. Each chunk is
+// first staged in shared memory with asynchronous copies issued by all threads at once
+// (U with kMaxK levels of history and the two x-halo points, the two y-neighbour rows, F_hat
+// and y), then every thread evaluates residuals from shared memory only.
 // ---------------------------------------------------------------------------
-size_t resid_fwd_smem(int N, int C) { return time_tile_bytes<float2>(N, C); }
+constexpr int kLK = 16;                      // levels per staged chunk
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+struct ResidStage {
+  // row-major [level][point] arrays of the staged chunk
+  int W;           // 2C + 2 (U incl. x halo)
+  int P2;          // 2C
+  float* Uh;       // [kLK + kMaxK][W]
+  float* Ul;
+  float* Yh;       // [2][kLK][P2]  (row below, row above)
+  float* Yl;
+  double* F;       // [kLK][P2]
+  double* Yc;      // [kLK][P2] (CQ history) or unused
+};
+
+__host__ __device__ inline size_t resid_stage_bytes(int C) {
+  const size_t W = 2 * (size_t)C + 2, P2 = 2 * (size_t)C;
+  return 2 * sizeof(float) * (kLK + kMaxK) * W + 2 * sizeof(float) * 2 * kLK * P2 +
+         2 * sizeof(double) * kLK * P2;
+}
+
+size_t resid_fwd_smem(int N, int C) { return time_tile_bytes<float2>(N, C) + resid_stage_bytes(C) + 16; }
 
 __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = a.N, C = a.C, M = a.M, logC = a.logC;
+  const int N = a.N, C = a.C, M = a.M, logC = a.logC, mx = a.mx;
   float2 *X, *tw;
   unsigned short* perm;
   time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
+  unsigned char* sp = reinterpret_cast<unsigned char*>(perm + N);
+  sp = reinterpret_cast<unsigned char*>(((size_t)sp + 15) & ~(size_t)15);
+  ResidStage st;
+  st.W = 2 * C + 2;
+  st.P2 = 2 * C;
+  st.F = reinterpret_cast<double*>(sp);
+  st.Yc = st.F + kLK * st.P2;
+  st.Uh = reinterpret_cast<float*>(st.Yc + kLK * st.P2);
+  st.Ul = st.Uh + (kLK + kMaxK) * st.W;
+  st.Yh = st.Ul + (kLK + kMaxK) * st.W;
+  st.Yl = st.Yh + 2 * kLK * st.P2;
 
   const int m0 = blockIdx.x * 2 * C;
-  const int c = threadIdx.x & (C - 1);
-  const int nch = blockDim.x >> logC;
-  const int tc = threadIdx.x >> logC;
-  const int Lc = N / nch;
-  const int i0 = tc * Lc;
+  const int P2 = st.P2, W = st.W;
   const int k = a.k;
   ff cw[kMaxK + 1];
 #pragma unroll
   for (int j = 0; j <= kMaxK; ++j) { cw[j].hi = a.c_hi[j]; cw[j].lo = a.c_lo[j]; }
   const ff gx = {a.gx_hi, a.gx_lo}, gy = {a.gy_hi, a.gy_lo};
+  const bool two_d = a.dim == 2;
 
-  // Lane layout: a warp holds whole groups of C consecutive columns that share one time
-  // chunk, so at every level the x-neighbours of a point sit in adjacent lanes (or in the
-  // other half of the pair): they come from warp shuffles, and only the two tile edges
-  // (points m0 - 1 and m0 + 2C) are loaded from memory. y-neighbours are plain loads.
-  const int lane = threadIdx.x & 31;
-  int mm[2];
-  bool valid[2];
-  int xx[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    mm[h] = m0 + h * C + c;
-    valid[h] = mm[h] < M;
-    xx[h] = valid[h] ? mm[h] % a.mx : 0;
-  }
-  const int src_l = c > 0 ? lane - 1 : lane + C - 1;       // left of half 1 when c == 0: half 0, col C-1
-  const int src_r = c < C - 1 ? lane + 1 : lane - (C - 1); // right of half 0 when c == C-1: half 1, col 0
-  ff win[2][kMaxK];
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int j = 0; j < kMaxK; ++j) {
-      const int lev = i0 - 1 - j;
-      win[h][j].hi = 0.f;
-      win[h][j].lo = 0.f;
-      if (j < k && valid[h] && lev >= 0) win[h][j] = ldff(a.Uhi, a.Ulo, (size_t)lev * M + mm[h]);
-    }
-#pragma unroll 2
-  for (int i = i0; i < i0 + Lc; ++i) {
-    const float si = __ldg(a.s + i);
-    const size_t row = (size_t)i * M;
-    ff u[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      u[h].hi = 0.f;
-      u[h].lo = 0.f;
-      if (valid[h]) u[h] = ldff(a.Uhi, a.Ulo, row + mm[h]);
-    }
-    // x-neighbours: a shuffle delivers the *sender's* argument, so each shuffle moves one
-    // fixed half and the receiver picks which result it needs.
-    ff lft[2], rgt[2];
-    {
-      const int sl = c > 0 ? lane - 1 : lane + C - 1;
-      const int sr = c < C - 1 ? lane + 1 : lane - (C - 1);
-      ff s1, s2, s3, s4;
-      s1.hi = __shfl_sync(0xffffffffu, u[0].hi, sl);      // c > 0: left of half 0; c == 0: left of half 1
-      s1.lo = __shfl_sync(0xffffffffu, u[0].lo, sl);
-      s2.hi = __shfl_sync(0xffffffffu, u[1].hi, lane - 1); // c > 0: left of half 1
-      s2.lo = __shfl_sync(0xffffffffu, u[1].lo, lane - 1);
-      s3.hi = __shfl_sync(0xffffffffu, u[1].hi, sr);      // c < C-1: right of half 1; c == C-1: right of half 0
-      s3.lo = __shfl_sync(0xffffffffu, u[1].lo, sr);
-      s4.hi = __shfl_sync(0xffffffffu, u[0].hi, lane + 1); // c < C-1: right of half 0
-      s4.lo = __shfl_sync(0xffffffffu, u[0].lo, lane + 1);
-      lft[0] = s1;
-      lft[1] = c > 0 ? s2 : s1;
-      rgt[0] = c < C - 1 ? s4 : s3;
-      rgt[1] = s3;
-    }
-    if (c == 0 && valid[0] && xx[0] > 0) lft[0] = ldff(a.Uhi, a.Ulo, row + mm[0] - 1);
-    if (c == C - 1 && valid[1] && xx[1] < a.mx - 1) rgt[1] = ldff(a.Uhi, a.Ulo, row + mm[1] + 1);
-    float r[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      r[h] = 0.f;
-      if (!valid[h]) continue;
-      const int m = mm[h];
-      const size_t idx = row + m;
-      ff_acc acc;
-      acc.init(ff_from_double(__ldg(a.F + idx)));
-      if (a.y) acc.sub(ff_from_double(__ldg(a.y + idx)));
-      acc.fma_term(cw[0], u[h], -1.f);
-#pragma unroll
-      for (int j = 1; j <= kMaxK; ++j)
-        if (j <= k) acc.fma_term(cw[j], win[h][j - 1], -1.f);
-      if (xx[h] > 0) acc.fma_term(gx, lft[h], 1.f);
-      if (xx[h] < a.mx - 1) acc.fma_term(gx, rgt[h], 1.f);
-      if (a.dim == 2) {
-        if (m >= a.mx) acc.fma_term(gy, ldff(a.Uhi, a.Ulo, idx - a.mx), 1.f);
-        if (m + a.mx < M) acc.fma_term(gy, ldff(a.Uhi, a.Ulo, idx + a.mx), 1.f);
+  // Each thread keeps one point q of the tile (2C divides the block size) and walks levels.
+  const int logP2 = logC + 1;
+  const int q = threadIdx.x & (P2 - 1);
+  const int lstep = blockDim.x >> logP2;
+  const int mq = m0 + q;
+  const bool qvalid = mq < M;
+  const int xq = qvalid ? mq % mx : 0;
+  for (int c0 = 0; c0 < N; c0 += kLK) {
+    const int LK = min(kLK, N - c0);
+    // ---- stage chunk levels [c0, c0 + LK) (+ kMaxK levels of history for U) ----
+    for (int e = threadIdx.x; e < (kLK + kMaxK) * W; e += blockDim.x) {
+      const int l = e / W, qq = e - l * W;
+      const int lev = c0 - kMaxK + l;
+      const int m = m0 - 1 + qq;
+      float* dh = st.Uh + e;
+      float* dl = st.Ul + e;
+      if (lev >= 0 && lev < N && m >= 0 && m < M) {
+        const size_t g = (size_t)lev * M + m;
+        cp_async4(dh, a.Uhi + g);
+        cp_async4(dl, a.Ulo + g);
+      } else {
+        *dh = 0.f;
+        *dl = 0.f;
       }
-      r[h] = acc.value() * si;
-#pragma unroll
-      for (int j = kMaxK - 1; j > 0; --j) win[h][j] = win[h][j - 1];
-      win[h][0] = u[h];
     }
-    X[(size_t)i * C + c] = make_float2(r[0], r[1]);
+    for (int l = threadIdx.x >> logP2; l < LK; l += lstep) {
+      const int e = (l << logP2) + q;
+      const size_t g = (size_t)(c0 + l) * M + mq;
+      if (qvalid) {
+        cp_async8(st.F + e, a.F + g);
+        if (a.y) cp_async8(st.Yc + e, a.y + g);
+      }
+      if (two_d) {
+        float* bh = st.Yh + e;
+        float* bl = st.Yl + e;
+        float* ah = st.Yh + kLK * P2 + e;
+        float* al = st.Yl + kLK * P2 + e;
+        if (qvalid && mq >= mx) { cp_async4(bh, a.Uhi + g - mx); cp_async4(bl, a.Ulo + g - mx); }
+        else { *bh = 0.f; *bl = 0.f; }
+        if (mq + mx < M) { cp_async4(ah, a.Uhi + g + mx); cp_async4(al, a.Ulo + g + mx); }
+        else { *ah = 0.f; *al = 0.f; }
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // ---- residuals of the chunk from shared memory ----
+    for (int l = threadIdx.x >> logP2; l < LK; l += lstep) {
+      const int e = (l << logP2) + q;
+      const int i = c0 + l;
+      float r = 0.f;
+      if (qvalid) {
+        const int ub = (l + kMaxK) * W + q + 1;  // this point in the U stage
+        ff_acc acc;
+        acc.init(ff_from_double(st.F[e]));
+        if (a.y) acc.sub(ff_from_double(st.Yc[e]));
+        acc.fma_term(cw[0], ff{st.Uh[ub], st.Ul[ub]}, -1.f);
+#pragma unroll
+        for (int j = 1; j <= kMaxK; ++j)
+          if (j <= k) acc.fma_term(cw[j], ff{st.Uh[ub - j * W], st.Ul[ub - j * W]}, -1.f);
+        if (xq > 0) acc.fma_term(gx, ff{st.Uh[ub - 1], st.Ul[ub - 1]}, 1.f);
+        if (xq < mx - 1) acc.fma_term(gx, ff{st.Uh[ub + 1], st.Ul[ub + 1]}, 1.f);
+        if (two_d) {
+          acc.fma_term(gy, ff{st.Yh[e], st.Yl[e]}, 1.f);
+          acc.fma_term(gy, ff{st.Yh[kLK * P2 + e], st.Yl[kLK * P2 + e]}, 1.f);
+        }
+        r = acc.value() * __ldg(a.s + i);
+      }
+      float* xs = reinterpret_cast<float*>(X + (size_t)i * C + (q & (C - 1)));
+      xs[q >= C ? 1 : 0] = r;
+    }
+    __syncthreads();  // the stage is reused by the next chunk
   }
-  __syncthreads();
   fft_forward(X, C, logC, N, tw);
   store_half_spectrum(X, perm, a.S, N, M, C, logC, m0);
 }
@@ -234,6 +263,7 @@ __global__ void __launch_bounds__(kThreads) k_inv_upd(InvUpdArgs a) {
   fft_inverse(X, C, logC, N, tw);
 
   float sc = 0.f, su = 0.f;  // per-thread partial norms (FP32: the FP64 pipe is ~1/70 rate)
+#pragma unroll 4
   for (int it = threadIdx.x; it < (N << logC); it += blockDim.x) {
     const int cc = it & (C - 1), i = it >> logC;
     const float2 z = X[(size_t)i * C + cc];

@@ -242,6 +242,7 @@ struct pint_plan_s {
   // tiles
   int Ct, Ctd, Cz, Cx, Cy, Ctri;    // columns per CTA: time (float), time (T), toeplitz, x, y, tri
   int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal
+  double q_floor;                   // predicted floor of the per-sweep contraction (inner precision)
 };
 
 #define PINT_CUDA_B(call)                                      \
@@ -374,7 +375,7 @@ extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan*
   if (d->eig != PINT_EIG_TRUNC_DFT && d->eig != PINT_EIG_CLOSED_FORM) return fail(PINT_EINVAL, "bad eig variant");
   if (d->eig == PINT_EIG_CLOSED_FORM && d->alpha != 1.0 && d->precision != PINT_MIXED)
     return fail(PINT_EINVAL, "CLOSED_FORM eigenvalues with alpha < 1 need the residual form (PINT_MIXED)");
-  if (d->ysolve < 0 || d->ysolve > 2) return fail(PINT_EINVAL, "bad ysolve variant");
+  if (d->ysolve < 0 || d->ysolve > 3) return fail(PINT_EINVAL, "bad ysolve variant");
   pint_plan p = new pint_plan_s();
   p->k = d->k; p->alpha = d->alpha; p->kappa = d->kappa; p->tau = d->tau; p->N = d->N;
   p->dim = d->grid.dim; p->mx = d->grid.mx; p->my = d->grid.dim == 2 ? d->grid.my : 1;
@@ -460,8 +461,29 @@ extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan*
   PINT_CUDA_B(cudaMemset(p->S, 0, JM * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2))));
   p->ysolve = 1;
   if (p->dim == 2 && p->prec != PINT_FP64) {
-    if (d->ysolve == 1 || d->ysolve == 2) p->ysolve = d->ysolve;
-    else if ((s = autotune_ysolve(p)) != PINT_OK) return bail(s);
+    if (d->ysolve == 2) p->ysolve = 2;
+    else if (d->ysolve == 3 && (s = autotune_ysolve(p)) != PINT_OK) return bail(s);
+  }
+  {
+    // Inner-solve accuracy bounds the per-sweep contraction from below: rounding of size
+    // eps * ||r|| in the transforms is amplified by the spread of the shifted spectrum
+    // (max over min of |g_j tau^-alpha + lambda|) and by the kappa^{-1} unscaling.
+    const double hx = 1.0 / (p->mx + 1), hy = 1.0 / (p->my + 1);
+    double lmin = 4.0 / (hx * hx) * std::pow(std::sin(M_PI * hx / 2), 2);
+    double lmax = 4.0 / (hx * hx);
+    if (p->dim == 2) {
+      lmin += 4.0 / (hy * hy) * std::pow(std::sin(M_PI * hy / 2), 2);
+      lmax += 4.0 / (hy * hy);
+    }
+    const double ta = std::pow(p->tau, -p->alpha);
+    double smax = 0.0, dmin = 1e300;
+    for (int j = 0; j <= N / 2; ++j) {
+      const cd sg = p->g[j] * ta;
+      smax = std::max(smax, std::abs(sg));
+      dmin = std::min(dmin, std::abs(sg + lmin));
+    }
+    const double eps = p->prec == PINT_FP64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+    p->q_floor = std::min(0.5, eps * (lmax + smax) / dmin / p->kappa);
   }
   *out = p;
   return PINT_OK;
@@ -742,7 +764,8 @@ extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, do
       done = upd <= 0.01 * tol;
     } else {
       const double q = prev > 0.0 ? upd / prev : 0.0;
-      if (q < 1.0) done = upd * q / (1.0 - q) <= tol;
+      const double qh = std::max(q, p->q_floor);
+      if (qh < 1.0) done = upd * qh / (1.0 - qh) <= tol;
       else done = upd <= tol;
     }
     prev = upd;

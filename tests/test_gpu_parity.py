@@ -106,8 +106,8 @@ def test_config_c2_heat2d_full():
     torch = torch_cuda()
     p = workloads.c2_heat2d()
     ref = oracle_solution(p)
-    for prec, bar in (("fp64", 1e-10), ("mixed", 1e-8)):
-        U, st, sweeps, upd = gpu_solve(p, torch, prec, tol=1e-9)
+    for prec, bar, tol in (("fp64", 1e-10, 1e-10), ("mixed", 1e-8, 1e-8)):
+        U, st, sweeps, upd = gpu_solve(p, torch, prec, tol=tol)
         assert st == 0
         assert rel_l2(U, ref) <= bar, (prec, sweeps, upd)
         # final-time error (the paper's e_m^N metric)
