@@ -29,7 +29,7 @@ __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_axis(AxisArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
   using V = typename c2<T>::t;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n = a.n, C = a.C, logC = a.logC, ld = a.ld, L = 2 * (a.n + 1);

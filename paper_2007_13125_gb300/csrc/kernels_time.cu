@@ -121,6 +121,14 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
 
 struct ResidStage {
   // row-major [level][point] arrays of the staged chunk
@@ -179,19 +187,24 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
   for (int c0 = 0; c0 < N; c0 += kLK) {
     const int LK = min(kLK, N - c0);
     // ---- stage chunk levels [c0, c0 + LK) (+ kMaxK levels of history for U) ----
-    for (int e = threadIdx.x; e < (kLK + kMaxK) * W; e += blockDim.x) {
-      const int l = e / W, qq = e - l * W;
-      const int lev = c0 - kMaxK + l;
-      const int m = m0 - 1 + qq;
-      float* dh = st.Uh + e;
-      float* dl = st.Ul + e;
-      if (lev >= 0 && lev < N && m >= 0 && m < M) {
-        const size_t g = (size_t)lev * M + m;
-        cp_async4(dh, a.Uhi + g);
-        cp_async4(dl, a.Ulo + g);
-      } else {
-        *dh = 0.f;
-        *dl = 0.f;
+    {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+      for (int l = warp; l < kLK + kMaxK; l += nwarp) {
+        const int lev = c0 - kMaxK + l;
+        const bool lok = lev >= 0 && lev < N;
+        const size_t grow = (size_t)(lok ? lev : 0) * M;
+        for (int qq = lane; qq < W; qq += 32) {
+          const int m = m0 - 1 + qq;
+          float* dh = st.Uh + l * W + qq;
+          float* dl = st.Ul + l * W + qq;
+          if (lok && m >= 0 && m < M) {
+            cp_async4(dh, a.Uhi + grow + m);
+            cp_async4(dl, a.Ulo + grow + m);
+          } else {
+            *dh = 0.f;
+            *dl = 0.f;
+          }
+        }
       }
     }
     for (int l = threadIdx.x >> logP2; l < LK; l += lstep) {
@@ -257,6 +270,19 @@ __global__ void __launch_bounds__(kThreads) k_inv_upd(InvUpdArgs a) {
   unsigned short* perm;
   time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
   const int m0 = blockIdx.x * 2 * C;
+  {
+    // the update reads this tile's rows of U after the inverse FFT: start pulling them into L2
+    // now. Each span is rounded out to 16-byte boundaries and clipped to the array.
+    const size_t total = (size_t)N * M;
+    const int p1 = min(m0 + 2 * C, M);
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
+      const float* base = (i & 1) ? a.Ulo : a.Uhi;
+      const size_t b0 = ((size_t)(i >> 1) * M + m0) & ~(size_t)3;
+      size_t b1 = ((size_t)(i >> 1) * M + p1 + 3) & ~(size_t)3;
+      if (b1 > (total & ~(size_t)3)) b1 = total & ~(size_t)3;
+      if (b1 > b0) prefetch_l2(base + b0, (unsigned)((b1 - b0) * 4));
+    }
+  }
   __syncthreads();
   load_half_spectrum(X, perm, a.S, N, M, C, logC, m0);
   __syncthreads();
