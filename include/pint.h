@@ -151,6 +151,28 @@ pint_status pint_wr_sweep(pint_plan plan, const double* Fhat, const double* U_pr
 pint_status pint_solve(pint_plan plan, const double* Fhat, double* U, double tol, int max_sweeps,
                        int* sweeps_out, double* upd_rel_out, void* stream);
 
+/* ---- a solve that allocates no device memory ----
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory when they run: code under a device-memory budget fixed up front,
+ * plugins whose host runtime owns every allocation, or real-time loops where a cudaMalloc
+ * (which may synchronise the device) is not acceptable. Such callers cannot build a plan.
+ *
+ * Q = P_kappa^{-1} R for the 1D heat problem (alpha = 1, FP64): Algorithm 1 steps 1-3 with the
+ * same kernels as a PINT_FP64 plan, i.e. the result of pint_wr_sweep with U_prev = 0 and
+ * Fhat = R. R, Q: [N][mx] FP64 device arrays owned by the caller (Q may not alias R).
+ * Limits: N a power of two in [8, 1024] with N > k; mx + 1 a power of two, 3 <= mx <= 1023;
+ * (N/2 + 1) * mx <= 262144. Larger sizes return PINT_EINVAL (message in pint_last_error).
+ * Memory: the intermediate spectrum and the constant tables live in one static device array of
+ * about 4.2 MiB that is part of the library: every GPU that loads the library holds it until
+ * the process exits. No cudaMalloc, cudaFree or other allocating routine is called.
+ * Set-up: the first call made on a device looks up that array's device address for the
+ * current device (a synchronous driver query), so make that first call before any stream
+ * capture. The array is shared by every call and keeps the last call's contents (the parts
+ * that must start at zero are cleared by each call): calls whose GPU work overlaps -- on
+ * different streams or from different host threads -- race on it; serialise them. */
+pint_status pint_kappa_solve_noalloc(int k, double kappa, double tau, int N, int mx, const double* R,
+                                     double* Q, void* stream);
+
 /* ---- host-only queries (no GPU needed) ---- */
 
 /* omega_0..omega_{n-1}: BDF-k weights (alpha = 1, zero past k; eq. (2.2)) or the CQ weights,

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstddef>
+#include <string>
 
 namespace pint {
 
@@ -124,6 +125,10 @@ cudaError_t launch_d2f(const double* x, float* y, size_t n, cudaStream_t st);
 cudaError_t launch_f2d(const float* x, double* y, size_t n, cudaStream_t st);
 cudaError_t launch_bcast_d(const double* v, double* U, int N, int M, cudaStream_t st);
 cudaError_t launch_bcast_d2ff(const double* v, float* hi, float* lo, int N, int M, cudaStream_t st);
+
+// Thread-local message returned by pint_last_error().
+void set_last_error(const char* msg);
+inline void set_last_error(const std::string& msg) { set_last_error(msg.c_str()); }
 
 // Kernel timing hooks (per-kernel CUDA events when profiling is on).
 void prof_begin(const char* name, cudaStream_t st);

@@ -28,6 +28,8 @@ static pint_status fail(pint_status s, const std::string& msg) {
   g_err = msg;
   return s;
 }
+void set_last_error(const char* msg) { g_err = msg; }
+
 static pint_status cuda_fail(cudaError_t e, const char* where) {
   g_err = std::string(where) + ": " + cudaGetErrorString(e);
   return PINT_ECUDA;

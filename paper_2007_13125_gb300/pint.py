@@ -80,6 +80,7 @@ def lib():
         "pint_status_string": (ctypes.c_char_p, [_I]),
         "pint_version": (ctypes.c_char_p, []),
         "pint_set_profiling": (_I, [_I]),
+        "pint_kappa_solve_noalloc": (_I, [_I, _D, _D, _I, _I, _P, _P, _P]),
         "pint_kernel_stats": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I),
                                    ctypes.POINTER(_D), _I]),
     }
@@ -168,6 +169,12 @@ def circulant_eigenvalues(k: int, alpha: float, kappa: float, N: int, eig: int =
                                            re_.ctypes.data_as(ctypes.POINTER(_D)),
                                            im_.ctypes.data_as(ctypes.POINTER(_D))))
     return re_ + 1j * im_
+
+
+def kappa_solve_noalloc(k, kappa, tau, N, mx, R, Q, stream=None):
+    """Q = P_kappa^{-1} R (1D heat, FP64) with no device allocation (see include/pint.h)."""
+    check(lib().pint_kappa_solve_noalloc(int(k), float(kappa), float(tau), int(N), int(mx), _ptr(R), _ptr(Q),
+                                         _stream(stream)))
 
 
 def set_profiling(on: bool):
