@@ -171,6 +171,25 @@ def run_reference(args):
     return 0
 
 
+def run_once(precision: str) -> int:
+    import torch
+    from paper_2007_13125_gb300 import Plan
+    p = problem_for_rank(0)
+    dev = torch.device("cuda", 0)
+    v = torch.tensor(p.v, device=dev)
+    f = torch.tensor(p.f(), device=dev)
+    fd = torch.tensor(p.fderiv(), device=dev)
+    with Plan.for_problem(p, precision) as plan:
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device=dev)
+        U = torch.empty_like(F)
+        plan.form_rhs(v, f, fd, F)
+        plan.initial_guess(v, U)
+        st, sweeps, upd = plan.solve(F, U, tol=TOL, max_sweeps=30)
+        torch.cuda.synchronize()
+    print(json.dumps({"once": precision, "workload": p.name, "sweeps": sweeps, "final_update": upd}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -178,9 +197,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--once", choices=["mixed", "fp64", "fp32"], default=None,
+                    help="run one untimed solve of the workload (for profiler captures) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.once:
+        return run_once(args.once)
 
     import torch
     rank, world, local = dist_env()

@@ -146,10 +146,58 @@ pint_status pint_wr_sweep(pint_plan plan, const double* Fhat, const double* U_pr
  * estimate is <= tol (or upd_1 <= tol/100), or, if q >= 1, when upd_m <= tol. Returns
  * PINT_ENOTCONV after max_sweeps otherwise (U then holds the last iterate).
  * Fhat [N][M] device input; U [N][M] device, in: initial guess, out: solution.
- * sweeps_out, upd_rel_out: optional host pointers. Synchronises `stream` once per sweep to read
- * two norms (16 bytes). */
+ * sweeps_out, upd_rel_out: optional host pointers. The whole solve is one CUDA-graph launch (a
+ * while-node repeats the sweep until a device-side check of the fused norms stops it); the graph
+ * is built on first use and reused while (Fhat, U, tol, max_sweeps) stay the same. The call waits
+ * for `stream` once. With per-kernel profiling on, sweeps are launched one by one instead. */
 pint_status pint_solve(pint_plan plan, const double* Fhat, double* U, double tol, int max_sweeps,
                        int* sweeps_out, double* upd_rel_out, void* stream);
+
+/* Solve n independent problems with one graph launch. Each plan's whole solve (prologue, a
+ * while-loop of sweeps with the device-side convergence check, epilogue) becomes an independent
+ * branch of one CUDA graph, so problems of different sizes, orders and alpha run concurrently on
+ * the GPU and each stops on its own. plans: n distinct plans; Fhat[i], U[i]: device arrays of
+ * plans[i] as in pint_solve; sweeps_out, upd_out: optional host arrays of length n. Waits for the
+ * stream once. Returns PINT_ENOTCONV if any problem reached max_sweeps above tol. */
+pint_status pint_batch_solve(pint_plan* plans, int n, const double* const* Fhat, double* const* U,
+                             double tol, int max_sweeps, int* sweeps_out, double* upd_out, void* stream);
+
+/* ---- serving: continuous batching of independent solves ----
+ * A server owns a device-memory budget (reserved once at creation and sub-allocated, so admission
+ * never calls cudaMalloc), up to max_active concurrent solves (one stream each) and a worker
+ * thread. Requests are admitted in arrival order while a slot is free and the budget holds their
+ * plan, F_hat, U, f and v; each admitted request runs as one graph launch (F_hat, U_0 = v, the
+ * whole WR solve with its device-side convergence loop), so requests admitted while others run
+ * overlap on the GPU. The iterate stays on the device until pint_poll copies it out and releases
+ * the request's memory. The server is thread-safe; plans are internal to it. */
+typedef struct pint_server_s* pint_server;
+typedef struct {
+  pint_plan_desc desc;  /* problem and precision (precision PINT_MIXED or PINT_FP64 recommended) */
+  double tol;           /* stopping tolerance as in pint_solve */
+  int max_sweeps;
+} pint_request;
+typedef struct {
+  int status;           /* PINT_OK, PINT_ENOTCONV, PINT_EBUDGET (larger than the budget), ... */
+  int sweeps;
+  double upd_rel;       /* last relative update */
+  double t_submit, t_start, t_done;  /* seconds since server creation: submitted, admitted, solved */
+} pint_solve_info;
+
+/* hbm_budget_bytes >= 1 MiB is reserved now (PINT_ENOMEM if it cannot be); max_active in 1..256. */
+pint_status pint_server_create(size_t hbm_budget_bytes, int max_active, pint_server* out);
+/* Finishes admitted work, frees everything (unpolled results are dropped). NULL is accepted. */
+pint_status pint_server_destroy(pint_server s);
+/* Host arrays v [M], f [N][M], fderiv [k-1][M] (NULL when k = 1) are copied before returning. */
+pint_status pint_submit(pint_server s, const pint_request* req, const double* v, const double* f,
+                        const double* fderiv, uint64_t* ticket);
+/* Wait up to timeout_us for the result: PINT_EAGAIN (timeout_us == 0) or PINT_ETIMEOUT if not
+ * done yet (the request stays live); otherwise the request's status, with U copied into the host
+ * array U_out [N][M] (may be NULL) and the request retired. PINT_ENOTFOUND for an unknown ticket.
+ * info (optional) receives the status, sweeps and timestamps. */
+pint_status pint_poll(pint_server s, uint64_t ticket, int timeout_us, double* U_out, pint_solve_info* info);
+/* out[8]: completed, active, queued, device bytes in use, DOF solved, sweeps, seconds since
+ * creation, peak device bytes in use. */
+pint_status pint_server_stats(pint_server s, double* out);
 
 /* ---- a solve that allocates no device memory ----
  * The paper has no counterpart to this entry point; it exists for callers that cannot

@@ -495,8 +495,47 @@ __global__ void k_f2d(const float* x, double* y, size_t n) {
 }
 
 // ---------------------------------------------------------------------------
+// convergence control inside a CUDA graph: a while-node repeats the sweep until k_converge
+// clears its condition (same decision as the host loop)
+// ---------------------------------------------------------------------------
+__global__ void k_ctl_init(SolveCtl* c, double tol, double q_floor, int max_sweeps) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    c->tol = tol;
+    c->q_floor = q_floor;
+    c->prev = -1.0;
+    c->upd = 0.0;
+    c->max_sweeps = max_sweeps;
+    c->m = 0;
+    c->done = 0;
+  }
+}
+
+__global__ void k_converge(const double* norms, SolveCtl* c, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double c2 = norms[0], u2 = norms[1];
+  const double upd = u2 > 0.0 ? sqrt(c2 / u2) : sqrt(c2);
+  const int m = c->m + 1;
+  const bool done = stop_decision(m, upd, c->prev, c->tol, c->q_floor);
+  c->m = m;
+  c->prev = upd;
+  c->upd = upd;
+  c->done = done ? 1 : 0;
+  cudaGraphSetConditional(h, (!done && m < c->max_sweeps) ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t launch_ctl_init(SolveCtl* ctl, double tol, double q_floor, int max_sweeps, cudaStream_t st) {
+  k_ctl_init<<<1, 32, 0, st>>>(ctl, tol, q_floor, max_sweeps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_converge(const double* norms, SolveCtl* ctl, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_converge<<<1, 32, 0, st>>>(norms, ctl, h);
+  return cudaGetLastError();
+}
+
 static int grid_for(size_t n) {
   size_t b = (n + kThreads - 1) / kThreads;
   if (b > 152 * 16) b = 152 * 16;

@@ -126,6 +126,26 @@ cudaError_t launch_f2d(const float* x, double* y, size_t n, cudaStream_t st);
 cudaError_t launch_bcast_d(const double* v, double* U, int N, int M, cudaStream_t st);
 cudaError_t launch_bcast_d2ff(const double* v, float* hi, float* lo, int N, int M, cudaStream_t st);
 
+// ---- convergence control (shared by the host loop and the graph's device-side check) ----
+struct SolveCtl {
+  double tol, q_floor, prev, upd;
+  int max_sweeps, m, done, pad;
+};
+
+// Stop after sweep m? upd = ||U_m - U_{m-1}|| / ||U_m||, prev = upd_{m-1}. For m >= 2 the
+// contraction is estimated as q = max(upd / prev, q_floor) (q_floor: rounding floor of the inner
+// solves) and the error as upd q / (1 - q).
+__host__ __device__ inline bool stop_decision(int m, double upd, double prev, double tol, double q_floor) {
+  if (m == 1) return upd <= 0.01 * tol;
+  const double q = prev > 0.0 ? upd / prev : 0.0;
+  const double qh = q > q_floor ? q : q_floor;
+  if (qh < 1.0) return upd * qh / (1.0 - qh) <= tol;
+  return upd <= tol;
+}
+
+cudaError_t launch_ctl_init(SolveCtl* ctl, double tol, double q_floor, int max_sweeps, cudaStream_t st);
+cudaError_t launch_converge(const double* norms, SolveCtl* ctl, cudaGraphConditionalHandle h, cudaStream_t st);
+
 // Thread-local message returned by pint_last_error().
 void set_last_error(const char* msg);
 inline void set_last_error(const std::string& msg) { set_last_error(msg.c_str()); }

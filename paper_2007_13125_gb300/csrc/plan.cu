@@ -14,6 +14,7 @@
 #include "../../include/pint.h"
 #include "fft.cuh"
 #include "pint_internal.h"
+#include "plan_internal.h"
 
 using cd = std::complex<double>;
 
@@ -198,54 +199,9 @@ static void eigenvalues(int k, double alpha, double kappa, int N, pint_eig_varia
   g = c;
 }
 
-// ---------------------------------------------------------------------------
-// plan
-// ---------------------------------------------------------------------------
-template <typename T> struct DevTables {
-  void* tw_time = nullptr;   // V[N]
-  T* s = nullptr;            // [N]
-  T* inv_s = nullptr;        // [N]
-  void* sigma = nullptr;     // V[N/2+1]
-  void* tw_x = nullptr;      // V[2(mx+1)]
-  void* tw_y = nullptr;      // V[2(my+1)]
-  T* lam_x = nullptr;        // [mx]
-  T* lam_y = nullptr;        // [my]
-};
-
 }  // namespace pint
 
 using namespace pint;
-
-struct pint_plan_s {
-  int k; double alpha, kappa, tau; int N;
-  int dim, mx, my, M;
-  pint_precision prec;
-  pint_eig_variant eig;
-  bool cq;
-  std::vector<double> omega;
-  double a[5];
-  double b[4][5];
-  std::vector<cd> g;
-  double gx, gy;
-  // device
-  std::vector<void*> allocs;
-  size_t bytes = 0;
-  DevTables<float> tf;
-  DevTables<double> td;
-  double* beta = nullptr;           // [N]
-  double2* tw_2n = nullptr;         // [2N]
-  double2* what_lo = nullptr;       // [2N] permuted, * tau^-alpha / 2N
-  double2* what_up = nullptr;       // [2N] permuted, * kappa tau^-alpha / 2N
-  float *Uhi = nullptr, *Ulo = nullptr, *Fhi = nullptr;  // MIXED: U double-float; FP32: U, F_hat
-  void* S = nullptr;                // spectrum
-  double* z = nullptr;              // CQ Toeplitz output [N][M]
-  double* norms = nullptr;          // device [2]
-  double* h_norms = nullptr;        // pinned host [2]
-  // tiles
-  int Ct, Ctd, Cz, Cx, Cy, Ctri;    // columns per CTA: time (float), time (T), toeplitz, x, y, tri
-  int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal
-  double q_floor;                   // predicted floor of the per-sweep contraction (inner precision)
-};
 
 #define PINT_CUDA_B(call)                                      \
   do {                                                         \
@@ -259,8 +215,13 @@ bool pow2(long x) { return x > 0 && (x & (x - 1)) == 0; }
 
 template <typename X> pint_status dalloc(pint_plan p, X** ptr, size_t count) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, count * sizeof(X));
-  if (e != cudaSuccess) return fail(PINT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  if (p->alloc) {
+    q = p->alloc->alloc(count * sizeof(X));
+    if (!q) return fail(PINT_ENOMEM, "device memory budget exhausted");
+  } else {
+    cudaError_t e = cudaMalloc(&q, count * sizeof(X));
+    if (e != cudaSuccess) return fail(PINT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
   p->allocs.push_back(q);
   p->bytes += count * sizeof(X);
   *ptr = reinterpret_cast<X*>(q);
@@ -358,8 +319,19 @@ pint_status validate(int k, double alpha, double kappa, double tau, int N, const
 
 void destroy_plan(pint_plan p) {
   if (!p) return;
-  for (void* q : p->allocs) cudaFree(q);
-  if (p->h_norms) cudaFreeHost(p->h_norms);
+  if (p->sg.exec) cudaGraphExecDestroy(p->sg.exec);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  for (void* q : p->allocs) {
+    if (p->alloc) p->alloc->release(q);
+    else cudaFree(q);
+  }
+  if (p->alloc) {
+    if (p->h_norms) p->alloc->host_release(p->h_norms);
+    if (p->h_ctl) p->alloc->host_release(p->h_ctl);
+  } else {
+    if (p->h_norms) cudaFreeHost(p->h_norms);
+    if (p->h_ctl) cudaFreeHost(p->h_ctl);
+  }
   delete p;
 }
 
@@ -370,6 +342,10 @@ pint_status autotune_ysolve(pint_plan p);
 }
 
 extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan* out) {
+  return plan_create_internal(d, nullptr, out);
+}
+
+pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A, pint_plan* out) {
   if (!d || !out) return fail(PINT_EINVAL, "NULL argument");
   pint_status s = validate(d->k, d->alpha, d->kappa, d->tau, d->N, &d->grid);
   if (s != PINT_OK) return s;
@@ -379,6 +355,7 @@ extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan*
     return fail(PINT_EINVAL, "CLOSED_FORM eigenvalues with alpha < 1 need the residual form (PINT_MIXED)");
   if (d->ysolve < 0 || d->ysolve > 3) return fail(PINT_EINVAL, "bad ysolve variant");
   pint_plan p = new pint_plan_s();
+  p->alloc = A;
   p->k = d->k; p->alpha = d->alpha; p->kappa = d->kappa; p->tau = d->tau; p->N = d->N;
   p->dim = d->grid.dim; p->mx = d->grid.mx; p->my = d->grid.dim == 2 ? d->grid.my : 1;
   p->M = p->mx * p->my;
@@ -447,7 +424,16 @@ extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan*
     p->S = S;
   }
   if ((s = dalloc(p, &p->norms, 2)) != PINT_OK) return bail(s);
-  if (cudaMallocHost(&p->h_norms, 2 * sizeof(double)) != cudaSuccess) return bail(fail(PINT_ENOMEM, "cudaMallocHost"));
+  if ((s = dalloc(p, &p->ctl, 1)) != PINT_OK) return bail(s);
+  if (p->alloc) {
+    p->h_norms = (double*)p->alloc->host_alloc(2 * sizeof(double));
+    p->h_ctl = (SolveCtl*)p->alloc->host_alloc(sizeof(SolveCtl));
+    if (!p->h_norms || !p->h_ctl) return bail(fail(PINT_ENOMEM, "pinned host buffer"));
+  } else {
+    if (cudaMallocHost(&p->h_norms, 2 * sizeof(double)) != cudaSuccess) return bail(fail(PINT_ENOMEM, "cudaMallocHost"));
+    if (cudaMallocHost(&p->h_ctl, sizeof(SolveCtl)) != cudaSuccess) return bail(fail(PINT_ENOMEM, "cudaMallocHost"));
+  }
+  PINT_CUDA_B(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
 
   // tile widths (columns per CTA), shared-memory budget ~96 KB
   const size_t budget = 96 * 1024;
@@ -728,6 +714,149 @@ pint_status sweep_user(pint_plan p, const double* Fhat, const double* Uin, doubl
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Whole solves as CUDA graphs: prologue (control init, conversions) -> while-node whose body is
+// one sweep plus the device-side convergence check -> epilogue (conversion back, copy of the
+// convergence state to pinned host memory). A solve is one graph launch; the host waits once.
+// ---------------------------------------------------------------------------
+namespace {
+
+pint_status capture_begin(pint_plan p, cudaGraph_t g) {
+  PINT_CUDA(cudaStreamBeginCaptureToGraph(p->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  return PINT_OK;
+}
+pint_status capture_end(pint_plan p, cudaGraph_t* g, pint_status body) {
+  cudaGraph_t out = *g;
+  cudaError_t e = cudaStreamEndCapture(p->cap, &out);
+  if (body != PINT_OK) return body;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  *g = out;
+  return PINT_OK;
+}
+
+pint_status sweep_body(pint_plan p, const double* F, double* U, cudaStream_t st) {
+  if (p->prec == PINT_MIXED) return sweep_mixed(p, F, st);
+  if (p->prec == PINT_FP64) return sweep_direct<double>(p, p->td, F, U, U, st);
+  return sweep_direct<float>(p, p->tf, p->Fhi, p->Uhi, p->Uhi, st);
+}
+
+}  // namespace
+
+pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, double* U, double tol,
+                                  int max_sweeps) {
+  const size_t NM = (size_t)p->N * p->M;
+  const bool prof = g_prof_on;
+  g_prof_on = false;  // per-kernel events are host-side records: keep them out of graphs
+  pint_status s = PINT_OK;
+  cudaGraph_t pro = nullptr, epi = nullptr, body = nullptr;
+  cudaGraphNode_t npro, nloop, nepi;
+  do {
+    // prologue
+    if (cudaGraphCreate(&pro, 0) != cudaSuccess) { s = fail(PINT_ECUDA, "cudaGraphCreate"); break; }
+    if ((s = capture_begin(p, pro)) != PINT_OK) break;
+    {
+      pint_status b = PINT_OK;
+      cudaError_t e = launch_ctl_init(p->ctl, tol, p->q_floor, max_sweeps, p->cap);
+      if (e == cudaSuccess && p->prec == PINT_MIXED) e = launch_d2ff(U, p->Uhi, p->Ulo, NM, p->cap);
+      if (e == cudaSuccess && p->prec == PINT_FP32) {
+        e = launch_d2f(F, p->Fhi, NM, p->cap);
+        if (e == cudaSuccess) e = launch_d2f(U, p->Uhi, NM, p->cap);
+      }
+      if (e != cudaSuccess) b = cuda_fail(e, "graph prologue");
+      if ((s = capture_end(p, &pro, b)) != PINT_OK) break;
+    }
+    if (cudaGraphAddChildGraphNode(&npro, g, nullptr, 0, pro) != cudaSuccess) {
+      s = fail(PINT_ECUDA, "cudaGraphAddChildGraphNode"); break;
+    }
+    // while-node with the sweep body
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { s = cuda_fail(e, "cudaGraphConditionalHandleCreate"); break; }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&nloop, g, &npro, nullptr, 1, &cp);
+    if (e != cudaSuccess) { s = cuda_fail(e, "cudaGraphAddNode(conditional)"); break; }
+    body = cp.conditional.phGraph_out[0];
+    if ((s = capture_begin(p, body)) != PINT_OK) break;
+    {
+      pint_status b = sweep_body(p, F, U, p->cap);
+      if (b == PINT_OK) {
+        cudaError_t e2 = launch_converge(p->norms, p->ctl, h, p->cap);
+        if (e2 != cudaSuccess) b = cuda_fail(e2, "convergence kernel");
+      }
+      if ((s = capture_end(p, &body, b)) != PINT_OK) break;
+    }
+    // epilogue
+    if (cudaGraphCreate(&epi, 0) != cudaSuccess) { s = fail(PINT_ECUDA, "cudaGraphCreate"); break; }
+    if ((s = capture_begin(p, epi)) != PINT_OK) break;
+    {
+      cudaError_t e3 = cudaSuccess;
+      if (p->prec == PINT_MIXED) e3 = launch_ff2d(p->Uhi, p->Ulo, U, NM, p->cap);
+      else if (p->prec == PINT_FP32) e3 = launch_f2d(p->Uhi, U, NM, p->cap);
+      if (e3 == cudaSuccess)
+        e3 = cudaMemcpyAsync(p->h_ctl, p->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, p->cap);
+      if ((s = capture_end(p, &epi, e3 == cudaSuccess ? PINT_OK : cuda_fail(e3, "graph epilogue"))) != PINT_OK)
+        break;
+    }
+    if (cudaGraphAddChildGraphNode(&nepi, g, &nloop, 1, epi) != cudaSuccess) {
+      s = fail(PINT_ECUDA, "cudaGraphAddChildGraphNode"); break;
+    }
+  } while (0);
+  if (pro) cudaGraphDestroy(pro);
+  if (epi) cudaGraphDestroy(epi);
+  g_prof_on = prof;
+  return s;
+}
+
+pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double tol, int max_sweeps,
+                                cudaStream_t st) {
+  SolveGraph& sg = p->sg;
+  if (!sg.exec || sg.F != F || sg.U != U || sg.tol != tol || sg.max_sweeps != max_sweeps) {
+    if (sg.exec) {
+      cudaGraphExecDestroy(sg.exec);
+      sg.exec = nullptr;
+    }
+    cudaGraph_t g;
+    PINT_CUDA(cudaGraphCreate(&g, 0));
+    pint_status s = add_solve_nodes(p, g, F, U, tol, max_sweeps);
+    if (s == PINT_OK) {
+      cudaError_t e = cudaGraphInstantiate(&sg.exec, g, 0);
+      if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphInstantiate");
+    }
+    cudaGraphDestroy(g);
+    if (s != PINT_OK) {
+      sg.exec = nullptr;
+      return s;
+    }
+    sg.F = F; sg.U = U; sg.tol = tol; sg.max_sweeps = max_sweeps;
+  }
+  PINT_CUDA(cudaGraphLaunch(sg.exec, st));
+  return PINT_OK;
+}
+
+void pint::solve_result(pint_plan p, int* sweeps, double* upd, bool* converged) {
+  if (sweeps) *sweeps = p->h_ctl->m;
+  if (upd) *upd = p->h_ctl->upd;
+  if (converged) *converged = p->h_ctl->done != 0;
+}
+
+void pint::plan_release(pint_plan p) { destroy_plan(p); }
+
+size_t pint::plan_bytes_estimate(const pint_plan_desc* d) {
+  const size_t N = d->N, M = (size_t)d->grid.mx * (d->grid.dim == 2 ? d->grid.my : 1);
+  const size_t NM = N * M, JM = (N / 2 + 1) * M;
+  size_t b = 0;
+  if (d->precision == PINT_MIXED) b += 8 * NM + 8 * JM;
+  else if (d->precision == PINT_FP32) b += 8 * NM + 8 * JM;
+  else b += 16 * JM;
+  if (d->alpha != 1.0) b += 8 * NM;
+  b += 64 * (N + d->grid.mx + d->grid.my) + 65536;  // tables, alignment slack
+  return b;
+}
+
 extern "C" pint_status pint_wr_sweep(pint_plan p, const double* Fhat, const double* U_prev, double* U_next,
                                      double* upd_rel, void* stream) {
   if (!p || !Fhat || !U_prev || !U_next) return fail(PINT_EINVAL, "NULL argument");
@@ -743,6 +872,20 @@ extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, do
   if (!p || !Fhat || !U) return fail(PINT_EINVAL, "NULL argument");
   if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
   cudaStream_t st = (cudaStream_t)stream;
+  if (!g_prof_on) {
+    // one graph launch runs every sweep; the host waits once for the result
+    pint_status gs = solve_enqueue(p, Fhat, U, tol, max_sweeps, st);
+    if (gs != PINT_OK) return gs;
+    PINT_CUDA(cudaStreamSynchronize(st));
+    int m = 0;
+    double upd = 0.0;
+    bool done = false;
+    solve_result(p, &m, &upd, &done);
+    if (sweeps_out) *sweeps_out = m;
+    if (upd_rel_out) *upd_rel_out = upd;
+    if (!done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
+    return PINT_OK;
+  }
   const size_t NM = (size_t)p->N * p->M;
   cudaError_t e;
   if (p->prec == PINT_MIXED) {
@@ -762,14 +905,7 @@ extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, do
     if (s != PINT_OK) return s;
     ++m;
     if ((s = read_norms(p, st, &upd)) != PINT_OK) return s;
-    if (m == 1) {
-      done = upd <= 0.01 * tol;
-    } else {
-      const double q = prev > 0.0 ? upd / prev : 0.0;
-      const double qh = std::max(q, p->q_floor);
-      if (qh < 1.0) done = upd * qh / (1.0 - qh) <= tol;
-      else done = upd <= tol;
-    }
+    done = stop_decision(m, upd, prev, tol, p->q_floor);
     prev = upd;
   }
   if (p->prec == PINT_MIXED) {
@@ -780,6 +916,46 @@ extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, do
   if (sweeps_out) *sweeps_out = m;
   if (upd_rel_out) *upd_rel_out = upd;
   if (!done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
+  return PINT_OK;
+}
+
+extern "C" pint_status pint_batch_solve(pint_plan* plans, int n, const double* const* Fhat, double* const* U,
+                                        double tol, int max_sweeps, int* sweeps_out, double* upd_out,
+                                        void* stream) {
+  if (n < 1 || !plans || !Fhat || !U) return fail(PINT_EINVAL, "bad batch arguments");
+  if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !Fhat[i] || !U[i]) return fail(PINT_EINVAL, "NULL plan or array in batch");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(PINT_EINVAL, "a plan appears twice in one batch");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaGraph_t g;
+  PINT_CUDA(cudaGraphCreate(&g, 0));
+  pint_status s = PINT_OK;
+  for (int i = 0; i < n && s == PINT_OK; ++i) s = add_solve_nodes(plans[i], g, Fhat[i], U[i], tol, max_sweeps);
+  cudaGraphExec_t ex = nullptr;
+  if (s == PINT_OK) {
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphInstantiate");
+  }
+  cudaGraphDestroy(g);
+  if (s != PINT_OK) return s;
+  cudaError_t e = cudaGraphLaunch(ex, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaGraphExecDestroy(ex);
+  if (e != cudaSuccess) return cuda_fail(e, "batch graph");
+  bool all = true;
+  for (int i = 0; i < n; ++i) {
+    int m = 0;
+    double upd = 0.0;
+    bool done = false;
+    solve_result(plans[i], &m, &upd, &done);
+    if (sweeps_out) sweeps_out[i] = m;
+    if (upd_out) upd_out[i] = upd;
+    all = all && done;
+  }
+  if (!all) return fail(PINT_ENOTCONV, "some problems reached max_sweeps above tol");
   return PINT_OK;
 }
 

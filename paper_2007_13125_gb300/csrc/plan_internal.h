@@ -1,0 +1,102 @@
+// The plan object and the internal entry points shared by the C-ABI translation units
+// (plan.cu: plans, sweeps and solves; server.cu: the serving loop).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <vector>
+
+#include "../../include/pint.h"
+#include "pint_internal.h"
+
+namespace pint {
+
+template <typename T> struct DevTables {
+  void* tw_time = nullptr;   // V[N]
+  T* s = nullptr;            // [N]
+  T* inv_s = nullptr;        // [N]
+  void* sigma = nullptr;     // V[N/2+1]
+  void* tw_x = nullptr;      // V[2(mx+1)]
+  void* tw_y = nullptr;      // V[2(my+1)]
+  T* lam_x = nullptr;        // [mx]
+  T* lam_y = nullptr;        // [my]
+};
+
+// Source of a plan's device memory: cudaMalloc by default, or a sub-allocator (the server's
+// budgeted arena). alloc returns nullptr on failure.
+struct DevAllocator {
+  virtual void* alloc(size_t bytes) = 0;
+  virtual void release(void* p) = 0;
+  // small pinned host buffers (convergence state read back by the host)
+  virtual void* host_alloc(size_t bytes) {
+    void* p = nullptr;
+    return cudaMallocHost(&p, bytes) == cudaSuccess ? p : nullptr;
+  }
+  virtual void host_release(void* p) { cudaFreeHost(p); }
+  virtual ~DevAllocator() {}
+};
+
+// Cached executable graph of one whole solve (prologue, while-loop of sweeps, epilogue).
+struct SolveGraph {
+  cudaGraphExec_t exec = nullptr;
+  const double* F = nullptr;
+  double* U = nullptr;
+  double tol = 0.0;
+  int max_sweeps = 0;
+};
+
+}  // namespace pint
+
+struct pint_plan_s {
+  int k; double alpha, kappa, tau; int N;
+  int dim, mx, my, M;
+  pint_precision prec;
+  pint_eig_variant eig;
+  bool cq;
+  std::vector<double> omega;
+  double a[5];
+  double b[4][5];
+  std::vector<std::complex<double>> g;
+  double gx, gy;
+  // device
+  pint::DevAllocator* alloc = nullptr;   // null: cudaMalloc / cudaFree
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  pint::DevTables<float> tf;
+  pint::DevTables<double> td;
+  double* beta = nullptr;           // [N]
+  double2* tw_2n = nullptr;         // [2N]
+  double2* what_lo = nullptr;       // [2N] permuted, * tau^-alpha / 2N
+  double2* what_up = nullptr;       // [2N] permuted, * kappa tau^-alpha / 2N
+  float *Uhi = nullptr, *Ulo = nullptr, *Fhi = nullptr;  // MIXED: U double-float; FP32: U, F_hat
+  void* S = nullptr;                // spectrum
+  double* z = nullptr;              // CQ Toeplitz output [N][M]
+  double* norms = nullptr;          // device [2]
+  double* h_norms = nullptr;        // pinned host [2]
+  pint::SolveCtl* ctl = nullptr;    // device convergence state
+  pint::SolveCtl* h_ctl = nullptr;  // pinned host copy written by the graph's epilogue
+  cudaStream_t cap = nullptr;       // stream used to capture graphs
+  pint::SolveGraph sg;
+  // tiles
+  int Ct, Ctd, Cz, Cx, Cy, Ctri;    // columns per CTA: time (float), time (T), toeplitz, x, y, tri
+  int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal
+  double q_floor;                   // predicted floor of the per-sweep contraction (inner precision)
+};
+
+namespace pint {
+
+// Plan creation with an explicit device-memory source (null: cudaMalloc).
+pint_status plan_create_internal(const pint_plan_desc* d, DevAllocator* A, pint_plan* out);
+// Free a plan's memory without synchronising the device (its work must have completed).
+void plan_release(pint_plan p);
+// Device bytes a plan for this description will hold (workspaces and tables).
+size_t plan_bytes_estimate(const pint_plan_desc* d);
+// Enqueue one whole solve on `st` as a single graph launch (building or reusing the cached graph);
+// the graph ends with a copy of the convergence state into pinned host memory.
+pint_status solve_enqueue(pint_plan p, const double* F, double* U, double tol, int max_sweeps, cudaStream_t st);
+// Result of the last enqueued solve (valid once its stream work has completed).
+void solve_result(pint_plan p, int* sweeps, double* upd, bool* converged);
+// Add one solve (prologue, while-loop, epilogue) of plan p as independent nodes of graph g.
+pint_status add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, double* U, double tol, int max_sweeps);
+
+}  // namespace pint

@@ -1,0 +1,148 @@
+"""Graph-launched solves, one-launch batches of mixed problems, and the serving loop."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import oracle_solution, rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+MIX = [
+    dict(dim=1, mx=63, N=64, k=2, alpha=1.0, kappa=0.1),
+    dict(dim=2, mx=31, N=32, k=4, alpha=1.0, kappa=0.05),
+    dict(dim=1, mx=127, N=128, k=3, alpha=0.5, kappa=0.1),
+    dict(dim=2, mx=15, N=64, k=6, alpha=1.0, kappa=0.1),
+    dict(dim=1, mx=31, N=256, k=1, alpha=0.3, kappa=0.01),
+    dict(dim=2, mx=63, N=16, k=5, alpha=0.7, kappa=0.1),
+]
+
+
+def _problems(seed0=20):
+    return [workloads.small_problem(seed=seed0 + i, **kw) for i, kw in enumerate(MIX)]
+
+
+def test_graph_solve_matches_host_loop():
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan, pint
+    p = workloads.small_problem(dim=2, mx=31, N=64, k=3, alpha=1.0, kappa=0.05)
+    dev = torch.device("cuda:0")
+    v = torch.tensor(p.v, device=dev); f = torch.tensor(p.f(), device=dev); fd = torch.tensor(p.fderiv(), device=dev)
+    out = []
+    for profiled in (False, True):   # profiling on -> sweeps launched one by one from the host
+        pint.set_profiling(profiled)
+        with Plan.for_problem(p, "mixed") as plan:
+            F = torch.empty((p.N, p.M), dtype=torch.float64, device=dev)
+            U = torch.empty_like(F)
+            plan.form_rhs(v, f, fd, F)
+            plan.initial_guess(v, U)
+            st, sweeps, upd = plan.solve(F, U, tol=1e-10)
+            # a second solve reuses the cached graph
+            plan.initial_guess(v, U)
+            st2, sweeps2, upd2 = plan.solve(F, U, tol=1e-10)
+            out.append((U.cpu().numpy(), sweeps, sweeps2, upd, upd2))
+        pint.kernel_stats(reset=True)
+    pint.set_profiling(False)
+    (Ug, sg, sg2, ug, ug2), (Uh, sh, sh2, uh, uh2) = out
+    assert sg == sh == sg2 == sh2
+    assert np.array_equal(Ug, Uh)
+    assert ug == pytest.approx(ug2, rel=1e-6)
+    assert rel_l2(Ug, oracle_solution(p)) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_batch_solve_mixed_problems(precision):
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan, pint
+    dev = torch.device("cuda:0")
+    probs = _problems()
+    plans, Fs, Us = [], [], []
+    for p in probs:
+        pl = Plan.for_problem(p, precision)
+        v = torch.tensor(p.v, device=dev); f = torch.tensor(p.f(), device=dev); fd = torch.tensor(p.fderiv(), device=dev)
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device=dev)
+        U = torch.empty_like(F)
+        pl.form_rhs(v, f, fd, F)
+        pl.initial_guess(v, U)
+        plans.append(pl); Fs.append(F); Us.append(U)
+    st, sweeps, upd = pint.batch_solve(plans, Fs, Us, tol=1e-10)
+    bar = 1e-8 if precision == "mixed" else 1e-10
+    for p, U, s in zip(probs, Us, sweeps):
+        assert rel_l2(U.cpu().numpy(), oracle_solution(p)) <= bar, (p.name, s)
+    for pl in plans:
+        pl.close()
+
+
+def _host_inputs(p):
+    return p.v, p.f(), p.fderiv()
+
+
+def test_server_solves_a_stream_and_matches_oracle():
+    torch_cuda()
+    from paper_2007_13125_gb300 import pint
+    probs = _problems(40)
+    with pint.Server(2 << 30, max_active=4) as srv:
+        tickets = []
+        for p in probs:
+            tickets.append(srv.submit(p, *_host_inputs(p), tol=1e-9))
+        for p, t in zip(probs, tickets):
+            out = np.empty((p.N, p.M))
+            st, info = srv.poll(t, out, timeout_us=30_000_000)
+            assert st == 0 and info.status == 0, (p.name, st)
+            assert info.t_submit <= info.t_start <= info.t_done
+            assert rel_l2(out, oracle_solution(p)) <= 1e-8, p.name
+        stats = srv.stats()
+        assert stats["completed"] == len(probs)
+        assert stats["peak_hbm"] <= 2 << 30
+        assert stats["hbm_in_use"] == 0
+
+
+def test_server_result_same_alone_and_in_mix():
+    """Invariance: a request's result does not depend on what else is being served."""
+    torch_cuda()
+    from paper_2007_13125_gb300 import pint
+    target = workloads.small_problem(dim=2, mx=63, N=64, k=4, alpha=1.0, kappa=0.05, seed=99)
+    out_alone = np.empty((target.N, target.M))
+    with pint.Server(2 << 30, max_active=4) as srv:
+        t = srv.submit(target, *_host_inputs(target), tol=1e-9)
+        st, info_alone = srv.poll(t, out_alone, timeout_us=30_000_000)
+        assert st == 0
+    out_mix = np.empty_like(out_alone)
+    with pint.Server(2 << 30, max_active=4) as srv:
+        others = [(p, srv.submit(p, *_host_inputs(p), tol=1e-9)) for p in _problems(60)[:3]]
+        t = srv.submit(target, *_host_inputs(target), tol=1e-9)
+        others += [(p, srv.submit(p, *_host_inputs(p), tol=1e-9)) for p in _problems(70)[3:]]
+        st, info_mix = srv.poll(t, out_mix, timeout_us=30_000_000)
+        assert st == 0
+        for p, tk in others:
+            o = np.empty((p.N, p.M))
+            assert srv.poll(tk, o, timeout_us=30_000_000)[0] == 0
+    # per-problem arithmetic is independent of the batch: identical sweeps, identical result
+    assert info_alone.sweeps == info_mix.sweeps
+    assert rel_l2(out_mix, out_alone) <= 1e-12
+    assert rel_l2(out_mix, oracle_solution(target)) <= 1e-8
+
+
+def test_server_budget_admission_and_errors():
+    torch_cuda()
+    from paper_2007_13125_gb300 import pint
+    big = workloads.small_problem(dim=2, mx=255, N=128, k=2, alpha=1.0, kappa=0.1, seed=5)   # ~8.3e6 DOF
+    small = workloads.small_problem(dim=1, mx=63, N=64, k=2, alpha=1.0, kappa=0.1, seed=6)
+    budget = 512 << 20            # holds one big request at a time (~0.35 GB each)
+    with pint.Server(budget, max_active=8) as srv:
+        tk = [srv.submit(big, *_host_inputs(big), tol=1e-8) for _ in range(3)]
+        ts = srv.submit(small, *_host_inputs(small), tol=1e-8)
+        huge = workloads.small_problem(dim=2, mx=511, N=256, k=2, alpha=1.0, kappa=0.1, seed=7)
+        th = srv.submit(huge, huge.v, np.zeros((huge.N, huge.M)), np.zeros((1, huge.M)), tol=1e-8)
+        st, info = srv.poll(th, None, timeout_us=30_000_000)
+        assert st == pint.PINT_EBUDGET
+        ref = oracle_solution(big)
+        for t in tk:
+            out = np.empty((big.N, big.M))
+            st, info = srv.poll(t, out, timeout_us=30_000_000)
+            assert st == 0 and rel_l2(out, ref) <= 1e-8
+        assert srv.poll(ts, np.empty((small.N, small.M)), timeout_us=30_000_000)[0] == 0
+        assert srv.stats()["peak_hbm"] <= budget
+        st, _ = srv.poll(123456, None, 0)
+        assert st == pint.PINT_ENOTFOUND
