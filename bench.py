@@ -57,6 +57,25 @@ def algo_bytes(name: str, N: int, M: int) -> float:
     return float(table.get(name, 0.0))
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# of the workload (profiles/k_resid_fwd_heat2d_255x255_N256_bdf4.md), valid while the kernel's
+# source is unchanged (sha1 of its translation unit)
+NCU_TRAFFIC = {"resid_fwd_ff": (312.7e6, "kernels_time.cu", "94001d2625844ad5381ff549495e60dbdcccae6d")}
+
+
+def traffic_for(name: str):
+    import hashlib
+    ent = NCU_TRAFFIC.get(name)
+    if not ent:
+        return None
+    path = os.path.join(ROOT, "paper_2007_13125_gb300", "csrc", ent[1])
+    try:
+        h = hashlib.sha1(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return ent[0] if h == ent[2] else None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -173,7 +192,8 @@ def run_reference(args):
 
 def run_once(precision: str) -> int:
     import torch
-    from paper_2007_13125_gb300 import Plan
+    from paper_2007_13125_gb300 import Plan, pint
+    pint.set_profiling(True)   # per-sweep launches
     p = problem_for_rank(0)
     dev = torch.device("cuda", 0)
     v = torch.tensor(p.v, device=dev)
@@ -198,7 +218,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--once", choices=["mixed", "fp64", "fp32"], default=None,
-                    help="run one untimed solve of the workload (for profiler captures) and exit")
+                    help="run one untimed solve of the workload with per-sweep launches (for profiler "
+                         "captures: kernels inside graphs with conditional nodes cannot be profiled) and exit")
+    ap.add_argument("--per-sweep-launches", action="store_true",
+                    help="launch sweeps one by one from the host instead of one graph per solve")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -272,19 +295,28 @@ def main():
         lats = [a.elapsed_time(b) for a, b in lat]
         return ms / steps, lats
 
-    # ---- main timed region: MIXED path, per-kernel events on, clocks sampled ----
+    # ---- main timed region: MIXED path (one graph launch per solve), clocks sampled ----
+    if args.per_sweep_launches:
+        pint.set_profiling(True)
     for _ in range(args.warmup):
         step("mixed")
     barrier()
-    pint.set_profiling(True)
-    pint.kernel_stats(reset=True)
     clk = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     clk.start()
     ms_mixed, lat_mixed = timed("mixed", args.steps, 0, per_step=True)
     clocks = clk.stop()
+    # our kernels per solve: form_rhs, initial guess, conversion in/out, sweeps x (sweep kernels +
+    # the device-side convergence check), control init
+    sweeps_main = last["mixed"][0]
+    per_sweep = 5 if p.dim == 2 else 3
+    launches = args.steps * (2 + 2 + 1 + sweeps_main * (per_sweep + (0 if args.per_sweep_launches else 1)))
+
+    # ---- per-kernel CUDA-event times: the same kernels launched sweep by sweep ----
+    pint.set_profiling(True)
+    pint.kernel_stats(reset=True)
+    timed("mixed", max(3, args.steps // 2), 1)
     kstats = pint.kernel_stats(reset=True)
     pint.set_profiling(False)
-    launches = sum(n for n, _ in kstats.values())
 
     # ---- FP64 diagonalised path, same workload ----
     ms_fp64, lat_fp64 = timed("fp64", max(2, args.steps // 2), 1, per_step=True)
@@ -339,7 +371,7 @@ def main():
         avg_s = tot / n * 1e-3
         ach = algo_bytes(name, N, M) / avg_s / 1e9
         roofline = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": hbm_peak,
-                    "unit": "GB/s", "frac": round(ach / hbm_peak, 3), "traffic": None,
+                    "unit": "GB/s", "frac": round(ach / hbm_peak, 3), "traffic": traffic_for(name),
                     "peak_source": peak_src + " hbm_gbs (STREAM-style copy)",
                     "algo_bytes_per_launch": algo_bytes(name, N, M)}
 
@@ -372,6 +404,7 @@ def main():
                           "latency_ms_p99": float(np.percentile(lat_fp64, 99))},
             "mixed_over_fp64": ms_fp64 / ms_mixed,
             "l2_policy": "inputs larger than L2 (U, F_hat, f: 133 MB each in FP64)",
+            "launch_mode": "per-sweep launches" if args.per_sweep_launches else "one CUDA graph per solve (device-side convergence loop)",
             "parallelism": f"replicas x{world}",
             "kernels": per_kernel,
         },
