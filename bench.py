@@ -53,6 +53,7 @@ def algo_bytes(name: str, N: int, M: int) -> float:
         "direct_inv_f64": 16 * JM + 16 * NM,
         "dst_f64": 32 * JM,
         "axis_solve_f64": 32 * JM,
+        "toeplitz_f64": 16 * NM,                # read U, write the history product
     }
     return float(table.get(name, 0.0))
 
@@ -141,9 +142,14 @@ def dist_env():
     return rank, world, local
 
 
+WORKLOADS = {"heat2d": workloads.c2_heat2d, "heat1d": workloads.c1_heat1d,
+             "subdiff1d": workloads.c3_subdiff1d}
+WORKLOAD = "heat2d"
+
+
 def problem_for_rank(rank: int):
     # weak scaling: every rank solves its own instance (replicas; no exchange step)
-    return workloads.c2_heat2d()
+    return WORKLOADS[WORKLOAD]()
 
 
 def oracle_sample(p, budget_s: float = 15.0):
@@ -190,6 +196,109 @@ def run_reference(args):
     return 0
 
 
+def _device_inputs(p, dev):
+    import torch
+    v = torch.tensor(p.v, device=dev)
+    ph = torch.tensor(p.f_space, device=dev)
+    f = torch.outer(torch.tensor(p.f_time, device=dev), ph).contiguous()
+    fd = (torch.outer(torch.tensor(p.f_derivs0, device=dev), ph).contiguous() if p.k >= 2
+          else torch.zeros((0, p.M), dtype=torch.float64, device=dev))
+    return v, f, fd
+
+
+def run_mix(args) -> int:
+    """64 mixed problems (1D/2D, per-axis 127/255/511, N 64..2048, k 1..6, alpha, kappa), one graph
+    launch per step for all of them (pint_batch_solve)."""
+    import torch
+    from paper_2007_13125_gb300 import Plan, pint
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", local)
+    probs = workloads.c4_batch(64, seed=2)
+    plans, Fs, Us, vs = [], [], [], []
+    for p in probs:
+        pl = Plan.for_problem(p, "mixed")
+        v, f, fd = _device_inputs(p, dev)
+        F = torch.empty_like(f)
+        pl.form_rhs(v, f, fd, F)
+        torch.cuda.synchronize()
+        del f, fd
+        plans.append(pl); Fs.append(F); Us.append(torch.empty_like(F)); vs.append(v)
+    dof = sum(p.dof for p in probs)
+
+    def step():
+        for pl, v, U in zip(plans, vs, Us):
+            pl.initial_guess(v, U)
+        return pint.batch_solve(plans, Fs, Us, tol=TOL, max_sweeps=30)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        st, sweeps, upd = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    kinds = {"heat": sum(1 for p in probs if p.alpha == 1.0), "subdiffusion": sum(1 for p in probs if p.alpha != 1.0)}
+    line = {"metric": METRIC, "value": dof / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
+            "config": {"workload": "mix64_seed2", "problems": len(probs), "dof": dof, "kinds": kinds,
+                       "device_bytes": sum(pl.workspace_bytes() for pl in plans) + 16 * dof,
+                       "sweeps": {"min": min(sweeps), "max": max(sweeps), "mean": sum(sweeps) / len(sweeps)},
+                       "launch_mode": "one CUDA graph for all 64 solves (independent branches)"}}
+    print(json.dumps(line), flush=True)
+    for pl in plans:
+        pl.close()
+    return 0
+
+
+def run_serve(args) -> int:
+    """Poisson arrivals (mean 200 / s, seed 3) of problems from the mixed distribution, served with
+    continuous batching under a 120 GB device budget; inputs are device arrays of the client."""
+    import torch
+    from paper_2007_13125_gb300 import pint
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", local)
+    arr = workloads.c5_arrivals(args.requests, rate=200.0, seed=3)
+    inputs = [_device_inputs(p, dev) for _, p in arr]
+    torch.cuda.synchronize()
+    infos = []
+    with pint.Server(120 << 30, max_active=16) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for (ta, p), (v, f, fd) in zip(arr, inputs):
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(p, v, f, fd, tol=TOL))
+        for t in tickets:
+            st, info = srv.poll(t, None, timeout_us=600_000_000)
+            infos.append((st, info.t_submit, info.t_start, info.t_done, info.sweeps))
+        stats = srv.stats()
+    lat = sorted(1e3 * (d - s) for _, s, _, d, _ in infos)
+    wait = sorted(1e3 * (a - s) for _, s, a, _, _ in infos)
+    span = max(d for *_, d, _ in infos) - min(s for _, s, *_ in infos)
+    dof = sum(p.dof for _, p in arr)
+    ok = sum(1 for st, *_ in infos if st == 0)
+    line = {"metric": METRIC, "value": dof / span, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+df64", "data": "synthetic",
+            "config": {"workload": "serve_poisson200_seed3", "requests": len(arr), "completed_ok": ok,
+                       "dof": dof, "offered_dof_per_s": dof / arr[-1][0],
+                       "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+                       "queue_wait_ms_p50": float(np.percentile(wait, 50)),
+                       "queue_wait_ms_p99": float(np.percentile(wait, 99)),
+                       "budget_bytes": 120 << 30, "peak_device_bytes": stats["peak_hbm"], "max_active": 16}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_once(precision: str) -> int:
     import torch
     from paper_2007_13125_gb300 import Plan, pint
@@ -222,7 +331,19 @@ def main():
                          "captures: kernels inside graphs with conditional nodes cannot be profiled) and exit")
     ap.add_argument("--per-sweep-launches", action="store_true",
                     help="launch sweeps one by one from the host instead of one graph per solve")
+    ap.add_argument("--workload", default="heat2d",
+                    choices=["heat2d", "heat1d", "subdiff1d", "mix64", "serve"],
+                    help="heat2d (default): 2D heat 255x255, N=256, BDF4; heat1d: M=63, N=64, BDF2; "
+                         "subdiff1d: alpha=0.5, M=1023, N=1024, CQ-BDF3; mix64: one graph launch over 64 "
+                         "mixed problems; serve: Poisson request stream through the serving loop")
+    ap.add_argument("--requests", type=int, default=100, help="serve: number of requests")
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = args.workload if args.workload in WORKLOADS else "heat2d"
+    if args.workload == "mix64":
+        return run_mix(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.once:
@@ -308,7 +429,7 @@ def main():
     # our kernels per solve: form_rhs, initial guess, conversion in/out, sweeps x (sweep kernels +
     # the device-side convergence check), control init
     sweeps_main = last["mixed"][0]
-    per_sweep = 5 if p.dim == 2 else 3
+    per_sweep = (5 if p.dim == 2 else 3) + (1 if p.alpha != 1.0 else 0)
     launches = args.steps * (2 + 2 + 1 + sweeps_main * (per_sweep + (0 if args.per_sweep_launches else 1)))
 
     # ---- per-kernel CUDA-event times: the same kernels launched sweep by sweep ----

@@ -175,6 +175,9 @@ typedef struct {
   pint_plan_desc desc;  /* problem and precision (precision PINT_MIXED or PINT_FP64 recommended) */
   double tol;           /* stopping tolerance as in pint_solve */
   int max_sweeps;
+  int inputs_on_device; /* 0: v, f, fderiv are host arrays, copied by pint_submit; 1: they are
+                           device arrays owned by the caller, read when the request is admitted,
+                           and must stay valid until the request has been polled */
 } pint_request;
 typedef struct {
   int status;           /* PINT_OK, PINT_ENOTCONV, PINT_EBUDGET (larger than the budget), ... */
@@ -187,7 +190,8 @@ typedef struct {
 pint_status pint_server_create(size_t hbm_budget_bytes, int max_active, pint_server* out);
 /* Finishes admitted work, frees everything (unpolled results are dropped). NULL is accepted. */
 pint_status pint_server_destroy(pint_server s);
-/* Host arrays v [M], f [N][M], fderiv [k-1][M] (NULL when k = 1) are copied before returning. */
+/* v [M], f [N][M], fderiv [k-1][M] (NULL when k = 1): host arrays copied before returning, or
+ * device arrays (req->inputs_on_device = 1) that are read when the request is admitted. */
 pint_status pint_submit(pint_server s, const pint_request* req, const double* v, const double* f,
                         const double* fderiv, uint64_t* ticket);
 /* Wait up to timeout_us for the result: PINT_EAGAIN (timeout_us == 0) or PINT_ETIMEOUT if not

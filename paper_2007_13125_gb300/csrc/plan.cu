@@ -203,6 +203,17 @@ static void eigenvalues(int k, double alpha, double kappa, int N, pint_eig_varia
 
 using namespace pint;
 
+namespace {
+// The last batch graph, reused while the same plans, arrays, tol and max_sweeps come back.
+struct BatchCache {
+  std::mutex mu;
+  std::vector<const void*> key;
+  double tol = 0.0;
+  int max_sweeps = 0;
+  cudaGraphExec_t exec = nullptr;
+} g_batch;
+}  // namespace
+
 #define PINT_CUDA_B(call)                                      \
   do {                                                         \
     cudaError_t _e = (call);                                   \
@@ -488,6 +499,14 @@ extern "C" pint_status pint_plan_create(int k, double alpha, double kappa, doubl
 
 extern "C" pint_status pint_plan_destroy(pint_plan p) {
   if (!p) return PINT_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_batch.mu);
+    if (g_batch.exec && std::find(g_batch.key.begin(), g_batch.key.end(), (const void*)p) != g_batch.key.end()) {
+      cudaGraphExecDestroy(g_batch.exec);
+      g_batch.exec = nullptr;
+      g_batch.key.clear();
+    }
+  }
   cudaDeviceSynchronize();
   destroy_plan(p);
   return PINT_OK;
@@ -924,26 +943,42 @@ extern "C" pint_status pint_batch_solve(pint_plan* plans, int n, const double* c
                                         void* stream) {
   if (n < 1 || !plans || !Fhat || !U) return fail(PINT_EINVAL, "bad batch arguments");
   if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
+  std::vector<const void*> key;
+  key.reserve(3 * (size_t)n);
   for (int i = 0; i < n; ++i) {
     if (!plans[i] || !Fhat[i] || !U[i]) return fail(PINT_EINVAL, "NULL plan or array in batch");
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return fail(PINT_EINVAL, "a plan appears twice in one batch");
+    key.push_back(plans[i]);
+    key.push_back(Fhat[i]);
+    key.push_back(U[i]);
   }
   cudaStream_t st = (cudaStream_t)stream;
-  cudaGraph_t g;
-  PINT_CUDA(cudaGraphCreate(&g, 0));
-  pint_status s = PINT_OK;
-  for (int i = 0; i < n && s == PINT_OK; ++i) s = add_solve_nodes(plans[i], g, Fhat[i], U[i], tol, max_sweeps);
-  cudaGraphExec_t ex = nullptr;
-  if (s == PINT_OK) {
-    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
-    if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphInstantiate");
+  std::lock_guard<std::mutex> lk(g_batch.mu);
+  if (!g_batch.exec || g_batch.key != key || g_batch.tol != tol || g_batch.max_sweeps != max_sweeps) {
+    if (g_batch.exec) {
+      cudaGraphExecDestroy(g_batch.exec);
+      g_batch.exec = nullptr;
+    }
+    cudaGraph_t g;
+    PINT_CUDA(cudaGraphCreate(&g, 0));
+    pint_status s = PINT_OK;
+    for (int i = 0; i < n && s == PINT_OK; ++i) s = add_solve_nodes(plans[i], g, Fhat[i], U[i], tol, max_sweeps);
+    if (s == PINT_OK) {
+      cudaError_t e = cudaGraphInstantiate(&g_batch.exec, g, 0);
+      if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphInstantiate");
+    }
+    cudaGraphDestroy(g);
+    if (s != PINT_OK) {
+      g_batch.exec = nullptr;
+      return s;
+    }
+    g_batch.key = key;
+    g_batch.tol = tol;
+    g_batch.max_sweeps = max_sweeps;
   }
-  cudaGraphDestroy(g);
-  if (s != PINT_OK) return s;
-  cudaError_t e = cudaGraphLaunch(ex, st);
+  cudaError_t e = cudaGraphLaunch(g_batch.exec, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaGraphExecDestroy(ex);
   if (e != cudaSuccess) return cuda_fail(e, "batch graph");
   bool all = true;
   for (int i = 0; i < n; ++i) {

@@ -115,7 +115,8 @@ enum ReqState { QUEUED, RUNNING, DONE };
 struct Request {
   uint64_t ticket;
   pint_request req;
-  std::vector<double> v, f, fd;
+  std::vector<double> v, f, fd;     // host inputs (copied at submit)
+  const double *uv = nullptr, *uf = nullptr, *ufd = nullptr;  // caller-owned device inputs
   size_t need = 0;
   ReqState state = QUEUED;
   pint_status status = PINT_OK;
@@ -166,8 +167,9 @@ size_t request_bytes(const pint_request& r) {
   const pint_plan_desc& d = r.desc;
   const size_t M = (size_t)d.grid.mx * (d.grid.dim == 2 ? d.grid.my : 1);
   const size_t NM = (size_t)d.N * M;
-  // F_hat, U, f on the device plus v and the time derivatives of f at 0
-  return plan_bytes_estimate(&d) + 3 * 8 * NM + 8 * M * (size_t)(d.k + 1) + 8 * 256;
+  // F_hat and U on the device, plus copies of f, v and d^l f(0) when the inputs come from the host
+  const size_t inputs = r.inputs_on_device ? 0 : 8 * NM + 8 * M * (size_t)(d.k + 1);
+  return plan_bytes_estimate(&d) + 2 * 8 * NM + inputs + 8 * 256;
 }
 
 void release_request_memory(pint_server_s* s, Request* r) {
@@ -196,21 +198,27 @@ void start_request(pint_server_s* s, Request* r) {
     *p = (double*)s->arena->alloc(std::max<size_t>(n, 1) * sizeof(double));
     if (!*p) status = PINT_ENOMEM;
   };
-  take(&r->dv, M);
-  take(&r->df, NM);
-  if (d.k >= 2) take(&r->dfd, (size_t)(d.k - 1) * M);
+  const bool dev_in = r->req.inputs_on_device != 0;
+  if (!dev_in) {
+    take(&r->dv, M);
+    take(&r->df, NM);
+    if (d.k >= 2) take(&r->dfd, (size_t)(d.k - 1) * M);
+  }
   take(&r->dF, NM);
   take(&r->dU, NM);
   cudaError_t e = cudaSuccess;
-  if (status == PINT_OK) {
+  const double* in_v = dev_in ? r->uv : r->dv;
+  const double* in_f = dev_in ? r->uf : r->df;
+  const double* in_fd = dev_in ? r->ufd : r->dfd;
+  if (status == PINT_OK && !dev_in) {
     e = cudaMemcpyAsync(r->dv, r->v.data(), M * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r->df, r->f.data(), NM * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && d.k >= 2)
       e = cudaMemcpyAsync(r->dfd, r->fd.data(), (size_t)(d.k - 1) * M * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) status = PINT_ECUDA;
   }
-  if (status == PINT_OK) status = pint_form_rhs(r->plan, r->dv, r->df, r->dfd, r->dF, st);
-  if (status == PINT_OK) status = pint_initial_guess(r->plan, r->dv, r->dU, st);
+  if (status == PINT_OK) status = pint_form_rhs(r->plan, in_v, in_f, in_fd, r->dF, st);
+  if (status == PINT_OK) status = pint_initial_guess(r->plan, in_v, r->dU, st);
   if (status == PINT_OK) status = solve_enqueue(r->plan, r->dF, r->dU, r->req.tol, r->req.max_sweeps, st);
   if (status == PINT_OK) {
     e = cudaEventRecord(s->events[r->slot], st);
@@ -426,9 +434,15 @@ extern "C" pint_status pint_submit(pint_server s, const pint_request* req, const
   r->req = *req;
   const size_t M = (size_t)d.grid.mx * (d.grid.dim == 2 ? d.grid.my : 1);
   const size_t NM = (size_t)d.N * M;
-  r->v.assign(v, v + M);
-  r->f.assign(f, f + NM);
-  if (d.k >= 2) r->fd.assign(fderiv, fderiv + (size_t)(d.k - 1) * M);
+  if (req->inputs_on_device) {
+    r->uv = v;
+    r->uf = f;
+    r->ufd = fderiv;
+  } else {
+    r->v.assign(v, v + M);
+    r->f.assign(f, f + NM);
+    if (d.k >= 2) r->fd.assign(fderiv, fderiv + (size_t)(d.k - 1) * M);
+  }
   r->need = request_bytes(*req);
   {
     std::lock_guard<std::mutex> lk(s->mu);

@@ -41,7 +41,8 @@ class _Desc(ctypes.Structure):
 
 
 class _Req(ctypes.Structure):
-    _fields_ = [("desc", _Desc), ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int)]
+    _fields_ = [("desc", _Desc), ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int),
+                ("inputs_on_device", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -290,12 +291,19 @@ class Server:
         self.close()
 
     def submit(self, p, v, f, fderiv, tol=1e-8, max_sweeps=50, precision="mixed"):
-        """v, f, fderiv: host float64 numpy arrays (copied at submit)."""
+        """v, f, fderiv: host float64 numpy arrays (copied at submit), or CUDA float64 tensors
+        (read at admission; the caller keeps them alive until the request is polled)."""
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         d = _Desc(p.k, float(p.alpha), float(p.kappa), float(p.tau), int(p.N),
                   _Grid(p.dim, p.mx, p.my if p.dim == 2 else 1), prec, PINT_EIG_TRUNC_DFT, 0)
-        req = _Req(d, float(tol), int(max_sweeps))
         t = ctypes.c_uint64(0)
+        if hasattr(v, "is_cuda"):
+            req = _Req(d, float(tol), int(max_sweeps), 1)
+            check(lib().pint_submit(self.handle, ctypes.byref(req), _ptr(v), _ptr(f),
+                                    _ptr(fderiv) if fderiv is not None and fderiv.numel() else None,
+                                    ctypes.byref(t)))
+            return int(t.value)
+        req = _Req(d, float(tol), int(max_sweeps), 0)
         v = np.ascontiguousarray(v, dtype=np.float64)
         f = np.ascontiguousarray(f, dtype=np.float64)
         fd = np.ascontiguousarray(fderiv, dtype=np.float64)

@@ -146,3 +146,19 @@ def test_server_budget_admission_and_errors():
         assert srv.stats()["peak_hbm"] <= budget
         st, _ = srv.poll(123456, None, 0)
         assert st == pint.PINT_ENOTFOUND
+
+
+def test_server_device_inputs():
+    """Requests whose inputs already live on the device are read at admission (no host copy)."""
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import pint
+    dev = torch.device("cuda:0")
+    probs = _problems(80)[:3]
+    inputs = [(torch.tensor(p.v, device=dev), torch.tensor(p.f(), device=dev), torch.tensor(p.fderiv(), device=dev))
+              for p in probs]
+    with pint.Server(1 << 30, max_active=2) as srv:
+        tickets = [srv.submit(p, *inp, tol=1e-9) for p, inp in zip(probs, inputs)]
+        for p, t in zip(probs, tickets):
+            out = np.empty((p.N, p.M))
+            st, info = srv.poll(t, out, timeout_us=30_000_000)
+            assert st == 0 and rel_l2(out, oracle_solution(p)) <= 1e-8
