@@ -69,6 +69,46 @@ __device__ __forceinline__ ff ff_add_f(ff x, float c) {
   return r;
 }
 
+// ---- double-float scalar and complex arithmetic (used by the FFTs of the CQ history) ----
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  ff r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.hi, -b.lo}); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  ff r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+
+// complex double-float: (rh + rl) + i (ih + il)
+struct ffc { float rh, rl, ih, il; };
+
+__device__ __forceinline__ ffc ffc_make(ff re, ff im) { return ffc{re.hi, re.lo, im.hi, im.lo}; }
+__device__ __forceinline__ ff ffc_re(ffc a) { return ff{a.rh, a.rl}; }
+__device__ __forceinline__ ff ffc_im(ffc a) { return ff{a.ih, a.il}; }
+__device__ __forceinline__ ffc cadd(ffc a, ffc b) {
+  return ffc_make(ff_add(ffc_re(a), ffc_re(b)), ff_add(ffc_im(a), ffc_im(b)));
+}
+__device__ __forceinline__ ffc csub(ffc a, ffc b) {
+  return ffc_make(ff_sub(ffc_re(a), ffc_re(b)), ff_sub(ffc_im(a), ffc_im(b)));
+}
+__device__ __forceinline__ ffc cmul(ffc a, ffc b) {
+  const ff ar = ffc_re(a), ai = ffc_im(a), br = ffc_re(b), bi = ffc_im(b);
+  return ffc_make(ff_sub(ff_mul(ar, br), ff_mul(ai, bi)), ff_add(ff_mul(ar, bi), ff_mul(ai, br)));
+}
+__device__ __forceinline__ ffc cmulc(ffc a, ffc b) {  // a * conj(b)
+  const ff ar = ffc_re(a), ai = ffc_im(a), br = ffc_re(b), bi = ffc_im(b);
+  return ffc_make(ff_add(ff_mul(ar, br), ff_mul(ai, bi)), ff_sub(ff_mul(ai, br), ff_mul(ar, bi)));
+}
+
 // Split a double into hi + lo with integer operations only. On GB300 every FP64<->FP32
 // conversion runs at the FP64 rate (~1/70 of FP32), so the bit patterns are taken apart
 // directly: hi = x rounded to 24 significant bits (nearest, ties to even), exact as a float;

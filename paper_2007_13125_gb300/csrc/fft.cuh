@@ -18,6 +18,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "ff.cuh"
+
 namespace pint {
 
 template <typename T> struct c2;
@@ -68,6 +70,22 @@ __device__ __forceinline__ V twid16(V v) {
   }
 }
 
+// The same rotation for a double-float complex value (ffc, ff.cuh), constants split into
+// hi + lo floats at compile time.
+template <int M, int DIR>
+__device__ __forceinline__ ffc twid16(ffc v) {
+  if constexpr (M == 0) {
+    return v;
+  } else if constexpr (M == 4) {
+    return DIR < 0 ? ffc{v.ih, v.il, -v.rh, -v.rl} : ffc{-v.ih, -v.il, v.rh, v.rl};
+  } else {
+    constexpr double c = cos16(M), s = DIR * sin16(M);
+    constexpr float ch = (float)c, sh = (float)s;
+    constexpr float cl = (float)(c - (double)ch), sl = (float)(s - (double)sh);
+    return cmul(v, ffc{ch, cl, sh, sl});
+  }
+}
+
 __host__ __device__ constexpr int ilog2c(int r) { return r <= 1 ? 0 : 1 + ilog2c(r >> 1); }
 __host__ __device__ constexpr int brev(int i, int bits) {
   return bits == 0 ? 0 : ((i & 1) << (bits - 1)) | brev(i >> 1, bits - 1);
@@ -115,25 +133,26 @@ __device__ __forceinline__ void dft_reg(V (&x)[R]) {
   for (int i = 0; i < R; ++i) x[i] = y[i];
 }
 
-// Radix schedule: np = ceil(log2 L / 4) passes with the bits spread evenly (first passes
-// take the extra bit), each radix in {2, 4, 8, 16}.
-__host__ __device__ inline int fft_npass(int L) {
+// Radix schedule: np = ceil(log2 L / MAXLOG) passes with the bits spread evenly (first passes
+// take the extra bit), each radix at most 2^MAXLOG (16 by default; smaller for wide element
+// types to bound registers).
+__host__ __device__ inline int fft_npass(int L, int maxlog = 4) {
   const int e = ilog2c(L);
-  return (e + 3) / 4;
+  return (e + maxlog - 1) / maxlog;
 }
-__host__ __device__ inline int fft_logradix(int L, int pass) {
+__host__ __device__ inline int fft_logradix(int L, int pass, int maxlog = 4) {
   const int e = ilog2c(L);
-  const int np = (e + 3) / 4;
+  const int np = (e + maxlog - 1) / maxlog;
   return e / np + (pass < e % np ? 1 : 0);
 }
-__host__ __device__ inline int fft_radix(int L, int pass) { return 1 << fft_logradix(L, pass); }
+__host__ __device__ inline int fft_radix(int L, int pass, int maxlog = 4) { return 1 << fft_logradix(L, pass, maxlog); }
 
 // position of frequency j in the output of the forward transform
-__host__ __device__ inline int fft_pos(int j, int L) {
-  const int np = fft_npass(L);
+__host__ __device__ inline int fft_pos(int j, int L, int maxlog = 4) {
+  const int np = fft_npass(L, maxlog);
   int p = 0, logLs = ilog2c(L);
   for (int i = 0; i < np; ++i) {
-    const int lr = fft_logradix(L, i);
+    const int lr = fft_logradix(L, i, maxlog);
     const int q = j & ((1 << lr) - 1);
     j >>= lr;
     logLs -= lr;
@@ -143,8 +162,8 @@ __host__ __device__ inline int fft_pos(int j, int L) {
 }
 
 // fill perm[j] = fft_pos(j, L), j < L (cooperatively, by the whole block)
-__device__ __forceinline__ void fft_perm_table(unsigned short* perm, int L) {
-  for (int j = threadIdx.x; j < L; j += blockDim.x) perm[j] = (unsigned short)fft_pos(j, L);
+__device__ __forceinline__ void fft_perm_table(unsigned short* perm, int L, int maxlog = 4) {
+  for (int j = threadIdx.x; j < L; j += blockDim.x) perm[j] = (unsigned short)fft_pos(j, L, maxlog);
 }
 
 // One pass of radix R = 2^LR at sub-length Ls = 2^logLs on a tile of C = 2^logC columns.
@@ -181,42 +200,46 @@ __device__ __forceinline__ void fft_pass(V* X, int ld, int logC, int logL, int l
   }
 }
 
-template <int DIR, typename V>
+template <int DIR, int MAXLOG, typename V>
 __device__ __forceinline__ void fft_pass_dispatch(int lr, V* X, int ld, int logC, int logL, int logLs,
                                                   const V* tw) {
   switch (lr) {
     case 1: fft_pass<1, DIR>(X, ld, logC, logL, logLs, tw); break;
     case 2: fft_pass<2, DIR>(X, ld, logC, logL, logLs, tw); break;
-    case 3: fft_pass<3, DIR>(X, ld, logC, logL, logLs, tw); break;
-    default: fft_pass<4, DIR>(X, ld, logC, logL, logLs, tw); break;
+    default:
+      if constexpr (MAXLOG >= 4) {
+        if (lr == 4) { fft_pass<4, DIR>(X, ld, logC, logL, logLs, tw); break; }
+      }
+      fft_pass<3, DIR>(X, ld, logC, logL, logLs, tw);
+      break;
   }
 }
 
-// Forward: natural order in, permuted (fft_pos) order out; exp(-2 pi i n j / L).
+// Forward: natural order in, permuted (fft_pos(., ., MAXLOG)) order out; exp(-2 pi i n j / L).
 // tw[m] = exp(-2 pi i m / L), m < L, must be visible to all threads. C = 2^logC columns.
-template <typename V>
+template <int MAXLOG = 4, typename V>
 __device__ void fft_forward(V* X, int ld, int logC, int L, const V* tw) {
   const int logL = ilog2c(L);
-  const int np = fft_npass(L);
+  const int np = fft_npass(L, MAXLOG);
   int logLs = logL;
   for (int i = 0; i < np; ++i) {
-    const int lr = fft_logradix(L, i);
-    fft_pass_dispatch<-1>(lr, X, ld, logC, logL, logLs, tw);
+    const int lr = fft_logradix(L, i, MAXLOG);
+    fft_pass_dispatch<-1, MAXLOG>(lr, X, ld, logC, logL, logLs, tw);
     logLs -= lr;
     __syncthreads();
   }
 }
 
 // Inverse: permuted order in, natural order out, unnormalised: x_n = sum_j X_j exp(+2 pi i n j / L).
-template <typename V>
+template <int MAXLOG = 4, typename V>
 __device__ void fft_inverse(V* X, int ld, int logC, int L, const V* tw) {
   const int logL = ilog2c(L);
-  const int np = fft_npass(L);
+  const int np = fft_npass(L, MAXLOG);
   int logLs = 0;
   for (int i = np - 1; i >= 0; --i) {
-    const int lr = fft_logradix(L, i);
+    const int lr = fft_logradix(L, i, MAXLOG);
     logLs += lr;
-    fft_pass_dispatch<1>(lr, X, ld, logC, logL, logLs, tw);
+    fft_pass_dispatch<1, MAXLOG>(lr, X, ld, logC, logL, logLs, tw);
     __syncthreads();
   }
 }

@@ -139,13 +139,20 @@ struct ResidStage {
   float* Yh;       // [2][kLK][P2]  (row below, row above)
   float* Yl;
   double* F;       // [kLK][P2]
-  double* Yc;      // [kLK][P2] (CQ history) or unused
+  float* Ych;      // [kLK][P2] (CQ history, double-float) or unused
+  float* Ycl;
 };
 
+// levels per staged chunk: at least kLK, and enough that every thread has a level
+__host__ __device__ inline int resid_chunk(int C) {
+  const int lk = kThreads / (2 * C);
+  return lk > kLK ? lk : kLK;
+}
+
 __host__ __device__ inline size_t resid_stage_bytes(int C) {
-  const size_t W = 2 * (size_t)C + 2, P2 = 2 * (size_t)C;
-  return 2 * sizeof(float) * (kLK + kMaxK) * W + 2 * sizeof(float) * 2 * kLK * P2 +
-         2 * sizeof(double) * kLK * P2;
+  const size_t W = 2 * (size_t)C + 2, P2 = 2 * (size_t)C, LK = resid_chunk(C);
+  return 2 * sizeof(float) * (LK + kMaxK) * W + 2 * sizeof(float) * 2 * LK * P2 +
+         2 * sizeof(double) * LK * P2;
 }
 
 size_t resid_fwd_smem(int N, int C) { return time_tile_bytes<float2>(N, C) + resid_stage_bytes(C) + 16; }
@@ -158,15 +165,17 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
   time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
   unsigned char* sp = reinterpret_cast<unsigned char*>(perm + N);
   sp = reinterpret_cast<unsigned char*>(((size_t)sp + 15) & ~(size_t)15);
+  const int LKC = resid_chunk(C);  // levels per staged chunk
   ResidStage st;
   st.W = 2 * C + 2;
   st.P2 = 2 * C;
   st.F = reinterpret_cast<double*>(sp);
-  st.Yc = st.F + kLK * st.P2;
-  st.Uh = reinterpret_cast<float*>(st.Yc + kLK * st.P2);
-  st.Ul = st.Uh + (kLK + kMaxK) * st.W;
-  st.Yh = st.Ul + (kLK + kMaxK) * st.W;
-  st.Yl = st.Yh + 2 * kLK * st.P2;
+  st.Ych = reinterpret_cast<float*>(st.F + LKC * st.P2);
+  st.Ycl = st.Ych + LKC * st.P2;
+  st.Uh = st.Ycl + LKC * st.P2;
+  st.Ul = st.Uh + (LKC + kMaxK) * st.W;
+  st.Yh = st.Ul + (LKC + kMaxK) * st.W;
+  st.Yl = st.Yh + 2 * LKC * st.P2;
 
   const int m0 = blockIdx.x * 2 * C;
   const int P2 = st.P2, W = st.W;
@@ -184,12 +193,12 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
   const int mq = m0 + q;
   const bool qvalid = mq < M;
   const int xq = qvalid ? mq % mx : 0;
-  for (int c0 = 0; c0 < N; c0 += kLK) {
-    const int LK = min(kLK, N - c0);
+  for (int c0 = 0; c0 < N; c0 += LKC) {
+    const int LK = min(LKC, N - c0);
     // ---- stage chunk levels [c0, c0 + LK) (+ kMaxK levels of history for U) ----
     {
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-      for (int l = warp; l < kLK + kMaxK; l += nwarp) {
+      for (int l = warp; l < LKC + kMaxK; l += nwarp) {
         const int lev = c0 - kMaxK + l;
         const bool lok = lev >= 0 && lev < N;
         const size_t grow = (size_t)(lok ? lev : 0) * M;
@@ -212,13 +221,16 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
       const size_t g = (size_t)(c0 + l) * M + mq;
       if (qvalid) {
         cp_async8(st.F + e, a.F + g);
-        if (a.y) cp_async8(st.Yc + e, a.y + g);
+        if (a.yhi) {
+          cp_async4(st.Ych + e, a.yhi + g);
+          cp_async4(st.Ycl + e, a.ylo + g);
+        }
       }
       if (two_d) {
         float* bh = st.Yh + e;
         float* bl = st.Yl + e;
-        float* ah = st.Yh + kLK * P2 + e;
-        float* al = st.Yl + kLK * P2 + e;
+        float* ah = st.Yh + LKC * P2 + e;
+        float* al = st.Yl + LKC * P2 + e;
         if (qvalid && mq >= mx) { cp_async4(bh, a.Uhi + g - mx); cp_async4(bl, a.Ulo + g - mx); }
         else { *bh = 0.f; *bl = 0.f; }
         if (mq + mx < M) { cp_async4(ah, a.Uhi + g + mx); cp_async4(al, a.Ulo + g + mx); }
@@ -236,7 +248,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
         const int ub = (l + kMaxK) * W + q + 1;  // this point in the U stage
         ff_acc acc;
         acc.init(ff_from_double(st.F[e]));
-        if (a.y) acc.sub(ff_from_double(st.Yc[e]));
+        if (a.yhi) acc.sub(ff{st.Ych[e], st.Ycl[e]});
         acc.fma_term(cw[0], ff{st.Uh[ub], st.Ul[ub]}, -1.f);
 #pragma unroll
         for (int j = 1; j <= kMaxK; ++j)
@@ -245,7 +257,7 @@ __global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
         if (xq < mx - 1) acc.fma_term(gx, ff{st.Uh[ub + 1], st.Ul[ub + 1]}, 1.f);
         if (two_d) {
           acc.fma_term(gy, ff{st.Yh[e], st.Yl[e]}, 1.f);
-          acc.fma_term(gy, ff{st.Yh[kLK * P2 + e], st.Yl[kLK * P2 + e]}, 1.f);
+          acc.fma_term(gy, ff{st.Yh[LKC * P2 + e], st.Yl[LKC * P2 + e]}, 1.f);
         }
         r = acc.value() * __ldg(a.s + i);
       }
@@ -430,6 +442,53 @@ __global__ void __launch_bounds__(kThreads) k_toeplitz(ToepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// MIXED CQ history y = tau^-alpha (omega * U) in double-float: the same circulant embedding
+// with 2N-point FFTs whose butterflies are error-free-transformation arithmetic on the FP32
+// pipes (~48-bit significand; GB300's FP64 pipe is ~70x slower than its FP32 pipes).
+// ---------------------------------------------------------------------------
+size_t toep_ff_smem(int N, int C) { return time_tile_bytes<ffc>(2 * N, C); }
+
+__global__ void __launch_bounds__(kThreads) k_toeplitz_ff(ToepFFArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = a.N, C = a.C, M = a.M, L = 2 * a.N, logC = a.logC;
+  ffc* X = reinterpret_cast<ffc*>(smraw);
+  ffc* tw = X + (size_t)L * C;
+  unsigned short* perm = reinterpret_cast<unsigned short*>(tw + L);
+  const ffc* gtw = reinterpret_cast<const ffc*>(a.tw);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = gtw[i];
+  (void)perm;
+  const int m0 = blockIdx.x * 2 * C;
+  for (int it = threadIdx.x; it < (L << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), i = it >> logC;
+    ffc v = {0.f, 0.f, 0.f, 0.f};
+    if (i < N) {
+      const int ma = m0 + cc, mb = m0 + C + cc;
+      const size_t row = (size_t)i * M;
+      if (ma < M) { v.rh = a.Uhi[row + ma]; v.rl = a.Ulo[row + ma]; }
+      if (mb < M) { v.ih = a.Uhi[row + mb]; v.il = a.Ulo[row + mb]; }
+    }
+    X[(size_t)i * C + cc] = v;
+  }
+  __syncthreads();
+  fft_forward<kToepFFMaxLog>(X, C, logC, L, tw);
+  const ffc* what = reinterpret_cast<const ffc*>(a.what);
+  for (int it = threadIdx.x; it < (L << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), p = it >> logC;
+    X[(size_t)p * C + cc] = cmul(X[(size_t)p * C + cc], what[p]);
+  }
+  __syncthreads();
+  fft_inverse<kToepFFMaxLog>(X, C, logC, L, tw);
+  for (int it = threadIdx.x; it < (N << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), i = it >> logC;
+    const ffc z = X[(size_t)i * C + cc];
+    const int ma = m0 + cc, mb = m0 + C + cc;
+    const size_t row = (size_t)i * M;
+    if (ma < M) { a.yhi[row + ma] = z.rh; a.ylo[row + ma] = z.rl; }
+    if (mb < M) { a.yhi[row + mb] = z.ih; a.ylo[row + mb] = z.il; }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Right-hand side: F_hat_n = f(t_n) + a_n (f(0) - A v) + sum_l b_{l,n} tau^l d^l f(0)
 //                            + tau^-alpha sum_{j<n} omega_j v        (eq. (2.1), (2.7), (3.7), (3.12))
 // ---------------------------------------------------------------------------
@@ -597,6 +656,16 @@ cudaError_t launch_toeplitz(const ToepArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   prof_begin("toeplitz_f64", st);
   k_toeplitz<<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_toeplitz_ff(const ToepFFArgs& a, cudaStream_t st) {
+  const size_t sm = toep_ff_smem(a.N, a.C);
+  cudaError_t e = set_smem(k_toeplitz_ff, sm);
+  if (e != cudaSuccess) return e;
+  prof_begin("toeplitz_ff", st);
+  k_toeplitz_ff<<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
 }

@@ -15,7 +15,7 @@ constexpr int kMaxK = 6;
 struct ResidFwdArgs {
   const float* Uhi; const float* Ulo;      // iterate U [N][M] (double-float)
   const double* F;                         // F_hat [N][M] (FP64, split to double-float on load)
-  const double* y;                         // CQ: tau^-alpha (L_omega U) [N][M], else null
+  const float* yhi; const float* ylo;      // CQ: tau^-alpha (L_omega U) [N][M] double-float, else null
   float2* S;                               // half spectrum [(N/2+1)][M]
   const float* s;                          // kappa^{i/N}, i < N
   const float2* tw;                        // exp(-2 pi i m / N), m < N
@@ -57,6 +57,15 @@ struct ToepArgs {
   const double2* what;                     // FFT_{2N}(omega, zero padded), permuted, pre-scaled
   const double2* tw;                       // exp(-2 pi i m / 2N)
   int N, M, C, logC, half;                 // half 0: z_0..z_{N-1}; 1: z_N..z_{2N-1}
+};
+
+// MIXED CQ: the same product in double-float arithmetic on the FP32 pipes.
+struct ToepFFArgs {
+  const float* Uhi; const float* Ulo;      // U [N][M] (double-float)
+  float* yhi; float* ylo;                  // tau^-alpha (L_omega U) [N][M] (double-float)
+  const void* what;                        // ffc [2N]: FFT_{2N}(omega), radix-8 permuted order, * tau^-alpha / 2N
+  const void* tw;                          // ffc [2N]: exp(-2 pi i m / 2N)
+  int N, M, C, logC;
 };
 
 // right-hand side F_hat (FP64)
@@ -113,6 +122,9 @@ cudaError_t launch_inv_upd(const InvUpdArgs& a, cudaStream_t st);
 template <typename T> cudaError_t launch_direct_fwd(const DirectFwdArgs<T>& a, cudaStream_t st);
 template <typename T> cudaError_t launch_direct_inv(const DirectInvArgs<T>& a, cudaStream_t st);
 cudaError_t launch_toeplitz(const ToepArgs& a, cudaStream_t st);
+cudaError_t launch_toeplitz_ff(const ToepFFArgs& a, cudaStream_t st);
+size_t toep_ff_smem(int N, int C);
+constexpr int kToepFFMaxLog = 3;           // radix <= 8 for the double-float FFT (register budget)
 cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t st);
 template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t st);
 cudaError_t launch_tri(const TriArgs& a, cudaStream_t st);

@@ -417,6 +417,28 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
     }
     if ((s = upload(p, &p->what_lo, lo)) != PINT_OK) return bail(s);
     if ((s = upload(p, &p->what_up, up)) != PINT_OK) return bail(s);
+    if (p->prec == PINT_MIXED) {
+      // double-float tables for the MIXED history product (FFT radix <= 8 ordering)
+      auto split = [](double x, float& h, float& l) {
+        h = (float)x;
+        l = (float)(x - (double)h);
+      };
+      std::vector<float4> wff(L), tff(L);
+      for (int j = 0; j < L; ++j) {
+        const int pos = fft_pos(j, L, kToepFFMaxLog);
+        const cd vlo = w[j] * (ta / L);
+        float4 q;
+        split(vlo.real(), q.x, q.y);
+        split(vlo.imag(), q.z, q.w);
+        wff[pos] = q;
+        const cd r = unit_root(j, L);
+        split(r.real(), q.x, q.y);
+        split(r.imag(), q.z, q.w);
+        tff[j] = q;
+      }
+      if ((s = upload(p, &p->what_ff, wff)) != PINT_OK) return bail(s);
+      if ((s = upload(p, &p->tw_ff, tff)) != PINT_OK) return bail(s);
+    }
     if ((s = dalloc(p, &p->z, (size_t)N * M)) != PINT_OK) return bail(s);
   }
   // workspaces
@@ -446,12 +468,15 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   }
   PINT_CUDA_B(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
 
-  // tile widths (columns per CTA), shared-memory budget ~96 KB
+  // tile widths (columns per CTA): limited by ~96 KB of shared memory, and narrow enough that
+  // the M points of a problem still give two CTAs per SM (small M: many narrow tiles rather
+  // than a few wide ones)
   const size_t budget = 96 * 1024;
-  const int cmin_t = std::max(1, kThreads / N);  // every thread needs >= 1 time level
-  p->Ct = pick_cols((size_t)N * sizeof(float2), budget, 32, cmin_t);
-  p->Ctd = pick_cols((size_t)N * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2)), budget, 32, cmin_t);
-  p->Cz = pick_cols((size_t)2 * N * sizeof(double2), 160 * 1024, 16, 1);
+  int occ = 1;
+  while (occ < 32 && (size_t)M / (size_t)(4 * occ) >= 2 * 152) occ *= 2;
+  p->Ct = std::min(pick_cols((size_t)N * sizeof(float2), budget, 32, 1), occ);
+  p->Ctd = std::min(pick_cols((size_t)N * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2)), budget, 32, 1), occ);
+  p->Cz = std::min(pick_cols((size_t)2 * N * sizeof(double2), 160 * 1024, 16, 1), occ);
   const size_t ve = p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2);
   // sine-transform tiles: ~40 KB of lines so that several CTAs share an SM
   p->Cx = pick_cols((size_t)2 * (p->mx + 1) * ve, 40 * 1024, 16, 1);
@@ -632,17 +657,20 @@ pint_status autotune_ysolve(pint_plan p) {
 // MIXED sweep on the plan's double-float iterate (Uhi/Ulo); F_hat read in FP64
 pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   const int N = p->N, M = p->M;
+  float* yhi = reinterpret_cast<float*>(p->z);
+  float* ylo = yhi + (size_t)N * M;
   if (p->cq) {
-    ToepArgs ta{};
-    ta.Uhi = p->Uhi; ta.Ulo = p->Ulo; ta.ukind = 1; ta.out = p->z; ta.what = p->what_lo;
-    ta.tw = p->tw_2n; ta.N = N; ta.M = M; ta.C = p->Cz; ta.logC = ilog2c(p->Cz); ta.half = 0;
-    cudaError_t e = launch_toeplitz(ta, st);
+    ToepFFArgs ta{};
+    ta.Uhi = p->Uhi; ta.Ulo = p->Ulo; ta.yhi = yhi; ta.ylo = ylo; ta.what = p->what_ff; ta.tw = p->tw_ff;
+    ta.N = N; ta.M = M; ta.C = p->Cz; ta.logC = ilog2c(p->Cz);
+    cudaError_t e = launch_toeplitz_ff(ta, st);
     if (e != cudaSuccess) return cuda_fail(e, "toeplitz kernel");
   }
   PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
   ResidFwdArgs r{};
   r.Uhi = p->Uhi; r.Ulo = p->Ulo; r.F = Fhat;
-  r.y = p->cq ? p->z : nullptr;
+  r.yhi = p->cq ? yhi : nullptr;
+  r.ylo = p->cq ? ylo : nullptr;
   r.S = reinterpret_cast<float2*>(p->S);
   r.s = p->tf.s; r.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
   r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Ct; r.logC = ilog2c(p->Ct);
