@@ -20,9 +20,16 @@
 
 namespace pint {
 
+// Tile layout: element (row, line) of a C-line tile at X[row * (C + 1) + line]. With C = 16 (the
+// usual width) a warp touches 16 lines of two rows in the FFT passes, or 32 consecutive rows of
+// one line when it moves a contiguous line between global and shared memory; the +1 pitch keeps
+// both patterns free of bank conflicts. Rows read in the FFT's digit-reversed order are first
+// brought into natural order through registers (lanes along lines), for the same reason.
+template <typename T> constexpr int axis_regs() { return sizeof(T) == 4 ? 16 : 8; }
 template <typename T> size_t axis_smem(int n, int C) {
   const size_t L = 2 * (size_t)(n + 1);
-  return sizeof(typename c2<T>::t) * (L * (C + 1) + L) + sizeof(unsigned short) * L + 2 * sizeof(int) * C;
+  return sizeof(typename c2<T>::t) * (L * (C + 1) + L + C) + sizeof(T) * (size_t)(n + 1) +
+         sizeof(unsigned short) * L + 2 * sizeof(int) * C + 64;
 }
 
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
@@ -31,11 +38,15 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
   using V = typename c2<T>::t;
+  constexpr int KR = axis_regs<T>();  // register slots per thread for the reordering
+  constexpr int KB = 8;               // global loads in flight per thread
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n = a.n, C = a.C, logC = a.logC, ld = a.ld, L = 2 * (a.n + 1);
   V* X = reinterpret_cast<V*>(smraw);
   V* tw = X + (size_t)L * ld;
-  unsigned short* perm = reinterpret_cast<unsigned short*>(tw + L);
+  V* dcol = tw + L;                                      // line -> sigma_j + lambda_other (op 1)
+  T* lam = reinterpret_cast<T*>(dcol + C);               // lambda along this axis (op 1)
+  unsigned short* perm = reinterpret_cast<unsigned short*>(lam + n + 1);
   int* lj = reinterpret_cast<int*>(perm + L + (L & 1));  // line -> j
   int* lp = lj + C;                                      // line -> position within its slice
   const V* gtw = reinterpret_cast<const V*>(a.tw);
@@ -53,44 +64,108 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
   const T zero = T(0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
 
-  // ---- load with odd extension ----
+  // ---- load with odd extension (KB independent loads per thread before the stores) ----
   if (a.mode == 0) {
     for (int cc = warp; cc < C; cc += nwarp) {
       const int line = line0 + cc;
-      for (int i = lane; i < n; i += 32) {
-        V v = mk(zero, zero);
-        if (line < a.lines) v = S[(size_t)line * n + i];
-        X[(size_t)(i + 1) * ld + cc] = v;
-        X[(size_t)(L - 1 - i) * ld + cc] = mk(-v.x, -v.y);
+      const bool ok = line < a.lines;
+      const V* src = S + (size_t)(ok ? line : 0) * n;
+      for (int i0 = 0; i0 < n; i0 += 32 * KB) {
+        V v[KB];
+#pragma unroll
+        for (int t = 0; t < KB; ++t) {
+          const int i = i0 + lane + 32 * t;
+          v[t] = (ok && i < n) ? src[i] : mk(zero, zero);
+        }
+#pragma unroll
+        for (int t = 0; t < KB; ++t) {
+          const int i = i0 + lane + 32 * t;
+          if (i < n) {
+            X[(size_t)(i + 1) * ld + cc] = v[t];
+            X[(size_t)(L - 1 - i) * ld + cc] = mk(-v[t].x, -v[t].y);
+          }
+        }
       }
     }
   } else {
-    for (int it = threadIdx.x; it < (n << logC); it += blockDim.x) {
-      const int cc = it & (C - 1), i = it >> logC;
-      const int line = line0 + cc;
-      V v = mk(zero, zero);
-      if (line < a.lines) v = S[((size_t)lj[cc] * n + i) * a.P + lp[cc]];
-      X[(size_t)(i + 1) * ld + cc] = v;
-      X[(size_t)(L - 1 - i) * ld + cc] = mk(-v.x, -v.y);
+    const int tot = n << logC;
+    for (int it0 = threadIdx.x; it0 < tot; it0 += KB * blockDim.x) {
+      V v[KB];
+#pragma unroll
+      for (int t = 0; t < KB; ++t) {
+        const int it = it0 + t * blockDim.x;
+        const int cc = it & (C - 1), i = it >> logC;
+        v[t] = (it < tot && line0 + cc < a.lines) ? S[((size_t)lj[cc] * n + i) * a.P + lp[cc]] : mk(zero, zero);
+      }
+#pragma unroll
+      for (int t = 0; t < KB; ++t) {
+        const int it = it0 + t * blockDim.x;
+        if (it < tot) {
+          const int cc = it & (C - 1), i = it >> logC;
+          X[(size_t)(i + 1) * ld + cc] = v[t];
+          X[(size_t)(L - 1 - i) * ld + cc] = mk(-v[t].x, -v[t].y);
+        }
+      }
     }
   }
   for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
     X[cc] = mk(zero, zero);
     X[(size_t)(n + 1) * ld + cc] = mk(zero, zero);
   }
+  if (a.op == 1) {
+    // per-line part of the divisor and the eigenvalues along this axis
+    const V* sigma = reinterpret_cast<const V*>(a.sigma);
+    for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+      V d = mk(zero, zero);
+      if (line0 + cc < a.lines) {
+        d = sigma[lj[cc]];
+        if (a.lam_other) d.x += a.lam_other[lp[cc]];
+      }
+      dcol[cc] = d;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = a.lam_axis[i];
+  }
   __syncthreads();
   fft_forward(X, ld, logC, L, tw);
 
   if (a.op == 0) {
     // D-transform only: -2i D x at frequencies 1..n, stored in natural order
-    if (a.mode == 0) {
+    const int tot = n << logC;
+    if (tot <= KR * (int)blockDim.x) {
+      // frequency p sits in row perm[p]: move rows perm[1..n] to rows 1..n through registers
+      V v[KR];
+#pragma unroll
+      for (int t = 0; t < KR; ++t) {
+        const int it = threadIdx.x + t * blockDim.x;
+        if (it < tot) v[t] = X[(size_t)perm[1 + (it >> logC)] * ld + (it & (C - 1))];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < KR; ++t) {
+        const int it = threadIdx.x + t * blockDim.x;
+        if (it < tot) X[(size_t)(1 + (it >> logC)) * ld + (it & (C - 1))] = v[t];
+      }
+      __syncthreads();
+      if (a.mode == 0) {
+        for (int cc = warp; cc < C; cc += nwarp) {
+          const int line = line0 + cc;
+          if (line >= a.lines) continue;
+          for (int i = lane; i < n; i += 32) S[(size_t)line * n + i] = X[(size_t)(i + 1) * ld + cc];
+        }
+      } else {
+        for (int it = threadIdx.x; it < tot; it += blockDim.x) {
+          const int cc = it & (C - 1), i = it >> logC;
+          if (line0 + cc < a.lines) S[((size_t)lj[cc] * n + i) * a.P + lp[cc]] = X[(size_t)(i + 1) * ld + cc];
+        }
+      }
+    } else if (a.mode == 0) {
       for (int cc = warp; cc < C; cc += nwarp) {
         const int line = line0 + cc;
         if (line >= a.lines) continue;
         for (int i = lane; i < n; i += 32) S[(size_t)line * n + i] = X[(size_t)perm[i + 1] * ld + cc];
       }
     } else {
-      for (int it = threadIdx.x; it < (n << logC); it += blockDim.x) {
+      for (int it = threadIdx.x; it < tot; it += blockDim.x) {
         const int cc = it & (C - 1), i = it >> logC;
         if (line0 + cc < a.lines)
           S[((size_t)lj[cc] * n + i) * a.P + lp[cc]] = X[(size_t)perm[i + 1] * ld + cc];
@@ -100,22 +175,24 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
   }
 
   // ---- divide by scale * (sigma_j + lambda_other + lambda_p) at frequencies p and L-p ----
-  const V* sigma = reinterpret_cast<const V*>(a.sigma);
-  for (int it = threadIdx.x; it < (L << logC); it += blockDim.x) {
-    const int cc = it & (C - 1), fq = it >> logC;
-    const int p = fq <= n + 1 ? fq : L - fq;
-    const size_t pos = (size_t)perm[fq] * ld + cc;
+  // (both rows share the divisor; frequencies 0 and n+1 are zero for an odd sequence)
+  for (int it = threadIdx.x; it < ((n + 2) << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), p = it >> logC;
+    const size_t pos = (size_t)perm[p] * ld + cc;
     if (p == 0 || p == n + 1 || line0 + cc >= a.lines) {
       X[pos] = mk(zero, zero);
+      if (p != 0 && p != n + 1) X[(size_t)perm[L - p] * ld + cc] = mk(zero, zero);
       continue;
     }
-    V d = sigma[lj[cc]];
-    d.x += a.lam_axis[p - 1];
-    if (a.lam_other) d.x += a.lam_other[lp[cc]];
+    V d = dcol[cc];
+    d.x += lam[p - 1];
     d.x *= a.scale;
     d.y *= a.scale;
     const T inv = rcp(d.x * d.x + d.y * d.y);
-    X[pos] = cmulc(X[pos], mk(d.x * inv, d.y * inv));   // X / d = X conj(d) / |d|^2
+    const V q = mk(d.x * inv, d.y * inv);
+    const size_t pos2 = (size_t)perm[L - p] * ld + cc;
+    X[pos] = cmulc(X[pos], q);   // X / d = X conj(d) / |d|^2
+    X[pos2] = cmulc(X[pos2], q);
   }
   __syncthreads();
   fft_inverse(X, ld, logC, L, tw);

@@ -105,219 +105,247 @@ __device__ __forceinline__ void load_half_spectrum(V* X, const unsigned short* p
 // K U = tau^-alpha sum_{j=0}^{min(n-1,k)} omega_j U^{n-j} + A_h U^n (BDF band, eq. (2.6) with
 // kappa = 0), or, for CQ, the precomputed Toeplitz history y plus A_h U^n.
 //
-// The tile (2C points x all N levels) is processed in chunks of kLK levels. Each chunk is
-// first staged in shared memory with asynchronous copies issued by all threads at once
-// (U with kMaxK levels of history and the two x-halo points, the two y-neighbour rows, F_hat
-// and y), then every thread evaluates residuals from shared memory only.
+// One thread owns one point of the tile and marches through a block of N/G consecutive levels
+// (G level groups per CTA). The k previous levels of its U stay in registers, so each level
+// reads U, its y neighbours, F_hat (and y) once, straight from global memory with coalesced
+// loads issued two levels ahead; x neighbours come from the adjacent lanes by warp shuffles
+// (global loads only at warp edges). The residuals go into the shared-memory tile, which is
+// then transformed along time.
+//
+// The stencil coefficients 1/hx^2, 1/hy^2 are powers of two (mx + 1, my + 1 are), so the four
+// neighbour terms are two exact double-float sums scaled exactly; only the BDF weights and the
+// stencil centre need error-free products.
 // ---------------------------------------------------------------------------
-constexpr int kLK = 16;                      // levels per staged chunk
 
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16).
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+// level groups of a residual tile: up to kThreads / 2C, each with at least 4 levels
+__host__ __device__ inline int resid_groups(int N, int C) {
+  int g = kThreads / (2 * C);
+  while (g > 1 && N / g < 4) g >>= 1;
+  return g;
 }
 
-struct ResidStage {
-  // row-major [level][point] arrays of the staged chunk
-  int W;           // 2C + 2 (U incl. x halo)
-  int P2;          // 2C
-  float* Uh;       // [kLK + kMaxK][W]
-  float* Ul;
-  float* Yh;       // [2][kLK][P2]  (row below, row above)
-  float* Yl;
-  double* F;       // [kLK][P2]
-  float* Ych;      // [kLK][P2] (CQ history, double-float) or unused
-  float* Ycl;
+size_t resid_fwd_smem(int N, int C) { return time_tile_bytes<float2>(N, C) + 16; }
+
+// one level of one point as loaded from global memory
+struct ResidLevel {
+  float uh, ul;    // U
+  float wh, wl;    // west neighbour (only where no lane holds it)
+  float eh, el;    // east neighbour (idem)
+  float sh, sl;    // south neighbour (m - mx)
+  float nh, nl;    // north neighbour (m + mx)
+  float yh, yl;    // CQ history
+  double f;        // F_hat
+  float s;         // kappa^{i/N}
 };
 
-// levels per staged chunk: at least kLK, and enough that every thread has a level
-__host__ __device__ inline int resid_chunk(int C) {
-  const int lk = kThreads / (2 * C);
-  return lk > kLK ? lk : kLK;
-}
-
-__host__ __device__ inline size_t resid_stage_bytes(int C) {
-  const size_t W = 2 * (size_t)C + 2, P2 = 2 * (size_t)C, LK = resid_chunk(C);
-  return 2 * sizeof(float) * (LK + kMaxK) * W + 2 * sizeof(float) * 2 * LK * P2 +
-         2 * sizeof(double) * LK * P2;
-}
-
-size_t resid_fwd_smem(int N, int C) { return time_tile_bytes<float2>(N, C) + resid_stage_bytes(C) + 16; }
-
-__global__ void __launch_bounds__(kThreads) k_resid_fwd(ResidFwdArgs a) {
+template <int K, bool CQ, bool TWO_D>
+__global__ void __launch_bounds__(kThreads, 3) k_resid_fwd(ResidFwdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = a.N, C = a.C, M = a.M, logC = a.logC, mx = a.mx;
   float2 *X, *tw;
   unsigned short* perm;
   time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
-  unsigned char* sp = reinterpret_cast<unsigned char*>(perm + N);
-  sp = reinterpret_cast<unsigned char*>(((size_t)sp + 15) & ~(size_t)15);
-  const int LKC = resid_chunk(C);  // levels per staged chunk
-  ResidStage st;
-  st.W = 2 * C + 2;
-  st.P2 = 2 * C;
-  st.F = reinterpret_cast<double*>(sp);
-  st.Ych = reinterpret_cast<float*>(st.F + LKC * st.P2);
-  st.Ycl = st.Ych + LKC * st.P2;
-  st.Uh = st.Ycl + LKC * st.P2;
-  st.Ul = st.Uh + (LKC + kMaxK) * st.W;
-  st.Yh = st.Ul + (LKC + kMaxK) * st.W;
-  st.Yl = st.Yh + 2 * LKC * st.P2;
 
-  const int m0 = blockIdx.x * 2 * C;
-  const int P2 = st.P2, W = st.W;
-  const int k = a.k;
-  ff cw[kMaxK + 1];
-#pragma unroll
-  for (int j = 0; j <= kMaxK; ++j) { cw[j].hi = a.c_hi[j]; cw[j].lo = a.c_lo[j]; }
-  const ff gx = {a.gx_hi, a.gx_lo}, gy = {a.gy_hi, a.gy_lo};
-  const bool two_d = a.dim == 2;
+  const int P2 = 2 * C, logP2 = logC + 1;
+  const int G = resid_groups(N, C), NL = N / G;
+  const int q = threadIdx.x & (P2 - 1), g = threadIdx.x >> logP2;
+  const int lane = threadIdx.x & 31;
+  const int m = blockIdx.x * P2 + q;
+  const bool valid = g < G && m < M;
+  constexpr bool two_d = TWO_D, cq = CQ;
+  const int xq = m % mx;
+  const bool hasW = valid && xq > 0, hasE = valid && xq < mx - 1;
+  const bool hasS = valid && two_d && m >= mx, hasN = valid && two_d && m + mx < M;
+  // x neighbours by shuffle when a warp holds 32 consecutive points of one level
+  const bool shfl = P2 >= 32;
+  const bool ldW = hasW && (!shfl || lane == 0), ldE = hasE && (!shfl || lane == 31);
+  float* Xf = reinterpret_cast<float*>(X) + 2 * (q & (C - 1)) + (q >= C ? 1 : 0);
 
-  // Each thread keeps one point q of the tile (2C divides the block size) and walks levels.
-  const int logP2 = logC + 1;
-  const int q = threadIdx.x & (P2 - 1);
-  const int lstep = blockDim.x >> logP2;
-  const int mq = m0 + q;
-  const bool qvalid = mq < M;
-  const int xq = qvalid ? mq % mx : 0;
-  for (int c0 = 0; c0 < N; c0 += LKC) {
-    const int LK = min(LKC, N - c0);
-    // ---- stage chunk levels [c0, c0 + LK) (+ kMaxK levels of history for U) ----
-    {
-      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-      for (int l = warp; l < LKC + kMaxK; l += nwarp) {
-        const int lev = c0 - kMaxK + l;
-        const bool lok = lev >= 0 && lev < N;
-        const size_t grow = (size_t)(lok ? lev : 0) * M;
-        for (int qq = lane; qq < W; qq += 32) {
-          const int m = m0 - 1 + qq;
-          float* dh = st.Uh + l * W + qq;
-          float* dl = st.Ul + l * W + qq;
-          if (lok && m >= 0 && m < M) {
-            cp_async4(dh, a.Uhi + grow + m);
-            cp_async4(dl, a.Ulo + grow + m);
-          } else {
-            *dh = 0.f;
-            *dl = 0.f;
-          }
-        }
-      }
+  auto load = [&](int i) {
+    ResidLevel v;
+    const size_t idx = (size_t)i * M + m;
+    v.uh = valid ? a.Uhi[idx] : 0.f;
+    v.ul = valid ? a.Ulo[idx] : 0.f;
+    v.wh = ldW ? a.Uhi[idx - 1] : 0.f;
+    v.wl = ldW ? a.Ulo[idx - 1] : 0.f;
+    v.eh = ldE ? a.Uhi[idx + 1] : 0.f;
+    v.el = ldE ? a.Ulo[idx + 1] : 0.f;
+    if (two_d) {
+      v.sh = hasS ? a.Uhi[idx - mx] : 0.f;
+      v.sl = hasS ? a.Ulo[idx - mx] : 0.f;
+      v.nh = hasN ? a.Uhi[idx + mx] : 0.f;
+      v.nl = hasN ? a.Ulo[idx + mx] : 0.f;
+    } else {
+      v.sh = v.sl = v.nh = v.nl = 0.f;
     }
-    for (int l = threadIdx.x >> logP2; l < LK; l += lstep) {
-      const int e = (l << logP2) + q;
-      const size_t g = (size_t)(c0 + l) * M + mq;
-      if (qvalid) {
-        cp_async8(st.F + e, a.F + g);
-        if (a.yhi) {
-          cp_async4(st.Ych + e, a.yhi + g);
-          cp_async4(st.Ycl + e, a.ylo + g);
-        }
-      }
-      if (two_d) {
-        float* bh = st.Yh + e;
-        float* bl = st.Yl + e;
-        float* ah = st.Yh + LKC * P2 + e;
-        float* al = st.Yl + LKC * P2 + e;
-        if (qvalid && mq >= mx) { cp_async4(bh, a.Uhi + g - mx); cp_async4(bl, a.Ulo + g - mx); }
-        else { *bh = 0.f; *bl = 0.f; }
-        if (mq + mx < M) { cp_async4(ah, a.Uhi + g + mx); cp_async4(al, a.Ulo + g + mx); }
-        else { *ah = 0.f; *al = 0.f; }
-      }
+    if (cq) {
+      v.yh = valid ? a.yhi[idx] : 0.f;
+      v.yl = valid ? a.ylo[idx] : 0.f;
+    } else {
+      v.yh = 0.f;
+      v.yl = 0.f;
     }
-    cp_async_wait_all();
-    __syncthreads();
-    // ---- residuals of the chunk from shared memory ----
-    for (int l = threadIdx.x >> logP2; l < LK; l += lstep) {
-      const int e = (l << logP2) + q;
-      const int i = c0 + l;
-      float r = 0.f;
-      if (qvalid) {
-        const int ub = (l + kMaxK) * W + q + 1;  // this point in the U stage
-        ff_acc acc;
-        acc.init(ff_from_double(st.F[e]));
-        if (a.yhi) acc.sub(ff{st.Ych[e], st.Ycl[e]});
-        acc.fma_term(cw[0], ff{st.Uh[ub], st.Ul[ub]}, -1.f);
+    v.f = valid ? a.F[idx] : 0.0;
+    v.s = __ldg(a.s + i);
+    return v;
+  };
+
+  if (g < G) {
+    const int i0 = g * NL, i1 = i0 + NL;
+    // U of the K levels before i0 (zero before level 0)
+    ff h[K > 0 ? K : 1];
 #pragma unroll
-        for (int j = 1; j <= kMaxK; ++j)
-          if (j <= k) acc.fma_term(cw[j], ff{st.Uh[ub - j * W], st.Ul[ub - j * W]}, -1.f);
-        if (xq > 0) acc.fma_term(gx, ff{st.Uh[ub - 1], st.Ul[ub - 1]}, 1.f);
-        if (xq < mx - 1) acc.fma_term(gx, ff{st.Uh[ub + 1], st.Ul[ub + 1]}, 1.f);
-        if (two_d) {
-          acc.fma_term(gy, ff{st.Yh[e], st.Yl[e]}, 1.f);
-          acc.fma_term(gy, ff{st.Yh[LKC * P2 + e], st.Yl[LKC * P2 + e]}, 1.f);
-        }
-        r = acc.value() * __ldg(a.s + i);
-      }
-      float* xs = reinterpret_cast<float*>(X + (size_t)i * C + (q & (C - 1)));
-      xs[q >= C ? 1 : 0] = r;
+    for (int t = 0; t < K; ++t) {
+      const int lev = i0 - 1 - t;
+      h[t].hi = (valid && lev >= 0) ? a.Uhi[(size_t)lev * M + m] : 0.f;
+      h[t].lo = (valid && lev >= 0) ? a.Ulo[(size_t)lev * M + m] : 0.f;
     }
-    __syncthreads();  // the stage is reused by the next chunk
+    const float gx = a.gx_hi, gy = a.gy_hi;
+    ResidLevel nx0 = load(i0), nx1 = load(i0 + 1 < i1 ? i0 + 1 : i0);
+#pragma unroll 2
+    for (int i = i0; i < i1; ++i) {
+      const ResidLevel c = nx0;
+      nx0 = nx1;
+      if (i + 2 < i1) nx1 = load(i + 2);
+
+      // x neighbours: adjacent lanes, or the global loads at warp edges
+      // (shfl is uniform over the CTA and then every warp is fully inside one level group)
+      float wh = c.wh, wl = c.wl, eh = c.eh, el = c.el;
+      if (shfl) {
+        const float uwh = __shfl_up_sync(0xffffffffu, c.uh, 1), uwl = __shfl_up_sync(0xffffffffu, c.ul, 1);
+        const float ueh = __shfl_down_sync(0xffffffffu, c.uh, 1), uel = __shfl_down_sync(0xffffffffu, c.ul, 1);
+        if (lane != 0) { wh = uwh; wl = uwl; }
+        if (lane != 31) { eh = ueh; el = uel; }
+      }
+      if (!hasW) { wh = 0.f; wl = 0.f; }
+      if (!hasE) { eh = 0.f; el = 0.f; }
+
+      // stencil centre, BDF history (and CQ history): error-free products
+      ff_acc A;
+      A.init(ff_from_double(c.f));
+      if constexpr (CQ) A.sub(ff{c.yh, c.yl});
+      A.fma_term(ff{a.c_hi[0], a.c_lo[0]}, ff{c.uh, c.ul}, -1.f);
+#pragma unroll
+      for (int t = 1; t <= K; ++t) A.fma_term(ff{a.c_hi[t], a.c_lo[t]}, h[t - 1], -1.f);
+      // neighbours: exact sums, exact power-of-two scaling
+      float bx, ex;
+      two_sum(wh, eh, bx, ex);
+      A.add_hi(gx * bx);
+      float lo = gx * (ex + (wl + el));
+      if constexpr (TWO_D) {
+        float by, ey;
+        two_sum(c.sh, c.nh, by, ey);
+        A.add_hi(gy * by);
+        lo = fmaf(gy, ey + (c.sl + c.nl), lo);
+      }
+      A.sl += lo;
+      Xf[(size_t)2 * i * C] = valid ? A.value() * c.s : 0.f;
+
+#pragma unroll
+      for (int t = K - 1; t > 0; --t) h[t] = h[t - 1];
+      if (K > 0) h[0] = ff{c.uh, c.ul};
+    }
   }
+  __syncthreads();
   fft_forward(X, C, logC, N, tw);
-  store_half_spectrum(X, perm, a.S, N, M, C, logC, m0);
+  store_half_spectrum(X, perm, a.S, N, M, C, logC, (int)blockIdx.x * P2);
 }
 
 // ---------------------------------------------------------------------------
 // MIXED: inverse DFT + unscale + U += c (double-float) + norms
 // ---------------------------------------------------------------------------
-size_t inv_upd_smem(int N, int C) { return time_tile_bytes<float2>(N, C); }
+size_t inv_upd_smem(int N, int C) {
+  return time_tile_bytes<float2>(N, C) + 16 + 2 * sizeof(float2) * (size_t)C;
+}
 
-__global__ void __launch_bounds__(kThreads) k_inv_upd(InvUpdArgs a) {
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = a.N, C = a.C, M = a.M, logC = a.logC;
   float2 *X, *tw;
   unsigned short* perm;
   time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
+  float2* B0 = reinterpret_cast<float2*>(((size_t)(perm + N) + 15) & ~(size_t)15);  // [2][C]
   const int m0 = blockIdx.x * 2 * C;
-  {
-    // the update reads this tile's rows of U after the inverse FFT: start pulling them into L2
-    // now. Each span is rounded out to 16-byte boundaries and clipped to the array.
-    const size_t total = (size_t)N * M;
-    const int p1 = min(m0 + 2 * C, M);
-    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
-      const float* base = (i & 1) ? a.Ulo : a.Uhi;
-      const size_t b0 = ((size_t)(i >> 1) * M + m0) & ~(size_t)3;
-      size_t b1 = ((size_t)(i >> 1) * M + p1 + 3) & ~(size_t)3;
-      if (b1 > (total & ~(size_t)3)) b1 = total & ~(size_t)3;
-      if (b1 > b0) prefetch_l2(base + b0, (unsigned)((b1 - b0) * 4));
+  const int J = N / 2 + 1;
+  __syncthreads();  // perm
+  // Half spectra straight into the FFT's permuted rows with asynchronous copies, all in flight
+  // at once: A_j (real-part point) into row perm[j], B_j (imaginary-part point) into row
+  // perm[N-j]; B_0 and B_{N/2}, whose partner rows are their own, into B0.
+  for (int it = threadIdx.x; it < (J << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), j = it >> logC;
+    const int ma = m0 + cc, mb = m0 + C + cc;
+    float2* da = X + (size_t)perm[j] * C + cc;
+    float2* db = (j == 0 || j == N / 2) ? B0 + (j == 0 ? 0 : C) + cc : X + (size_t)perm[N - j] * C + cc;
+    if (ma < M) cp_async8(da, a.S + (size_t)j * M + ma);
+    else *da = make_float2(0.f, 0.f);
+    if (mb < M) cp_async8(db, a.S + (size_t)j * M + mb);
+    else *db = make_float2(0.f, 0.f);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // Z_j = A_j + i B_j and Z_{N-j} = conj(A_j) + i conj(B_j), each pair by one thread
+  for (int it = threadIdx.x; it < (J << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), j = it >> logC;
+    float2* pa = X + (size_t)perm[j] * C + cc;
+    const float2 A = *pa;
+    if (j == 0 || j == N / 2) {
+      const float2 B = B0[(j == 0 ? 0 : C) + cc];
+      *pa = make_float2(A.x - B.y, A.y + B.x);
+    } else {
+      float2* pb = X + (size_t)perm[N - j] * C + cc;
+      const float2 B = *pb;
+      *pa = make_float2(A.x - B.y, A.y + B.x);
+      *pb = make_float2(A.x + B.y, B.x - A.y);
     }
   }
   __syncthreads();
-  load_half_spectrum(X, perm, a.S, N, M, C, logC, m0);
-  __syncthreads();
   fft_inverse(X, C, logC, N, tw);
 
+  // U += c: the loads of UB items are issued together before any store (the stores go to the
+  // same arrays, so the compiler could not move later loads above them)
+  constexpr int UB = 8;
   float sc = 0.f, su = 0.f;  // per-thread partial norms (FP32: the FP64 pipe is ~1/70 rate)
-#pragma unroll 4
-  for (int it = threadIdx.x; it < (N << logC); it += blockDim.x) {
-    const int cc = it & (C - 1), i = it >> logC;
-    const float2 z = X[(size_t)i * C + cc];
-    const float is = __ldg(a.inv_s + i);
+  const int tot = N << logC;
+  for (int it0 = threadIdx.x; it0 < tot; it0 += UB * blockDim.x) {
+    float uh[UB][2], ul[UB][2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int m = m0 + h * C + cc;
-      if (m >= M) continue;
-      const float cval = (h ? z.y : z.x) * is;
-      const size_t idx = (size_t)i * M + m;
-      ff u = {a.Uhi[idx], a.Ulo[idx]};
-      u = ff_add_f(u, cval);
-      a.Uhi[idx] = u.hi;
-      a.Ulo[idx] = u.lo;
-      sc = fmaf(cval, cval, sc);
-      su = fmaf(u.hi, u.hi, su);
+    for (int t = 0; t < UB; ++t) {
+      const int it = it0 + t * blockDim.x;
+      const int cc = it & (C - 1), i = it >> logC;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = m0 + h * C + cc;
+        const bool ok = it < tot && m < M;
+        const size_t idx = (size_t)i * M + m;
+        uh[t][h] = ok ? a.Uhi[idx] : 0.f;
+        ul[t][h] = ok ? a.Ulo[idx] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < UB; ++t) {
+      const int it = it0 + t * blockDim.x;
+      if (it >= tot) break;
+      const int cc = it & (C - 1), i = it >> logC;
+      const float2 z = X[(size_t)i * C + cc];
+      const float is = __ldg(a.inv_s + i);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = m0 + h * C + cc;
+        if (m >= M) continue;
+        const float cval = (h ? z.y : z.x) * is;
+        const size_t idx = (size_t)i * M + m;
+        const ff u = ff_add_f(ff{uh[t][h], ul[t][h]}, cval);
+        a.Uhi[idx] = u.hi;
+        a.Ulo[idx] = u.lo;
+        sc = fmaf(cval, cval, sc);
+        su = fmaf(u.hi, u.hi, su);
+      }
     }
   }
   block_reduce_add2((double)sc, (double)su, a.norms);
@@ -492,65 +520,124 @@ __global__ void __launch_bounds__(kThreads) k_toeplitz_ff(ToepFFArgs a) {
 // Right-hand side: F_hat_n = f(t_n) + a_n (f(0) - A v) + sum_l b_{l,n} tau^l d^l f(0)
 //                            + tau^-alpha sum_{j<n} omega_j v        (eq. (2.1), (2.7), (3.7), (3.12))
 // ---------------------------------------------------------------------------
+// grid: x over points (one thread per point m), y over slices of consecutive levels
 __global__ void k_rhs(RhsArgs a) {
-  const size_t total = (size_t)a.N * a.M;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / a.M);
-    const int m = (int)(t - (size_t)i * a.M);
-    const double vm = a.v[m];
-    double F = fma(a.beta[i], vm, a.f[t]);
-    if (i < a.k - 1) {
-      const int x = m % a.mx;
-      double Av = 2.0 * a.gx * vm;
-      if (x > 0) Av -= a.gx * a.v[m - 1];
-      if (x < a.mx - 1) Av -= a.gx * a.v[m + 1];
-      if (a.dim == 2) {
-        Av += 2.0 * a.gy * vm;
-        if (m >= a.mx) Av -= a.gy * a.v[m - a.mx];
-        if (m + a.mx < a.M) Av -= a.gy * a.v[m + a.mx];
-      }
-      F += a.a[i] * (a.fd[m] - Av);
-      for (int l = 1; l <= a.k - 2; ++l) F += a.bt[l][i] * a.fd[(size_t)l * a.M + m];
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= a.M) return;
+  const int per = (a.N + gridDim.y - 1) / gridDim.y;
+  const int i0 = blockIdx.y * per, i1 = min(a.N, i0 + per);
+  const double vm = a.v[m];
+  double Av = 0.0;
+  if (i0 < a.k - 1) {
+    const int x = m % a.mx;
+    Av = 2.0 * a.gx * vm;
+    if (x > 0) Av -= a.gx * a.v[m - 1];
+    if (x < a.mx - 1) Av -= a.gx * a.v[m + 1];
+    if (a.dim == 2) {
+      Av += 2.0 * a.gy * vm;
+      if (m >= a.mx) Av -= a.gy * a.v[m - a.mx];
+      if (m + a.mx < a.M) Av -= a.gy * a.v[m + a.mx];
     }
-    a.F[t] = F;
+  }
+  constexpr int B = 4;
+  for (int ib = i0; ib < i1; ib += B) {
+    double f[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) f[b] = ib + b < i1 ? a.f[(size_t)(ib + b) * a.M + m] : 0.0;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int i = ib + b;
+      if (i >= i1) break;
+      double F = fma(a.beta[i], vm, f[b]);
+      if (i < a.k - 1) {
+        F += a.a[i] * (a.fd[m] - Av);
+        for (int l = 1; l <= a.k - 2; ++l) F += a.bt[l][i] * a.fd[(size_t)l * a.M + m];
+      }
+      a.F[(size_t)i * a.M + m] = F;
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // conversions (integer bit manipulation; see ff.cuh)
 // ---------------------------------------------------------------------------
-__global__ void k_d2ff(const double* x, float* hi, float* lo, size_t n) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const ff r = ff_from_double(x[t]);
-    hi[t] = r.hi;
-    lo[t] = r.lo;
+__global__ void k_d2ff(const double* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
+  constexpr int B = 4;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t0 < n; t0 += B * stride) {
+    double v[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) v[b] = t0 + b * stride < n ? x[t0 + b * stride] : 0.0;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const size_t t = t0 + b * stride;
+      if (t < n) {
+        const ff r = ff_from_double(v[b]);
+        hi[t] = r.hi;
+        lo[t] = r.lo;
+      }
+    }
   }
 }
+// grid: x over points, y over slices of levels; U^n = v for every level n
 __global__ void k_bcast_d2ff(const double* v, float* hi, float* lo, int N, int M) {
-  const size_t total = (size_t)N * M;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const ff r = ff_from_double(v[t % M]);
-    hi[t] = r.hi;
-    lo[t] = r.lo;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int per = (N + gridDim.y - 1) / gridDim.y;
+  const int i0 = blockIdx.y * per, i1 = min(N, i0 + per);
+  const ff r = ff_from_double(v[m]);
+  for (int i = i0; i < i1; ++i) {
+    hi[(size_t)i * M + m] = r.hi;
+    lo[(size_t)i * M + m] = r.lo;
   }
 }
 __global__ void k_bcast_d(const double* v, double* U, int N, int M) {
-  const size_t total = (size_t)N * M;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x)
-    U[t] = v[t % M];
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int per = (N + gridDim.y - 1) / gridDim.y;
+  const int i0 = blockIdx.y * per, i1 = min(N, i0 + per);
+  const double vm = v[m];
+  for (int i = i0; i < i1; ++i) U[(size_t)i * M + m] = vm;
 }
-__global__ void k_ff2d(const float* hi, const float* lo, double* x, size_t n) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-    x[t] = ff_to_double(ff{hi[t], lo[t]});
+__global__ void k_ff2d(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ x, size_t n) {
+  constexpr int B = 4;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t0 < n; t0 += B * stride) {
+    float h[B], l[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const size_t t = t0 + b * stride;
+      h[b] = t < n ? hi[t] : 0.f;
+      l[b] = t < n ? lo[t] : 0.f;
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+      if (t0 + b * stride < n) x[t0 + b * stride] = ff_to_double(ff{h[b], l[b]});
+  }
 }
-__global__ void k_d2f(const double* x, float* y, size_t n) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-    y[t] = ff_from_double(x[t]).hi;
+__global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, size_t n) {
+  constexpr int B = 4;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t0 < n; t0 += B * stride) {
+    double v[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) v[b] = t0 + b * stride < n ? x[t0 + b * stride] : 0.0;
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+      if (t0 + b * stride < n) y[t0 + b * stride] = ff_from_double(v[b]).hi;
+  }
 }
-__global__ void k_f2d(const float* x, double* y, size_t n) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-    y[t] = f2d_bits(x[t]);
+__global__ void k_f2d(const float* __restrict__ x, double* __restrict__ y, size_t n) {
+  constexpr int B = 4;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t0 < n; t0 += B * stride) {
+    float v[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) v[b] = t0 + b * stride < n ? x[t0 + b * stride] : 0.f;
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+      if (t0 + b * stride < n) y[t0 + b * stride] = f2d_bits(v[b]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -595,6 +682,15 @@ cudaError_t launch_converge(const double* norms, SolveCtl* ctl, cudaGraphConditi
   return cudaGetLastError();
 }
 
+// points along x (one thread each), slices of levels along y: about 8 CTAs per SM in total
+static dim3 grid_pts(int M, int N) {
+  const int bx = (M + kThreads - 1) / kThreads;
+  int by = (152 * 8 + bx - 1) / bx;
+  if (by > N) by = N;
+  if (by < 1) by = 1;
+  return dim3((unsigned)bx, (unsigned)by, 1);
+}
+
 static int grid_for(size_t n) {
   size_t b = (n + kThreads - 1) / kThreads;
   if (b > 152 * 16) b = 152 * 16;
@@ -610,14 +706,34 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 
 static int tiles(int M, int C) { return (M + 2 * C - 1) / (2 * C); }
 
-cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st) {
-  const size_t sm = resid_fwd_smem(a.N, a.C);
-  cudaError_t e = set_smem(k_resid_fwd, sm);
+template <int K, bool CQ, bool TWO_D>
+static cudaError_t launch_resid_k(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
+  cudaError_t e = set_smem(k_resid_fwd<K, CQ, TWO_D>, sm);
   if (e != cudaSuccess) return e;
   prof_begin("resid_fwd_ff", st);
-  k_resid_fwd<<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
+  k_resid_fwd<K, CQ, TWO_D><<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
+}
+
+template <bool TWO_D> static cudaError_t launch_resid_d(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
+  if (a.yhi) return a.k == 0 ? launch_resid_k<0, true, TWO_D>(a, sm, st) : cudaErrorInvalidValue;
+  switch (a.k) {
+    case 1: return launch_resid_k<1, false, TWO_D>(a, sm, st);
+    case 2: return launch_resid_k<2, false, TWO_D>(a, sm, st);
+    case 3: return launch_resid_k<3, false, TWO_D>(a, sm, st);
+    case 4: return launch_resid_k<4, false, TWO_D>(a, sm, st);
+    case 5: return launch_resid_k<5, false, TWO_D>(a, sm, st);
+    case 6: return launch_resid_k<6, false, TWO_D>(a, sm, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st) {
+  // the neighbour terms assume exact power-of-two stencil coefficients
+  if (a.gx_lo != 0.f || a.gy_lo != 0.f) return cudaErrorInvalidValue;
+  const size_t sm = resid_fwd_smem(a.N, a.C);
+  return a.dim == 2 ? launch_resid_d<true>(a, sm, st) : launch_resid_d<false>(a, sm, st);
 }
 
 cudaError_t launch_inv_upd(const InvUpdArgs& a, cudaStream_t st) {
@@ -672,7 +788,7 @@ cudaError_t launch_toeplitz_ff(const ToepFFArgs& a, cudaStream_t st) {
 
 cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t st) {
   prof_begin("rhs_f64", st);
-  k_rhs<<<grid_for((size_t)a.N * a.M), kThreads, 0, st>>>(a);
+  k_rhs<<<grid_pts(a.M, a.N), kThreads, 0, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
 }
@@ -685,13 +801,13 @@ cudaError_t launch_d2ff(const double* x, float* hi, float* lo, size_t n, cudaStr
 }
 cudaError_t launch_bcast_d2ff(const double* v, float* hi, float* lo, int N, int M, cudaStream_t st) {
   prof_begin("cvt_bcast_d2ff", st);
-  k_bcast_d2ff<<<grid_for((size_t)N * M), kThreads, 0, st>>>(v, hi, lo, N, M);
+  k_bcast_d2ff<<<grid_pts(M, N), kThreads, 0, st>>>(v, hi, lo, N, M);
   prof_end(st);
   return cudaGetLastError();
 }
 cudaError_t launch_bcast_d(const double* v, double* U, int N, int M, cudaStream_t st) {
   prof_begin("initial_guess", st);
-  k_bcast_d<<<grid_for((size_t)N * M), kThreads, 0, st>>>(v, U, N, M);
+  k_bcast_d<<<grid_pts(M, N), kThreads, 0, st>>>(v, U, N, M);
   prof_end(st);
   return cudaGetLastError();
 }

@@ -475,12 +475,14 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   int occ = 1;
   while (occ < 32 && (size_t)M / (size_t)(4 * occ) >= 2 * 152) occ *= 2;
   p->Ct = std::min(pick_cols((size_t)N * sizeof(float2), budget, 32, 1), occ);
+  p->Cr = std::min(p->Ct, 16);
   p->Ctd = std::min(pick_cols((size_t)N * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2)), budget, 32, 1), occ);
   p->Cz = std::min(pick_cols((size_t)2 * N * sizeof(double2), 160 * 1024, 16, 1), occ);
   const size_t ve = p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2);
-  // sine-transform tiles: ~40 KB of lines so that several CTAs share an SM
-  p->Cx = pick_cols((size_t)2 * (p->mx + 1) * ve, 40 * 1024, 16, 1);
-  p->Cy = pick_cols((size_t)2 * (p->my + 1) * ve, 40 * 1024, 16, 1);
+  // sine-transform tiles: up to 64 KB of extended lines (16 lines of 512 FP32 complex points),
+  // three CTAs per SM
+  p->Cx = pick_cols((size_t)2 * (p->mx + 1) * ve, 64 * 1024, 16, 1);
+  p->Cy = pick_cols((size_t)2 * (p->my + 1) * ve, 64 * 1024, 16, 1);
   p->Ctri = pick_cols((size_t)p->my * sizeof(float2), 72 * 1024, 32, 1);
   PINT_CUDA_B(cudaMemset(p->S, 0, JM * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2))));
   p->ysolve = 1;
@@ -673,7 +675,7 @@ pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   r.ylo = p->cq ? ylo : nullptr;
   r.S = reinterpret_cast<float2*>(p->S);
   r.s = p->tf.s; r.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
-  r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Ct; r.logC = ilog2c(p->Ct);
+  r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Cr; r.logC = ilog2c(p->Cr);
   const double ta = std::pow(p->tau, -p->alpha);
   double c0 = 2.0 * p->gx + 2.0 * p->gy;
   if (!p->cq) {

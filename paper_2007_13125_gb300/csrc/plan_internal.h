@@ -80,7 +80,7 @@ struct pint_plan_s {
   cudaStream_t cap = nullptr;       // stream used to capture graphs
   pint::SolveGraph sg;
   // tiles
-  int Ct, Ctd, Cz, Cx, Cy, Ctri;    // columns per CTA: time (float), time (T), toeplitz, x, y, tri
+  int Ct, Cr, Ctd, Cz, Cx, Cy, Ctri;  // columns per CTA: time (float), residual, time (T), toeplitz, x, y, tri
   int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal
   double q_floor;                   // predicted floor of the per-sweep contraction (inner precision)
 };
