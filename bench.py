@@ -78,37 +78,48 @@ def traffic_for(name: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+
+    The sampler is started (and its first sample awaited) before the warm-up, so that starting
+    nvidia-smi does not fall inside the timed region; every line is stamped with the host time
+    at which it arrived and stop(t0, t1) keeps the samples of [t0, t1] (the nearest one when the
+    region is shorter than the sampling interval)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
         self.thread = None
+        self.ready = threading.Event()
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        self.ready.wait(wait_s)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+            self.ready.set()
 
-    def stop(self) -> dict:
+    def stop(self, t0: float, t1: float) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        lag = 2 * self.INTERVAL_MS / 1000.0
+        time.sleep(lag)  # the sample covering t1 arrives a little later
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -116,9 +127,15 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
+        inside = [ln for t, ln in self.lines if t0 <= t <= t1 + lag]
+        where = "timed region"
+        if not inside and self.lines:
+            t_mid = 0.5 * (t0 + t1)
+            inside = [min(self.lines, key=lambda tl: abs(tl[0] - t_mid))[1]]
+            where = "nearest sample to the timed region"
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in inside:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -132,7 +149,7 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": where}
 
 
 def dist_env():
@@ -419,13 +436,14 @@ def main():
     # ---- main timed region: MIXED path (one graph launch per solve), clocks sampled ----
     if args.per_sweep_launches:
         pint.set_profiling(True)
+    clk = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clk.start()
     for _ in range(args.warmup):
         step("mixed")
     barrier()
-    clk = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
-    clk.start()
+    t_clk0 = time.monotonic()
     ms_mixed, lat_mixed = timed("mixed", args.steps, 0, per_step=True)
-    clocks = clk.stop()
+    clocks = clk.stop(t_clk0, time.monotonic())
     # our kernels per solve: form_rhs, initial guess, conversion in/out, sweeps x (sweep kernels +
     # the device-side convergence check), control init
     sweeps_main = last["mixed"][0]

@@ -244,4 +244,76 @@ __device__ void fft_inverse(V* X, int ld, int logC, int L, const V* tw) {
   }
 }
 
+// ---- compile-time variant: L = 2^LOGL, C = 2^LOGC columns, pitch LD, all known to the
+// compiler, so every shared-memory address is a base register plus an immediate and the
+// twiddle indices need no masks. Same radix schedule (and output order) as above.
+__host__ __device__ constexpr int ct_npass(int logL, int maxlog) { return (logL + maxlog - 1) / maxlog; }
+__host__ __device__ constexpr int ct_logradix(int logL, int pass, int maxlog) {
+  return logL / ct_npass(logL, maxlog) + (pass < logL % ct_npass(logL, maxlog) ? 1 : 0);
+}
+
+template <int LR, int DIR, int LOGL, int LOGLS, int LOGC, int LD, typename V>
+__device__ __forceinline__ void fft_pass_ct(V* X, const V* tw) {
+  constexpr int R = 1 << LR, LOGS = LOGLS - LR, S = 1 << LOGS, C = 1 << LOGC;
+  constexpr int ITEMS = 1 << (LOGL - LR + LOGC);
+  constexpr int TSHIFT = LOGL - LOGLS;  // W_Ls^e = W_L^{e << TSHIFT}
+  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
+    const int c = it & (C - 1);
+    const int g = it >> LOGC;
+    const int n2 = g & (S - 1);
+    const int base = ((g >> LOGS) << LOGLS) + n2;
+    V* p = X + base * LD + c;
+    V x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = p[r * S * LD];
+    if constexpr (DIR < 0) {
+      dft_reg<R, -1>(x);
+      if constexpr (S > 1) {
+        const V* w = tw + (n2 << TSHIFT);
+#pragma unroll
+        for (int q = 1; q < R; ++q) x[q] = cmul(x[q], w[(q - 1) * (n2 << TSHIFT)]);
+      }
+    } else {
+      if constexpr (S > 1) {
+        const V* w = tw + (n2 << TSHIFT);
+#pragma unroll
+        for (int q = 1; q < R; ++q) x[q] = cmulc(x[q], w[(q - 1) * (n2 << TSHIFT)]);
+      }
+      dft_reg<R, 1>(x);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) p[r * S * LD] = x[r];
+  }
+}
+
+template <int P, int NP, int LOGL, int LOGLS, int LOGC, int LD, int MAXLOG, typename V>
+__device__ __forceinline__ void fft_forward_ct_rec(V* X, const V* tw) {
+  if constexpr (P < NP) {
+    constexpr int LR = ct_logradix(LOGL, P, MAXLOG);
+    fft_pass_ct<LR, -1, LOGL, LOGLS, LOGC, LD>(X, tw);
+    __syncthreads();
+    fft_forward_ct_rec<P + 1, NP, LOGL, LOGLS - LR, LOGC, LD, MAXLOG>(X, tw);
+  }
+}
+
+template <int P, int LOGL, int LOGLS, int LOGC, int LD, int MAXLOG, typename V>
+__device__ __forceinline__ void fft_inverse_ct_rec(V* X, const V* tw) {
+  if constexpr (P >= 0) {
+    constexpr int LR = ct_logradix(LOGL, P, MAXLOG);
+    fft_pass_ct<LR, 1, LOGL, LOGLS + LR, LOGC, LD>(X, tw);
+    __syncthreads();
+    fft_inverse_ct_rec<P - 1, LOGL, LOGLS + LR, LOGC, LD, MAXLOG>(X, tw);
+  }
+}
+
+// Same contracts as fft_forward / fft_inverse.
+template <int LOGL, int LOGC, int LD, int MAXLOG = 4, typename V>
+__device__ void fft_forward_ct(V* X, const V* tw) {
+  fft_forward_ct_rec<0, ct_npass(LOGL, MAXLOG), LOGL, LOGL, LOGC, LD, MAXLOG>(X, tw);
+}
+template <int LOGL, int LOGC, int LD, int MAXLOG = 4, typename V>
+__device__ void fft_inverse_ct(V* X, const V* tw) {
+  fft_inverse_ct_rec<ct_npass(LOGL, MAXLOG) - 1, LOGL, 0, LOGC, LD, MAXLOG>(X, tw);
+}
+
 }  // namespace pint

@@ -35,13 +35,18 @@ template <typename T> size_t axis_smem(int n, int C) {
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
-template <typename T>
+// LOGL > 0: compiled for lines of L = 2^LOGL extended points in tiles of 2^LOGC lines (the
+// shapes of the usual grids); LOGL = 0: any shape, taken from the arguments.
+template <typename T, int LOGL, int LOGC>
 __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
   using V = typename c2<T>::t;
   constexpr int KR = axis_regs<T>();  // register slots per thread for the reordering
   constexpr int KB = 8;               // global loads in flight per thread
+  constexpr bool CT = LOGL > 0;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int n = a.n, C = a.C, logC = a.logC, ld = a.ld, L = 2 * (a.n + 1);
+  const int n = CT ? (1 << (LOGL - 1)) - 1 : a.n;
+  const int C = CT ? (1 << LOGC) : a.C, logC = CT ? LOGC : a.logC, ld = CT ? (1 << LOGC) + 1 : a.ld;
+  const int L = 2 * (n + 1);
   V* X = reinterpret_cast<V*>(smraw);
   V* tw = X + (size_t)L * ld;
   V* dcol = tw + L;                                      // line -> sigma_j + lambda_other (op 1)
@@ -126,7 +131,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = a.lam_axis[i];
   }
   __syncthreads();
-  fft_forward(X, ld, logC, L, tw);
+  if constexpr (CT) fft_forward_ct<LOGL, LOGC, (1 << LOGC) + 1>(X, tw);
+  else fft_forward(X, ld, logC, L, tw);
 
   if (a.op == 0) {
     // D-transform only: -2i D x at frequencies 1..n, stored in natural order
@@ -195,7 +201,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
     X[pos2] = cmulc(X[pos2], q);
   }
   __syncthreads();
-  fft_inverse(X, ld, logC, L, tw);
+  if constexpr (CT) fft_inverse_ct<LOGL, LOGC, (1 << LOGC) + 1>(X, tw);
+  else fft_inverse(X, ld, logC, L, tw);
 
   if (a.mode == 0) {
     for (int cc = warp; cc < C; cc += nwarp) {
@@ -211,19 +218,36 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
   }
 }
 
-template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t st) {
-  const size_t sm = axis_smem<T>(a.n, a.C);
+template <typename T, int LOGL, int LOGC>
+static cudaError_t launch_axis_k(const AxisArgs<T>& a, size_t sm, cudaStream_t st) {
   if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_axis<T, LOGL, LOGC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
   const int blocks = (a.lines + a.C - 1) / a.C;
   const char* name = a.op == 0 ? (sizeof(T) == 8 ? "dst_f64" : "dst_f32")
                                : (sizeof(T) == 8 ? "axis_solve_f64" : "axis_solve_f32");
   prof_begin(name, st);
-  k_axis<T><<<blocks, kThreads, sm, st>>>(a);
+  k_axis<T, LOGL, LOGC><<<blocks, kThreads, sm, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t st) {
+  const size_t sm = axis_smem<T>(a.n, a.C);
+  if constexpr (sizeof(T) == 4) {
+    // compiled shapes: n = 2^q - 1 with the tile widths the plan picks for them
+    const int L = 2 * (a.n + 1);
+    if (a.ld == a.C + 1) {
+      if (L == 128 && a.C == 16) return launch_axis_k<T, 7, 4>(a, sm, st);
+      if (L == 256 && a.C == 16) return launch_axis_k<T, 8, 4>(a, sm, st);
+      if (L == 512 && a.C == 16) return launch_axis_k<T, 9, 4>(a, sm, st);
+      if (L == 1024 && a.C == 8) return launch_axis_k<T, 10, 3>(a, sm, st);
+      if (L == 2048 && a.C == 4) return launch_axis_k<T, 11, 2>(a, sm, st);
+      if (L == 4096 && a.C == 2) return launch_axis_k<T, 12, 1>(a, sm, st);
+    }
+  }
+  return launch_axis_k<T, 0, 0>(a, sm, st);
 }
 
 // ---------------------------------------------------------------------------
