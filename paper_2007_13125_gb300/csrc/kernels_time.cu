@@ -254,30 +254,87 @@ __global__ void __launch_bounds__(kThreads, 3) k_resid_fwd(ResidFwdArgs a) {
 // ---------------------------------------------------------------------------
 // MIXED: inverse DFT + unscale + U += c (double-float) + norms
 // ---------------------------------------------------------------------------
-size_t inv_upd_smem(int N, int C) {
-  return time_tile_bytes<float2>(N, C) + 16 + 2 * sizeof(float2) * (size_t)C;
+// U staging ring of the update: RING levels x 2C points, hi and lo
+__host__ __device__ constexpr size_t inv_ring_bytes(int C, int ring) { return 2 * sizeof(float) * (size_t)ring * 2 * C; }
+__host__ __device__ constexpr size_t inv_upd_smem_ring(int N, int C, int ring) {
+  return sizeof(float2) * ((size_t)N * C + N) + sizeof(unsigned short) * (size_t)N + 16 +
+         2 * sizeof(float2) * (size_t)C + 16 + inv_ring_bytes(C, ring);
 }
+// ring depth: as many levels (a power of two, at most 64) as fit next to the tile with three
+// CTAs per SM, at least one round of kThreads / 2C levels and at most N
+__host__ __device__ constexpr int inv_ring_levels(int N, int C) {
+  int ring = 64;
+  while (ring > kThreads / (2 * C) && inv_upd_smem_ring(N, C, ring) > 72 * 1024) ring >>= 1;
+  if (ring > N) ring = N;
+  if (ring < kThreads / (2 * C)) ring = kThreads / (2 * C);
+  return ring;
+}
+size_t inv_upd_smem(int N, int C) { return inv_upd_smem_ring(N, C, inv_ring_levels(N, C)); }
 
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Wait until at most n of this thread's most recent copy groups are pending (n > 7 waits as
+// for 7: stricter, never weaker).
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<5>(); break;
+    case 6: cp_async_wait<6>(); break;
+    default: cp_async_wait<7>(); break;
+  }
+}
+
+// Inverse time DFT of the tile, unscaling, and U += c with the norms of c and U.
+// Thread (q, r) of the update owns point q and the levels i = r (mod kThreads / 2C). Its U values
+// stream through a per-thread ring of shared-memory slots filled by asynchronous copies: the
+// first rounds are requested before the spectrum arrives and the FFT runs, and each consumed
+// slot is refilled with the level RING further on, so the loads stay in flight behind the
+// arithmetic and the stores. A thread reads only slots it filled itself (no block barrier).
+// LOGN > 0: compiled for N = 2^LOGN levels and 2^LOGC columns; LOGN = 0: any shape.
+template <int LOGN, int LOGC>
 __global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
+  constexpr bool CT = LOGN > 0;
+  constexpr int CT_RING = CT ? inv_ring_levels(1 << LOGN, 1 << LOGC) : 1;
+  constexpr int CT_DEPTH = CT ? CT_RING / (kThreads >> (LOGC + 1)) : 1;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = a.N, C = a.C, M = a.M, logC = a.logC;
+  const int N = CT ? (1 << LOGN) : a.N, M = a.M;
+  const int C = CT ? (1 << LOGC) : a.C, logC = CT ? LOGC : a.logC;
   float2 *X, *tw;
   unsigned short* perm;
   time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
   float2* B0 = reinterpret_cast<float2*>(((size_t)(perm + N) + 15) & ~(size_t)15);  // [2][C]
-  const int m0 = blockIdx.x * 2 * C;
+  float* ring_h = reinterpret_cast<float*>(((size_t)(B0 + 2 * C) + 15) & ~(size_t)15);
+  const int RING = CT ? CT_RING : a.ring, P2 = 2 * C, logP2 = logC + 1;
+  float* ring_l = ring_h + (size_t)RING * P2;
+  const int m0 = blockIdx.x * P2;
   const int J = N / 2 + 1;
+  const int q = threadIdx.x & (P2 - 1), r0 = threadIdx.x >> logP2;
+  const int LPR = kThreads >> logP2;     // levels per round
+  const int depth = CT ? CT_DEPTH : RING / LPR;  // rounds in flight
+  const int m = m0 + q;
+  const bool valid = m < M;
   __syncthreads();  // perm
-  // Half spectra straight into the FFT's permuted rows with asynchronous copies, all in flight
-  // at once: A_j (real-part point) into row perm[j], B_j (imaginary-part point) into row
-  // perm[N-j]; B_0 and B_{N/2}, whose partner rows are their own, into B0.
-  for (int it = threadIdx.x; it < (J << logC); it += blockDim.x) {
+
+  // 1. the half spectra straight into the FFT's permuted rows: A_j (real-part point) into row
+  //    perm[j], B_j (imaginary-part point) into row perm[N-j]; B_0 and B_{N/2}, whose partner
+  //    rows are their own, into B0
+  for (int it = threadIdx.x; it < (J << logC); it += kThreads) {
     const int cc = it & (C - 1), j = it >> logC;
     const int ma = m0 + cc, mb = m0 + C + cc;
     float2* da = X + (size_t)perm[j] * C + cc;
@@ -287,10 +344,23 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
     if (mb < M) cp_async8(db, a.S + (size_t)j * M + mb);
     else *db = make_float2(0.f, 0.f);
   }
-  cp_async_wait_all();
+  cp_async_commit();
+  // 2. the first rounds of U into the ring (one group per round)
+  const float* uh_src = a.Uhi + m;
+  const float* ul_src = a.Ulo + m;
+  for (int d = 0; d < depth; ++d) {
+    const int i = d * LPR + r0;  // < RING
+    if (valid && i < N) {
+      cp_async4(ring_h + (i << logP2) + q, uh_src + (size_t)i * M);
+      cp_async4(ring_l + (i << logP2) + q, ul_src + (size_t)i * M);
+    }
+    cp_async_commit();
+  }
+  // 3. spectrum complete (the depth U groups committed after it may still be pending)
+  if constexpr (CT) cp_async_wait<CT_DEPTH < 7 ? CT_DEPTH : 7>();
+  else cp_async_wait_pending(depth);
   __syncthreads();
-  // Z_j = A_j + i B_j and Z_{N-j} = conj(A_j) + i conj(B_j), each pair by one thread
-  for (int it = threadIdx.x; it < (J << logC); it += blockDim.x) {
+  for (int it = threadIdx.x; it < (J << logC); it += kThreads) {
     const int cc = it & (C - 1), j = it >> logC;
     float2* pa = X + (size_t)perm[j] * C + cc;
     const float2 A = *pa;
@@ -300,54 +370,39 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
     } else {
       float2* pb = X + (size_t)perm[N - j] * C + cc;
       const float2 B = *pb;
-      *pa = make_float2(A.x - B.y, A.y + B.x);
-      *pb = make_float2(A.x + B.y, B.x - A.y);
+      *pa = make_float2(A.x - B.y, A.y + B.x);   // Z_j = A_j + i B_j
+      *pb = make_float2(A.x + B.y, B.x - A.y);   // Z_{N-j} = conj(A_j) + i conj(B_j)
     }
   }
   __syncthreads();
-  fft_inverse(X, C, logC, N, tw);
+  if constexpr (CT) fft_inverse_ct<LOGN, LOGC, (1 << LOGC)>(X, tw);
+  else fft_inverse(X, C, logC, N, tw);
 
-  // U += c: the loads of UB items are issued together before any store (the stores go to the
-  // same arrays, so the compiler could not move later loads above them)
-  constexpr int UB = 8;
+  // 4. U += c, level by level through the ring
   float sc = 0.f, su = 0.f;  // per-thread partial norms (FP32: the FP64 pipe is ~1/70 rate)
-  const int tot = N << logC;
-  for (int it0 = threadIdx.x; it0 < tot; it0 += UB * blockDim.x) {
-    float uh[UB][2], ul[UB][2];
-#pragma unroll
-    for (int t = 0; t < UB; ++t) {
-      const int it = it0 + t * blockDim.x;
-      const int cc = it & (C - 1), i = it >> logC;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = m0 + h * C + cc;
-        const bool ok = it < tot && m < M;
-        const size_t idx = (size_t)i * M + m;
-        uh[t][h] = ok ? a.Uhi[idx] : 0.f;
-        ul[t][h] = ok ? a.Ulo[idx] : 0.f;
-      }
+  const float* Xf = reinterpret_cast<const float*>(X) + 2 * (q & (C - 1)) + (q >= C ? 1 : 0);
+  float* uh_dst = a.Uhi + m;
+  float* ul_dst = a.Ulo + m;
+  for (int i = r0; i < N; i += LPR) {
+    if constexpr (CT) cp_async_wait<(CT_DEPTH - 1 < 7 ? CT_DEPTH - 1 : 7)>();
+    else cp_async_wait_pending(depth - 1);  // the group of level i is complete
+    const int slot = ((i & (RING - 1)) << logP2) + q;
+    const float cval = Xf[(size_t)2 * i * C] * __ldg(a.inv_s + i);
+    const size_t row = (size_t)i * M;
+    if (valid) {
+      const ff u = ff_add_f(ff{ring_h[slot], ring_l[slot]}, cval);
+      uh_dst[row] = u.hi;
+      ul_dst[row] = u.lo;
+      sc = fmaf(cval, cval, sc);
+      su = fmaf(u.hi, u.hi, su);
     }
-#pragma unroll
-    for (int t = 0; t < UB; ++t) {
-      const int it = it0 + t * blockDim.x;
-      if (it >= tot) break;
-      const int cc = it & (C - 1), i = it >> logC;
-      const float2 z = X[(size_t)i * C + cc];
-      const float is = __ldg(a.inv_s + i);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = m0 + h * C + cc;
-        if (m >= M) continue;
-        const float cval = (h ? z.y : z.x) * is;
-        const size_t idx = (size_t)i * M + m;
-        const ff u = ff_add_f(ff{uh[t][h], ul[t][h]}, cval);
-        a.Uhi[idx] = u.hi;
-        a.Ulo[idx] = u.lo;
-        sc = fmaf(cval, cval, sc);
-        su = fmaf(u.hi, u.hi, su);
-      }
+    if (valid && i + RING < N) {
+      cp_async4(ring_h + slot, uh_src + row + (size_t)RING * M);
+      cp_async4(ring_l + slot, ul_src + row + (size_t)RING * M);
     }
+    cp_async_commit();
   }
+  cp_async_wait_all();
   block_reduce_add2((double)sc, (double)su, a.norms);
 }
 
@@ -736,14 +791,27 @@ cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st) {
   return a.dim == 2 ? launch_resid_d<true>(a, sm, st) : launch_resid_d<false>(a, sm, st);
 }
 
-cudaError_t launch_inv_upd(const InvUpdArgs& a, cudaStream_t st) {
+template <int LOGN, int LOGC> static cudaError_t launch_inv_k(const InvUpdArgs& a, cudaStream_t st) {
   const size_t sm = inv_upd_smem(a.N, a.C);
-  cudaError_t e = set_smem(k_inv_upd, sm);
+  cudaError_t e = set_smem(k_inv_upd<LOGN, LOGC>, sm);
   if (e != cudaSuccess) return e;
   prof_begin("inv_update_ff", st);
-  k_inv_upd<<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
+  InvUpdArgs b = a;
+  b.ring = inv_ring_levels(a.N, a.C);
+  k_inv_upd<LOGN, LOGC><<<tiles(a.M, a.C), kThreads, sm, st>>>(b);
   prof_end(st);
   return cudaGetLastError();
+}
+
+cudaError_t launch_inv_upd(const InvUpdArgs& a, cudaStream_t st) {
+  // compiled shapes: the tile widths the plan picks for large grids at these N
+  if (a.N == 128 && a.C == 16) return launch_inv_k<7, 4>(a, st);
+  if (a.N == 256 && a.C == 16) return launch_inv_k<8, 4>(a, st);
+  if (a.N == 512 && a.C == 16) return launch_inv_k<9, 4>(a, st);
+  if (a.N == 1024 && a.C == 8) return launch_inv_k<10, 3>(a, st);
+  if (a.N == 2048 && a.C == 4) return launch_inv_k<11, 2>(a, st);
+  if (a.N == 4096 && a.C == 2) return launch_inv_k<12, 1>(a, st);
+  return launch_inv_k<0, 0>(a, st);
 }
 
 template <typename T> cudaError_t launch_direct_fwd(const DirectFwdArgs<T>& a, cudaStream_t st) {

@@ -30,6 +30,7 @@ struct InvUpdArgs {
   const float* inv_s; const float2* tw;
   int N, M, C, logC;
   double* norms;                           // [0] += sum c^2, [1] += sum U^2
+  int ring;                                // levels in the U staging ring (set by the launcher)
 };
 
 // FP64 / FP32: F_{m-1} = F_hat + (P - K) U_{m-1}, times kappa^{i/N}, DFT.

@@ -695,7 +695,7 @@ pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   InvUpdArgs u{};
   u.S = reinterpret_cast<const float2*>(p->S); u.Uhi = p->Uhi; u.Ulo = p->Ulo;
   u.inv_s = p->tf.inv_s; u.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
-  u.N = N; u.M = M; u.C = p->Ct; u.logC = ilog2c(p->Ct); u.norms = p->norms;
+  u.N = N; u.M = M; u.C = p->Cr; u.logC = ilog2c(p->Cr); u.norms = p->norms;
   e = launch_inv_upd(u, st);
   if (e != cudaSuccess) return cuda_fail(e, "update kernel");
   return PINT_OK;
