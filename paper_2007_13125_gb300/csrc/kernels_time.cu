@@ -108,9 +108,9 @@ __device__ __forceinline__ void load_half_spectrum(V* X, const unsigned short* p
 // One thread owns one point of the tile and marches through a block of N/G consecutive levels
 // (G level groups per CTA). The k previous levels of its U stay in registers, so each level
 // reads U, its y neighbours, F_hat (and y) once, straight from global memory with coalesced
-// loads issued two levels ahead; x neighbours come from the adjacent lanes by warp shuffles
-// (global loads only at warp edges). The residuals go into the shared-memory tile, which is
-// then transformed along time.
+// loads issued one level ahead (four CTAs per SM hide the rest of the latency); x neighbours
+// come from the adjacent lanes by warp shuffles (global loads only at warp edges). The
+// residuals go into the shared-memory tile, which is then transformed along time.
 //
 // The stencil coefficients 1/hx^2, 1/hy^2 are powers of two (mx + 1, my + 1 are), so the four
 // neighbour terms are two exact double-float sums scaled exactly; only the BDF weights and the
@@ -139,7 +139,7 @@ struct ResidLevel {
 };
 
 template <int K, bool CQ, bool TWO_D>
-__global__ void __launch_bounds__(kThreads, 3) k_resid_fwd(ResidFwdArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = a.N, C = a.C, M = a.M, logC = a.logC, mx = a.mx;
   float2 *X, *tw;
@@ -201,12 +201,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_resid_fwd(ResidFwdArgs a) {
       h[t].lo = (valid && lev >= 0) ? a.Ulo[(size_t)lev * M + m] : 0.f;
     }
     const float gx = a.gx_hi, gy = a.gy_hi;
-    ResidLevel nx0 = load(i0), nx1 = load(i0 + 1 < i1 ? i0 + 1 : i0);
+    ResidLevel nx = load(i0);
 #pragma unroll 2
     for (int i = i0; i < i1; ++i) {
-      const ResidLevel c = nx0;
-      nx0 = nx1;
-      if (i + 2 < i1) nx1 = load(i + 2);
+      const ResidLevel c = nx;
+      if (i + 1 < i1) nx = load(i + 1);
 
       // x neighbours: adjacent lanes, or the global loads at warp edges
       // (shfl is uniform over the CTA and then every warp is fully inside one level group)
