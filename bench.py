@@ -37,7 +37,7 @@ METRIC = "space-time DOF/s to rel err 1e-8 (mixed vs FP64 diag); p50/p99 solve l
 UNIT = "DOF/s"
 TOL = 1e-8
 
-# algorithmic bytes per launch of each kernel, as a function of (N, M); see the design doc
+# algorithmic bytes per launch of each kernel, as a function of (N, M)
 def algo_bytes(name: str, N: int, M: int) -> float:
     NM, JM = N * M, (N // 2 + 1) * M
     table = {
@@ -54,12 +54,13 @@ def algo_bytes(name: str, N: int, M: int) -> float:
         "dst_f64": 32 * JM,
         "axis_solve_f64": 32 * JM,
         "toeplitz_f64": 16 * NM,                # read U, write the history product
+        "toeplitz_ff": 16 * NM,                 # read U (hi, lo), write the history (hi, lo)
     }
     return float(table.get(name, 0.0))
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
-# of the workload (profiles/k_resid_fwd_heat2d_255x255_N256_bdf4.md), valid while the kernel's
+# of the workload (`ncu --set full` of `bench.py --once mixed`), valid while the kernel's
 # source is unchanged (sha1 of its translation unit)
 NCU_TRAFFIC = {"resid_fwd_ff": (340.93e6, "kernels_time.cu", "91f56743f4519061aedccfbf6956c77348244a66")}
 

@@ -95,7 +95,9 @@ typedef struct {
                              (default), 2 = tridiagonal (FP32 inner solves only; FP64 uses 1),
                              3 = whichever of 1 and 2 runs faster on this GPU, timed at plan
                              creation (cached per shape). The sine transform is the default: its
-                             inner solves are more accurate, which saves a sweep (see DESIGN) */
+                             FP32 inner solves are more accurate (the tridiagonal recurrences
+                             amplify rounding with the condition of the line systems), which
+                             saves a sweep at tol 1e-8 on a 255 x 255, N = 256 heat problem */
 } pint_plan_desc;
 
 /* Build a plan: FP64 constant tables (BDF / CQ weights omega_j of eq. (2.2) / eq. (3.2) --
