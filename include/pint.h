@@ -150,10 +150,24 @@ pint_status pint_wr_sweep(pint_plan plan, const double* Fhat, const double* U_pr
  * Fhat [N][M] device input; U [N][M] device, in: initial guess, out: solution.
  * sweeps_out, upd_rel_out: optional host pointers. The whole solve is one CUDA-graph launch (a
  * while-node repeats the sweep until a device-side check of the fused norms stops it); the graph
- * is built on first use and reused while (Fhat, U, tol, max_sweeps) stay the same. The call waits
+ * is built on first use of an (Fhat, U, tol, max_sweeps) combination and reused for it (a plan
+ * keeps the four most recently used, so alternating buffer sets do not rebuild). The call waits
  * for `stream` once. With per-kernel profiling on, sweeps are launched one by one instead. */
 pint_status pint_solve(pint_plan plan, const double* Fhat, double* U, double tol, int max_sweeps,
                        int* sweeps_out, double* upd_rel_out, void* stream);
+
+/* The whole solve of pint_solve (one graph launch) enqueued on `stream` without waiting, so that
+ * host transfers or other work can be queued behind it. The plan's workspaces stay in use until
+ * the stream has completed the solve: later calls on the same plan must be ordered after it
+ * (same stream, or an event). Fhat, U, tol, max_sweeps as in pint_solve. PINT_EINVAL while
+ * per-kernel profiling is on (that mode launches sweeps from the host). */
+pint_status pint_solve_async(pint_plan plan, const double* Fhat, double* U, double tol, int max_sweeps,
+                             void* stream);
+
+/* Outcome of the plan's most recent graph-launched solve: sweeps, final relative update, and
+ * PINT_OK if it met tol, PINT_ENOTCONV if it stopped at max_sweeps. Valid once the stream has
+ * completed that solve; the next solve on the plan overwrites it. */
+pint_status pint_solve_result(pint_plan plan, int* sweeps_out, double* upd_rel_out);
 
 /* Solve n independent problems with one graph launch. Each plan's whole solve (prologue, a
  * while-loop of sweeps with the device-side convergence check, epilogue) becomes an independent

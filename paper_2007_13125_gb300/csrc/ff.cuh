@@ -138,6 +138,24 @@ __device__ __forceinline__ ff ff_from_double(double x) {
   return r;
 }
 
+// FP64 -> double-float by truncation, from the two 32-bit halves of the double: hi keeps the
+// leading 24 significant bits (exact as a float), lo is the remaining 29-bit integer scaled by
+// 2^(e-1075) and rounded once to 24 bits: |hi + lo - x| <= 2^-47 |x| for |x| in [2^-74, 2^127),
+// |lo| < ulp(hi) (not normalised: fine as the start of an accumulation). Cheaper than
+// ff_from_double (no 64-bit rounding carry). Below 2^-74 lo is dropped, below 2^-126 all is 0.
+__device__ __forceinline__ ff ff_split_trunc(double x) {
+  const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+  const unsigned e = (h >> 20) & 0x7FFu;
+  const unsigned sgn = h & 0x80000000u;
+  ff r;
+  const unsigned hb = sgn | ((e - 896u) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29);
+  r.hi = e >= 897u ? __uint_as_float(hb) : 0.f;
+  const float scale = e >= 949u ? __uint_as_float((e - 948u) << 23) : 0.f;
+  const float lo = __uint2float_rn(l & 0x1FFFFFFFu) * scale;
+  r.lo = __uint_as_float(__float_as_uint(lo) | sgn);
+  return r;
+}
+
 // Exact float -> double by bit construction (no FP64 conversion instruction).
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned int u = __float_as_uint(f);

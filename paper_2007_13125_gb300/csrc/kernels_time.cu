@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
 
       // stencil centre, BDF history (and CQ history): error-free products
       ff_acc A;
-      A.init(ff_from_double(c.f));
+      A.init(ff_split_trunc(c.f));
       if constexpr (CQ) A.sub(ff{c.yh, c.yl});
       A.fma_term(ff{a.c_hi[0], a.c_lo[0]}, ff{c.uh, c.ul}, -1.f);
 #pragma unroll

@@ -330,7 +330,8 @@ pint_status validate(int k, double alpha, double kappa, double tau, int N, const
 
 void destroy_plan(pint_plan p) {
   if (!p) return;
-  if (p->sg.exec) cudaGraphExecDestroy(p->sg.exec);
+  for (SolveGraph& c : p->sg)
+    if (c.exec) cudaGraphExecDestroy(c.exec);
   if (p->cap) cudaStreamDestroy(p->cap);
   for (void* q : p->allocs) {
     if (p->alloc) p->alloc->release(q);
@@ -862,8 +863,17 @@ pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, d
 
 pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double tol, int max_sweeps,
                                 cudaStream_t st) {
-  SolveGraph& sg = p->sg;
-  if (!sg.exec || sg.F != F || sg.U != U || sg.tol != tol || sg.max_sweeps != max_sweeps) {
+  SolveGraph* hit = nullptr;
+  for (SolveGraph& c : p->sg)
+    if (c.exec && c.F == F && c.U == U && c.tol == tol && c.max_sweeps == max_sweeps) hit = &c;
+  if (!hit) {
+    // an empty slot, else the least recently used one
+    hit = &p->sg[0];
+    for (SolveGraph& c : p->sg) {
+      if (!c.exec) { hit = &c; break; }
+      if (c.last_use < hit->last_use) hit = &c;
+    }
+    SolveGraph& sg = *hit;
     if (sg.exec) {
       cudaGraphExecDestroy(sg.exec);
       sg.exec = nullptr;
@@ -882,7 +892,8 @@ pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double 
     }
     sg.F = F; sg.U = U; sg.tol = tol; sg.max_sweeps = max_sweeps;
   }
-  PINT_CUDA(cudaGraphLaunch(sg.exec, st));
+  hit->last_use = ++p->sg_clock;
+  PINT_CUDA(cudaGraphLaunch(hit->exec, st));
   return PINT_OK;
 }
 
@@ -913,6 +924,26 @@ extern "C" pint_status pint_wr_sweep(pint_plan p, const double* Fhat, const doub
   pint_status s = sweep_user(p, Fhat, U_prev, U_next, st);
   if (s != PINT_OK) return s;
   if (upd_rel) return read_norms(p, st, upd_rel);
+  return PINT_OK;
+}
+
+extern "C" pint_status pint_solve_async(pint_plan p, const double* Fhat, double* U, double tol, int max_sweeps,
+                                        void* stream) {
+  if (!p || !Fhat || !U) return fail(PINT_EINVAL, "NULL argument");
+  if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
+  if (g_prof_on) return fail(PINT_EINVAL, "pint_solve_async: not available while per-kernel profiling is on");
+  return solve_enqueue(p, Fhat, U, tol, max_sweeps, (cudaStream_t)stream);
+}
+
+extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* upd_rel_out) {
+  if (!p) return fail(PINT_EINVAL, "NULL argument");
+  int m = 0;
+  double upd = 0.0;
+  bool done = false;
+  solve_result(p, &m, &upd, &done);
+  if (sweeps_out) *sweeps_out = m;
+  if (upd_rel_out) *upd_rel_out = upd;
+  if (!done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
   return PINT_OK;
 }
 

@@ -37,13 +37,18 @@ struct DevAllocator {
 };
 
 // Cached executable graph of one whole solve (prologue, while-loop of sweeps, epilogue).
+// One instantiated whole-solve graph and the arguments it was built for.
 struct SolveGraph {
   cudaGraphExec_t exec = nullptr;
   const double* F = nullptr;
   double* U = nullptr;
   double tol = 0.0;
   int max_sweeps = 0;
+  unsigned long long last_use = 0;
 };
+// Graphs cached per plan (least recently used replaced): callers that alternate between a few
+// buffer sets, e.g. to overlap host transfers with solves, reuse their graphs.
+constexpr int kSolveGraphs = 4;
 
 }  // namespace pint
 
@@ -78,7 +83,8 @@ struct pint_plan_s {
   pint::SolveCtl* ctl = nullptr;    // device convergence state
   pint::SolveCtl* h_ctl = nullptr;  // pinned host copy written by the graph's epilogue
   cudaStream_t cap = nullptr;       // stream used to capture graphs
-  pint::SolveGraph sg;
+  pint::SolveGraph sg[pint::kSolveGraphs];
+  unsigned long long sg_clock = 0;
   // tiles
   int Ct, Cr, Ctd, Cz, Cx, Cy, Ctri;  // columns per CTA: time (float), residual, time (T), toeplitz, x, y, tri
   int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal

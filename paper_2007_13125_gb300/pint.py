@@ -74,6 +74,8 @@ def lib():
         "pint_initial_guess": (_I, [_P, _P, _P, _P]),
         "pint_wr_sweep": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D), _P]),
         "pint_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+        "pint_solve_async": (_I, [_P, _P, _P, _D, _I, _P]),
+        "pint_solve_result": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
         "pint_time_weights": (_I, [_I, _D, _I, ctypes.POINTER(_D)]),
         "pint_correction_coefficients": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
         "pint_circulant_eigenvalues": (_I, [_I, _D, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -251,6 +253,20 @@ class Plan:
         upd = _D(0.0)
         st = lib().pint_solve(self.handle, _ptr(Fhat), _ptr(U), float(tol), int(max_sweeps),
                               ctypes.byref(sweeps), ctypes.byref(upd), _stream(stream))
+        if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
+            raise PintError(st, last_error())
+        return st, sweeps.value, upd.value
+
+    def solve_async(self, Fhat, U, tol=1e-10, max_sweeps=50, stream=None):
+        """Enqueue the whole solve on `stream` without waiting (pint_solve_async)."""
+        check(lib().pint_solve_async(self.handle, _ptr(Fhat), _ptr(U), float(tol), int(max_sweeps),
+                                     _stream(stream)))
+
+    def solve_result(self, raise_on_notconv=True):
+        """(status, sweeps, update) of the last graph-launched solve, once its stream completed it."""
+        sweeps = _I(0)
+        upd = _D(0.0)
+        st = lib().pint_solve_result(self.handle, ctypes.byref(sweeps), ctypes.byref(upd))
         if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
             raise PintError(st, last_error())
         return st, sweeps.value, upd.value

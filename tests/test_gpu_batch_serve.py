@@ -51,6 +51,71 @@ def test_graph_solve_matches_host_loop():
     assert rel_l2(Ug, oracle_solution(p)) <= 1e-8
 
 
+def test_graph_cache_rotating_buffers():
+    """Solves over more buffer sets than a plan caches graphs for (least recently used replaced):
+    every solve gives the same result as the first, bit for bit."""
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = workloads.small_problem(dim=2, mx=31, N=32, k=4, alpha=1.0, kappa=0.05, seed=5)
+    dev = torch.device("cuda:0")
+    v = torch.tensor(p.v, device=dev); f = torch.tensor(p.f(), device=dev); fd = torch.tensor(p.fderiv(), device=dev)
+    with Plan.for_problem(p, "mixed") as plan:
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device=dev)
+        plan.form_rhs(v, f, fd, F)
+        Us = [torch.empty_like(F) for _ in range(5)]
+        results = []
+        for r in range(3):
+            for i in (0, 1, 2, 3, 4, 1, 0):
+                plan.initial_guess(v, Us[i])
+                st, sweeps, upd = plan.solve(F, Us[i], tol=1e-9)
+                results.append((Us[i].cpu().numpy(), sweeps))
+    U0, s0 = results[0]
+    for Ui, si in results[1:]:
+        assert si == s0
+        assert np.array_equal(Ui, U0)
+    assert rel_l2(U0, oracle_solution(p)) <= 1e-8
+
+
+def test_solve_async_back_to_back():
+    """Solves enqueued back to back (pint_solve_async) on two buffer sets, with the copies of the
+    results to host memory queued behind them, give the synchronous solve's result."""
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan, pint
+    from paper_2007_13125_gb300.pint import PintError
+    p = workloads.small_problem(dim=2, mx=31, N=32, k=3, alpha=1.0, kappa=0.05, seed=7)
+    dev = torch.device("cuda:0")
+    v = torch.tensor(p.v, device=dev); f = torch.tensor(p.f(), device=dev); fd = torch.tensor(p.fderiv(), device=dev)
+    with Plan.for_problem(p, "mixed") as plan:
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device=dev)
+        plan.form_rhs(v, f, fd, F)
+        Uref = torch.empty_like(F)
+        plan.initial_guess(v, Uref)
+        st, sweeps, upd = plan.solve(F, Uref, tol=1e-9)
+        ref = Uref.cpu().numpy()
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        Us = [torch.empty_like(F) for _ in range(2)]
+        outs = [torch.empty((p.N, p.M), dtype=torch.float64).pin_memory() for _ in range(4)]
+        with torch.cuda.stream(s):
+            for i in range(4):
+                plan.initial_guess(v, Us[i % 2], s)
+                plan.solve_async(F, Us[i % 2], tol=1e-9, stream=s)
+                outs[i].copy_(Us[i % 2], non_blocking=True)
+        s.synchronize()
+        st2, sweeps2, upd2 = plan.solve_result()
+        assert sweeps2 == sweeps and upd2 == pytest.approx(upd, rel=1e-9)  # atomically summed norms
+        for o in outs:
+            assert np.array_equal(o.numpy(), ref)
+        pint.set_profiling(True)
+        try:
+            with pytest.raises(PintError):
+                plan.solve_async(F, Us[0], tol=1e-9)
+        finally:
+            pint.set_profiling(False)
+            pint.kernel_stats(reset=True)
+    assert rel_l2(ref, oracle_solution(p)) <= 1e-8
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_batch_solve_mixed_problems(precision):
     torch = torch_cuda()
