@@ -76,6 +76,15 @@ typedef enum { PINT_EIG_TRUNC_DFT = 0, PINT_EIG_CLOSED_FORM = 1 } pint_eig_varia
  * the sequential solution as its fixed point for any preconditioner, whereas the printed direct
  * form's kappa-term (eq. (3.12)) belongs to the truncated matrix (PINT_EINVAL otherwise). */
 
+/* Spatial discretisation of the Dirichlet Laplacian on the unit interval / square, interior
+ * nodes only, h = 1/(m+1) per axis:
+ * FD:     finite differences, A_h = the 3-/5-point stencil (1/h^2) [-1 2 -1] per axis.
+ * FEM_P1: piecewise-linear Galerkin finite elements on the uniform mesh (Sec. 4, the space
+ *         discretisation of the paper's 1D tests): the time derivative acts through the mass
+ *         matrix M_h = (h/6) tridiag(1, 4, 1) and the Laplacian is the stiffness matrix
+ *         K_h = (1/h) tridiag(-1, 2, -1); unknowns are nodal values. 1D and PINT_MIXED only. */
+typedef enum { PINT_SPACE_FD = 0, PINT_SPACE_FEM_P1 = 1 } pint_space;
+
 typedef struct {
   int dim;  /* 1 or 2 */
   int mx;   /* interior points along x */
@@ -98,6 +107,7 @@ typedef struct {
                              FP32 inner solves are more accurate (the tridiagonal recurrences
                              amplify rounding with the condition of the line systems), which
                              saves a sweep at tol 1e-8 on a 255 x 255, N = 256 heat problem */
+  int space;              /* pint_space (0 = FD, the default when the struct is zeroed) */
 } pint_plan_desc;
 
 /* Build a plan: FP64 constant tables (BDF / CQ weights omega_j of eq. (2.2) / eq. (3.2) --
@@ -124,6 +134,9 @@ size_t pint_plan_workspace_bytes(pint_plan plan);
  * f      [N][M]   device, f(t_n) on the grid
  * fderiv [k-1][M] device, row l = d_t^l f(0) (row 0 = f(0)); may be NULL when k = 1
  * Fhat   [N][M]   device, output (FP64)
+ * With PINT_SPACE_FEM_P1 the same formula holds in weak form: v holds the nodal values of v_h,
+ * f and fderiv hold load vectors ((f(t_n), phi_i) and (d_t^l f(0), phi_i)), A v becomes K_h v
+ * and the last term tau^-alpha sum_j omega_j M_h v.
  * Enqueued on `stream`; asynchronous. */
 pint_status pint_form_rhs(pint_plan plan, const double* v, const double* f, const double* fderiv,
                           double* Fhat, void* stream);

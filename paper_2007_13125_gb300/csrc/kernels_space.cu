@@ -26,9 +26,10 @@ namespace pint {
 // both patterns free of bank conflicts. Rows read in the FFT's digit-reversed order are first
 // brought into natural order through registers (lanes along lines), for the same reason.
 template <typename T> constexpr int axis_regs() { return sizeof(T) == 4 ? 16 : 8; }
-template <typename T> size_t axis_smem(int n, int C) {
+// (the mass-eigenvalue table is carved only for P1 FEM lines: has_mu)
+template <typename T> size_t axis_smem(int n, int C, bool has_mu) {
   const size_t L = 2 * (size_t)(n + 1);
-  return sizeof(typename c2<T>::t) * (L * (C + 1) + L + C) + sizeof(T) * (size_t)(n + 1) +
+  return sizeof(typename c2<T>::t) * (L * (C + 1) + L + C) + (has_mu ? 2 : 1) * sizeof(T) * (size_t)(n + 1) +
          sizeof(unsigned short) * L + 2 * sizeof(int) * C + 64;
 }
 
@@ -51,7 +52,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
   V* tw = X + (size_t)L * ld;
   V* dcol = tw + L;                                      // line -> sigma_j + lambda_other (op 1)
   T* lam = reinterpret_cast<T*>(dcol + C);               // lambda along this axis (op 1)
-  unsigned short* perm = reinterpret_cast<unsigned short*>(lam + n + 1);
+  T* mu = lam + n + 1;                                   // P1 mass eigenvalues (op 1, FEM)
+  unsigned short* perm = reinterpret_cast<unsigned short*>(a.mu_axis ? mu + n + 1 : mu);
   int* lj = reinterpret_cast<int*>(perm + L + (L & 1));  // line -> j
   int* lp = lj + C;                                      // line -> position within its slice
   const V* gtw = reinterpret_cast<const V*>(a.tw);
@@ -128,7 +130,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
       }
       dcol[cc] = d;
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = a.lam_axis[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      lam[i] = a.lam_axis[i];
+      if (a.mu_axis) mu[i] = a.mu_axis[i];
+    }
   }
   __syncthreads();
   if constexpr (CT) fft_forward_ct<LOGL, LOGC, (1 << LOGC) + 1>(X, tw);
@@ -190,8 +195,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
       if (p != 0 && p != n + 1) X[(size_t)perm[L - p] * ld + cc] = mk(zero, zero);
       continue;
     }
+    // sigma_j mu_p + lambda_p (mu_p = 1 for finite differences)
     V d = dcol[cc];
-    d.x += lam[p - 1];
+    const T mp = a.mu_axis ? mu[p - 1] : T(1);
+    d.x = d.x * mp + lam[p - 1];
+    d.y *= mp;
     d.x *= a.scale;
     d.y *= a.scale;
     const T inv = rcp(d.x * d.x + d.y * d.y);
@@ -234,7 +242,7 @@ static cudaError_t launch_axis_k(const AxisArgs<T>& a, size_t sm, cudaStream_t s
 }
 
 template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t st) {
-  const size_t sm = axis_smem<T>(a.n, a.C);
+  const size_t sm = axis_smem<T>(a.n, a.C, a.mu_axis != nullptr);
   if constexpr (sizeof(T) == 4) {
     // compiled shapes: n = 2^q - 1 with the tile widths the plan picks for them
     const int L = 2 * (a.n + 1);
@@ -370,8 +378,8 @@ cudaError_t launch_tri(const TriArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template size_t axis_smem<float>(int, int);
-template size_t axis_smem<double>(int, int);
+template size_t axis_smem<float>(int, int, bool);
+template size_t axis_smem<double>(int, int, bool);
 template cudaError_t launch_axis<float>(const AxisArgs<float>&, cudaStream_t);
 template cudaError_t launch_axis<double>(const AxisArgs<double>&, cudaStream_t);
 

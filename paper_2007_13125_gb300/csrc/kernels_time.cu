@@ -134,11 +134,15 @@ struct ResidLevel {
   float sh, sl;    // south neighbour (m - mx)
   float nh, nl;    // north neighbour (m + mx)
   float yh, yl;    // CQ history
+  float ywh, ywl;  // P1 FEM + CQ: west / east neighbours of the history (warp edges)
+  float yeh, yel;
   double f;        // F_hat
   float s;         // kappa^{i/N}
 };
 
-template <int K, bool CQ, bool TWO_D>
+// FEM = P1 finite elements (1D): the time terms act on V = M_h U, the history registers hold V,
+// and the stiffness K_h U = (1/h)(2 U_i - U_{i-1} - U_{i+1}) replaces the FD stencil.
+template <int K, bool CQ, bool TWO_D, bool FEM>
 __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = a.N, C = a.C, M = a.M, logC = a.logC, mx = a.mx;
@@ -185,20 +189,60 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
       v.yh = 0.f;
       v.yl = 0.f;
     }
+    if (FEM && cq) {
+      v.ywh = ldW ? a.yhi[idx - 1] : 0.f;
+      v.ywl = ldW ? a.ylo[idx - 1] : 0.f;
+      v.yeh = ldE ? a.yhi[idx + 1] : 0.f;
+      v.yel = ldE ? a.ylo[idx + 1] : 0.f;
+    } else {
+      v.ywh = v.ywl = v.yeh = v.yel = 0.f;
+    }
     v.f = valid ? a.F[idx] : 0.0;
     v.s = __ldg(a.s + i);
     return v;
   };
 
+  // x neighbours of a per-point double-float value: adjacent lanes, or the values loaded at warp
+  // edges; zero beyond the Dirichlet boundary. (shfl is uniform over the CTA and then every warp
+  // is fully inside one level group.)
+  auto neighbours = [&](float ch, float cl, float ewh, float ewl, float eeh, float eel, float& wh, float& wl,
+                        float& eh, float& el) {
+    wh = ewh; wl = ewl; eh = eeh; el = eel;
+    if (shfl) {
+      const float uwh = __shfl_up_sync(0xffffffffu, ch, 1), uwl = __shfl_up_sync(0xffffffffu, cl, 1);
+      const float ueh = __shfl_down_sync(0xffffffffu, ch, 1), uel = __shfl_down_sync(0xffffffffu, cl, 1);
+      if (lane != 0) { wh = uwh; wl = uwl; }
+      if (lane != 31) { eh = ueh; el = uel; }
+    }
+    if (!hasW) { wh = 0.f; wl = 0.f; }
+    if (!hasE) { eh = 0.f; el = 0.f; }
+  };
+  // one row of the P1 mass matrix, (h/6)(u_{i-1} + 4 u_i + u_{i+1}), in double-float
+  auto mass = [&](float ch, float cl, float wh, float wl, float eh, float el) {
+    float b1, e1, b2, e2;
+    two_sum(wh, eh, b1, e1);
+    two_sum(b1, 4.f * ch, b2, e2);
+    const float lo = e1 + e2 + ((wl + el) + 4.f * cl);
+    return ff_mul(ff{b2, lo}, ff{a.m_hi, a.m_lo});
+  };
+
   if (g < G) {
     const int i0 = g * NL, i1 = i0 + NL;
-    // U of the K levels before i0 (zero before level 0)
+    // the K levels before i0 (zero before level 0): U, or M_h U for P1 elements
     ff h[K > 0 ? K : 1];
 #pragma unroll
     for (int t = 0; t < K; ++t) {
       const int lev = i0 - 1 - t;
-      h[t].hi = (valid && lev >= 0) ? a.Uhi[(size_t)lev * M + m] : 0.f;
-      h[t].lo = (valid && lev >= 0) ? a.Ulo[(size_t)lev * M + m] : 0.f;
+      const size_t idx = (size_t)(lev >= 0 ? lev : 0) * M + m;
+      h[t].hi = (valid && lev >= 0) ? a.Uhi[idx] : 0.f;
+      h[t].lo = (valid && lev >= 0) ? a.Ulo[idx] : 0.f;
+      if constexpr (FEM) {
+        float wh, wl, eh, el;
+        neighbours(h[t].hi, h[t].lo, (ldW && lev >= 0) ? a.Uhi[idx - 1] : 0.f,
+                   (ldW && lev >= 0) ? a.Ulo[idx - 1] : 0.f, (ldE && lev >= 0) ? a.Uhi[idx + 1] : 0.f,
+                   (ldE && lev >= 0) ? a.Ulo[idx + 1] : 0.f, wh, wl, eh, el);
+        h[t] = mass(h[t].hi, h[t].lo, wh, wl, eh, el);
+      }
     }
     const float gx = a.gx_hi, gy = a.gy_hi;
     ResidLevel nx = load(i0);
@@ -207,42 +251,56 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
       const ResidLevel c = nx;
       if (i + 1 < i1) nx = load(i + 1);
 
-      // x neighbours: adjacent lanes, or the global loads at warp edges
-      // (shfl is uniform over the CTA and then every warp is fully inside one level group)
-      float wh = c.wh, wl = c.wl, eh = c.eh, el = c.el;
-      if (shfl) {
-        const float uwh = __shfl_up_sync(0xffffffffu, c.uh, 1), uwl = __shfl_up_sync(0xffffffffu, c.ul, 1);
-        const float ueh = __shfl_down_sync(0xffffffffu, c.uh, 1), uel = __shfl_down_sync(0xffffffffu, c.ul, 1);
-        if (lane != 0) { wh = uwh; wl = uwl; }
-        if (lane != 31) { eh = ueh; el = uel; }
-      }
-      if (!hasW) { wh = 0.f; wl = 0.f; }
-      if (!hasE) { eh = 0.f; el = 0.f; }
+      float wh, wl, eh, el;
+      neighbours(c.uh, c.ul, c.wh, c.wl, c.eh, c.el, wh, wl, eh, el);
 
-      // stencil centre, BDF history (and CQ history): error-free products
       ff_acc A;
       A.init(ff_split_trunc(c.f));
-      if constexpr (CQ) A.sub(ff{c.yh, c.yl});
-      A.fma_term(ff{a.c_hi[0], a.c_lo[0]}, ff{c.uh, c.ul}, -1.f);
+      ff cur;  // what the history keeps of this level
+      if constexpr (FEM) {
+        // F_hat - M_h (tau^-alpha sum_j omega_j U^{n-j}) - K_h U^n
+        cur = mass(c.uh, c.ul, wh, wl, eh, el);
+        if constexpr (CQ) {
+          float ywh, ywl, yeh, yel;
+          neighbours(c.yh, c.yl, c.ywh, c.ywl, c.yeh, c.yel, ywh, ywl, yeh, yel);
+          A.sub(mass(c.yh, c.yl, ywh, ywl, yeh, yel));
+        } else {
+          A.fma_term(ff{a.c_hi[0], a.c_lo[0]}, cur, -1.f);
+        }
 #pragma unroll
-      for (int t = 1; t <= K; ++t) A.fma_term(ff{a.c_hi[t], a.c_lo[t]}, h[t - 1], -1.f);
-      // neighbours: exact sums, exact power-of-two scaling
-      float bx, ex;
-      two_sum(wh, eh, bx, ex);
-      A.add_hi(gx * bx);
-      float lo = gx * (ex + (wl + el));
-      if constexpr (TWO_D) {
-        float by, ey;
-        two_sum(c.sh, c.nh, by, ey);
-        A.add_hi(gy * by);
-        lo = fmaf(gy, ey + (c.sl + c.nl), lo);
+        for (int t = 1; t <= K; ++t) A.fma_term(ff{a.c_hi[t], a.c_lo[t]}, h[t - 1], -1.f);
+        // stiffness centre 2/h and neighbours 1/h: powers of two, exact
+        A.add_hi(-2.f * gx * c.uh);
+        A.sl = fmaf(-2.f * gx, c.ul, A.sl);
+        float bx, ex;
+        two_sum(wh, eh, bx, ex);
+        A.add_hi(gx * bx);
+        A.sl += gx * (ex + (wl + el));
+      } else {
+        cur = ff{c.uh, c.ul};
+        // stencil centre, BDF history (and CQ history): error-free products
+        if constexpr (CQ) A.sub(ff{c.yh, c.yl});
+        A.fma_term(ff{a.c_hi[0], a.c_lo[0]}, cur, -1.f);
+#pragma unroll
+        for (int t = 1; t <= K; ++t) A.fma_term(ff{a.c_hi[t], a.c_lo[t]}, h[t - 1], -1.f);
+        // neighbours: exact sums, exact power-of-two scaling
+        float bx, ex;
+        two_sum(wh, eh, bx, ex);
+        A.add_hi(gx * bx);
+        float lo = gx * (ex + (wl + el));
+        if constexpr (TWO_D) {
+          float by, ey;
+          two_sum(c.sh, c.nh, by, ey);
+          A.add_hi(gy * by);
+          lo = fmaf(gy, ey + (c.sl + c.nl), lo);
+        }
+        A.sl += lo;
       }
-      A.sl += lo;
       Xf[(size_t)2 * i * C] = valid ? A.value() * c.s : 0.f;
 
 #pragma unroll
       for (int t = K - 1; t > 0; --t) h[t] = h[t - 1];
-      if (K > 0) h[0] = ff{c.uh, c.ul};
+      if (K > 0) h[0] = cur;
     }
   }
   __syncthreads();
@@ -581,6 +639,16 @@ __global__ void k_rhs(RhsArgs a) {
   const int per = (a.N + gridDim.y - 1) / gridDim.y;
   const int i0 = blockIdx.y * per, i1 = min(a.N, i0 + per);
   const double vm = a.v[m];
+  // the beta term acts on v (FD) or on M_h v = (h/6)(v_{i-1} + 4 v_i + v_{i+1}) (P1 FEM); A v is
+  // the stencil with weight gx (1/h^2 FD, 1/h for the P1 stiffness)
+  double bv = vm;
+  if (a.fem) {
+    const int x = m % a.mx;
+    bv = 4.0 * vm;
+    if (x > 0) bv += a.v[m - 1];
+    if (x < a.mx - 1) bv += a.v[m + 1];
+    bv *= a.mass6;
+  }
   double Av = 0.0;
   if (i0 < a.k - 1) {
     const int x = m % a.mx;
@@ -602,7 +670,7 @@ __global__ void k_rhs(RhsArgs a) {
     for (int b = 0; b < B; ++b) {
       const int i = ib + b;
       if (i >= i1) break;
-      double F = fma(a.beta[i], vm, f[b]);
+      double F = fma(a.beta[i], bv, f[b]);
       if (i < a.k - 1) {
         F += a.a[i] * (a.fd[m] - Av);
         for (int l = 1; l <= a.k - 2; ++l) F += a.bt[l][i] * a.fd[(size_t)l * a.M + m];
@@ -760,25 +828,25 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 
 static int tiles(int M, int C) { return (M + 2 * C - 1) / (2 * C); }
 
-template <int K, bool CQ, bool TWO_D>
+template <int K, bool CQ, bool TWO_D, bool FEM>
 static cudaError_t launch_resid_k(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
-  cudaError_t e = set_smem(k_resid_fwd<K, CQ, TWO_D>, sm);
+  cudaError_t e = set_smem(k_resid_fwd<K, CQ, TWO_D, FEM>, sm);
   if (e != cudaSuccess) return e;
   prof_begin("resid_fwd_ff", st);
-  k_resid_fwd<K, CQ, TWO_D><<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
+  k_resid_fwd<K, CQ, TWO_D, FEM><<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
 }
 
-template <bool TWO_D> static cudaError_t launch_resid_d(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
-  if (a.yhi) return a.k == 0 ? launch_resid_k<0, true, TWO_D>(a, sm, st) : cudaErrorInvalidValue;
+template <bool TWO_D, bool FEM> static cudaError_t launch_resid_d(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
+  if (a.yhi) return a.k == 0 ? launch_resid_k<0, true, TWO_D, FEM>(a, sm, st) : cudaErrorInvalidValue;
   switch (a.k) {
-    case 1: return launch_resid_k<1, false, TWO_D>(a, sm, st);
-    case 2: return launch_resid_k<2, false, TWO_D>(a, sm, st);
-    case 3: return launch_resid_k<3, false, TWO_D>(a, sm, st);
-    case 4: return launch_resid_k<4, false, TWO_D>(a, sm, st);
-    case 5: return launch_resid_k<5, false, TWO_D>(a, sm, st);
-    case 6: return launch_resid_k<6, false, TWO_D>(a, sm, st);
+    case 1: return launch_resid_k<1, false, TWO_D, FEM>(a, sm, st);
+    case 2: return launch_resid_k<2, false, TWO_D, FEM>(a, sm, st);
+    case 3: return launch_resid_k<3, false, TWO_D, FEM>(a, sm, st);
+    case 4: return launch_resid_k<4, false, TWO_D, FEM>(a, sm, st);
+    case 5: return launch_resid_k<5, false, TWO_D, FEM>(a, sm, st);
+    case 6: return launch_resid_k<6, false, TWO_D, FEM>(a, sm, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -787,7 +855,8 @@ cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st) {
   // the neighbour terms assume exact power-of-two stencil coefficients
   if (a.gx_lo != 0.f || a.gy_lo != 0.f) return cudaErrorInvalidValue;
   const size_t sm = resid_fwd_smem(a.N, a.C);
-  return a.dim == 2 ? launch_resid_d<true>(a, sm, st) : launch_resid_d<false>(a, sm, st);
+  if (a.fem) return a.dim == 1 ? launch_resid_d<false, true>(a, sm, st) : cudaErrorInvalidValue;
+  return a.dim == 2 ? launch_resid_d<true, false>(a, sm, st) : launch_resid_d<false, false>(a, sm, st);
 }
 
 template <int LOGN, int LOGC> static cudaError_t launch_inv_k(const InvUpdArgs& a, cudaStream_t st) {

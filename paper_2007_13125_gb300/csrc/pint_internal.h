@@ -20,8 +20,10 @@ struct ResidFwdArgs {
   const float* s;                          // kappa^{i/N}, i < N
   const float2* tw;                        // exp(-2 pi i m / N), m < N
   int N, M, mx, dim, k, C, logC;
-  float c_hi[kMaxK + 1], c_lo[kMaxK + 1];  // c_0 (incl. stencil centre), c_j = omega_j tau^-alpha
-  float gx_hi, gx_lo, gy_hi, gy_lo;        // 1/hx^2, 1/hy^2
+  float c_hi[kMaxK + 1], c_lo[kMaxK + 1];  // c_0 (FD: incl. stencil centre), c_j = omega_j tau^-alpha
+  float gx_hi, gx_lo, gy_hi, gy_lo;        // off-diagonal Laplacian weights: 1/h^2 (FD), 1/h (P1)
+  int fem;                                 // P1 FEM (1D): time terms act on M_h U, centre 2/h
+  float m_hi, m_lo;                        // P1 FEM: h/6 (mass matrix off-diagonal)
 };
 
 // MIXED: inverse DFT, times 1/(N kappa^{i/N}), U += c (double-float), norms.
@@ -77,6 +79,8 @@ struct RhsArgs {
   double gx, gy;
   double a[kMaxK];                         // a_n, n = 1..k-1
   double bt[kMaxK][kMaxK];                 // b_{l,n} tau^l
+  int fem;                                 // P1 FEM: A v -> K_h v, v -> M_h v in the beta term
+  double mass6;                            // h/6
 };
 
 // ---- spatial kernels (kernels_space.cu) ----
@@ -91,6 +95,8 @@ template <typename T> struct AxisArgs {
   const void* sigma;                       // T2 [N/2+1] (op 1)
   const T* lam_axis;                       // [n] eigenvalues along this axis (op 1)
   const T* lam_other;                      // mode 1: [P] eigenvalues of the other axis
+  const T* mu_axis;                        // P1 FEM: [n] mass eigenvalues along this axis (divisor
+                                           // sigma_j mu_p + lam_p), else null
   T scale;                                 // op 1 divisor scale
   int lines_per_j;                         // op 1: j = line / lines_per_j
   const void* tw;                          // exp(-2 pi i m / L), L = 2(n+1)
@@ -116,7 +122,7 @@ size_t resid_fwd_smem(int N, int C);
 size_t inv_upd_smem(int N, int C);
 template <typename T> size_t direct_smem(int N, int C);
 size_t toep_smem(int N, int C);
-template <typename T> size_t axis_smem(int n, int C);
+template <typename T> size_t axis_smem(int n, int C, bool has_mu = false);
 
 cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st);
 cudaError_t launch_inv_upd(const InvUpdArgs& a, cudaStream_t st);

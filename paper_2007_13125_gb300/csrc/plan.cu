@@ -33,6 +33,10 @@ void set_last_error(const char* msg) { g_err = msg; }
 
 static pint_status cuda_fail(cudaError_t e, const char* where) {
   g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  // the error is reported through the status; clear the runtime's per-thread error so that a
+  // recoverable one (e.g. an over-sized launch request) does not surface in the caller's next
+  // unrelated CUDA call (a sticky error stays regardless)
+  (void)cudaGetLastError();
   return PINT_ECUDA;
 }
 #define PINT_CUDA(call)                                        \
@@ -287,21 +291,35 @@ pint_status build_tables(pint_plan p, DevTables<T>& t) {
   V* dsig;
   if ((s = upload(p, &dsig, sig)) != PINT_OK) return s;
   t.sigma = dsig;
-  auto lam_of = [](int m) {
+  // eigenvalues of the discrete Laplacian on sin(q pi x): (4/h^2) sin^2(q pi h/2) (FD stencil),
+  // (4/h) sin^2(q pi h/2) (P1 stiffness); P1 mass: (h/3)(2 + cos(q pi h))
+  const bool fem = p->fem;
+  auto lam_of = [fem](int m) {
     std::vector<T> l(m);
     const double h = 1.0 / (m + 1);
     for (int q = 1; q <= m; ++q) {
       double sn, cs;
       sincospi(0.5 * q * h, &sn, &cs);
-      l[q - 1] = (T)(4.0 / (h * h) * sn * sn);
+      l[q - 1] = (T)((fem ? 4.0 / h : 4.0 / (h * h)) * sn * sn);
     }
     return l;
+  };
+  auto mu_of = [](int m) {
+    std::vector<T> u(m);
+    const double h = 1.0 / (m + 1);
+    for (int q = 1; q <= m; ++q) {
+      double sn, cs;
+      sincospi((double)q * h, &sn, &cs);
+      u[q - 1] = (T)(h / 3.0 * (2.0 + cs));
+    }
+    return u;
   };
   std::vector<V> twx = tw_of(2 * (p->mx + 1));
   V* dtwx;
   if ((s = upload(p, &dtwx, twx)) != PINT_OK) return s;
   t.tw_x = dtwx;
   if ((s = upload(p, &t.lam_x, lam_of(p->mx))) != PINT_OK) return s;
+  if (fem && (s = upload(p, &t.mu_x, mu_of(p->mx))) != PINT_OK) return s;
   if (p->dim == 2) {
     std::vector<V> twy = tw_of(2 * (p->my + 1));
     V* dtwy;
@@ -366,6 +384,9 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   if (d->eig == PINT_EIG_CLOSED_FORM && d->alpha != 1.0 && d->precision != PINT_MIXED)
     return fail(PINT_EINVAL, "CLOSED_FORM eigenvalues with alpha < 1 need the residual form (PINT_MIXED)");
   if (d->ysolve < 0 || d->ysolve > 3) return fail(PINT_EINVAL, "bad ysolve variant");
+  if (d->space != PINT_SPACE_FD && d->space != PINT_SPACE_FEM_P1) return fail(PINT_EINVAL, "bad space discretisation");
+  if (d->space == PINT_SPACE_FEM_P1 && (d->grid.dim != 1 || d->precision != PINT_MIXED))
+    return fail(PINT_EINVAL, "P1 finite elements are supported in 1D with PINT_MIXED");
   pint_plan p = new pint_plan_s();
   p->alloc = A;
   p->k = d->k; p->alpha = d->alpha; p->kappa = d->kappa; p->tau = d->tau; p->N = d->N;
@@ -373,13 +394,15 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   p->M = p->mx * p->my;
   p->prec = d->precision; p->eig = d->eig;
   p->cq = d->alpha != 1.0;
+  p->fem = d->space == PINT_SPACE_FEM_P1;
   const int N = p->N, M = p->M;
   p->omega.resize(N);
   time_weights(p->k, p->alpha, N, p->omega.data());
   table1(p->k, p->a, p->b);
   eigenvalues(p->k, p->alpha, p->kappa, N, p->eig, p->omega, p->g);
   const double hx = 1.0 / (p->mx + 1), hy = 1.0 / (p->my + 1);
-  p->gx = 1.0 / (hx * hx);
+  // off-diagonal weight of the discrete Laplacian: 1/h^2 (FD stencil), 1/h (P1 stiffness)
+  p->gx = p->fem ? 1.0 / hx : 1.0 / (hx * hx);
   p->gy = p->dim == 2 ? 1.0 / (hy * hy) : 0.0;
 
   auto bail = [&](pint_status st) { destroy_plan(p); return st; };
@@ -498,6 +521,11 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
     const double hx = 1.0 / (p->mx + 1), hy = 1.0 / (p->my + 1);
     double lmin = 4.0 / (hx * hx) * std::pow(std::sin(M_PI * hx / 2), 2);
     double lmax = 4.0 / (hx * hx);
+    if (p->fem) {
+      // generalized eigenvalues (stiffness over mass) of the P1 pencil, q = 1 and q = mx
+      lmin = 12.0 / (hx * hx) * std::pow(std::sin(M_PI * hx / 2), 2) / (2.0 + std::cos(M_PI * hx));
+      lmax = 12.0 / (hx * hx) * std::pow(std::sin(M_PI * hx * p->mx / 2), 2) / (2.0 + std::cos(M_PI * hx * p->mx));
+    }
     if (p->dim == 2) {
       lmin += 4.0 / (hy * hy) * std::pow(std::sin(M_PI * hy / 2), 2);
       lmax += 4.0 / (hy * hy);
@@ -519,7 +547,7 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
 extern "C" pint_status pint_plan_create(int k, double alpha, double kappa, double tau, int N,
                                         const pint_grid* grid, pint_precision precision, pint_plan* out) {
   if (!grid) return fail(PINT_EINVAL, "grid is NULL");
-  pint_plan_desc d;
+  pint_plan_desc d{};
   d.k = k; d.alpha = alpha; d.kappa = kappa; d.tau = tau; d.N = N; d.grid = *grid;
   d.precision = precision; d.eig = PINT_EIG_TRUNC_DFT; d.ysolve = 0;
   return pint_plan_create_desc(&d, out);
@@ -550,6 +578,8 @@ extern "C" pint_status pint_form_rhs(pint_plan p, const double* v, const double*
   a.v = v; a.f = f; a.fd = fderiv; a.F = Fhat; a.beta = p->beta;
   a.N = p->N; a.M = p->M; a.mx = p->mx; a.dim = p->dim; a.k = p->k;
   a.gx = p->gx; a.gy = p->gy;
+  a.fem = p->fem ? 1 : 0;
+  a.mass6 = 1.0 / (6.0 * (p->mx + 1));  // h/6
   for (int n = 0; n < kMaxK - 1; ++n) {
     a.a[n] = n < 5 ? p->a[n] : 0.0;
     for (int l = 1; l <= 4; ++l) a.bt[l][n] = p->b[l - 1][n] * std::pow(p->tau, l);
@@ -582,7 +612,7 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
   if (p->dim == 1) {
     AxisArgs<T> a{};
     a.S = p->S; a.n = p->mx; a.lines = J; a.mode = 0; a.P = 1; a.op = 1;
-    a.sigma = t.sigma; a.lam_axis = t.lam_x; a.lam_other = nullptr;
+    a.sigma = t.sigma; a.lam_axis = t.lam_x; a.lam_other = nullptr; a.mu_axis = t.mu_x;
     a.scale = (T)(2.0 * (p->mx + 1)); a.lines_per_j = 1; a.tw = t.tw_x;
     a.C = p->Cx; a.logC = ilog2c(p->Cx); a.ld = p->Cx + 1;
     return launch_axis(a, st);
@@ -678,7 +708,11 @@ pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   r.s = p->tf.s; r.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
   r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Cr; r.logC = ilog2c(p->Cr);
   const double ta = std::pow(p->tau, -p->alpha);
-  double c0 = 2.0 * p->gx + 2.0 * p->gy;
+  // FD: c_0 includes the stencil centre; P1: the time terms act on M_h U and the stiffness
+  // centre 2/h is applied separately (exact: h is a power of two)
+  double c0 = p->fem ? 0.0 : 2.0 * p->gx + 2.0 * p->gy;
+  r.fem = p->fem ? 1 : 0;
+  split_ff(1.0 / (6.0 * (p->mx + 1)), r.m_hi, r.m_lo);
   if (!p->cq) {
     r.k = p->k;
     c0 += p->omega[0] * ta;

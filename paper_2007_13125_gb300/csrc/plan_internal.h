@@ -20,6 +20,7 @@ template <typename T> struct DevTables {
   void* tw_y = nullptr;      // V[2(my+1)]
   T* lam_x = nullptr;        // [mx]
   T* lam_y = nullptr;        // [my]
+  T* mu_x = nullptr;         // [mx] mass-matrix eigenvalues (P1 FEM only)
 };
 
 // Source of a plan's device memory: cudaMalloc by default, or a sub-allocator (the server's
@@ -58,6 +59,7 @@ struct pint_plan_s {
   pint_precision prec;
   pint_eig_variant eig;
   bool cq;
+  bool fem;                         // P1 finite elements (1D): mass matrix in the time terms
   std::vector<double> omega;
   double a[5];
   double b[4][5];

@@ -22,6 +22,8 @@ PINT_ETIMEOUT, PINT_EAGAIN, PINT_EBUDGET, PINT_ENOTFOUND = 5, 6, 7, 8
 PINT_FP64, PINT_MIXED, PINT_FP32 = 0, 1, 2
 PINT_EIG_TRUNC_DFT, PINT_EIG_CLOSED_FORM = 0, 1
 PRECISIONS = {"fp64": PINT_FP64, "mixed": PINT_MIXED, "fp32": PINT_FP32}
+PINT_SPACE_FD, PINT_SPACE_FEM_P1 = 0, 1
+SPACES = {"fd": PINT_SPACE_FD, "fem": PINT_SPACE_FEM_P1}
 
 
 class PintError(RuntimeError):
@@ -37,7 +39,8 @@ class _Grid(ctypes.Structure):
 class _Desc(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("alpha", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("tau", ctypes.c_double), ("N", ctypes.c_int), ("grid", _Grid),
-                ("precision", ctypes.c_int), ("eig", ctypes.c_int), ("ysolve", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("eig", ctypes.c_int), ("ysolve", ctypes.c_int),
+                ("space", ctypes.c_int)]
 
 
 class _Req(ctypes.Structure):
@@ -199,10 +202,11 @@ class Plan:
     """Owns a pint_plan handle."""
 
     def __init__(self, k, alpha, kappa, tau, N, dim, mx, my=1, precision="mixed",
-                 eig=PINT_EIG_TRUNC_DFT, ysolve=0):
+                 eig=PINT_EIG_TRUNC_DFT, ysolve=0, space="fd"):
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        spc = SPACES[space] if isinstance(space, str) else int(space)
         d = _Desc(k, float(alpha), float(kappa), float(tau), int(N), _Grid(dim, mx, my if dim == 2 else 1),
-                  prec, eig, int(ysolve))
+                  prec, eig, int(ysolve), spc)
         h = _P()
         check(lib().pint_plan_create_desc(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -213,7 +217,8 @@ class Plan:
 
     @classmethod
     def for_problem(cls, p, precision="mixed", eig=PINT_EIG_TRUNC_DFT, ysolve=0):
-        return cls(p.k, p.alpha, p.kappa, p.tau, p.N, p.dim, p.mx, p.my, precision, eig, ysolve)
+        return cls(p.k, p.alpha, p.kappa, p.tau, p.N, p.dim, p.mx, p.my, precision, eig, ysolve,
+                   getattr(p, "space", "fd"))
 
     def close(self):
         if self.handle:
@@ -311,7 +316,8 @@ class Server:
         (read at admission; the caller keeps them alive until the request is polled)."""
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         d = _Desc(p.k, float(p.alpha), float(p.kappa), float(p.tau), int(p.N),
-                  _Grid(p.dim, p.mx, p.my if p.dim == 2 else 1), prec, PINT_EIG_TRUNC_DFT, 0)
+                  _Grid(p.dim, p.mx, p.my if p.dim == 2 else 1), prec, PINT_EIG_TRUNC_DFT, 0,
+                  SPACES[getattr(p, "space", "fd")])
         t = ctypes.c_uint64(0)
         if hasattr(v, "is_cuda"):
             req = _Req(d, float(tol), int(max_sweeps), 1)

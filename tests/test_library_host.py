@@ -66,3 +66,29 @@ def test_invalid_plans_rejected_before_device_use(pint):
             pint.Plan(*args)
         assert e.value.status == pint.PINT_EINVAL
     assert "status" in pint.status_string(1) or pint.status_string(1) == "PINT_EINVAL"
+
+
+def test_invalid_fem_plans_rejected_before_device_use(pint):
+    # P1 finite elements: 1D and PINT_MIXED only; an unknown space code is rejected too
+    for kw in [dict(dim=2, mx=31, my=31, precision="mixed", space="fem"),
+               dict(dim=1, mx=31, precision="fp64", space="fem"),
+               dict(dim=1, mx=31, precision="fp32", space="fem"),
+               dict(dim=1, mx=31, precision="mixed", space=7)]:
+        with pytest.raises(pint.PintError) as e:
+            pint.Plan(2, 1.0, 0.1, 0.01, 32, **kw)
+        assert e.value.status == pint.PINT_EINVAL
+
+
+def test_fem_load_vectors_are_exact_integrals():
+    # the input generator's load vectors (f, phi_i) against adaptive quadrature
+    import workloads
+    from scipy.integrate import quad
+    m = 31
+    h = 1.0 / (m + 1)
+    x = workloads.grid_points(m)
+    ls, lc = workloads.fem_load_sine(m, 3), workloads.fem_load_cos(m)
+    for i in (0, 9, 30):
+        hat = lambda t, i=i: max(0.0, 1.0 - abs(t - x[i]) / h)
+        qs = quad(lambda t: np.sin(3 * np.pi * t) * hat(t), x[i] - h, x[i] + h, points=[x[i]])[0]
+        qc = quad(lambda t: np.cos(t) * hat(t), x[i] - h, x[i] + h, points=[x[i]])[0]
+        assert abs(qs - ls[i]) < 1e-14 and abs(qc - lc[i]) < 1e-14

@@ -40,6 +40,7 @@ class Problem:
     f_space: np.ndarray                 # [M] phi(x)
     f_derivs0: np.ndarray               # [k-1] d^l g/dt^l (0), l = 0..k-2
     meta: dict = field(default_factory=dict)
+    space: str = "fd"                   # "fd" (grid samples) or "fem" (P1: nodal v, load vectors)
 
     @property
     def M(self) -> int:
@@ -200,4 +201,46 @@ def small_problem(dim=1, mx=31, N=32, k=2, alpha=1.0, kappa=0.1, T=1.0, seed=7,
         fs = mode_field(2, mx, my, 1, 2)
     p = make_problem(f"small_{dim}d_{mx}x{my}_N{N}_k{k}_a{alpha}", dim, mx, my, N, k, alpha, kappa,
                      T, v, time_kind, fs)
+    return p
+
+
+# ---------------------------------------------------------------------------
+# 1D P1 finite-element problems (nodal values of v; f given by its load vectors (f, phi_i))
+# ---------------------------------------------------------------------------
+
+
+def fem_load_sine(m: int, p: int) -> np.ndarray:
+    """(sin(p pi x), phi_i) for the hat functions of the uniform mesh with m interior nodes:
+    sin(p pi x_i) * 2 (1 - cos(p pi h)) / (p^2 pi^2 h), the exact integral."""
+    h = 1.0 / (m + 1)
+    w = p * np.pi
+    return np.sin(w * grid_points(m)) * 2.0 * (1.0 - np.cos(w * h)) / (w * w * h)
+
+
+def fem_load_cos(m: int) -> np.ndarray:
+    """(cos x, phi_i) = 2 cos(x_i) (1 - cos h) / h, the exact integral."""
+    h = 1.0 / (m + 1)
+    return 2.0 * np.cos(grid_points(m)) * (1.0 - np.cos(h)) / h
+
+
+def fem_problem(mx=63, N=32, k=2, alpha=1.0, kappa=0.1, T=1.0, seed=7, modes=8, data="modes") -> Problem:
+    """1D P1-FEM problems.
+    data = "modes":    v_h = random sine series (nodal values, seed), f = e^{-t} (sin(pi x) + 0.3 sin(3 pi x));
+    data = "example1": the data of the paper's Example 1 on this mesh: v_h = nodal values of the
+                       indicator of (0, 1/2) (1/2 at x = 1/2), f = e^t cos x."""
+    if data == "modes":
+        rng = np.random.default_rng(seed)
+        v = random_v(1, mx, 1, min(modes, mx), rng)
+        load = fem_load_sine(mx, 1) + 0.3 * fem_load_sine(mx, 3)
+        time_kind = "exp"
+    elif data == "example1":
+        x = grid_points(mx)
+        v = np.where(x < 0.5, 1.0, np.where(x == 0.5, 0.5, 0.0))
+        load = fem_load_cos(mx)
+        time_kind = "exp_growth"
+    else:
+        raise ValueError(data)
+    p = make_problem(f"fem1d_{data}_M{mx}_N{N}_k{k}_a{alpha}", 1, mx, 1, N, k, alpha, kappa, T, v,
+                     time_kind, load)
+    p.space = "fem"
     return p
