@@ -304,7 +304,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
     }
   }
   __syncthreads();
-  fft_forward(X, C, logC, N, tw);
+  // compiled transform shapes for the tile widths the plan picks at these N (uniform branch)
+  if (N == 256 && C == 16) fft_forward_ct<8, 4, 16>(X, tw);
+  else if (N == 512 && C == 16) fft_forward_ct<9, 4, 16>(X, tw);
+  else if (N == 1024 && C == 8) fft_forward_ct<10, 3, 8>(X, tw);
+  else fft_forward(X, C, logC, N, tw);
   store_half_spectrum(X, perm, a.S, N, M, C, logC, (int)blockIdx.x * P2);
 }
 
