@@ -165,7 +165,10 @@ WORKLOADS = {"heat2d": workloads.c2_heat2d, "heat1d": workloads.c1_heat1d,
              # Example 1's data (Sec. 4) with P1 finite elements at the paper's scale on a
              # power-of-two mesh: 1023 nodes, N = 128, T = 0.5, BDF3, kappa = 0.5
              "fem1d": lambda: workloads.fem_problem(mx=1023, N=128, k=3, alpha=1.0, kappa=0.5, T=0.5,
-                                                    data="example1")}
+                                                    data="example1"),
+             # periodic boundary conditions (FFT in space), the heat2d scale: 256 x 256, N = 256
+             "periodic2d": lambda: workloads.periodic_problem(dim=2, mx=256, my=256, N=256, k=4, alpha=1.0,
+                                                              kappa=0.05, seed=1, modes=32)}
 WORKLOAD = "heat2d"
 
 
@@ -187,7 +190,7 @@ def oracle_sample(p, budget_s: float = 15.0):
             fem.solve_sequential_fem(p.k, p.alpha, p.tau, Mh, Kh, p.v, f_full[:n_s], fd)
             return time.perf_counter() - t0
     else:
-        A = grid.laplacian(p.mx, p.my, p.dim)
+        A = grid.operator(p)
 
         def run(n_s):
             t0 = time.perf_counter()
@@ -362,10 +365,11 @@ def main():
     ap.add_argument("--per-sweep-launches", action="store_true",
                     help="launch sweeps one by one from the host instead of one graph per solve")
     ap.add_argument("--workload", default="heat2d",
-                    choices=["heat2d", "heat1d", "subdiff1d", "fem1d", "mix64", "serve"],
+                    choices=["heat2d", "heat1d", "subdiff1d", "fem1d", "periodic2d", "mix64", "serve"],
                     help="heat2d (default): 2D heat 255x255, N=256, BDF4; heat1d: M=63, N=64, BDF2; "
                          "subdiff1d: alpha=0.5, M=1023, N=1024, CQ-BDF3; fem1d: P1 FEM, Example 1 data, "
-                         "1023 nodes, N=128, BDF3; mix64: one graph launch over 64 "
+                         "1023 nodes, N=128, BDF3; periodic2d: periodic 256x256, N=256, BDF4; "
+                         "mix64: one graph launch over 64 "
                          "mixed problems; serve: Poisson request stream through the serving loop")
     ap.add_argument("--requests", type=int, default=100, help="serve: number of requests")
     args = ap.parse_args()

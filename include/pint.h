@@ -82,8 +82,12 @@ typedef enum { PINT_EIG_TRUNC_DFT = 0, PINT_EIG_CLOSED_FORM = 1 } pint_eig_varia
  * FEM_P1: piecewise-linear Galerkin finite elements on the uniform mesh (Sec. 4, the space
  *         discretisation of the paper's 1D tests): the time derivative acts through the mass
  *         matrix M_h = (h/6) tridiag(1, 4, 1) and the Laplacian is the stiffness matrix
- *         K_h = (1/h) tridiag(-1, 2, -1); unknowns are nodal values. 1D and PINT_MIXED only. */
-typedef enum { PINT_SPACE_FD = 0, PINT_SPACE_FEM_P1 = 1 } pint_space;
+ *         K_h = (1/h) tridiag(-1, 2, -1); unknowns are nodal values. 1D and PINT_MIXED only.
+ * PERIODIC: finite differences with periodic boundary conditions (the remark of Sec. 2.2: the
+ *         spatial systems are then diagonalised by the FFT): m points per axis, x_i = i/m,
+ *         h = 1/m, m a power of two in [8, 4096] (mx, and my in 2D); the 3-/5-point stencil
+ *         wraps around. Every precision. */
+typedef enum { PINT_SPACE_FD = 0, PINT_SPACE_FEM_P1 = 1, PINT_SPACE_PERIODIC = 2 } pint_space;
 
 typedef struct {
   int dim;  /* 1 or 2 */

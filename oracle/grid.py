@@ -11,6 +11,12 @@ interior points only, h = 1/(M_x + 1):
 A_h is symmetric positive definite, i.e. it satisfies the coercivity assumption of
 eq. (1.2). Its eigenvectors are the sampled sine modes sin(p pi x_i) with eigenvalues
 lambda_p = (4/h^2) sin^2(p pi h / 2) -- the textbook closed form used by the pins.
+
+Periodic boundary conditions (the remark of Sec. 2.2, where the spatial systems become FFT-
+diagonalisable): m points per axis, x_i = i/m, h = 1/m, the same stencil wrapping around
+(``laplacian_periodic``). A_h is then a symmetric circulant, positive semi-definite (the
+constant mode is its kernel), with eigenvectors e^{2 pi i p x} and eigenvalues
+(4/h^2) sin^2(pi p / m), p = 0..m-1.
 """
 from __future__ import annotations
 
@@ -42,3 +48,25 @@ def sine_eigenvalues(m: int) -> np.ndarray:
 def sine_mode(m: int, p: int) -> np.ndarray:
     x = np.arange(1, m + 1) / (m + 1)
     return np.sin(p * np.pi * x)
+
+
+def lap1d_periodic(m: int) -> sp.csr_matrix:
+    h = 1.0 / m
+    e = np.ones(m)
+    A = sp.diags([-e[1:], 2 * e, -e[1:]], [-1, 0, 1], format="lil")
+    A[0, m - 1] = -1.0
+    A[m - 1, 0] = -1.0
+    return A.tocsr() / (h * h)
+
+
+def laplacian_periodic(mx: int, my: int = 1, dim: int = 1) -> sp.csr_matrix:
+    if dim == 1:
+        return lap1d_periodic(mx)
+    return (sp.kron(sp.identity(my), lap1d_periodic(mx)) + sp.kron(lap1d_periodic(my), sp.identity(mx))).tocsr()
+
+
+def operator(p) -> sp.csr_matrix:
+    """A_h of a workloads.Problem: Dirichlet FD or periodic FD (by p.space)."""
+    if getattr(p, "space", "fd") == "periodic":
+        return laplacian_periodic(p.mx, p.my, p.dim)
+    return laplacian(p.mx, p.my, p.dim)

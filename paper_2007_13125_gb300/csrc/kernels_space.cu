@@ -259,6 +259,187 @@ template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t
 }
 
 // ---------------------------------------------------------------------------
+// Periodic axis (the remark of Sec. 2.2: with periodic boundary conditions the spatial systems are
+// diagonalised by the FFT itself). Lines of n points, n a power of two, x_i = i/n; the circulant
+// Laplacian (1/h^2)[-1 2 -1] has eigenvalues lambda_p = (4/h^2) sin^2(pi p/n) on e^{2 pi i p x}.
+// op 0: forward FFT of each line, spectrum stored in natural order;
+// op 1: forward FFT, divide by scale * (sigma_j + lambda_other + lambda_p), inverse FFT;
+// op 2: inverse FFT of a natural-order spectrum (unnormalised; the 1/(nx ny) sits in op 1's scale).
+// Same tile layout as k_axis (C lines, row pitch C + 1).
+// ---------------------------------------------------------------------------
+template <typename T> size_t axis_per_smem(int n, int C, int ld) {
+  return sizeof(typename c2<T>::t) * ((size_t)n * ld + n + C) + sizeof(T) * (size_t)n +
+         sizeof(unsigned short) * (size_t)n + 2 * sizeof(int) * C + 64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) k_axis_per(AxisArgs<T> a) {
+  using V = typename c2<T>::t;
+  constexpr int KR = axis_regs<T>();
+  constexpr int KB = 8;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int n = a.n, C = a.C, logC = a.logC, ld = a.ld, L = a.n;
+  V* X = reinterpret_cast<V*>(smraw);
+  V* tw = X + (size_t)L * ld;
+  V* dcol = tw + L;
+  T* lam = reinterpret_cast<T*>(dcol + C);
+  unsigned short* perm = reinterpret_cast<unsigned short*>(lam + n);
+  int* lj = reinterpret_cast<int*>(perm + L + (L & 1));
+  int* lp = lj + C;
+  const V* gtw = reinterpret_cast<const V*>(a.tw);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = gtw[i];
+  fft_perm_table(perm, L);
+  V* S = reinterpret_cast<V*>(a.S);
+  const int line0 = blockIdx.x * C;
+  const int per = a.mode == 0 ? a.lines_per_j : a.P;
+  for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+    const int line = line0 + cc;
+    lj[cc] = line / per;
+    lp[cc] = line - lj[cc] * per;
+  }
+  __syncthreads();
+  const T zero = T(0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int tot = n << logC;
+  auto gidx = [&](int cc, int i) -> size_t {  // element i of tile line cc in S
+    return a.mode == 0 ? (size_t)(line0 + cc) * n + i : ((size_t)lj[cc] * n + i) * a.P + lp[cc];
+  };
+  // op 2 on a tile too large for the register reordering: load straight into digit-reversed rows
+  const bool direct_perm = a.op == 2 && tot > KR * (int)blockDim.x;
+  auto row_of = [&](int i) { return direct_perm ? (int)perm[i] : i; };
+
+  // ---- load rows 0..n-1 in natural order (KB loads in flight per thread) ----
+  if (a.mode == 0) {
+    for (int cc = warp; cc < C; cc += nwarp) {
+      const bool ok = line0 + cc < a.lines;
+      for (int i0 = 0; i0 < n; i0 += 32 * KB) {
+        V v[KB];
+#pragma unroll
+        for (int t = 0; t < KB; ++t) {
+          const int i = i0 + lane + 32 * t;
+          v[t] = (ok && i < n) ? S[gidx(cc, i)] : mk(zero, zero);
+        }
+#pragma unroll
+        for (int t = 0; t < KB; ++t) {
+          const int i = i0 + lane + 32 * t;
+          if (i < n) X[(size_t)row_of(i) * ld + cc] = v[t];
+        }
+      }
+    }
+  } else {
+    for (int it0 = threadIdx.x; it0 < tot; it0 += KB * blockDim.x) {
+      V v[KB];
+#pragma unroll
+      for (int t = 0; t < KB; ++t) {
+        const int it = it0 + t * blockDim.x;
+        const int cc = it & (C - 1), i = it >> logC;
+        v[t] = (it < tot && line0 + cc < a.lines) ? S[gidx(cc, i)] : mk(zero, zero);
+      }
+#pragma unroll
+      for (int t = 0; t < KB; ++t) {
+        const int it = it0 + t * blockDim.x;
+        if (it < tot) X[(size_t)row_of(it >> logC) * ld + (it & (C - 1))] = v[t];
+      }
+    }
+  }
+  if (a.op == 1) {
+    const V* sigma = reinterpret_cast<const V*>(a.sigma);
+    for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+      V d = mk(zero, zero);
+      if (line0 + cc < a.lines) {
+        d = sigma[lj[cc]];
+        if (a.lam_other) d.x += a.lam_other[lp[cc]];
+      }
+      dcol[cc] = d;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = a.lam_axis[i];
+  }
+  __syncthreads();
+
+  // move row r to row map(r) through registers (lanes along lines: no bank conflicts);
+  // to_perm: natural -> digit-reversed (before an inverse), else digit-reversed -> natural
+  auto reorder = [&](bool to_perm) {
+    if (tot <= KR * (int)blockDim.x) {
+      V v[KR];
+#pragma unroll
+      for (int t = 0; t < KR; ++t) {
+        const int it = threadIdx.x + t * blockDim.x;
+        const int r = it >> logC;
+        if (it < tot) v[t] = X[(size_t)(to_perm ? r : perm[r]) * ld + (it & (C - 1))];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < KR; ++t) {
+        const int it = threadIdx.x + t * blockDim.x;
+        const int r = it >> logC;
+        if (it < tot) X[(size_t)(to_perm ? perm[r] : r) * ld + (it & (C - 1))] = v[t];
+      }
+      __syncthreads();
+      return true;
+    }
+    return false;
+  };
+
+  // forward transform (rows end digit-reversed), or for op 2 the natural-order spectrum moved to
+  // the digit-reversed rows the inverse transform consumes
+  if (a.op != 2) fft_forward(X, ld, logC, L, tw);
+  else if (!direct_perm) reorder(true);
+  if (a.op == 1) {
+    for (int it = threadIdx.x; it < tot; it += blockDim.x) {
+      const int cc = it & (C - 1), p = it >> logC;
+      const size_t pos = (size_t)perm[p] * ld + cc;
+      if (line0 + cc >= a.lines) { X[pos] = mk(zero, zero); continue; }
+      V d = dcol[cc];
+      d.x += lam[p];
+      d.x *= a.scale;
+      d.y *= a.scale;
+      const T inv = rcp(d.x * d.x + d.y * d.y);
+      X[pos] = cmulc(X[pos], mk(d.x * inv, d.y * inv));   // X / d
+    }
+    __syncthreads();
+  }
+  if (a.op == 0) {
+    if (!reorder(false)) {
+      // no room to reorder through registers: store through perm
+      for (int it = threadIdx.x; it < tot; it += blockDim.x) {
+        const int cc = it & (C - 1), i = it >> logC;
+        if (line0 + cc < a.lines) S[gidx(cc, i)] = X[(size_t)perm[i] * ld + cc];
+      }
+      return;
+    }
+  } else {
+    fft_inverse(X, ld, logC, L, tw);
+  }
+  // ---- store rows 0..n-1 (natural order) ----
+  if (a.mode == 0) {
+    for (int cc = warp; cc < C; cc += nwarp) {
+      if (line0 + cc >= a.lines) continue;
+      for (int i = lane; i < n; i += 32) S[gidx(cc, i)] = X[(size_t)i * ld + cc];
+    }
+  } else {
+    for (int it = threadIdx.x; it < tot; it += blockDim.x) {
+      const int cc = it & (C - 1), i = it >> logC;
+      if (line0 + cc < a.lines) S[gidx(cc, i)] = X[(size_t)i * ld + cc];
+    }
+  }
+}
+
+template <typename T> cudaError_t launch_axis_per(const AxisArgs<T>& a, cudaStream_t st) {
+  const size_t sm = axis_per_smem<T>(a.n, a.C, a.ld);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_axis_per<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  const int blocks = (a.lines + a.C - 1) / a.C;
+  const char* name = a.op == 1 ? (sizeof(T) == 8 ? "axis_solve_per_f64" : "axis_solve_per_f32")
+                               : (sizeof(T) == 8 ? "fft_per_f64" : "fft_per_f32");
+  prof_begin(name, st);
+  k_axis_per<T><<<blocks, kThreads, sm, st>>>(a);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Tridiagonal y-solve: d q_y - g (q_{y-1} + q_{y+1}) = b_y, d = sigma_j + lambda_p^x + 2g.
 // With r + 1/r = d/g, |r| < 1 (r = 1 + e/2 - sqrt(e + e^2/4), e = (sigma_j + lambda_p^x)/g,
 // evaluated without cancellation), the matrix is
@@ -382,5 +563,7 @@ template size_t axis_smem<float>(int, int, bool);
 template size_t axis_smem<double>(int, int, bool);
 template cudaError_t launch_axis<float>(const AxisArgs<float>&, cudaStream_t);
 template cudaError_t launch_axis<double>(const AxisArgs<double>&, cudaStream_t);
+template cudaError_t launch_axis_per<float>(const AxisArgs<float>&, cudaStream_t);
+template cudaError_t launch_axis_per<double>(const AxisArgs<double>&, cudaStream_t);
 
 }  // namespace pint

@@ -158,11 +158,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
   const bool valid = g < G && m < M;
   constexpr bool two_d = TWO_D, cq = CQ;
   const int xq = m % mx;
-  const bool hasW = valid && xq > 0, hasE = valid && xq < mx - 1;
-  const bool hasS = valid && two_d && m >= mx, hasN = valid && two_d && m + mx < M;
-  // x neighbours by shuffle when a warp holds 32 consecutive points of one level
+  // neighbour offsets (wrapping around on periodic axes) and which neighbours exist
+  const bool per = a.periodic != 0;
+  const int dW = xq > 0 ? -1 : mx - 1, dE = xq < mx - 1 ? 1 : 1 - mx;
+  const int dS = m >= mx ? -mx : M - mx, dN = m + mx < M ? mx : mx - M;
+  const bool hasW = valid && (xq > 0 || per), hasE = valid && (xq < mx - 1 || per);
+  const bool hasS = valid && two_d && (m >= mx || per), hasN = valid && two_d && (m + mx < M || per);
+  // x neighbours by shuffle when a warp holds 32 consecutive points of one level; a lane loads
+  // its neighbour itself at warp edges and where a periodic row wraps
   const bool shfl = P2 >= 32;
-  const bool ldW = hasW && (!shfl || lane == 0), ldE = hasE && (!shfl || lane == 31);
+  const bool ldW = hasW && (!shfl || lane == 0 || (per && xq == 0));
+  const bool ldE = hasE && (!shfl || lane == 31 || (per && xq == mx - 1));
   float* Xf = reinterpret_cast<float*>(X) + 2 * (q & (C - 1)) + (q >= C ? 1 : 0);
 
   auto load = [&](int i) {
@@ -170,15 +176,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
     const size_t idx = (size_t)i * M + m;
     v.uh = valid ? a.Uhi[idx] : 0.f;
     v.ul = valid ? a.Ulo[idx] : 0.f;
-    v.wh = ldW ? a.Uhi[idx - 1] : 0.f;
-    v.wl = ldW ? a.Ulo[idx - 1] : 0.f;
-    v.eh = ldE ? a.Uhi[idx + 1] : 0.f;
-    v.el = ldE ? a.Ulo[idx + 1] : 0.f;
+    v.wh = ldW ? a.Uhi[idx + dW] : 0.f;
+    v.wl = ldW ? a.Ulo[idx + dW] : 0.f;
+    v.eh = ldE ? a.Uhi[idx + dE] : 0.f;
+    v.el = ldE ? a.Ulo[idx + dE] : 0.f;
     if (two_d) {
-      v.sh = hasS ? a.Uhi[idx - mx] : 0.f;
-      v.sl = hasS ? a.Ulo[idx - mx] : 0.f;
-      v.nh = hasN ? a.Uhi[idx + mx] : 0.f;
-      v.nl = hasN ? a.Ulo[idx + mx] : 0.f;
+      v.sh = hasS ? a.Uhi[idx + dS] : 0.f;
+      v.sl = hasS ? a.Ulo[idx + dS] : 0.f;
+      v.nh = hasN ? a.Uhi[idx + dN] : 0.f;
+      v.nl = hasN ? a.Ulo[idx + dN] : 0.f;
     } else {
       v.sh = v.sl = v.nh = v.nl = 0.f;
     }
@@ -190,10 +196,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
       v.yl = 0.f;
     }
     if (FEM && cq) {
-      v.ywh = ldW ? a.yhi[idx - 1] : 0.f;
-      v.ywl = ldW ? a.ylo[idx - 1] : 0.f;
-      v.yeh = ldE ? a.yhi[idx + 1] : 0.f;
-      v.yel = ldE ? a.ylo[idx + 1] : 0.f;
+      v.ywh = ldW ? a.yhi[idx + dW] : 0.f;
+      v.ywl = ldW ? a.ylo[idx + dW] : 0.f;
+      v.yeh = ldE ? a.yhi[idx + dE] : 0.f;
+      v.yel = ldE ? a.ylo[idx + dE] : 0.f;
     } else {
       v.ywh = v.ywl = v.yeh = v.yel = 0.f;
     }
@@ -202,17 +208,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
     return v;
   };
 
-  // x neighbours of a per-point double-float value: adjacent lanes, or the values loaded at warp
-  // edges; zero beyond the Dirichlet boundary. (shfl is uniform over the CTA and then every warp
-  // is fully inside one level group.)
+  // x neighbours of a per-point double-float value: adjacent lanes, or the values this lane
+  // loaded itself (warp edges, periodic wrap); zero beyond a Dirichlet boundary. (shfl is
+  // uniform over the CTA and then every warp is fully inside one level group.)
   auto neighbours = [&](float ch, float cl, float ewh, float ewl, float eeh, float eel, float& wh, float& wl,
                         float& eh, float& el) {
     wh = ewh; wl = ewl; eh = eeh; el = eel;
     if (shfl) {
       const float uwh = __shfl_up_sync(0xffffffffu, ch, 1), uwl = __shfl_up_sync(0xffffffffu, cl, 1);
       const float ueh = __shfl_down_sync(0xffffffffu, ch, 1), uel = __shfl_down_sync(0xffffffffu, cl, 1);
-      if (lane != 0) { wh = uwh; wl = uwl; }
-      if (lane != 31) { eh = ueh; el = uel; }
+      if (!ldW) { wh = uwh; wl = uwl; }
+      if (!ldE) { eh = ueh; el = uel; }
     }
     if (!hasW) { wh = 0.f; wl = 0.f; }
     if (!hasE) { eh = 0.f; el = 0.f; }
@@ -238,9 +244,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
       h[t].lo = (valid && lev >= 0) ? a.Ulo[idx] : 0.f;
       if constexpr (FEM) {
         float wh, wl, eh, el;
-        neighbours(h[t].hi, h[t].lo, (ldW && lev >= 0) ? a.Uhi[idx - 1] : 0.f,
-                   (ldW && lev >= 0) ? a.Ulo[idx - 1] : 0.f, (ldE && lev >= 0) ? a.Uhi[idx + 1] : 0.f,
-                   (ldE && lev >= 0) ? a.Ulo[idx + 1] : 0.f, wh, wl, eh, el);
+        neighbours(h[t].hi, h[t].lo, (ldW && lev >= 0) ? a.Uhi[idx + dW] : 0.f,
+                   (ldW && lev >= 0) ? a.Ulo[idx + dW] : 0.f, (ldE && lev >= 0) ? a.Uhi[idx + dE] : 0.f,
+                   (ldE && lev >= 0) ? a.Ulo[idx + dE] : 0.f, wh, wl, eh, el);
         h[t] = mass(h[t].hi, h[t].lo, wh, wl, eh, el);
       }
     }
@@ -655,14 +661,20 @@ __global__ void k_rhs(RhsArgs a) {
   }
   double Av = 0.0;
   if (i0 < a.k - 1) {
+    // the stencil; on periodic axes the neighbours wrap around
     const int x = m % a.mx;
+    const bool per = a.periodic != 0;
     Av = 2.0 * a.gx * vm;
     if (x > 0) Av -= a.gx * a.v[m - 1];
+    else if (per) Av -= a.gx * a.v[m + a.mx - 1];
     if (x < a.mx - 1) Av -= a.gx * a.v[m + 1];
+    else if (per) Av -= a.gx * a.v[m + 1 - a.mx];
     if (a.dim == 2) {
       Av += 2.0 * a.gy * vm;
       if (m >= a.mx) Av -= a.gy * a.v[m - a.mx];
+      else if (per) Av -= a.gy * a.v[m - a.mx + a.M];
       if (m + a.mx < a.M) Av -= a.gy * a.v[m + a.mx];
+      else if (per) Av -= a.gy * a.v[m + a.mx - a.M];
     }
   }
   constexpr int B = 4;

@@ -24,6 +24,7 @@ struct ResidFwdArgs {
   float gx_hi, gx_lo, gy_hi, gy_lo;        // off-diagonal Laplacian weights: 1/h^2 (FD), 1/h (P1)
   int fem;                                 // P1 FEM (1D): time terms act on M_h U, centre 2/h
   float m_hi, m_lo;                        // P1 FEM: h/6 (mass matrix off-diagonal)
+  int periodic;                            // periodic boundary conditions: neighbours wrap around
 };
 
 // MIXED: inverse DFT, times 1/(N kappa^{i/N}), U += c (double-float), norms.
@@ -81,6 +82,7 @@ struct RhsArgs {
   double bt[kMaxK][kMaxK];                 // b_{l,n} tau^l
   int fem;                                 // P1 FEM: A v -> K_h v, v -> M_h v in the beta term
   double mass6;                            // h/6
+  int periodic;                            // periodic boundary conditions: neighbours wrap around
 };
 
 // ---- spatial kernels (kernels_space.cu) ----
@@ -134,6 +136,8 @@ size_t toep_ff_smem(int N, int C);
 constexpr int kToepFFMaxLog = 3;           // radix <= 8 for the double-float FFT (register budget)
 cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t st);
 template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t st);
+// periodic lines (complex FFT of n points): op 0 forward, 1 shifted solve, 2 inverse
+template <typename T> cudaError_t launch_axis_per(const AxisArgs<T>& a, cudaStream_t st);
 cudaError_t launch_tri(const TriArgs& a, cudaStream_t st);
 size_t tri_smem(int n, int C);
 

@@ -314,23 +314,34 @@ pint_status build_tables(pint_plan p, DevTables<T>& t) {
     }
     return u;
   };
-  std::vector<V> twx = tw_of(2 * (p->mx + 1));
+  // periodic axis of m points: eigenvalues (4 m^2) sin^2(pi q/m), q = 0..m-1, m-point twiddles
+  auto lam_per = [](int m) {
+    std::vector<T> l(m);
+    for (int q = 0; q < m; ++q) {
+      double sn, cs;
+      sincospi((double)q / m, &sn, &cs);
+      l[q] = (T)(4.0 * m * (double)m * sn * sn);
+    }
+    return l;
+  };
+  const bool per = p->periodic;
+  std::vector<V> twx = tw_of(per ? p->mx : 2 * (p->mx + 1));
   V* dtwx;
   if ((s = upload(p, &dtwx, twx)) != PINT_OK) return s;
   t.tw_x = dtwx;
-  if ((s = upload(p, &t.lam_x, lam_of(p->mx))) != PINT_OK) return s;
+  if ((s = upload(p, &t.lam_x, per ? lam_per(p->mx) : lam_of(p->mx))) != PINT_OK) return s;
   if (fem && (s = upload(p, &t.mu_x, mu_of(p->mx))) != PINT_OK) return s;
   if (p->dim == 2) {
-    std::vector<V> twy = tw_of(2 * (p->my + 1));
+    std::vector<V> twy = tw_of(per ? p->my : 2 * (p->my + 1));
     V* dtwy;
     if ((s = upload(p, &dtwy, twy)) != PINT_OK) return s;
     t.tw_y = dtwy;
-    if ((s = upload(p, &t.lam_y, lam_of(p->my))) != PINT_OK) return s;
+    if ((s = upload(p, &t.lam_y, per ? lam_per(p->my) : lam_of(p->my))) != PINT_OK) return s;
   }
   return PINT_OK;
 }
 
-pint_status validate(int k, double alpha, double kappa, double tau, int N, const pint_grid* g) {
+pint_status validate(int k, double alpha, double kappa, double tau, int N, const pint_grid* g, int space) {
   if (!g) return fail(PINT_EINVAL, "grid is NULL");
   if (k < 1 || k > kMaxK) return fail(PINT_EINVAL, "k must be in 1..6");
   if (!(alpha > 0.0 && alpha <= 1.0)) return fail(PINT_EINVAL, "alpha must be in (0, 1]");
@@ -340,6 +351,12 @@ pint_status validate(int k, double alpha, double kappa, double tau, int N, const
   if (alpha != 1.0 && N > 2048) return fail(PINT_EINVAL, "CQ (alpha < 1) supports N <= 2048");
   if (N <= k) return fail(PINT_EINVAL, "N must exceed k");
   if (g->dim != 1 && g->dim != 2) return fail(PINT_EINVAL, "grid.dim must be 1 or 2");
+  if (space == PINT_SPACE_PERIODIC) {
+    if (!pow2(g->mx) || g->mx < 8 || g->mx > 4096) return fail(PINT_EINVAL, "periodic: mx must be a power of two in [8, 4096]");
+    if (g->dim == 2 && (!pow2(g->my) || g->my < 8 || g->my > 4096))
+      return fail(PINT_EINVAL, "periodic: my must be a power of two in [8, 4096]");
+    return PINT_OK;
+  }
   if (!pow2(g->mx + 1) || g->mx < 3 || g->mx > 2047) return fail(PINT_EINVAL, "mx + 1 must be a power of two, 3 <= mx <= 2047");
   if (g->dim == 2 && (!pow2(g->my + 1) || g->my < 3 || g->my > 2047))
     return fail(PINT_EINVAL, "my + 1 must be a power of two, 3 <= my <= 2047");
@@ -377,14 +394,15 @@ extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan*
 
 pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A, pint_plan* out) {
   if (!d || !out) return fail(PINT_EINVAL, "NULL argument");
-  pint_status s = validate(d->k, d->alpha, d->kappa, d->tau, d->N, &d->grid);
+  pint_status s = validate(d->k, d->alpha, d->kappa, d->tau, d->N, &d->grid, d->space);
   if (s != PINT_OK) return s;
   if (d->precision < PINT_FP64 || d->precision > PINT_FP32) return fail(PINT_EINVAL, "bad precision");
   if (d->eig != PINT_EIG_TRUNC_DFT && d->eig != PINT_EIG_CLOSED_FORM) return fail(PINT_EINVAL, "bad eig variant");
   if (d->eig == PINT_EIG_CLOSED_FORM && d->alpha != 1.0 && d->precision != PINT_MIXED)
     return fail(PINT_EINVAL, "CLOSED_FORM eigenvalues with alpha < 1 need the residual form (PINT_MIXED)");
   if (d->ysolve < 0 || d->ysolve > 3) return fail(PINT_EINVAL, "bad ysolve variant");
-  if (d->space != PINT_SPACE_FD && d->space != PINT_SPACE_FEM_P1) return fail(PINT_EINVAL, "bad space discretisation");
+  if (d->space != PINT_SPACE_FD && d->space != PINT_SPACE_FEM_P1 && d->space != PINT_SPACE_PERIODIC)
+    return fail(PINT_EINVAL, "bad space discretisation");
   if (d->space == PINT_SPACE_FEM_P1 && (d->grid.dim != 1 || d->precision != PINT_MIXED))
     return fail(PINT_EINVAL, "P1 finite elements are supported in 1D with PINT_MIXED");
   pint_plan p = new pint_plan_s();
@@ -395,12 +413,15 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   p->prec = d->precision; p->eig = d->eig;
   p->cq = d->alpha != 1.0;
   p->fem = d->space == PINT_SPACE_FEM_P1;
+  p->periodic = d->space == PINT_SPACE_PERIODIC;
   const int N = p->N, M = p->M;
   p->omega.resize(N);
   time_weights(p->k, p->alpha, N, p->omega.data());
   table1(p->k, p->a, p->b);
   eigenvalues(p->k, p->alpha, p->kappa, N, p->eig, p->omega, p->g);
-  const double hx = 1.0 / (p->mx + 1), hy = 1.0 / (p->my + 1);
+  // mesh widths: 1/(m+1) for Dirichlet nodes, 1/m on a periodic axis
+  const double hx = p->periodic ? 1.0 / p->mx : 1.0 / (p->mx + 1);
+  const double hy = p->periodic ? 1.0 / p->my : 1.0 / (p->my + 1);
   // off-diagonal weight of the discrete Laplacian: 1/h^2 (FD stencil), 1/h (P1 stiffness)
   p->gx = p->fem ? 1.0 / hx : 1.0 / (hx * hx);
   p->gy = p->dim == 2 ? 1.0 / (hy * hy) : 0.0;
@@ -507,10 +528,21 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   // three CTAs per SM
   p->Cx = pick_cols((size_t)2 * (p->mx + 1) * ve, 64 * 1024, 16, 1);
   p->Cy = pick_cols((size_t)2 * (p->my + 1) * ve, 64 * 1024, 16, 1);
+  if (p->periodic) {
+    // periodic lines of m points; m * C within the registers of the in-tile reordering
+    const size_t rlim = (p->prec == PINT_FP64 ? 8 : 16) * (size_t)kThreads;
+    auto pc = [&](int m) {
+      int C = pick_cols((size_t)m * ve, 64 * 1024, 16, 1);
+      while (C > 1 && (size_t)m * C > rlim) C >>= 1;
+      return C;
+    };
+    p->Cx = pc(p->mx);
+    p->Cy = pc(p->my);
+  }
   p->Ctri = pick_cols((size_t)p->my * sizeof(float2), 72 * 1024, 32, 1);
   PINT_CUDA_B(cudaMemset(p->S, 0, JM * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2))));
   p->ysolve = 1;
-  if (p->dim == 2 && p->prec != PINT_FP64) {
+  if (p->dim == 2 && p->prec != PINT_FP64 && !p->periodic) {
     if (d->ysolve == 2) p->ysolve = 2;
     else if (d->ysolve == 3 && (s = autotune_ysolve(p)) != PINT_OK) return bail(s);
   }
@@ -530,6 +562,11 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
       lmin += 4.0 / (hy * hy) * std::pow(std::sin(M_PI * hy / 2), 2);
       lmax += 4.0 / (hy * hy);
     }
+    if (p->periodic) {
+      // circulant Laplacian: the constant mode has eigenvalue 0, the largest is 4/h^2 per axis
+      lmin = 0.0;
+      lmax = 4.0 * p->mx * (double)p->mx + (p->dim == 2 ? 4.0 * p->my * (double)p->my : 0.0);
+    }
     const double ta = std::pow(p->tau, -p->alpha);
     double smax = 0.0, dmin = 1e300;
     for (int j = 0; j <= N / 2; ++j) {
@@ -539,6 +576,12 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
     }
     const double eps = p->prec == PINT_FP64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
     p->q_floor = std::min(0.5, eps * (lmax + smax) / dmin / p->kappa);
+    if (p->periodic) {
+      // the constant mode (lambda = 0) is not damped in time: its WR contraction is
+      // kappa / (1 - kappa) (the k = 1 closed form kappa r^N / (1 - kappa r^N) at r = 1), a rate
+      // the observed update ratios of the first sweeps can underestimate
+      p->q_floor = std::max(p->q_floor, std::min(0.99, p->kappa / (1.0 - p->kappa)));
+    }
   }
   *out = p;
   return PINT_OK;
@@ -580,6 +623,7 @@ extern "C" pint_status pint_form_rhs(pint_plan p, const double* v, const double*
   a.gx = p->gx; a.gy = p->gy;
   a.fem = p->fem ? 1 : 0;
   a.mass6 = 1.0 / (6.0 * (p->mx + 1));  // h/6
+  a.periodic = p->periodic ? 1 : 0;
   for (int n = 0; n < kMaxK - 1; ++n) {
     a.a[n] = n < 5 ? p->a[n] : 0.0;
     for (int l = 1; l <= 4; ++l) a.bt[l][n] = p->b[l - 1][n] * std::pow(p->tau, l);
@@ -609,6 +653,31 @@ template <typename T> bool ysolve_tri(pint_plan p) { return sizeof(T) == 4 && p-
 template <typename T>
 cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
   const int J = p->N / 2 + 1;
+  if (p->periodic) {
+    // FFT diagonalisation: 1D one fused solve; 2D forward FFT along x, fused solve along y,
+    // inverse FFT along x (the 1/(mx my) normalisation in the solve's divisor)
+    AxisArgs<T> a{};
+    a.S = p->S; a.sigma = t.sigma;
+    // row pitch C + 1 keeps multi-line tiles free of bank conflicts; a one-line tile needs none
+    auto pitch = [](int C) { return C > 1 ? C + 1 : 1; };
+    if (p->dim == 1) {
+      a.n = p->mx; a.lines = J; a.mode = 0; a.P = 1; a.op = 1; a.lines_per_j = 1;
+      a.lam_axis = t.lam_x; a.scale = (T)p->mx; a.tw = t.tw_x;
+      a.C = p->Cx; a.logC = ilog2c(p->Cx); a.ld = pitch(p->Cx);
+      return launch_axis_per(a, st);
+    }
+    AxisArgs<T> ax{};
+    ax.S = p->S; ax.n = p->mx; ax.lines = J * p->my; ax.mode = 0; ax.P = 1; ax.op = 0;
+    ax.lines_per_j = p->my; ax.tw = t.tw_x; ax.C = p->Cx; ax.logC = ilog2c(p->Cx); ax.ld = pitch(p->Cx);
+    cudaError_t e = launch_axis_per(ax, st);
+    if (e != cudaSuccess) return e;
+    a.n = p->my; a.lines = J * p->mx; a.mode = 1; a.P = p->mx; a.op = 1; a.lines_per_j = p->mx;
+    a.lam_axis = t.lam_y; a.lam_other = t.lam_x; a.scale = (T)((double)p->mx * p->my);
+    a.tw = t.tw_y; a.C = p->Cy; a.logC = ilog2c(p->Cy); a.ld = pitch(p->Cy);
+    if ((e = launch_axis_per(a, st)) != cudaSuccess) return e;
+    ax.op = 2;
+    return launch_axis_per(ax, st);
+  }
   if (p->dim == 1) {
     AxisArgs<T> a{};
     a.S = p->S; a.n = p->mx; a.lines = J; a.mode = 0; a.P = 1; a.op = 1;
@@ -712,6 +781,7 @@ pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   // centre 2/h is applied separately (exact: h is a power of two)
   double c0 = p->fem ? 0.0 : 2.0 * p->gx + 2.0 * p->gy;
   r.fem = p->fem ? 1 : 0;
+  r.periodic = p->periodic ? 1 : 0;
   split_ff(1.0 / (6.0 * (p->mx + 1)), r.m_hi, r.m_lo);
   if (!p->cq) {
     r.k = p->k;

@@ -60,6 +60,7 @@ struct pint_plan_s {
   pint_eig_variant eig;
   bool cq;
   bool fem;                         // P1 finite elements (1D): mass matrix in the time terms
+  bool periodic;                    // periodic boundary conditions (FFT in space)
   std::vector<double> omega;
   double a[5];
   double b[4][5];

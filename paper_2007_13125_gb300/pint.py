@@ -22,8 +22,8 @@ PINT_ETIMEOUT, PINT_EAGAIN, PINT_EBUDGET, PINT_ENOTFOUND = 5, 6, 7, 8
 PINT_FP64, PINT_MIXED, PINT_FP32 = 0, 1, 2
 PINT_EIG_TRUNC_DFT, PINT_EIG_CLOSED_FORM = 0, 1
 PRECISIONS = {"fp64": PINT_FP64, "mixed": PINT_MIXED, "fp32": PINT_FP32}
-PINT_SPACE_FD, PINT_SPACE_FEM_P1 = 0, 1
-SPACES = {"fd": PINT_SPACE_FD, "fem": PINT_SPACE_FEM_P1}
+PINT_SPACE_FD, PINT_SPACE_FEM_P1, PINT_SPACE_PERIODIC = 0, 1, 2
+SPACES = {"fd": PINT_SPACE_FD, "fem": PINT_SPACE_FEM_P1, "periodic": PINT_SPACE_PERIODIC}
 
 
 class PintError(RuntimeError):

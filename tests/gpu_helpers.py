@@ -15,12 +15,12 @@ def torch_cuda():
 
 
 def oracle_solution(p, corrected=True):
-    A = grid.laplacian(p.mx, p.my, p.dim)
+    A = grid.operator(p)
     return sequential.solve_sequential(p.k, p.alpha, p.tau, A, p.v, p.f(), p.fderiv(), corrected)
 
 
 def oracle_rhs(p):
-    A = grid.laplacian(p.mx, p.my, p.dim)
+    A = grid.operator(p)
     return sequential.all_at_once_rhs(p.k, p.alpha, p.tau, A, p.v, p.f(), p.fderiv())
 
 

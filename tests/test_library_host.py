@@ -92,3 +92,11 @@ def test_fem_load_vectors_are_exact_integrals():
         qs = quad(lambda t: np.sin(3 * np.pi * t) * hat(t), x[i] - h, x[i] + h, points=[x[i]])[0]
         qc = quad(lambda t: np.cos(t) * hat(t), x[i] - h, x[i] + h, points=[x[i]])[0]
         assert abs(qs - ls[i]) < 1e-14 and abs(qc - lc[i]) < 1e-14
+
+
+def test_invalid_periodic_plans_rejected_before_device_use(pint):
+    # periodic axes take m a power of two in [8, 4096]
+    for kw in [dict(dim=1, mx=63), dict(dim=1, mx=4), dict(dim=2, mx=32, my=31), dict(dim=1, mx=8192)]:
+        with pytest.raises(pint.PintError) as e:
+            pint.Plan(2, 1.0, 0.1, 0.01, 32, precision="mixed", space="periodic", **kw)
+        assert e.value.status == pint.PINT_EINVAL

@@ -40,7 +40,8 @@ class Problem:
     f_space: np.ndarray                 # [M] phi(x)
     f_derivs0: np.ndarray               # [k-1] d^l g/dt^l (0), l = 0..k-2
     meta: dict = field(default_factory=dict)
-    space: str = "fd"                   # "fd" (grid samples) or "fem" (P1: nodal v, load vectors)
+    space: str = "fd"                   # "fd" (grid samples), "fem" (P1: nodal v, load vectors),
+                                        # "periodic" (grid samples at x_i = i/m, periodic axes)
 
     @property
     def M(self) -> int:
@@ -243,4 +244,43 @@ def fem_problem(mx=63, N=32, k=2, alpha=1.0, kappa=0.1, T=1.0, seed=7, modes=8, 
     p = make_problem(f"fem1d_{data}_M{mx}_N{N}_k{k}_a{alpha}", 1, mx, 1, N, k, alpha, kappa, T, v,
                      time_kind, load)
     p.space = "fem"
+    return p
+
+
+# ---------------------------------------------------------------------------
+# Periodic problems: m points per axis at x_i = i/m (periodic boundary conditions)
+# ---------------------------------------------------------------------------
+
+
+def periodic_points(m: int) -> np.ndarray:
+    return np.arange(m) / m
+
+
+def periodic_problem(dim=1, mx=32, N=32, k=2, alpha=1.0, kappa=0.1, T=1.0, seed=7, modes=6, my=None,
+                     time_kind="exp") -> Problem:
+    """v = random real Fourier series (modes 0..modes-1 per axis, coefficients / (1 + p^2) (seed)),
+    f = g(t) (cos 2 pi x + 0.5 sin 4 pi x) [(cos 2 pi y)] with g(t) = e^{-t} by default."""
+    rng = np.random.default_rng(seed)
+    my = mx if my is None else my
+    x = periodic_points(mx)
+    modes = min(modes, mx // 2)
+    if dim == 1:
+        v = np.zeros(mx)
+        for q in range(modes):
+            a, b = rng.standard_normal(2) / (1 + q * q)
+            v += a * np.cos(2 * np.pi * q * x) + b * np.sin(2 * np.pi * q * x)
+        fs = np.cos(2 * np.pi * x) + 0.5 * np.sin(4 * np.pi * x)
+    else:
+        y = periodic_points(my)
+        v = np.zeros((my, mx))
+        for qy in range(modes):
+            for qx in range(modes):
+                a, b = rng.standard_normal(2) / (1 + qx * qx + qy * qy)
+                v += a * np.outer(np.cos(2 * np.pi * qy * y), np.cos(2 * np.pi * qx * x)) \
+                    + b * np.outer(np.sin(2 * np.pi * qy * y), np.sin(2 * np.pi * qx * x))
+        v = v.reshape(-1)
+        fs = np.outer(np.cos(2 * np.pi * y), np.cos(2 * np.pi * x) + 0.5 * np.sin(4 * np.pi * x)).reshape(-1)
+    p = make_problem(f"periodic{dim}d_{mx}_N{N}_k{k}_a{alpha}", dim, mx, my, N, k, alpha, kappa, T, v,
+                     time_kind, fs)
+    p.space = "periodic"
     return p
