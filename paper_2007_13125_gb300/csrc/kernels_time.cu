@@ -142,7 +142,9 @@ struct ResidLevel {
 
 // FEM = P1 finite elements (1D): the time terms act on V = M_h U, the history registers hold V,
 // and the stiffness K_h U = (1/h)(2 U_i - U_{i-1} - U_{i+1}) replaces the FD stencil.
-template <int K, bool CQ, bool TWO_D, bool FEM>
+// PER = periodic axes: the stencil's neighbours wrap around (compile-time, so that Dirichlet
+// instances keep constant neighbour offsets).
+template <int K, bool CQ, bool TWO_D, bool FEM, bool PER>
 __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = a.N, C = a.C, M = a.M, logC = a.logC, mx = a.mx;
@@ -159,9 +161,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
   constexpr bool two_d = TWO_D, cq = CQ;
   const int xq = m % mx;
   // neighbour offsets (wrapping around on periodic axes) and which neighbours exist
-  const bool per = a.periodic != 0;
-  const int dW = xq > 0 ? -1 : mx - 1, dE = xq < mx - 1 ? 1 : 1 - mx;
-  const int dS = m >= mx ? -mx : M - mx, dN = m + mx < M ? mx : mx - M;
+  constexpr bool per = PER;
+  const int dW = (!per || xq > 0) ? -1 : mx - 1, dE = (!per || xq < mx - 1) ? 1 : 1 - mx;
+  const int dS = (!per || m >= mx) ? -mx : M - mx, dN = (!per || m + mx < M) ? mx : mx - M;
   const bool hasW = valid && (xq > 0 || per), hasE = valid && (xq < mx - 1 || per);
   const bool hasS = valid && two_d && (m >= mx || per), hasN = valid && two_d && (m + mx < M || per);
   // x neighbours by shuffle when a warp holds 32 consecutive points of one level; a lane loads
@@ -844,25 +846,26 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 
 static int tiles(int M, int C) { return (M + 2 * C - 1) / (2 * C); }
 
-template <int K, bool CQ, bool TWO_D, bool FEM>
+template <int K, bool CQ, bool TWO_D, bool FEM, bool PER>
 static cudaError_t launch_resid_k(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
-  cudaError_t e = set_smem(k_resid_fwd<K, CQ, TWO_D, FEM>, sm);
+  cudaError_t e = set_smem(k_resid_fwd<K, CQ, TWO_D, FEM, PER>, sm);
   if (e != cudaSuccess) return e;
   prof_begin("resid_fwd_ff", st);
-  k_resid_fwd<K, CQ, TWO_D, FEM><<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
+  k_resid_fwd<K, CQ, TWO_D, FEM, PER><<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
 }
 
-template <bool TWO_D, bool FEM> static cudaError_t launch_resid_d(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
-  if (a.yhi) return a.k == 0 ? launch_resid_k<0, true, TWO_D, FEM>(a, sm, st) : cudaErrorInvalidValue;
+template <bool TWO_D, bool FEM, bool PER>
+static cudaError_t launch_resid_d(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
+  if (a.yhi) return a.k == 0 ? launch_resid_k<0, true, TWO_D, FEM, PER>(a, sm, st) : cudaErrorInvalidValue;
   switch (a.k) {
-    case 1: return launch_resid_k<1, false, TWO_D, FEM>(a, sm, st);
-    case 2: return launch_resid_k<2, false, TWO_D, FEM>(a, sm, st);
-    case 3: return launch_resid_k<3, false, TWO_D, FEM>(a, sm, st);
-    case 4: return launch_resid_k<4, false, TWO_D, FEM>(a, sm, st);
-    case 5: return launch_resid_k<5, false, TWO_D, FEM>(a, sm, st);
-    case 6: return launch_resid_k<6, false, TWO_D, FEM>(a, sm, st);
+    case 1: return launch_resid_k<1, false, TWO_D, FEM, PER>(a, sm, st);
+    case 2: return launch_resid_k<2, false, TWO_D, FEM, PER>(a, sm, st);
+    case 3: return launch_resid_k<3, false, TWO_D, FEM, PER>(a, sm, st);
+    case 4: return launch_resid_k<4, false, TWO_D, FEM, PER>(a, sm, st);
+    case 5: return launch_resid_k<5, false, TWO_D, FEM, PER>(a, sm, st);
+    case 6: return launch_resid_k<6, false, TWO_D, FEM, PER>(a, sm, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -871,8 +874,10 @@ cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st) {
   // the neighbour terms assume exact power-of-two stencil coefficients
   if (a.gx_lo != 0.f || a.gy_lo != 0.f) return cudaErrorInvalidValue;
   const size_t sm = resid_fwd_smem(a.N, a.C);
-  if (a.fem) return a.dim == 1 ? launch_resid_d<false, true>(a, sm, st) : cudaErrorInvalidValue;
-  return a.dim == 2 ? launch_resid_d<true, false>(a, sm, st) : launch_resid_d<false, false>(a, sm, st);
+  if (a.fem) return a.dim == 1 && !a.periodic ? launch_resid_d<false, true, false>(a, sm, st) : cudaErrorInvalidValue;
+  if (a.periodic)
+    return a.dim == 2 ? launch_resid_d<true, false, true>(a, sm, st) : launch_resid_d<false, false, true>(a, sm, st);
+  return a.dim == 2 ? launch_resid_d<true, false, false>(a, sm, st) : launch_resid_d<false, false, false>(a, sm, st);
 }
 
 template <int LOGN, int LOGC> static cudaError_t launch_inv_k(const InvUpdArgs& a, cudaStream_t st) {
