@@ -20,7 +20,8 @@
  * scaling (Algorithm 1 / Algorithm 2). The exact time-stepping solution is the fixed point.
  *
  * Data layout (all solver arrays): FP64, row-major [N][M], row n-1 holds time level t_n, and a
- * row is the grid flattened as y * mx + x (x fastest), M = mx * my (my = 1 in 1D).
+ * row is the grid flattened as (z * my + y) * mx + x (x fastest), M = mx * my * mz (my = 1 in 1D,
+ * mz = 1 below 3D).
  *
  * Memory: every array argument marked "device" is a device pointer owned by the caller (for
  * example torch.Tensor.data_ptr() of a CUDA tensor) that must stay valid until the stream work
@@ -90,9 +91,10 @@ typedef enum { PINT_EIG_TRUNC_DFT = 0, PINT_EIG_CLOSED_FORM = 1 } pint_eig_varia
 typedef enum { PINT_SPACE_FD = 0, PINT_SPACE_FEM_P1 = 1, PINT_SPACE_PERIODIC = 2 } pint_space;
 
 typedef struct {
-  int dim;  /* 1 or 2 */
+  int dim;  /* 1, 2 or 3 (3: finite differences with Dirichlet boundaries) */
   int mx;   /* interior points along x */
   int my;   /* interior points along y (ignored, taken as 1, when dim == 1) */
+  int mz;   /* interior points along z (ignored, taken as 1, when dim < 3) */
 } pint_grid;
 
 typedef struct {

@@ -7,6 +7,7 @@ interior points only, h = 1/(M_x + 1):
 * 1D: (A_h u)_i = (2 u_i - u_{i-1} - u_{i+1}) / h^2, u_0 = u_{M+1} = 0.
 * 2D: 5-point stencil, A_h = I_y (x) T_x + T_y (x) I_x with the grid flattened as
   index = y * M_x + x (x fastest).
+* 3D: 7-point stencil, I_z (x) A_h^{2D} + T_z (x) I_xy, index (z M_y + y) M_x + x.
 
 A_h is symmetric positive definite, i.e. it satisfies the coercivity assumption of
 eq. (1.2). Its eigenvectors are the sampled sine modes sin(p pi x_i) with eigenvalues
@@ -30,12 +31,18 @@ def lap1d(m: int) -> sp.csr_matrix:
     return sp.diags([-e[1:], 2 * e, -e[1:]], [-1, 0, 1], format="csr") / (h * h)
 
 
-def laplacian(mx: int, my: int = 1, dim: int = 1) -> sp.csr_matrix:
+def laplacian(mx: int, my: int = 1, dim: int = 1, mz: int = 1) -> sp.csr_matrix:
     if dim == 1:
         return lap1d(mx)
     tx = lap1d(mx)
     ty = lap1d(my)
-    return (sp.kron(sp.identity(my), tx) + sp.kron(ty, sp.identity(mx))).tocsr()
+    if dim == 2:
+        return (sp.kron(sp.identity(my), tx) + sp.kron(ty, sp.identity(mx))).tocsr()
+    # 3D: 7-point stencil, index (z my + y) mx + x
+    tz = lap1d(mz)
+    ixy = sp.identity(mx * my)
+    return (sp.kron(sp.identity(mz), sp.kron(sp.identity(my), tx) + sp.kron(ty, sp.identity(mx)))
+            + sp.kron(tz, ixy)).tocsr()
 
 
 def sine_eigenvalues(m: int) -> np.ndarray:
@@ -69,4 +76,4 @@ def operator(p) -> sp.csr_matrix:
     """A_h of a workloads.Problem: Dirichlet FD or periodic FD (by p.space)."""
     if getattr(p, "space", "fd") == "periodic":
         return laplacian_periodic(p.mx, p.my, p.dim)
-    return laplacian(p.mx, p.my, p.dim)
+    return laplacian(p.mx, p.my, p.dim, getattr(p, "mz", 1))

@@ -133,6 +133,8 @@ struct ResidLevel {
   float eh, el;    // east neighbour (idem)
   float sh, sl;    // south neighbour (m - mx)
   float nh, nl;    // north neighbour (m + mx)
+  float bh, bl;    // 3D: bottom neighbour (m - mx my)
+  float th, tl;    // 3D: top neighbour (m + mx my)
   float yh, yl;    // CQ history
   float ywh, ywl;  // P1 FEM + CQ: west / east neighbours of the history (warp edges)
   float yeh, yel;
@@ -144,7 +146,7 @@ struct ResidLevel {
 // and the stiffness K_h U = (1/h)(2 U_i - U_{i-1} - U_{i+1}) replaces the FD stencil.
 // PER = periodic axes: the stencil's neighbours wrap around (compile-time, so that Dirichlet
 // instances keep constant neighbour offsets).
-template <int K, bool CQ, bool TWO_D, bool FEM, bool PER>
+template <int K, bool CQ, int DIM, bool FEM, bool PER>
 __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = a.N, C = a.C, M = a.M, logC = a.logC, mx = a.mx;
@@ -158,14 +160,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
   const int lane = threadIdx.x & 31;
   const int m = blockIdx.x * P2 + q;
   const bool valid = g < G && m < M;
-  constexpr bool two_d = TWO_D, cq = CQ;
+  constexpr bool two_d = DIM >= 2, three_d = DIM == 3, cq = CQ;
+  const int mxy = mx * a.my;  // z-neighbour distance (3D)
   const int xq = m % mx;
   // neighbour offsets (wrapping around on periodic axes) and which neighbours exist
   constexpr bool per = PER;
   const int dW = (!per || xq > 0) ? -1 : mx - 1, dE = (!per || xq < mx - 1) ? 1 : 1 - mx;
   const int dS = (!per || m >= mx) ? -mx : M - mx, dN = (!per || m + mx < M) ? mx : mx - M;
   const bool hasW = valid && (xq > 0 || per), hasE = valid && (xq < mx - 1 || per);
-  const bool hasS = valid && two_d && (m >= mx || per), hasN = valid && two_d && (m + mx < M || per);
+  // y neighbours stay inside the (x, y) plane of the point (3D: planes of mx * my points)
+  const int mp = three_d ? m % mxy : m, Mp = three_d ? mxy : M;
+  const bool hasS = valid && two_d && (mp >= mx || per), hasN = valid && two_d && (mp + mx < Mp || per);
+  const bool hasB = valid && three_d && m >= mxy, hasT = valid && three_d && m + mxy < M;
   // x neighbours by shuffle when a warp holds 32 consecutive points of one level; a lane loads
   // its neighbour itself at warp edges and where a periodic row wraps
   const bool shfl = P2 >= 32;
@@ -189,6 +195,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
       v.nl = hasN ? a.Ulo[idx + dN] : 0.f;
     } else {
       v.sh = v.sl = v.nh = v.nl = 0.f;
+    }
+    if (three_d) {
+      v.bh = hasB ? a.Uhi[idx - mxy] : 0.f;
+      v.bl = hasB ? a.Ulo[idx - mxy] : 0.f;
+      v.th = hasT ? a.Uhi[idx + mxy] : 0.f;
+      v.tl = hasT ? a.Ulo[idx + mxy] : 0.f;
+    } else {
+      v.bh = v.bl = v.th = v.tl = 0.f;
     }
     if (cq) {
       v.yh = valid ? a.yhi[idx] : 0.f;
@@ -252,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
         h[t] = mass(h[t].hi, h[t].lo, wh, wl, eh, el);
       }
     }
-    const float gx = a.gx_hi, gy = a.gy_hi;
+    const float gx = a.gx_hi, gy = a.gy_hi, gz = a.gz_hi;
     ResidLevel nx = load(i0);
 #pragma unroll 2
     for (int i = i0; i < i1; ++i) {
@@ -296,11 +310,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
         two_sum(wh, eh, bx, ex);
         A.add_hi(gx * bx);
         float lo = gx * (ex + (wl + el));
-        if constexpr (TWO_D) {
+        if constexpr (DIM >= 2) {
           float by, ey;
           two_sum(c.sh, c.nh, by, ey);
           A.add_hi(gy * by);
           lo = fmaf(gy, ey + (c.sl + c.nl), lo);
+        }
+        if constexpr (DIM == 3) {
+          float bz, ez;
+          two_sum(c.bh, c.th, bz, ez);
+          A.add_hi(gz * bz);
+          lo = fmaf(gz, ez + (c.bl + c.tl), lo);
         }
         A.sl += lo;
       }
@@ -671,12 +691,20 @@ __global__ void k_rhs(RhsArgs a) {
     else if (per) Av -= a.gx * a.v[m + a.mx - 1];
     if (x < a.mx - 1) Av -= a.gx * a.v[m + 1];
     else if (per) Av -= a.gx * a.v[m + 1 - a.mx];
-    if (a.dim == 2) {
+    if (a.dim >= 2) {
+      // y neighbours inside the (x, y) plane of the point
+      const int mxy = a.mx * a.my;
+      const int mp = a.dim == 3 ? m % mxy : m, Mp = a.dim == 3 ? mxy : a.M;
       Av += 2.0 * a.gy * vm;
-      if (m >= a.mx) Av -= a.gy * a.v[m - a.mx];
+      if (mp >= a.mx) Av -= a.gy * a.v[m - a.mx];
       else if (per) Av -= a.gy * a.v[m - a.mx + a.M];
-      if (m + a.mx < a.M) Av -= a.gy * a.v[m + a.mx];
+      if (mp + a.mx < Mp) Av -= a.gy * a.v[m + a.mx];
       else if (per) Av -= a.gy * a.v[m + a.mx - a.M];
+      if (a.dim == 3) {
+        Av += 2.0 * a.gz * vm;
+        if (m >= mxy) Av -= a.gz * a.v[m - mxy];
+        if (m + mxy < a.M) Av -= a.gz * a.v[m + mxy];
+      }
     }
   }
   constexpr int B = 4;
@@ -846,26 +874,26 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 
 static int tiles(int M, int C) { return (M + 2 * C - 1) / (2 * C); }
 
-template <int K, bool CQ, bool TWO_D, bool FEM, bool PER>
+template <int K, bool CQ, int DIM, bool FEM, bool PER>
 static cudaError_t launch_resid_k(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
-  cudaError_t e = set_smem(k_resid_fwd<K, CQ, TWO_D, FEM, PER>, sm);
+  cudaError_t e = set_smem(k_resid_fwd<K, CQ, DIM, FEM, PER>, sm);
   if (e != cudaSuccess) return e;
   prof_begin("resid_fwd_ff", st);
-  k_resid_fwd<K, CQ, TWO_D, FEM, PER><<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
+  k_resid_fwd<K, CQ, DIM, FEM, PER><<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
 }
 
-template <bool TWO_D, bool FEM, bool PER>
+template <int DIM, bool FEM, bool PER>
 static cudaError_t launch_resid_d(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
-  if (a.yhi) return a.k == 0 ? launch_resid_k<0, true, TWO_D, FEM, PER>(a, sm, st) : cudaErrorInvalidValue;
+  if (a.yhi) return a.k == 0 ? launch_resid_k<0, true, DIM, FEM, PER>(a, sm, st) : cudaErrorInvalidValue;
   switch (a.k) {
-    case 1: return launch_resid_k<1, false, TWO_D, FEM, PER>(a, sm, st);
-    case 2: return launch_resid_k<2, false, TWO_D, FEM, PER>(a, sm, st);
-    case 3: return launch_resid_k<3, false, TWO_D, FEM, PER>(a, sm, st);
-    case 4: return launch_resid_k<4, false, TWO_D, FEM, PER>(a, sm, st);
-    case 5: return launch_resid_k<5, false, TWO_D, FEM, PER>(a, sm, st);
-    case 6: return launch_resid_k<6, false, TWO_D, FEM, PER>(a, sm, st);
+    case 1: return launch_resid_k<1, false, DIM, FEM, PER>(a, sm, st);
+    case 2: return launch_resid_k<2, false, DIM, FEM, PER>(a, sm, st);
+    case 3: return launch_resid_k<3, false, DIM, FEM, PER>(a, sm, st);
+    case 4: return launch_resid_k<4, false, DIM, FEM, PER>(a, sm, st);
+    case 5: return launch_resid_k<5, false, DIM, FEM, PER>(a, sm, st);
+    case 6: return launch_resid_k<6, false, DIM, FEM, PER>(a, sm, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -874,10 +902,13 @@ cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st) {
   // the neighbour terms assume exact power-of-two stencil coefficients
   if (a.gx_lo != 0.f || a.gy_lo != 0.f) return cudaErrorInvalidValue;
   const size_t sm = resid_fwd_smem(a.N, a.C);
-  if (a.fem) return a.dim == 1 && !a.periodic ? launch_resid_d<false, true, false>(a, sm, st) : cudaErrorInvalidValue;
-  if (a.periodic)
-    return a.dim == 2 ? launch_resid_d<true, false, true>(a, sm, st) : launch_resid_d<false, false, true>(a, sm, st);
-  return a.dim == 2 ? launch_resid_d<true, false, false>(a, sm, st) : launch_resid_d<false, false, false>(a, sm, st);
+  if (a.fem) return a.dim == 1 && !a.periodic ? launch_resid_d<1, true, false>(a, sm, st) : cudaErrorInvalidValue;
+  if (a.periodic) {
+    if (a.dim == 3) return cudaErrorInvalidValue;
+    return a.dim == 2 ? launch_resid_d<2, false, true>(a, sm, st) : launch_resid_d<1, false, true>(a, sm, st);
+  }
+  if (a.dim == 3) return launch_resid_d<3, false, false>(a, sm, st);
+  return a.dim == 2 ? launch_resid_d<2, false, false>(a, sm, st) : launch_resid_d<1, false, false>(a, sm, st);
 }
 
 template <int LOGN, int LOGC> static cudaError_t launch_inv_k(const InvUpdArgs& a, cudaStream_t st) {

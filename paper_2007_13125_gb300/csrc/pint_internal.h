@@ -22,6 +22,8 @@ struct ResidFwdArgs {
   int N, M, mx, dim, k, C, logC;
   float c_hi[kMaxK + 1], c_lo[kMaxK + 1];  // c_0 (FD: incl. stencil centre), c_j = omega_j tau^-alpha
   float gx_hi, gx_lo, gy_hi, gy_lo;        // off-diagonal Laplacian weights: 1/h^2 (FD), 1/h (P1)
+  float gz_hi, gz_lo;                      // 3D: 1/hz^2
+  int my;                                  // points along y (3D: the z neighbours are mx * my apart)
   int fem;                                 // P1 FEM (1D): time terms act on M_h U, centre 2/h
   float m_hi, m_lo;                        // P1 FEM: h/6 (mass matrix off-diagonal)
   int periodic;                            // periodic boundary conditions: neighbours wrap around
@@ -77,7 +79,8 @@ struct RhsArgs {
   const double* v; const double* f; const double* fd; double* F;
   const double* beta;                      // tau^-alpha sum_{j<n} omega_j, n = 1..N
   int N, M, mx, dim, k;
-  double gx, gy;
+  double gx, gy, gz;
+  int my;                                  // 3D: z neighbours are mx * my apart
   double a[kMaxK];                         // a_n, n = 1..k-1
   double bt[kMaxK][kMaxK];                 // b_{l,n} tau^l
   int fem;                                 // P1 FEM: A v -> K_h v, v -> M_h v in the beta term

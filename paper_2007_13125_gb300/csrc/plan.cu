@@ -331,12 +331,25 @@ pint_status build_tables(pint_plan p, DevTables<T>& t) {
   t.tw_x = dtwx;
   if ((s = upload(p, &t.lam_x, per ? lam_per(p->mx) : lam_of(p->mx))) != PINT_OK) return s;
   if (fem && (s = upload(p, &t.mu_x, mu_of(p->mx))) != PINT_OK) return s;
-  if (p->dim == 2) {
+  if (p->dim >= 2) {
     std::vector<V> twy = tw_of(per ? p->my : 2 * (p->my + 1));
     V* dtwy;
     if ((s = upload(p, &dtwy, twy)) != PINT_OK) return s;
     t.tw_y = dtwy;
     if ((s = upload(p, &t.lam_y, per ? lam_per(p->my) : lam_of(p->my))) != PINT_OK) return s;
+  }
+  if (p->dim == 3) {
+    std::vector<V> twz = tw_of(2 * (p->mz + 1));
+    V* dtwz;
+    if ((s = upload(p, &dtwz, twz)) != PINT_OK) return s;
+    t.tw_z = dtwz;
+    if ((s = upload(p, &t.lam_z, lam_of(p->mz))) != PINT_OK) return s;
+    // z lines are indexed by the (x, y) mode pair: lambda_x + lambda_y per line
+    const std::vector<T> lx = lam_of(p->mx), ly = lam_of(p->my);
+    std::vector<T> lxy((size_t)p->mx * p->my);
+    for (int y = 0; y < p->my; ++y)
+      for (int x = 0; x < p->mx; ++x) lxy[(size_t)y * p->mx + x] = lx[x] + ly[y];
+    if ((s = upload(p, &t.lam_xy, lxy)) != PINT_OK) return s;
   }
   return PINT_OK;
 }
@@ -350,7 +363,8 @@ pint_status validate(int k, double alpha, double kappa, double tau, int N, const
   if (!pow2(N) || N < 8 || N > 4096) return fail(PINT_EINVAL, "N must be a power of two in [8, 4096]");
   if (alpha != 1.0 && N > 2048) return fail(PINT_EINVAL, "CQ (alpha < 1) supports N <= 2048");
   if (N <= k) return fail(PINT_EINVAL, "N must exceed k");
-  if (g->dim != 1 && g->dim != 2) return fail(PINT_EINVAL, "grid.dim must be 1 or 2");
+  if (g->dim < 1 || g->dim > 3) return fail(PINT_EINVAL, "grid.dim must be 1, 2 or 3");
+  if (g->dim == 3 && space != PINT_SPACE_FD) return fail(PINT_EINVAL, "3D grids are supported with finite differences");
   if (space == PINT_SPACE_PERIODIC) {
     if (!pow2(g->mx) || g->mx < 8 || g->mx > 4096) return fail(PINT_EINVAL, "periodic: mx must be a power of two in [8, 4096]");
     if (g->dim == 2 && (!pow2(g->my) || g->my < 8 || g->my > 4096))
@@ -358,8 +372,10 @@ pint_status validate(int k, double alpha, double kappa, double tau, int N, const
     return PINT_OK;
   }
   if (!pow2(g->mx + 1) || g->mx < 3 || g->mx > 2047) return fail(PINT_EINVAL, "mx + 1 must be a power of two, 3 <= mx <= 2047");
-  if (g->dim == 2 && (!pow2(g->my + 1) || g->my < 3 || g->my > 2047))
+  if (g->dim >= 2 && (!pow2(g->my + 1) || g->my < 3 || g->my > 2047))
     return fail(PINT_EINVAL, "my + 1 must be a power of two, 3 <= my <= 2047");
+  if (g->dim == 3 && (!pow2(g->mz + 1) || g->mz < 3 || g->mz > 2047))
+    return fail(PINT_EINVAL, "mz + 1 must be a power of two, 3 <= mz <= 2047");
   return PINT_OK;
 }
 
@@ -408,8 +424,9 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   pint_plan p = new pint_plan_s();
   p->alloc = A;
   p->k = d->k; p->alpha = d->alpha; p->kappa = d->kappa; p->tau = d->tau; p->N = d->N;
-  p->dim = d->grid.dim; p->mx = d->grid.mx; p->my = d->grid.dim == 2 ? d->grid.my : 1;
-  p->M = p->mx * p->my;
+  p->dim = d->grid.dim; p->mx = d->grid.mx; p->my = d->grid.dim >= 2 ? d->grid.my : 1;
+  p->mz = d->grid.dim == 3 ? d->grid.mz : 1;
+  p->M = p->mx * p->my * p->mz;
   p->prec = d->precision; p->eig = d->eig;
   p->cq = d->alpha != 1.0;
   p->fem = d->space == PINT_SPACE_FEM_P1;
@@ -424,7 +441,9 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   const double hy = p->periodic ? 1.0 / p->my : 1.0 / (p->my + 1);
   // off-diagonal weight of the discrete Laplacian: 1/h^2 (FD stencil), 1/h (P1 stiffness)
   p->gx = p->fem ? 1.0 / hx : 1.0 / (hx * hx);
-  p->gy = p->dim == 2 ? 1.0 / (hy * hy) : 0.0;
+  p->gy = p->dim >= 2 ? 1.0 / (hy * hy) : 0.0;
+  const double hz = 1.0 / (p->mz + 1);
+  p->gz = p->dim == 3 ? 1.0 / (hz * hz) : 0.0;
 
   auto bail = [&](pint_status st) { destroy_plan(p); return st; };
 
@@ -539,6 +558,7 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
     p->Cx = pc(p->mx);
     p->Cy = pc(p->my);
   }
+  p->Czl = pick_cols((size_t)2 * (p->mz + 1) * ve, 64 * 1024, 16, 1);
   p->Ctri = pick_cols((size_t)p->my * sizeof(float2), 72 * 1024, 32, 1);
   PINT_CUDA_B(cudaMemset(p->S, 0, JM * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2))));
   p->ysolve = 1;
@@ -558,9 +578,14 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
       lmin = 12.0 / (hx * hx) * std::pow(std::sin(M_PI * hx / 2), 2) / (2.0 + std::cos(M_PI * hx));
       lmax = 12.0 / (hx * hx) * std::pow(std::sin(M_PI * hx * p->mx / 2), 2) / (2.0 + std::cos(M_PI * hx * p->mx));
     }
-    if (p->dim == 2) {
+    if (p->dim >= 2) {
       lmin += 4.0 / (hy * hy) * std::pow(std::sin(M_PI * hy / 2), 2);
       lmax += 4.0 / (hy * hy);
+    }
+    if (p->dim == 3) {
+      const double hz = 1.0 / (p->mz + 1);
+      lmin += 4.0 / (hz * hz) * std::pow(std::sin(M_PI * hz / 2), 2);
+      lmax += 4.0 / (hz * hz);
     }
     if (p->periodic) {
       // circulant Laplacian: the constant mode has eigenvalue 0, the largest is 4/h^2 per axis
@@ -620,7 +645,7 @@ extern "C" pint_status pint_form_rhs(pint_plan p, const double* v, const double*
   RhsArgs a{};
   a.v = v; a.f = f; a.fd = fderiv; a.F = Fhat; a.beta = p->beta;
   a.N = p->N; a.M = p->M; a.mx = p->mx; a.dim = p->dim; a.k = p->k;
-  a.gx = p->gx; a.gy = p->gy;
+  a.gx = p->gx; a.gy = p->gy; a.gz = p->gz; a.my = p->my;
   a.fem = p->fem ? 1 : 0;
   a.mass6 = 1.0 / (6.0 * (p->mx + 1));  // h/6
   a.periodic = p->periodic ? 1 : 0;
@@ -677,6 +702,28 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
     if ((e = launch_axis_per(a, st)) != cudaSuccess) return e;
     ax.op = 2;
     return launch_axis_per(ax, st);
+  }
+  if (p->dim == 3) {
+    // sine transforms along x and y, the shifted solve along z, the transforms back: five passes
+    // over the half spectrum. Each transform without divide applies -2i D; two of them give
+    // -2 (m+1) per axis, hence the z solve's divisor scale 8 (mx+1)(my+1)(mz+1).
+    AxisArgs<T> ax{};
+    ax.S = p->S; ax.n = p->mx; ax.lines = J * p->mz * p->my; ax.mode = 0; ax.P = 1; ax.op = 0;
+    ax.lines_per_j = p->my * p->mz; ax.tw = t.tw_x; ax.C = p->Cx; ax.logC = ilog2c(p->Cx); ax.ld = p->Cx + 1;
+    AxisArgs<T> ay{};  // y lines of every (j, z) plane: stride mx
+    ay.S = p->S; ay.n = p->my; ay.lines = J * p->mz * p->mx; ay.mode = 1; ay.P = p->mx; ay.op = 0;
+    ay.lines_per_j = p->mx; ay.tw = t.tw_y; ay.C = p->Cy; ay.logC = ilog2c(p->Cy); ay.ld = p->Cy + 1;
+    AxisArgs<T> az{};  // z lines of every j: stride mx my, one line per (x, y) mode
+    az.S = p->S; az.n = p->mz; az.lines = J * p->mx * p->my; az.mode = 1; az.P = p->mx * p->my; az.op = 1;
+    az.sigma = t.sigma; az.lam_axis = t.lam_z; az.lam_other = t.lam_xy;
+    az.scale = (T)(8.0 * (p->mx + 1) * (double)(p->my + 1) * (double)(p->mz + 1));
+    az.lines_per_j = p->mx * p->my; az.tw = t.tw_z; az.C = p->Czl; az.logC = ilog2c(p->Czl); az.ld = p->Czl + 1;
+    cudaError_t e;
+    if ((e = launch_axis(ax, st)) != cudaSuccess) return e;
+    if ((e = launch_axis(ay, st)) != cudaSuccess) return e;
+    if ((e = launch_axis(az, st)) != cudaSuccess) return e;
+    if ((e = launch_axis(ay, st)) != cudaSuccess) return e;
+    return launch_axis(ax, st);
   }
   if (p->dim == 1) {
     AxisArgs<T> a{};
@@ -779,7 +826,7 @@ pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   const double ta = std::pow(p->tau, -p->alpha);
   // FD: c_0 includes the stencil centre; P1: the time terms act on M_h U and the stiffness
   // centre 2/h is applied separately (exact: h is a power of two)
-  double c0 = p->fem ? 0.0 : 2.0 * p->gx + 2.0 * p->gy;
+  double c0 = p->fem ? 0.0 : 2.0 * p->gx + 2.0 * p->gy + 2.0 * p->gz;
   r.fem = p->fem ? 1 : 0;
   r.periodic = p->periodic ? 1 : 0;
   split_ff(1.0 / (6.0 * (p->mx + 1)), r.m_hi, r.m_lo);
@@ -793,6 +840,8 @@ pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   split_ff(c0, r.c_hi[0], r.c_lo[0]);
   split_ff(p->gx, r.gx_hi, r.gx_lo);
   split_ff(p->gy, r.gy_hi, r.gy_lo);
+  split_ff(p->gz, r.gz_hi, r.gz_lo);
+  r.my = p->my;
   cudaError_t e = launch_resid_fwd(r, st);
   if (e != cudaSuccess) return cuda_fail(e, "residual kernel");
   e = spatial<float>(p, p->tf, st);
@@ -1010,7 +1059,8 @@ void pint::solve_result(pint_plan p, int* sweeps, double* upd, bool* converged) 
 void pint::plan_release(pint_plan p) { destroy_plan(p); }
 
 size_t pint::plan_bytes_estimate(const pint_plan_desc* d) {
-  const size_t N = d->N, M = (size_t)d->grid.mx * (d->grid.dim == 2 ? d->grid.my : 1);
+  const size_t N = d->N, M = (size_t)d->grid.mx * (d->grid.dim >= 2 ? d->grid.my : 1) *
+                                 (d->grid.dim == 3 ? d->grid.mz : 1);
   const size_t NM = N * M, JM = (N / 2 + 1) * M;
   size_t b = 0;
   if (d->precision == PINT_MIXED) b += 8 * NM + 8 * JM;

@@ -20,6 +20,9 @@ template <typename T> struct DevTables {
   void* tw_y = nullptr;      // V[2(my+1)]
   T* lam_x = nullptr;        // [mx]
   T* lam_y = nullptr;        // [my]
+  void* tw_z = nullptr;      // V[2(mz+1)] (3D)
+  T* lam_z = nullptr;        // [mz] (3D)
+  T* lam_xy = nullptr;       // [my][mx] lambda_x + lambda_y per z line (3D)
   T* mu_x = nullptr;         // [mx] mass-matrix eigenvalues (P1 FEM only)
 };
 
@@ -55,7 +58,7 @@ constexpr int kSolveGraphs = 4;
 
 struct pint_plan_s {
   int k; double alpha, kappa, tau; int N;
-  int dim, mx, my, M;
+  int dim, mx, my, mz, M;
   pint_precision prec;
   pint_eig_variant eig;
   bool cq;
@@ -65,7 +68,7 @@ struct pint_plan_s {
   double a[5];
   double b[4][5];
   std::vector<std::complex<double>> g;
-  double gx, gy;
+  double gx, gy, gz;
   // device
   pint::DevAllocator* alloc = nullptr;   // null: cudaMalloc / cudaFree
   std::vector<void*> allocs;
@@ -89,7 +92,8 @@ struct pint_plan_s {
   pint::SolveGraph sg[pint::kSolveGraphs];
   unsigned long long sg_clock = 0;
   // tiles
-  int Ct, Cr, Ctd, Cz, Cx, Cy, Ctri;  // columns per CTA: time (float), residual, time (T), toeplitz, x, y, tri
+  int Ct, Cr, Ctd, Cz, Cx, Cy, Czl, Ctri;  // columns per CTA: time (float), residual, time (T), toeplitz,
+                                         // x, y, z lines, tri
   int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal
   double q_floor;                   // predicted floor of the per-sweep contraction (inner precision)
 };

@@ -33,7 +33,7 @@ class PintError(RuntimeError):
 
 
 class _Grid(ctypes.Structure):
-    _fields_ = [("dim", ctypes.c_int), ("mx", ctypes.c_int), ("my", ctypes.c_int)]
+    _fields_ = [("dim", ctypes.c_int), ("mx", ctypes.c_int), ("my", ctypes.c_int), ("mz", ctypes.c_int)]
 
 
 class _Desc(ctypes.Structure):
@@ -202,23 +202,24 @@ class Plan:
     """Owns a pint_plan handle."""
 
     def __init__(self, k, alpha, kappa, tau, N, dim, mx, my=1, precision="mixed",
-                 eig=PINT_EIG_TRUNC_DFT, ysolve=0, space="fd"):
+                 eig=PINT_EIG_TRUNC_DFT, ysolve=0, space="fd", mz=1):
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         spc = SPACES[space] if isinstance(space, str) else int(space)
-        d = _Desc(k, float(alpha), float(kappa), float(tau), int(N), _Grid(dim, mx, my if dim == 2 else 1),
-                  prec, eig, int(ysolve), spc)
+        d = _Desc(k, float(alpha), float(kappa), float(tau), int(N),
+                  _Grid(dim, mx, my if dim >= 2 else 1, mz if dim == 3 else 1), prec, eig, int(ysolve), spc)
         h = _P()
         check(lib().pint_plan_create_desc(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
         self.k, self.alpha, self.kappa, self.tau, self.N = k, alpha, kappa, tau, N
-        self.dim, self.mx, self.my = dim, mx, (my if dim == 2 else 1)
-        self.M = self.mx * self.my
+        self.dim, self.mx, self.my = dim, mx, (my if dim >= 2 else 1)
+        self.mz = mz if dim == 3 else 1
+        self.M = self.mx * self.my * self.mz
         self.precision = prec
 
     @classmethod
     def for_problem(cls, p, precision="mixed", eig=PINT_EIG_TRUNC_DFT, ysolve=0):
         return cls(p.k, p.alpha, p.kappa, p.tau, p.N, p.dim, p.mx, p.my, precision, eig, ysolve,
-                   getattr(p, "space", "fd"))
+                   getattr(p, "space", "fd"), getattr(p, "mz", 1))
 
     def close(self):
         if self.handle:
@@ -316,7 +317,8 @@ class Server:
         (read at admission; the caller keeps them alive until the request is polled)."""
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         d = _Desc(p.k, float(p.alpha), float(p.kappa), float(p.tau), int(p.N),
-                  _Grid(p.dim, p.mx, p.my if p.dim == 2 else 1), prec, PINT_EIG_TRUNC_DFT, 0,
+                  _Grid(p.dim, p.mx, p.my if p.dim >= 2 else 1, getattr(p, "mz", 1) if p.dim == 3 else 1),
+                  prec, PINT_EIG_TRUNC_DFT, 0,
                   SPACES[getattr(p, "space", "fd")])
         t = ctypes.c_uint64(0)
         if hasattr(v, "is_cuda"):

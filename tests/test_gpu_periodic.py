@@ -25,7 +25,8 @@ CASES = [
 def test_periodic_solve_matches_oracle(kw, precision, bar):
     torch = torch_cuda()
     p = workloads.periodic_problem(seed=13, **kw)
-    U, st, sweeps, upd = gpu_solve(p, torch, precision, tol=bar)
+    # the solver stops on an a-posteriori estimate of the error: ask for a tenth of the bar
+    U, st, sweeps, upd = gpu_solve(p, torch, precision, tol=0.1 * bar)
     assert rel_l2(U, oracle_solution(p)) <= bar, (sweeps, upd)
 
 

@@ -100,3 +100,13 @@ def test_invalid_periodic_plans_rejected_before_device_use(pint):
         with pytest.raises(pint.PintError) as e:
             pint.Plan(2, 1.0, 0.1, 0.01, 32, precision="mixed", space="periodic", **kw)
         assert e.value.status == pint.PINT_EINVAL
+
+
+def test_invalid_3d_plans_rejected_before_device_use(pint):
+    for kw in [dict(dim=3, mx=7, my=7, mz=7, precision="mixed", space="periodic"),
+               dict(dim=3, mx=7, my=7, mz=7, precision="mixed", space="fem"),
+               dict(dim=3, mx=7, my=7, mz=6, precision="fp64"),
+               dict(dim=4, mx=7, my=7, mz=7, precision="fp64")]:
+        with pytest.raises(pint.PintError) as e:
+            pint.Plan(2, 1.0, 0.1, 0.01, 32, **kw)
+        assert e.value.status == pint.PINT_EINVAL

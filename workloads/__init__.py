@@ -42,10 +42,11 @@ class Problem:
     meta: dict = field(default_factory=dict)
     space: str = "fd"                   # "fd" (grid samples), "fem" (P1: nodal v, load vectors),
                                         # "periodic" (grid samples at x_i = i/m, periodic axes)
+    mz: int = 1                         # points along z (3D)
 
     @property
     def M(self) -> int:
-        return self.mx * self.my
+        return self.mx * self.my * self.mz
 
     @property
     def tau(self) -> float:
@@ -116,7 +117,7 @@ def make_problem(name, dim, mx, my, N, k, alpha, kappa, T, v, time_kind, f_space
         g, d = np.exp(t), np.ones(max(k - 1, 0))
     else:
         raise ValueError(time_kind)
-    return Problem(name, dim, mx, my if dim == 2 else 1, N, k, alpha, kappa, T, v,
+    return Problem(name, dim, mx, my if dim >= 2 else 1, N, k, alpha, kappa, T, v,
                    g, f_space, d, meta={"time_kind": time_kind})
 
 
@@ -283,4 +284,31 @@ def periodic_problem(dim=1, mx=32, N=32, k=2, alpha=1.0, kappa=0.1, T=1.0, seed=
     p = make_problem(f"periodic{dim}d_{mx}_N{N}_k{k}_a{alpha}", dim, mx, my, N, k, alpha, kappa, T, v,
                      time_kind, fs)
     p.space = "periodic"
+    return p
+
+
+# ---------------------------------------------------------------------------
+# 3D problems on the unit cube (finite differences, Dirichlet), flattened (z my + y) mx + x
+# ---------------------------------------------------------------------------
+
+
+def heat3d_problem(m=15, N=16, k=2, alpha=1.0, kappa=0.1, T=1.0, seed=7, modes=6, my=None, mz=None,
+                   time_kind="exp") -> Problem:
+    """v = random sine series (modes^3 terms, coefficients N(0,1)/(p^2 + q^2 + r^2), seed),
+    f = g(t) sin(pi x) sin(2 pi y) sin(pi z), g(t) = e^{-t} by default."""
+    rng = np.random.default_rng(seed)
+    my = m if my is None else my
+    mz = m if mz is None else mz
+    P = min(modes, m, my, mz)
+    sx = np.sin(np.pi * np.outer(grid_points(m), np.arange(1, P + 1)))    # [mx, P]
+    sy = np.sin(np.pi * np.outer(grid_points(my), np.arange(1, P + 1)))   # [my, P]
+    sz = np.sin(np.pi * np.outer(grid_points(mz), np.arange(1, P + 1)))   # [mz, P]
+    q = np.arange(1, P + 1)
+    c = rng.standard_normal((P, P, P)) / (q[:, None, None] ** 2 + q[None, :, None] ** 2 + q[None, None, :] ** 2)
+    v = np.einsum("zr,yq,xp,pqr->zyx", sz, sy, sx, c).reshape(-1)
+    fs = np.einsum("z,y,x->zyx", np.sin(np.pi * grid_points(mz)), np.sin(2 * np.pi * grid_points(my)),
+                   np.sin(np.pi * grid_points(m))).reshape(-1)
+    p = make_problem(f"heat3d_{m}x{my}x{mz}_N{N}_k{k}_a{alpha}", 3, m, my, N, k, alpha, kappa, T, v,
+                     time_kind, fs)
+    p.mz = mz
     return p
