@@ -168,7 +168,10 @@ WORKLOADS = {"heat2d": workloads.c2_heat2d, "heat1d": workloads.c1_heat1d,
                                                     data="example1"),
              # periodic boundary conditions (FFT in space), the heat2d scale: 256 x 256, N = 256
              "periodic2d": lambda: workloads.periodic_problem(dim=2, mx=256, my=256, N=256, k=4, alpha=1.0,
-                                                              kappa=0.05, seed=1, modes=32)}
+                                                              kappa=0.05, seed=1, modes=32),
+             # 3D heat on the unit cube: 127^3 interior points, N = 128, BDF4 (2.1 GB per FP64 array)
+             "heat3d": lambda: workloads.heat3d_problem(m=127, N=128, k=4, alpha=1.0, kappa=0.05, seed=1,
+                                                        modes=8)}
 WORKLOAD = "heat2d"
 
 
@@ -179,6 +182,9 @@ def problem_for_rank(rank: int):
 
 def oracle_sample(p, budget_s: float = 15.0):
     """Time the CPU oracle on the first n_s time levels of the workload (bounded)."""
+    if p.dim == 3 and p.M > 300_000:
+        # the oracle's sparse LU of a 3D operator this large (fill-in) exceeds a bounded sample
+        raise RuntimeError(f"not run: sparse LU of the 3D operator ({p.M} unknowns) exceeds a bounded CPU sample")
     from oracle import fem, grid, sequential
     f_full = p.f()
     fd = p.fderiv()
@@ -365,10 +371,11 @@ def main():
     ap.add_argument("--per-sweep-launches", action="store_true",
                     help="launch sweeps one by one from the host instead of one graph per solve")
     ap.add_argument("--workload", default="heat2d",
-                    choices=["heat2d", "heat1d", "subdiff1d", "fem1d", "periodic2d", "mix64", "serve"],
+                    choices=["heat2d", "heat1d", "subdiff1d", "fem1d", "periodic2d", "heat3d", "mix64", "serve"],
                     help="heat2d (default): 2D heat 255x255, N=256, BDF4; heat1d: M=63, N=64, BDF2; "
                          "subdiff1d: alpha=0.5, M=1023, N=1024, CQ-BDF3; fem1d: P1 FEM, Example 1 data, "
                          "1023 nodes, N=128, BDF3; periodic2d: periodic 256x256, N=256, BDF4; "
+                         "heat3d: 127^3, N=128, BDF4; "
                          "mix64: one graph launch over 64 "
                          "mixed problems; serve: Poisson request stream through the serving loop")
     ap.add_argument("--requests", type=int, default=100, help="serve: number of requests")
