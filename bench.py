@@ -62,7 +62,7 @@ def algo_bytes(name: str, N: int, M: int) -> float:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the workload (`ncu --set full` of `bench.py --once mixed`), valid while the kernel's
 # source is unchanged (sha1 of its translation unit)
-NCU_TRAFFIC = {"resid_fwd_ff": (340.93e6, "kernels_time.cu", "91f56743f4519061aedccfbf6956c77348244a66")}
+NCU_TRAFFIC = {"resid_fwd_ff": (318.59e6, "kernels_time.cu", "dc0370d7664232048cd8c377e5c408bf737d1ac8")}
 
 
 def traffic_for(name: str):
