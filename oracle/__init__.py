@@ -25,6 +25,12 @@ Secondary routes, for pinning and for iterate-by-iterate references:
 * ``allatonce``  -- dense all-at-once matrices K and P_kappa (eq. (2.5),
                     eq. (3.9)), the dense paper-literal WR iteration
                     (eq. (2.4), eq. (3.8)) and per-mode contraction factors.
+* ``fem``        -- the P1 finite-element form used by the paper's 1D tests
+                    (Sec. 4): Tables 2 and 3.
+* ``nonlinear``  -- the semilinear scheme (eq. (4.4)) stepped with Newton's
+                    method, and Algorithm 3 (modified Newton with the
+                    Jacobian at the time average, inner WR of eq. (4.7)):
+                    Table 4.
 
 Parity status of each function is stated in its docstring; every function
 listed above is pinned by ``tests/test_oracle_*.py``.
