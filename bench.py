@@ -55,6 +55,12 @@ def algo_bytes(name: str, N: int, M: int) -> float:
         "axis_solve_f64": 32 * JM,
         "toeplitz_f64": 16 * NM,                # read U, write the history product
         "toeplitz_ff": 16 * NM,                 # read U (hi, lo), write the history (hi, lo)
+        "trivar_solve_f32": 32 * JM,            # read + write spectrum, read the two LU factors
+        "trivar_solve_f64": 64 * JM,
+        "trivar_factor": 16 * JM,               # write the two LU factors (FP32)
+        "nl_linearise": 8 * NM,                 # read U
+        "nl_rhs": 32 * NM,                      # read F_hat, U; write the linearised F_hat, U_{l-1}
+        "nl_norms": 16 * NM,                    # read U, U_{l-1}
     }
     return float(table.get(name, 0.0))
 
@@ -172,12 +178,18 @@ WORKLOADS = {"heat2d": workloads.c2_heat2d, "heat1d": workloads.c1_heat1d,
              # 3D heat on the unit cube: 127^3 interior points, N = 128, BDF4 (2.1 GB per FP64 array)
              "heat3d": lambda: workloads.heat3d_problem(m=127, N=128, k=4, alpha=1.0, kappa=0.05, seed=1,
                                                         modes=8)}
+# Example 4 (Sec. 4.3, Allen-Cahn, eps = 1) with P1 elements at the paper's scale on a power-of-two
+# mesh: 1023 nodes, N = 128 (the paper: 999 nodes, N = 100), T = 0.4, alpha = 0.75, CQ-BDF3, kappa = 0.1
+NL_WORKLOADS = {"allencahn1d": lambda: workloads.allen_cahn_problem("fem", mx=1023, N=128, k=3, alpha=0.75,
+                                                                    kappa=0.1, T=0.4, eps=1.0,
+                                                                    data="example4")}
+NL_NEWTON_TOL, NL_TOL = 1e-8, 1e-10
 WORKLOAD = "heat2d"
 
 
 def problem_for_rank(rank: int):
     # weak scaling: every rank solves its own instance (replicas; no exchange step)
-    return WORKLOADS[WORKLOAD]()
+    return (NL_WORKLOADS if WORKLOAD in NL_WORKLOADS else WORKLOADS)[WORKLOAD]()
 
 
 def oracle_sample(p, budget_s: float = 15.0):
@@ -185,9 +197,25 @@ def oracle_sample(p, budget_s: float = 15.0):
     if p.dim == 3 and p.M > 300_000:
         # the oracle's sparse LU of a 3D operator this large (fill-in) exceeds a bounded sample
         raise RuntimeError(f"not run: sparse LU of the 3D operator ({p.M} unknowns) exceeds a bounded CPU sample")
-    from oracle import fem, grid, sequential
+    from oracle import fem, grid, nonlinear, sequential
     f_full = p.f()
     fd = p.fderiv()
+    if isinstance(p, workloads.NlProblem):
+        Mass, A, w = nonlinear.space_ops(p.space, p.mx)
+
+        def run(n_s):
+            t0 = time.perf_counter()
+            Fh = nonlinear.nl_rhs(p.k, p.alpha, p.tau, Mass, A, w, p.g, p.v, f_full[:n_s], fd)
+            nonlinear.solve_sequential_nl(p.k, p.alpha, p.tau, Mass, A, w, p.g, Fh)
+            return time.perf_counter() - t0
+
+        t8 = run(8)
+        per = t8 / 8
+        n_s = int(max(8, min(p.N, budget_s / max(per, 1e-9))))
+        t = run(n_s)
+        return {"value": p.M * n_s / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"sequential FP64 semilinear CQ-BDF{p.k} (Newton per step, sparse LU) over the first "
+                          f"{n_s} of {p.N} time levels of the workload, {t:.2f} s"}
     if getattr(p, "space", "fd") == "fem":
         _, Mh, Kh = fem.fem_matrices(p.mx)
 
@@ -338,6 +366,170 @@ def run_serve(args) -> int:
     return 0
 
 
+def run_nl(args) -> int:
+    """Algorithm 3 on a semilinear workload: one step = F_hat of the semilinear scheme, U_0 = v and
+    the modified Newton iteration (inner WR solves to NL_TOL) until the outer estimate is below
+    NL_NEWTON_TOL. value = N M / device time per step (MIXED, inputs resident)."""
+    import torch
+    from paper_2007_13125_gb300 import Plan, pint
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    p = problem_for_rank(rank)
+    N, M = p.N, p.M
+    v_h, f_h, fd_h = p.v, p.f(), p.fderiv()
+    v = torch.tensor(v_h, device=dev)
+    f = torch.tensor(f_h, device=dev)
+    fd = torch.tensor(fd_h, device=dev)
+    F = torch.empty((N, M), dtype=torch.float64, device=dev)
+    U = torch.empty((N, M), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = Plan.for_problem(p, "mixed")
+    last = {}
+
+    def step(vv=v, ff=f, ffd=fd):
+        plan.nl_form_rhs(p.g, vv, ff, ffd, F, stream)
+        plan.initial_guess(vv, U, stream)
+        last["nl"] = plan.nl_solve(p.g, F, U, newton_tol=NL_NEWTON_TOL, max_steps=20, tol=NL_TOL, max_sweeps=40,
+                                   stream=stream)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(steps, per_step=False):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        lat = []
+        e0.record(stream)
+        for _ in range(steps):
+            if per_step:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            step()
+            if per_step:
+                b.record(stream)
+                lat.append((a, b))
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if pg is not None:
+            t = torch.tensor([ms], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, [a.elapsed_time(b) for a, b in lat]
+
+    clk = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clk.start()
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    t_clk0 = time.monotonic()
+    ms, lat = timed(args.steps, per_step=True)
+    clocks = clk.stop(t_clk0, time.monotonic())
+    st, sweeps, upds = last["nl"]
+    # launches per step: 2 (source) + 1 (U_0); per outer step 4 (linearise, rhs, factor, norms) and
+    # the inner solve graph: control init, conversion in / out, per sweep the sweep kernels + check
+    per_sweep = 3 + (1 if p.alpha != 1.0 else 0) + 1
+    launches = args.steps * (3 + sum(4 + 3 + s * per_sweep for s in sweeps))
+
+    # per-kernel CUDA-event times: the same step with sweeps launched one by one
+    pint.set_profiling(True)
+    pint.kernel_stats(reset=True)
+    timed(max(3, args.steps // 2))
+    kstats = pint.kernel_stats(reset=True)
+    pint.set_profiling(False)
+
+    # end to end: inputs from pinned host memory and U back, inside the timed region
+    v_pin = torch.tensor(v_h).pin_memory()
+    f_pin = torch.tensor(f_h).pin_memory()
+    fd_pin = torch.tensor(fd_h).pin_memory()
+    U_pin = torch.empty((N, M), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        v.copy_(v_pin, non_blocking=True)
+        f.copy_(f_pin, non_blocking=True)
+        fd.copy_(fd_pin, non_blocking=True)
+        step()
+        U_pin.copy_(U, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ke = max(10, args.steps)
+    e0.record(stream)
+    for _ in range(ke):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / ke
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    per_kernel = {}
+    tot_all = sum(t for _, t in kstats.values()) or 1.0
+    for name, (n, tot) in kstats.items():
+        avg_ms = tot / max(n, 1)
+        b = algo_bytes(name, N, M)
+        per_kernel[name] = {"launches": n, "avg_us": round(1e3 * avg_ms, 2), "share": round(tot / tot_all, 3),
+                            "algo_GBps": round(b / (avg_ms * 1e-3) / 1e9, 1) if b else None}
+    roofline = None
+    if kstats:
+        name, (n, tot) = max(kstats.items(), key=lambda kv: kv[1][1])
+        ach = algo_bytes(name, N, M) / (tot / n * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(ach / hbm_peak, 4), "traffic": traffic_for(name),
+                    "peak_source": peak_src + " hbm_gbs (STREAM-style copy)",
+                    "algo_bytes_per_launch": algo_bytes(name, N, M),
+                    "note": f"1D problem of {N * M * 8 / 1e6:.1f} MB per FP64 array: latency-bound, no bandwidth claim"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = oracle_sample(p)
+        except Exception as e:
+            cpu = {"error": str(e)}
+    dof_total = p.dof * world
+    line = {
+        "metric": METRIC, "value": dof_total / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
+        "config": {"workload": p.name, "dim": 1, "mx": p.mx, "N": N, "k": p.k, "alpha": p.alpha, "kappa": p.kappa,
+                   "eps": p.meta.get("eps"), "space": p.space, "dof_per_gpu": p.dof, "precision": "mixed",
+                   "newton_tol": NL_NEWTON_TOL, "inner_tol": NL_TOL, "outer_steps": len(sweeps),
+                   "inner_sweeps": sweeps, "outer_updates": upds,
+                   "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+                   "l2_policy": f"small problem: arrays of {N * M * 8 / 1e6:.1f} MB stay L2-resident between steps (latency figure)",
+                   "launch_mode": "per outer step: linearisation kernels + one CUDA graph for the inner WR solve",
+                   "parallelism": f"replicas x{world}", "kernels": per_kernel},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": dof_total / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": (v_h.size + f_h.size + fd_h.size) * 8,
+                "d2h_bytes_per_step": N * M * 8, "ms_per_step": ms_e2e},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
 def run_once(precision: str) -> int:
     import torch
     from paper_2007_13125_gb300 import Plan, pint
@@ -371,17 +563,21 @@ def main():
     ap.add_argument("--per-sweep-launches", action="store_true",
                     help="launch sweeps one by one from the host instead of one graph per solve")
     ap.add_argument("--workload", default="heat2d",
-                    choices=["heat2d", "heat1d", "subdiff1d", "fem1d", "periodic2d", "heat3d", "mix64", "serve"],
+                    choices=["heat2d", "heat1d", "subdiff1d", "fem1d", "periodic2d", "heat3d", "allencahn1d", "mix64",
+                             "serve"],
                     help="heat2d (default): 2D heat 255x255, N=256, BDF4; heat1d: M=63, N=64, BDF2; "
                          "subdiff1d: alpha=0.5, M=1023, N=1024, CQ-BDF3; fem1d: P1 FEM, Example 1 data, "
                          "1023 nodes, N=128, BDF3; periodic2d: periodic 256x256, N=256, BDF4; "
-                         "heat3d: 127^3, N=128, BDF4; "
+                         "heat3d: 127^3, N=128, BDF4; allencahn1d: Algorithm 3 on Example 4 (P1, 1023 nodes, "
+                         "N=128, alpha=0.75, CQ-BDF3); "
                          "mix64: one graph launch over 64 "
                          "mixed problems; serve: Poisson request stream through the serving loop")
     ap.add_argument("--requests", type=int, default=100, help="serve: number of requests")
     args = ap.parse_args()
     global WORKLOAD
-    WORKLOAD = args.workload if args.workload in WORKLOADS else "heat2d"
+    WORKLOAD = args.workload if (args.workload in WORKLOADS or args.workload in NL_WORKLOADS) else "heat2d"
+    if args.workload in NL_WORKLOADS and args.impl != "reference" and not args.once:
+        return run_nl(args)
     if args.workload == "mix64":
         return run_mix(args)
     if args.workload == "serve":

@@ -143,6 +143,8 @@ size_t pint_plan_workspace_bytes(pint_plan plan);
  * With PINT_SPACE_FEM_P1 the same formula holds in weak form: v holds the nodal values of v_h,
  * f and fderiv hold load vectors ((f(t_n), phi_i) and (d_t^l f(0), phi_i)), A v becomes K_h v
  * and the last term tau^-alpha sum_j omega_j M_h v.
+ * With a reaction term installed (pint_set_reaction) the starting correction uses the operator
+ * with it: a_n^(k) (f(0) - A v - w c v).
  * Enqueued on `stream`; asynchronous. */
 pint_status pint_form_rhs(pint_plan plan, const double* v, const double* f, const double* fderiv,
                           double* Fhat, void* stream);
@@ -196,6 +198,63 @@ pint_status pint_solve_result(pint_plan plan, int* sweeps_out, double* upd_rel_o
  * stream once. Returns PINT_ENOTCONV if any problem reached max_sweeps above tol. */
 pint_status pint_batch_solve(pint_plan* plans, int n, const double* const* Fhat, double* const* U,
                              double tol, int max_sweeps, int* sweeps_out, double* upd_out, void* stream);
+
+/* ---- reaction terms and semilinear problems (Sec. 4.3, Algorithm 3) ----
+ * 1D plans with Dirichlet boundaries (PINT_SPACE_FD in every precision, PINT_SPACE_FEM_P1 with
+ * PINT_MIXED); other plans return PINT_EINVAL. A reaction coefficient enters each row with the
+ * weight w = 1 (finite differences) or w = h (P1 elements: (c U_h, phi_i) and (g(U_h), phi_i) by
+ * nodal quadrature, h c_i U_i and h g(U_i)). */
+
+/* Install a space-varying reaction term in the plan's linear solves: A becomes A + w diag(c), so
+ * pint_wr_sweep, pint_solve, pint_solve_async and pint_batch_solve then solve
+ * (D_tau^alpha + A + w diag(c)) U = F_hat. c [M] device, FP64, copied before the call's stream
+ * work ends (the caller may reuse it afterwards); NULL removes the term. With the term present the
+ * shifted systems sigma_j M + A + w diag(c) of Algorithm 1 / 2 step 2 are no longer diagonalised by
+ * the sine transform: each frequency's tridiagonal system is solved by Gaussian elimination with
+ * LU factors computed here (FP64 arithmetic, stored in the plan's inner precision); sweeps then use
+ * the forward / backward substitutions. The elimination does not pivot: it is meant for
+ * A + w diag(c) positive definite (c > -lambda_min(A) / w suffices), the case of the linearised
+ * operators of Algorithm 3. Enqueued on `stream`. */
+pint_status pint_set_reaction(pint_plan plan, const double* c, void* stream);
+
+/* Cubic nonlinearity g(u) = c[0] + c[1] u + c[2] u^2 + c[3] u^3 of the semilinear problem
+ * D_t^alpha u + A u + g(u) = f (eq. (4.3)); the Allen-Cahn term of Example 4 is
+ * c = {0, -1/eps^2, 0, 1/eps^2}. */
+typedef struct { double c[4]; } pint_poly;
+
+/* F_hat of the semilinear scheme (eq. (4.4)): pint_form_rhs with the starting correction
+ * a_n^(k) (f(0) - A v - w g(v)) in place of a_n^(k) (f(0) - A v); arguments as there. The scheme
+ * is then the all-at-once system K U + w g(U) = F_hat. PINT_EINVAL while a reaction term is
+ * installed. Asynchronous on `stream`. */
+pint_status pint_nl_form_rhs(pint_plan plan, const pint_poly* g, const double* v, const double* f,
+                             const double* fderiv, double* Fhat, void* stream);
+
+#define PINT_NL_MAX_STEPS 64
+typedef struct {
+  int steps;                        /* outer (Newton) steps taken */
+  int sweeps[PINT_NL_MAX_STEPS];    /* inner WR sweeps of each outer step */
+  double upd[PINT_NL_MAX_STEPS];    /* ||U_l - U_{l-1}|| / ||U_l|| (space-time l2) of each step */
+} pint_nl_info;
+
+/* Algorithm 3 (modified Newton iteration, eqs. (4.6)-(4.7)): from the iterate in U (Algorithm 3
+ * starts from U_0^n = v: pint_initial_guess), step l = 1, 2, ...
+ *   Ubar = (1/N) sum_n U_{l-1}^n,  D = g'(Ubar)  (one spatial field for all levels),
+ *   solve (K + I (x) w D) W = F_hat - K U_{l-1} - w g(U_{l-1}) by the WR iteration from W_0 = 0,
+ *   U_l = U_{l-1} + W,
+ * where the inner solve is pint_solve of the plan with the reaction term w D installed (its
+ * stopping rule and tolerance `tol`, at most max_sweeps sweeps; one graph launch) applied to
+ * V = U_{l-1} + W. The linearised term carries +g'(Ubar), the sign of Newton's linearisation
+ * (eqs. (4.6)-(4.7) print -g'(Ubar); only + reproduces the contraction of Table 4). The outer
+ * loop stops by the rule of pint_solve applied to upd_l = ||U_l - U_{l-1}|| / ||U_l|| with
+ * newton_tol and no floor (upd_1 <= newton_tol / 100, or upd_l q / (1 - q) <= newton_tol with
+ * q = upd_l / upd_{l-1}). Fhat [N][M] device (pint_nl_form_rhs); U [N][M] device, in: initial
+ * iterate, out: U_l. info: optional host pointer. The solve installs w D in the plan's reaction
+ * slot and removes it before returning; PINT_EINVAL if a reaction term is already installed.
+ * Waits for `stream` once per outer step. Returns PINT_ENOTCONV
+ * if max_steps (<= PINT_NL_MAX_STEPS) outer steps did not meet newton_tol or an inner solve
+ * stopped at max_sweeps (U then holds the last iterate). */
+pint_status pint_nl_solve(pint_plan plan, const pint_poly* g, const double* Fhat, double* U, double newton_tol,
+                          int max_steps, double tol, int max_sweeps, pint_nl_info* info, void* stream);
 
 /* ---- serving: continuous batching of independent solves ----
  * A server owns a device-memory budget (reserved once at creation and sub-allocated, so admission

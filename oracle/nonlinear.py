@@ -200,42 +200,6 @@ def algorithm3(k, alpha, kappa, tau, Mass, A, w, c, Fhat, v, L, tol_inf=1e-12, m
     return its, counts
 
 
-# ---------------------------------------------------------------------------
-# Example 4 data
-# ---------------------------------------------------------------------------
-
-def _sine_load(omega, x, h):
-    """(sin(omega x), phi_i) for the P1 hat functions of a uniform mesh (exact)."""
-    return np.sin(omega * x) * 2.0 * (1.0 - np.cos(omega * h)) / (omega ** 2 * h)
-
-
-def example4_data(alpha, space="fem", m=999, N=100, T=0.4, eps=1.0):
-    """Example 4: u = t^2/Gamma(3) sin(2 pi x), f = D_t^alpha u - u_xx + (u^3 - u)/eps^2, v = 0.
-    D_t^alpha (t^2 / 2) = t^{2-alpha} / Gamma(3 - alpha). Returns (tau, v, F_t [N, m], F_der [2, m], c):
-    P1 loads (f(t_n), phi_i) exact (sin^3 = (3 sin - sin 3.) / 4), or point samples for finite
-    differences. F_der holds d_t^l f(0) for l = 0, 1 (both zero for alpha < 1: f ~ t^{2-alpha});
-    higher derivatives of f do not exist at t = 0 for alpha < 1, so k <= 3 there."""
-    h = 1.0 / (m + 1)
-    x = h * np.arange(1, m + 1)
-    tau = T / N
-    t = tau * np.arange(1, N + 1)
-    w2 = 2.0 * math.pi
-    if space == "fem":
-        s1 = _sine_load(w2, x, h)
-        s3 = (3.0 * s1 - _sine_load(3.0 * w2, x, h)) / 4.0
-    else:
-        s1 = np.sin(w2 * x)
-        s3 = s1 ** 3
-    amp = t ** 2 / 2.0
-    lin = t ** (2.0 - alpha) / math.gamma(3.0 - alpha) + w2 ** 2 * amp
-    F_t = lin[:, None] * s1[None, :] + (amp ** 3)[:, None] * s3[None, :] / eps ** 2 \
-        - amp[:, None] * s1[None, :] / eps ** 2
-    F_der = np.zeros((2, m))
-    if alpha == 1.0:
-        F_der[1] = s1  # d_t f(0): the t^{2-alpha} / Gamma(3-alpha) = t term
-    return tau, np.zeros(m), F_t, F_der, allen_cahn(eps)
-
-
 def l2_norm(space, Mass, x, m):
     """||x||_{L2(0,1)}: x^T M x for P1 elements, h sum x_i^2 for grid functions."""
     if space == "fem":

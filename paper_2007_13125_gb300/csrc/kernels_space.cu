@@ -15,6 +15,12 @@
 //
 // k_tri -- the y direction as a tridiagonal solve (after the x sine transform every line
 // (j, p) is a constant-coefficient system): thread per line, data staged in shared memory.
+//
+// k_trivar_factor / k_trivar_solve -- 1D shifted systems whose diagonal varies along x (a
+// reaction term, the linearised operator of Algorithm 3): no transform diagonalises them, so
+// each frequency's tridiagonal system is solved by Gaussian elimination without pivoting (the
+// systems are diagonally dominant up to the reaction term: sigma_j lies in the sector where the
+// BDF / CQ symbols live, and A_h + w diag(c) is positive definite for the reactions of interest).
 #include "fft.cuh"
 #include "pint_internal.h"
 
@@ -559,11 +565,106 @@ cudaError_t launch_tri(const TriArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---- variable-coefficient tridiagonal systems (thread per frequency j) ----
+template <typename T> struct cx_ops;
+template <> struct cx_ops<float> {
+  using V = float2;
+  static __device__ __forceinline__ V mul(V a, V b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+  }
+  static __device__ __forceinline__ V fms(V d, V a, V y) {  // d - a * y
+    return make_float2(fmaf(-a.x, y.x, fmaf(a.y, y.y, d.x)), fmaf(-a.x, y.y, fmaf(-a.y, y.x, d.y)));
+  }
+};
+template <> struct cx_ops<double> {
+  using V = double2;
+  static __device__ __forceinline__ V mul(V a, V b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+  }
+  static __device__ __forceinline__ V fms(V d, V a, V y) {
+    return make_double2(fma(-a.x, y.x, fma(a.y, y.y, d.x)), fma(-a.x, y.y, fma(-a.y, y.x, d.y)));
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_trivar_factor(TriVarArgs<T> a) {
+  using V = typename c2<T>::t;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.J) return;
+  const V sg = reinterpret_cast<const V*>(a.sigma)[j];
+  const double sx = (double)sg.x, sy = (double)sg.y;
+  const double ox = sx * a.mo + a.ko, oy = sy * a.mo;  // off-diagonal sigma_j m_o + k_o
+  V* ip = reinterpret_cast<V*>(a.ip);
+  V* cp = reinterpret_cast<V*>(a.cp);
+  double cx = 0.0, cy = 0.0;                           // c'_{i-1}
+  for (int i = 0; i < a.n; ++i) {
+    // pivot_i = b_i - o c'_{i-1}
+    const double px = sx * a.md + a.kd + a.r[i] - (ox * cx - oy * cy);
+    const double py = sy * a.md - (ox * cy + oy * cx);
+    const double d = 1.0 / (px * px + py * py);
+    const double ix = px * d, iy = -py * d;            // 1 / pivot_i
+    cx = ox * ix - oy * iy;                            // c'_i = o / pivot_i
+    cy = ox * iy + oy * ix;
+    const size_t at = (size_t)i * a.J + j;
+    ip[at].x = (T)ix; ip[at].y = (T)iy;
+    cp[at].x = (T)cx; cp[at].y = (T)cy;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_trivar_solve(TriVarArgs<T> a) {
+  using V = typename c2<T>::t;
+  using O = cx_ops<T>;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.J) return;
+  const V sg = reinterpret_cast<const V*>(a.sigma)[j];
+  V o;                                                 // off-diagonal sigma_j m_o + k_o
+  o.x = (T)((double)sg.x * a.mo + a.ko);
+  o.y = (T)((double)sg.y * a.mo);
+  V* row = reinterpret_cast<V*>(a.S) + (size_t)j * a.n;
+  const V* ip = reinterpret_cast<const V*>(a.ip) + j;
+  const V* cp = reinterpret_cast<const V*>(a.cp) + j;
+  const size_t J = a.J;
+  // forward: y_i = (b_i - o y_{i-1}) / pivot_i
+  V y;
+  y.x = 0; y.y = 0;
+#pragma unroll 4
+  for (int i = 0; i < a.n; ++i) {
+    y = O::mul(O::fms(row[i], o, y), ip[(size_t)i * J]);
+    row[i] = y;
+  }
+  // backward: q_i = y_i - c'_i q_{i+1}
+  V q;
+  q.x = 0; q.y = 0;
+#pragma unroll 4
+  for (int i = a.n - 1; i >= 0; --i) {
+    q = O::fms(row[i], cp[(size_t)i * J], q);
+    row[i] = q;
+  }
+}
+
+template <typename T> cudaError_t launch_trivar_factor(const TriVarArgs<T>& a, cudaStream_t st) {
+  prof_begin("trivar_factor", st);
+  k_trivar_factor<T><<<(a.J + 63) / 64, 64, 0, st>>>(a);
+  prof_end(st);
+  return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_trivar_solve(const TriVarArgs<T>& a, cudaStream_t st) {
+  prof_begin(sizeof(T) == 4 ? "trivar_solve_f32" : "trivar_solve_f64", st);
+  k_trivar_solve<T><<<(a.J + 63) / 64, 64, 0, st>>>(a);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
 template size_t axis_smem<float>(int, int, bool);
 template size_t axis_smem<double>(int, int, bool);
 template cudaError_t launch_axis<float>(const AxisArgs<float>&, cudaStream_t);
 template cudaError_t launch_axis<double>(const AxisArgs<double>&, cudaStream_t);
 template cudaError_t launch_axis_per<float>(const AxisArgs<float>&, cudaStream_t);
 template cudaError_t launch_axis_per<double>(const AxisArgs<double>&, cudaStream_t);
+template cudaError_t launch_trivar_factor<float>(const TriVarArgs<float>&, cudaStream_t);
+template cudaError_t launch_trivar_factor<double>(const TriVarArgs<double>&, cudaStream_t);
+template cudaError_t launch_trivar_solve<float>(const TriVarArgs<float>&, cudaStream_t);
+template cudaError_t launch_trivar_solve<double>(const TriVarArgs<double>&, cudaStream_t);
 
 }  // namespace pint

@@ -267,6 +267,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
       }
     }
     const float gx = a.gx_hi, gy = a.gy_hi, gz = a.gz_hi;
+    // reaction term w c_i U_i^n (1D, the linearised operator of Algorithm 3): one coefficient per point
+    const bool react = DIM == 1 && a.react != nullptr;
+    const ff rc = (react && valid) ? ff_from_double(a.react[m]) : ff{0.f, 0.f};
     ResidLevel nx = load(i0);
 #pragma unroll 2
     for (int i = i0; i < i1; ++i) {
@@ -323,6 +326,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
           lo = fmaf(gz, ez + (c.bl + c.tl), lo);
         }
         A.sl += lo;
+      }
+      if constexpr (DIM == 1) {
+        if (react) A.fma_term(rc, ff{c.uh, c.ul}, -1.f);
       }
       Xf[(size_t)2 * i * C] = valid ? A.value() * c.s : 0.f;
 

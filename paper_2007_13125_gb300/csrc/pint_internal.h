@@ -27,6 +27,8 @@ struct ResidFwdArgs {
   int fem;                                 // P1 FEM (1D): time terms act on M_h U, centre 2/h
   float m_hi, m_lo;                        // P1 FEM: h/6 (mass matrix off-diagonal)
   int periodic;                            // periodic boundary conditions: neighbours wrap around
+  const double* react;                     // 1D: [M] weighted reaction coefficient w c_i; the
+                                           // residual loses w c_i U_i^n (null: no reaction term)
 };
 
 // MIXED: inverse DFT, times 1/(N kappa^{i/N}), U += c (double-float), norms.
@@ -123,6 +125,24 @@ struct TriArgs {
   int C, logC;
 };
 
+// 1D shifted systems with a space-varying reaction term (the linearised operator of Algorithm 3,
+// Sec. 4.3): for each frequency j the tridiagonal system
+//   (sigma_j m_d + k_d + r_i) q_i + (sigma_j m_o + k_o) (q_{i-1} + q_{i+1}) = b_i,  i = 0..n-1,
+// with (m_d, m_o) the mass row ((1, 0) for finite differences, (4h/6, h/6) for P1 elements),
+// (k_d, k_o) the stiffness row and r = w c the weighted reaction coefficient. The factor kernel
+// computes the LU factors (in FP64) once per reaction coefficient; the solve kernel runs the two
+// substitutions in T on the half spectrum in place. Factors are stored [n][J] (i major), so the
+// threads of a warp (consecutive j) read consecutive addresses.
+template <typename T> struct TriVarArgs {
+  void* S;                                 // T2 spectrum [J][n] (in place; solve only)
+  void* ip;                                // T2 [n][J]: 1 / pivot_i
+  void* cp;                                // T2 [n][J]: (sigma_j m_o + k_o) / pivot_i
+  const void* sigma;                       // T2 [J]: g_j tau^-alpha
+  const double* r;                         // [n]: w c_i (factor only)
+  int n, J;
+  double md, mo, kd, ko;
+};
+
 size_t resid_fwd_smem(int N, int C);
 size_t inv_upd_smem(int N, int C);
 template <typename T> size_t direct_smem(int N, int C);
@@ -142,6 +162,8 @@ template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t
 // periodic lines (complex FFT of n points): op 0 forward, 1 shifted solve, 2 inverse
 template <typename T> cudaError_t launch_axis_per(const AxisArgs<T>& a, cudaStream_t st);
 cudaError_t launch_tri(const TriArgs& a, cudaStream_t st);
+template <typename T> cudaError_t launch_trivar_factor(const TriVarArgs<T>& a, cudaStream_t st);
+template <typename T> cudaError_t launch_trivar_solve(const TriVarArgs<T>& a, cudaStream_t st);
 size_t tri_smem(int n, int C);
 
 // conversions
@@ -151,6 +173,22 @@ cudaError_t launch_d2f(const double* x, float* y, size_t n, cudaStream_t st);
 cudaError_t launch_f2d(const float* x, double* y, size_t n, cudaStream_t st);
 cudaError_t launch_bcast_d(const double* v, double* U, int N, int M, cudaStream_t st);
 cudaError_t launch_bcast_d2ff(const double* v, float* hi, float* lo, int N, int M, cudaStream_t st);
+
+// ---- semilinear extension (kernels_nl.cu) ----
+struct NlPoly { double c[4]; };          // g(u) = c[0] + c[1] u + c[2] u^2 + c[3] u^3
+// r_i = w g'(Ubar_i), Ubar the time average of U [N][M]
+cudaError_t launch_nl_linearise(const double* U, int N, int M, const NlPoly& g, double w, double* r,
+                                cudaStream_t st);
+// Fout = F - w g(U) + r U, U0 = U ([N][M])
+cudaError_t launch_nl_rhs(const double* F, const double* U, const double* r, const NlPoly& g, double w, int N,
+                          int M, double* Fout, double* U0, cudaStream_t st);
+// norms[0] += ||U - U0||^2, norms[1] += ||U||^2
+cudaError_t launch_nl_norms(const double* U, const double* U0, size_t NM, double* norms, cudaStream_t st);
+// out [rows][M] = fd with row 0 minus w g(v) and minus r v (r: [M] or null)
+cudaError_t launch_nl_fd0(const double* fd, const double* v, const NlPoly& g, double w, const double* r, int rows,
+                          int M, double* out, cudaStream_t st);
+// out = w c ([M])
+cudaError_t launch_scale(const double* c, double w, int M, double* out, cudaStream_t st);
 
 // ---- convergence control (shared by the host loop and the graph's device-side check) ----
 struct SolveCtl {

@@ -391,9 +391,11 @@ void destroy_plan(pint_plan p) {
   if (p->alloc) {
     if (p->h_norms) p->alloc->host_release(p->h_norms);
     if (p->h_ctl) p->alloc->host_release(p->h_ctl);
+    if (p->nl_h) p->alloc->host_release(p->nl_h);
   } else {
     if (p->h_norms) cudaFreeHost(p->h_norms);
     if (p->h_ctl) cudaFreeHost(p->h_ctl);
+    if (p->nl_h) cudaFreeHost(p->nl_h);
   }
   delete p;
 }
@@ -638,10 +640,25 @@ extern "C" pint_status pint_plan_destroy(pint_plan p) {
 
 extern "C" size_t pint_plan_workspace_bytes(pint_plan p) { return p ? p->bytes : 0; }
 
-extern "C" pint_status pint_form_rhs(pint_plan p, const double* v, const double* f, const double* fderiv,
-                                     double* Fhat, void* stream) {
+namespace {
+pint_status nl_alloc_fd(pint_plan p);
+double react_weight(pint_plan p);
+// F_hat with the starting correction a_n (f(0) - A v - w c v - w g(v)): the reaction term when one
+// is installed, the nonlinearity when g is given (the rows of fderiv are then copied with f(0)
+// replaced first)
+pint_status form_rhs(pint_plan p, const double* v, const double* f, const double* fderiv, double* Fhat,
+                     cudaStream_t st, const NlPoly* g) {
   if (!p || !v || !f || !Fhat) return fail(PINT_EINVAL, "NULL argument");
   if (p->k >= 2 && !fderiv) return fail(PINT_EINVAL, "fderiv is required for k >= 2");
+  if (p->k >= 2 && (g || p->react_on)) {
+    pint_status s = nl_alloc_fd(p);
+    if (s != PINT_OK) return s;
+    NlPoly zero{};
+    cudaError_t e = launch_nl_fd0(fderiv, v, g ? *g : zero, react_weight(p), p->react_on ? p->react : nullptr,
+                                  p->k - 1, p->M, p->nl_fd, st);
+    if (e != cudaSuccess) return cuda_fail(e, "source correction kernel");
+    fderiv = p->nl_fd;
+  }
   RhsArgs a{};
   a.v = v; a.f = f; a.fd = fderiv; a.F = Fhat; a.beta = p->beta;
   a.N = p->N; a.M = p->M; a.mx = p->mx; a.dim = p->dim; a.k = p->k;
@@ -653,9 +670,15 @@ extern "C" pint_status pint_form_rhs(pint_plan p, const double* v, const double*
     a.a[n] = n < 5 ? p->a[n] : 0.0;
     for (int l = 1; l <= 4; ++l) a.bt[l][n] = p->b[l - 1][n] * std::pow(p->tau, l);
   }
-  cudaError_t e = launch_rhs(a, (cudaStream_t)stream);
+  cudaError_t e = launch_rhs(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "rhs kernel");
   return PINT_OK;
+}
+}  // namespace
+
+extern "C" pint_status pint_form_rhs(pint_plan p, const double* v, const double* f, const double* fderiv,
+                                     double* Fhat, void* stream) {
+  return form_rhs(p, v, f, fderiv, Fhat, (cudaStream_t)stream, nullptr);
 }
 
 extern "C" pint_status pint_initial_guess(pint_plan p, const double* v, double* U, void* stream) {
@@ -675,9 +698,26 @@ void split_ff(double x, float& hi, float& lo) {
 template <typename T> bool ysolve_tri(pint_plan p) { return sizeof(T) == 4 && p->ysolve == 2; }
 
 // spatial step on the half spectrum for T (float: MIXED/FP32, double: FP64)
+// mass and stiffness rows (diagonal, off-diagonal) of a 1D plan: finite differences (1, 0) and
+// (2/h^2, -1/h^2); P1 elements (4h/6, h/6) and (2/h, -1/h)
+void row_coefficients(pint_plan p, double& md, double& mo, double& kd, double& ko) {
+  const double h = 1.0 / (p->mx + 1);
+  md = p->fem ? 4.0 * h / 6.0 : 1.0;
+  mo = p->fem ? h / 6.0 : 0.0;
+  kd = 2.0 * p->gx;
+  ko = -p->gx;
+}
+
 template <typename T>
 cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
   const int J = p->N / 2 + 1;
+  if (p->react_on) {
+    // 1D with a reaction term: each frequency's tridiagonal system by its stored LU factors
+    TriVarArgs<T> a{};
+    a.S = p->S; a.ip = p->tri_ip; a.cp = p->tri_cp; a.sigma = t.sigma; a.n = p->mx; a.J = J;
+    row_coefficients(p, a.md, a.mo, a.kd, a.ko);
+    return launch_trivar_solve<T>(a, st);
+  }
   if (p->periodic) {
     // FFT diagonalisation: 1D one fused solve; 2D forward FFT along x, fused solve along y,
     // inverse FFT along x (the 1/(mx my) normalisation in the solve's divisor)
@@ -842,6 +882,7 @@ pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   split_ff(p->gy, r.gy_hi, r.gy_lo);
   split_ff(p->gz, r.gz_hi, r.gz_lo);
   r.my = p->my;
+  r.react = p->react_on ? p->react : nullptr;
   cudaError_t e = launch_resid_fwd(r, st);
   if (e != cudaSuccess) return cuda_fail(e, "residual kernel");
   e = spatial<float>(p, p->tf, st);
@@ -1018,7 +1059,8 @@ pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double 
                                 cudaStream_t st) {
   SolveGraph* hit = nullptr;
   for (SolveGraph& c : p->sg)
-    if (c.exec && c.F == F && c.U == U && c.tol == tol && c.max_sweeps == max_sweeps) hit = &c;
+    if (c.exec && c.F == F && c.U == U && c.tol == tol && c.max_sweeps == max_sweeps && c.react == p->react_on)
+      hit = &c;
   if (!hit) {
     // an empty slot, else the least recently used one
     hit = &p->sg[0];
@@ -1043,7 +1085,7 @@ pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double 
       sg.exec = nullptr;
       return s;
     }
-    sg.F = F; sg.U = U; sg.tol = tol; sg.max_sweeps = max_sweeps;
+    sg.F = F; sg.U = U; sg.tol = tol; sg.max_sweeps = max_sweeps; sg.react = p->react_on;
   }
   hit->last_use = ++p->sg_clock;
   PINT_CUDA(cudaGraphLaunch(hit->exec, st));
@@ -1159,7 +1201,7 @@ extern "C" pint_status pint_batch_solve(pint_plan* plans, int n, const double* c
   if (n < 1 || !plans || !Fhat || !U) return fail(PINT_EINVAL, "bad batch arguments");
   if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
   std::vector<const void*> key;
-  key.reserve(3 * (size_t)n);
+  key.reserve(4 * (size_t)n);
   for (int i = 0; i < n; ++i) {
     if (!plans[i] || !Fhat[i] || !U[i]) return fail(PINT_EINVAL, "NULL plan or array in batch");
     for (int j = 0; j < i; ++j)
@@ -1167,6 +1209,7 @@ extern "C" pint_status pint_batch_solve(pint_plan* plans, int n, const double* c
     key.push_back(plans[i]);
     key.push_back(Fhat[i]);
     key.push_back(U[i]);
+    key.push_back(plans[i]->react_on ? plans[i]->react : nullptr);  // spatial solve captured
   }
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(g_batch.mu);
@@ -1303,4 +1346,162 @@ extern "C" int pint_kernel_stats(int max, const char** names, int* launches, dou
     g_prof_recs.clear();
   }
   return n;
+}
+
+// ---------------------------------------------------------------------------
+// Reaction term and the semilinear extension (Sec. 4.3, Algorithm 3)
+// ---------------------------------------------------------------------------
+namespace {
+
+// reaction weight of a row: 1 (finite differences), h (P1 elements, nodal quadrature)
+double react_weight(pint_plan p) { return p->fem ? 1.0 / (p->mx + 1) : 1.0; }
+
+pint_status react_check(pint_plan p) {
+  if (!p) return fail(PINT_EINVAL, "NULL plan");
+  if (p->dim != 1 || p->periodic)
+    return fail(PINT_EINVAL, "reaction terms are supported on 1D plans with Dirichlet boundaries");
+  return PINT_OK;
+}
+
+pint_status react_alloc(pint_plan p) {
+  if (p->react) return PINT_OK;
+  const size_t JM = (size_t)(p->N / 2 + 1) * p->M;
+  const size_t vb = p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2);
+  pint_status s;
+  unsigned char *ip, *cp;
+  if ((s = dalloc(p, &ip, JM * vb)) != PINT_OK) return s;
+  if ((s = dalloc(p, &cp, JM * vb)) != PINT_OK) return s;
+  if ((s = dalloc(p, &p->react, (size_t)p->M)) != PINT_OK) return s;
+  p->tri_ip = ip;
+  p->tri_cp = cp;
+  return PINT_OK;
+}
+
+// LU factors of (sigma_j M + A + diag(react)) for every frequency j
+pint_status react_factor(pint_plan p, cudaStream_t st) {
+  cudaError_t e;
+  if (p->prec == PINT_FP64) {
+    TriVarArgs<double> a{};
+    a.ip = p->tri_ip; a.cp = p->tri_cp; a.sigma = p->td.sigma; a.r = p->react; a.n = p->mx; a.J = p->N / 2 + 1;
+    row_coefficients(p, a.md, a.mo, a.kd, a.ko);
+    e = launch_trivar_factor<double>(a, st);
+  } else {
+    TriVarArgs<float> a{};
+    a.ip = p->tri_ip; a.cp = p->tri_cp; a.sigma = p->tf.sigma; a.r = p->react; a.n = p->mx; a.J = p->N / 2 + 1;
+    row_coefficients(p, a.md, a.mo, a.kd, a.ko);
+    e = launch_trivar_factor<float>(a, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tridiagonal factor kernel");
+  return PINT_OK;
+}
+
+pint_status nl_alloc_fd(pint_plan p) {
+  if (p->nl_fd) return PINT_OK;
+  return dalloc(p, &p->nl_fd, (size_t)(p->k - 1) * p->M);
+}
+
+pint_status poly_check(const pint_poly* g) {
+  if (!g) return fail(PINT_EINVAL, "NULL nonlinearity");
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(g->c[i])) return fail(PINT_EINVAL, "non-finite nonlinearity coefficient");
+  return PINT_OK;
+}
+
+NlPoly to_poly(const pint_poly* g) {
+  NlPoly q;
+  for (int i = 0; i < 4; ++i) q.c[i] = g->c[i];
+  return q;
+}
+
+}  // namespace
+
+extern "C" pint_status pint_set_reaction(pint_plan p, const double* c, void* stream) {
+  pint_status s = react_check(p);
+  if (s != PINT_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!c) {
+    p->react_on = false;
+    return PINT_OK;
+  }
+  if ((s = react_alloc(p)) != PINT_OK) return s;
+  cudaError_t e = launch_scale(c, react_weight(p), p->M, p->react, st);
+  if (e != cudaSuccess) return cuda_fail(e, "reaction kernel");
+  if ((s = react_factor(p, st)) != PINT_OK) return s;
+  p->react_on = true;
+  return PINT_OK;
+}
+
+extern "C" pint_status pint_nl_form_rhs(pint_plan p, const pint_poly* g, const double* v, const double* f,
+                                        const double* fderiv, double* Fhat, void* stream) {
+  pint_status s = react_check(p);
+  if (s != PINT_OK) return s;
+  if ((s = poly_check(g)) != PINT_OK) return s;
+  if (p->react_on) return fail(PINT_EINVAL, "a reaction term is installed (pint_set_reaction(plan, NULL) removes it)");
+  const NlPoly q = to_poly(g);
+  return form_rhs(p, v, f, fderiv, Fhat, (cudaStream_t)stream, &q);
+}
+
+extern "C" pint_status pint_nl_solve(pint_plan p, const pint_poly* g, const double* Fhat, double* U,
+                                     double newton_tol, int max_steps, double tol, int max_sweeps,
+                                     pint_nl_info* info, void* stream) {
+  pint_status s = react_check(p);
+  if (s != PINT_OK) return s;
+  if ((s = poly_check(g)) != PINT_OK) return s;
+  if (!Fhat || !U) return fail(PINT_EINVAL, "NULL argument");
+  if (p->react_on) return fail(PINT_EINVAL, "a reaction term is installed (pint_set_reaction(plan, NULL) removes it)");
+  if (!(newton_tol > 0.0) || !(tol > 0.0) || max_sweeps < 1 || max_steps < 1 || max_steps > PINT_NL_MAX_STEPS)
+    return fail(PINT_EINVAL, "tolerances must be > 0, max_sweeps >= 1, 1 <= max_steps <= PINT_NL_MAX_STEPS");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t NM = (size_t)p->N * p->M;
+  if ((s = react_alloc(p)) != PINT_OK) return s;
+  if (!p->nl_F) {
+    if ((s = dalloc(p, &p->nl_F, NM)) != PINT_OK) return s;
+    if ((s = dalloc(p, &p->nl_U0, NM)) != PINT_OK) return s;
+    if ((s = dalloc(p, &p->nl_norms, 2)) != PINT_OK) return s;
+  }
+  if (!p->nl_h) {
+    p->nl_h = p->alloc ? (double*)p->alloc->host_alloc(2 * sizeof(double)) : nullptr;
+    if (!p->alloc && cudaMallocHost(&p->nl_h, 2 * sizeof(double)) != cudaSuccess) p->nl_h = nullptr;
+    if (!p->nl_h) return fail(PINT_ENOMEM, "pinned host buffer");
+  }
+  const NlPoly q = to_poly(g);
+  const double w = react_weight(p);
+  if (info) std::memset(info, 0, sizeof(*info));
+  p->react_on = true;
+  double prev = 0.0;
+  bool converged = false, inner_ok = true;
+  int l = 0;
+  while (l < max_steps && !converged) {
+    ++l;
+    // linearise at the time average of U_{l-1}: react = w g'(Ubar), its factors, and the
+    // right-hand side F_hat - w g(U_{l-1}) + w D U_{l-1} of (K + I (x) w D) U_l = ...
+    cudaError_t e = launch_nl_linearise(U, p->N, p->M, q, w, p->react, st);
+    if (e == cudaSuccess) e = launch_nl_rhs(Fhat, U, p->react, q, w, p->N, p->M, p->nl_F, p->nl_U0, st);
+    if (e != cudaSuccess) { p->react_on = false; return cuda_fail(e, "linearisation kernels"); }
+    if ((s = react_factor(p, st)) != PINT_OK) { p->react_on = false; return s; }
+    // the inner WR from U_{l-1} (W_0 = 0)
+    int sweeps = 0;
+    double upd_in = 0.0;
+    s = pint_solve(p, p->nl_F, U, tol, max_sweeps, &sweeps, &upd_in, stream);
+    if (s == PINT_ENOTCONV) inner_ok = false;
+    else if (s != PINT_OK) { p->react_on = false; return s; }
+    // ||U_l - U_{l-1}|| / ||U_l||
+    e = cudaMemsetAsync(p->nl_norms, 0, 2 * sizeof(double), st);
+    if (e == cudaSuccess) e = launch_nl_norms(U, p->nl_U0, NM, p->nl_norms, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->nl_h, p->nl_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { p->react_on = false; return cuda_fail(e, "outer update norms"); }
+    const double upd = p->nl_h[1] > 0.0 ? std::sqrt(p->nl_h[0] / p->nl_h[1]) : std::sqrt(p->nl_h[0]);
+    if (info) {
+      info->steps = l;
+      info->sweeps[l - 1] = sweeps;
+      info->upd[l - 1] = upd;
+    }
+    converged = stop_decision(l, upd, prev, newton_tol, 0.0);
+    prev = upd;
+  }
+  p->react_on = false;
+  if (!converged) return fail(PINT_ENOTCONV, "max_steps reached above newton_tol");
+  if (!inner_ok) return fail(PINT_ENOTCONV, "an inner solve reached max_sweeps above tol");
+  return PINT_OK;
 }

@@ -48,6 +48,7 @@ struct SolveGraph {
   double* U = nullptr;
   double tol = 0.0;
   int max_sweeps = 0;
+  bool react = false;               // captured with the reaction term's spatial solve
   unsigned long long last_use = 0;
 };
 // Graphs cached per plan (least recently used replaced): callers that alternate between a few
@@ -96,6 +97,18 @@ struct pint_plan_s {
                                          // x, y, z lines, tri
   int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal
   double q_floor;                   // predicted floor of the per-sweep contraction (inner precision)
+  // reaction term (1D, Dirichlet): the spatial operator A + w diag(c) of the linear solves
+  // (pint_set_reaction; the linearised operator of Algorithm 3)
+  bool react_on = false;
+  double* react = nullptr;          // [M] w c_i
+  void* tri_ip = nullptr;           // [M][N/2+1] T2: inverse pivots of the shifted systems
+  void* tri_cp = nullptr;           // [M][N/2+1] T2: eliminated super-diagonal
+  // Algorithm 3 workspaces (allocated on first use)
+  double* nl_F = nullptr;           // [N][M] right-hand side of the linearised problem
+  double* nl_U0 = nullptr;          // [N][M] previous outer iterate
+  double* nl_fd = nullptr;          // [k-1][M] derivative rows with f(0) - w g(v)
+  double* nl_norms = nullptr;       // device [2]
+  double* nl_h = nullptr;           // pinned host [2]
 };
 
 namespace pint {

@@ -48,6 +48,26 @@ class _Req(ctypes.Structure):
                 ("inputs_on_device", ctypes.c_int)]
 
 
+class _Poly(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double * 4)]
+
+
+PINT_NL_MAX_STEPS = 64
+
+
+class _NlInfo(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("sweeps", ctypes.c_int * PINT_NL_MAX_STEPS),
+                ("upd", ctypes.c_double * PINT_NL_MAX_STEPS)]
+
+
+def _poly(g):
+    """pint_poly from 4 coefficients c_0..c_3 of g(u) = sum_i c_i u^i."""
+    c = [float(x) for x in g]
+    if len(c) != 4:
+        raise ValueError("g: four coefficients c_0..c_3")
+    return _Poly((ctypes.c_double * 4)(*c))
+
+
 class _Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("sweeps", ctypes.c_int), ("upd_rel", ctypes.c_double),
                 ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
@@ -91,6 +111,9 @@ def lib():
                                   ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
         "pint_kernel_stats": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I),
                                    ctypes.POINTER(_D), _I]),
+        "pint_set_reaction": (_I, [_P, _P, _P]),
+        "pint_nl_form_rhs": (_I, [_P, ctypes.POINTER(_Poly), _P, _P, _P, _P, _P]),
+        "pint_nl_solve": (_I, [_P, ctypes.POINTER(_Poly), _P, _P, _D, _I, _D, _I, ctypes.POINTER(_NlInfo), _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -267,6 +290,30 @@ class Plan:
         """Enqueue the whole solve on `stream` without waiting (pint_solve_async)."""
         check(lib().pint_solve_async(self.handle, _ptr(Fhat), _ptr(U), float(tol), int(max_sweeps),
                                      _stream(stream)))
+
+    def set_reaction(self, c, stream=None):
+        """Reaction term A + w diag(c) for the linear solves (pint_set_reaction); None removes it."""
+        check(lib().pint_set_reaction(self.handle, _ptr(c) if c is not None else None, _stream(stream)))
+
+    def nl_form_rhs(self, g, v, f, fderiv, Fhat, stream=None):
+        """F_hat of the semilinear scheme (pint_nl_form_rhs); g = (c_0, c_1, c_2, c_3)."""
+        q = _poly(g)
+        check(lib().pint_nl_form_rhs(self.handle, ctypes.byref(q), _ptr(v), _ptr(f),
+                                     _ptr(fderiv) if fderiv is not None and fderiv.numel() else None,
+                                     _ptr(Fhat), _stream(stream)))
+
+    def nl_solve(self, g, Fhat, U, newton_tol=1e-8, max_steps=20, tol=1e-10, max_sweeps=50, stream=None,
+                 raise_on_notconv=True):
+        """Algorithm 3 (pint_nl_solve): (status, [inner sweeps per outer step], [outer updates])."""
+        q = _poly(g)
+        info = _NlInfo()
+        st = lib().pint_nl_solve(self.handle, ctypes.byref(q), _ptr(Fhat), _ptr(U), float(newton_tol),
+                                 int(max_steps), float(tol), int(max_sweeps), ctypes.byref(info),
+                                 _stream(stream))
+        if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
+            raise PintError(st, last_error())
+        n = info.steps
+        return st, list(info.sweeps[:n]), list(info.upd[:n])
 
     def solve_result(self, raise_on_notconv=True):
         """(status, sweeps, update) of the last graph-launched solve, once its stream completed it."""

@@ -1,0 +1,192 @@
+"""Reaction terms and Algorithm 3 (Sec. 4.3) through the C ABI against the oracle: the linear
+solve with A + w diag(c) (tridiagonal spatial solves), the semilinear source, the outer iterates
+of the modified Newton iteration, and its limit, the sequential semilinear solution."""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import device_inputs, rel_l2, torch_cuda
+from oracle import nonlinear as nl
+
+pytestmark = pytest.mark.gpu
+
+BAR = {"mixed": 1e-8, "fp64": 1e-10}
+
+
+def oracle_ops(p):
+    return nl.space_ops(p.space, p.mx)
+
+
+def reaction_field(p, seed=5):
+    """A positive-definite perturbation: c(x) in [-2, 6] (well above -lambda_min(A))."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(1, p.mx + 1) / (p.mx + 1)
+    return 2.0 + 3.0 * np.sin(3 * np.pi * x) + rng.uniform(-1.0, 1.0, p.mx)
+
+
+REACT_CASES = [
+    dict(space="fd", precision="fp64", mx=127, N=64, k=2, alpha=1.0, kappa=0.1),
+    dict(space="fd", precision="mixed", mx=127, N=64, k=2, alpha=1.0, kappa=0.1),
+    dict(space="fd", precision="mixed", mx=255, N=128, k=4, alpha=1.0, kappa=0.05),
+    dict(space="fd", precision="fp64", mx=63, N=64, k=3, alpha=0.5, kappa=0.1),
+    dict(space="fd", precision="mixed", mx=63, N=64, k=3, alpha=0.5, kappa=0.1),
+    dict(space="fem", precision="mixed", mx=255, N=64, k=3, alpha=1.0, kappa=0.1),
+    dict(space="fem", precision="mixed", mx=127, N=128, k=2, alpha=0.7, kappa=0.1),
+    dict(space="fd", precision="fp64", mx=31, N=16, k=6, alpha=1.0, kappa=0.1),
+]
+
+
+@pytest.mark.parametrize("kw", REACT_CASES, ids=lambda kw: "{space}_{precision}_M{mx}_N{N}_k{k}_a{alpha}".format(**kw))
+def test_reaction_solve_matches_oracle(kw):
+    # (D_tau^alpha + A + w diag(c)) U = F_hat, F_hat with the starting correction of A + w diag(c)
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    kw = dict(kw)
+    prec = kw.pop("precision")
+    p = workloads.allen_cahn_problem(data="modes", T=1.0, seed=3, **kw)
+    c = reaction_field(p)
+    Mass, A, w = oracle_ops(p)
+    zero = (0.0, 0.0, 0.0, 0.0)
+    Ar = A + w * np.diag(c)
+    Fo = nl.nl_rhs(p.k, p.alpha, p.tau, Mass, Ar, w, zero, p.v, p.f(), p.fderiv())
+    ref = nl.solve_sequential_nl(p.k, p.alpha, p.tau, Mass, Ar, w, zero, Fo)
+    v, f, fd = device_inputs(p, torch)
+    cd = torch.tensor(c, dtype=torch.float64, device="cuda:0")
+    with Plan.for_problem(p, prec) as plan:
+        plan.set_reaction(cd)
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        plan.form_rhs(v, f, fd, F)
+        U = torch.empty_like(F)
+        plan.initial_guess(v, U)
+        st, sweeps, upd = plan.solve(F, U, tol=0.1 * BAR[prec], max_sweeps=60)
+        torch.cuda.synchronize()
+        Fg = F.cpu().numpy()
+        Ug = U.cpu().numpy()
+        # removing the term restores the plain solve (a separately cached graph)
+        plan.set_reaction(None)
+        plan.initial_guess(v, U)
+        plan.form_rhs(v, f, fd, F)
+        plan.solve(F, U, tol=0.1 * BAR[prec], max_sweeps=60)
+        torch.cuda.synchronize()
+        U_plain = U.cpu().numpy()
+    assert rel_l2(Fg, Fo) <= 1e-13
+    assert rel_l2(Ug, ref) <= BAR[prec], (sweeps, upd)
+    Fp = nl.nl_rhs(p.k, p.alpha, p.tau, Mass, A, w, zero, p.v, p.f(), p.fderiv())
+    ref_plain = nl.solve_sequential_nl(p.k, p.alpha, p.tau, Mass, A, w, zero, Fp)
+    assert rel_l2(U_plain, ref_plain) <= BAR[prec]
+
+
+@pytest.mark.parametrize("space,k", [("fd", 3), ("fem", 2)])
+def test_nl_form_rhs_matches_oracle(space, k):
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = workloads.allen_cahn_problem(space, mx=63, N=32, k=k, alpha=1.0, T=1.0, eps=0.5, data="modes")
+    Mass, A, w = oracle_ops(p)
+    Fo = nl.nl_rhs(p.k, p.alpha, p.tau, Mass, A, w, p.g, p.v, p.f(), p.fderiv())
+    v, f, fd = device_inputs(p, torch)
+    with Plan.for_problem(p, "mixed") as plan:
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        plan.nl_form_rhs(p.g, v, f, fd, F)
+        torch.cuda.synchronize()
+    assert rel_l2(F.cpu().numpy(), Fo) <= 1e-13
+
+
+NL_CASES = [
+    dict(space="fd", precision="fp64", mx=127, N=64, k=2, alpha=1.0, kappa=0.1, eps=0.5, data="modes"),
+    dict(space="fd", precision="mixed", mx=127, N=64, k=2, alpha=1.0, kappa=0.1, eps=0.5, data="modes"),
+    dict(space="fd", precision="mixed", mx=255, N=128, k=4, alpha=1.0, kappa=0.05, eps=0.5, data="modes"),
+    dict(space="fd", precision="fp64", mx=63, N=64, k=3, alpha=0.5, kappa=0.1, eps=0.5, data="modes"),
+    dict(space="fd", precision="mixed", mx=63, N=64, k=3, alpha=0.5, kappa=0.1, eps=0.5, data="modes"),
+    dict(space="fem", precision="mixed", mx=255, N=64, k=2, alpha=0.75, kappa=0.1, eps=1.0, data="example4"),
+    dict(space="fem", precision="mixed", mx=127, N=128, k=3, alpha=0.75, kappa=0.1, eps=1.0, data="example4"),
+    dict(space="fem", precision="mixed", mx=255, N=64, k=1, alpha=0.25, kappa=0.1, eps=1.0, data="example4"),
+    dict(space="fd", precision="fp64", mx=255, N=64, k=2, alpha=0.25, kappa=0.1, eps=1.0, data="example4"),
+]
+
+
+def run_nl(p, prec, torch, newton_tol, max_steps=30, tol=None):
+    from paper_2007_13125_gb300 import Plan
+    v, f, fd = device_inputs(p, torch)
+    with Plan.for_problem(p, prec) as plan:
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        plan.nl_form_rhs(p.g, v, f, fd, F)
+        U = torch.empty_like(F)
+        plan.initial_guess(v, U)                 # Algorithm 3 starts from U_0^n = v
+        out = plan.nl_solve(p.g, F, U, newton_tol=newton_tol, max_steps=max_steps,
+                            tol=tol if tol is not None else 0.1 * newton_tol, max_sweeps=60)
+        torch.cuda.synchronize()
+        return U.cpu().numpy(), out
+
+
+@pytest.mark.parametrize("kw", NL_CASES, ids=lambda kw: "{space}_{precision}_{data}_M{mx}_N{N}_k{k}_a{alpha}".format(**kw))
+def test_nl_solve_reaches_the_sequential_semilinear_solution(kw):
+    torch = torch_cuda()
+    kw = dict(kw)
+    prec = kw.pop("precision")
+    T = 0.4 if kw["data"] == "example4" else 1.0
+    p = workloads.allen_cahn_problem(T=T, seed=4, **kw)
+    Mass, A, w = oracle_ops(p)
+    Fo = nl.nl_rhs(p.k, p.alpha, p.tau, Mass, A, w, p.g, p.v, p.f(), p.fderiv())
+    ref = nl.solve_sequential_nl(p.k, p.alpha, p.tau, Mass, A, w, p.g, Fo)
+    U, (st, sweeps, upds) = run_nl(p, prec, torch, newton_tol=0.1 * BAR[prec])
+    assert st == 0 and len(sweeps) >= 2
+    assert rel_l2(U, ref) <= BAR[prec], (sweeps, upds)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_nl_outer_iterates_follow_algorithm3(prec):
+    # the first outer steps of Algorithm 3 (inner WR converged far below the outer change) against
+    # the oracle's iterates U_1, U_2, U_3 on Example 4's data (finite differences, alpha = 0.75)
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = workloads.allen_cahn_problem("fd", mx=255, N=64, k=2, alpha=0.75, kappa=0.1, T=0.4, eps=1.0)
+    Mass, A, w = oracle_ops(p)
+    Fo = nl.nl_rhs(p.k, p.alpha, p.tau, Mass, A, w, p.g, p.v, p.f(), p.fderiv())
+    its, counts = nl.algorithm3(p.k, p.alpha, p.kappa, p.tau, Mass, A, w, p.g, Fo, p.v, 3, tol_inf=1e-15)
+    v, f, fd = device_inputs(p, torch)
+    for L in (1, 2, 3):
+        with Plan.for_problem(p, prec) as plan:
+            F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+            plan.nl_form_rhs(p.g, v, f, fd, F)
+            U = torch.empty_like(F)
+            plan.initial_guess(v, U)
+            st, sweeps, upds = plan.nl_solve(p.g, F, U, newton_tol=1e-30, max_steps=L, tol=1e-3 * BAR[prec],
+                                             max_sweeps=60, raise_on_notconv=False)
+            torch.cuda.synchronize()
+        assert len(sweeps) == L
+        # the outer change at step L is ~1e-4^L; the GPU iterate agrees with the oracle's to the
+        # precision bar relative to U
+        assert rel_l2(U.cpu().numpy(), its[L]) <= BAR[prec], (L, sweeps, upds)
+    # outer updates contract like Table 4 (~1e-4 per step on this data)
+    assert upds[1] < 1e-3 * upds[0] and upds[2] < 1e-3 * upds[1]
+
+
+def test_nl_entry_points_reject_bad_arguments():
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    from paper_2007_13125_gb300.pint import PintError, PINT_EINVAL
+    p = workloads.allen_cahn_problem("fd", mx=31, N=16, k=2)
+    q = workloads.c2_heat2d(mx=31, N=16)
+    F = torch.zeros((p.N, p.M), dtype=torch.float64, device="cuda:0")
+    U = torch.zeros_like(F)
+    c = torch.zeros(p.M, dtype=torch.float64, device="cuda:0")
+    with Plan.for_problem(q, "mixed") as plan2d:
+        with pytest.raises(PintError) as e:
+            plan2d.set_reaction(torch.zeros(q.M, dtype=torch.float64, device="cuda:0"))
+        assert e.value.status == PINT_EINVAL
+    with Plan.for_problem(p, "mixed") as plan:
+        for kwargs in [dict(newton_tol=0.0), dict(max_steps=0), dict(max_steps=65), dict(max_sweeps=0)]:
+            with pytest.raises(PintError) as e:
+                plan.nl_solve(p.g, F, U, **kwargs)
+            assert e.value.status == PINT_EINVAL
+        with pytest.raises(PintError) as e:
+            plan.nl_solve((float("nan"), 0.0, 0.0, 1.0), F, U)
+        assert e.value.status == PINT_EINVAL
+        plan.set_reaction(c)
+        with pytest.raises(PintError) as e:
+            plan.nl_solve(p.g, F, U)
+        assert e.value.status == PINT_EINVAL
+        plan.set_reaction(None)
+        st, sweeps, upds = plan.nl_solve((0.0, 0.0, 0.0, 0.0), F, U, newton_tol=1e-8)  # g = 0, F = 0
+        torch.cuda.synchronize()
+        assert float(U.abs().max()) == 0.0

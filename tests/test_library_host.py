@@ -110,3 +110,45 @@ def test_invalid_3d_plans_rejected_before_device_use(pint):
         with pytest.raises(pint.PintError) as e:
             pint.Plan(2, 1.0, 0.1, 0.01, 32, **kw)
         assert e.value.status == pint.PINT_EINVAL
+
+
+def test_reaction_and_semilinear_entry_points_reject_null_plans(pint):
+    # argument checks run before any CUDA call
+    import ctypes
+    L = pint.lib()
+    g = pint._poly((0.0, -1.0, 0.0, 1.0))
+    assert L.pint_set_reaction(None, None, None) == pint.PINT_EINVAL
+    assert L.pint_nl_form_rhs(None, ctypes.byref(g), None, None, None, None, None) == pint.PINT_EINVAL
+    assert L.pint_nl_solve(None, ctypes.byref(g), None, None, 1e-8, 10, 1e-10, 20, None, None) == pint.PINT_EINVAL
+    with pytest.raises(ValueError):
+        pint._poly((1.0, 2.0))
+
+
+def test_allen_cahn_inputs_are_the_manufactured_source():
+    # Example 4 (Sec. 4.3): f = D_t^alpha u - u_xx + u^3 - u for u = t^2/2 sin(2 pi x); the finite-
+    # difference samples against the formula evaluated independently, the P1 loads against
+    # 4-point Gauss quadrature of f phi_i on each element
+    import math
+    import numpy.polynomial.legendre as leg
+    import workloads
+    alpha, T, N, m = 0.75, 0.4, 10, 31
+    p = workloads.allen_cahn_problem("fd", mx=m, N=N, k=2, alpha=alpha, T=T)
+    x = np.arange(1, m + 1) / (m + 1)
+    t = T * np.arange(1, N + 1) / N
+
+    def f(tt, xx):
+        u = tt ** 2 / 2 * np.sin(2 * np.pi * xx)
+        return (tt ** (2 - alpha) / math.gamma(3 - alpha) * np.sin(2 * np.pi * xx)
+                + 4 * np.pi ** 2 * u + u ** 3 - u)
+
+    assert np.allclose(p.f(), f(t[:, None], x[None, :]), rtol=1e-13, atol=1e-15)
+    q = workloads.allen_cahn_problem("fem", mx=m, N=N, k=2, alpha=alpha, T=T)
+    h = 1.0 / (m + 1)
+    gx, gw = leg.leggauss(4)
+    ref = np.zeros((N, m))
+    for i in range(m):
+        for a, b in ((x[i] - h, x[i]), (x[i], x[i] + h)):
+            xs = (a + b) / 2 + (b - a) / 2 * gx
+            phi = 1.0 - np.abs(xs - x[i]) / h
+            ref[:, i] += (b - a) / 2 * (f(t[:, None], xs[None, :]) * phi * gw).sum(axis=1)
+    assert np.allclose(q.f(), ref, rtol=1e-6, atol=1e-9)

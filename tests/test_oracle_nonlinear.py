@@ -8,6 +8,7 @@ import numpy.polynomial.polynomial as P
 import pytest
 import scipy.sparse as sp
 
+import workloads
 from oracle import bdf, fem, nonlinear as nl, sequential
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -28,10 +29,12 @@ def table4():
 def table4_ours():
     out = {}
     for alpha, ks in ((0.25, (1, 2)), (0.75, (1, 2, 3))):
-        tau, v, F_t, F_der, c = nl.example4_data(alpha)
         Mass, A, w = nl.space_ops("fem", 999)
         for k in ks:
-            Fh = nl.nl_rhs(k, alpha, tau, Mass, A, w, c, v, F_t, F_der)
+            # Example 4: T = 0.4, tau = T/100, h = 1/1000, kappa = 0.1, eps = 1
+            p = workloads.allen_cahn_problem("fem", mx=999, N=100, k=k, alpha=alpha, kappa=0.1, T=0.4)
+            tau, v, c = p.tau, p.v, p.g
+            Fh = nl.nl_rhs(k, alpha, tau, Mass, A, w, c, v, p.f(), p.fderiv())
             U = nl.solve_sequential_nl(k, alpha, tau, Mass, A, w, c, Fh)
             its, counts = nl.algorithm3(k, alpha, 0.1, tau, Mass, A, w, c, Fh, v, 3)
             errs = [nl.l2_norm("fem", Mass, X[-1] - U[-1], 999) for X in its]
@@ -62,9 +65,10 @@ def test_printed_sign_does_not_reproduce_table4():
     # eqs. (4.6)-(4.7) print -g'(Ubar) W; with that sign the first outer step reduces the error by
     # ~5e-2 instead of the ~1.5e-4 of Table 4, so the Newton sign +g'(Ubar) is the reading
     alpha, k = 0.25, 1
-    tau, v, F_t, F_der, c = nl.example4_data(alpha, m=255)
+    p = workloads.allen_cahn_problem("fem", mx=255, N=100, k=k, alpha=alpha, kappa=0.1, T=0.4)
+    tau, v, c = p.tau, p.v, p.g
     Mass, A, w = nl.space_ops("fem", 255)
-    Fh = nl.nl_rhs(k, alpha, tau, Mass, A, w, c, v, F_t, F_der)
+    Fh = nl.nl_rhs(k, alpha, tau, Mass, A, w, c, v, p.f(), p.fderiv())
     U = nl.solve_sequential_nl(k, alpha, tau, Mass, A, w, c, Fh)
     ratio = {}
     for sign in (1.0, -1.0):

@@ -19,6 +19,7 @@ Random draws use ``numpy.random.default_rng(seed).standard_normal``:
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -311,4 +312,81 @@ def heat3d_problem(m=15, N=16, k=2, alpha=1.0, kappa=0.1, T=1.0, seed=7, modes=6
     p = make_problem(f"heat3d_{m}x{my}x{mz}_N{N}_k{k}_a{alpha}", 3, m, my, N, k, alpha, kappa, T, v,
                      time_kind, fs)
     p.mz = mz
+    return p
+
+
+# ---------------------------------------------------------------------------
+# Semilinear problems (Sec. 4.3): D_t^alpha u + A u + g(u) = f, 1D, g a cubic
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class NlProblem(Problem):
+    """A semilinear problem: g(u) = g[0] + g[1] u + g[2] u^2 + g[3] u^3, and a source that is
+    not a single product g(t) phi(x): F_t [N, M] holds f(t_n) (grid samples, or P1 load
+    vectors), F_der [k-1, M] holds d_t^l f(0)."""
+    g: tuple = (0.0, 0.0, 0.0, 0.0)
+    F_t: np.ndarray | None = None
+    F_der: np.ndarray | None = None
+
+    def f(self) -> np.ndarray:
+        return self.F_t
+
+    def fderiv(self) -> np.ndarray:
+        return self.F_der[: max(self.k - 1, 0)]
+
+
+def allen_cahn_g(eps: float) -> tuple:
+    """Example 4: g(u) = (u^3 - u) / eps^2."""
+    return (0.0, -1.0 / eps ** 2, 0.0, 1.0 / eps ** 2)
+
+
+def allen_cahn_problem(space="fem", mx=255, N=64, k=2, alpha=0.75, kappa=0.1, T=0.4, eps=1.0,
+                       data="example4", seed=7, modes=8, amp=0.6) -> NlProblem:
+    """1D semilinear problems with the Allen-Cahn term (u^3 - u) / eps^2, finite differences
+    ("fd": grid samples) or P1 elements ("fem": nodal v, load vectors (f, phi_i), exact).
+    data = "example4": Example 4's manufactured solution u = t^2/2 sin(2 pi x) (v = 0):
+        f = [t^{2-alpha}/Gamma(3-alpha) + 2 pi^2 t^2] sin(2 pi x) + ((t^2/2)^3 sin^3(2 pi x)
+            - (t^2/2) sin(2 pi x)) / eps^2,
+      d_t f(0) = sin(2 pi x) when alpha = 1 and 0 for alpha < 1; higher derivatives of f at 0 do
+      not exist for alpha < 1 (f ~ t^{2-alpha}), so k <= 3 there.
+    data = "modes": v = amp * (random sine series, seed) normalised to max |v| = 1,
+      f = e^{-t} (sin(pi x) + 0.3 sin(3 pi x)) * 4."""
+    if alpha < 1.0 and k > 3 and data == "example4":
+        raise ValueError("Example 4's source has no second time derivative at t = 0 for alpha < 1")
+    h = 1.0 / (mx + 1)
+    x = grid_points(mx)
+    t = np.arange(1, N + 1) * (T / N)
+    g = allen_cahn_g(eps)
+    if space == "fem":
+        s1 = fem_load_sine(mx, 2)
+        s3 = (3.0 * s1 - fem_load_sine(mx, 6)) / 4.0  # sin^3 = (3 sin - sin 3.) / 4
+    else:
+        s1 = np.sin(2 * np.pi * x)
+        s3 = s1 ** 3
+    F_der = np.zeros((max(k - 1, 1), mx))
+    if data == "example4":
+        v = np.zeros(mx)
+        a = t ** 2 / 2.0
+        lin = t ** (2.0 - alpha) / math.gamma(3.0 - alpha) + (2 * np.pi) ** 2 * a
+        F_t = np.outer(lin, s1) + np.outer(a ** 3, s3) / eps ** 2 - np.outer(a, s1) / eps ** 2
+        if alpha == 1.0 and k >= 3:
+            F_der[1] = s1
+    elif data == "modes":
+        rng = np.random.default_rng(seed)
+        v = random_v(1, mx, 1, min(modes, mx), rng)
+        v = amp * v / np.max(np.abs(v))
+        if space == "fem":
+            load = 4.0 * (fem_load_sine(mx, 1) + 0.3 * fem_load_sine(mx, 3))
+        else:
+            load = 4.0 * (np.sin(np.pi * x) + 0.3 * np.sin(3 * np.pi * x))
+        F_t = np.outer(np.exp(-t), load)
+        for l in range(F_der.shape[0]):
+            F_der[l] = (-1.0) ** l * load
+    else:
+        raise ValueError(data)
+    p = NlProblem(f"allencahn_{space}_{data}_M{mx}_N{N}_k{k}_a{alpha}", 1, mx, 1, N, k, alpha, kappa, T, v,
+                  np.zeros(N), np.zeros(mx), np.zeros(max(k - 1, 0)), g=g, F_t=F_t, F_der=F_der)
+    p.space = space
+    p.meta.update(dict(eps=eps, data=data, h=h))
     return p
