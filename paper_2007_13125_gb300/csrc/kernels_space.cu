@@ -18,7 +18,8 @@
 //
 // k_trivar_factor / k_trivar_solve -- 1D shifted systems whose diagonal varies along x (a
 // reaction term, the linearised operator of Algorithm 3): no transform diagonalises them, so
-// each frequency's tridiagonal system is solved by Gaussian elimination without pivoting (the
+// each frequency's tridiagonal system is solved by Gaussian elimination without pivoting, the
+// substitutions as parallel scans of affine maps (the
 // systems are diagonally dominant up to the reaction term: sigma_j lies in the sector where the
 // BDF / CQ symbols live, and A_h + w diag(c) is positive definite for the reactions of interest).
 #include "fft.cuh"
@@ -565,15 +566,26 @@ cudaError_t launch_tri(const TriArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// ---- variable-coefficient tridiagonal systems (thread per frequency j) ----
+// ---- variable-coefficient tridiagonal systems ----
 template <typename T> struct cx_ops;
 template <> struct cx_ops<float> {
   using V = float2;
   static __device__ __forceinline__ V mul(V a, V b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
   }
-  static __device__ __forceinline__ V fms(V d, V a, V y) {  // d - a * y
-    return make_float2(fmaf(-a.x, y.x, fmaf(a.y, y.y, d.x)), fmaf(-a.x, y.y, fmaf(-a.y, y.x, d.y)));
+  static __device__ __forceinline__ V fma_(V a, V b, V c) {  // a * b + c
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+  }
+  static __device__ __forceinline__ V inv(V a) {
+    const float d = __frcp_rn(fmaf(a.x, a.x, a.y * a.y));
+    return make_float2(a.x * d, -a.y * d);
+  }
+  static __device__ __forceinline__ V mk(float x, float y) { return make_float2(x, y); }
+  static __device__ __forceinline__ V shfl_up(V v, int d) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+  }
+  static __device__ __forceinline__ V shfl_down(V v, int d) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
   }
 };
 template <> struct cx_ops<double> {
@@ -581,77 +593,261 @@ template <> struct cx_ops<double> {
   static __device__ __forceinline__ V mul(V a, V b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
   }
-  static __device__ __forceinline__ V fms(V d, V a, V y) {
-    return make_double2(fma(-a.x, y.x, fma(a.y, y.y, d.x)), fma(-a.x, y.y, fma(-a.y, y.x, d.y)));
+  static __device__ __forceinline__ V fma_(V a, V b, V c) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+  }
+  static __device__ __forceinline__ V inv(V a) {
+    const double d = 1.0 / fma(a.x, a.x, a.y * a.y);
+    return make_double2(a.x * d, -a.y * d);
+  }
+  static __device__ __forceinline__ V mk(double x, double y) { return make_double2(x, y); }
+  static __device__ __forceinline__ V shfl_up(V v, int d) {
+    return make_double2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+  }
+  static __device__ __forceinline__ V shfl_down(V v, int d) {
+    return make_double2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
   }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(64) k_trivar_factor(TriVarArgs<T> a) {
+// LU factors of each frequency's system, in FP64, stored in T ([J][n]): pivot_i = b_i - o c'_{i-1},
+// c'_i = o / pivot_i, b_i = sigma_j m_d + k_d + r_i, o = sigma_j m_o + k_o. The low frequencies
+// give systems close to the (singular-looking) Laplacian, where this recurrence is only neutrally
+// stable and FP32 rounding would accumulate along the line, hence FP64. The recurrence is a
+// Moebius map of c'_{i-1}: with c' = u / v, (u_i, v_i) = M_i (u_{i-1}, v_{i-1}),
+// M_i = [[0, o], [-o, b_i]], (u_{-1}, v_{-1}) = (0, 1). One CTA per frequency: each thread
+// multiplies the matrices of its PER rows, a scan of the products (rescaled by powers of two,
+// which leaves the ratio u / v unchanged) gives c' entering each chunk, and the thread then runs
+// the recurrence over its rows.
+struct cm2 { double2 a, b, c, d; };  // [[a, b], [c, d]]
+__device__ __forceinline__ double2 zmul(double2 x, double2 y) {
+  return make_double2(fma(x.x, y.x, -x.y * y.y), fma(x.x, y.y, x.y * y.x));
+}
+__device__ __forceinline__ double2 zfma(double2 x, double2 y, double2 z) {
+  return make_double2(fma(x.x, y.x, fma(-x.y, y.y, z.x)), fma(x.x, y.y, fma(x.y, y.x, z.y)));
+}
+__device__ __forceinline__ cm2 cm_mul(const cm2& X, const cm2& Y) {  // X Y
+  cm2 R;
+  R.a = zfma(X.a, Y.a, zmul(X.b, Y.c));
+  R.b = zfma(X.a, Y.b, zmul(X.b, Y.d));
+  R.c = zfma(X.c, Y.a, zmul(X.d, Y.c));
+  R.d = zfma(X.c, Y.b, zmul(X.d, Y.d));
+  return R;
+}
+__device__ __forceinline__ cm2 cm_rescale(cm2 X) {  // divide by a power of two near the largest entry
+  const double m = fmax(fmax(fmax(fabs(X.a.x), fabs(X.a.y)), fmax(fabs(X.b.x), fabs(X.b.y))),
+                        fmax(fmax(fabs(X.c.x), fabs(X.c.y)), fmax(fabs(X.d.x), fabs(X.d.y))));
+  if (!(m > 0.0)) return X;
+  int e;
+  frexp(m, &e);
+  const double s = ldexp(1.0, -e);
+  X.a.x *= s; X.a.y *= s; X.b.x *= s; X.b.y *= s; X.c.x *= s; X.c.y *= s; X.d.x *= s; X.d.y *= s;
+  return X;
+}
+__device__ __forceinline__ cm2 cm_shfl_up(const cm2& X, int d) {
+  cm2 R;
+  R.a = make_double2(__shfl_up_sync(0xffffffffu, X.a.x, d), __shfl_up_sync(0xffffffffu, X.a.y, d));
+  R.b = make_double2(__shfl_up_sync(0xffffffffu, X.b.x, d), __shfl_up_sync(0xffffffffu, X.b.y, d));
+  R.c = make_double2(__shfl_up_sync(0xffffffffu, X.c.x, d), __shfl_up_sync(0xffffffffu, X.c.y, d));
+  R.d = make_double2(__shfl_up_sync(0xffffffffu, X.d.x, d), __shfl_up_sync(0xffffffffu, X.d.y, d));
+  return R;
+}
+
+template <typename T, int PER>
+__global__ void __launch_bounds__(256) k_trivar_factor(TriVarArgs<T> a) {
   using V = typename c2<T>::t;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.J) return;
+  __shared__ cm2 tot[8];
+  const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int n = a.n, i0 = t * PER;
   const V sg = reinterpret_cast<const V*>(a.sigma)[j];
-  const double sx = (double)sg.x, sy = (double)sg.y;
-  const double ox = sx * a.mo + a.ko, oy = sy * a.mo;  // off-diagonal sigma_j m_o + k_o
-  V* ip = reinterpret_cast<V*>(a.ip);
-  V* cp = reinterpret_cast<V*>(a.cp);
-  double cx = 0.0, cy = 0.0;                           // c'_{i-1}
-  for (int i = 0; i < a.n; ++i) {
-    // pivot_i = b_i - o c'_{i-1}
-    const double px = sx * a.md + a.kd + a.r[i] - (ox * cx - oy * cy);
-    const double py = sy * a.md - (ox * cy + oy * cx);
-    const double d = 1.0 / (px * px + py * py);
-    const double ix = px * d, iy = -py * d;            // 1 / pivot_i
-    cx = ox * ix - oy * iy;                            // c'_i = o / pivot_i
-    cy = ox * iy + oy * ix;
-    const size_t at = (size_t)i * a.J + j;
-    ip[at].x = (T)ix; ip[at].y = (T)iy;
-    cp[at].x = (T)cx; cp[at].y = (T)cy;
+  const double2 o = make_double2((double)sg.x * a.mo + a.ko, (double)sg.y * a.mo);
+  const double2 mo_ = make_double2(-o.x, -o.y);
+  const double bx = (double)sg.x * a.md + a.kd, by = (double)sg.y * a.md;
+  const double2 z0 = make_double2(0.0, 0.0), one = make_double2(1.0, 0.0);
+  // product of this chunk's matrices, later rows on the left
+  cm2 P{one, z0, z0, one};
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = i0 + q;
+    if (i < n) {
+      const double2 bi = make_double2(bx + a.r[i], by);
+      // [[0, o], [-o, b_i]] P
+      cm2 R;
+      R.a = zmul(o, P.c);
+      R.b = zmul(o, P.d);
+      R.c = zfma(mo_, P.a, zmul(bi, P.c));
+      R.d = zfma(mo_, P.b, zmul(bi, P.d));
+      P = R;
+    }
+  }
+  P = cm_rescale(P);
+  // inclusive warp scan: P <- P (lower lanes' product)
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const cm2 U = cm_shfl_up(P, d);
+    if (lane >= d) P = cm_rescale(cm_mul(P, U));
+  }
+  if (lane == 31) tot[w] = P;
+  __syncthreads();
+  // (u, v) entering the chunk: the warps below, then the lanes below, applied to (0, 1)
+  double2 u = z0, v = one;
+  for (int q = 0; q < w; ++q) {
+    const cm2& X = tot[q];
+    const double2 nu = zfma(X.a, u, zmul(X.b, v)), nv = zfma(X.c, u, zmul(X.d, v));
+    u = nu; v = nv;
+  }
+  {
+    const cm2 E = cm_shfl_up(P, 1);
+    if (lane > 0) {
+      const double2 nu = zfma(E.a, u, zmul(E.b, v)), nv = zfma(E.c, u, zmul(E.d, v));
+      u = nu; v = nv;
+    }
+  }
+  // c'_{i0-1} = u / v, then the recurrence over the chunk
+  double2 c;
+  {
+    const double dd = 1.0 / fma(v.x, v.x, v.y * v.y);
+    c = zmul(u, make_double2(v.x * dd, -v.y * dd));
+  }
+  V* ip = reinterpret_cast<V*>(a.ip) + (size_t)j * n;
+  V* cp = reinterpret_cast<V*>(a.cp) + (size_t)j * n;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = i0 + q;
+    if (i < n) {
+      const double2 piv = zfma(mo_, c, make_double2(bx + a.r[i], by));
+      const double dd = 1.0 / fma(piv.x, piv.x, piv.y * piv.y);
+      const double2 iq = make_double2(piv.x * dd, -piv.y * dd);
+      c = zmul(o, iq);
+      ip[i].x = (T)iq.x; ip[i].y = (T)iq.y;
+      cp[i].x = (T)c.x; cp[i].y = (T)c.y;
+    }
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(64) k_trivar_solve(TriVarArgs<T> a) {
+// One CTA per frequency j. Both substitutions are first-order affine recurrences,
+//   forward  y_i = A_i y_{i-1} + B_i,   A_i = -o / pivot_i,  B_i = b_i / pivot_i,
+//   backward q_i = -c'_i q_{i+1} + y_i,
+// evaluated as parallel scans of the affine maps x -> A x + B under composition: each thread
+// composes the maps of its PER consecutive rows (registers), a warp scan with shuffles and a scan
+// of the 8 warp totals give each thread the value entering its chunk, and the thread then runs its
+// rows. |A_i| < 1 for the diagonally dominant systems, so the composed products stay bounded.
+template <typename T, int PER>
+__global__ void __launch_bounds__(256) k_trivar_solve(TriVarArgs<T> a) {
   using V = typename c2<T>::t;
   using O = cx_ops<T>;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.J) return;
+  __shared__ V tA[8], tB[8];
+  const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int n = a.n;
   const V sg = reinterpret_cast<const V*>(a.sigma)[j];
-  V o;                                                 // off-diagonal sigma_j m_o + k_o
-  o.x = (T)((double)sg.x * a.mo + a.ko);
-  o.y = (T)((double)sg.y * a.mo);
-  V* row = reinterpret_cast<V*>(a.S) + (size_t)j * a.n;
-  const V* ip = reinterpret_cast<const V*>(a.ip) + j;
-  const V* cp = reinterpret_cast<const V*>(a.cp) + j;
-  const size_t J = a.J;
-  // forward: y_i = (b_i - o y_{i-1}) / pivot_i
-  V y;
-  y.x = 0; y.y = 0;
-#pragma unroll 4
-  for (int i = 0; i < a.n; ++i) {
-    y = O::mul(O::fms(row[i], o, y), ip[(size_t)i * J]);
-    row[i] = y;
+  const V mo = O::mk((T)(-((double)sg.x * a.mo + a.ko)), (T)(-((double)sg.y * a.mo)));  // -o
+  V* row = reinterpret_cast<V*>(a.S) + (size_t)j * n;
+  const V* ip = reinterpret_cast<const V*>(a.ip) + (size_t)j * n;
+  const V* cp = reinterpret_cast<const V*>(a.cp) + (size_t)j * n;
+  const V one = O::mk(1, 0), zero = O::mk(0, 0);
+  const int i0 = t * PER;
+  V b[PER], p[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = i0 + q;
+    b[q] = i < n ? row[i] : zero;
+    p[q] = i < n ? ip[i] : zero;   // beyond n: A = B = 0 (a constant map to 0, never used)
   }
-  // backward: q_i = y_i - c'_i q_{i+1}
-  V q;
-  q.x = 0; q.y = 0;
-#pragma unroll 4
-  for (int i = a.n - 1; i >= 0; --i) {
-    q = O::fms(row[i], cp[(size_t)i * J], q);
-    row[i] = q;
+  // ---- forward: compose this chunk's maps (rows in increasing order) ----
+  V cA = one, cB = zero;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    if (i0 + q < n) {
+      const V Ai = O::mul(mo, p[q]), Bi = O::mul(b[q], p[q]);
+      cB = O::fma_(Ai, cB, Bi);
+      cA = O::mul(Ai, cA);
+    }
+  }
+  // inclusive warp scan: (cA, cB) <- mine o lower lanes'
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const V uA = O::shfl_up(cA, d), uB = O::shfl_up(cB, d);
+    if (lane >= d) {
+      cB = O::fma_(cA, uB, cB);
+      cA = O::mul(cA, uA);
+    }
+  }
+  if (lane == 31) { tA[w] = cA; tB[w] = cB; }
+  __syncthreads();
+  // value entering the chunk: (inclusive scan of the lanes below) applied to the warps below
+  V x = zero;  // y_{-1} = 0
+  for (int q = 0; q < w; ++q) x = O::fma_(tA[q], x, tB[q]);
+  {
+    const V eA = O::shfl_up(cA, 1), eB = O::shfl_up(cB, 1);
+    if (lane > 0) x = O::fma_(eA, x, eB);
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    if (i0 + q < n) {
+      x = O::fma_(O::mul(mo, p[q]), x, O::mul(b[q], p[q]));
+      b[q] = x;  // y_i
+    }
+  }
+  __syncthreads();  // the warp totals are reused below
+  // ---- backward: q_i = -c'_i q_{i+1} + y_i, chunks composed from the top ----
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = i0 + q;
+    p[q] = i < n ? cp[i] : zero;
+    p[q] = O::mk(-p[q].x, -p[q].y);
+  }
+  cA = one;
+  cB = zero;
+#pragma unroll
+  for (int q = PER - 1; q >= 0; --q) {
+    if (i0 + q < n) {
+      cB = O::fma_(p[q], cB, b[q]);
+      cA = O::mul(p[q], cA);
+    }
+  }
+  // inclusive suffix scan over lanes: (cA, cB) <- mine o higher lanes'
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const V uA = O::shfl_down(cA, d), uB = O::shfl_down(cB, d);
+    if (lane + d < 32) {
+      cB = O::fma_(cA, uB, cB);
+      cA = O::mul(cA, uA);
+    }
+  }
+  if (lane == 0) { tA[w] = cA; tB[w] = cB; }
+  __syncthreads();
+  x = zero;  // q_n = 0
+  for (int q = (int)(blockDim.x >> 5) - 1; q > w; --q) x = O::fma_(tA[q], x, tB[q]);
+  {
+    const V eA = O::shfl_down(cA, 1), eB = O::shfl_down(cB, 1);
+    if (lane < 31) x = O::fma_(eA, x, eB);
+  }
+#pragma unroll
+  for (int q = PER - 1; q >= 0; --q) {
+    if (i0 + q < n) {
+      x = O::fma_(p[q], x, b[q]);
+      row[i0 + q] = x;
+    }
   }
 }
 
 template <typename T> cudaError_t launch_trivar_factor(const TriVarArgs<T>& a, cudaStream_t st) {
+  if (a.n < 1 || a.n > 8 * 256) return cudaErrorInvalidValue;
   prof_begin("trivar_factor", st);
-  k_trivar_factor<T><<<(a.J + 63) / 64, 64, 0, st>>>(a);
+  if (a.n <= 256) k_trivar_factor<T, 1><<<a.J, 256, 0, st>>>(a);
+  else if (a.n <= 512) k_trivar_factor<T, 2><<<a.J, 256, 0, st>>>(a);
+  else if (a.n <= 1024) k_trivar_factor<T, 4><<<a.J, 256, 0, st>>>(a);
+  else k_trivar_factor<T, 8><<<a.J, 256, 0, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_trivar_solve(const TriVarArgs<T>& a, cudaStream_t st) {
+  if (a.n < 1 || a.n > 8 * 256) return cudaErrorInvalidValue;
   prof_begin(sizeof(T) == 4 ? "trivar_solve_f32" : "trivar_solve_f64", st);
-  k_trivar_solve<T><<<(a.J + 63) / 64, 64, 0, st>>>(a);
+  // rows per thread: the smallest of 1, 2, 4, 8 that covers the line with 256 threads
+  if (a.n <= 256) k_trivar_solve<T, 1><<<a.J, 256, 0, st>>>(a);
+  else if (a.n <= 512) k_trivar_solve<T, 2><<<a.J, 256, 0, st>>>(a);
+  else if (a.n <= 1024) k_trivar_solve<T, 4><<<a.J, 256, 0, st>>>(a);
+  else k_trivar_solve<T, 8><<<a.J, 256, 0, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
 }

@@ -130,13 +130,13 @@ struct TriArgs {
 //   (sigma_j m_d + k_d + r_i) q_i + (sigma_j m_o + k_o) (q_{i-1} + q_{i+1}) = b_i,  i = 0..n-1,
 // with (m_d, m_o) the mass row ((1, 0) for finite differences, (4h/6, h/6) for P1 elements),
 // (k_d, k_o) the stiffness row and r = w c the weighted reaction coefficient. The factor kernel
-// computes the LU factors (in FP64) once per reaction coefficient; the solve kernel runs the two
-// substitutions in T on the half spectrum in place. Factors are stored [n][J] (i major), so the
-// threads of a warp (consecutive j) read consecutive addresses.
+// computes the LU factors (in FP64, stored in T) once per reaction coefficient; the solve kernel runs the two
+// substitutions in T on the half spectrum in place. Factors are stored [J][n] (a frequency's
+// factors contiguous).
 template <typename T> struct TriVarArgs {
   void* S;                                 // T2 spectrum [J][n] (in place; solve only)
-  void* ip;                                // T2 [n][J]: 1 / pivot_i
-  void* cp;                                // T2 [n][J]: (sigma_j m_o + k_o) / pivot_i
+  void* ip;                                // T2 [J][n]: 1 / pivot_i
+  void* cp;                                // T2 [J][n]: (sigma_j m_o + k_o) / pivot_i
   const void* sigma;                       // T2 [J]: g_j tau^-alpha
   const double* r;                         // [n]: w c_i (factor only)
   int n, J;

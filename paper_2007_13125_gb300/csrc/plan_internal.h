@@ -101,8 +101,8 @@ struct pint_plan_s {
   // (pint_set_reaction; the linearised operator of Algorithm 3)
   bool react_on = false;
   double* react = nullptr;          // [M] w c_i
-  void* tri_ip = nullptr;           // [M][N/2+1] T2: inverse pivots of the shifted systems
-  void* tri_cp = nullptr;           // [M][N/2+1] T2: eliminated super-diagonal
+  void* tri_ip = nullptr;           // [N/2+1][M] T2: inverse pivots of the shifted systems
+  void* tri_cp = nullptr;           // [N/2+1][M] T2: eliminated super-diagonal
   // Algorithm 3 workspaces (allocated on first use)
   double* nl_F = nullptr;           // [N][M] right-hand side of the linearised problem
   double* nl_U0 = nullptr;          // [N][M] previous outer iterate

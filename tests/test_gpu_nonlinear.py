@@ -3,6 +3,7 @@ solve with A + w diag(c) (tridiagonal spatial solves), the semilinear source, th
 of the modified Newton iteration, and its limit, the sequential semilinear solution."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import workloads
 from gpu_helpers import device_inputs, rel_l2, torch_cuda
@@ -47,7 +48,7 @@ def test_reaction_solve_matches_oracle(kw):
     c = reaction_field(p)
     Mass, A, w = oracle_ops(p)
     zero = (0.0, 0.0, 0.0, 0.0)
-    Ar = A + w * np.diag(c)
+    Ar = sp.csc_matrix(A + w * sp.diags(c))
     Fo = nl.nl_rhs(p.k, p.alpha, p.tau, Mass, Ar, w, zero, p.v, p.f(), p.fderiv())
     ref = nl.solve_sequential_nl(p.k, p.alpha, p.tau, Mass, Ar, w, zero, Fo)
     v, f, fd = device_inputs(p, torch)
