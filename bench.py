@@ -542,9 +542,15 @@ def run_once(precision: str) -> int:
     with Plan.for_problem(p, precision) as plan:
         F = torch.empty((p.N, p.M), dtype=torch.float64, device=dev)
         U = torch.empty_like(F)
-        plan.form_rhs(v, f, fd, F)
-        plan.initial_guess(v, U)
-        st, sweeps, upd = plan.solve(F, U, tol=TOL, max_sweeps=30)
+        if isinstance(p, workloads.NlProblem):
+            plan.nl_form_rhs(p.g, v, f, fd, F)
+            plan.initial_guess(v, U)
+            st, sweeps, upd = plan.nl_solve(p.g, F, U, newton_tol=NL_NEWTON_TOL, max_steps=20, tol=NL_TOL,
+                                            max_sweeps=40)
+        else:
+            plan.form_rhs(v, f, fd, F)
+            plan.initial_guess(v, U)
+            st, sweeps, upd = plan.solve(F, U, tol=TOL, max_sweeps=30)
         torch.cuda.synchronize()
     print(json.dumps({"once": precision, "workload": p.name, "sweeps": sweeps, "final_update": upd}))
     return 0
