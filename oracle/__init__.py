@@ -31,6 +31,9 @@ Secondary routes, for pinning and for iterate-by-iterate references:
                     method, and Algorithm 3 (modified Newton with the
                     Jacobian at the time average, inner WR of eq. (4.7)):
                     Table 4.
+* ``windows``    -- time windows for BDF-k (the remark closing Sec. 4.3):
+                    the right-hand side of a window after the first, and
+                    Algorithm 3 window by window.
 
 Parity status of each function is stated in its docstring; every function
 listed above is pinned by ``tests/test_oracle_*.py``.
