@@ -149,6 +149,22 @@ size_t pint_plan_workspace_bytes(pint_plan plan);
 pint_status pint_form_rhs(pint_plan plan, const double* v, const double* f, const double* fderiv,
                           double* Fhat, void* stream);
 
+/* Time windows (BDF-k, alpha = 1; the remark closing Sec. 4.3): a horizon of W N levels solved as
+ * W windows of N levels with this plan, each window restarted from the previous one. K is lower
+ * triangular with k sub-diagonal blocks in time, so window w >= 2 is the all-at-once system
+ * K U = F_hat of this plan with
+ *   F_hat_n = f(t_n) - tau^-1 sum_{j=n}^{k} omega_j U_prev^{N+n-j}   (n = 1..k),   f(t_n)   (n > k),
+ * U_prev the previous window's solution (P1 elements: M_h U_prev), and the windows together are
+ * the sequential solution of the whole horizon. The first window is formed by pint_form_rhs /
+ * pint_nl_form_rhs; a natural initial guess for window w is its predecessor's last level
+ * (pint_initial_guess with v = U_prev + (N-1) M). The semilinear term is pointwise in time, so
+ * pint_nl_solve runs per window unchanged (its linearisation point follows the window).
+ * f [N][M] device: f(t_n) (or load vectors) at the window's levels; U_prev [N][M] device;
+ * Fhat [N][M] device output. PINT_EINVAL for alpha < 1 (the CQ history would reach every earlier
+ * window) or while a reaction term is installed. Asynchronous on `stream`. */
+pint_status pint_form_rhs_window(pint_plan plan, const double* f, const double* U_prev, double* Fhat,
+                                 void* stream);
+
 /* Initial guess U_0^n = v for n = 1..N (the starting iterate of Theorem 2.7).
  * v [M] device; U [N][M] device, output. Asynchronous on `stream`. */
 pint_status pint_initial_guess(pint_plan plan, const double* v, double* U, void* stream);

@@ -95,6 +95,26 @@ __global__ void __launch_bounds__(256) k_nl_fd0(const double* __restrict__ fd, c
   out[idx] = x;
 }
 
+// Right-hand side of a time window after the first (BDF-k, alpha = 1): level n (0-based) of
+// F = f minus the BDF terms reaching into the previous window Up [Np][M]:
+//   F_n = f_n - sum_{j=n+1}^{k} c_j (M Up)_{Np + n - j},   c_j = omega_j / tau,
+// with M the identity, or the P1 mass matrix (h/6)[1 4 1] (fem). Grid (points, levels).
+__global__ void __launch_bounds__(256) k_window_rhs(const double* __restrict__ f, const double* __restrict__ Up,
+                                                    double* __restrict__ F, int Np, int M, int k, WinCoef c, int fem,
+                                                    double m6) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int n = blockIdx.y;
+  double x = f[(size_t)n * M + i];
+  for (int j = n + 1; j <= k; ++j) {
+    const double* row = Up + (size_t)(Np + n - j) * M;
+    double u = row[i];
+    if (fem) u = m6 * (4.0 * u + (i > 0 ? row[i - 1] : 0.0) + (i + 1 < M ? row[i + 1] : 0.0));
+    x -= c.c[j] * u;
+  }
+  F[(size_t)n * M + i] = x;
+}
+
 // out = w c
 __global__ void __launch_bounds__(256) k_scale(const double* __restrict__ c, double w, int M, double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,6 +149,14 @@ cudaError_t launch_nl_norms(const double* U, const double* U0, size_t NM, double
 cudaError_t launch_nl_fd0(const double* fd, const double* v, const NlPoly& g, double w, const double* r, int rows,
                           int M, double* out, cudaStream_t st) {
   k_nl_fd0<<<dim3((M + 255) / 256, rows), 256, 0, st>>>(fd, v, g, w, r, M, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_rhs(const double* f, const double* Up, double* F, int N, int Np, int M, int k,
+                              const WinCoef& c, int fem, double m6, cudaStream_t st) {
+  prof_begin("window_rhs", st);
+  k_window_rhs<<<dim3((M + 255) / 256, N), 256, 0, st>>>(f, Up, F, Np, M, k, c, fem, m6);
+  prof_end(st);
   return cudaGetLastError();
 }
 

@@ -189,6 +189,10 @@ cudaError_t launch_nl_fd0(const double* fd, const double* v, const NlPoly& g, do
                           int M, double* out, cudaStream_t st);
 // out = w c ([M])
 cudaError_t launch_scale(const double* c, double w, int M, double* out, cudaStream_t st);
+// time windows (BDF-k): F = f minus the BDF terms on the previous window's levels Up [Np][M]
+struct WinCoef { double c[kMaxK + 1]; };  // omega_j / tau
+cudaError_t launch_window_rhs(const double* f, const double* Up, double* F, int N, int Np, int M, int k,
+                              const WinCoef& c, int fem, double m6, cudaStream_t st);
 
 // ---- convergence control (shared by the host loop and the graph's device-side check) ----
 struct SolveCtl {

@@ -681,6 +681,19 @@ extern "C" pint_status pint_form_rhs(pint_plan p, const double* v, const double*
   return form_rhs(p, v, f, fderiv, Fhat, (cudaStream_t)stream, nullptr);
 }
 
+extern "C" pint_status pint_form_rhs_window(pint_plan p, const double* f, const double* U_prev, double* Fhat,
+                                            void* stream) {
+  if (!p || !f || !U_prev || !Fhat) return fail(PINT_EINVAL, "NULL argument");
+  if (p->cq) return fail(PINT_EINVAL, "time windows need alpha = 1 (the CQ history reaches every earlier window)");
+  if (p->react_on) return fail(PINT_EINVAL, "a reaction term is installed (pint_set_reaction(plan, NULL) removes it)");
+  WinCoef c{};
+  for (int j = 0; j <= p->k; ++j) c.c[j] = p->omega[j] / p->tau;
+  cudaError_t e = launch_window_rhs(f, U_prev, Fhat, p->N, p->N, p->M, p->k, c, p->fem ? 1 : 0,
+                                    1.0 / (6.0 * (p->mx + 1)), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "window rhs kernel");
+  return PINT_OK;
+}
+
 extern "C" pint_status pint_initial_guess(pint_plan p, const double* v, double* U, void* stream) {
   if (!p || !v || !U) return fail(PINT_EINVAL, "NULL argument");
   cudaError_t e = launch_bcast_d(v, U, p->N, p->M, (cudaStream_t)stream);

@@ -112,6 +112,7 @@ def lib():
         "pint_kernel_stats": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I),
                                    ctypes.POINTER(_D), _I]),
         "pint_set_reaction": (_I, [_P, _P, _P]),
+        "pint_form_rhs_window": (_I, [_P, _P, _P, _P, _P]),
         "pint_nl_form_rhs": (_I, [_P, ctypes.POINTER(_Poly), _P, _P, _P, _P, _P]),
         "pint_nl_solve": (_I, [_P, ctypes.POINTER(_Poly), _P, _P, _D, _I, _D, _I, ctypes.POINTER(_NlInfo), _P]),
     }
@@ -267,6 +268,10 @@ class Plan:
     def form_rhs(self, v, f, fderiv, Fhat, stream=None):
         check(lib().pint_form_rhs(self.handle, _ptr(v), _ptr(f), _ptr(fderiv) if fderiv is not None and fderiv.numel() else None,
                                   _ptr(Fhat), _stream(stream)))
+
+    def form_rhs_window(self, f, U_prev, Fhat, stream=None):
+        """F_hat of a time window after the first (pint_form_rhs_window)."""
+        check(lib().pint_form_rhs_window(self.handle, _ptr(f), _ptr(U_prev), _ptr(Fhat), _stream(stream)))
 
     def initial_guess(self, v, U, stream=None):
         check(lib().pint_initial_guess(self.handle, _ptr(v), _ptr(U), _stream(stream)))
