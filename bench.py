@@ -68,7 +68,7 @@ def algo_bytes(name: str, N: int, M: int) -> float:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the workload (`ncu --set full` of `bench.py --once mixed`), valid while the kernel's
 # source is unchanged (sha1 of its translation unit)
-NCU_TRAFFIC = {"resid_fwd_ff": (318.59e6, "kernels_time.cu", "dc0370d7664232048cd8c377e5c408bf737d1ac8")}
+NCU_TRAFFIC = {"resid_fwd_ff": (318.81e6, "kernels_time.cu", "4d2355f1518451d0a3722c6f4b2a1a3ebda0262f")}
 
 
 def traffic_for(name: str):
