@@ -3,7 +3,8 @@
 Workload (one "step" = one whole solve through the hot path): 2D heat on the unit square,
 255 x 255 interior points, N = 256 steps, T = 1, BDF4 with starting-step corrections,
 kappa = 0.05, f = e^{-t} sin(pi x) sin(2 pi y), v a 64 x 64-mode random sine series (seed 1).
-A step forms F_hat from (v, f, d^l f(0)), sets U_0 = v and runs WR sweeps until the
+A step forms F_hat from (v, f, d^l f(0)) and runs WR sweeps from U_0^n = v (pint_solve_v: the
+first sweep's residual F_hat - beta_n v - A v is formed from v, U_0 is never written) until the
 solver's a-posteriori error estimate is below tol = 1e-8 (the estimate includes the rounding
 floor of the FP32 inner solves; relative l2 error <= 1e-8 against the sequential FP64 solution
 is checked at this size and tolerance by tests/test_gpu_parity.py).
@@ -42,6 +43,8 @@ def algo_bytes(name: str, N: int, M: int) -> float:
     NM, JM = N * M, (N // 2 + 1) * M
     table = {
         "resid_fwd_ff": 16 * NM + 8 * JM,       # read U, F_hat (double-float); write half spectrum
+        "resid_v0_ff": 8 * NM + 8 * JM,         # first sweep from v: read F_hat; write half spectrum
+        "inv_update_v0_ff": 8 * JM + 8 * NM,    # first sweep: read spectrum; write U (double-float)
         "inv_update_ff": 8 * JM + 16 * NM,      # read spectrum; read + write U (double-float)
         "dst_f32": 16 * JM,                     # read + write spectrum (complex float)
         "axis_solve_f32": 16 * JM,
@@ -549,8 +552,7 @@ def run_once(precision: str) -> int:
                                             max_sweeps=40)
         else:
             plan.form_rhs(v, f, fd, F)
-            plan.initial_guess(v, U)
-            st, sweeps, upd = plan.solve(F, U, tol=TOL, max_sweeps=30)
+            st, sweeps, upd = plan.solve_v(F, v, U, tol=TOL, max_sweeps=30)
         torch.cuda.synchronize()
     print(json.dumps({"once": precision, "workload": p.name, "sweeps": sweeps, "final_update": upd}))
     return 0
@@ -628,8 +630,7 @@ def main():
     def step(prec):
         plan = plans[prec]
         plan.form_rhs(v, f, fd, F, stream)
-        plan.initial_guess(v, U, stream)
-        st, sweeps, upd = plan.solve(F, U, tol=TOL, max_sweeps=30, stream=stream)
+        st, sweeps, upd = plan.solve_v(F, v, U, tol=TOL, max_sweeps=30, stream=stream)
         last[prec] = (sweeps, upd)
 
     def barrier():
@@ -675,11 +676,14 @@ def main():
     t_clk0 = time.monotonic()
     ms_mixed, lat_mixed = timed("mixed", args.steps, 0, per_step=True)
     clocks = clk.stop(t_clk0, time.monotonic())
-    # our kernels per solve: form_rhs, initial guess, conversion in/out, sweeps x (sweep kernels +
-    # the device-side convergence check), control init
+    # our kernels per solve: form_rhs, control init, the first sweep from v (no history product),
+    # the later sweeps (with the CQ history product), each with the device-side convergence check
+    # (graph launches), conversion out
     sweeps_main = last["mixed"][0]
-    per_sweep = (5 if p.dim == 2 else 3) + (1 if p.alpha != 1.0 else 0)
-    launches = args.steps * (2 + 2 + 1 + sweeps_main * (per_sweep + (0 if args.per_sweep_launches else 1)))
+    spatial_k = {1: 1, 2: 3, 3: 5}[p.dim]
+    per_sweep = 2 + spatial_k + (1 if p.alpha != 1.0 else 0)
+    check = 0 if args.per_sweep_launches else 1
+    launches = args.steps * (1 + 1 + (2 + spatial_k + check) + (sweeps_main - 1) * (per_sweep + check) + 1)
 
     # ---- per-kernel CUDA-event times: the same kernels launched sweep by sweep ----
     pint.set_profiling(True)
@@ -730,8 +734,7 @@ def main():
             if i - 2 in ev_out:
                 stream.wait_event(ev_out[i - 2])  # U of this set copied out by step i-2
             plan_m.form_rhs(vv, ff, ffd, F, stream)
-            plan_m.initial_guess(vv, UU, stream)
-            plan_m.solve_async(F, UU, tol=TOL, max_sweeps=30, stream=stream)
+            plan_m.solve_v_async(F, vv, UU, tol=TOL, max_sweeps=30, stream=stream)
             ev = torch.cuda.Event()
             ev.record(stream)
             ev_c[i] = ev

@@ -193,6 +193,21 @@ pint_status pint_wr_sweep(pint_plan plan, const double* Fhat, const double* U_pr
 pint_status pint_solve(pint_plan plan, const double* Fhat, double* U, double tol, int max_sweeps,
                        int* sweeps_out, double* upd_rel_out, void* stream);
 
+/* pint_solve from the initial guess U_0^n = v of Theorem 2.7 (every level equal to the initial
+ * value), without materialising it: for that iterate K U_0 = beta_n M v + A v with
+ * beta_n = tau^-alpha sum_{j<n} omega_j (BDF and CQ alike), so the first residual is
+ * F_hat_n - beta_n M v - A v, formed in one pass over F_hat with no read of U (and, for CQ, no
+ * history product), and the first update writes U_1 = v + c. The iterates and the stopping rule
+ * are those of pint_initial_guess followed by pint_solve. v [M] device (FP64); U [N][M] device,
+ * output only (its input content is not read). PINT_MIXED runs the first sweep this way; the
+ * FP64 and FP32 paths broadcast v into U inside the solve's graph. */
+pint_status pint_solve_v(pint_plan plan, const double* Fhat, const double* v, double* U, double tol,
+                         int max_sweeps, int* sweeps_out, double* upd_rel_out, void* stream);
+
+/* pint_solve_v enqueued without waiting (as pint_solve_async; result by pint_solve_result). */
+pint_status pint_solve_v_async(pint_plan plan, const double* Fhat, const double* v, double* U, double tol,
+                               int max_sweeps, void* stream);
+
 /* The whole solve of pint_solve (one graph launch) enqueued on `stream` without waiting, so that
  * host transfers or other work can be queued behind it. The plan's workspaces stay in use until
  * the stream has completed the solve: later calls on the same plan must be ordered after it

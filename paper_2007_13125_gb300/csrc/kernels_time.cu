@@ -402,7 +402,8 @@ __device__ __forceinline__ void cp_async_wait_pending(int n) {
 // slot is refilled with the level RING further on, so the loads stay in flight behind the
 // arithmetic and the stores. A thread reads only slots it filled itself (no block barrier).
 // LOGN > 0: compiled for N = 2^LOGN levels and 2^LOGC columns; LOGN = 0: any shape.
-template <int LOGN, int LOGC>
+// V0: the first sweep from U_0^n = v: U = v + c, v read once per point (no U stream, no ring)
+template <int LOGN, int LOGC, bool V0>
 __global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
   constexpr bool CT = LOGN > 0;
   constexpr int CT_RING = CT ? inv_ring_levels(1 << LOGN, 1 << LOGC) : 1;
@@ -443,17 +444,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
   // 2. the first rounds of U into the ring (one group per round)
   const float* uh_src = a.Uhi + m;
   const float* ul_src = a.Ulo + m;
-  for (int d = 0; d < depth; ++d) {
-    const int i = d * LPR + r0;  // < RING
-    if (valid && i < N) {
-      cp_async4(ring_h + (i << logP2) + q, uh_src + (size_t)i * M);
-      cp_async4(ring_l + (i << logP2) + q, ul_src + (size_t)i * M);
+  if constexpr (!V0) {
+    for (int d = 0; d < depth; ++d) {
+      const int i = d * LPR + r0;  // < RING
+      if (valid && i < N) {
+        cp_async4(ring_h + (i << logP2) + q, uh_src + (size_t)i * M);
+        cp_async4(ring_l + (i << logP2) + q, ul_src + (size_t)i * M);
+      }
+      cp_async_commit();
     }
-    cp_async_commit();
+    // 3. spectrum complete (the depth U groups committed after it may still be pending)
+    if constexpr (CT) cp_async_wait<CT_DEPTH < 7 ? CT_DEPTH : 7>();
+    else cp_async_wait_pending(depth);
+  } else {
+    cp_async_wait_all();
   }
-  // 3. spectrum complete (the depth U groups committed after it may still be pending)
-  if constexpr (CT) cp_async_wait<CT_DEPTH < 7 ? CT_DEPTH : 7>();
-  else cp_async_wait_pending(depth);
   __syncthreads();
   for (int it = threadIdx.x; it < (J << logC); it += kThreads) {
     const int cc = it & (C - 1), j = it >> logC;
@@ -478,6 +483,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
   const float* Xf = reinterpret_cast<const float*>(X) + 2 * (q & (C - 1)) + (q >= C ? 1 : 0);
   float* uh_dst = a.Uhi + m;
   float* ul_dst = a.Ulo + m;
+  if constexpr (V0) {
+    const ff u0 = valid ? ff_from_double(a.v[m]) : ff{0.f, 0.f};
+    for (int i = r0; i < N; i += LPR) {
+      const float cval = Xf[(size_t)2 * i * C] * __ldg(a.inv_s + i);
+      if (valid) {
+        const ff u = ff_add_f(u0, cval);
+        uh_dst[(size_t)i * M] = u.hi;
+        ul_dst[(size_t)i * M] = u.lo;
+        sc = fmaf(cval, cval, sc);
+        su = fmaf(u.hi, u.hi, su);
+      }
+    }
+    block_reduce_add2((double)sc, (double)su, a.norms);
+    return;
+  }
   for (int i = r0; i < N; i += LPR) {
     if constexpr (CT) cp_async_wait<(CT_DEPTH - 1 < 7 ? CT_DEPTH - 1 : 7)>();
     else cp_async_wait_pending(depth - 1);  // the group of level i is complete
@@ -880,6 +900,108 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 
 static int tiles(int M, int C) { return (M + 2 * C - 1) / (2 * C); }
 
+// ---------------------------------------------------------------------------
+// MIXED, first sweep from the initial guess U_0^n = v of every level (Theorem 2.7). Then
+// K U_0 = tau^-alpha (sum_{j<n} omega_j) M v + A v = beta_n M v + A v for BDF and CQ alike, so
+//   r_0^n = F_hat_n - beta_n M v - A v   (- w c v with a reaction term),
+// with A v (and M v) formed once per point: no U is read, no history is formed, and the kernel
+// reads F_hat and writes the half spectrum like k_resid_fwd (same tile, same transform).
+// ---------------------------------------------------------------------------
+template <int DIM, bool FEM, bool PER>
+__global__ void __launch_bounds__(kThreads, 4) k_resid_v0(ResidFwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = a.N, C = a.C, M = a.M, logC = a.logC, mx = a.mx;
+  float2 *X, *tw;
+  unsigned short* perm;
+  time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
+  const int P2 = 2 * C, logP2 = logC + 1;
+  const int G = resid_groups(N, C), NL = N / G;
+  const int q = threadIdx.x & (P2 - 1), g = threadIdx.x >> logP2;
+  const int m = blockIdx.x * P2 + q;
+  const bool valid = g < G && m < M;
+  constexpr bool two_d = DIM >= 2, three_d = DIM == 3, per = PER;
+  const int mxy = mx * a.my;
+  const int xq = m % mx;
+  const int dW = (!per || xq > 0) ? -1 : mx - 1, dE = (!per || xq < mx - 1) ? 1 : 1 - mx;
+  const int dS = (!per || m >= mx) ? -mx : M - mx, dN = (!per || m + mx < M) ? mx : mx - M;
+  const bool hasW = valid && (xq > 0 || per), hasE = valid && (xq < mx - 1 || per);
+  const int mp = three_d ? m % mxy : m, Mp = three_d ? mxy : M;
+  const bool hasS = valid && two_d && (mp >= mx || per), hasN = valid && two_d && (mp + mx < Mp || per);
+  const bool hasB = valid && three_d && m >= mxy, hasT = valid && three_d && m + mxy < M;
+  float* Xf = reinterpret_cast<float*>(X) + 2 * (q & (C - 1)) + (q >= C ? 1 : 0);
+
+  // A v (and M v for P1) at this point, in double-float
+  const ff vc = valid ? ff_from_double(a.v[m]) : ff{0.f, 0.f};
+  const ff vw = hasW ? ff_from_double(a.v[m + dW]) : ff{0.f, 0.f};
+  const ff ve = hasE ? ff_from_double(a.v[m + dE]) : ff{0.f, 0.f};
+  const float gx = a.gx_hi;
+  ff_acc Av;
+  Av.init(ff{0.f, 0.f});
+  // centre: 2 gx + 2 gy + 2 gz (FD), 2/h (P1 stiffness) -- exact multiples of powers of two
+  {
+    float b0, e0;
+    two_sum(vw.hi, ve.hi, b0, e0);
+    Av.add_hi(2.f * gx * vc.hi);
+    Av.sl = fmaf(2.f * gx, vc.lo, Av.sl);
+    Av.add_hi(-gx * b0);
+    Av.sl -= gx * (e0 + (vw.lo + ve.lo));
+  }
+  if constexpr (DIM >= 2) {
+    const float gy = a.gy_hi;
+    const ff vs = hasS ? ff_from_double(a.v[m + dS]) : ff{0.f, 0.f};
+    const ff vn = hasN ? ff_from_double(a.v[m + dN]) : ff{0.f, 0.f};
+    float b1, e1;
+    two_sum(vs.hi, vn.hi, b1, e1);
+    Av.add_hi(2.f * gy * vc.hi);
+    Av.sl = fmaf(2.f * gy, vc.lo, Av.sl);
+    Av.add_hi(-gy * b1);
+    Av.sl -= gy * (e1 + (vs.lo + vn.lo));
+  }
+  if constexpr (DIM == 3) {
+    const float gz = a.gz_hi;
+    const ff vb = hasB ? ff_from_double(a.v[m - mxy]) : ff{0.f, 0.f};
+    const ff vt = hasT ? ff_from_double(a.v[m + mxy]) : ff{0.f, 0.f};
+    float b2, e2;
+    two_sum(vb.hi, vt.hi, b2, e2);
+    Av.add_hi(2.f * gz * vc.hi);
+    Av.sl = fmaf(2.f * gz, vc.lo, Av.sl);
+    Av.add_hi(-gz * b2);
+    Av.sl -= gz * (e2 + (vb.lo + vt.lo));
+  }
+  if (DIM == 1 && a.react && valid) Av.fma_term(ff_from_double(a.react[m]), vc, 1.f);
+  const ff Avn = Av.normalized();
+  ff Mv = vc;
+  if constexpr (FEM) {
+    // (h/6)(v_{i-1} + 4 v_i + v_{i+1}) in double-float
+    float b1, e1, b2, e2;
+    two_sum(vw.hi, ve.hi, b1, e1);
+    two_sum(b1, 4.f * vc.hi, b2, e2);
+    const float lo = e1 + e2 + ((vw.lo + ve.lo) + 4.f * vc.lo);
+    Mv = ff_mul(ff{b2, lo}, ff{a.m_hi, a.m_lo});
+  }
+
+  if (g < G) {
+    const int i0 = g * NL, i1 = i0 + NL;
+    double fn = valid ? a.F[(size_t)i0 * M + m] : 0.0;
+#pragma unroll 4
+    for (int i = i0; i < i1; ++i) {
+      const double f = fn;
+      if (i + 1 < i1) fn = valid ? a.F[(size_t)(i + 1) * M + m] : 0.0;
+      ff_acc A;
+      A.init(ff_split_trunc(f));
+      A.fma_term(ff_from_double(__ldg(a.beta + i)), Mv, -1.f);
+      A.sub(Avn);
+      Xf[(size_t)2 * i * C] = valid ? A.value() * __ldg(a.s + i) : 0.f;
+    }
+  }
+  __syncthreads();
+  if (N == 256 && C == 16) fft_forward_ct<8, 4, 16>(X, tw);
+  else if (N == 512 && C == 16) fft_forward_ct<9, 4, 16>(X, tw);
+  else if (N == 1024 && C == 8) fft_forward_ct<10, 3, 8>(X, tw);
+  else fft_forward(X, C, logC, N, tw);
+  store_half_spectrum(X, perm, a.S, N, M, C, logC, (int)blockIdx.x * P2);
+}
+
 template <int K, bool CQ, int DIM, bool FEM, bool PER>
 static cudaError_t launch_resid_k(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
   cudaError_t e = set_smem(k_resid_fwd<K, CQ, DIM, FEM, PER>, sm);
@@ -917,14 +1039,43 @@ cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st) {
   return a.dim == 2 ? launch_resid_d<2, false, false>(a, sm, st) : launch_resid_d<1, false, false>(a, sm, st);
 }
 
+template <int DIM, bool FEM, bool PER>
+static cudaError_t launch_v0_k(const ResidFwdArgs& a, size_t sm, cudaStream_t st) {
+  cudaError_t e = set_smem(k_resid_v0<DIM, FEM, PER>, sm);
+  if (e != cudaSuccess) return e;
+  prof_begin("resid_v0_ff", st);
+  k_resid_v0<DIM, FEM, PER><<<tiles(a.M, a.C), kThreads, sm, st>>>(a);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_v0(const ResidFwdArgs& a, cudaStream_t st) {
+  if (a.gx_lo != 0.f || a.gy_lo != 0.f || !a.v || !a.beta) return cudaErrorInvalidValue;
+  const size_t sm = resid_fwd_smem(a.N, a.C);
+  if (a.fem) return a.dim == 1 && !a.periodic ? launch_v0_k<1, true, false>(a, sm, st) : cudaErrorInvalidValue;
+  if (a.periodic) {
+    if (a.dim == 3) return cudaErrorInvalidValue;
+    return a.dim == 2 ? launch_v0_k<2, false, true>(a, sm, st) : launch_v0_k<1, false, true>(a, sm, st);
+  }
+  if (a.dim == 3) return launch_v0_k<3, false, false>(a, sm, st);
+  return a.dim == 2 ? launch_v0_k<2, false, false>(a, sm, st) : launch_v0_k<1, false, false>(a, sm, st);
+}
+
 template <int LOGN, int LOGC> static cudaError_t launch_inv_k(const InvUpdArgs& a, cudaStream_t st) {
   const size_t sm = inv_upd_smem(a.N, a.C);
-  cudaError_t e = set_smem(k_inv_upd<LOGN, LOGC>, sm);
-  if (e != cudaSuccess) return e;
-  prof_begin("inv_update_ff", st);
   InvUpdArgs b = a;
   b.ring = inv_ring_levels(a.N, a.C);
-  k_inv_upd<LOGN, LOGC><<<tiles(a.M, a.C), kThreads, sm, st>>>(b);
+  if (a.v) {
+    cudaError_t e = set_smem(k_inv_upd<LOGN, LOGC, true>, sm);
+    if (e != cudaSuccess) return e;
+    prof_begin("inv_update_v0_ff", st);
+    k_inv_upd<LOGN, LOGC, true><<<tiles(a.M, a.C), kThreads, sm, st>>>(b);
+  } else {
+    cudaError_t e = set_smem(k_inv_upd<LOGN, LOGC, false>, sm);
+    if (e != cudaSuccess) return e;
+    prof_begin("inv_update_ff", st);
+    k_inv_upd<LOGN, LOGC, false><<<tiles(a.M, a.C), kThreads, sm, st>>>(b);
+  }
   prof_end(st);
   return cudaGetLastError();
 }

@@ -29,6 +29,9 @@ struct ResidFwdArgs {
   int periodic;                            // periodic boundary conditions: neighbours wrap around
   const double* react;                     // 1D: [M] weighted reaction coefficient w c_i; the
                                            // residual loses w c_i U_i^n (null: no reaction term)
+  // first sweep from U_0^n = v (k_resid_v0): r_0^n = F_hat_n - beta_n M v - A v
+  const double* v;                         // [M] (FP64)
+  const double* beta;                      // [N] tau^-alpha sum_{j<n} omega_j, n = 1..N
 };
 
 // MIXED: inverse DFT, times 1/(N kappa^{i/N}), U += c (double-float), norms.
@@ -38,6 +41,7 @@ struct InvUpdArgs {
   int N, M, C, logC;
   double* norms;                           // [0] += sum c^2, [1] += sum U^2
   int ring;                                // levels in the U staging ring (set by the launcher)
+  const double* v;                         // first sweep from U_0^n = v: U = v + c ([M]), else null
 };
 
 // FP64 / FP32: F_{m-1} = F_hat + (P - K) U_{m-1}, times kappa^{i/N}, DFT.
@@ -150,6 +154,8 @@ size_t toep_smem(int N, int C);
 template <typename T> size_t axis_smem(int n, int C, bool has_mu = false);
 
 cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st);
+// first sweep from U_0^n = v (a.v, a.beta set): no U read, no history
+cudaError_t launch_resid_v0(const ResidFwdArgs& a, cudaStream_t st);
 cudaError_t launch_inv_upd(const InvUpdArgs& a, cudaStream_t st);
 template <typename T> cudaError_t launch_direct_fwd(const DirectFwdArgs<T>& a, cudaStream_t st);
 template <typename T> cudaError_t launch_direct_inv(const DirectInvArgs<T>& a, cudaStream_t st);

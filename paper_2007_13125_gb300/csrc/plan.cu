@@ -909,6 +909,38 @@ pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   return PINT_OK;
 }
 
+// MIXED first sweep from U_0^n = v (Theorem 2.7): r_0 = F_hat - beta_n M v - A v in one pass over
+// F_hat (no U read; for CQ no history product), the spatial solves, and U_1 = v + c written as
+// the double-float iterate
+pint_status sweep_mixed_v0(pint_plan p, const double* Fhat, const double* v, cudaStream_t st) {
+  const int N = p->N, M = p->M;
+  PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
+  ResidFwdArgs r{};
+  r.F = Fhat; r.v = v; r.beta = p->beta;
+  r.S = reinterpret_cast<float2*>(p->S);
+  r.s = p->tf.s; r.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
+  r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Cr; r.logC = ilog2c(p->Cr);
+  r.fem = p->fem ? 1 : 0;
+  r.periodic = p->periodic ? 1 : 0;
+  split_ff(1.0 / (6.0 * (p->mx + 1)), r.m_hi, r.m_lo);
+  split_ff(p->gx, r.gx_hi, r.gx_lo);
+  split_ff(p->gy, r.gy_hi, r.gy_lo);
+  split_ff(p->gz, r.gz_hi, r.gz_lo);
+  r.my = p->my;
+  r.react = p->react_on ? p->react : nullptr;
+  cudaError_t e = launch_resid_v0(r, st);
+  if (e != cudaSuccess) return cuda_fail(e, "first-sweep residual kernel");
+  e = spatial<float>(p, p->tf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "spatial kernel");
+  InvUpdArgs u{};
+  u.S = reinterpret_cast<const float2*>(p->S); u.Uhi = p->Uhi; u.Ulo = p->Ulo;
+  u.inv_s = p->tf.inv_s; u.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
+  u.N = N; u.M = M; u.C = p->Cr; u.logC = ilog2c(p->Cr); u.norms = p->norms; u.v = v;
+  e = launch_inv_upd(u, st);
+  if (e != cudaSuccess) return cuda_fail(e, "update kernel");
+  return PINT_OK;
+}
+
 // FP64 / FP32 direct-form sweep: Uout = P^-1 (F + (P - K) Uin)
 template <typename T>
 pint_status sweep_direct(pint_plan p, const DevTables<T>& t, const T* F, const T* Uin, T* Uout,
@@ -1000,7 +1032,7 @@ pint_status sweep_body(pint_plan p, const double* F, double* U, cudaStream_t st)
 }  // namespace
 
 pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, double* U, double tol,
-                                  int max_sweeps) {
+                                  int max_sweeps, const double* v) {
   const size_t NM = (size_t)p->N * p->M;
   const bool prof = g_prof_on;
   g_prof_on = false;  // per-kernel events are host-side records: keep them out of graphs
@@ -1008,27 +1040,36 @@ pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, d
   cudaGraph_t pro = nullptr, epi = nullptr, body = nullptr;
   cudaGraphNode_t npro, nloop, nepi;
   do {
-    // prologue
+    // the while-node's condition (set by the convergence check of each sweep)
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { s = cuda_fail(e, "cudaGraphConditionalHandleCreate"); break; }
+    // prologue (with v and MIXED: the first sweep from U_0^n = v and its convergence check)
     if (cudaGraphCreate(&pro, 0) != cudaSuccess) { s = fail(PINT_ECUDA, "cudaGraphCreate"); break; }
     if ((s = capture_begin(p, pro)) != PINT_OK) break;
     {
       pint_status b = PINT_OK;
-      cudaError_t e = launch_ctl_init(p->ctl, tol, p->q_floor, max_sweeps, p->cap);
-      if (e == cudaSuccess && p->prec == PINT_MIXED) e = launch_d2ff(U, p->Uhi, p->Ulo, NM, p->cap);
-      if (e == cudaSuccess && p->prec == PINT_FP32) {
-        e = launch_d2f(F, p->Fhi, NM, p->cap);
-        if (e == cudaSuccess) e = launch_d2f(U, p->Uhi, NM, p->cap);
+      cudaError_t e1 = launch_ctl_init(p->ctl, tol, p->q_floor, max_sweeps, p->cap);
+      if (e1 == cudaSuccess && v && p->prec != PINT_MIXED) e1 = launch_bcast_d(v, U, p->N, p->M, p->cap);
+      if (e1 == cudaSuccess && p->prec == PINT_MIXED) {
+        if (v) {
+          b = sweep_mixed_v0(p, F, v, p->cap);
+          if (b == PINT_OK) e1 = launch_converge(p->norms, p->ctl, h, p->cap);
+        } else {
+          e1 = launch_d2ff(U, p->Uhi, p->Ulo, NM, p->cap);
+        }
       }
-      if (e != cudaSuccess) b = cuda_fail(e, "graph prologue");
+      if (e1 == cudaSuccess && p->prec == PINT_FP32) {
+        e1 = launch_d2f(F, p->Fhi, NM, p->cap);
+        if (e1 == cudaSuccess) e1 = launch_d2f(U, p->Uhi, NM, p->cap);
+      }
+      if (b == PINT_OK && e1 != cudaSuccess) b = cuda_fail(e1, "graph prologue");
       if ((s = capture_end(p, &pro, b)) != PINT_OK) break;
     }
     if (cudaGraphAddChildGraphNode(&npro, g, nullptr, 0, pro) != cudaSuccess) {
       s = fail(PINT_ECUDA, "cudaGraphAddChildGraphNode"); break;
     }
     // while-node with the sweep body
-    cudaGraphConditionalHandle h;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) { s = cuda_fail(e, "cudaGraphConditionalHandleCreate"); break; }
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
@@ -1069,10 +1110,11 @@ pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, d
 }
 
 pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double tol, int max_sweeps,
-                                cudaStream_t st) {
+                                cudaStream_t st, const double* v) {
   SolveGraph* hit = nullptr;
   for (SolveGraph& c : p->sg)
-    if (c.exec && c.F == F && c.U == U && c.tol == tol && c.max_sweeps == max_sweeps && c.react == p->react_on)
+    if (c.exec && c.F == F && c.U == U && c.v == v && c.tol == tol && c.max_sweeps == max_sweeps &&
+        c.react == p->react_on)
       hit = &c;
   if (!hit) {
     // an empty slot, else the least recently used one
@@ -1088,7 +1130,7 @@ pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double 
     }
     cudaGraph_t g;
     PINT_CUDA(cudaGraphCreate(&g, 0));
-    pint_status s = add_solve_nodes(p, g, F, U, tol, max_sweeps);
+    pint_status s = add_solve_nodes(p, g, F, U, tol, max_sweeps, v);
     if (s == PINT_OK) {
       cudaError_t e = cudaGraphInstantiate(&sg.exec, g, 0);
       if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphInstantiate");
@@ -1098,7 +1140,7 @@ pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double 
       sg.exec = nullptr;
       return s;
     }
-    sg.F = F; sg.U = U; sg.tol = tol; sg.max_sweeps = max_sweeps; sg.react = p->react_on;
+    sg.F = F; sg.U = U; sg.v = v; sg.tol = tol; sg.max_sweeps = max_sweeps; sg.react = p->react_on;
   }
   hit->last_use = ++p->sg_clock;
   PINT_CUDA(cudaGraphLaunch(hit->exec, st));
@@ -1144,6 +1186,14 @@ extern "C" pint_status pint_solve_async(pint_plan p, const double* Fhat, double*
   return solve_enqueue(p, Fhat, U, tol, max_sweeps, (cudaStream_t)stream);
 }
 
+extern "C" pint_status pint_solve_v_async(pint_plan p, const double* Fhat, const double* v, double* U, double tol,
+                                          int max_sweeps, void* stream) {
+  if (!p || !Fhat || !v || !U) return fail(PINT_EINVAL, "NULL argument");
+  if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
+  if (g_prof_on) return fail(PINT_EINVAL, "pint_solve_v_async: not available while per-kernel profiling is on");
+  return solve_enqueue(p, Fhat, U, tol, max_sweeps, (cudaStream_t)stream, v);
+}
+
 extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* upd_rel_out) {
   if (!p) return fail(PINT_EINVAL, "NULL argument");
   int m = 0;
@@ -1156,14 +1206,15 @@ extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* u
   return PINT_OK;
 }
 
-extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, double tol, int max_sweeps,
-                                  int* sweeps_out, double* upd_rel_out, void* stream) {
+namespace {
+// pint_solve (v null: from the content of U) and pint_solve_v (from U_0^n = v)
+pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double* U, double tol, int max_sweeps,
+                       int* sweeps_out, double* upd_rel_out, cudaStream_t st) {
   if (!p || !Fhat || !U) return fail(PINT_EINVAL, "NULL argument");
   if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
-  cudaStream_t st = (cudaStream_t)stream;
   if (!g_prof_on) {
     // one graph launch runs every sweep; the host waits once for the result
-    pint_status gs = solve_enqueue(p, Fhat, U, tol, max_sweeps, st);
+    pint_status gs = solve_enqueue(p, Fhat, U, tol, max_sweeps, st, v);
     if (gs != PINT_OK) return gs;
     PINT_CUDA(cudaStreamSynchronize(st));
     int m = 0;
@@ -1177,16 +1228,27 @@ extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, do
   }
   const size_t NM = (size_t)p->N * p->M;
   cudaError_t e;
-  if (p->prec == PINT_MIXED) {
-    if ((e = launch_d2ff(U, p->Uhi, p->Ulo, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
-  } else if (p->prec == PINT_FP32) {
-    if ((e = launch_d2f(Fhat, p->Fhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
-    if ((e = launch_d2f(U, p->Uhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
-  }
   double prev = -1.0, upd = 0.0;
   int m = 0;
   bool done = false;
   pint_status s = PINT_OK;
+  if (v && p->prec != PINT_MIXED && (e = launch_bcast_d(v, U, p->N, p->M, st)) != cudaSuccess)
+    return cuda_fail(e, "initial guess kernel");
+  if (p->prec == PINT_MIXED) {
+    if (v) {
+      // first sweep from U_0^n = v
+      if ((s = sweep_mixed_v0(p, Fhat, v, st)) != PINT_OK) return s;
+      m = 1;
+      if ((s = read_norms(p, st, &upd)) != PINT_OK) return s;
+      done = stop_decision(m, upd, prev, tol, p->q_floor);
+      prev = upd;
+    } else if ((e = launch_d2ff(U, p->Uhi, p->Ulo, NM, st)) != cudaSuccess) {
+      return cuda_fail(e, "convert");
+    }
+  } else if (p->prec == PINT_FP32) {
+    if ((e = launch_d2f(Fhat, p->Fhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+    if ((e = launch_d2f(U, p->Uhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+  }
   while (m < max_sweeps && !done) {
     if (p->prec == PINT_MIXED) s = sweep_mixed(p, Fhat, st);
     else if (p->prec == PINT_FP64) s = sweep_direct<double>(p, p->td, Fhat, U, U, st);
@@ -1206,6 +1268,18 @@ extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, do
   if (upd_rel_out) *upd_rel_out = upd;
   if (!done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
   return PINT_OK;
+}
+}  // namespace
+
+extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, double tol, int max_sweeps,
+                                  int* sweeps_out, double* upd_rel_out, void* stream) {
+  return solve_impl(p, Fhat, nullptr, U, tol, max_sweeps, sweeps_out, upd_rel_out, (cudaStream_t)stream);
+}
+
+extern "C" pint_status pint_solve_v(pint_plan p, const double* Fhat, const double* v, double* U, double tol,
+                                    int max_sweeps, int* sweeps_out, double* upd_rel_out, void* stream) {
+  if (!v) return fail(PINT_EINVAL, "NULL argument");
+  return solve_impl(p, Fhat, v, U, tol, max_sweeps, sweeps_out, upd_rel_out, (cudaStream_t)stream);
 }
 
 extern "C" pint_status pint_batch_solve(pint_plan* plans, int n, const double* const* Fhat, double* const* U,

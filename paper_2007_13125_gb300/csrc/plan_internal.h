@@ -46,6 +46,7 @@ struct SolveGraph {
   cudaGraphExec_t exec = nullptr;
   const double* F = nullptr;
   double* U = nullptr;
+  const double* v = nullptr;        // solve from U_0^n = v (null: from the content of U)
   double tol = 0.0;
   int max_sweeps = 0;
   bool react = false;               // captured with the reaction term's spatial solve
@@ -121,10 +122,13 @@ void plan_release(pint_plan p);
 size_t plan_bytes_estimate(const pint_plan_desc* d);
 // Enqueue one whole solve on `st` as a single graph launch (building or reusing the cached graph);
 // the graph ends with a copy of the convergence state into pinned host memory.
-pint_status solve_enqueue(pint_plan p, const double* F, double* U, double tol, int max_sweeps, cudaStream_t st);
+pint_status solve_enqueue(pint_plan p, const double* F, double* U, double tol, int max_sweeps, cudaStream_t st,
+                          const double* v = nullptr);
 // Result of the last enqueued solve (valid once its stream work has completed).
 void solve_result(pint_plan p, int* sweeps, double* upd, bool* converged);
 // Add one solve (prologue, while-loop, epilogue) of plan p as independent nodes of graph g.
-pint_status add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, double* U, double tol, int max_sweeps);
+// v: start from U_0^n = v (MIXED: the first sweep in the prologue; otherwise v is broadcast into U).
+pint_status add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, double* U, double tol, int max_sweeps,
+                            const double* v = nullptr);
 
 }  // namespace pint

@@ -98,6 +98,8 @@ def lib():
         "pint_wr_sweep": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D), _P]),
         "pint_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
         "pint_solve_async": (_I, [_P, _P, _P, _D, _I, _P]),
+        "pint_solve_v": (_I, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+        "pint_solve_v_async": (_I, [_P, _P, _P, _P, _D, _I, _P]),
         "pint_solve_result": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
         "pint_time_weights": (_I, [_I, _D, _I, ctypes.POINTER(_D)]),
         "pint_correction_coefficients": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -290,6 +292,20 @@ class Plan:
         if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
             raise PintError(st, last_error())
         return st, sweeps.value, upd.value
+
+    def solve_v(self, Fhat, v, U, tol=1e-10, max_sweeps=50, stream=None, raise_on_notconv=True):
+        """pint_solve from U_0^n = v without materialising it (pint_solve_v); U is output only."""
+        sweeps = _I(0)
+        upd = _D(0.0)
+        st = lib().pint_solve_v(self.handle, _ptr(Fhat), _ptr(v), _ptr(U), float(tol), int(max_sweeps),
+                                ctypes.byref(sweeps), ctypes.byref(upd), _stream(stream))
+        if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
+            raise PintError(st, last_error())
+        return st, sweeps.value, upd.value
+
+    def solve_v_async(self, Fhat, v, U, tol=1e-10, max_sweeps=50, stream=None):
+        check(lib().pint_solve_v_async(self.handle, _ptr(Fhat), _ptr(v), _ptr(U), float(tol), int(max_sweeps),
+                                       _stream(stream)))
 
     def solve_async(self, Fhat, U, tol=1e-10, max_sweeps=50, stream=None):
         """Enqueue the whole solve on `stream` without waiting (pint_solve_async)."""

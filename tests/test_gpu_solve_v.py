@@ -1,0 +1,127 @@
+"""pint_solve_v (the solve from U_0^n = v without materialising it) against the oracle and against
+pint_initial_guess + pint_solve / pint_wr_sweep, for every space discretisation and precision."""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import device_inputs, oracle_solution, rel_l2, torch_cuda
+from oracle import fem, nonlinear as nl
+
+pytestmark = pytest.mark.gpu
+
+BAR = {"mixed": 1e-8, "fp64": 1e-10}
+
+PROBLEMS = {
+    "fd1d_bdf2": lambda: workloads.small_problem(dim=1, mx=255, N=64, k=2, kappa=0.1, seed=3),
+    "fd1d_bdf6": lambda: workloads.small_problem(dim=1, mx=127, N=128, k=6, kappa=0.1, seed=4),
+    "fd1d_cq": lambda: workloads.small_problem(dim=1, mx=255, N=128, k=3, alpha=0.5, kappa=0.05, seed=5),
+    "fd2d_bdf4": lambda: workloads.small_problem(dim=2, mx=63, my=63, N=128, k=4, kappa=0.05, seed=6),
+    "fd2d_cq": lambda: workloads.small_problem(dim=2, mx=31, my=63, N=64, k=2, alpha=0.7, kappa=0.1, seed=7),
+    "fd3d": lambda: workloads.heat3d_problem(m=15, N=32, k=3, kappa=0.1, seed=8),
+    "periodic1d": lambda: workloads.periodic_problem(dim=1, mx=256, N=64, k=3, kappa=0.1, seed=9),
+    "periodic2d": lambda: workloads.periodic_problem(dim=2, mx=64, my=32, N=64, k=2, kappa=0.1, seed=10),
+    "fem_bdf3": lambda: workloads.fem_problem(mx=255, N=64, k=3, kappa=0.1, seed=11),
+    "fem_cq": lambda: workloads.fem_problem(mx=127, N=128, k=2, alpha=0.5, kappa=0.1, seed=12),
+}
+
+
+def oracle_ref(p):
+    if getattr(p, "space", "fd") == "fem":
+        h, Mh, Kh = fem.fem_matrices(p.mx)
+        return fem.solve_sequential_fem(p.k, p.alpha, p.tau, Mh, Kh, p.v, p.f(), p.fderiv())
+    return oracle_solution(p)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_solve_v_matches_oracle_and_the_materialised_start(name, prec):
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = PROBLEMS[name]()
+    if prec == "fp64" and getattr(p, "space", "fd") == "fem":
+        pytest.skip("P1 elements run MIXED only")
+    v, f, fd = device_inputs(p, torch)
+    tol = 0.1 * BAR[prec]
+    with Plan.for_problem(p, prec) as plan:
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        plan.form_rhs(v, f, fd, F)
+        U1 = torch.full_like(F, float("nan"))        # output only: its content must not matter
+        st1, sw1, up1 = plan.solve_v(F, v, U1, tol=tol, max_sweeps=40)
+        U2 = torch.empty_like(F)
+        plan.initial_guess(v, U2)
+        st2, sw2, up2 = plan.solve(F, U2, tol=tol, max_sweeps=40)
+        torch.cuda.synchronize()
+    ref = oracle_ref(p)
+    a, b = U1.cpu().numpy(), U2.cpu().numpy()
+    assert rel_l2(a, ref) <= BAR[prec], (sw1, up1)
+    assert abs(sw1 - sw2) <= 1
+    assert rel_l2(a, b) <= BAR[prec]
+
+
+@pytest.mark.parametrize("name", ["fd1d_bdf2", "fd2d_bdf4", "fd1d_cq", "fem_cq", "periodic2d", "fd3d"])
+def test_first_sweep_from_v_equals_one_materialised_sweep(name):
+    # max_sweeps = 1: U_1 of the fused first sweep against pint_wr_sweep from U_0^n = v
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = PROBLEMS[name]()
+    v, f, fd = device_inputs(p, torch)
+    with Plan.for_problem(p, "mixed") as plan:
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        plan.form_rhs(v, f, fd, F)
+        U1 = torch.empty_like(F)
+        plan.solve_v(F, v, U1, tol=1e-30, max_sweeps=1, raise_on_notconv=False)
+        U0 = torch.empty_like(F)
+        plan.initial_guess(v, U0)
+        U2 = torch.empty_like(F)
+        plan.wr_sweep(F, U0, U2)
+        torch.cuda.synchronize()
+    # both are U_0 + (FP32 inner solve of a double-float residual): the residuals agree to
+    # ~2^-47 of their terms, the corrections to FP32 rounding of the correction
+    d = rel_l2(U1.cpu().numpy(), U2.cpu().numpy())
+    assert d <= 1e-6, d
+
+
+def test_solve_v_with_a_reaction_term_and_profiling_path():
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan, pint
+    p = workloads.allen_cahn_problem("fd", mx=127, N=64, k=2, alpha=1.0, kappa=0.1, T=1.0, data="modes")
+    c = 1.0 + np.sin(np.pi * np.arange(1, p.mx + 1) / (p.mx + 1))
+    Mass, A, w = nl.space_ops("fd", p.mx)
+    import scipy.sparse as sp
+    Ar = sp.csc_matrix(A + sp.diags(c))
+    zero = (0.0, 0.0, 0.0, 0.0)
+    Fo = nl.nl_rhs(p.k, 1.0, p.tau, Mass, Ar, w, zero, p.v, p.f(), p.fderiv())
+    ref = nl.solve_sequential_nl(p.k, 1.0, p.tau, Mass, Ar, w, zero, Fo)
+    v, f, fd = device_inputs(p, torch)
+    out = []
+    for prof in (False, True):
+        pint.set_profiling(prof)
+        try:
+            with Plan.for_problem(p, "mixed") as plan:
+                plan.set_reaction(torch.tensor(c, dtype=torch.float64, device="cuda:0"))
+                F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+                plan.form_rhs(v, f, fd, F)
+                U = torch.empty_like(F)
+                plan.solve_v(F, v, U, tol=1e-9, max_sweeps=40)
+                torch.cuda.synchronize()
+                out.append(U.cpu().numpy())
+        finally:
+            pint.set_profiling(False)
+    for U in out:
+        assert rel_l2(U, ref) <= 1e-8
+
+
+def test_solve_v_async_and_result():
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = PROBLEMS["fd2d_bdf4"]()
+    v, f, fd = device_inputs(p, torch)
+    with Plan.for_problem(p, "mixed") as plan:
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        plan.form_rhs(v, f, fd, F)
+        U = torch.empty_like(F)
+        plan.solve_v_async(F, v, U, tol=1e-9, max_sweeps=40)
+        torch.cuda.synchronize()
+        st, sweeps, upd = plan.solve_result()
+    assert st == 0 and sweeps >= 2
+    assert rel_l2(U.cpu().numpy(), oracle_ref(p)) <= 1e-8
