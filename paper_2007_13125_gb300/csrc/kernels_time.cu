@@ -981,17 +981,25 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_v0(ResidFwdArgs a) {
   }
 
   if (g < G) {
+    // F_hat in batches of 8 independent loads per thread (the only stream of this kernel)
     const int i0 = g * NL, i1 = i0 + NL;
-    double fn = valid ? a.F[(size_t)i0 * M + m] : 0.0;
-#pragma unroll 4
-    for (int i = i0; i < i1; ++i) {
-      const double f = fn;
-      if (i + 1 < i1) fn = valid ? a.F[(size_t)(i + 1) * M + m] : 0.0;
-      ff_acc A;
-      A.init(ff_split_trunc(f));
-      A.fma_term(ff_from_double(__ldg(a.beta + i)), Mv, -1.f);
-      A.sub(Avn);
-      Xf[(size_t)2 * i * C] = valid ? A.value() * __ldg(a.s + i) : 0.f;
+    const double* Fp = a.F + m;
+    for (int b = i0; b < i1; b += 8) {
+      double f[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) f[t] = (valid && b + t < i1) ? Fp[(size_t)(b + t) * M] : 0.0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = b + t;
+        if (i < i1) {
+          ff_acc A;
+          A.init(ff_split_trunc(f[t]));
+          const float2 bt = __ldg(a.beta_ff + i);
+          A.fma_term(ff{bt.x, bt.y}, Mv, -1.f);
+          A.sub(Avn);
+          Xf[(size_t)2 * i * C] = valid ? A.value() * __ldg(a.s + i) : 0.f;
+        }
+      }
     }
   }
   __syncthreads();
@@ -1050,7 +1058,7 @@ static cudaError_t launch_v0_k(const ResidFwdArgs& a, size_t sm, cudaStream_t st
 }
 
 cudaError_t launch_resid_v0(const ResidFwdArgs& a, cudaStream_t st) {
-  if (a.gx_lo != 0.f || a.gy_lo != 0.f || !a.v || !a.beta) return cudaErrorInvalidValue;
+  if (a.gx_lo != 0.f || a.gy_lo != 0.f || !a.v || !a.beta_ff) return cudaErrorInvalidValue;
   const size_t sm = resid_fwd_smem(a.N, a.C);
   if (a.fem) return a.dim == 1 && !a.periodic ? launch_v0_k<1, true, false>(a, sm, st) : cudaErrorInvalidValue;
   if (a.periodic) {

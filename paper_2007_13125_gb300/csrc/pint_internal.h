@@ -31,7 +31,7 @@ struct ResidFwdArgs {
                                            // residual loses w c_i U_i^n (null: no reaction term)
   // first sweep from U_0^n = v (k_resid_v0): r_0^n = F_hat_n - beta_n M v - A v
   const double* v;                         // [M] (FP64)
-  const double* beta;                      // [N] tau^-alpha sum_{j<n} omega_j, n = 1..N
+  const float2* beta_ff;                   // [N] tau^-alpha sum_{j<n} omega_j, n = 1..N (double-float)
 };
 
 // MIXED: inverse DFT, times 1/(N kappa^{i/N}), U += c (double-float), norms.

