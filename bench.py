@@ -298,9 +298,8 @@ def run_mix(args) -> int:
     dof = sum(p.dof for p in probs)
 
     def step():
-        for pl, v, U in zip(plans, vs, Us):
-            pl.initial_guess(v, U)
-        return pint.batch_solve(plans, Fs, Us, tol=TOL, max_sweeps=30)
+        # every problem from U_0^n = v (the first sweep reads v)
+        return pint.batch_solve_v(plans, Fs, vs, Us, tol=TOL, max_sweeps=30)
 
     for _ in range(args.warmup):
         step()

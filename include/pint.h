@@ -230,6 +230,12 @@ pint_status pint_solve_result(pint_plan plan, int* sweeps_out, double* upd_rel_o
 pint_status pint_batch_solve(pint_plan* plans, int n, const double* const* Fhat, double* const* U,
                              double tol, int max_sweeps, int* sweeps_out, double* upd_out, void* stream);
 
+/* pint_batch_solve with every problem started from U_0^n = v[i] as in pint_solve_v (v[i]: [M]
+ * device arrays of plans[i]; U[i] output only). */
+pint_status pint_batch_solve_v(pint_plan* plans, int n, const double* const* Fhat, const double* const* v,
+                               double* const* U, double tol, int max_sweeps, int* sweeps_out, double* upd_out,
+                               void* stream);
+
 /* ---- reaction terms and semilinear problems (Sec. 4.3, Algorithm 3) ----
  * 1D plans with Dirichlet boundaries (PINT_SPACE_FD in every precision, PINT_SPACE_FEM_P1 with
  * PINT_MIXED); other plans return PINT_EINVAL. A reaction coefficient enters each row with the

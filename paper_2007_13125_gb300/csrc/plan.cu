@@ -1290,23 +1290,25 @@ extern "C" pint_status pint_solve_v(pint_plan p, const double* Fhat, const doubl
   return solve_impl(p, Fhat, v, U, tol, max_sweeps, sweeps_out, upd_rel_out, (cudaStream_t)stream);
 }
 
-extern "C" pint_status pint_batch_solve(pint_plan* plans, int n, const double* const* Fhat, double* const* U,
-                                        double tol, int max_sweeps, int* sweeps_out, double* upd_out,
-                                        void* stream) {
+namespace {
+// pint_batch_solve (v null: each solve from the content of its U) and pint_batch_solve_v
+pint_status batch_impl(pint_plan* plans, int n, const double* const* Fhat, const double* const* v,
+                       double* const* U, double tol, int max_sweeps, int* sweeps_out, double* upd_out,
+                       cudaStream_t st) {
   if (n < 1 || !plans || !Fhat || !U) return fail(PINT_EINVAL, "bad batch arguments");
   if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
   std::vector<const void*> key;
   key.reserve(4 * (size_t)n);
   for (int i = 0; i < n; ++i) {
-    if (!plans[i] || !Fhat[i] || !U[i]) return fail(PINT_EINVAL, "NULL plan or array in batch");
+    if (!plans[i] || !Fhat[i] || !U[i] || (v && !v[i])) return fail(PINT_EINVAL, "NULL plan or array in batch");
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return fail(PINT_EINVAL, "a plan appears twice in one batch");
     key.push_back(plans[i]);
     key.push_back(Fhat[i]);
     key.push_back(U[i]);
     key.push_back(plans[i]->react_on ? plans[i]->react : nullptr);  // spatial solve captured
+    key.push_back(v ? v[i] : nullptr);
   }
-  cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(g_batch.mu);
   if (!g_batch.exec || g_batch.key != key || g_batch.tol != tol || g_batch.max_sweeps != max_sweeps) {
     if (g_batch.exec) {
@@ -1316,7 +1318,8 @@ extern "C" pint_status pint_batch_solve(pint_plan* plans, int n, const double* c
     cudaGraph_t g;
     PINT_CUDA(cudaGraphCreate(&g, 0));
     pint_status s = PINT_OK;
-    for (int i = 0; i < n && s == PINT_OK; ++i) s = add_solve_nodes(plans[i], g, Fhat[i], U[i], tol, max_sweeps);
+    for (int i = 0; i < n && s == PINT_OK; ++i)
+      s = add_solve_nodes(plans[i], g, Fhat[i], U[i], tol, max_sweeps, v ? v[i] : nullptr);
     if (s == PINT_OK) {
       cudaError_t e = cudaGraphInstantiate(&g_batch.exec, g, 0);
       if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphInstantiate");
@@ -1345,6 +1348,20 @@ extern "C" pint_status pint_batch_solve(pint_plan* plans, int n, const double* c
   }
   if (!all) return fail(PINT_ENOTCONV, "some problems reached max_sweeps above tol");
   return PINT_OK;
+}
+}  // namespace
+
+extern "C" pint_status pint_batch_solve(pint_plan* plans, int n, const double* const* Fhat, double* const* U,
+                                        double tol, int max_sweeps, int* sweeps_out, double* upd_out,
+                                        void* stream) {
+  return batch_impl(plans, n, Fhat, nullptr, U, tol, max_sweeps, sweeps_out, upd_out, (cudaStream_t)stream);
+}
+
+extern "C" pint_status pint_batch_solve_v(pint_plan* plans, int n, const double* const* Fhat,
+                                          const double* const* v, double* const* U, double tol, int max_sweeps,
+                                          int* sweeps_out, double* upd_out, void* stream) {
+  if (!v) return fail(PINT_EINVAL, "bad batch arguments");
+  return batch_impl(plans, n, Fhat, v, U, tol, max_sweeps, sweeps_out, upd_out, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,7 +1,7 @@
 // Continuous-batching solve server: requests of any (N, grid, k, alpha, kappa) arrive at any
 // time; a worker thread admits them while a device-memory budget and a slot count allow, runs
-// each admitted request as one graph launch (F_hat formation, initial guess, the whole WR solve
-// with its device-side convergence loop) on its own stream, and retires it when its completion
+// each admitted request as one graph launch (F_hat formation and the whole WR solve from
+// U_0 = v with its device-side convergence loop) on its own stream, and retires it when its completion
 // event fires. Requests admitted while others run share the GPU: their kernels overlap.
 // Iterates stay on the device from admission until the caller polls the result out.
 //
@@ -185,7 +185,7 @@ void release_request_memory(pint_server_s* s, Request* r) {
 }
 
 // Set up one admitted request on its slot's stream: plan (from the arena), device arrays,
-// uploads, F_hat, U_0 = v, and the whole solve as one graph launch, then the completion event.
+// uploads, F_hat, and the whole solve from U_0 = v as one graph launch, then the completion event.
 void start_request(pint_server_s* s, Request* r) {
   cudaSetDevice(s->device);
   const pint_plan_desc& d = r->req.desc;
@@ -218,8 +218,8 @@ void start_request(pint_server_s* s, Request* r) {
     if (e != cudaSuccess) status = PINT_ECUDA;
   }
   if (status == PINT_OK) status = pint_form_rhs(r->plan, in_v, in_f, in_fd, r->dF, st);
-  if (status == PINT_OK) status = pint_initial_guess(r->plan, in_v, r->dU, st);
-  if (status == PINT_OK) status = solve_enqueue(r->plan, r->dF, r->dU, r->req.tol, r->req.max_sweeps, st);
+  // the whole solve from U_0^n = v (the first sweep reads v; U_0 is never written)
+  if (status == PINT_OK) status = solve_enqueue(r->plan, r->dF, r->dU, r->req.tol, r->req.max_sweeps, st, in_v);
   if (status == PINT_OK) {
     e = cudaEventRecord(s->events[r->slot], st);
     if (e != cudaSuccess) status = PINT_ECUDA;

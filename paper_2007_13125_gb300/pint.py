@@ -111,6 +111,8 @@ def lib():
         "pint_kappa_solve_noalloc": (_I, [_I, _D, _D, _I, _I, _P, _P, _P]),
         "pint_batch_solve": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I,
                                   ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+        "pint_batch_solve_v": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                    _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
         "pint_kernel_stats": (_I, [_I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I),
                                    ctypes.POINTER(_D), _I]),
         "pint_set_reaction": (_I, [_P, _P, _P]),
@@ -355,6 +357,21 @@ def batch_solve(plans, Fhats, Us, tol=1e-8, max_sweeps=50, stream=None, raise_on
     sw = (_I * n)()
     up = (_D * n)()
     st = lib().pint_batch_solve(ph, n, fh, uh, float(tol), int(max_sweeps), sw, up, _stream(stream))
+    if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
+        raise PintError(st, last_error())
+    return st, list(sw), list(up)
+
+
+def batch_solve_v(plans, Fhats, vs, Us, tol=1e-8, max_sweeps=50, stream=None, raise_on_notconv=True):
+    """pint_batch_solve_v: every problem from U_0^n = v (U output only)."""
+    n = len(plans)
+    ph = (_P * n)(*[pl.handle for pl in plans])
+    fh = (_P * n)(*[_ptr(F) for F in Fhats])
+    vh = (_P * n)(*[_ptr(v) for v in vs])
+    uh = (_P * n)(*[_ptr(U) for U in Us])
+    sw = (_I * n)()
+    up = (_D * n)()
+    st = lib().pint_batch_solve_v(ph, n, fh, vh, uh, float(tol), int(max_sweeps), sw, up, _stream(stream))
     if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
         raise PintError(st, last_error())
     return st, list(sw), list(up)

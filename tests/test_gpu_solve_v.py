@@ -127,3 +127,23 @@ def test_solve_v_async_and_result():
         st, sweeps, upd = plan.solve_result()
     assert st == 0 and sweeps >= 2
     assert rel_l2(U.cpu().numpy(), oracle_ref(p)) <= 1e-8
+
+
+def test_batch_solve_v_matches_individual_solves():
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan, pint
+    probs = [PROBLEMS[k]() for k in ("fd1d_bdf2", "fd2d_cq", "fem_cq", "periodic1d")]
+    plans, Fs, vs, Us = [], [], [], []
+    for p in probs:
+        pl = Plan.for_problem(p, "mixed")
+        v, f, fd = device_inputs(p, torch)
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        pl.form_rhs(v, f, fd, F)
+        plans.append(pl); Fs.append(F); vs.append(v); Us.append(torch.empty_like(F))
+    st, sweeps, upds = pint.batch_solve_v(plans, Fs, vs, Us, tol=1e-9, max_sweeps=40)
+    torch.cuda.synchronize()
+    assert st == 0
+    for p, U in zip(probs, Us):
+        assert rel_l2(U.cpu().numpy(), oracle_ref(p)) <= 1e-8
+    for pl in plans:
+        pl.close()
