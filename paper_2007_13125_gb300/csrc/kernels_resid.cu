@@ -103,25 +103,26 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
   auto load = [&](int i) {
     ResidLevel v;
     const size_t idx = (size_t)i * M + m;
-    v.uh = valid ? a.Uhi[idx] : 0.f;
-    v.ul = valid ? a.Ulo[idx] : 0.f;
-    v.wh = ldW ? a.Uhi[idx + dW] : 0.f;
-    v.wl = ldW ? a.Ulo[idx + dW] : 0.f;
-    v.eh = ldE ? a.Uhi[idx + dE] : 0.f;
-    v.el = ldE ? a.Ulo[idx + dE] : 0.f;
+    const float2 z2 = make_float2(0.f, 0.f);
+    const float2 u = valid ? a.U[idx] : z2;
+    const float2 uw = ldW ? a.U[idx + dW] : z2;
+    const float2 ue = ldE ? a.U[idx + dE] : z2;
+    v.uh = u.x; v.ul = u.y;
+    v.wh = uw.x; v.wl = uw.y;
+    v.eh = ue.x; v.el = ue.y;
     if (two_d) {
-      v.sh = hasS ? a.Uhi[idx + dS] : 0.f;
-      v.sl = hasS ? a.Ulo[idx + dS] : 0.f;
-      v.nh = hasN ? a.Uhi[idx + dN] : 0.f;
-      v.nl = hasN ? a.Ulo[idx + dN] : 0.f;
+      const float2 us = hasS ? a.U[idx + dS] : z2;
+      const float2 un = hasN ? a.U[idx + dN] : z2;
+      v.sh = us.x; v.sl = us.y;
+      v.nh = un.x; v.nl = un.y;
     } else {
       v.sh = v.sl = v.nh = v.nl = 0.f;
     }
     if (three_d) {
-      v.bh = hasB ? a.Uhi[idx - mxy] : 0.f;
-      v.bl = hasB ? a.Ulo[idx - mxy] : 0.f;
-      v.th = hasT ? a.Uhi[idx + mxy] : 0.f;
-      v.tl = hasT ? a.Ulo[idx + mxy] : 0.f;
+      const float2 ub = hasB ? a.U[idx - mxy] : z2;
+      const float2 ut = hasT ? a.U[idx + mxy] : z2;
+      v.bh = ub.x; v.bl = ub.y;
+      v.th = ut.x; v.tl = ut.y;
     } else {
       v.bh = v.bl = v.th = v.tl = 0.f;
     }
@@ -177,13 +178,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
     for (int t = 0; t < K; ++t) {
       const int lev = i0 - 1 - t;
       const size_t idx = (size_t)(lev >= 0 ? lev : 0) * M + m;
-      h[t].hi = (valid && lev >= 0) ? a.Uhi[idx] : 0.f;
-      h[t].lo = (valid && lev >= 0) ? a.Ulo[idx] : 0.f;
+      const float2 z2 = make_float2(0.f, 0.f);
+      const float2 u = (valid && lev >= 0) ? a.U[idx] : z2;
+      h[t].hi = u.x;
+      h[t].lo = u.y;
       if constexpr (FEM) {
         float wh, wl, eh, el;
-        neighbours(h[t].hi, h[t].lo, (ldW && lev >= 0) ? a.Uhi[idx + dW] : 0.f,
-                   (ldW && lev >= 0) ? a.Ulo[idx + dW] : 0.f, (ldE && lev >= 0) ? a.Uhi[idx + dE] : 0.f,
-                   (ldE && lev >= 0) ? a.Ulo[idx + dE] : 0.f, wh, wl, eh, el);
+        const float2 uw = (ldW && lev >= 0) ? a.U[idx + dW] : z2;
+        const float2 ue = (ldE && lev >= 0) ? a.U[idx + dE] : z2;
+        neighbours(h[t].hi, h[t].lo, uw.x, uw.y, ue.x, ue.y, wh, wl, eh, el);
         h[t] = mass(h[t].hi, h[t].lo, wh, wl, eh, el);
       }
     }

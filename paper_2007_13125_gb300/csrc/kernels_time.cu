@@ -71,7 +71,7 @@ __device__ __forceinline__ void cp_async_wait_pending(int n) {
 // LOGN > 0: compiled for N = 2^LOGN levels and 2^LOGC columns; LOGN = 0: any shape.
 // V0: the first sweep from U_0^n = v: U = v + c, v read once per point (no U stream, no ring)
 template <int LOGN, int LOGC, bool V0>
-__global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_inv_upd(InvUpdArgs a) {
   constexpr bool CT = LOGN > 0;
   constexpr int CT_RING = CT ? inv_ring_levels(1 << LOGN, 1 << LOGC) : 1;
   constexpr int CT_DEPTH = CT ? CT_RING / (kThreads >> (LOGC + 1)) : 1;
@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
   unsigned short* perm;
   time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
   float2* B0 = reinterpret_cast<float2*>(((size_t)(perm + N) + 15) & ~(size_t)15);  // [2][C]
-  float* ring_h = reinterpret_cast<float*>(((size_t)(B0 + 2 * C) + 15) & ~(size_t)15);
+  // U staging ring: RING levels x 2C points of (hi, lo) pairs
+  float2* ring = reinterpret_cast<float2*>(((size_t)(B0 + 2 * C) + 15) & ~(size_t)15);
   const int RING = CT ? CT_RING : a.ring, P2 = 2 * C, logP2 = logC + 1;
-  float* ring_l = ring_h + (size_t)RING * P2;
   const int m0 = blockIdx.x * P2;
   const int J = N / 2 + 1;
   const int q = threadIdx.x & (P2 - 1), r0 = threadIdx.x >> logP2;
@@ -109,15 +109,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
   }
   cp_async_commit();
   // 2. the first rounds of U into the ring (one group per round)
-  const float* uh_src = a.Uhi + m;
-  const float* ul_src = a.Ulo + m;
+  const float2* u_src = a.U + m;
   if constexpr (!V0) {
     for (int d = 0; d < depth; ++d) {
       const int i = d * LPR + r0;  // < RING
-      if (valid && i < N) {
-        cp_async4(ring_h + (i << logP2) + q, uh_src + (size_t)i * M);
-        cp_async4(ring_l + (i << logP2) + q, ul_src + (size_t)i * M);
-      }
+      if (valid && i < N) cp_async8(ring + (i << logP2) + q, u_src + (size_t)i * M);
       cp_async_commit();
     }
     // 3. spectrum complete (the depth U groups committed after it may still be pending)
@@ -148,16 +144,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
   // 4. U += c, level by level through the ring
   float sc = 0.f, su = 0.f;  // per-thread partial norms (FP32: the FP64 pipe is ~1/70 rate)
   const float* Xf = reinterpret_cast<const float*>(X) + 2 * (q & (C - 1)) + (q >= C ? 1 : 0);
-  float* uh_dst = a.Uhi + m;
-  float* ul_dst = a.Ulo + m;
+  float2* u_dst = a.U + m;
   if constexpr (V0) {
     const ff u0 = valid ? ff_from_double(a.v[m]) : ff{0.f, 0.f};
     for (int i = r0; i < N; i += LPR) {
       const float cval = Xf[(size_t)2 * i * C] * __ldg(a.inv_s + i);
       if (valid) {
         const ff u = ff_add_f(u0, cval);
-        uh_dst[(size_t)i * M] = u.hi;
-        ul_dst[(size_t)i * M] = u.lo;
+        u_dst[(size_t)i * M] = make_float2(u.hi, u.lo);
         sc = fmaf(cval, cval, sc);
         su = fmaf(u.hi, u.hi, su);
       }
@@ -172,16 +166,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_inv_upd(InvUpdArgs a) {
     const float cval = Xf[(size_t)2 * i * C] * __ldg(a.inv_s + i);
     const size_t row = (size_t)i * M;
     if (valid) {
-      const ff u = ff_add_f(ff{ring_h[slot], ring_l[slot]}, cval);
-      uh_dst[row] = u.hi;
-      ul_dst[row] = u.lo;
+      const float2 r = ring[slot];
+      const ff u = ff_add_f(ff{r.x, r.y}, cval);
+      u_dst[row] = make_float2(u.hi, u.lo);
       sc = fmaf(cval, cval, sc);
       su = fmaf(u.hi, u.hi, su);
     }
-    if (valid && i + RING < N) {
-      cp_async4(ring_h + slot, uh_src + row + (size_t)RING * M);
-      cp_async4(ring_l + slot, ul_src + row + (size_t)RING * M);
-    }
+    if (valid && i + RING < N) cp_async8(ring + slot, u_src + row + (size_t)RING * M);
     cp_async_commit();
   }
   cp_async_wait_all();
@@ -283,7 +274,7 @@ __global__ void __launch_bounds__(kThreads) k_toeplitz(ToepArgs a) {
         if (m >= M) continue;
         const size_t idx = (size_t)i * M + m;
         if (a.ukind == 0) val[h] = a.Ud[idx];
-        else if (a.ukind == 1) val[h] = ff_to_double(ff{a.Uhi[idx], a.Ulo[idx]});
+        else if (a.ukind == 1) val[h] = ff_to_double(ff{a.Uff[idx].x, a.Uff[idx].y});
         else val[h] = f2d_bits(a.Uf[idx]);
       }
     }
@@ -329,8 +320,8 @@ __global__ void __launch_bounds__(kThreads) k_toeplitz_ff(ToepFFArgs a) {
     if (i < N) {
       const int ma = m0 + cc, mb = m0 + C + cc;
       const size_t row = (size_t)i * M;
-      if (ma < M) { v.rh = a.Uhi[row + ma]; v.rl = a.Ulo[row + ma]; }
-      if (mb < M) { v.ih = a.Uhi[row + mb]; v.il = a.Ulo[row + mb]; }
+      if (ma < M) { const float2 u = a.U[row + ma]; v.rh = u.x; v.rl = u.y; }
+      if (mb < M) { const float2 u = a.U[row + mb]; v.ih = u.x; v.il = u.y; }
     }
     X[(size_t)i * C + cc] = v;
   }
@@ -422,7 +413,7 @@ __global__ void k_rhs(RhsArgs a) {
 // ---------------------------------------------------------------------------
 // conversions (integer bit manipulation; see ff.cuh)
 // ---------------------------------------------------------------------------
-__global__ void k_d2ff(const double* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
+__global__ void k_d2ff(const double* __restrict__ x, float2* __restrict__ y, size_t n) {
   constexpr int B = 4;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t0 < n; t0 += B * stride) {
@@ -434,23 +425,19 @@ __global__ void k_d2ff(const double* __restrict__ x, float* __restrict__ hi, flo
       const size_t t = t0 + b * stride;
       if (t < n) {
         const ff r = ff_from_double(v[b]);
-        hi[t] = r.hi;
-        lo[t] = r.lo;
+        y[t] = make_float2(r.hi, r.lo);
       }
     }
   }
 }
 // grid: x over points, y over slices of levels; U^n = v for every level n
-__global__ void k_bcast_d2ff(const double* v, float* hi, float* lo, int N, int M) {
+__global__ void k_bcast_d2ff(const double* v, float2* U, int N, int M) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
   const int per = (N + gridDim.y - 1) / gridDim.y;
   const int i0 = blockIdx.y * per, i1 = min(N, i0 + per);
   const ff r = ff_from_double(v[m]);
-  for (int i = i0; i < i1; ++i) {
-    hi[(size_t)i * M + m] = r.hi;
-    lo[(size_t)i * M + m] = r.lo;
-  }
+  for (int i = i0; i < i1; ++i) U[(size_t)i * M + m] = make_float2(r.hi, r.lo);
 }
 __global__ void k_bcast_d(const double* v, double* U, int N, int M) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -460,20 +447,19 @@ __global__ void k_bcast_d(const double* v, double* U, int N, int M) {
   const double vm = v[m];
   for (int i = i0; i < i1; ++i) U[(size_t)i * M + m] = vm;
 }
-__global__ void k_ff2d(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ x, size_t n) {
+__global__ void k_ff2d(const float2* __restrict__ y, double* __restrict__ x, size_t n) {
   constexpr int B = 4;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t0 < n; t0 += B * stride) {
-    float h[B], l[B];
+    float2 h[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const size_t t = t0 + b * stride;
-      h[b] = t < n ? hi[t] : 0.f;
-      l[b] = t < n ? lo[t] : 0.f;
+      h[b] = t < n ? y[t] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int b = 0; b < B; ++b)
-      if (t0 + b * stride < n) x[t0 + b * stride] = ff_to_double(ff{h[b], l[b]});
+      if (t0 + b * stride < n) x[t0 + b * stride] = ff_to_double(ff{h[b].x, h[b].y});
   }
 }
 __global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, size_t n) {
@@ -639,15 +625,15 @@ cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_d2ff(const double* x, float* hi, float* lo, size_t n, cudaStream_t st) {
+cudaError_t launch_d2ff(const double* x, float2* y, size_t n, cudaStream_t st) {
   prof_begin("cvt_d2ff", st);
-  k_d2ff<<<grid_for(n), kThreads, 0, st>>>(x, hi, lo, n);
+  k_d2ff<<<grid_for(n), kThreads, 0, st>>>(x, y, n);
   prof_end(st);
   return cudaGetLastError();
 }
-cudaError_t launch_bcast_d2ff(const double* v, float* hi, float* lo, int N, int M, cudaStream_t st) {
+cudaError_t launch_bcast_d2ff(const double* v, float2* U, int N, int M, cudaStream_t st) {
   prof_begin("cvt_bcast_d2ff", st);
-  k_bcast_d2ff<<<grid_pts(M, N), kThreads, 0, st>>>(v, hi, lo, N, M);
+  k_bcast_d2ff<<<grid_pts(M, N), kThreads, 0, st>>>(v, U, N, M);
   prof_end(st);
   return cudaGetLastError();
 }
@@ -657,9 +643,9 @@ cudaError_t launch_bcast_d(const double* v, double* U, int N, int M, cudaStream_
   prof_end(st);
   return cudaGetLastError();
 }
-cudaError_t launch_ff2d(const float* hi, const float* lo, double* x, size_t n, cudaStream_t st) {
+cudaError_t launch_ff2d(const float2* y, double* x, size_t n, cudaStream_t st) {
   prof_begin("cvt_ff2d", st);
-  k_ff2d<<<grid_for(n), kThreads, 0, st>>>(hi, lo, x, n);
+  k_ff2d<<<grid_for(n), kThreads, 0, st>>>(y, x, n);
   prof_end(st);
   return cudaGetLastError();
 }

@@ -13,7 +13,7 @@ constexpr int kMaxK = 6;
 
 // MIXED: r = F_hat - K U in double-float, times kappa^{i/N}, real -> half-complex DFT.
 struct ResidFwdArgs {
-  const float* Uhi; const float* Ulo;      // iterate U [N][M] (double-float)
+  const float2* U;                         // iterate U [N][M] (double-float pairs: hi, lo)
   const double* F;                         // F_hat [N][M] (FP64, split to double-float on load)
   const float* yhi; const float* ylo;      // CQ: tau^-alpha (L_omega U) [N][M] double-float, else null
   float2* S;                               // half spectrum [(N/2+1)][M]
@@ -36,7 +36,7 @@ struct ResidFwdArgs {
 
 // MIXED: inverse DFT, times 1/(N kappa^{i/N}), U += c (double-float), norms.
 struct InvUpdArgs {
-  const float2* S; float* Uhi; float* Ulo;
+  const float2* S; float2* U;             // U [N][M] double-float pairs (hi, lo)
   const float* inv_s; const float2* tw;
   int N, M, C, logC;
   double* norms;                           // [0] += sum c^2, [1] += sum U^2
@@ -63,7 +63,7 @@ template <typename T> struct DirectInvArgs {
 
 // CQ Toeplitz product z = omega * U (linear convolution along time, 2N-point FFTs).
 struct ToepArgs {
-  const double* Ud; const float* Uhi; const float* Ulo; const float* Uf;
+  const double* Ud; const float2* Uff; const float* Uf;
   int ukind;                               // 0 double, 1 double-float, 2 float
   double* out;                             // [N][M]
   const double2* what;                     // FFT_{2N}(omega, zero padded), permuted, pre-scaled
@@ -73,7 +73,7 @@ struct ToepArgs {
 
 // MIXED CQ: the same product in double-float arithmetic on the FP32 pipes.
 struct ToepFFArgs {
-  const float* Uhi; const float* Ulo;      // U [N][M] (double-float)
+  const float2* U;                         // U [N][M] (double-float pairs)
   float* yhi; float* ylo;                  // tau^-alpha (L_omega U) [N][M] (double-float)
   const void* what;                        // ffc [2N]: FFT_{2N}(omega), radix-8 permuted order, * tau^-alpha / 2N
   const void* tw;                          // ffc [2N]: exp(-2 pi i m / 2N)
@@ -173,12 +173,12 @@ template <typename T> cudaError_t launch_trivar_solve(const TriVarArgs<T>& a, cu
 size_t tri_smem(int n, int C);
 
 // conversions
-cudaError_t launch_d2ff(const double* x, float* hi, float* lo, size_t n, cudaStream_t st);
-cudaError_t launch_ff2d(const float* hi, const float* lo, double* x, size_t n, cudaStream_t st);
+cudaError_t launch_d2ff(const double* x, float2* y, size_t n, cudaStream_t st);
+cudaError_t launch_ff2d(const float2* y, double* x, size_t n, cudaStream_t st);
 cudaError_t launch_d2f(const double* x, float* y, size_t n, cudaStream_t st);
 cudaError_t launch_f2d(const float* x, double* y, size_t n, cudaStream_t st);
 cudaError_t launch_bcast_d(const double* v, double* U, int N, int M, cudaStream_t st);
-cudaError_t launch_bcast_d2ff(const double* v, float* hi, float* lo, int N, int M, cudaStream_t st);
+cudaError_t launch_bcast_d2ff(const double* v, float2* U, int N, int M, cudaStream_t st);
 
 // ---- semilinear extension (kernels_nl.cu) ----
 struct NlPoly { double c[4]; };          // g(u) = c[0] + c[1] u + c[2] u^2 + c[3] u^3

@@ -518,8 +518,7 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   // workspaces
   const size_t NM = (size_t)N * M, JM = (size_t)(N / 2 + 1) * M;
   if (p->prec == PINT_MIXED) {
-    if ((s = dalloc(p, &p->Uhi, NM)) != PINT_OK) return bail(s);
-    if ((s = dalloc(p, &p->Ulo, NM)) != PINT_OK) return bail(s);
+    if ((s = dalloc(p, &p->Uff, NM)) != PINT_OK) return bail(s);
   } else if (p->prec == PINT_FP32) {
     if ((s = dalloc(p, &p->Uhi, NM)) != PINT_OK) return bail(s);
     if ((s = dalloc(p, &p->Fhi, NM)) != PINT_OK) return bail(s);
@@ -864,21 +863,21 @@ pint_status autotune_ysolve(pint_plan p) {
   return PINT_OK;
 }
 
-// MIXED sweep on the plan's double-float iterate (Uhi/Ulo); F_hat read in FP64
+// MIXED sweep on the plan's double-float iterate (Uff); F_hat read in FP64
 pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   const int N = p->N, M = p->M;
   float* yhi = reinterpret_cast<float*>(p->z);
   float* ylo = yhi + (size_t)N * M;
   if (p->cq) {
     ToepFFArgs ta{};
-    ta.Uhi = p->Uhi; ta.Ulo = p->Ulo; ta.yhi = yhi; ta.ylo = ylo; ta.what = p->what_ff; ta.tw = p->tw_ff;
+    ta.U = p->Uff; ta.yhi = yhi; ta.ylo = ylo; ta.what = p->what_ff; ta.tw = p->tw_ff;
     ta.N = N; ta.M = M; ta.C = p->Cz; ta.logC = ilog2c(p->Cz);
     cudaError_t e = launch_toeplitz_ff(ta, st);
     if (e != cudaSuccess) return cuda_fail(e, "toeplitz kernel");
   }
   PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
   ResidFwdArgs r{};
-  r.Uhi = p->Uhi; r.Ulo = p->Ulo; r.F = Fhat;
+  r.U = p->Uff; r.F = Fhat;
   r.yhi = p->cq ? yhi : nullptr;
   r.ylo = p->cq ? ylo : nullptr;
   r.S = reinterpret_cast<float2*>(p->S);
@@ -909,7 +908,7 @@ pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   e = spatial<float>(p, p->tf, st);
   if (e != cudaSuccess) return cuda_fail(e, "spatial kernel");
   InvUpdArgs u{};
-  u.S = reinterpret_cast<const float2*>(p->S); u.Uhi = p->Uhi; u.Ulo = p->Ulo;
+  u.S = reinterpret_cast<const float2*>(p->S); u.U = p->Uff;
   u.inv_s = p->tf.inv_s; u.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
   u.N = N; u.M = M; u.C = p->Cr; u.logC = ilog2c(p->Cr); u.norms = p->norms;
   e = launch_inv_upd(u, st);
@@ -941,7 +940,7 @@ pint_status sweep_mixed_v0(pint_plan p, const double* Fhat, const double* v, cud
   e = spatial<float>(p, p->tf, st);
   if (e != cudaSuccess) return cuda_fail(e, "spatial kernel");
   InvUpdArgs u{};
-  u.S = reinterpret_cast<const float2*>(p->S); u.Uhi = p->Uhi; u.Ulo = p->Ulo;
+  u.S = reinterpret_cast<const float2*>(p->S); u.U = p->Uff;
   u.inv_s = p->tf.inv_s; u.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
   u.N = N; u.M = M; u.C = p->Cr; u.logC = ilog2c(p->Cr); u.norms = p->norms; u.v = v;
   e = launch_inv_upd(u, st);
@@ -995,10 +994,10 @@ pint_status sweep_user(pint_plan p, const double* Fhat, const double* Uin, doubl
   cudaError_t e;
   if (p->prec == PINT_FP64) return sweep_direct<double>(p, p->td, Fhat, Uin, Uout, st);
   if (p->prec == PINT_MIXED) {
-    if ((e = launch_d2ff(Uin, p->Uhi, p->Ulo, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+    if ((e = launch_d2ff(Uin, p->Uff, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
     pint_status s = sweep_mixed(p, Fhat, st);
     if (s != PINT_OK) return s;
-    if ((e = launch_ff2d(p->Uhi, p->Ulo, Uout, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+    if ((e = launch_ff2d(p->Uff, Uout, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
     return PINT_OK;
   }
   if ((e = launch_d2f(Fhat, p->Fhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
@@ -1064,7 +1063,7 @@ pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, d
           b = sweep_mixed_v0(p, F, v, p->cap);
           if (b == PINT_OK) e1 = launch_converge(p->norms, p->ctl, h, p->cap);
         } else {
-          e1 = launch_d2ff(U, p->Uhi, p->Ulo, NM, p->cap);
+          e1 = launch_d2ff(U, p->Uff, NM, p->cap);
         }
       }
       if (e1 == cudaSuccess && p->prec == PINT_FP32) {
@@ -1100,7 +1099,7 @@ pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, d
     if ((s = capture_begin(p, epi)) != PINT_OK) break;
     {
       cudaError_t e3 = cudaSuccess;
-      if (p->prec == PINT_MIXED) e3 = launch_ff2d(p->Uhi, p->Ulo, U, NM, p->cap);
+      if (p->prec == PINT_MIXED) e3 = launch_ff2d(p->Uff, U, NM, p->cap);
       else if (p->prec == PINT_FP32) e3 = launch_f2d(p->Uhi, U, NM, p->cap);
       if (e3 == cudaSuccess)
         e3 = cudaMemcpyAsync(p->h_ctl, p->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, p->cap);
@@ -1250,7 +1249,7 @@ pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double*
       if ((s = read_norms(p, st, &upd)) != PINT_OK) return s;
       done = stop_decision(m, upd, prev, tol, p->q_floor);
       prev = upd;
-    } else if ((e = launch_d2ff(U, p->Uhi, p->Ulo, NM, st)) != cudaSuccess) {
+    } else if ((e = launch_d2ff(U, p->Uff, NM, st)) != cudaSuccess) {
       return cuda_fail(e, "convert");
     }
   } else if (p->prec == PINT_FP32) {
@@ -1268,7 +1267,7 @@ pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double*
     prev = upd;
   }
   if (p->prec == PINT_MIXED) {
-    if ((e = launch_ff2d(p->Uhi, p->Ulo, U, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
+    if ((e = launch_ff2d(p->Uff, U, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
   } else if (p->prec == PINT_FP32) {
     if ((e = launch_f2d(p->Uhi, U, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
   }

@@ -84,7 +84,8 @@ struct pint_plan_s {
   double2* what_up = nullptr;       // [2N] permuted, * kappa tau^-alpha / 2N
   float4* what_ff = nullptr;        // MIXED CQ: [2N] double-float complex, radix-8 permuted, * tau^-alpha / 2N
   float4* tw_ff = nullptr;          // MIXED CQ: [2N] double-float complex exp(-2 pi i m / 2N)
-  float *Uhi = nullptr, *Ulo = nullptr, *Fhi = nullptr;  // MIXED: U double-float; FP32: U, F_hat
+  float2* Uff = nullptr;            // MIXED: U as double-float pairs (hi, lo) [N][M]
+  float *Uhi = nullptr, *Fhi = nullptr;  // FP32: U, F_hat
   void* S = nullptr;                // spectrum
   double* z = nullptr;              // CQ Toeplitz output [N][M]
   double* norms = nullptr;          // device [2]
