@@ -71,7 +71,13 @@ def algo_bytes(name: str, N: int, M: int) -> float:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the workload (`ncu --set full` of `bench.py --once mixed`), valid while the kernel's
 # source is unchanged (sha1 of its translation unit)
-NCU_TRAFFIC = {"resid_fwd_ff": (318.81e6, "kernels_time.cu", "4d2355f1518451d0a3722c6f4b2a1a3ebda0262f")}
+NCU_TRAFFIC = {
+    "resid_fwd_ff": (317.30e6, "kernels_resid.cu", "14925015af74420b5b84e552eca4f6cd526b8b3c"),
+    "resid_v0_ff": (168.34e6, "kernels_resid.cu", "14925015af74420b5b84e552eca4f6cd526b8b3c"),
+    "inv_update_v0_ff": (142.29e6, "kernels_time.cu", "a6f669b407b4ea149940ecaf393e8634dda1d6d6"),
+    "dst_f32": (76.13e6, "kernels_space.cu", "3c527803de8656af72e4ff171420e7c68d2f8b5f"),
+    "axis_solve_f32": (78.56e6, "kernels_space.cu", "3c527803de8656af72e4ff171420e7c68d2f8b5f"),
+}
 
 
 def traffic_for(name: str):
