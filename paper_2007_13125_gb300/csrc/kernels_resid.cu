@@ -54,12 +54,13 @@ struct ResidLevel {
 // CTF: the tile shape (N, C) is one of the compiled transforms; otherwise the runtime-shape one.
 // Keeping the two apart keeps the compiled instances within 64 registers without spill code.
 __host__ __device__ inline bool compiled_time_fft(int N, int C) {
-  return (N == 256 && C == 16) || (N == 512 && C == 16) || (N == 1024 && C == 8);
+  return (N == 128 && C == 16) || (N == 256 && C == 16) || (N == 512 && C == 16) || (N == 1024 && C == 8);
 }
 template <bool CTF>
 __device__ __forceinline__ void resid_time_fft(float2* X, int C, int logC, int N, const float2* tw) {
   if constexpr (CTF) {
-    if (N == 256) fft_forward_ct<8, 4, 16>(X, tw);
+    if (N == 128) fft_forward_ct<7, 4, 16>(X, tw);
+    else if (N == 256) fft_forward_ct<8, 4, 16>(X, tw);
     else if (N == 512) fft_forward_ct<9, 4, 16>(X, tw);
     else fft_forward_ct<10, 3, 8>(X, tw);
   } else {
@@ -195,7 +196,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
     const bool react = DIM == 1 && a.react != nullptr;
     const ff rc = (react && valid) ? ff_from_double(a.react[m]) : ff{0.f, 0.f};
     ResidLevel nx = load(i0);
-#pragma unroll 2
+    // (3D: no unrolling, which keeps the two extra neighbour streams within 64 registers)
+#pragma unroll (DIM == 3 ? 1 : 2)
     for (int i = i0; i < i1; ++i) {
       const ResidLevel c = nx;
       if (i + 1 < i1) nx = load(i + 1);
