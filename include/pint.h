@@ -122,7 +122,11 @@ typedef struct {
  * eigenvalues, FFT twiddles) on the host, one upload, and the device workspaces.
  * Returns PINT_EINVAL for k outside 1..6, alpha outside (0,1], kappa outside (0,1), tau <= 0,
  * or unsupported N / mx / my; PINT_ENOMEM / PINT_ECUDA on device failure. *out is set only on
- * success. Synchronous. */
+ * success. Synchronous. Tile widths of the time kernels: as many points per CTA as shared memory
+ * allows, narrowed so that the points still give two CTAs per SM; when that narrowing applies to a
+ * PINT_MIXED problem of at least 2^18 space-time unknowns, the residual, update and CQ-history
+ * kernels are timed at every admissible width on the new plan's workspaces and each keeps its
+ * fastest width (a few milliseconds; cached per problem shape for the process). */
 pint_status pint_plan_create(int k, double alpha, double kappa, double tau, int N,
                              const pint_grid* grid, pint_precision precision, pint_plan* out);
 pint_status pint_plan_create_desc(const pint_plan_desc* desc, pint_plan* out);

@@ -404,6 +404,7 @@ void destroy_plan(pint_plan p) {
 
 namespace {
 pint_status autotune_ysolve(pint_plan p);
+pint_status tune_time_tiles(pint_plan p, int cmax_t, int cmax_z);
 }
 
 extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan* out) {
@@ -549,6 +550,7 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   while (occ < 32 && (size_t)M / (size_t)(4 * occ) >= 2 * 152) occ *= 2;
   p->Ct = std::min(pick_cols((size_t)N * sizeof(float2), budget, 32, 1), occ);
   p->Cr = std::min(p->Ct, 16);
+  p->Ci = p->Cr;
   p->Ctd = std::min(pick_cols((size_t)N * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2)), budget, 32, 1), occ);
   p->Cz = std::min(pick_cols((size_t)2 * N * sizeof(double2), 160 * 1024, 16, 1), occ);
   const size_t ve = p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2);
@@ -616,6 +618,18 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
       // the observed update ratios of the first sweeps can underestimate
       p->q_floor = std::max(p->q_floor, std::min(0.99, p->kappa / (1.0 - p->kappa)));
     }
+  }
+  {
+    // Few points (the occupancy rule narrowed the time tiles below what shared memory allows):
+    // the best width depends on the kernel (threads per FFT pass against CTAs per SM), so time
+    // each MIXED time kernel at the admissible widths and keep the fastest (plans created through
+    // the public entry points; server plans keep the rule).
+    const int cmax_t = std::min(pick_cols((size_t)N * sizeof(float2), budget, 32, 1), 16);
+    const int cmax_z = pick_cols((size_t)2 * N * sizeof(double2), 160 * 1024, 16, 1);
+    // (below 2^18 space-time unknowns launch latency dominates and the timings carry no signal)
+    if (!A && p->prec == PINT_MIXED && occ < cmax_t && (size_t)N * M >= ((size_t)1 << 18) &&
+        (s = tune_time_tiles(p, cmax_t, cmax_z)) != PINT_OK)
+      return bail(s);
   }
   *out = p;
   return PINT_OK;
@@ -864,22 +878,22 @@ pint_status autotune_ysolve(pint_plan p) {
 }
 
 // MIXED sweep on the plan's double-float iterate (Uff); F_hat read in FP64
-pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
+// The three time kernels of a MIXED sweep, each on its own (the tile-width tuner times them apart).
+cudaError_t mixed_toeplitz(pint_plan p, cudaStream_t st) {
+  ToepFFArgs ta{};
+  float* yhi = reinterpret_cast<float*>(p->z);
+  ta.U = p->Uff; ta.yhi = yhi; ta.ylo = yhi + (size_t)p->N * p->M; ta.what = p->what_ff; ta.tw = p->tw_ff;
+  ta.N = p->N; ta.M = p->M; ta.C = p->Cz; ta.logC = ilog2c(p->Cz);
+  return launch_toeplitz_ff(ta, st);
+}
+
+cudaError_t mixed_resid(pint_plan p, const double* Fhat, cudaStream_t st) {
   const int N = p->N, M = p->M;
   float* yhi = reinterpret_cast<float*>(p->z);
-  float* ylo = yhi + (size_t)N * M;
-  if (p->cq) {
-    ToepFFArgs ta{};
-    ta.U = p->Uff; ta.yhi = yhi; ta.ylo = ylo; ta.what = p->what_ff; ta.tw = p->tw_ff;
-    ta.N = N; ta.M = M; ta.C = p->Cz; ta.logC = ilog2c(p->Cz);
-    cudaError_t e = launch_toeplitz_ff(ta, st);
-    if (e != cudaSuccess) return cuda_fail(e, "toeplitz kernel");
-  }
-  PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
   ResidFwdArgs r{};
   r.U = p->Uff; r.F = Fhat;
   r.yhi = p->cq ? yhi : nullptr;
-  r.ylo = p->cq ? ylo : nullptr;
+  r.ylo = p->cq ? yhi + (size_t)N * M : nullptr;
   r.S = reinterpret_cast<float2*>(p->S);
   r.s = p->tf.s; r.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
   r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Cr; r.logC = ilog2c(p->Cr);
@@ -903,16 +917,95 @@ pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
   split_ff(p->gz, r.gz_hi, r.gz_lo);
   r.my = p->my;
   r.react = p->react_on ? p->react : nullptr;
-  cudaError_t e = launch_resid_fwd(r, st);
-  if (e != cudaSuccess) return cuda_fail(e, "residual kernel");
-  e = spatial<float>(p, p->tf, st);
-  if (e != cudaSuccess) return cuda_fail(e, "spatial kernel");
+  return launch_resid_fwd(r, st);
+}
+
+cudaError_t mixed_update(pint_plan p, const double* v, cudaStream_t st) {
   InvUpdArgs u{};
   u.S = reinterpret_cast<const float2*>(p->S); u.U = p->Uff;
   u.inv_s = p->tf.inv_s; u.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
-  u.N = N; u.M = M; u.C = p->Cr; u.logC = ilog2c(p->Cr); u.norms = p->norms;
-  e = launch_inv_upd(u, st);
-  if (e != cudaSuccess) return cuda_fail(e, "update kernel");
+  u.N = p->N; u.M = p->M; u.C = p->Ci; u.logC = ilog2c(p->Ci); u.norms = p->norms; u.v = v;
+  return launch_inv_upd(u, st);
+}
+
+// MIXED sweep on the plan's double-float iterate (Uff); F_hat read in FP64
+pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
+  cudaError_t e;
+  if (p->cq && (e = mixed_toeplitz(p, st)) != cudaSuccess) return cuda_fail(e, "toeplitz kernel");
+  PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
+  if ((e = mixed_resid(p, Fhat, st)) != cudaSuccess) return cuda_fail(e, "residual kernel");
+  if ((e = spatial<float>(p, p->tf, st)) != cudaSuccess) return cuda_fail(e, "spatial kernel");
+  if ((e = mixed_update(p, nullptr, st)) != cudaSuccess) return cuda_fail(e, "update kernel");
+  return PINT_OK;
+}
+
+// Tile widths of the MIXED time kernels (residual, update, CQ history) by measurement: each kernel
+// is launched alone on the plan's workspaces (zero right-hand side) at every admissible width,
+// three timed launches after one warm-up, and the fastest width is kept. Results are cached per
+// problem shape for the process.
+pint_status tune_time_tiles(pint_plan p, int cmax_t, int cmax_z) {
+  static std::mutex mu;
+  struct Entry { long long key[4]; int cr, ci, cz; };
+  static std::vector<Entry> cache;
+  const long long key[4] = {(long long)p->N * 8192 + p->k, ((long long)p->mx * 4096 + p->my) * 4096 + p->mz,
+                            (long long)p->dim * 16 + (p->cq ? 8 : 0) + (p->fem ? 4 : 0) + (p->periodic ? 2 : 0),
+                            (long long)cmax_t * 64 + cmax_z};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry& c : cache)
+      if (std::equal(key, key + 4, c.key)) { p->Cr = c.cr; p->Ci = c.ci; p->Cz = c.cz; return PINT_OK; }
+  }
+  const size_t NM = (size_t)p->N * p->M;
+  double* F = nullptr;
+  PINT_CUDA(cudaMalloc(&F, NM * sizeof(double)));
+  cudaStream_t st;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { cudaFree(F); return cuda_fail(e, "tile tuning"); }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bool prof = g_prof_on;
+  g_prof_on = false;
+  if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, NM * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->Uff, 0, NM * sizeof(float2), st);
+  if (e == cudaSuccess && p->cq) e = cudaMemsetAsync(p->z, 0, NM * sizeof(double), st);
+  // kind 0: residual (Cr), 1: update (Ci), 2: CQ history (Cz)
+  auto run = [&](int kind) -> cudaError_t {
+    if (kind == 0) return mixed_resid(p, F, st);
+    if (kind == 1) return mixed_update(p, nullptr, st);
+    return mixed_toeplitz(p, st);
+  };
+  int* width[3] = {&p->Cr, &p->Ci, &p->Cz};
+  for (int kind = 0; kind < 3 && e == cudaSuccess; ++kind) {
+    if (kind == 2 && !p->cq) break;
+    const int cmax = kind == 2 ? cmax_z : cmax_t;
+    float best = 1e30f;
+    int bestc = *width[kind];
+    for (int c = 1; c <= cmax && e == cudaSuccess; c *= 2) {
+      *width[kind] = c;
+      e = run(kind);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = run(kind);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) { best = ms; bestc = c; }
+    }
+    *width[kind] = bestc;
+  }
+  g_prof_on = prof;
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  cudaFree(F);
+  if (e != cudaSuccess) return cuda_fail(e, "tile tuning");
+  std::lock_guard<std::mutex> lk(mu);
+  Entry en;
+  std::copy(key, key + 4, en.key);
+  en.cr = p->Cr; en.ci = p->Ci; en.cz = p->Cz;
+  cache.push_back(en);
   return PINT_OK;
 }
 
@@ -939,11 +1032,7 @@ pint_status sweep_mixed_v0(pint_plan p, const double* Fhat, const double* v, cud
   if (e != cudaSuccess) return cuda_fail(e, "first-sweep residual kernel");
   e = spatial<float>(p, p->tf, st);
   if (e != cudaSuccess) return cuda_fail(e, "spatial kernel");
-  InvUpdArgs u{};
-  u.S = reinterpret_cast<const float2*>(p->S); u.U = p->Uff;
-  u.inv_s = p->tf.inv_s; u.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
-  u.N = N; u.M = M; u.C = p->Cr; u.logC = ilog2c(p->Cr); u.norms = p->norms; u.v = v;
-  e = launch_inv_upd(u, st);
+  e = mixed_update(p, v, st);
   if (e != cudaSuccess) return cuda_fail(e, "update kernel");
   return PINT_OK;
 }

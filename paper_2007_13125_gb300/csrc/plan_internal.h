@@ -96,8 +96,8 @@ struct pint_plan_s {
   pint::SolveGraph sg[pint::kSolveGraphs];
   unsigned long long sg_clock = 0;
   // tiles
-  int Ct, Cr, Ctd, Cz, Cx, Cy, Czl, Ctri;  // columns per CTA: time (float), residual, time (T), toeplitz,
-                                         // x, y, z lines, tri
+  int Ct, Cr, Ci, Ctd, Cz, Cx, Cy, Czl, Ctri;  // columns per CTA: time (float), residual, update, time (T),
+                                             // toeplitz, x, y, z lines, tri
   int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal
   double q_floor;                   // predicted floor of the per-sweep contraction (inner precision)
   // reaction term (1D, Dirichlet): the spatial operator A + w diag(c) of the linear solves
