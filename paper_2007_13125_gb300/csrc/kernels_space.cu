@@ -22,6 +22,7 @@
 // substitutions as parallel scans of affine maps (the
 // systems are diagonally dominant up to the reaction term: sigma_j lies in the sector where the
 // BDF / CQ symbols live, and A_h + w diag(c) is positive definite for the reactions of interest).
+#include "ff.cuh"
 #include "fft.cuh"
 #include "pint_internal.h"
 
@@ -830,13 +831,130 @@ __global__ void __launch_bounds__(256) k_trivar_solve(TriVarArgs<T> a) {
   }
 }
 
+// The same factorisation for factors stored in FP32 (MIXED / FP32 plans), in double-float
+// arithmetic on the FP32 pipes (~48-bit significands: the accuracy the low frequencies need,
+// without the FP64 pipe, which runs at a small fraction of the FP32 rate). Same scan structure.
+struct cmf { ffc a, b, c, d; };  // [[a, b], [c, d]]
+__device__ __forceinline__ ffc cfma_ff(ffc x, ffc y, ffc z) { return cadd(cmul(x, y), z); }
+__device__ __forceinline__ cmf cmf_mul(const cmf& X, const cmf& Y) {  // X Y
+  cmf R;
+  R.a = cfma_ff(X.a, Y.a, cmul(X.b, Y.c));
+  R.b = cfma_ff(X.a, Y.b, cmul(X.b, Y.d));
+  R.c = cfma_ff(X.c, Y.a, cmul(X.d, Y.c));
+  R.d = cfma_ff(X.c, Y.b, cmul(X.d, Y.d));
+  return R;
+}
+__device__ __forceinline__ ffc ffc_scale(ffc x, float s) { return ffc{x.rh * s, x.rl * s, x.ih * s, x.il * s}; }
+__device__ __forceinline__ cmf cmf_rescale(cmf X) {  // divide by a power of two near the largest entry
+  const float m = fmaxf(fmaxf(fmaxf(fabsf(X.a.rh), fabsf(X.a.ih)), fmaxf(fabsf(X.b.rh), fabsf(X.b.ih))),
+                        fmaxf(fmaxf(fabsf(X.c.rh), fabsf(X.c.ih)), fmaxf(fabsf(X.d.rh), fabsf(X.d.ih))));
+  if (!(m > 0.f)) return X;
+  int e;
+  frexpf(m, &e);
+  const float s = ldexpf(1.f, -e);
+  X.a = ffc_scale(X.a, s); X.b = ffc_scale(X.b, s); X.c = ffc_scale(X.c, s); X.d = ffc_scale(X.d, s);
+  return X;
+}
+__device__ __forceinline__ ffc ffc_shfl_up(ffc x, int d) {
+  return ffc{__shfl_up_sync(0xffffffffu, x.rh, d), __shfl_up_sync(0xffffffffu, x.rl, d),
+             __shfl_up_sync(0xffffffffu, x.ih, d), __shfl_up_sync(0xffffffffu, x.il, d)};
+}
+__device__ __forceinline__ cmf cmf_shfl_up(const cmf& X, int d) {
+  return cmf{ffc_shfl_up(X.a, d), ffc_shfl_up(X.b, d), ffc_shfl_up(X.c, d), ffc_shfl_up(X.d, d)};
+}
+// 1 / d for a double-float d > 0: FP32 reciprocal refined by one Newton step (error ~2^-46)
+__device__ __forceinline__ ff ff_recip(ff d) {
+  const float q = __frcp_rn(d.hi);
+  const ff e = ff_add(ff{1.f, 0.f}, ff_mul(d, ff{-q, 0.f}));  // 1 - d q
+  return ff_add(ff{q, 0.f}, ff_mul(ff{q, 0.f}, e));
+}
+__device__ __forceinline__ ffc ffc_inv(ffc z) {  // conj(z) / |z|^2
+  const ff re = ffc_re(z), im = ffc_im(z);
+  const ff n = ff_add(ff_mul(re, re), ff_mul(im, im));
+  const ff r = ff_recip(n);
+  return ffc_make(ff_mul(re, r), ff_mul(ff{-im.hi, -im.lo}, r));
+}
+
+template <int PER>
+__global__ void __launch_bounds__(256) k_trivar_factor_ff(TriVarArgs<float> a) {
+  __shared__ cmf tot[8];
+  const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int n = a.n, i0 = t * PER;
+  const float2 sg = reinterpret_cast<const float2*>(a.sigma)[j];
+  const ff sx{sg.x, 0.f}, sy{sg.y, 0.f};
+  const ff md = ff_from_double(a.md), mo = ff_from_double(a.mo), kd = ff_from_double(a.kd),
+           ko = ff_from_double(a.ko);
+  const ffc o = ffc_make(ff_add(ff_mul(sx, mo), ko), ff_mul(sy, mo));   // sigma_j m_o + k_o
+  const ffc mo_ = ffc{-o.rh, -o.rl, -o.ih, -o.il};
+  const ff bx = ff_add(ff_mul(sx, md), kd), by = ff_mul(sy, md);        // sigma_j m_d + k_d
+  const ffc z0{0.f, 0.f, 0.f, 0.f}, one{1.f, 0.f, 0.f, 0.f};
+  cmf P{one, z0, z0, one};
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = i0 + q;
+    if (i < n) {
+      const ffc bi = ffc_make(ff_add(bx, ff_from_double(a.r[i])), by);
+      cmf R;
+      R.a = cmul(o, P.c);
+      R.b = cmul(o, P.d);
+      R.c = cfma_ff(mo_, P.a, cmul(bi, P.c));
+      R.d = cfma_ff(mo_, P.b, cmul(bi, P.d));
+      P = R;
+      if ((q & 1) == 1) P = cmf_rescale(P);  // keep the FP32 exponent range
+    }
+  }
+  P = cmf_rescale(P);
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const cmf U = cmf_shfl_up(P, d);
+    if (lane >= d) P = cmf_rescale(cmf_mul(P, U));
+  }
+  if (lane == 31) tot[w] = P;
+  __syncthreads();
+  ffc u = z0, v = one;
+  for (int q = 0; q < w; ++q) {
+    const cmf& X = tot[q];
+    const ffc nu = cfma_ff(X.a, u, cmul(X.b, v)), nv = cfma_ff(X.c, u, cmul(X.d, v));
+    const float s = ldexpf(1.f, -ilogbf(fmaxf(fmaxf(fabsf(nu.rh), fabsf(nu.ih)), fmaxf(fabsf(nv.rh), fabsf(nv.ih))) + 1e-30f));
+    u = ffc_scale(nu, s); v = ffc_scale(nv, s);
+  }
+  {
+    const cmf E = cmf_shfl_up(P, 1);
+    if (lane > 0) {
+      const ffc nu = cfma_ff(E.a, u, cmul(E.b, v)), nv = cfma_ff(E.c, u, cmul(E.d, v));
+      u = nu; v = nv;
+    }
+  }
+  ffc c = cmul(u, ffc_inv(v));  // c'_{i0-1}
+  float2* ip = reinterpret_cast<float2*>(a.ip) + (size_t)j * n;
+  float2* cp = reinterpret_cast<float2*>(a.cp) + (size_t)j * n;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = i0 + q;
+    if (i < n) {
+      const ffc piv = cfma_ff(mo_, c, ffc_make(ff_add(bx, ff_from_double(a.r[i])), by));
+      const ffc iq = ffc_inv(piv);
+      c = cmul(o, iq);
+      ip[i] = make_float2(__fadd_rn(iq.rh, iq.rl), __fadd_rn(iq.ih, iq.il));
+      cp[i] = make_float2(__fadd_rn(c.rh, c.rl), __fadd_rn(c.ih, c.il));
+    }
+  }
+}
+
 template <typename T> cudaError_t launch_trivar_factor(const TriVarArgs<T>& a, cudaStream_t st) {
   if (a.n < 1 || a.n > 8 * 256) return cudaErrorInvalidValue;
   prof_begin("trivar_factor", st);
-  if (a.n <= 256) k_trivar_factor<T, 1><<<a.J, 256, 0, st>>>(a);
-  else if (a.n <= 512) k_trivar_factor<T, 2><<<a.J, 256, 0, st>>>(a);
-  else if (a.n <= 1024) k_trivar_factor<T, 4><<<a.J, 256, 0, st>>>(a);
-  else k_trivar_factor<T, 8><<<a.J, 256, 0, st>>>(a);
+  if constexpr (sizeof(T) == 4) {
+    if (a.n <= 256) k_trivar_factor_ff<1><<<a.J, 256, 0, st>>>(a);
+    else if (a.n <= 512) k_trivar_factor_ff<2><<<a.J, 256, 0, st>>>(a);
+    else if (a.n <= 1024) k_trivar_factor_ff<4><<<a.J, 256, 0, st>>>(a);
+    else k_trivar_factor_ff<8><<<a.J, 256, 0, st>>>(a);
+  } else {
+    if (a.n <= 256) k_trivar_factor<T, 1><<<a.J, 256, 0, st>>>(a);
+    else if (a.n <= 512) k_trivar_factor<T, 2><<<a.J, 256, 0, st>>>(a);
+    else if (a.n <= 1024) k_trivar_factor<T, 4><<<a.J, 256, 0, st>>>(a);
+    else k_trivar_factor<T, 8><<<a.J, 256, 0, st>>>(a);
+  }
   prof_end(st);
   return cudaGetLastError();
 }
