@@ -304,7 +304,9 @@ pint_status pint_nl_solve(pint_plan plan, const pint_poly* g, const double* Fhat
  * plan, F_hat, U, f and v; each admitted request runs as one graph launch (F_hat, U_0 = v, the
  * whole WR solve with its device-side convergence loop), so requests admitted while others run
  * overlap on the GPU. The iterate stays on the device until pint_poll copies it out and releases
- * the request's memory. The server is thread-safe; plans are internal to it. */
+ * the request's memory: a finished solution is held on the device (counted against the budget)
+ * until it is polled, except that when held solutions keep a queued request out, the oldest is
+ * moved to host memory first. The server is thread-safe; plans are internal to it. */
 typedef struct pint_server_s* pint_server;
 typedef struct {
   pint_plan_desc desc;  /* problem and precision (precision PINT_MIXED or PINT_FP64 recommended) */

@@ -123,7 +123,9 @@ struct Request {
   std::string err;
   pint_plan plan = nullptr;
   double *dv = nullptr, *df = nullptr, *dfd = nullptr, *dF = nullptr, *dU = nullptr;
-  std::vector<double> result;       // the solution, copied to the host when the solve completes
+  std::vector<double> result;       // the solution, once moved to the host to free the budget
+  bool held = false;                // finished, solution still on the device (dU), not yet polled
+  bool spilling = false;            // the worker is moving the solution to the host
   int slot = -1;
   int sweeps = 0;
   double upd = 0.0;
@@ -149,6 +151,7 @@ struct pint_server_s {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> queue;
+  std::deque<Request*> held;        // finished requests whose solution waits on the device
   std::unordered_map<uint64_t, Request*> reqs;
   uint64_t next_ticket = 1;
   bool stop = false;
@@ -172,16 +175,56 @@ size_t request_bytes(const pint_request& r) {
   return plan_bytes_estimate(&d) + 2 * 8 * NM + inputs + 8 * 256;
 }
 
-void release_request_memory(pint_server_s* s, Request* r) {
+// everything but the solution U
+void release_request_inputs(pint_server_s* s, Request* r) {
   if (r->plan) {
     plan_release(r->plan);
     r->plan = nullptr;
   }
-  double** arrays[] = {&r->dv, &r->df, &r->dfd, &r->dF, &r->dU};
+  double** arrays[] = {&r->dv, &r->df, &r->dfd, &r->dF};
   for (double** a : arrays) {
     if (*a) s->arena->release(*a);
     *a = nullptr;
   }
+}
+
+void release_request_memory(pint_server_s* s, Request* r) {
+  release_request_inputs(s, r);
+  if (r->dU) s->arena->release(r->dU);
+  r->dU = nullptr;
+}
+
+size_t request_unknowns(const Request* r) {
+  const pint_plan_desc& d = r->req.desc;
+  return (size_t)d.N * d.grid.mx * (d.grid.dim == 2 ? d.grid.my : 1);
+}
+
+// Move the oldest finished-but-unpolled solution to host memory and return its device memory to the
+// budget (when held results keep a queued request out). Returns false if none is held.
+bool spill_oldest(pint_server_s* s) {
+  Request* r = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->held.empty()) return false;
+    r = s->held.front();
+    s->held.pop_front();
+    r->spilling = true;
+  }
+  r->result.resize(request_unknowns(r));
+  const cudaError_t ce = cudaMemcpy(r->result.data(), r->dU, r->result.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost);
+  s->arena->release(r->dU);
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->dU = nullptr;
+  r->held = false;
+  r->spilling = false;
+  if (ce != cudaSuccess) {
+    r->status = PINT_ECUDA;
+    r->err = cudaGetErrorString(ce);
+    r->result.clear();
+  }
+  s->cv_done.notify_all();
+  return true;
 }
 
 // Set up one admitted request on its slot's stream: plan (from the arena), device arrays,
@@ -243,6 +286,7 @@ void worker_loop(pint_server_s* s) {
   for (;;) {
     to_start.clear();
     bool progressed = false;
+    bool spill = false;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       bool busy = false;
@@ -277,8 +321,12 @@ void worker_loop(pint_server_s* s) {
         for (int i = 0; i < s->max_active; ++i)
           if (!s->slots[i]) { slot = i; break; }
         if (slot < 0) break;
-        // memory held by running and by finished-but-unpolled requests is what the arena holds
-        if (s->arena->used() + r->need > s->budget) break;
+        // memory held by running and by finished-but-unpolled requests is what the arena holds;
+        // unpolled solutions give way to queued work (moved to the host, oldest first)
+        if (s->arena->used() + r->need > s->budget) {
+          spill = !s->held.empty();
+          break;
+        }
         s->queue.pop_front();
         r->slot = slot;
         r->state = RUNNING;
@@ -287,6 +335,7 @@ void worker_loop(pint_server_s* s) {
         to_start.push_back(r);
       }
     }
+    if (spill && spill_oldest(s)) progressed = true;
     for (Request* r : to_start) {
       start_request(s, r);
       progressed = true;
@@ -295,7 +344,7 @@ void worker_loop(pint_server_s* s) {
         s->slots[r->slot] = nullptr;
         bool others = false;
         for (Request* a : s->slots) others = others || a;
-        if (r->status == PINT_ENOMEM && others) {
+        if (r->status == PINT_ENOMEM && (others || !s->held.empty())) {
           // the arena is fragmented or the estimate was short: retry once others finish
           r->status = PINT_OK;
           r->state = QUEUED;
@@ -321,24 +370,21 @@ void worker_loop(pint_server_s* s) {
       if (q == cudaErrorNotReady) continue;
       bool conv = false;
       if (q == cudaSuccess) {
+        // the solution stays on the device until it is polled (or moved to the host when its
+        // memory is needed for queued requests); everything else returns to the budget now
         solve_result(r->plan, &r->sweeps, &r->upd, &conv);
         r->status = conv ? PINT_OK : PINT_ENOTCONV;
-        // move the solution to the host now so its device memory returns to the budget at once
-        // (a result that waits to be polled must not block admission of later requests)
-        const pint_plan_desc& dd = r->req.desc;
-        const size_t NM = (size_t)dd.N * dd.grid.mx * (dd.grid.dim == 2 ? dd.grid.my : 1);
-        r->result.resize(NM);
-        const cudaError_t ce = cudaMemcpy(r->result.data(), r->dU, NM * sizeof(double), cudaMemcpyDeviceToHost);
-        if (ce != cudaSuccess) {
-          r->status = PINT_ECUDA;
-          r->err = cudaGetErrorString(ce);
-        }
+        release_request_inputs(s, r);
       } else {
         r->status = PINT_ECUDA;
         r->err = cudaGetErrorString(q);
+        release_request_memory(s, r);
       }
-      release_request_memory(s, r);
       std::lock_guard<std::mutex> lk(s->mu);
+      if (r->dU) {
+        r->held = true;
+        s->held.push_back(r);
+      }
       r->t_done = s->now();
       r->state = DONE;
       s->slots[i] = nullptr;
@@ -478,11 +524,28 @@ extern "C" pint_status pint_poll(pint_server s, uint64_t ticket, int timeout_us,
       }
       return timeout_us > 0 ? PINT_ETIMEOUT : PINT_EAGAIN;
     }
+    // a solution being moved to the host by the worker: wait for the move (it is one copy)
+    while (r->spilling) s->cv_done.wait_for(lk, std::chrono::milliseconds(10));
     s->reqs.erase(it);
+    if (r->held) {
+      s->held.erase(std::find(s->held.begin(), s->held.end(), r));
+      r->held = false;
+    }
   }
   pint_status st = r->status;
-  if ((st == PINT_OK || st == PINT_ENOTCONV) && U_out && !r->result.empty())
-    std::memcpy(U_out, r->result.data(), r->result.size() * sizeof(double));
+  if ((st == PINT_OK || st == PINT_ENOTCONV) && U_out) {
+    if (r->dU) {
+      const cudaError_t ce = cudaMemcpy(U_out, r->dU, request_unknowns(r) * sizeof(double), cudaMemcpyDeviceToHost);
+      if (ce != cudaSuccess) {
+        st = PINT_ECUDA;
+        r->err = cudaGetErrorString(ce);
+      }
+    } else if (!r->result.empty()) {
+      std::memcpy(U_out, r->result.data(), r->result.size() * sizeof(double));
+    }
+  }
+  if (r->dU) s->arena->release(r->dU);
+  r->dU = nullptr;
   if (info) {
     info->status = st;
     info->sweeps = r->sweeps;

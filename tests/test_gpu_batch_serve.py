@@ -227,3 +227,21 @@ def test_server_device_inputs():
             out = np.empty((p.N, p.M))
             st, info = srv.poll(t, out, timeout_us=30_000_000)
             assert st == 0 and rel_l2(out, oracle_solution(p)) <= 1e-8
+
+
+def test_server_unpolled_results_give_way_to_queued_requests():
+    """Finished solutions wait on the device until polled; when they keep a queued request out of
+    a tight budget the oldest are moved to host memory, so polling in any order completes."""
+    torch_cuda()
+    from paper_2007_13125_gb300 import pint
+    probs = [workloads.small_problem(dim=2, mx=255, N=128, k=2, alpha=1.0, kappa=0.1, seed=30 + i) for i in range(5)]
+    budget = 400 << 20            # one running request (~0.35 GB) plus about one held solution (67 MB)
+    with pint.Server(budget, max_active=4) as srv:
+        tickets = [srv.submit(p, *_host_inputs(p), tol=1e-8) for p in probs]
+        for p, t in reversed(list(zip(probs, tickets))):
+            out = np.empty((p.N, p.M))
+            st, info = srv.poll(t, out, timeout_us=60_000_000)
+            assert st == 0 and rel_l2(out, oracle_solution(p)) <= 1e-8
+        stats = srv.stats()
+        assert stats["peak_hbm"] <= budget
+        assert stats["hbm_in_use"] == 0
