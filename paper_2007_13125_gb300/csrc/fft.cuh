@@ -36,6 +36,8 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
   r.y = a.x * b.y + a.y * b.x;
   return r;
 }
+template <typename V> __device__ __forceinline__ V cneg(V a) { V r; r.x = -a.x; r.y = -a.y; return r; }
+template <typename V> __device__ __forceinline__ V czero() { V r; r.x = 0; r.y = 0; return r; }
 // a * conj(b)
 template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
   V r;
@@ -87,6 +89,16 @@ __device__ __forceinline__ ffc twid16(ffc v) {
 }
 
 __host__ __device__ constexpr int ilog2c(int r) { return r <= 1 ? 0 : 1 + ilog2c(r >> 1); }
+// the same for values known only at run time (ilog2c recurses when its argument is not a constant)
+__host__ __device__ inline int ilog2r(int r) {
+#ifdef __CUDA_ARCH__
+  return r <= 1 ? 0 : 31 - __clz(r);
+#else
+  int e = 0;
+  while (r > 1) { r >>= 1; ++e; }
+  return e;
+#endif
+}
 __host__ __device__ constexpr int brev(int i, int bits) {
   return bits == 0 ? 0 : ((i & 1) << (bits - 1)) | brev(i >> 1, bits - 1);
 }
@@ -137,11 +149,11 @@ __device__ __forceinline__ void dft_reg(V (&x)[R]) {
 // take the extra bit), each radix at most 2^MAXLOG (16 by default; smaller for wide element
 // types to bound registers).
 __host__ __device__ inline int fft_npass(int L, int maxlog = 4) {
-  const int e = ilog2c(L);
+  const int e = ilog2r(L);
   return (e + maxlog - 1) / maxlog;
 }
 __host__ __device__ inline int fft_logradix(int L, int pass, int maxlog = 4) {
-  const int e = ilog2c(L);
+  const int e = ilog2r(L);
   const int np = (e + maxlog - 1) / maxlog;
   return e / np + (pass < e % np ? 1 : 0);
 }
@@ -149,10 +161,10 @@ __host__ __device__ inline int fft_radix(int L, int pass, int maxlog = 4) { retu
 
 // position of frequency j in the output of the forward transform
 __host__ __device__ inline int fft_pos(int j, int L, int maxlog = 4) {
-  const int np = fft_npass(L, maxlog);
-  int p = 0, logLs = ilog2c(L);
+  const int e = ilog2r(L), np = (e + maxlog - 1) / maxlog, base = e / np, extra = e - base * np;
+  int p = 0, logLs = e;
   for (int i = 0; i < np; ++i) {
-    const int lr = fft_logradix(L, i, maxlog);
+    const int lr = base + (i < extra ? 1 : 0);
     const int q = j & ((1 << lr) - 1);
     j >>= lr;
     logLs -= lr;
@@ -219,7 +231,7 @@ __device__ __forceinline__ void fft_pass_dispatch(int lr, V* X, int ld, int logC
 // tw[m] = exp(-2 pi i m / L), m < L, must be visible to all threads. C = 2^logC columns.
 template <int MAXLOG = 4, typename V>
 __device__ void fft_forward(V* X, int ld, int logC, int L, const V* tw) {
-  const int logL = ilog2c(L);
+  const int logL = ilog2r(L);
   const int np = fft_npass(L, MAXLOG);
   int logLs = logL;
   for (int i = 0; i < np; ++i) {
@@ -233,7 +245,7 @@ __device__ void fft_forward(V* X, int ld, int logC, int L, const V* tw) {
 // Inverse: permuted order in, natural order out, unnormalised: x_n = sum_j X_j exp(+2 pi i n j / L).
 template <int MAXLOG = 4, typename V>
 __device__ void fft_inverse(V* X, int ld, int logC, int L, const V* tw) {
-  const int logL = ilog2c(L);
+  const int logL = ilog2r(L);
   const int np = fft_npass(L, MAXLOG);
   int logLs = 0;
   for (int i = np - 1; i >= 0; --i) {
@@ -252,10 +264,12 @@ __host__ __device__ constexpr int ct_logradix(int logL, int pass, int maxlog) {
   return logL / ct_npass(logL, maxlog) + (pass < logL % ct_npass(logL, maxlog) ? 1 : 0);
 }
 
-template <int LR, int DIR, int LOGL, int LOGLS, int LOGC, int LD, typename V>
+// NITEMS > 0 restricts the pass to its first NITEMS (group, column) items, i.e. to the leading
+// rows NITEMS / C * R of the tile (whole blocks of sub-length 2^LOGLS).
+template <int LR, int DIR, int LOGL, int LOGLS, int LOGC, int LD, int NITEMS = 0, typename V>
 __device__ __forceinline__ void fft_pass_ct(V* X, const V* tw) {
   constexpr int R = 1 << LR, LOGS = LOGLS - LR, S = 1 << LOGS, C = 1 << LOGC;
-  constexpr int ITEMS = 1 << (LOGL - LR + LOGC);
+  constexpr int ITEMS = NITEMS > 0 ? NITEMS : 1 << (LOGL - LR + LOGC);
   constexpr int TSHIFT = LOGL - LOGLS;  // W_Ls^e = W_L^{e << TSHIFT}
   for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
     const int c = it & (C - 1);
@@ -304,6 +318,203 @@ __device__ __forceinline__ void fft_inverse_ct_rec(V* X, const V* tw) {
     __syncthreads();
     fft_inverse_ct_rec<P - 1, LOGL, LOGLS + LR, LOGC, LD, MAXLOG>(X, tw);
   }
+}
+
+// ---- transforms of odd sequences, x_{L-i} = -x_i (the odd extension behind the sine transform),
+// compiled shapes, radix schedule MAXLOG = 4. The spectrum of an odd sequence is odd, Y_{L-j} = -Y_j,
+// and the first forward pass (radix R = 2^LR0, stride S = L/R) sends frequency j to block j mod R
+// (rows (j mod R) S .. + S - 1), so blocks q > R/2 are the negated mirrors of blocks R - q and are
+// never formed: the tile holds ODD_ROWS = (R/2 + 1) S rows instead of L, and every pass after the
+// first runs on those rows only.
+//   odd_forward_pass0: rows 0..L/2 hold x_0..x_{L/2} (x_0 = x_{L/2} = 0) on entry; on exit blocks
+//     0..R/2 hold what the full first pass writes there. Items pair n2 = t with S - t (t = 0 pairs
+//     0 with S/2): between them they read exactly the rows they write, so the pass is in place.
+//   odd_inverse_pass0: the inverse's last pass from blocks 0..R/2, using for q > R/2
+//     z_q(n2) = -W_S^{n2} z_{R-q}(S - n2) (z_q the inverse sub-transforms of the blocks, W_S =
+//     exp(-2 pi i / S)); writes x_n at rows n < L/2.
+//   Where the pairs would leave threads of an NT-thread block idle (S C <= NT), each n2 is an item
+//   of its own instead: one item per thread, all loads, a barrier, then the stores.
+// Frequency j (j mod R <= R/2) sits at row fft_pos(j); odd_pos gives the row and sign of any j.
+template <int LOGL> __host__ __device__ constexpr int odd_rows() {
+  return ((1 << (ct_logradix(LOGL, 0, 4) - 1)) + 1) << (LOGL - ct_logradix(LOGL, 0, 4));
+}
+
+template <int LOGL, int LOGC, int LD, int NT, typename V>
+__device__ __forceinline__ void odd_forward_pass0(V* X, const V* tw) {
+  constexpr int LR = ct_logradix(LOGL, 0, 4), R = 1 << LR, H = R / 2, S = 1 << (LOGL - LR), C = 1 << LOGC;
+  if constexpr ((S << LOGC) <= NT) {
+    const int it = threadIdx.x, c = it & (C - 1), n2 = it >> LOGC;
+    const bool act = it < (S << LOGC);
+    V* col = X + c;
+    V a[R];
+    if (act) {
+#pragma unroll
+      for (int u = 0; u < H; ++u) a[u] = col[(n2 + S * u) * LD];
+#pragma unroll
+      for (int s = 1; s <= H; ++s) a[R - s] = cneg(col[(S * s - n2) * LD]);
+    }
+    __syncthreads();
+    if (act) {
+      dft_reg<R, -1>(a);
+#pragma unroll
+      for (int q = 0; q <= H; ++q) col[(n2 + S * q) * LD] = q ? cmul(a[q], tw[n2 * q]) : a[q];
+    }
+    return;
+  }
+  constexpr int ITEMS = (S / 2) << LOGC;
+  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
+    const int c = it & (C - 1), t = it >> LOGC;
+    V* col = X + c;
+    V a[R], b[R];
+    int na, nb;
+    if (t == 0) {
+      na = 0;
+      nb = S / 2;
+      a[0] = czero<V>();
+      a[H] = czero<V>();
+#pragma unroll
+      for (int u = 1; u < H; ++u) {
+        const V v = col[(S * u) * LD];
+        a[u] = v;
+        a[R - u] = cneg(v);
+      }
+#pragma unroll
+      for (int u = 0; u < H; ++u) {
+        const V v = col[(S / 2 + S * u) * LD];
+        b[u] = v;
+        b[R - 1 - u] = cneg(v);
+      }
+    } else {
+      na = t;
+      nb = S - t;
+#pragma unroll
+      for (int u = 0; u < H; ++u) {
+        const V d = col[(t + S * u) * LD];
+        a[u] = d;
+        b[R - 1 - u] = cneg(d);
+      }
+#pragma unroll
+      for (int s = 1; s <= H; ++s) {
+        const V e = col[(S * s - t) * LD];
+        a[R - s] = cneg(e);
+        b[s - 1] = e;
+      }
+    }
+    dft_reg<R, -1>(a);
+#pragma unroll
+    for (int q = 0; q <= H; ++q) col[(na + S * q) * LD] = q ? cmul(a[q], tw[na * q]) : a[q];
+    dft_reg<R, -1>(b);
+#pragma unroll
+    for (int q = 0; q <= H; ++q) col[(nb + S * q) * LD] = q ? cmul(b[q], tw[nb * q]) : b[q];
+  }
+}
+
+template <int LOGL, int LOGC, int LD, int NT, typename V>
+__device__ __forceinline__ void odd_inverse_pass0(V* X, const V* tw) {
+  constexpr int LR = ct_logradix(LOGL, 0, 4), R = 1 << LR, H = R / 2, S = 1 << (LOGL - LR), C = 1 << LOGC;
+  if constexpr ((S << LOGC) <= NT) {
+    const int it = threadIdx.x, c = it & (C - 1), n2 = it >> LOGC, m2 = (S - n2) & (S - 1);
+    const bool act = it < (S << LOGC);
+    V* col = X + c;
+    V z[H + 1], zm[H];
+    if (act) {
+#pragma unroll
+      for (int q = 0; q <= H; ++q) z[q] = col[(S * q + n2) * LD];
+#pragma unroll
+      for (int q = 1; q < H; ++q) zm[q] = col[(S * q + m2) * LD];
+    }
+    __syncthreads();
+    if (act) {
+      V y[R];
+      y[0] = z[0];
+#pragma unroll
+      for (int q = 1; q <= H; ++q) y[q] = cmulc(z[q], tw[n2 * q]);
+#pragma unroll
+      for (int q = 1; q < H; ++q) y[R - q] = cneg(cmul(zm[q], tw[n2 * q]));
+      dft_reg<R, 1>(y);
+#pragma unroll
+      for (int r = 0; r < H; ++r) col[(n2 + S * r) * LD] = y[r];
+    }
+    return;
+  }
+  constexpr int ITEMS = (S / 2) << LOGC;
+  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
+    const int c = it & (C - 1), t = it >> LOGC;
+    V* col = X + c;
+    const int na = t == 0 ? 0 : t, nb = t == 0 ? S / 2 : S - t;
+    V za[H + 1], zb[H + 1];
+#pragma unroll
+    for (int q = 0; q <= H; ++q) {
+      za[q] = col[(S * q + na) * LD];
+      zb[q] = col[(S * q + nb) * LD];
+    }
+    // n2 = na: its mirror S - na is na itself when t = 0, else nb
+    {
+      V y[R];
+      y[0] = za[0];
+#pragma unroll
+      for (int q = 1; q <= H; ++q) y[q] = cmulc(za[q], tw[na * q]);
+#pragma unroll
+      for (int q = 1; q < H; ++q) y[R - q] = cneg(cmul(t == 0 ? za[q] : zb[q], tw[na * q]));
+      dft_reg<R, 1>(y);
+#pragma unroll
+      for (int r = 0; r < H; ++r) col[(na + S * r) * LD] = y[r];
+    }
+    {
+      V y[R];
+      y[0] = zb[0];
+#pragma unroll
+      for (int q = 1; q <= H; ++q) y[q] = cmulc(zb[q], tw[nb * q]);
+#pragma unroll
+      for (int q = 1; q < H; ++q) y[R - q] = cneg(cmul(t == 0 ? zb[q] : za[q], tw[nb * q]));
+      dft_reg<R, 1>(y);
+#pragma unroll
+      for (int r = 0; r < H; ++r) col[(nb + S * r) * LD] = y[r];
+    }
+  }
+}
+
+// forward passes P..NP-1 (inverse passes P..1) on the leading ROWS rows; __syncthreads after each
+template <int P, int NP, int LOGL, int LOGLS, int LOGC, int LD, int ROWS, typename V>
+__device__ __forceinline__ void odd_forward_rec(V* X, const V* tw) {
+  if constexpr (P < NP) {
+    constexpr int LR = ct_logradix(LOGL, P, 4);
+    fft_pass_ct<LR, -1, LOGL, LOGLS, LOGC, LD, (ROWS >> LR) << LOGC>(X, tw);
+    __syncthreads();
+    odd_forward_rec<P + 1, NP, LOGL, LOGLS - LR, LOGC, LD, ROWS>(X, tw);
+  }
+}
+template <int P, int LOGL, int LOGLS, int LOGC, int LD, int ROWS, typename V>
+__device__ __forceinline__ void odd_inverse_rec(V* X, const V* tw) {
+  if constexpr (P >= 1) {
+    constexpr int LR = ct_logradix(LOGL, P, 4);
+    fft_pass_ct<LR, 1, LOGL, LOGLS + LR, LOGC, LD, (ROWS >> LR) << LOGC>(X, tw);
+    __syncthreads();
+    odd_inverse_rec<P - 1, LOGL, LOGLS + LR, LOGC, LD, ROWS>(X, tw);
+  }
+}
+
+// row of frequency j in the odd-sequence spectrum, with bit 15 set where the row holds -Y_j
+template <int LOGL>
+__device__ __forceinline__ int odd_pos(int j) {
+  constexpr int R = 1 << ct_logradix(LOGL, 0, 4), L = 1 << LOGL;
+  return (j & (R - 1)) > R / 2 ? (fft_pos(L - j, L) | 0x8000) : fft_pos(j, L);
+}
+
+// ct_freq maps a row of the permuted spectrum to its frequency (the inverse of fft_pos for the
+// compiled shapes).
+template <int LOGL, int MAXLOG = 4>
+__device__ __forceinline__ int ct_freq(int pos) {
+  constexpr int NP = ct_npass(LOGL, MAXLOG);
+  int j = 0, shift = 0, logLs = LOGL;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const int lr = ct_logradix(LOGL, i, MAXLOG);
+    logLs -= lr;
+    j += ((pos >> logLs) & ((1 << lr) - 1)) << shift;
+    shift += lr;
+  }
+  return j;
 }
 
 // Same contracts as fft_forward / fft_inverse.

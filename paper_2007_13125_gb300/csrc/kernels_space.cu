@@ -35,19 +35,68 @@ namespace pint {
 // brought into natural order through registers (lanes along lines), for the same reason.
 template <typename T> constexpr int axis_regs() { return sizeof(T) == 4 ? 16 : 8; }
 // (the mass-eigenvalue table is carved only for P1 FEM lines: has_mu)
-template <typename T> size_t axis_smem(int n, int C, bool has_mu) {
+// (rows: tile rows, L for the generic instance, odd_rows<LOGL>() for the compiled shapes)
+template <typename T> size_t axis_smem(int n, int C, bool has_mu, int rows) {
   const size_t L = 2 * (size_t)(n + 1);
-  return sizeof(typename c2<T>::t) * (L * (C + 1) + L + C) + (has_mu ? 2 : 1) * sizeof(T) * (size_t)(n + 1) +
+  return sizeof(typename c2<T>::t) * ((size_t)rows * (C + 1) + L + C) + (has_mu ? 2 : 1) * sizeof(T) * (size_t)(n + 1) +
          sizeof(unsigned short) * L + 2 * sizeof(int) * C + 64;
 }
 
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
+// The divide of op 1 for the compiled shapes, fused with the last forward and the first inverse
+// FFT pass: both work on groups of R = 2^LR consecutive rows without twiddles, so each thread takes
+// one group of one line through forward DFT-R, division, inverse DFT-R in registers (one shared-
+// memory round trip instead of three). Row base + q of the permuted spectrum holds frequency
+// ct_freq(base) + q L / R; frequencies f and L - f share the divisor, 0 and n + 1 are zero. Only
+// the odd_rows<LOGL>() rows of the spectrum that are formed are visited.
+template <typename T, int LOGL, int LOGC, typename V>
+__device__ __forceinline__ void axis_divide_fused(V* X, const V* dcol, const T* lam, const T* mu, bool has_mu,
+                                                  T scale, int cols) {
+  constexpr int NP = ct_npass(LOGL, 4), LR = ct_logradix(LOGL, NP - 1, 4);
+  constexpr int R = 1 << LR, C = 1 << LOGC, LD = C + 1, L = 1 << LOGL, n = L / 2 - 1;
+  constexpr int ITEMS = (odd_rows<LOGL>() >> LR) << LOGC;
+  const T zero = T(0);
+  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
+    const int c = it & (C - 1);
+    const int base = (it >> LOGC) << LR;
+    V* p = X + base * LD + c;
+    V x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = p[r * LD];
+    dft_reg<R, -1>(x);
+    const V dc = dcol[c];
+    const bool ok = c < cols;
+    const int f0 = ct_freq<LOGL>(base);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      int f = f0 + q * (L / R);
+      if (f > n + 1) f = L - f;
+      if (!ok || f == 0 || f == n + 1) {
+        x[q] = mk(zero, zero);
+      } else {
+        // scale * (sigma_j mu_f + lambda_other + lambda_f), mu_f = 1 for finite differences
+        const T mp = has_mu ? mu[f - 1] : T(1);
+        const T dx = (dc.x * mp + lam[f - 1]) * scale, dy = dc.y * mp * scale;
+        const T inv = rcp(dx * dx + dy * dy);
+        x[q] = cmulc(x[q], mk(dx * inv, dy * inv));  // x / d = x conj(d) / |d|^2
+      }
+    }
+    dft_reg<R, 1>(x);
+#pragma unroll
+    for (int r = 0; r < R; ++r) p[r * LD] = x[r];
+  }
+}
+
+// (L = 512, radix 8 everywhere: 64 registers and a 50 KB tile, so four CTAs fit on an SM; the
+// radix-16 shapes need about 80 registers.)
 // LOGL > 0: compiled for lines of L = 2^LOGL extended points in tiles of 2^LOGC lines (the
-// shapes of the usual grids); LOGL = 0: any shape, taken from the arguments.
+// shapes of the usual grids), transformed as odd sequences (only rows 0..L/2 of the extension are
+// stored, and only the odd_rows<LOGL>() rows of the spectrum that are not mirrors of others are
+// formed); LOGL = 0: any shape, taken from the arguments, with the full odd extension.
 template <typename T, int LOGL, int LOGC>
-__global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, LOGL == 9 ? 4 : 3) k_axis(AxisArgs<T> a) {
   using V = typename c2<T>::t;
   constexpr int KR = axis_regs<T>();  // register slots per thread for the reordering
   constexpr int KB = 8;               // global loads in flight per thread
@@ -56,8 +105,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
   const int n = CT ? (1 << (LOGL - 1)) - 1 : a.n;
   const int C = CT ? (1 << LOGC) : a.C, logC = CT ? LOGC : a.logC, ld = CT ? (1 << LOGC) + 1 : a.ld;
   const int L = 2 * (n + 1);
+  constexpr int XROWS = odd_rows<(CT ? LOGL : 7)>();
   V* X = reinterpret_cast<V*>(smraw);
-  V* tw = X + (size_t)L * ld;
+  V* tw = X + (size_t)(CT ? XROWS : L) * ld;
   V* dcol = tw + L;                                      // line -> sigma_j + lambda_other (op 1)
   T* lam = reinterpret_cast<T*>(dcol + C);               // lambda along this axis (op 1)
   T* mu = lam + n + 1;                                   // P1 mass eigenvalues (op 1, FEM)
@@ -66,7 +116,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
   int* lp = lj + C;                                      // line -> position within its slice
   const V* gtw = reinterpret_cast<const V*>(a.tw);
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = gtw[i];
-  fft_perm_table(perm, L);
+  if constexpr (CT) {
+    // (op 1 finds frequencies arithmetically)
+    if (a.op == 0)
+      for (int j = threadIdx.x; j < L; j += blockDim.x) perm[j] = (unsigned short)odd_pos<(CT ? LOGL : 7)>(j);
+  } else {
+    fft_perm_table(perm, L);
+  }
   V* S = reinterpret_cast<V*>(a.S);
   const int line0 = blockIdx.x * C;
   const int per = a.mode == 0 ? a.lines_per_j : a.P;
@@ -78,6 +134,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
   __syncthreads();
   const T zero = T(0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  // rows 1..n of the tile back to the lines (op 1's result)
+  auto store_lines = [&]() {
+    if (a.mode == 0) {
+      for (int cc = warp; cc < C; cc += nwarp) {
+        const int line = line0 + cc;
+        if (line >= a.lines) continue;
+        for (int i = lane; i < n; i += 32) S[(size_t)line * n + i] = X[(size_t)(i + 1) * ld + cc];
+      }
+    } else {
+      for (int it = threadIdx.x; it < (n << logC); it += blockDim.x) {
+        const int cc = it & (C - 1), i = it >> logC;
+        if (line0 + cc < a.lines) S[((size_t)lj[cc] * n + i) * a.P + lp[cc]] = X[(size_t)(i + 1) * ld + cc];
+      }
+    }
+  };
 
   // ---- load with odd extension (KB independent loads per thread before the stores) ----
   if (a.mode == 0) {
@@ -97,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
           const int i = i0 + lane + 32 * t;
           if (i < n) {
             X[(size_t)(i + 1) * ld + cc] = v[t];
-            X[(size_t)(L - 1 - i) * ld + cc] = mk(-v[t].x, -v[t].y);
+            if constexpr (!CT) X[(size_t)(L - 1 - i) * ld + cc] = mk(-v[t].x, -v[t].y);
           }
         }
       }
@@ -118,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
         if (it < tot) {
           const int cc = it & (C - 1), i = it >> logC;
           X[(size_t)(i + 1) * ld + cc] = v[t];
-          X[(size_t)(L - 1 - i) * ld + cc] = mk(-v[t].x, -v[t].y);
+          if constexpr (!CT) X[(size_t)(L - 1 - i) * ld + cc] = mk(-v[t].x, -v[t].y);
         }
       }
     }
@@ -144,11 +215,37 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
     }
   }
   __syncthreads();
-  if constexpr (CT) fft_forward_ct<LOGL, LOGC, (1 << LOGC) + 1>(X, tw);
-  else fft_forward(X, ld, logC, L, tw);
+  if constexpr (CT) {
+    constexpr int LD = (1 << LOGC) + 1, NP = ct_npass(LOGL, 4), LR0 = ct_logradix(LOGL, 0, 4);
+    constexpr int LRL = ct_logradix(LOGL, NP - 1, 4);
+    odd_forward_pass0<LOGL, LOGC, LD, kThreads>(X, tw);
+    __syncthreads();
+    odd_forward_rec<1, NP - 1, LOGL, LOGL - LR0, LOGC, LD, XROWS>(X, tw);
+    if (a.op == 1) {
+      axis_divide_fused<T, LOGL, LOGC>(X, dcol, lam, mu, a.mu_axis != nullptr, a.scale, a.lines - line0);
+      __syncthreads();
+      odd_inverse_rec<NP - 2, LOGL, LRL, LOGC, LD, XROWS>(X, tw);
+      odd_inverse_pass0<LOGL, LOGC, LD, kThreads>(X, tw);
+      __syncthreads();
+      store_lines();
+      return;
+    }
+    odd_forward_rec<NP - 1, NP, LOGL, LRL, LOGC, LD, XROWS>(X, tw);
+  } else {
+    fft_forward(X, ld, logC, L, tw);
+  }
 
   if (a.op == 0) {
-    // D-transform only: -2i D x at frequencies 1..n, stored in natural order
+    // D-transform only: -2i D x at frequencies 1..n, stored in natural order. A perm entry is the
+    // row of a frequency; for the compiled shapes bit 15 marks a row holding the negated value.
+    auto fetch = [&](unsigned short e, int cc) {
+      if constexpr (CT) {
+        const V v = X[(size_t)(e & 0x7fff) * ld + cc];
+        return (e & 0x8000) ? mk(-v.x, -v.y) : v;
+      } else {
+        return X[(size_t)e * ld + cc];
+      }
+    };
     const int tot = n << logC;
     if (tot <= KR * (int)blockDim.x) {
       // frequency p sits in row perm[p]: move rows perm[1..n] to rows 1..n through registers
@@ -156,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
 #pragma unroll
       for (int t = 0; t < KR; ++t) {
         const int it = threadIdx.x + t * blockDim.x;
-        if (it < tot) v[t] = X[(size_t)perm[1 + (it >> logC)] * ld + (it & (C - 1))];
+        if (it < tot) v[t] = fetch(perm[1 + (it >> logC)], it & (C - 1));
       }
       __syncthreads();
 #pragma unroll
@@ -181,13 +278,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
       for (int cc = warp; cc < C; cc += nwarp) {
         const int line = line0 + cc;
         if (line >= a.lines) continue;
-        for (int i = lane; i < n; i += 32) S[(size_t)line * n + i] = X[(size_t)perm[i + 1] * ld + cc];
+        for (int i = lane; i < n; i += 32) S[(size_t)line * n + i] = fetch(perm[i + 1], cc);
       }
     } else {
       for (int it = threadIdx.x; it < tot; it += blockDim.x) {
         const int cc = it & (C - 1), i = it >> logC;
         if (line0 + cc < a.lines)
-          S[((size_t)lj[cc] * n + i) * a.P + lp[cc]] = X[(size_t)perm[i + 1] * ld + cc];
+          S[((size_t)lj[cc] * n + i) * a.P + lp[cc]] = fetch(perm[i + 1], cc);
       }
     }
     return;
@@ -195,6 +292,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
 
   // ---- divide by scale * (sigma_j + lambda_other + lambda_p) at frequencies p and L-p ----
   // (both rows share the divisor; frequencies 0 and n+1 are zero for an odd sequence)
+  if constexpr (!CT) {
   for (int it = threadIdx.x; it < ((n + 2) << logC); it += blockDim.x) {
     const int cc = it & (C - 1), p = it >> logC;
     const size_t pos = (size_t)perm[p] * ld + cc;
@@ -217,25 +315,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_axis(AxisArgs<T> a) {
     X[pos2] = cmulc(X[pos2], q);
   }
   __syncthreads();
-  if constexpr (CT) fft_inverse_ct<LOGL, LOGC, (1 << LOGC) + 1>(X, tw);
-  else fft_inverse(X, ld, logC, L, tw);
-
-  if (a.mode == 0) {
-    for (int cc = warp; cc < C; cc += nwarp) {
-      const int line = line0 + cc;
-      if (line >= a.lines) continue;
-      for (int i = lane; i < n; i += 32) S[(size_t)line * n + i] = X[(size_t)(i + 1) * ld + cc];
-    }
-  } else {
-    for (int it = threadIdx.x; it < (n << logC); it += blockDim.x) {
-      const int cc = it & (C - 1), i = it >> logC;
-      if (line0 + cc < a.lines) S[((size_t)lj[cc] * n + i) * a.P + lp[cc]] = X[(size_t)(i + 1) * ld + cc];
-    }
+  fft_inverse(X, ld, logC, L, tw);
+  store_lines();
   }
 }
 
 template <typename T, int LOGL, int LOGC>
-static cudaError_t launch_axis_k(const AxisArgs<T>& a, size_t sm, cudaStream_t st) {
+static cudaError_t launch_axis_k(const AxisArgs<T>& a, cudaStream_t st) {
+  const size_t sm = axis_smem<T>(a.n, a.C, a.mu_axis != nullptr, LOGL > 0 ? odd_rows<(LOGL > 0 ? LOGL : 7)>()
+                                                                          : 2 * (a.n + 1));
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_axis<T, LOGL, LOGC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -250,20 +338,19 @@ static cudaError_t launch_axis_k(const AxisArgs<T>& a, size_t sm, cudaStream_t s
 }
 
 template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t st) {
-  const size_t sm = axis_smem<T>(a.n, a.C, a.mu_axis != nullptr);
   if constexpr (sizeof(T) == 4) {
     // compiled shapes: n = 2^q - 1 with the tile widths the plan picks for them
     const int L = 2 * (a.n + 1);
     if (a.ld == a.C + 1) {
-      if (L == 128 && a.C == 16) return launch_axis_k<T, 7, 4>(a, sm, st);
-      if (L == 256 && a.C == 16) return launch_axis_k<T, 8, 4>(a, sm, st);
-      if (L == 512 && a.C == 16) return launch_axis_k<T, 9, 4>(a, sm, st);
-      if (L == 1024 && a.C == 8) return launch_axis_k<T, 10, 3>(a, sm, st);
-      if (L == 2048 && a.C == 4) return launch_axis_k<T, 11, 2>(a, sm, st);
-      if (L == 4096 && a.C == 2) return launch_axis_k<T, 12, 1>(a, sm, st);
+      if (L == 128 && a.C == 16) return launch_axis_k<T, 7, 4>(a, st);
+      if (L == 256 && a.C == 16) return launch_axis_k<T, 8, 4>(a, st);
+      if (L == 512 && a.C == 16) return launch_axis_k<T, 9, 4>(a, st);
+      if (L == 1024 && a.C == 8) return launch_axis_k<T, 10, 3>(a, st);
+      if (L == 2048 && a.C == 4) return launch_axis_k<T, 11, 2>(a, st);
+      if (L == 4096 && a.C == 2) return launch_axis_k<T, 12, 1>(a, st);
     }
   }
-  return launch_axis_k<T, 0, 0>(a, sm, st);
+  return launch_axis_k<T, 0, 0>(a, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -970,8 +1057,8 @@ template <typename T> cudaError_t launch_trivar_solve(const TriVarArgs<T>& a, cu
   return cudaGetLastError();
 }
 
-template size_t axis_smem<float>(int, int, bool);
-template size_t axis_smem<double>(int, int, bool);
+template size_t axis_smem<float>(int, int, bool, int);
+template size_t axis_smem<double>(int, int, bool, int);
 template cudaError_t launch_axis<float>(const AxisArgs<float>&, cudaStream_t);
 template cudaError_t launch_axis<double>(const AxisArgs<double>&, cudaStream_t);
 template cudaError_t launch_axis_per<float>(const AxisArgs<float>&, cudaStream_t);

@@ -151,7 +151,7 @@ size_t resid_fwd_smem(int N, int C);
 size_t inv_upd_smem(int N, int C);
 template <typename T> size_t direct_smem(int N, int C);
 size_t toep_smem(int N, int C);
-template <typename T> size_t axis_smem(int n, int C, bool has_mu = false);
+template <typename T> size_t axis_smem(int n, int C, bool has_mu, int rows);
 
 cudaError_t launch_resid_fwd(const ResidFwdArgs& a, cudaStream_t st);
 // first sweep from U_0^n = v (a.v, a.beta set): no U read, no history

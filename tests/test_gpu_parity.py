@@ -181,6 +181,22 @@ def test_edge_sizes():
             assert rel_l2(U, ref) <= bar, (case, prec, sweeps)
 
 
+@pytest.mark.parametrize("dim,mx,my", [(1, 63, 0), (1, 127, 0), (1, 255, 0), (1, 511, 0), (1, 1023, 0), (1, 2047, 0),
+                                       (2, 63, 63), (2, 127, 31), (2, 255, 15), (2, 511, 15), (2, 1023, 7),
+                                       (2, 15, 511), (2, 7, 1023)])
+def test_compiled_line_lengths(dim, mx, my):
+    # every compiled sine-transform length (odd sequences of L = 128 .. 4096 points), as the x
+    # transform / solve along contiguous lines and as the y solve across rows
+    torch = torch_cuda()
+    kw = {"my": my} if dim == 2 else {}
+    p = workloads.small_problem(dim=dim, mx=mx, N=16, k=3, alpha=1.0, kappa=0.1, **kw)
+    ref = oracle_solution(p)
+    for prec, bar in (("fp64", 1e-10), ("mixed", 1e-8)):
+        U, st, sweeps, upd = gpu_solve(p, torch, prec, tol=bar)
+        assert st == 0, prec
+        assert rel_l2(U, ref) <= bar, (prec, sweeps)
+
+
 def test_rectangular_2d_grid():
     torch = torch_cuda()
     p = workloads.small_problem(dim=2, mx=31, my=15, N=32, k=3, alpha=1.0, kappa=0.1)
