@@ -363,7 +363,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_v0(ResidFwdArgs a) {
           ff_acc A;
           A.init(ff_split_trunc(f[t]));
           const float2 bt = __ldg(a.beta_ff + i);
-          A.fma_term(ff{bt.x, bt.y}, Mv, -1.f);
+          // (warp-uniform: beta_n = 0 beyond the first k levels of BDF-k)
+          if (bt.x != 0.f) A.fma_term(ff{bt.x, bt.y}, Mv, -1.f);
           A.sub(Avn);
           Xf[(size_t)2 * i * C] = valid ? A.value() * __ldg(a.s + i) : 0.f;
         }

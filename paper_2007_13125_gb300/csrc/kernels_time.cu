@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_upd(InvUpdArgs a) {
         su = fmaf(u.hi, u.hi, su);
       }
     }
-    block_reduce_add2((double)sc, (double)su, a.norms);
+    block_reduce_add2f(sc, su, a.norms);
     return;
   }
   for (int i = r0; i < N; i += LPR) {
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_upd(InvUpdArgs a) {
     cp_async_commit();
   }
   cp_async_wait_all();
-  block_reduce_add2((double)sc, (double)su, a.norms);
+  block_reduce_add2f(sc, su, a.norms);
 }
 
 // ---------------------------------------------------------------------------
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) k_direct_inv(DirectInvArgs<T> a) {
   load_half_spectrum(X, perm, reinterpret_cast<const V*>(a.S), N, M, C, logC, m0);
   __syncthreads();
   fft_inverse(X, C, logC, N, tw);
-  double sd = 0.0, su = 0.0;
+  T sd = T(0), su = T(0);
   for (int it = threadIdx.x; it < (N << logC); it += blockDim.x) {
     const int cc = it & (C - 1), i = it >> logC;
     const V z = X[(size_t)i * C + cc];
@@ -244,11 +244,12 @@ __global__ void __launch_bounds__(kThreads) k_direct_inv(DirectInvArgs<T> a) {
       const T un = (h ? z.y : z.x) * a.inv_s[i];
       const T d = un - a.Uold[idx];
       a.Uout[idx] = un;
-      sd += (double)(d * d);
-      su += (double)(un * un);
+      sd += d * d;
+      su += un * un;
     }
   }
-  block_reduce_add2(sd, su, a.norms);
+  if constexpr (sizeof(T) == 4) block_reduce_add2f(sd, su, a.norms);
+  else block_reduce_add2(sd, su, a.norms);
 }
 
 // ---------------------------------------------------------------------------
@@ -400,7 +401,10 @@ __global__ void k_rhs(RhsArgs a) {
     for (int b = 0; b < B; ++b) {
       const int i = ib + b;
       if (i >= i1) break;
-      double F = fma(a.beta[i], bv, f[b]);
+      // (beta_n = 0 beyond the first k levels of BDF-k: no FP64 arithmetic there, the FP64
+      // pipe runs at ~1/70 of the FP32 rate; the test is on the bit pattern, an integer compare)
+      const double bn = a.beta[i];
+      double F = __double_as_longlong(bn) != 0 ? fma(bn, bv, f[b]) : f[b];
       if (i < a.k - 1) {
         F += a.a[i] * (a.fd[m] - Av);
         for (int l = 1; l <= a.k - 2; ++l) F += a.bt[l][i] * a.fd[(size_t)l * a.M + m];

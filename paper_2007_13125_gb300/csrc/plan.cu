@@ -461,7 +461,8 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   double cs = 0.0;
   for (int i = 0; i < N; ++i) {
     cs += p->omega[i];
-    beta[i] = ta * cs;
+    // BDF-k (alpha = 1): sum_{j<=i} omega_j = delta_k(1) = 0 exactly once i >= k
+    beta[i] = (p->alpha == 1.0 && i >= p->k) ? 0.0 : ta * cs;
   }
   if ((s = upload(p, &p->beta, beta)) != PINT_OK) return bail(s);
   if (p->prec == PINT_MIXED) {

@@ -16,6 +16,33 @@ __device__ __forceinline__ ff ldff(const float* hi, const float* lo, size_t idx)
   return r;
 }
 
+// out[0] += sum of a, out[1] += sum of b over the block. The float version adds in FP32 within
+// the block and converts once per block (FP64 instructions run at ~1/70 of the FP32 rate here);
+// it serves the stopping test's norms, where a relative error of 1e-5 is immaterial.
+__device__ __forceinline__ void block_reduce_add2f(float a, float b, double* out) {
+  __shared__ float redf[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { redf[0][w] = a; redf[1][w] = b; }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    a = l < nw ? redf[0][l] : 0.f;
+    b = l < nw ? redf[1][l] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (l == 0) {
+      atomicAdd(out, (double)a);
+      atomicAdd(out + 1, (double)b);
+    }
+  }
+}
+
 __device__ __forceinline__ void block_reduce_add2(double a, double b, double* out) {
   __shared__ double red[2][32];
   for (int o = 16; o > 0; o >>= 1) {
