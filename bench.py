@@ -72,11 +72,12 @@ def algo_bytes(name: str, N: int, M: int) -> float:
 # of the workload (`ncu --set full` of `bench.py --once mixed`), valid while the kernel's
 # source is unchanged (sha1 of its translation unit)
 NCU_TRAFFIC = {
-    "resid_fwd_ff": (317.30e6, "kernels_resid.cu", "14925015af74420b5b84e552eca4f6cd526b8b3c"),
-    "resid_v0_ff": (168.34e6, "kernels_resid.cu", "14925015af74420b5b84e552eca4f6cd526b8b3c"),
-    "inv_update_v0_ff": (142.29e6, "kernels_time.cu", "a6f669b407b4ea149940ecaf393e8634dda1d6d6"),
-    "dst_f32": (76.13e6, "kernels_space.cu", "3c527803de8656af72e4ff171420e7c68d2f8b5f"),
-    "axis_solve_f32": (78.56e6, "kernels_space.cu", "3c527803de8656af72e4ff171420e7c68d2f8b5f"),
+    "resid_fwd_ff": (317.58e6, "kernels_resid.cu", "b48ed6cac8d6424f3c0746711fca42871516c65a"),
+    "resid_v0_ff": (167.32e6, "kernels_resid.cu", "b48ed6cac8d6424f3c0746711fca42871516c65a"),
+    "inv_update_v0_ff": (141.93e6, "kernels_time.cu", "0bc8ac29227b21a86fd09c32fa8a66a830a2dfcc"),
+    "inv_update_ff": (277.50e6, "kernels_time.cu", "0bc8ac29227b21a86fd09c32fa8a66a830a2dfcc"),
+    "dst_f32": (76.16e6, "kernels_space.cu", "481cdea001d1c5629944d60849106b33e388ead1"),
+    "axis_solve_f32": (78.60e6, "kernels_space.cu", "481cdea001d1c5629944d60849106b33e388ead1"),
 }
 
 
