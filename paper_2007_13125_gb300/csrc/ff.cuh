@@ -109,6 +109,62 @@ __device__ __forceinline__ ffc cmulc(ffc a, ffc b) {  // a * conj(b)
   return ffc_make(ff_add(ff_mul(ar, br), ff_mul(ai, bi)), ff_sub(ff_mul(ai, br), ff_mul(ar, bi)));
 }
 
+// Lazy complex double-float for FFT butterflies (the CQ history's transforms): the same
+// unevaluated sums hi + lo, but sums and products skip the renormalisation, so within one FFT
+// pass a low part may reach a few ulp of its high part. Every rounding error stays of order
+// 2^-48 of the magnitudes entering the operation (the norm-wise error model of an FFT); the pass
+// renormalises each value once when it stores it (fft_store, with an exact two_sum).
+struct ffz { float rh, rl, ih, il; };
+__device__ __forceinline__ void lazy_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  float e;
+  two_sum(ah, bh, sh, e);
+  sl = __fadd_rn(e, __fadd_rn(al, bl));
+}
+__device__ __forceinline__ void lazy_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+  ph = __fmul_rn(ah, bh);
+  pl = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fmaf_rn(ah, bh, -ph)));
+}
+__device__ __forceinline__ ffz cadd(ffz a, ffz b) {
+  ffz r;
+  lazy_add(a.rh, a.rl, b.rh, b.rl, r.rh, r.rl);
+  lazy_add(a.ih, a.il, b.ih, b.il, r.ih, r.il);
+  return r;
+}
+__device__ __forceinline__ ffz csub(ffz a, ffz b) {
+  ffz r;
+  lazy_add(a.rh, a.rl, -b.rh, -b.rl, r.rh, r.rl);
+  lazy_add(a.ih, a.il, -b.ih, -b.il, r.ih, r.il);
+  return r;
+}
+__device__ __forceinline__ ffz cmul(ffz a, ffz b) {
+  float p1h, p1l, p2h, p2l, p3h, p3l, p4h, p4l;
+  lazy_mul(a.rh, a.rl, b.rh, b.rl, p1h, p1l);  // ar br
+  lazy_mul(a.ih, a.il, b.ih, b.il, p2h, p2l);  // ai bi
+  lazy_mul(a.rh, a.rl, b.ih, b.il, p3h, p3l);  // ar bi
+  lazy_mul(a.ih, a.il, b.rh, b.rl, p4h, p4l);  // ai br
+  ffz r;
+  lazy_add(p1h, p1l, -p2h, -p2l, r.rh, r.rl);
+  lazy_add(p3h, p3l, p4h, p4l, r.ih, r.il);
+  return r;
+}
+__device__ __forceinline__ ffz cmulc(ffz a, ffz b) {  // a * conj(b)
+  float p1h, p1l, p2h, p2l, p3h, p3l, p4h, p4l;
+  lazy_mul(a.rh, a.rl, b.rh, b.rl, p1h, p1l);  // ar br
+  lazy_mul(a.ih, a.il, b.ih, b.il, p2h, p2l);  // ai bi
+  lazy_mul(a.ih, a.il, b.rh, b.rl, p3h, p3l);  // ai br
+  lazy_mul(a.rh, a.rl, b.ih, b.il, p4h, p4l);  // ar bi
+  ffz r;
+  lazy_add(p1h, p1l, p2h, p2l, r.rh, r.rl);
+  lazy_add(p3h, p3l, -p4h, -p4l, r.ih, r.il);
+  return r;
+}
+__device__ __forceinline__ ffz fft_store(ffz v) {
+  ffz r;
+  two_sum(v.rh, v.rl, r.rh, r.rl);
+  two_sum(v.ih, v.il, r.ih, r.il);
+  return r;
+}
+
 // Split a double into hi + lo with integer operations only. On GB300 every FP64<->FP32
 // conversion runs at the FP64 rate (~1/70 of FP32), so the bit patterns are taken apart
 // directly: hi = x rounded to 24 significant bits (nearest, ties to even), exact as a float;

@@ -88,6 +88,24 @@ __device__ __forceinline__ ffc twid16(ffc v) {
   }
 }
 
+// ... and for the lazy double-float complex type (ffz, ff.cuh)
+template <int M, int DIR>
+__device__ __forceinline__ ffz twid16(ffz v) {
+  if constexpr (M == 0) {
+    return v;
+  } else if constexpr (M == 4) {
+    return DIR < 0 ? ffz{v.ih, v.il, -v.rh, -v.rl} : ffz{-v.ih, -v.il, v.rh, v.rl};
+  } else {
+    constexpr double c = cos16(M), s = DIR * sin16(M);
+    constexpr float ch = (float)c, sh = (float)s;
+    constexpr float cl = (float)(c - (double)ch), sl = (float)(s - (double)sh);
+    return cmul(v, ffz{ch, cl, sh, sl});
+  }
+}
+
+// value as a pass stores it: unchanged, except for types that renormalise there (ffz)
+template <typename V> __device__ __forceinline__ V fft_store(V v) { return v; }
+
 __host__ __device__ constexpr int ilog2c(int r) { return r <= 1 ? 0 : 1 + ilog2c(r >> 1); }
 // the same for values known only at run time (ilog2c recurses when its argument is not a constant)
 __host__ __device__ inline int ilog2r(int r) {
@@ -208,7 +226,7 @@ __device__ __forceinline__ void fft_pass(V* X, int ld, int logC, int logL, int l
       dft_reg<R, 1>(x);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) X[(base + (r << logS)) * ld + c] = x[r];
+    for (int r = 0; r < R; ++r) X[(base + (r << logS)) * ld + c] = fft_store(x[r]);
   }
 }
 

@@ -301,23 +301,24 @@ __global__ void __launch_bounds__(kThreads) k_toeplitz(ToepArgs a) {
 // ---------------------------------------------------------------------------
 // MIXED CQ history y = tau^-alpha (omega * U) in double-float: the same circulant embedding
 // with 2N-point FFTs whose butterflies are error-free-transformation arithmetic on the FP32
-// pipes (~48-bit significand; GB300's FP64 pipe is ~70x slower than its FP32 pipes).
+// pipes (~48-bit significand; GB300's FP64 pipe is ~70x slower than its FP32 pipes), in the
+// lazy form (ffz: renormalised once per pass, when a value is stored).
 // ---------------------------------------------------------------------------
 size_t toep_ff_smem(int N, int C) { return time_tile_bytes<ffc>(2 * N, C); }
 
 __global__ void __launch_bounds__(kThreads) k_toeplitz_ff(ToepFFArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = a.N, C = a.C, M = a.M, L = 2 * a.N, logC = a.logC;
-  ffc* X = reinterpret_cast<ffc*>(smraw);
-  ffc* tw = X + (size_t)L * C;
+  ffz* X = reinterpret_cast<ffz*>(smraw);
+  ffz* tw = X + (size_t)L * C;
   unsigned short* perm = reinterpret_cast<unsigned short*>(tw + L);
-  const ffc* gtw = reinterpret_cast<const ffc*>(a.tw);
+  const ffz* gtw = reinterpret_cast<const ffz*>(a.tw);
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = gtw[i];
   (void)perm;
   const int m0 = blockIdx.x * 2 * C;
   for (int it = threadIdx.x; it < (L << logC); it += blockDim.x) {
     const int cc = it & (C - 1), i = it >> logC;
-    ffc v = {0.f, 0.f, 0.f, 0.f};
+    ffz v = {0.f, 0.f, 0.f, 0.f};
     if (i < N) {
       const int ma = m0 + cc, mb = m0 + C + cc;
       const size_t row = (size_t)i * M;
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_toeplitz_ff(ToepFFArgs a) {
   }
   __syncthreads();
   fft_forward<kToepFFMaxLog>(X, C, logC, L, tw);
-  const ffc* what = reinterpret_cast<const ffc*>(a.what);
+  const ffz* what = reinterpret_cast<const ffz*>(a.what);
   for (int it = threadIdx.x; it < (L << logC); it += blockDim.x) {
     const int cc = it & (C - 1), p = it >> logC;
     X[(size_t)p * C + cc] = cmul(X[(size_t)p * C + cc], what[p]);
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) k_toeplitz_ff(ToepFFArgs a) {
   fft_inverse<kToepFFMaxLog>(X, C, logC, L, tw);
   for (int it = threadIdx.x; it < (N << logC); it += blockDim.x) {
     const int cc = it & (C - 1), i = it >> logC;
-    const ffc z = X[(size_t)i * C + cc];
+    const ffz z = X[(size_t)i * C + cc];
     const int ma = m0 + cc, mb = m0 + C + cc;
     const size_t row = (size_t)i * M;
     if (ma < M) { a.yhi[row + ma] = z.rh; a.ylo[row + ma] = z.rl; }
