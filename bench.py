@@ -197,6 +197,27 @@ NL_NEWTON_TOL, NL_TOL = 1e-8, 1e-10
 WORKLOAD = "heat2d"
 
 
+def max_over_ranks(pg, ms: float, device=None) -> float:
+    """The job's time for a step: the slowest rank's (all_reduce MAX); unchanged on one rank."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_units(pg, units: float, device=None) -> float:
+    """Units (space-time DOF) that all ranks processed (all_reduce SUM): the ranks are replicas
+    with their own problems, so the job's work grows with the rank count (weak scaling)."""
+    if pg is None:
+        return units
+    import torch
+    t = torch.tensor([units], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
 def problem_for_rank(rank: int):
     # weak scaling: every rank solves its own instance (replicas; no exchange step)
     return (NL_WORKLOADS if WORKLOAD in NL_WORKLOADS else WORKLOADS)[WORKLOAD]()
@@ -437,10 +458,7 @@ def run_nl(args) -> int:
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1) / steps
-        if pg is not None:
-            t = torch.tensor([ms], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(pg, ms, dev)
         return ms, [a.elapsed_time(b) for a, b in lat]
 
     clk = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
@@ -518,7 +536,7 @@ def run_nl(args) -> int:
             cpu = oracle_sample(p)
         except Exception as e:
             cpu = {"error": str(e)}
-    dof_total = p.dof * world
+    dof_total = job_units(pg, p.dof, dev)
     line = {
         "metric": METRIC, "value": dof_total / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -671,10 +689,7 @@ def main():
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
-        if pg is not None:
-            t = torch.tensor([ms], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(pg, ms, dev)
         lats = [a.elapsed_time(b) for a, b in lat]
         return ms / steps, lats
 
@@ -770,10 +785,7 @@ def main():
     e1.record(stream)
     barrier()
     ms_e2e = e0.elapsed_time(e1) / ke
-    if pg is not None:
-        t = torch.tensor([ms_e2e], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(pg, ms_e2e, dev)
     h2d = (v_h.size + f_h.size + fd_h.size) * 8
     d2h = N * M * 8
     # the last solution that came back agrees with the device result, and that solve converged
@@ -806,8 +818,7 @@ def main():
                     "peak_source": peak_src + " hbm_gbs (STREAM-style copy)",
                     "algo_bytes_per_launch": algo_bytes(name, N, M)}
 
-    n_world = world
-    dof_total = p.dof * n_world
+    dof_total = job_units(pg, p.dof, dev)
     value = dof_total / (ms_mixed * 1e-3)
     lat_sorted = sorted(lat_mixed)
     p50 = float(np.percentile(lat_sorted, 50)) if lat_sorted else None

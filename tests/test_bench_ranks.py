@@ -1,0 +1,83 @@
+"""The multi-rank path of bench.py on the CPU. Under torchrun the bench runs one process per GPU;
+the ranks are replicas (each solves its own instance of the workload, no data-path collective),
+the job's time is the slowest rank's and its work the sum over ranks. That host-side logic is
+checked here with two gloo ranks launched the way torchrun launches them (RANK, WORLD_SIZE,
+MASTER_ADDR, MASTER_PORT in the environment); no GPU is involved."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+RANK_SCRIPT = r"""
+import json, os, sys
+sys.path.insert(0, os.environ["BENCH_ROOT"])
+import torch.distributed as dist
+import bench
+rank, world, local = bench.dist_env()
+dist.init_process_group("gloo", rank=rank, world_size=world)
+try:
+    ms = bench.max_over_ranks(dist, 1.0 + 2.0 * rank)        # rank 0: 1 ms, rank 1: 3 ms
+    units = bench.job_units(dist, 100.0 + rank)             # 100 and 101 DOF
+    p = bench.problem_for_rank(rank)
+    print(json.dumps({"rank": rank, "world": world, "local": local, "ms": ms, "units": units,
+                      "N": p.N, "M": p.M, "k": p.k}), flush=True)
+finally:
+    dist.destroy_process_group()
+"""
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _env(rank, world, port):
+    env = dict(os.environ)
+    env.update(RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1",
+               MASTER_PORT=str(port), BENCH_ROOT=ROOT, CUDA_VISIBLE_DEVICES="")
+    return env
+
+
+def test_two_gloo_ranks_reduce_like_the_bench():
+    pytest.importorskip("torch.distributed")
+    port = _free_port()
+    procs = [subprocess.Popen([sys.executable, "-c", RANK_SCRIPT], env=_env(r, 2, port), cwd=ROOT,
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True) for r in range(2)]
+    outs = []
+    for pr in procs:
+        try:
+            out, err = pr.communicate(timeout=180)
+        except subprocess.TimeoutExpired:
+            for q in procs:
+                q.kill()
+            raise
+        assert pr.returncode == 0, err[-2000:]
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    for r, o in enumerate(outs):
+        assert (o["rank"], o["world"], o["local"]) == (r, 2, r)
+        assert o["ms"] == 3.0            # the slowest rank's time, on every rank
+        assert o["units"] == 201.0       # the work of both ranks
+    # replicas: every rank solves an instance of the same shape
+    assert (outs[0]["N"], outs[0]["M"], outs[0]["k"]) == (outs[1]["N"], outs[1]["M"], outs[1]["k"])
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(None, 2.5) == 2.5
+    assert bench.job_units(None, 7.0) == 7.0
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    # under torchrun the oracle arm runs and prints on rank 0; the other ranks exit 0 without work
+    env = _env(1, 2, _free_port())
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=180)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""
