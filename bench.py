@@ -69,21 +69,23 @@ def algo_bytes(name: str, N: int, M: int) -> float:
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
-# of the workload (`ncu --set full` of `bench.py --once mixed`), valid while the kernel's
-# source is unchanged (sha1 of its translation unit)
+# of a workload (`ncu --set full` of `bench.py --once mixed`), per workload and kernel, valid while
+# the kernel's source is unchanged (sha1 of its translation unit); other workloads report null
 NCU_TRAFFIC = {
-    "resid_fwd_ff": (317.58e6, "kernels_resid.cu", "b48ed6cac8d6424f3c0746711fca42871516c65a"),
-    "resid_v0_ff": (167.32e6, "kernels_resid.cu", "b48ed6cac8d6424f3c0746711fca42871516c65a"),
-    "inv_update_v0_ff": (141.93e6, "kernels_time.cu", "0bc8ac29227b21a86fd09c32fa8a66a830a2dfcc"),
-    "inv_update_ff": (277.50e6, "kernels_time.cu", "0bc8ac29227b21a86fd09c32fa8a66a830a2dfcc"),
-    "dst_f32": (76.16e6, "kernels_space.cu", "481cdea001d1c5629944d60849106b33e388ead1"),
-    "axis_solve_f32": (78.60e6, "kernels_space.cu", "481cdea001d1c5629944d60849106b33e388ead1"),
+    "heat2d_255x255_N256_bdf4": {
+        "resid_fwd_ff": (316.93e6, "kernels_resid.cu", "b48ed6cac8d6424f3c0746711fca42871516c65a"),
+        "resid_v0_ff": (167.08e6, "kernels_resid.cu", "b48ed6cac8d6424f3c0746711fca42871516c65a"),
+        "inv_update_v0_ff": (141.95e6, "kernels_time.cu", "5394d4dd1afe55ae78ee7de2ccad83cad9d216cf"),
+        "inv_update_ff": (277.44e6, "kernels_time.cu", "5394d4dd1afe55ae78ee7de2ccad83cad9d216cf"),
+        "dst_f32": (76.13e6, "kernels_space.cu", "481cdea001d1c5629944d60849106b33e388ead1"),
+        "axis_solve_f32": (78.62e6, "kernels_space.cu", "481cdea001d1c5629944d60849106b33e388ead1"),
+    },
 }
 
 
-def traffic_for(name: str):
+def traffic_for(name: str, workload: str):
     import hashlib
-    ent = NCU_TRAFFIC.get(name)
+    ent = NCU_TRAFFIC.get(workload, {}).get(name)
     if not ent:
         return None
     path = os.path.join(ROOT, "paper_2007_13125_gb300", "csrc", ent[1])
@@ -526,7 +528,7 @@ def run_nl(args) -> int:
         name, (n, tot) = max(kstats.items(), key=lambda kv: kv[1][1])
         ach = algo_bytes(name, N, M) / (tot / n * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                    "frac": round(ach / hbm_peak, 4), "traffic": traffic_for(name),
+                    "frac": round(ach / hbm_peak, 4), "traffic": traffic_for(name, p.name),
                     "peak_source": peak_src + " hbm_gbs (STREAM-style copy)",
                     "algo_bytes_per_launch": algo_bytes(name, N, M),
                     "note": f"1D problem of {N * M * 8 / 1e6:.1f} MB per FP64 array: latency-bound, no bandwidth claim"}
@@ -814,7 +816,7 @@ def main():
         avg_s = tot / n * 1e-3
         ach = algo_bytes(name, N, M) / avg_s / 1e9
         roofline = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": hbm_peak,
-                    "unit": "GB/s", "frac": round(ach / hbm_peak, 3), "traffic": traffic_for(name),
+                    "unit": "GB/s", "frac": round(ach / hbm_peak, 3), "traffic": traffic_for(name, p.name),
                     "peak_source": peak_src + " hbm_gbs (STREAM-style copy)",
                     "algo_bytes_per_launch": algo_bytes(name, N, M)}
 

@@ -81,3 +81,17 @@ def test_reference_arm_runs_on_rank_zero_only():
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=180)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_stored_ncu_traffic_applies_to_its_own_workload_only():
+    # the DRAM traffic bench.py reports beside a roofline comes from an ncu capture of one
+    # workload; another workload's launch of the same kernel moves different bytes
+    sys.path.insert(0, ROOT)
+    import bench
+    captured = "heat2d_255x255_N256_bdf4"
+    assert captured in bench.NCU_TRAFFIC
+    for name, (value, src, _sha) in bench.NCU_TRAFFIC[captured].items():
+        assert bench.traffic_for(name, captured) in (None, value)   # null once the source changed
+        assert bench.traffic_for(name, "periodic2d_256x256_N256_bdf4") is None
+        assert bench.traffic_for(name, "fem_example1_M1023_N128_k3") is None
+    assert bench.traffic_for("no_such_kernel", captured) is None
