@@ -5,8 +5,11 @@
  *
  * Problem (Sec. 1, eq. (1.1) and eq. (1.4)):  D_t^alpha u + A u = f on (0, T], u(0) = v, with
  * D_t^alpha the first derivative (alpha = 1) or the Caputo derivative (0 < alpha < 1), and A the
- * finite-difference Dirichlet Laplacian on the unit interval (dim = 1) or unit square (dim = 2):
- * interior points only, h_x = 1/(mx+1), h_y = 1/(my+1), 3-point / 5-point stencil.
+ * finite-difference Dirichlet Laplacian on the unit interval (dim = 1), square (dim = 2) or cube
+ * (dim = 3): interior points only, h_x = 1/(mx+1), h_y = 1/(my+1), h_z = 1/(mz+1), 3/5/7-point
+ * stencil. pint_plan_desc also selects periodic boundaries (the remark of Sec. 2.2) and P1 finite
+ * elements in 1D (the discretisation of Sec. 4), and a semilinear term g(u) is handled by
+ * Algorithm 3 (pint_nl_solve).
  *
  * Discretisation: uniform steps t_n = n tau, n = 1..N; corrected BDF-k (Sec. 2.1, eq. (2.1)) or
  * corrected CQ-BDF-k (Sec. 3.1, eq. (3.7)) with the starting-step constants of Table 1. The
@@ -32,8 +35,9 @@
  * leaves a message retrievable with pint_last_error() (thread-local). Invalid arguments return
  * PINT_EINVAL before anything is enqueued. A plan is not thread-safe; use one per host thread.
  *
- * Supported sizes: N a power of two, 8 <= N <= 4096 (CQ: N <= 2048); mx + 1 and my + 1 powers
- * of two, 3 <= mx, my <= 2047 (the sine transforms run as FFTs of length 2(m+1)).
+ * Supported sizes: N a power of two, 8 <= N <= 4096 (CQ: N <= 2048); mx + 1, my + 1, mz + 1
+ * powers of two, 3 <= mx, my, mz <= 2047 (the sine transforms run as FFTs of length 2(m+1));
+ * periodic axes take m points, m a power of two, 8 <= m <= 4096.
  */
 #ifndef PINT_H
 #define PINT_H
