@@ -27,6 +27,7 @@ SPACES = {"fd": PINT_SPACE_FD, "fem": PINT_SPACE_FEM_P1, "periodic": PINT_SPACE_
 
 
 class PintError(RuntimeError):
+    """A pint_status other than PINT_OK, with the library's message (pint_last_error)."""
     def __init__(self, status: int, msg: str):
         super().__init__(f"{status_string(status)}: {msg}")
         self.status = status
@@ -151,6 +152,7 @@ def header_functions() -> list[str]:
 
 
 def status_string(s: int) -> str:
+    """Name of a pint_status (pint_status_string)."""
     try:
         return lib().pint_status_string(s).decode()
     except Exception:  # library not loadable: still format the number
@@ -158,10 +160,12 @@ def status_string(s: int) -> str:
 
 
 def last_error() -> str:
+    """Message of the calling thread's last failed call (pint_last_error)."""
     return lib().pint_last_error().decode()
 
 
 def check(status: int):
+    """Raise PintError for a status other than PINT_OK."""
     if status != PINT_OK:
         raise PintError(status, last_error())
 
@@ -186,12 +190,14 @@ def _stream(stream):
 
 # ---- host-only queries ----
 def time_weights(k: int, alpha: float, n: int) -> np.ndarray:
+    """omega_0..omega_{n-1} of BDF-k (alpha = 1) or CQ-BDF-k (pint_time_weights)."""
     out = np.zeros(n)
     check(lib().pint_time_weights(k, alpha, n, out.ctypes.data_as(ctypes.POINTER(_D))))
     return out
 
 
 def correction_coefficients(k: int):
+    """Table 1 for BDF-k: (a_n [5], b_{l,n} [4][5]) (pint_correction_coefficients)."""
     a = np.zeros(5)
     b = np.zeros(20)
     check(lib().pint_correction_coefficients(k, a.ctypes.data_as(ctypes.POINTER(_D)),
@@ -200,6 +206,7 @@ def correction_coefficients(k: int):
 
 
 def circulant_eigenvalues(k: int, alpha: float, kappa: float, N: int, eig: int = PINT_EIG_TRUNC_DFT):
+    """Eigenvalues g_0..g_{N-1} of B_k(kappa) (pint_circulant_eigenvalues), complex."""
     re_, im_ = np.zeros(N), np.zeros(N)
     check(lib().pint_circulant_eigenvalues(k, alpha, kappa, N, eig,
                                            re_.ctypes.data_as(ctypes.POINTER(_D)),
@@ -214,10 +221,12 @@ def kappa_solve_noalloc(k, kappa, tau, N, mx, R, Q, stream=None):
 
 
 def set_profiling(on: bool):
+    """Launch sweeps one by one with per-kernel CUDA-event timing (pint_set_profiling)."""
     check(lib().pint_set_profiling(1 if on else 0))
 
 
 def kernel_stats(reset: bool = True) -> dict:
+    """{kernel: (launches, total ms)} timed while profiling is on (pint_kernel_stats)."""
     n = 64
     names = (ctypes.c_char_p * n)()
     launches = (_I * n)()
@@ -246,10 +255,12 @@ class Plan:
 
     @classmethod
     def for_problem(cls, p, precision="mixed", eig=PINT_EIG_TRUNC_DFT, ysolve=0):
+        """Plan for a workloads.Problem (its k, alpha, kappa, tau, N, grid and space)."""
         return cls(p.k, p.alpha, p.kappa, p.tau, p.N, p.dim, p.mx, p.my, precision, eig, ysolve,
                    getattr(p, "space", "fd"), getattr(p, "mz", 1))
 
     def close(self):
+        """Destroy the plan (pint_plan_destroy); idempotent."""
         if self.handle:
             lib().pint_plan_destroy(self.handle)
             self.handle = None
@@ -267,9 +278,11 @@ class Plan:
             pass
 
     def workspace_bytes(self) -> int:
+        """Device bytes the plan owns (pint_plan_workspace_bytes)."""
         return int(lib().pint_plan_workspace_bytes(self.handle))
 
     def form_rhs(self, v, f, fderiv, Fhat, stream=None):
+        """F_hat [N][M] from v [M], f [N][M] and the derivatives of f at 0 (pint_form_rhs)."""
         check(lib().pint_form_rhs(self.handle, _ptr(v), _ptr(f), _ptr(fderiv) if fderiv is not None and fderiv.numel() else None,
                                   _ptr(Fhat), _stream(stream)))
 
@@ -278,15 +291,18 @@ class Plan:
         check(lib().pint_form_rhs_window(self.handle, _ptr(f), _ptr(U_prev), _ptr(Fhat), _stream(stream)))
 
     def initial_guess(self, v, U, stream=None):
+        """U_0^n = v for every level (pint_initial_guess)."""
         check(lib().pint_initial_guess(self.handle, _ptr(v), _ptr(U), _stream(stream)))
 
     def wr_sweep(self, Fhat, U_prev, U_next, stream=None, want_update=True) -> float | None:
+        """One WR sweep U_prev -> U_next (pint_wr_sweep); returns ||U_next - U_prev|| / ||U_next||."""
         upd = _D(0.0)
         check(lib().pint_wr_sweep(self.handle, _ptr(Fhat), _ptr(U_prev), _ptr(U_next),
                                   ctypes.byref(upd) if want_update else None, _stream(stream)))
         return upd.value if want_update else None
 
     def solve(self, Fhat, U, tol=1e-10, max_sweeps=50, stream=None, raise_on_notconv=True):
+        """Sweeps from the guess in U until the stopping rule meets tol (pint_solve): (status, sweeps, update)."""
         sweeps = _I(0)
         upd = _D(0.0)
         st = lib().pint_solve(self.handle, _ptr(Fhat), _ptr(U), float(tol), int(max_sweeps),
@@ -306,6 +322,7 @@ class Plan:
         return st, sweeps.value, upd.value
 
     def solve_v_async(self, Fhat, v, U, tol=1e-10, max_sweeps=50, stream=None):
+        """pint_solve_v enqueued on `stream` without waiting (pint_solve_v_async); see solve_result."""
         check(lib().pint_solve_v_async(self.handle, _ptr(Fhat), _ptr(v), _ptr(U), float(tol), int(max_sweeps),
                                        _stream(stream)))
 
@@ -387,6 +404,7 @@ class Server:
         self.handle = h
 
     def close(self):
+        """Destroy the server, cancelling queued requests (pint_server_destroy); idempotent."""
         if self.handle:
             lib().pint_server_destroy(self.handle)
             self.handle = None
@@ -422,12 +440,15 @@ class Server:
         return int(t.value)
 
     def poll(self, ticket: int, out: np.ndarray | None, timeout_us: int = 0):
+        """Wait up to timeout_us for a request (pint_poll): (status, info); on PINT_OK the solution
+        is copied into `out` (host float64 [N][M]) and the request is released."""
         info = _Info()
         st = lib().pint_poll(self.handle, ctypes.c_uint64(ticket), int(timeout_us),
                              out.ctypes.data_as(_P) if out is not None else None, ctypes.byref(info))
         return st, info
 
     def stats(self) -> dict:
+        """Server counters (pint_server_stats)."""
         v = (_D * 8)()
         check(lib().pint_server_stats(self.handle, v))
         keys = ["completed", "active", "queued", "hbm_in_use", "dof_done", "sweeps_done", "busy_s", "peak_hbm"]
