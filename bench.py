@@ -64,6 +64,7 @@ def algo_bytes(name: str, N: int, M: int) -> float:
         "nl_linearise": 8 * NM,                 # read U
         "nl_rhs": 32 * NM,                      # read F_hat, U; write the linearised F_hat, U_{l-1}
         "nl_norms": 16 * NM,                    # read U, U_{l-1}
+        "small_solve_ff": 16 * NM,              # one-CTA solve: read F_hat, write U (the rest stays on chip)
     }
     return float(table.get(name, 0.0))
 

@@ -206,6 +206,29 @@ struct SolveCtl {
   int max_sweeps, m, done, pad;
 };
 
+// Whole MIXED solve of a small 1D problem in one CTA (kernels_small.cu): finite differences,
+// Dirichlet, BDF-k, no reaction term; tables as for the multi-kernel sweep (float).
+constexpr int kSmallThreads = 512;
+struct SmallArgs {
+  const double* F;        // F_hat [N][M]
+  double* U;              // in: the guess (when v is null); out: the solution
+  const double* v;        // non-null: start from U_0^n = v
+  const float2* tw_t;     // [N] time twiddles
+  const float* s;         // [N] kappa^{n/N}
+  const float* inv_s;     // [N] kappa^{-n/N} / N
+  const float2* sigma;    // [N/2+1] g_j tau^-alpha
+  const float* lam;       // [M] eigenvalues of the stencil on the sine modes
+  const float2* tw_x;     // [L] twiddles of the odd extension, L = 2(M+1)
+  float c_hi[kMaxK + 1], c_lo[kMaxK + 1];  // c_0 = omega_0 / tau + 2/h^2, c_j = omega_j / tau
+  float gx;               // 1/h^2 (a power of two)
+  int k, N, M, Ct, logCt, L, Cs, logCs;    // Ct = (M+1)/2 time-tile columns, Cs lines per batch
+  double tol, q_floor;
+  int max_sweeps;
+  SolveCtl* ctl;          // written at the end: sweeps, last update, done
+};
+size_t small_smem(int N, int M, int Ct, int L, int Cs);
+cudaError_t launch_small_solve(const SmallArgs& a, cudaStream_t st);
+
 // Stop after sweep m? upd = ||U_m - U_{m-1}|| / ||U_m||, prev = upd_{m-1}. For m >= 2 the
 // contraction is estimated as q = max(upd / prev, q_floor) (q_floor: rounding floor of the inner
 // solves) and the error as upd q / (1 - q).

@@ -103,6 +103,10 @@ struct pint_plan_s {
   // reaction term (1D, Dirichlet): the spatial operator A + w diag(c) of the linear solves
   // (pint_set_reaction; the linearised operator of Algorithm 3)
   bool react_on = false;
+  // small 1D problems: the whole MIXED solve in one CTA (kernels_small.cu); time-tile columns and
+  // spatial lines per batch of that kernel
+  bool small = false;
+  int small_Ct = 0, small_Cs = 0;
   double* react = nullptr;          // [M] w c_i
   void* tri_ip = nullptr;           // [N/2+1][M] T2: inverse pivots of the shifted systems
   void* tri_cp = nullptr;           // [N/2+1][M] T2: eliminated super-diagonal
