@@ -197,7 +197,10 @@ pint_status pint_wr_sweep(pint_plan plan, const double* Fhat, const double* U_pr
  * while-node repeats the sweep until a device-side check of the fused norms stops it); the graph
  * is built on first use of an (Fhat, U, tol, max_sweeps) combination and reused for it (a plan
  * keeps the four most recently used, so alternating buffer sets do not rebuild). The call waits
- * for `stream` once. With per-kernel profiling on, sweeps are launched one by one instead. */
+ * for `stream` once. With per-kernel profiling on, sweeps are launched one by one instead.
+ * Small 1D problems (MIXED, finite differences, Dirichlet, BDF-k, N * M <= 4096) run the whole
+ * solve, every sweep and the same stopping rule (evaluated in FP32), as one kernel in one CTA,
+ * in either mode (the profile then lists "small_solve_ff"). */
 pint_status pint_solve(pint_plan plan, const double* Fhat, double* U, double tol, int max_sweeps,
                        int* sweeps_out, double* upd_rel_out, void* stream);
 
