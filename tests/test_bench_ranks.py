@@ -95,3 +95,18 @@ def test_stored_ncu_traffic_applies_to_its_own_workload_only():
         assert bench.traffic_for(name, "periodic2d_256x256_N256_bdf4") is None
         assert bench.traffic_for(name, "fem_example1_M1023_N128_k3") is None
     assert bench.traffic_for("no_such_kernel", captured) is None
+
+
+def test_oracle_sample_reports_the_error_of_given_solutions():
+    # the bench line's accuracy figure: each GPU solution against the oracle's levels
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads
+    from oracle import grid, sequential
+    p = workloads.c1_heat1d()
+    ref = sequential.solve_sequential(p.k, p.alpha, p.tau, grid.operator(p), p.v, p.f(), p.fderiv())
+    info = bench.oracle_sample(p, budget_s=1.0, results={"same": ref, "off": ref * (1 + 1e-9)})
+    n_s = info["levels_compared"]
+    assert 8 <= n_s <= p.N
+    assert info["rel_err_vs_oracle"]["same"] == 0.0
+    assert abs(info["rel_err_vs_oracle"]["off"] - 1e-9) <= 1e-12
