@@ -11,8 +11,8 @@
 //      (point m in complex column m mod Ct, real part for m < Ct, imaginary part otherwise);
 //   2. forward FFT along time; the two half spectra of each column separated;
 //   3. for each frequency j <= N/2 (in batches of Cs lines, Cs dividing N/2, and the line j = N/2
-//      alone): sine transform of the odd extension,
-//      divide by 2(M+1) (sigma_j + lambda_p), inverse transform (eq. of the 1D shifted systems);
+//      alone): sine transform of the odd extension, divide by 2(M+1) (sigma_j + lambda_p), inverse
+//      transform -- the shifted systems (sigma_j + A_h) q_j = h_j of Algorithm 1, step 2;
 //   4. the spectra recombined, inverse FFT along time, unscaled by kappa^{-n/N}/N;
 //   5. U += c in double-float, the norms of c and U (FP32 partials), the stopping rule.
 #include "ff.cuh"
