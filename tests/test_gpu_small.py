@@ -128,3 +128,30 @@ def test_small_cases_take_the_one_cta_solve(case):
         finally:
             pint.set_profiling(False)
     assert set(stats) == {"small_solve_ff"}, (case, stats)
+
+
+def test_batch_mixing_one_cta_and_multi_kernel_solves():
+    # one graph holding both kinds of solve: the small problems' single kernels and the larger
+    # problems' while-loops of sweeps
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan, pint
+    probs = [workloads.small_problem(dim=1, mx=31, N=32, k=2, alpha=1.0, kappa=0.1, seed=1),
+             workloads.small_problem(dim=2, mx=31, N=32, k=3, alpha=1.0, kappa=0.1, seed=2),
+             workloads.small_problem(dim=1, mx=63, N=64, k=4, alpha=1.0, kappa=0.1, seed=3),
+             workloads.small_problem(dim=1, mx=127, N=64, k=2, alpha=0.5, kappa=0.1, seed=4)]
+    plans, Fs, vs, Us = [], [], [], []
+    for p in probs:
+        v, f, fd = device_inputs(p, torch)
+        pl = Plan.for_problem(p, "mixed")
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        pl.form_rhs(v, f, fd, F)
+        plans.append(pl); Fs.append(F); vs.append(v); Us.append(torch.empty_like(F))
+    try:
+        st, sweeps, upds = pint.batch_solve_v(plans, Fs, vs, Us, tol=1e-10)
+        torch.cuda.synchronize()
+        assert st == 0
+        for p, U in zip(probs, Us):
+            assert rel_l2(U.cpu().numpy(), oracle_solution(p)) <= 1e-8
+    finally:
+        for pl in plans:
+            pl.close()
