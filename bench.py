@@ -279,6 +279,27 @@ def oracle_sample(p, budget_s: float = 15.0, results=None):
                                    f"{n_s} of {p.N} time levels of the workload, {t:.2f} s"}, results, Ur)
 
 
+def diag_wr_sample(p, sweeps):
+    """The second CPU reference: the diagonalised WR solve of the whole workload in FP64 with
+    NumPy/SciPy FFTs on all host cores (oracle/diag_wr.py), F_hat formation and the same number of
+    sweeps as the GPU's MIXED solve from U_0^n = v. Finite differences, Dirichlet, 1D/2D only.
+    Returns (info, U) or None."""
+    if isinstance(p, workloads.NlProblem) or p.dim > 2 or getattr(p, "space", "fd") != "fd" or p.N * p.M > 50_000_000:
+        return None
+    from oracle import diag_wr, grid, sequential
+    f_t, fd = p.f(), p.fderiv()
+    A = grid.laplacian(p.mx, p.my, p.dim)
+    t0 = time.perf_counter()
+    Fh = sequential.all_at_once_rhs(p.k, p.alpha, p.tau, A, p.v, f_t, fd)
+    U = np.tile(p.v, (p.N, 1))
+    for _ in range(sweeps):
+        U, _c = diag_wr.sweep(p.k, p.alpha, p.kappa, p.tau, p.mx, p.my, p.dim, Fh, U, A)
+    t = time.perf_counter() - t0
+    return ({"value": p.dof / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "cpu diagonalised WR (FP64)",
+             "sample": f"the whole workload: F_hat and {sweeps} sweeps from U_0 = v with NumPy/SciPy FFTs "
+                       f"(SciPy FFT workers = all cores; the stencil product single-threaded), {t:.2f} s"}, U)
+
+
 def _with_errors(info, results, Ur):
     """Add the space-time relative l2 error of each GPU solution against the oracle's levels."""
     if results:
@@ -848,6 +869,7 @@ def main():
     p99 = float(np.percentile(lat_sorted, 99)) if lat_sorted else None
 
     cpu = None
+    cpu_diag = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             # (after the timed regions) the solutions of both paths, compared with the oracle's
@@ -856,7 +878,15 @@ def main():
                 step(prec)
                 torch.cuda.synchronize(dev)
                 results[prec] = U.cpu().numpy()
+            try:
+                dw = diag_wr_sample(p, last["mixed"][0])
+            except Exception as e:
+                dw = ({"error": str(e)}, None)
+            if dw is not None and dw[1] is not None:
+                results["cpu_diag_wr"] = dw[1]
             cpu = oracle_sample(p, results=results)
+            if dw is not None:
+                cpu_diag = dw[0]
         except Exception as e:  # never let the baseline break the bench line
             cpu = {"error": str(e)}
 
@@ -884,6 +914,7 @@ def main():
         },
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "cpu_diag_wr": cpu_diag,
         "e2e": {"value": dof_total / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                 "overlap": "two buffer sets, solves enqueued without host waits: copies of steps i-1 / i+1 overlap solve i",

@@ -27,6 +27,9 @@ Secondary routes, for pinning and for iterate-by-iterate references:
                     (eq. (2.4), eq. (3.8)) and per-mode contraction factors.
 * ``fem``        -- the P1 finite-element form used by the paper's 1D tests
                     (Sec. 4): Tables 2 and 3.
+* ``diag_wr``    -- the diagonalised WR solve (Algorithms 1 / 2) in FP64 with NumPy/SciPy
+                    FFTs: a second CPU reference for timing, pinned against ``allatonce``
+                    and ``sequential``.
 * ``nonlinear``  -- the semilinear scheme (eq. (4.4)) stepped with Newton's
                     method, and Algorithm 3 (modified Newton with the
                     Jacobian at the time average, inner WR of eq. (4.7)):

@@ -110,3 +110,17 @@ def test_oracle_sample_reports_the_error_of_given_solutions():
     assert 8 <= n_s <= p.N
     assert info["rel_err_vs_oracle"]["same"] == 0.0
     assert abs(info["rel_err_vs_oracle"]["off"] - 1e-9) <= 1e-12
+
+
+def test_second_cpu_reference_sample():
+    # the diagonalised WR solve on the host (bench's cpu_diag_wr entry): the GPU's sweep count from
+    # U_0 = v, its accuracy reported against the oracle beside the GPU solutions'
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads
+    p = workloads.c1_heat1d()
+    info, U = bench.diag_wr_sample(p, 3)
+    assert info["value"] > 0 and info["cores"] >= 1 and U.shape == (p.N, p.M)
+    errs = bench.oracle_sample(p, budget_s=1.0, results={"cpu_diag_wr": U})["rel_err_vs_oracle"]
+    assert errs["cpu_diag_wr"] <= 1e-10
+    assert bench.diag_wr_sample(workloads.fem_problem(mx=15, N=16, k=2), 3) is None   # FD only
