@@ -65,6 +65,17 @@ def algo_bytes(name: str, N: int, M: int) -> float:
         "nl_rhs": 32 * NM,                      # read F_hat, U; write the linearised F_hat, U_{l-1}
         "nl_norms": 16 * NM,                    # read U, U_{l-1}
         "small_solve_ff": 16 * NM,              # one-CTA solve: read F_hat, write U (the rest stays on chip)
+        "cvt_bcast_d2ff": 8 * NM,               # write U_0 = v on every level (double-float)
+        "cvt_d2f": 12 * NM,                     # read FP64, write FP32
+        "cvt_f2d": 12 * NM,
+        "tri_y_f32": 16 * JM,                   # read + write spectrum (complex float)
+        "axis_solve_per_f32": 16 * JM,
+        "fft_per_f32": 16 * JM,
+        "axis_solve_per_f64": 32 * JM,
+        "fft_per_f64": 32 * JM,
+        "direct_fwd_f32": 4 * NM + 8 * JM,      # read F (FP32), write half spectrum
+        "direct_inv_f32": 8 * JM + 8 * NM,      # read spectrum, U old; write U (FP32)
+        "window_rhs": 16 * NM,                  # read f, write F_hat
     }
     return float(table.get(name, 0.0))
 

@@ -124,3 +124,24 @@ def test_second_cpu_reference_sample():
     errs = bench.oracle_sample(p, budget_s=1.0, results={"cpu_diag_wr": U})["rel_err_vs_oracle"]
     assert errs["cpu_diag_wr"] <= 1e-10
     assert bench.diag_wr_sample(workloads.fem_problem(mx=15, N=16, k=2), 3) is None   # FD only
+
+
+def test_every_profiled_kernel_has_algorithmic_bytes():
+    # bench.py's roofline divides a kernel's algorithmic bytes by its CUDA-event time: every name
+    # the library's per-kernel profiler can report needs an entry
+    import re
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = os.path.join(ROOT, "paper_2007_13125_gb300", "csrc")
+    names = set()
+    for fn in os.listdir(csrc):
+        if not fn.endswith(".cu"):
+            continue
+        text = open(os.path.join(csrc, fn)).read()
+        for m in re.finditer(r"prof_begin\(([^;]*);", text):
+            names |= set(re.findall(r'"([a-z0-9_]+)"', m.group(1)))
+        for m in re.finditer(r"const char\* name = ([^;]*);", text):
+            names |= set(re.findall(r'"([a-z0-9_]+)"', m.group(1)))
+    assert len(names) >= 25
+    missing = sorted(n for n in names if bench.algo_bytes(n, 64, 63) <= 0)
+    assert not missing, missing
