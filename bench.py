@@ -240,10 +240,11 @@ def problem_for_rank(rank: int):
     return (NL_WORKLOADS if WORKLOAD in NL_WORKLOADS else WORKLOADS)[WORKLOAD]()
 
 
-def oracle_sample(p, budget_s: float = 15.0, results=None):
-    """Time the CPU oracle on the first n_s time levels of the workload (bounded). results:
-    optional {label: GPU solution [N][M]}; each is compared with the oracle's solution on the
-    levels the sample covers (the schemes are causal, so those levels are exact)."""
+def oracle_sample(p, budget_s: float = 15.0, results=None, full: bool = False):
+    """Time the CPU oracle on the first n_s time levels of the workload (bounded; all N levels
+    when full). results: optional {label: GPU solution [N][M]}; each is compared with the oracle's
+    solution on the levels the sample covers (the schemes are causal, so those levels are exact).
+    The returned dict carries the measured seconds and the levels run ("seconds", "levels")."""
     if p.dim == 3 and p.M > 300_000:
         # the oracle's sparse LU of a 3D operator this large (fill-in) exceeds a bounded sample
         raise RuntimeError(f"not run: sparse LU of the 3D operator ({p.M} unknowns) exceeds a bounded CPU sample")
@@ -259,11 +260,10 @@ def oracle_sample(p, budget_s: float = 15.0, results=None):
             Ur = nonlinear.solve_sequential_nl(p.k, p.alpha, p.tau, Mass, A, w, p.g, Fh)
             return time.perf_counter() - t0, Ur
 
-        t8, _ = run(8)
-        per = t8 / 8
-        n_s = int(max(8, min(p.N, budget_s / max(per, 1e-9))))
+        n_s = p.N if full else _levels_in_budget(run, p.N, budget_s)
         t, Ur = run(n_s)
         return _with_errors({"value": p.M * n_s / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "seconds": t, "levels": n_s,
                              "sample": f"sequential FP64 semilinear CQ-BDF{p.k} (Newton per step, sparse LU) over the "
                                        f"first {n_s} of {p.N} time levels of the workload, {t:.2f} s"}, results, Ur)
     if getattr(p, "space", "fd") == "fem":
@@ -281,13 +281,21 @@ def oracle_sample(p, budget_s: float = 15.0, results=None):
             Ur = sequential.solve_sequential(p.k, p.alpha, p.tau, A, p.v, f_full[:n_s], fd)
             return time.perf_counter() - t0, Ur
 
-    t8, _ = run(8)
-    per = t8 / 8
-    n_s = int(max(8, min(p.N, budget_s / max(per, 1e-9))))
+    n_s = p.N if full else _levels_in_budget(run, p.N, budget_s)
     t, Ur = run(n_s)
+    scheme = f"BDF{p.k}" if p.alpha == 1.0 else f"CQ-BDF{p.k} (alpha = {p.alpha})"
     return _with_errors({"value": p.M * n_s / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"sequential FP64 BDF{p.k} (sparse LU, SuperLU single-threaded) over the first "
-                                   f"{n_s} of {p.N} time levels of the workload, {t:.2f} s"}, results, Ur)
+                         "seconds": t, "levels": n_s,
+                         "sample": f"sequential FP64 {scheme} (sparse LU, SuperLU single-threaded) over "
+                                   f"{'all' if n_s == p.N else 'the first'} {n_s} of {p.N} time levels of the "
+                                   f"workload, {t:.2f} s"}, results, Ur)
+
+
+def _levels_in_budget(run, N: int, budget_s: float) -> int:
+    """Levels of the oracle that fit in budget_s, from the time of its first 8 levels."""
+    t8, _ = run(min(8, N))
+    per = t8 / min(8, N)
+    return int(max(min(8, N), min(N, budget_s / max(per, 1e-9))))
 
 
 def diag_wr_sample(p, sweeps):
@@ -323,23 +331,27 @@ def _with_errors(info, results, Ur):
 
 
 def run_reference(args):
+    """The oracle arm: every step is the oracle's whole sequential solve of the workload (all N
+    levels; about 2.7 s for heat2d on one Arm core), timed on the host; ms_per_step is the median
+    measured step time and value = N * M / that time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     p = problem_for_rank(0)
-    samples = []
+    secs = []
     info = None
     for i in range(args.warmup + args.steps):
-        info = oracle_sample(p, budget_s=min(20.0, 150.0 / max(1, args.warmup + args.steps)))
+        info = oracle_sample(p, full=True)
         if i >= args.warmup:
-            samples.append(info["value"])
-    value = statistics.median(samples)
+            secs.append(info["seconds"])
+    t_step = statistics.median(secs)
+    value = p.dof / t_step
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * p.dof / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": p.name, "dof": p.dof},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": info["sample"]},
+                             "sample": info["sample"] + f"; median of {len(secs)} timed steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -881,6 +893,7 @@ def main():
 
     cpu = None
     cpu_diag = None
+    fp32_info = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             # (after the timed regions) the solutions of both paths, compared with the oracle's
@@ -889,6 +902,16 @@ def main():
                 step(prec)
                 torch.cuda.synchronize(dev)
                 results[prec] = U.cpu().numpy()
+            if has_fp64:
+                # the pure-FP32 floor (Algorithm 1 entirely in single precision): sweeps until the
+                # update stalls at its rounding floor (at most 8), reported beside the MIXED error
+                with Plan.for_problem(p, "fp32") as p32:
+                    p32.form_rhs(v, f, fd, F, stream)
+                    st32, sw32, up32 = p32.solve_v(F, v, U, tol=1e-14, max_sweeps=8, stream=stream,
+                                                   raise_on_notconv=False)
+                    torch.cuda.synchronize(dev)
+                    results["fp32"] = U.cpu().numpy()
+                    fp32_info = {"sweeps": sw32, "final_update": up32}
             try:
                 dw = diag_wr_sample(p, last["mixed"][0])
             except Exception as e:
@@ -936,6 +959,10 @@ def main():
     if rank == 0:
         if isinstance(cpu, dict) and "rel_err_vs_oracle" in cpu:
             line["config"]["rel_err_vs_oracle"] = cpu["rel_err_vs_oracle"]
+            if "fp32" in cpu["rel_err_vs_oracle"]:
+                line["config"]["fp32_floor_rel_err"] = cpu["rel_err_vs_oracle"]["fp32"]
+                line["config"]["fp32_floor"] = dict(fp32_info or {}, note="PINT_FP32: Algorithm 1 in single "
+                                                    "precision, stalled at its rounding floor (reported, not a target)")
         print(json.dumps(line), flush=True)
     for pl in plans.values():
         pl.close()

@@ -353,9 +353,13 @@ pint_status pint_server_stats(pint_server s, double* out);
  * plugins whose host runtime owns every allocation, or real-time loops where a cudaMalloc
  * (which may synchronise the device) is not acceptable. Such callers cannot build a plan.
  *
- * Q = P_kappa^{-1} R for the 1D heat problem (alpha = 1, FP64): Algorithm 1 steps 1-3 with the
- * same kernels as a PINT_FP64 plan, i.e. the result of pint_wr_sweep with U_prev = 0 and
- * Fhat = R. R, Q: [N][mx] FP64 device arrays owned by the caller (Q may not alias R).
+ * Q = P_kappa^{-1} R for the 1D heat problem (alpha = 1, FP64, finite differences): scale level
+ * n by kappa^{n/N}, transform along time, solve the N/2 + 1 complex-shifted 1D systems by the
+ * sine transform, transform back and undo the scaling -- the same kernels as a PINT_FP64 plan,
+ * i.e. the result of pint_wr_sweep with U_prev = 0 and Fhat = R.
+ * R, Q: [N][mx] FP64 arrays of the current device owned by the caller; Q may not overlap R
+ * (PINT_EINVAL for host pointers, arrays of another device, or overlapping arrays; the sizes of
+ * the arrays cannot be checked from raw pointers: each must hold N * mx doubles).
  * Limits: N a power of two in [8, 1024] with N > k; mx + 1 a power of two, 3 <= mx <= 1023;
  * (N/2 + 1) * mx <= 262144. Larger sizes return PINT_EINVAL (message in pint_last_error).
  * Memory: the intermediate spectrum and the constant tables live in one static device array of
@@ -363,9 +367,12 @@ pint_status pint_server_stats(pint_server s, double* out);
  * the process exits. No cudaMalloc, cudaFree or other allocating routine is called.
  * Set-up: the first call made on a device looks up that array's device address for the
  * current device (a synchronous driver query), so make that first call before any stream
- * capture. The array is shared by every call and keeps the last call's contents (the parts
- * that must start at zero are cleared by each call): calls whose GPU work overlaps -- on
- * different streams or from different host threads -- race on it; serialise them. */
+ * capture. The address is kept per device together with the ID of the context it was found in;
+ * after a cudaDeviceReset the next call (again the first in the new context, so again before
+ * any capture) looks it up anew. The array is shared by every call and keeps the last call's
+ * contents (the parts that must start at zero are cleared by each call): calls whose GPU work
+ * overlaps -- on different streams or from different host threads -- race on it; serialise
+ * them. */
 pint_status pint_kappa_solve_noalloc(int k, double kappa, double tau, int N, int mx, const double* R,
                                      double* Q, void* stream);
 

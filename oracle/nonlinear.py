@@ -33,8 +33,9 @@ sign contracts by ~5e-2 per outer step on Example 4, Table 4 shows ~1e-4
 (tests/test_oracle_nonlinear.py::test_printed_sign_does_not_reproduce_table4).
 
 Pins (tests/test_oracle_nonlinear.py): Table 4's inner iteration counts exactly and its errors
-after the solution-amplitude rescaling that its m = 0 row implies (reading r18 of the design
-notes: the printed e_0 are 11% / 5% above the norm of the stated manufactured solution); order-k
+after the solution-amplitude rescaling that its m = 0 row implies (the printed e_0 are 11% / 5%
+above the norm of the stated manufactured solution, and the modified-Newton error after l steps
+scales with the amplitude r like r^(2l+1)); order-k
 convergence to an exact semi-discrete solution (alpha = 1, finite differences, the discrete
 eigenvalue in f); a linear g reduces Algorithm 3 to one step of the linear method with a shifted
 operator; the sequential solution solves the all-at-once nonlinear system (global Newton on the

@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(kThreads) k_direct_fwd(DirectFwdArgs<T> a) {
       if (a.z) {
         f += (T)a.z[idx];
       } else if (i < a.k) {
-        // row n = i+1 <= k: kappa tau^-1 sum_{j=n}^{k} omega_j U^{N+n-j}  (eq. (2.7), reading r1)
+        // row n = i+1 <= k: kappa tau^-1 sum_{j=n}^{k} omega_j U^{N+n-j}, the kappa-term of eq. (2.7)
+        // indexed to match B_k(kappa) of eq. (2.6) (the printed sum_{j=1}^{n} omega_j U^{N-j+1} has another
+        // fixed point)
 #pragma unroll
         for (int j = 1; j <= kMaxK; ++j)
           if (j > i && j <= a.k) f += a.kw[j] * a.U[(size_t)(N + i - j) * M + m];

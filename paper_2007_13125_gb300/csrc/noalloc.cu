@@ -11,9 +11,11 @@
 // The array is part of the library image: every GPU that loads the library holds it until the
 // process exits. All calls share it, so calls whose GPU work overlaps (on different streams, or
 // from different host threads) race on it; serialise them on one stream.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -37,8 +39,54 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of g_noalloc_scratch per device ordinal, looked up on the first call made
 // with that device current (cudaGetSymbolAddress; never a device pointer taken from host code).
+// The address belongs to the context the library's module was loaded into: after a
+// cudaDeviceReset the device gets a new primary context, the module is loaded again and the
+// array may sit elsewhere. So each slot also records the ID of the context it was looked up in
+// (cuCtxGetId, reached through the runtime's driver entry points, so no libcuda link), and a
+// call made in another context looks the address up again.
+struct NaSlot {
+  unsigned long long ctx_id;
+  void* ptr;
+};
 static std::mutex g_na_mu;
-static void* g_na_ptr[64] = {nullptr};
+static NaSlot g_na[64] = {};
+
+// ID of the calling thread's current context; false if there is none yet or the driver cannot
+// report it (the caller then looks the address up on every call). Called under g_na_mu.
+static bool current_ctx_id(unsigned long long* id) {
+  using GetCur = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCur get_cur = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<GetCur>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(p);
+  }
+  if (!get_cur || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device ordinal of a device (or managed) allocation, -1 otherwise.
+static int pointer_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the (non-sticky) error left by an unknown pointer
+    return -1;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return -1;
+  return at.device;
+}
 
 // Constant tables of the solve, computed on the device in FP64 (CUDA math functions):
 // tw[m] = exp(-2 pi i m/N), s_i = kappa^{i/N}, inv_s_i = kappa^{-i/N}/N,
@@ -117,21 +165,34 @@ extern "C" pint_status pint_kappa_solve_noalloc(int k, double kappa, double tau,
     return na_fail(PINT_EINVAL, "mx + 1 must be a power of two, 3 <= mx <= 1023");
   if ((size_t)(N / 2 + 1) * (size_t)mx > kNoAllocSpectrum)
     return na_fail(PINT_EINVAL, "(N/2+1)*mx exceeds the static scratch capacity of 262144 complex values");
+  {
+    // R and Q hold N * mx doubles each and may not overlap
+    const size_t bytes = sizeof(double) * (size_t)N * (size_t)mx;
+    const uintptr_t r0 = reinterpret_cast<uintptr_t>(R), q0 = reinterpret_cast<uintptr_t>(Q);
+    if (r0 < q0 + bytes && q0 < r0 + bytes) return na_fail(PINT_EINVAL, "Q overlaps R");
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_fail(PINT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= 64) return na_fail(PINT_EINVAL, "device ordinal out of range");
+  // the scratch array used is the current device's: R and Q must live on that device too
+  if (pointer_device(R) != dev || pointer_device(Q) != dev)
+    return na_fail(PINT_EINVAL, "R and Q must be device arrays of the current device");
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    unsigned long long id = 0;
+    bool have_id = g_na[dev].ptr && current_ctx_id(&id);
+    if (!have_id || g_na[dev].ctx_id != id) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess)
         return na_fail(PINT_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_na_ptr[dev] = p;
+      have_id = current_ctx_id(&id);
+      g_na[dev].ctx_id = have_id ? id : 0;
+      g_na[dev].ptr = p;
     }
-    base = reinterpret_cast<unsigned char*>(g_na_ptr[dev]);
+    base = reinterpret_cast<unsigned char*>(g_na[dev].ptr);
   }
   cudaStream_t st = (cudaStream_t)stream;
   const int J = N / 2 + 1, L = 2 * (mx + 1);

@@ -215,8 +215,22 @@ def circulant_eigenvalues(k: int, alpha: float, kappa: float, N: int, eig: int =
 
 
 def kappa_solve_noalloc(k, kappa, tau, N, mx, R, Q, stream=None):
-    """Q = P_kappa^{-1} R (1D heat, FP64) with no device allocation (see include/pint.h)."""
-    check(lib().pint_kappa_solve_noalloc(int(k), float(kappa), float(tau), int(N), int(mx), _ptr(R), _ptr(Q),
+    """Q = P_kappa^{-1} R (1D heat, FP64) with no device allocation (pint_kappa_solve_noalloc).
+
+    R and Q must each hold N * mx elements, be distinct tensors, and live on the current CUDA
+    device (the library uses that device's static scratch array); ValueError otherwise, before
+    anything reaches the library."""
+    n = int(N) * int(mx)
+    if R.numel() != n or Q.numel() != n:
+        raise ValueError(f"R and Q must hold N * mx = {n} elements (got {R.numel()} and {Q.numel()})")
+    if R.data_ptr() == Q.data_ptr():
+        raise ValueError("Q may not alias R")
+    pr, pq = _ptr(R), _ptr(Q)
+    import torch
+    cur = torch.cuda.current_device()
+    if R.device.index != cur or Q.device.index != cur:
+        raise ValueError(f"R and Q must be on the current CUDA device (cuda:{cur})")
+    check(lib().pint_kappa_solve_noalloc(int(k), float(kappa), float(tau), int(N), int(mx), pr, pq,
                                          _stream(stream)))
 
 

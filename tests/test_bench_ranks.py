@@ -83,6 +83,20 @@ def test_reference_arm_runs_on_rank_zero_only():
     assert r.stdout.strip() == ""
 
 
+def test_reference_arm_times_the_whole_oracle_solve():
+    # one rank: every step is the oracle's solve of all N levels, and ms_per_step is that measured
+    # time (value = N M / time), not an extrapolation from a sample of levels
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
+                        "--workload", "heat1d"], cwd=ROOT, capture_output=True, text=True, timeout=180)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert "all 64 of 64 time levels" in line["cpu_baseline"]["sample"]
+    dof = line["config"]["dof"]
+    assert abs(line["ms_per_step"] - 1e3 * dof / line["value"]) <= 1e-9 * line["ms_per_step"]
+    assert line["e2e"]["value"] == line["value"]
+
+
 def test_stored_ncu_traffic_applies_to_its_own_workload_only():
     # the DRAM traffic bench.py reports beside a roofline comes from an ncu capture of one
     # workload; another workload's launch of the same kernel moves different bytes

@@ -153,3 +153,15 @@ def test_allen_cahn_inputs_are_the_manufactured_source():
             phi = 1.0 - np.abs(xs - x[i]) / h
             ref[:, i] += (b - a) / 2 * (f(t[:, None], xs[None, :]) * phi * gw).sum(axis=1)
     assert np.allclose(q.f(), ref, rtol=1e-6, atol=1e-9)
+
+
+def test_noalloc_wrapper_checks_buffer_sizes_without_a_gpu(pint):
+    """The binding of pint_kappa_solve_noalloc refuses buffers that do not hold N * mx elements
+    before anything reaches the library (the C entry point cannot see the sizes)."""
+    torch = pytest.importorskip("torch")
+    R = torch.zeros((64, 63), dtype=torch.float64)
+    Q = torch.zeros((32, 63), dtype=torch.float64)
+    with pytest.raises(ValueError, match="N \\* mx"):
+        pint.kappa_solve_noalloc(2, 0.1, 1.0 / 64, 64, 63, R, Q)
+    with pytest.raises(ValueError):
+        pint.kappa_solve_noalloc(2, 0.1, 1.0 / 64, 64, 63, R, R)
