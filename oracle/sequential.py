@@ -14,10 +14,13 @@ step by step as the paper defines it, is what the GPU path is compared with.
                            sequential scheme is K U = F_hat, K = tau^{-alpha} (L (x) I) + I (x) A.
 * ``solve_sequential``  -- steps n = 1..N of
                            (omega_0 I + tau^alpha A) U^n
-                              = tau^alpha f_bar_n + omega_0 v + sum_{j=1}^{n-1} omega_j (v - U^{n-j}),
-                           the per-step system of Sec. 3.2 (speedup analysis of Algorithm 2),
-                           which for alpha = 1 (omega_j = 0, j > k) is the BDF-k scheme
-                           eq. (2.1) with U^{-(k-1)} = ... = U^0 = v.
+                              = tau^alpha f_bar_n - sum_{j=1}^{n-1} omega_j U^{n-j}
+                                + (sum_{j=0}^{n-1} omega_j) v,
+                           the per-step system of Sec. 3.2 (speedup analysis of Algorithm 2,
+                           multiplied by tau^alpha; its history sum and its v-sum are printed
+                           separately, and so are they computed here), which for alpha = 1
+                           (omega_j = 0, j > k) is the BDF-k scheme eq. (2.1) with
+                           U^{-(k-1)} = ... = U^0 = v.
 
 Pins (tests/test_oracle_sequential.py): order-k convergence against the exact solution
 of a scalar ODE (alpha = 1) and by self-convergence (alpha < 1); first order without the
@@ -78,12 +81,15 @@ def solve_sequential(k, alpha, tau, A, v, f_t, dfs, corrected=True, omega=None):
     lu = spla.splu(sp.csc_matrix(w[0] * sp.identity(M) + ta * A))
     U = np.zeros((N, M))
     nz = int(np.max(np.nonzero(w)[0])) if np.any(w) else 0  # last nonzero weight
+    csum = np.cumsum(w)                  # csum[j] = sum_{i=0}^{j} omega_i
+    Lw = len(w)
+    wrev = np.ascontiguousarray(w[::-1])  # wrev[Lw-1-j] = omega_j (a contiguous vector for BLAS)
     for n in range(1, N + 1):
-        rhs = ta * fbar[n - 1] + w[0] * v
-        jmax = min(n - 1, nz)
+        jmax = min(n - 1, nz)            # omega_j = 0 beyond nz, so the sums stop there
+        rhs = ta * fbar[n - 1] + csum[jmax] * v
         if jmax >= 1:
-            # sum_{j=1}^{jmax} omega_j (v - U^{n-j});  U^{n-j} is row n-j-1
-            hist = w[1:jmax + 1] @ (v[None, :] - U[n - 2::-1][:jmax])
-            rhs = rhs + hist
+            # sum_{j=1}^{jmax} omega_j U^{n-j}: U^{n-j} is row n-j-1, so rows n-1-jmax .. n-2
+            # meet omega_jmax .. omega_1
+            rhs = rhs - wrev[Lw - 1 - jmax:Lw - 1] @ U[n - 1 - jmax:n - 1]
         U[n - 1] = lu.solve(rhs)
     return U
