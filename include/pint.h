@@ -293,9 +293,11 @@ typedef struct {
  * stopping rule and tolerance `tol`, at most max_sweeps sweeps; one graph launch) applied to
  * V = U_{l-1} + W. The linearised term carries +g'(Ubar), the sign of Newton's linearisation
  * (eqs. (4.6)-(4.7) print -g'(Ubar); only + reproduces the contraction of Table 4). The outer
- * loop stops by the rule of pint_solve applied to upd_l = ||U_l - U_{l-1}|| / ||U_l|| with
- * newton_tol and no floor (upd_1 <= newton_tol / 100, or upd_l q / (1 - q) <= newton_tol with
- * q = upd_l / upd_{l-1}). Fhat [N][M] device (pint_nl_form_rhs); U [N][M] device, in: initial
+ * loop stops on upd_l = ||U_l - U_{l-1}|| / ||U_l||: at l = 1 or 2 when upd_l <= newton_tol / 100
+ * (the ratio upd_2 / upd_1 reflects the distance of the starting iterate, not the contraction of
+ * later steps, so it is not used on its own); from l = 3 when upd_l q / (1 - q) <= newton_tol with
+ * q the larger of upd_l / upd_{l-1} and upd_{l-1} / upd_{l-2}.
+ * Fhat [N][M] device (pint_nl_form_rhs); U [N][M] device, in: initial
  * iterate, out: U_l. info: optional host pointer. The solve installs w D in the plan's reaction
  * slot and removes it before returning; PINT_EINVAL if a reaction term is already installed.
  * Waits for `stream` once per outer step. Returns PINT_ENOTCONV
@@ -396,6 +398,20 @@ pint_status pint_circulant_eigenvalues(int k, double alpha, double kappa, int N,
 const char* pint_last_error(void);
 const char* pint_status_string(pint_status s);
 const char* pint_version(void);
+
+/* Device memory, in bytes, that the library holds right now through cudaMalloc: the workspaces of
+ * live plans and the budgets of live servers (the static array of pint_kappa_solve_noalloc is not
+ * counted). Every creation that fails gives back what it took, so the figure returns to its earlier
+ * value once the plans and servers created since are destroyed or failed. */
+long long pint_device_bytes_held(void);
+
+/* Failure-path hook for tests: the n-th next memory allocation the library attempts (n = 0: the
+ * very next one; a cudaMalloc, a cudaMallocHost, or a sub-allocation from a server's budget) fails
+ * as if the memory were exhausted, taking the same error path and clean-up as a real failure
+ * (PINT_ENOMEM from plan creation and server creation; a request whose memory cannot be taken while
+ * nothing else runs finishes with PINT_EBUDGET). n < 0 disarms it. Process-wide; returns the
+ * previous setting. Nothing is faulted on the GPU. */
+int pint_debug_fail_allocation(int n);
 
 /* Per-kernel timing with CUDA events recorded around every launch on its stream (off by
  * default). pint_kernel_stats waits for the recorded events, then fills up to `max` entries

@@ -244,6 +244,18 @@ cudaError_t launch_ctl_init(SolveCtl* ctl, double tol, double q_floor, int max_s
 cudaError_t launch_converge(const double* norms, SolveCtl* ctl, cudaGraphConditionalHandle h, cudaStream_t st);
 
 // Thread-local message returned by pint_last_error().
+// Every allocation of the library goes through these (device: cudaMalloc / cudaFree, pinned host:
+// cudaMallocHost / cudaFreeHost), so that the failure-path hook pint_debug_fail_allocation can make
+// any of them fail and pint_device_bytes_held can count what is held. lib_free takes the size that
+// lib_malloc was given.
+cudaError_t lib_malloc(void** p, size_t bytes);
+void lib_free(void* p, size_t bytes);
+cudaError_t lib_malloc_host(void** p, size_t bytes);
+void lib_free_host(void* p);
+// The failure-path hook for allocations that are not cudaMalloc calls (sub-allocations from a
+// server's budget): true if this allocation is to fail.
+bool inject_alloc_failure();
+
 void set_last_error(const char* msg);
 inline void set_last_error(const std::string& msg) { set_last_error(msg.c_str()); }
 

@@ -7,6 +7,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -44,6 +45,47 @@ static pint_status cuda_fail(cudaError_t e, const char* where) {
     cudaError_t _e = (call);                                   \
     if (_e != cudaSuccess) return cuda_fail(_e, #call);        \
   } while (0)
+
+// ---------------------------------------------------------------------------
+// allocations: the failure-path hook and the count of device bytes held
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_fail_countdown{-1};   // < 0: off; 0: the next allocation fails
+static std::atomic<long long> g_device_bytes{0};
+
+bool inject_alloc_failure() {
+  int v = g_fail_countdown.load();
+  while (v >= 0) {
+    if (g_fail_countdown.compare_exchange_weak(v, v - 1)) return v == 0;
+  }
+  return false;
+}
+
+cudaError_t lib_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (inject_alloc_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_device_bytes += (long long)bytes;
+  else (void)cudaGetLastError();
+  return e;
+}
+
+void lib_free(void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  g_device_bytes -= (long long)bytes;
+}
+
+cudaError_t lib_malloc_host(void** p, size_t bytes) {
+  *p = nullptr;
+  if (inject_alloc_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMallocHost(p, bytes);
+  if (e != cudaSuccess) (void)cudaGetLastError();
+  return e;
+}
+
+void lib_free_host(void* p) {
+  if (p) cudaFreeHost(p);
+}
 
 // ---------------------------------------------------------------------------
 // per-kernel timing
@@ -234,10 +276,11 @@ template <typename X> pint_status dalloc(pint_plan p, X** ptr, size_t count) {
     q = p->alloc->alloc(count * sizeof(X));
     if (!q) return fail(PINT_ENOMEM, "device memory budget exhausted");
   } else {
-    cudaError_t e = cudaMalloc(&q, count * sizeof(X));
+    cudaError_t e = lib_malloc(&q, count * sizeof(X));
     if (e != cudaSuccess) return fail(PINT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   }
   p->allocs.push_back(q);
+  p->alloc_sizes.push_back(count * sizeof(X));
   p->bytes += count * sizeof(X);
   *ptr = reinterpret_cast<X*>(q);
   return PINT_OK;
@@ -384,18 +427,18 @@ void destroy_plan(pint_plan p) {
   for (SolveGraph& c : p->sg)
     if (c.exec) cudaGraphExecDestroy(c.exec);
   if (p->cap) cudaStreamDestroy(p->cap);
-  for (void* q : p->allocs) {
-    if (p->alloc) p->alloc->release(q);
-    else cudaFree(q);
+  for (size_t i = 0; i < p->allocs.size(); ++i) {
+    if (p->alloc) p->alloc->release(p->allocs[i]);
+    else lib_free(p->allocs[i], p->alloc_sizes[i]);
   }
   if (p->alloc) {
     if (p->h_norms) p->alloc->host_release(p->h_norms);
     if (p->h_ctl) p->alloc->host_release(p->h_ctl);
     if (p->nl_h) p->alloc->host_release(p->nl_h);
   } else {
-    if (p->h_norms) cudaFreeHost(p->h_norms);
-    if (p->h_ctl) cudaFreeHost(p->h_ctl);
-    if (p->nl_h) cudaFreeHost(p->nl_h);
+    if (p->h_norms) lib_free_host(p->h_norms);
+    if (p->h_ctl) lib_free_host(p->h_ctl);
+    if (p->nl_h) lib_free_host(p->nl_h);
   }
   delete p;
 }
@@ -538,8 +581,12 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
     p->h_ctl = (SolveCtl*)p->alloc->host_alloc(sizeof(SolveCtl));
     if (!p->h_norms || !p->h_ctl) return bail(fail(PINT_ENOMEM, "pinned host buffer"));
   } else {
-    if (cudaMallocHost(&p->h_norms, 2 * sizeof(double)) != cudaSuccess) return bail(fail(PINT_ENOMEM, "cudaMallocHost"));
-    if (cudaMallocHost(&p->h_ctl, sizeof(SolveCtl)) != cudaSuccess) return bail(fail(PINT_ENOMEM, "cudaMallocHost"));
+    void* hn = nullptr;
+    void* hc = nullptr;
+    if (lib_malloc_host(&hn, 2 * sizeof(double)) != cudaSuccess) return bail(fail(PINT_ENOMEM, "cudaMallocHost"));
+    p->h_norms = (double*)hn;
+    if (lib_malloc_host(&hc, sizeof(SolveCtl)) != cudaSuccess) return bail(fail(PINT_ENOMEM, "cudaMallocHost"));
+    p->h_ctl = (SolveCtl*)hc;
   }
   PINT_CUDA_B(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
 
@@ -979,10 +1026,15 @@ pint_status tune_time_tiles(pint_plan p, int cmax_t, int cmax_z) {
   }
   const size_t NM = (size_t)p->N * p->M;
   double* F = nullptr;
-  PINT_CUDA(cudaMalloc(&F, NM * sizeof(double)));
+  {
+    void* q = nullptr;
+    const cudaError_t ea = lib_malloc(&q, NM * sizeof(double));
+    if (ea != cudaSuccess) return fail(PINT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(ea));
+    F = (double*)q;
+  }
   cudaStream_t st;
   cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-  if (e != cudaSuccess) { cudaFree(F); return cuda_fail(e, "tile tuning"); }
+  if (e != cudaSuccess) { lib_free(F, NM * sizeof(double)); return cuda_fail(e, "tile tuning"); }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1021,7 +1073,7 @@ pint_status tune_time_tiles(pint_plan p, int cmax_t, int cmax_z) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(st);
-  cudaFree(F);
+  lib_free(F, NM * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(e, "tile tuning");
   std::lock_guard<std::mutex> lk(mu);
   Entry en;
@@ -1717,6 +1769,21 @@ extern "C" pint_status pint_nl_form_rhs(pint_plan p, const pint_poly* g, const d
   return form_rhs(p, v, f, fderiv, Fhat, (cudaStream_t)stream, &q);
 }
 
+// Outer stopping rule of Algorithm 3 after step l (upd = upd_l, prev = upd_{l-1}, prev2 = upd_{l-2}).
+// The first update is the whole Newton step from the starting iterate, so the ratio upd_2 / upd_1
+// measures how far that iterate was, not the contraction of the later steps (on Example 4 the
+// step 2 -> 3 contraction is larger): it is never trusted alone. l = 1 or 2: stop only when the
+// update itself is below tol / 100; l >= 3: q = the larger of the last two ratios, and the error
+// estimate upd_l q / (1 - q) must be <= tol (upd_l <= tol if q >= 1).
+static bool outer_stop_decision(int l, double upd, double prev, double prev2, double tol) {
+  if (l <= 2) return upd <= 0.01 * tol;
+  double q = prev > 0.0 ? upd / prev : 0.0;
+  const double q2 = prev2 > 0.0 ? prev / prev2 : 0.0;
+  if (q2 > q) q = q2;
+  if (q < 1.0) return upd * q / (1.0 - q) <= tol;
+  return upd <= tol;
+}
+
 extern "C" pint_status pint_nl_solve(pint_plan p, const pint_poly* g, const double* Fhat, double* U,
                                      double newton_tol, int max_steps, double tol, int max_sweeps,
                                      pint_nl_info* info, void* stream) {
@@ -1737,14 +1804,17 @@ extern "C" pint_status pint_nl_solve(pint_plan p, const pint_poly* g, const doub
   }
   if (!p->nl_h) {
     p->nl_h = p->alloc ? (double*)p->alloc->host_alloc(2 * sizeof(double)) : nullptr;
-    if (!p->alloc && cudaMallocHost(&p->nl_h, 2 * sizeof(double)) != cudaSuccess) p->nl_h = nullptr;
+    if (!p->alloc) {
+      void* q = nullptr;
+      p->nl_h = lib_malloc_host(&q, 2 * sizeof(double)) == cudaSuccess ? (double*)q : nullptr;
+    }
     if (!p->nl_h) return fail(PINT_ENOMEM, "pinned host buffer");
   }
   const NlPoly q = to_poly(g);
   const double w = react_weight(p);
   if (info) std::memset(info, 0, sizeof(*info));
   p->react_on = true;
-  double prev = 0.0;
+  double prev = 0.0, prev2 = 0.0;
   bool converged = false, inner_ok = true;
   int l = 0;
   while (l < max_steps && !converged) {
@@ -1773,7 +1843,8 @@ extern "C" pint_status pint_nl_solve(pint_plan p, const pint_poly* g, const doub
       info->sweeps[l - 1] = sweeps;
       info->upd[l - 1] = upd;
     }
-    converged = stop_decision(l, upd, prev, newton_tol, 0.0);
+    converged = outer_stop_decision(l, upd, prev, prev2, newton_tol);
+    prev2 = prev;
     prev = upd;
   }
   p->react_on = false;
@@ -1781,3 +1852,7 @@ extern "C" pint_status pint_nl_solve(pint_plan p, const pint_poly* g, const doub
   if (!inner_ok) return fail(PINT_ENOTCONV, "an inner solve reached max_sweeps above tol");
   return PINT_OK;
 }
+
+extern "C" long long pint_device_bytes_held(void) { return pint::g_device_bytes.load(); }
+
+extern "C" int pint_debug_fail_allocation(int n) { return pint::g_fail_countdown.exchange(n < 0 ? -1 : n); }

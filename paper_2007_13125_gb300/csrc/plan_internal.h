@@ -34,9 +34,9 @@ struct DevAllocator {
   // small pinned host buffers (convergence state read back by the host)
   virtual void* host_alloc(size_t bytes) {
     void* p = nullptr;
-    return cudaMallocHost(&p, bytes) == cudaSuccess ? p : nullptr;
+    return lib_malloc_host(&p, bytes) == cudaSuccess ? p : nullptr;
   }
-  virtual void host_release(void* p) { cudaFreeHost(p); }
+  virtual void host_release(void* p) { lib_free_host(p); }
   virtual ~DevAllocator() {}
 };
 
@@ -74,6 +74,7 @@ struct pint_plan_s {
   // device
   pint::DevAllocator* alloc = nullptr;   // null: cudaMalloc / cudaFree
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_sizes;
   size_t bytes = 0;
   pint::DevTables<float> tf;
   pint::DevTables<double> td;

@@ -38,6 +38,7 @@ class Arena : public DevAllocator {
     for (int i = nslots - 1; i >= 0; --i) host_free_.push_back(pinned_ + (size_t)i * kHostBlock);
   }
   void* host_alloc(size_t bytes) override {
+    if (inject_alloc_failure()) return nullptr;
     std::lock_guard<std::mutex> lk(mu_);
     if (bytes > kHostBlock || host_free_.empty()) return nullptr;
     void* p = host_free_.back();
@@ -51,6 +52,7 @@ class Arena : public DevAllocator {
   }
   void* alloc(size_t bytes) override {
     bytes = (bytes + 255) & ~(size_t)255;
+    if (inject_alloc_failure()) return nullptr;  // the failure-path hook: as if the budget were full
     std::lock_guard<std::mutex> lk(mu_);
     for (auto it = free_.begin(); it != free_.end(); ++it) {
       if (it->second >= bytes) {
@@ -417,15 +419,15 @@ extern "C" pint_status pint_server_create(size_t hbm_budget_bytes, int max_activ
   s->max_active = max_active;
   cudaGetDevice(&s->device);
   void* base = nullptr;
-  cudaError_t e = cudaMalloc(&base, hbm_budget_bytes);
+  cudaError_t e = lib_malloc(&base, hbm_budget_bytes);
   if (e != cudaSuccess) {
     delete s;
     return srv_fail(PINT_ENOMEM, "cannot reserve the device-memory budget");
   }
   s->base = (char*)base;
   void* pinned = nullptr;
-  if (cudaMallocHost(&pinned, (size_t)max_active * 4 * Arena::kHostBlock) != cudaSuccess) {
-    cudaFree(base);
+  if (lib_malloc_host(&pinned, (size_t)max_active * 4 * Arena::kHostBlock) != cudaSuccess) {
+    lib_free(base, hbm_budget_bytes);
     delete s;
     return srv_fail(PINT_ENOMEM, "cannot allocate pinned host buffers");
   }
@@ -461,8 +463,8 @@ extern "C" pint_status pint_server_destroy(pint_server s) {
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
   delete s->arena;
-  cudaFree(s->base);
-  cudaFreeHost(s->pinned);
+  lib_free(s->base, s->budget);
+  lib_free_host(s->pinned);
   delete s;
   return PINT_OK;
 }

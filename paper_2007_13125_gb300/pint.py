@@ -110,6 +110,8 @@ def lib():
         "pint_version": (ctypes.c_char_p, []),
         "pint_set_profiling": (_I, [_I]),
         "pint_kappa_solve_noalloc": (_I, [_I, _D, _D, _I, _I, _P, _P, _P]),
+        "pint_device_bytes_held": (ctypes.c_longlong, []),
+        "pint_debug_fail_allocation": (_I, [_I]),
         "pint_batch_solve": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I,
                                   ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
         "pint_batch_solve_v": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -232,6 +234,16 @@ def kappa_solve_noalloc(k, kappa, tau, N, mx, R, Q, stream=None):
         raise ValueError(f"R and Q must be on the current CUDA device (cuda:{cur})")
     check(lib().pint_kappa_solve_noalloc(int(k), float(kappa), float(tau), int(N), int(mx), pr, pq,
                                          _stream(stream)))
+
+
+def device_bytes_held() -> int:
+    """Device bytes held by live plans and servers (pint_device_bytes_held)."""
+    return int(lib().pint_device_bytes_held())
+
+
+def debug_fail_allocation(n: int) -> int:
+    """Make the n-th next allocation of the library fail (n < 0 disarms; pint_debug_fail_allocation)."""
+    return int(lib().pint_debug_fail_allocation(int(n)))
 
 
 def set_profiling(on: bool):

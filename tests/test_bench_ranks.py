@@ -11,6 +11,8 @@ import sys
 
 import pytest
 
+import workloads
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 RANK_SCRIPT = r"""
@@ -159,3 +161,17 @@ def test_every_profiled_kernel_has_algorithmic_bytes():
     assert len(names) >= 25
     missing = sorted(n for n in names if bench.algo_bytes(n, 64, 63) <= 0)
     assert not missing, missing
+
+
+def test_oracle_check_of_returned_solutions():
+    # the mix64 / serve lines compare a bounded subset of returned solutions with the oracle
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import grid, sequential
+    p = workloads.small_problem(dim=1, mx=31, N=32, k=2, alpha=0.5, kappa=0.1)
+    ref = sequential.solve_sequential(p.k, p.alpha, p.tau, grid.operator(p), p.v, p.f(), p.fderiv())
+    big = workloads.c2_heat2d()     # N M = 16.6 M: skipped as too large for a bounded CPU run
+    out = bench.oracle_check([(p, ref), (big, None), (p, ref * (1 + 1e-9))])
+    assert out["checked"] == 2
+    assert out["per_problem"][0]["rel_err"] == 0.0
+    assert abs(out["max_rel_err_by_kind"]["1d_cq"] - 1e-9) < 1e-12

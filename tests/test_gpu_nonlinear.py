@@ -134,6 +134,21 @@ def test_nl_solve_reaches_the_sequential_semilinear_solution(kw):
     assert rel_l2(U, ref) <= BAR[prec], (sweeps, upds)
 
 
+def test_nl_solve_at_the_metric_tolerance():
+    """The allencahn1d workload (Example 4 with P1 elements, 1023 nodes, N = 128, alpha = 0.75,
+    CQ-BDF3, kappa = 0.1) at outer tolerance 1e-8 lands within 1e-8 of the oracle's sequential
+    semilinear solution (the outer rule must not stop on the ratio of the first two updates)."""
+    torch = torch_cuda()
+    p = workloads.allen_cahn_problem("fem", mx=1023, N=128, k=3, alpha=0.75, kappa=0.1, T=0.4, eps=1.0,
+                                     data="example4")
+    Mass, A, w = oracle_ops(p)
+    Fo = nl.nl_rhs(p.k, p.alpha, p.tau, Mass, A, w, p.g, p.v, p.f(), p.fderiv())
+    ref = nl.solve_sequential_nl(p.k, p.alpha, p.tau, Mass, A, w, p.g, Fo)
+    U, (st, sweeps, upds) = run_nl(p, "mixed", torch, newton_tol=1e-8, tol=1e-10)
+    assert st == 0 and len(sweeps) >= 3, (sweeps, upds)
+    assert rel_l2(U, ref) <= 1e-8, (sweeps, upds)
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_nl_outer_iterates_follow_algorithm3(prec):
     # the first outer steps of Algorithm 3 (inner WR converged far below the outer change) against

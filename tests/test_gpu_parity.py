@@ -101,6 +101,11 @@ def test_config_c1_heat1d():
         assert rel_l2(U, ref) <= bar, (prec, sweeps, upd)
 
 
+def per_level_rel(U, ref):
+    """Relative l2 error of each time level (row n-1 = level t_n)."""
+    return np.linalg.norm(U - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+
+
 def test_config_c2_heat2d_full():
     """2D heat 255x255, N=256, BDF4 with corrections, kappa=0.05: full comparison."""
     torch = torch_cuda()
@@ -112,6 +117,10 @@ def test_config_c2_heat2d_full():
         assert rel_l2(U, ref) <= bar, (prec, sweeps, upd)
         # final-time error (the paper's e_m^N metric)
         assert np.linalg.norm(U[-1] - ref[-1]) <= bar * np.linalg.norm(ref[-1])
+        # every level on its own (an error confined to early levels, where the starting
+        # corrections act, cannot hide under the norm of all 256 levels)
+        lev = per_level_rel(U, ref)
+        assert lev.max() <= 10 * bar, (prec, int(lev.argmax()), float(lev.max()))
 
 
 def test_config_c3_subdiffusion_full():
@@ -123,6 +132,8 @@ def test_config_c3_subdiffusion_full():
         U, st, sweeps, upd = gpu_solve(p, torch, prec, tol=1e-9)
         assert st == 0
         assert rel_l2(U, ref) <= bar, (prec, sweeps, upd)
+        lev = per_level_rel(U, ref)
+        assert lev.max() <= 10 * bar, (prec, int(lev.argmax()), float(lev.max()))
 
 
 def test_fp32_floor_reported():

@@ -180,6 +180,16 @@ def c4_batch(n: int = 64, seed: int = 2, axis=C4_AXIS, Ns=C4_N) -> list[Problem]
     return [c4_draw(rng, i, axis, Ns) for i in range(n)]
 
 
+def c4_problem(dim: int, m: int, N: int, k: int, alpha: float, kappa: float, seed: int = 2) -> Problem:
+    """One problem of the batch distribution with its parameters fixed instead of drawn (for
+    parity cases at chosen corners of the distribution): v a 16 (x 16)-mode sine series from
+    default_rng(seed), f = e^{-t} sin(pi x) [sin(2 pi y)], T = 1."""
+    rng = np.random.default_rng(seed)
+    v = random_v(dim, m, m, 16, rng)
+    return make_problem(f"c4_{dim}d_{m}_N{N}_k{k}_a{alpha}_kap{kappa}", dim, m, m, N, k, alpha, kappa, 1.0, v,
+                        "exp", mode_field(dim, m, m, 1, 2))
+
+
 def c5_arrivals(n: int, rate: float = 200.0, seed: int = 3, axis=C4_AXIS, Ns=C4_N):
     """Poisson arrival stream: (arrival time in s, Problem) pairs, exponential
     inter-arrival times with mean 1/rate, problems drawn from the batch distribution."""
