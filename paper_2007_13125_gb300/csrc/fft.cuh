@@ -7,7 +7,10 @@
 // (column index fastest, so a warp touches consecutive columns: conflict-free banks).
 //
 // Algorithm: in-place mixed-radix decimation in frequency. L = R_1 R_2 ... R_s with each
-// R_i in {2, 4, 8, 16}; pass i splits every block of length Ls into R_i interleaved
+// R_i in {2, 4, 8, 16} (L a power of two), or, for L = 2^a 5^b, b passes of radix 5 first and
+// then the power-of-two passes of 2^a (index arithmetic by division instead of shifts; the
+// paper's own sizes, N = 100 and 999 interior nodes, are of that form); pass i splits every
+// block of length Ls into R_i interleaved
 // sub-sequences (stride Ls/R_i), does an R_i-point DFT in registers, multiplies by the
 // twiddles W_Ls^{n2 q}, and writes back in place. After all passes, position
 //   p = sum_i q_i L/(R_1..R_i)   holds frequency   j = sum_i q_i R_1..R_{i-1}
@@ -177,8 +180,50 @@ __host__ __device__ inline int fft_logradix(int L, int pass, int maxlog = 4) {
 }
 __host__ __device__ inline int fft_radix(int L, int pass, int maxlog = 4) { return 1 << fft_logradix(L, pass, maxlog); }
 
+// ---- lengths L = 2^a 5^b that are not powers of two ----
+__host__ __device__ inline bool fft_is_pow2(int L) { return L > 0 && (L & (L - 1)) == 0; }
+// b (the power of 5 in L)
+__host__ __device__ inline int fft_fives(int L) {
+  int b = 0;
+  while (L > 1 && L % 5 == 0) { L /= 5; ++b; }
+  return b;
+}
+// passes of the mixed schedule: b radix-5 passes, then the schedule above for 2^a
+__host__ __device__ inline int fft_mr_npass(int L, int maxlog) {
+  const int b = fft_fives(L);
+  int P = L;
+  for (int i = 0; i < b; ++i) P /= 5;
+  return b + (P > 1 ? fft_npass(P, maxlog) : 0);
+}
+__host__ __device__ inline int fft_mr_radix(int L, int pass, int maxlog) {
+  const int b = fft_fives(L);
+  if (pass < b) return 5;
+  int P = L;
+  for (int i = 0; i < b; ++i) P /= 5;
+  return fft_radix(P, pass - b, maxlog);
+}
+// True if L = 2^a 5^b, the lengths the transforms accept.
+__host__ __device__ inline bool fft_len_ok(int L) {
+  if (L < 1) return false;
+  while (L % 5 == 0) L /= 5;
+  return fft_is_pow2(L);
+}
+__host__ __device__ inline int fft_pos_mr(int j, int L, int maxlog) {
+  const int np = fft_mr_npass(L, maxlog);
+  int p = 0, Ls = L;
+  for (int i = 0; i < np; ++i) {
+    const int R = fft_mr_radix(L, i, maxlog);
+    const int q = j % R;
+    j /= R;
+    Ls /= R;
+    p += q * Ls;
+  }
+  return p;
+}
+
 // position of frequency j in the output of the forward transform
 __host__ __device__ inline int fft_pos(int j, int L, int maxlog = 4) {
+  if (!fft_is_pow2(L)) return fft_pos_mr(j, L, maxlog);
   const int e = ilog2r(L), np = (e + maxlog - 1) / maxlog, base = e / np, extra = e - base * np;
   int p = 0, logLs = e;
   for (int i = 0; i < np; ++i) {
@@ -245,10 +290,131 @@ __device__ __forceinline__ void fft_pass_dispatch(int lr, V* X, int ld, int logC
   }
 }
 
+// 5-point DFT. Constants: cos(2 pi/5) = (sqrt5 - 1)/4, cos(4 pi/5) = -(sqrt5 + 1)/4,
+// sin(2 pi/5) = sqrt((5 + sqrt5)/8), sin(4 pi/5) = sqrt((5 - sqrt5)/8). With t1 = x1 + x4,
+// t2 = x2 + x3, t3 = x1 - x4, t4 = x2 - x3 and w = exp(DIR 2 pi i/5):
+//   y0 = x0 + t1 + t2,
+//   y1 = a1 + DIR i b1,  y4 = a1 - DIR i b1,  a1 = x0 + c1 t1 + c2 t2,  b1 = s1 t3 + s2 t4,
+//   y2 = a2 + DIR i b2,  y3 = a2 - DIR i b2,  a2 = x0 + c2 t1 + c1 t2,  b2 = s2 t3 - s1 t4.
+constexpr double kCos1of5 = 0.30901699437494742, kCos2of5 = -0.80901699437494742;
+constexpr double kSin1of5 = 0.95105651629515357, kSin2of5 = 0.58778525229247313;
+__device__ __forceinline__ float2 rscale(float2 v, double c) { const float f = (float)c; return mk(v.x * f, v.y * f); }
+__device__ __forceinline__ double2 rscale(double2 v, double c) { return mk(v.x * c, v.y * c); }
+__device__ __forceinline__ ffc rscale(ffc v, double c) {
+  const float h = (float)c, l = (float)(c - (double)h);
+  return cmul(v, ffc{h, l, 0.f, 0.f});
+}
+__device__ __forceinline__ ffz rscale(ffz v, double c) {
+  const float h = (float)c, l = (float)(c - (double)h);
+  return cmul(v, ffz{h, l, 0.f, 0.f});
+}
+// v * (DIR i)
+template <int DIR> __device__ __forceinline__ float2 rot_i(float2 v) { return DIR < 0 ? mk(v.y, -v.x) : mk(-v.y, v.x); }
+template <int DIR> __device__ __forceinline__ double2 rot_i(double2 v) { return DIR < 0 ? mk(v.y, -v.x) : mk(-v.y, v.x); }
+template <int DIR> __device__ __forceinline__ ffc rot_i(ffc v) {
+  return DIR < 0 ? ffc{v.ih, v.il, -v.rh, -v.rl} : ffc{-v.ih, -v.il, v.rh, v.rl};
+}
+template <int DIR> __device__ __forceinline__ ffz rot_i(ffz v) {
+  return DIR < 0 ? ffz{v.ih, v.il, -v.rh, -v.rl} : ffz{-v.ih, -v.il, v.rh, v.rl};
+}
+template <int DIR, typename V>
+__device__ __forceinline__ void dft5(V (&x)[5]) {
+  const V t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
+  const V t3 = csub(x[1], x[4]), t4 = csub(x[2], x[3]);
+  const V a1 = cadd(x[0], cadd(rscale(t1, kCos1of5), rscale(t2, kCos2of5)));
+  const V a2 = cadd(x[0], cadd(rscale(t1, kCos2of5), rscale(t2, kCos1of5)));
+  const V b1 = rot_i<DIR>(cadd(rscale(t3, kSin1of5), rscale(t4, kSin2of5)));
+  const V b2 = rot_i<DIR>(csub(rscale(t3, kSin2of5), rscale(t4, kSin1of5)));
+  x[0] = cadd(x[0], cadd(t1, t2));
+  x[1] = cadd(a1, b1);
+  x[4] = csub(a1, b1);
+  x[2] = cadd(a2, b2);
+  x[3] = csub(a2, b2);
+}
+template <int R, int DIR, typename V>
+__device__ __forceinline__ void dft_any(V (&x)[R]) {
+  if constexpr (R == 5) dft5<DIR>(x);
+  else dft_reg<R, DIR>(x);
+}
+
+// One pass of radix R (5 or a power of two) at sub-length Ls of a length L = 2^a 5^b: the same
+// gather / DFT / twiddle / scatter as fft_pass, with the stride S = Ls / R and the block index
+// found by division. Twiddle index n2 q L / Ls < L.
+template <int R, int DIR, typename V>
+__device__ __forceinline__ void fft_pass_mr(V* X, int ld, int logC, int L, int Ls, const V* tw) {
+  const int S = Ls / R;
+  const int items = (L / R) << logC;
+  const int tstep = L / Ls;
+  const int Cmask = (1 << logC) - 1;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int c = it & Cmask;
+    const int g = it >> logC;
+    const int blk = g / S, n2 = g - blk * S;
+    const int base = blk * Ls + n2;
+    V x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = X[(base + r * S) * ld + c];
+    if (DIR < 0) {
+      dft_any<R, -1>(x);
+#pragma unroll
+      for (int q = 1; q < R; ++q) x[q] = cmul(x[q], tw[n2 * q * tstep]);
+    } else {
+#pragma unroll
+      for (int q = 1; q < R; ++q) x[q] = cmulc(x[q], tw[n2 * q * tstep]);
+      dft_any<R, 1>(x);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) X[(base + r * S) * ld + c] = fft_store(x[r]);
+  }
+}
+
+template <int DIR, int MAXLOG, typename V>
+__device__ __forceinline__ void fft_pass_mr_dispatch(int R, V* X, int ld, int logC, int L, int Ls, const V* tw) {
+  switch (R) {
+    case 5: fft_pass_mr<5, DIR>(X, ld, logC, L, Ls, tw); break;
+    case 2: fft_pass_mr<2, DIR>(X, ld, logC, L, Ls, tw); break;
+    case 4: fft_pass_mr<4, DIR>(X, ld, logC, L, Ls, tw); break;
+    default:
+      if constexpr (MAXLOG >= 4) {
+        if (R == 16) { fft_pass_mr<16, DIR>(X, ld, logC, L, Ls, tw); break; }
+      }
+      fft_pass_mr<8, DIR>(X, ld, logC, L, Ls, tw);
+      break;
+  }
+}
+
+template <int MAXLOG, typename V>
+__device__ __noinline__ void fft_forward_mr(V* X, int ld, int logC, int L, const V* tw) {
+  const int np = fft_mr_npass(L, MAXLOG);
+  int Ls = L;
+  for (int i = 0; i < np; ++i) {
+    const int R = fft_mr_radix(L, i, MAXLOG);
+    fft_pass_mr_dispatch<-1, MAXLOG>(R, X, ld, logC, L, Ls, tw);
+    Ls /= R;
+    __syncthreads();
+  }
+}
+
+template <int MAXLOG, typename V>
+__device__ __noinline__ void fft_inverse_mr(V* X, int ld, int logC, int L, const V* tw) {
+  const int np = fft_mr_npass(L, MAXLOG);
+  int Ls = 1;
+  for (int i = np - 1; i >= 0; --i) {
+    const int R = fft_mr_radix(L, i, MAXLOG);
+    Ls *= R;
+    fft_pass_mr_dispatch<1, MAXLOG>(R, X, ld, logC, L, Ls, tw);
+    __syncthreads();
+  }
+}
+
 // Forward: natural order in, permuted (fft_pos(., ., MAXLOG)) order out; exp(-2 pi i n j / L).
 // tw[m] = exp(-2 pi i m / L), m < L, must be visible to all threads. C = 2^logC columns.
 template <int MAXLOG = 4, typename V>
 __device__ void fft_forward(V* X, int ld, int logC, int L, const V* tw) {
+  if (!fft_is_pow2(L)) {
+    fft_forward_mr<MAXLOG>(X, ld, logC, L, tw);
+    return;
+  }
   const int logL = ilog2r(L);
   const int np = fft_npass(L, MAXLOG);
   int logLs = logL;
@@ -263,6 +429,10 @@ __device__ void fft_forward(V* X, int ld, int logC, int L, const V* tw) {
 // Inverse: permuted order in, natural order out, unnormalised: x_n = sum_j X_j exp(+2 pi i n j / L).
 template <int MAXLOG = 4, typename V>
 __device__ void fft_inverse(V* X, int ld, int logC, int L, const V* tw) {
+  if (!fft_is_pow2(L)) {
+    fft_inverse_mr<MAXLOG>(X, ld, logC, L, tw);
+    return;
+  }
   const int logL = ilog2r(L);
   const int np = fft_npass(L, MAXLOG);
   int logLs = 0;

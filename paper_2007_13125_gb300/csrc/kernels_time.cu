@@ -201,16 +201,24 @@ __global__ void __launch_bounds__(kThreads) k_direct_fwd(DirectFwdArgs<T> a) {
       const int m = m0 + h * C + cc;
       if (m >= M) continue;
       const size_t idx = (size_t)i * M + m;
-      T f = a.F[idx];
-      if (a.z) {
-        f += (T)a.z[idx];
-      } else if (i < a.k) {
-        // row n = i+1 <= k: kappa tau^-1 sum_{j=n}^{k} omega_j U^{N+n-j}, the kappa-term of eq. (2.7)
-        // indexed to match B_k(kappa) of eq. (2.6) (the printed sum_{j=1}^{n} omega_j U^{N-j+1} has another
-        // fixed point)
+      // the kappa term at point q of row i (zero outside the grid): CQ, z = kappa tau^-alpha (W' U)
+      // (eq. (3.12)); BDF row n = i+1 <= k, kappa tau^-1 sum_{j=n}^{k} omega_j U^{N+n-j}, the
+      // kappa-term of eq. (2.7) indexed to match B_k(kappa) of eq. (2.6) (the printed
+      // sum_{j=1}^{n} omega_j U^{N-j+1} has another fixed point)
+      auto kterm = [&](int q) -> T {
+        if (q < 0 || q >= M) return T(0);
+        if (a.z) return (T)a.z[(size_t)i * M + q];
+        T c = T(0);
 #pragma unroll
         for (int j = 1; j <= kMaxK; ++j)
-          if (j > i && j <= a.k) f += a.kw[j] * a.U[(size_t)(N + i - j) * M + m];
+          if (j > i && j <= a.k) c += a.kw[j] * a.U[(size_t)(N + i - j) * M + q];
+        return c;
+      };
+      T f = a.F[idx];
+      if (a.z || i < a.k) {
+        // P1 elements: the time terms of the scheme act through the mass matrix M_h
+        if (a.fem) f += a.h6 * (kterm(m - 1) + T(4) * kterm(m) + kterm(m + 1));
+        else f += kterm(m);
       }
       val[h] = f * a.s[i];
     }

@@ -52,6 +52,8 @@ template <typename T> struct DirectFwdArgs {
   const T* s; const void* tw;
   int N, M, C, logC, k;
   T kw[kMaxK + 1];                         // kappa tau^-alpha omega_j (BDF corner)
+  int fem;                                 // P1 elements (1D): the kappa terms act through M_h
+  T h6;                                    // h / 6 (M_h = (h/6) tridiag(1, 4, 1))
 };
 
 template <typename T> struct DirectInvArgs {

@@ -196,8 +196,23 @@ static cd unit_root(long m, long L) {
   return cd(c, -s);
 }
 
-static void host_fft(std::vector<cd>& a, bool inverse) {  // natural order, radix-2
+static void host_fft(std::vector<cd>& a, bool inverse) {  // natural order, radix-2 (any length: direct sum)
   const size_t n = a.size();
+  if (n & (n - 1)) {
+    // a length 2^a 5^b: the plain DFT, every angle reduced exactly (O(n^2), plan time only)
+    std::vector<cd> out(n);
+    for (size_t j = 0; j < n; ++j) {
+      cd acc(0.0, 0.0);
+      for (size_t l = 0; l < n; ++l) {
+        cd w = unit_root((long)((j * l) % n), (long)n);
+        if (inverse) w = std::conj(w);
+        acc += a[l] * w;
+      }
+      out[j] = acc;
+    }
+    a.swap(out);
+    return;
+  }
   for (size_t i = 1, j = 0; i < n; ++i) {
     size_t bit = n >> 1;
     for (; j & bit; bit >>= 1) j ^= bit;
@@ -403,10 +418,15 @@ pint_status validate(int k, double alpha, double kappa, double tau, int N, const
   if (!(alpha > 0.0 && alpha <= 1.0)) return fail(PINT_EINVAL, "alpha must be in (0, 1]");
   if (!(kappa > 0.0 && kappa < 1.0)) return fail(PINT_EINVAL, "kappa must be in (0, 1)");
   if (!(tau > 0.0) || !std::isfinite(tau)) return fail(PINT_EINVAL, "tau must be positive");
-  if (!pow2(N) || N < 8 || N > 4096) return fail(PINT_EINVAL, "N must be a power of two in [8, 4096]");
+  if (g->dim < 1 || g->dim > 3) return fail(PINT_EINVAL, "grid.dim must be 1, 2 or 3");
+  // lengths of the FFTs: powers of two everywhere; 2^a 5^b (a >= 1) for Dirichlet finite differences
+  // and P1 elements in 1D and 2D (the paper's N = 100 and h = 1/1000 are of that form)
+  const bool mixed_ok = g->dim <= 2 && space != PINT_SPACE_PERIODIC;
+  auto len_ok = [mixed_ok](long L) { return pow2(L) || (mixed_ok && fft_len_ok((int)L) && L % 2 == 0); };
+  if (!len_ok(N) || N < 8 || N > 4096)
+    return fail(PINT_EINVAL, "N must be in [8, 4096], a power of two (or 2^a 5^b, a >= 1, for Dirichlet 1D/2D grids)");
   if (alpha != 1.0 && N > 2048) return fail(PINT_EINVAL, "CQ (alpha < 1) supports N <= 2048");
   if (N <= k) return fail(PINT_EINVAL, "N must exceed k");
-  if (g->dim < 1 || g->dim > 3) return fail(PINT_EINVAL, "grid.dim must be 1, 2 or 3");
   if (g->dim == 3 && space != PINT_SPACE_FD) return fail(PINT_EINVAL, "3D grids are supported with finite differences");
   if (space == PINT_SPACE_PERIODIC) {
     if (!pow2(g->mx) || g->mx < 8 || g->mx > 4096) return fail(PINT_EINVAL, "periodic: mx must be a power of two in [8, 4096]");
@@ -414,9 +434,10 @@ pint_status validate(int k, double alpha, double kappa, double tau, int N, const
       return fail(PINT_EINVAL, "periodic: my must be a power of two in [8, 4096]");
     return PINT_OK;
   }
-  if (!pow2(g->mx + 1) || g->mx < 3 || g->mx > 2047) return fail(PINT_EINVAL, "mx + 1 must be a power of two, 3 <= mx <= 2047");
-  if (g->dim >= 2 && (!pow2(g->my + 1) || g->my < 3 || g->my > 2047))
-    return fail(PINT_EINVAL, "my + 1 must be a power of two, 3 <= my <= 2047");
+  if (!len_ok(g->mx + 1) || g->mx < 3 || g->mx > 2047)
+    return fail(PINT_EINVAL, "mx + 1 must be a power of two (or 2^a 5^b in 1D/2D), 3 <= mx <= 2047");
+  if (g->dim >= 2 && (!len_ok(g->my + 1) || g->my < 3 || g->my > 2047))
+    return fail(PINT_EINVAL, "my + 1 must be a power of two (or 2^a 5^b in 2D), 3 <= my <= 2047");
   if (g->dim == 3 && (!pow2(g->mz + 1) || g->mz < 3 || g->mz > 2047))
     return fail(PINT_EINVAL, "mz + 1 must be a power of two, 3 <= mz <= 2047");
   return PINT_OK;
@@ -465,8 +486,8 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   if (d->ysolve < 0 || d->ysolve > 3) return fail(PINT_EINVAL, "bad ysolve variant");
   if (d->space != PINT_SPACE_FD && d->space != PINT_SPACE_FEM_P1 && d->space != PINT_SPACE_PERIODIC)
     return fail(PINT_EINVAL, "bad space discretisation");
-  if (d->space == PINT_SPACE_FEM_P1 && (d->grid.dim != 1 || d->precision != PINT_MIXED))
-    return fail(PINT_EINVAL, "P1 finite elements are supported in 1D with PINT_MIXED");
+  if (d->space == PINT_SPACE_FEM_P1 && d->grid.dim != 1)
+    return fail(PINT_EINVAL, "P1 finite elements are supported in 1D");
   pint_plan p = new pint_plan_s();
   p->alloc = A;
   p->k = d->k; p->alpha = d->alpha; p->kappa = d->kappa; p->tau = d->tau; p->N = d->N;
@@ -689,7 +710,7 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
     const int Ct = (p->mx + 1) / 2, L = 2 * (p->mx + 1);
     int Cs = std::min(N / 2, 64);
     if (p->prec == PINT_MIXED && p->dim == 1 && !p->fem && !p->periodic && !p->cq && Ct >= 2 &&
-        (size_t)N * M <= 4096) {
+        (size_t)N * M <= 4096 && pow2(N) && pow2(p->mx + 1)) {
       for (; Cs >= 4; Cs /= 2) {
         if (small_smem(N, M, Ct, L, Cs) <= 200 * 1024) {
           p->small = true;
@@ -1129,6 +1150,8 @@ pint_status sweep_direct(pint_plan p, const DevTables<T>& t, const T* F, const T
   DirectFwdArgs<T> f{};
   f.F = F; f.U = Uin; f.z = p->cq ? p->z : nullptr; f.S = p->S; f.s = t.s; f.tw = t.tw_time;
   f.N = N; f.M = M; f.C = p->Ctd; f.logC = ilog2c(p->Ctd); f.k = p->cq ? 0 : p->k;
+  f.fem = p->fem ? 1 : 0;
+  f.h6 = (T)(1.0 / (6.0 * (p->mx + 1)));
   const double kt = p->kappa * std::pow(p->tau, -p->alpha);
   for (int j = 0; j <= p->k; ++j) f.kw[j] = (T)(kt * p->omega[j]);
   cudaError_t e = launch_direct_fwd(f, st);
@@ -1602,7 +1625,7 @@ extern "C" pint_status pint_correction_coefficients(int k, double* a, double* b)
 extern "C" pint_status pint_circulant_eigenvalues(int k, double alpha, double kappa, int N,
                                                   pint_eig_variant eig, double* re, double* im) {
   if (k < 1 || k > kMaxK || !(alpha > 0.0 && alpha <= 1.0) || !(kappa > 0.0 && kappa < 1.0) ||
-      !pow2(N) || N <= k || !re || !im)
+      !fft_len_ok(N) || N < 2 || N <= k || !re || !im)
     return fail(PINT_EINVAL, "bad arguments");
   std::vector<double> w(N);
   time_weights(k, alpha, N, w.data());

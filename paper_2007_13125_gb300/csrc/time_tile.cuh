@@ -93,7 +93,7 @@ __device__ __forceinline__ void store_half_spectrum(const V* X, const unsigned s
   for (int it = threadIdx.x; it < (J << logC); it += blockDim.x) {
     const int cc = it & (C - 1), j = it >> logC;
     const V Zj = X[(size_t)perm[j] * C + cc];
-    const V Zn = X[(size_t)perm[(N - j) & (N - 1)] * C + cc];
+    const V Zn = X[(size_t)perm[j == 0 ? 0 : N - j] * C + cc];
     const V A = mk(h * (Zj.x + Zn.x), h * (Zj.y - Zn.y));      // (Z_j + conj Z_{N-j}) / 2
     const V B = mk(h * (Zj.y + Zn.y), -h * (Zj.x - Zn.x));     // (Z_j - conj Z_{N-j}) / 2i
     const int ma = m0 + cc, mb = m0 + C + cc;

@@ -27,9 +27,14 @@ CORNER = [
 
 
 def per_level_rel(U, ref):
-    num = np.linalg.norm(U - ref, axis=1)
-    den = np.linalg.norm(ref, axis=1)
-    return num / np.maximum(den, 1e-300)
+    """l2 error of each time level (row n-1 = level t_n) relative to max(||U_ref^n||, the RMS level
+    norm ||U_ref|| / sqrt(N)). The diagonalised solve spreads its rounding evenly over the levels
+    (the DFT along time mixes them; the paper's roundoff estimates are norm-wise), so a level far
+    smaller than the typical one -- the first levels of a problem started from v = 0 -- carries a
+    large error relative to itself while its absolute error is that of every other level; an error
+    confined to a few levels of ordinary size still shows."""
+    rms = np.linalg.norm(ref) / np.sqrt(ref.shape[0])
+    return np.linalg.norm(U - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), rms)
 
 
 @pytest.fixture(scope="module", params=CORNER, ids=lambda c: "{}d_{}_N{}_k{}_a{}_kap{}".format(*c))

@@ -102,8 +102,14 @@ def test_config_c1_heat1d():
 
 
 def per_level_rel(U, ref):
-    """Relative l2 error of each time level (row n-1 = level t_n)."""
-    return np.linalg.norm(U - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+    """l2 error of each time level (row n-1 = level t_n) relative to max(||U_ref^n||, the RMS level
+    norm ||U_ref|| / sqrt(N)). The diagonalised solve spreads its rounding evenly over the levels
+    (the DFT along time mixes them; the paper's roundoff estimates are norm-wise), so a level far
+    smaller than the typical one -- the first levels of a problem started from v = 0 -- carries a
+    large error relative to itself while its absolute error is that of every other level; an error
+    confined to a few levels of ordinary size still shows."""
+    rms = np.linalg.norm(ref) / np.sqrt(ref.shape[0])
+    return np.linalg.norm(U - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), rms)
 
 
 def test_config_c2_heat2d_full():
@@ -230,7 +236,26 @@ def test_invalid_arguments_rejected():
     from paper_2007_13125_gb300 import Plan, PintError
     for args in [(0, 1.0, 0.1, 0.01, 64, 1, 63), (2, 1.5, 0.1, 0.01, 64, 1, 63),
                  (2, 1.0, 1.0, 0.01, 64, 1, 63), (2, 1.0, 0.1, -1.0, 64, 1, 63),
-                 (2, 1.0, 0.1, 0.01, 100, 1, 63), (2, 1.0, 0.1, 0.01, 64, 1, 64),
+                 (2, 1.0, 0.1, 0.01, 96, 1, 63), (2, 1.0, 0.1, 0.01, 64, 1, 64),
                  (2, 0.5, 0.1, 0.01, 4096, 1, 63)]:
         with pytest.raises(PintError):
             Plan(*args)
+
+
+@pytest.mark.parametrize("case", [
+    # lengths 2^a 5^b: the time FFT (N) and / or the sine transforms (2 (m + 1)) take radix-5 passes
+    (1, 99, 100, 3, 1.0, 0.1),      # N = 100, L = 200
+    (1, 999, 100, 2, 0.5, 0.1),     # CQ: 2N = 200, L = 2000
+    (1, 127, 40, 4, 1.0, 0.05),     # N = 40 only
+    (1, 49, 64, 6, 1.0, 0.1),       # L = 100 only
+    (2, 49, 20, 3, 1.0, 0.1),       # 2D, both
+    (2, 39, 80, 2, 0.7, 0.1),       # 2D CQ, L = 80, N = 80
+])
+def test_radix5_sizes(case):
+    torch = torch_cuda()
+    p = _p(*case)
+    ref = oracle_solution(p)
+    for prec, bar in (("fp64", 1e-10), ("mixed", 1e-8)):
+        U, st, sweeps, upd = gpu_solve(p, torch, prec, tol=bar)
+        assert st == 0, (case, prec)
+        assert rel_l2(U, ref) <= bar, (case, prec, sweeps)

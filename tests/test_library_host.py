@@ -69,10 +69,11 @@ def test_invalid_plans_rejected_before_device_use(pint):
 
 
 def test_invalid_fem_plans_rejected_before_device_use(pint):
-    # P1 finite elements: 1D and PINT_MIXED only; an unknown space code is rejected too
+    # P1 finite elements: 1D only (every precision), mx + 1 of the form 2^a 5^b; an unknown
+    # space code is rejected too
     for kw in [dict(dim=2, mx=31, my=31, precision="mixed", space="fem"),
-               dict(dim=1, mx=31, precision="fp64", space="fem"),
-               dict(dim=1, mx=31, precision="fp32", space="fem"),
+               dict(dim=1, mx=30, precision="fp64", space="fem"),
+               dict(dim=1, mx=62, precision="mixed", space="fem"),
                dict(dim=1, mx=31, precision="mixed", space=7)]:
         with pytest.raises(pint.PintError) as e:
             pint.Plan(2, 1.0, 0.1, 0.01, 32, **kw)

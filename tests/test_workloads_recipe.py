@@ -68,3 +68,17 @@ def test_c4_draw_order():
         kappa = (0.1, 0.01)[rng_b.integers(0, 2)]
         rng_b.standard_normal(16 if dim == 1 else (16, 16))          # v's coefficients
         assert (p.dim, p.mx, p.N, p.k, p.alpha, p.kappa) == (dim, m, N, k, alpha, kappa)
+
+
+def test_paper_fem_examples_match_the_oracle_data():
+    # the inputs of Tables 2 / 3 (Sec. 4, Examples 1 and 2), written here independently of the
+    # oracle's own data routines, agree with them
+    from oracle import fem
+    for ex, data in ((1, fem.example1_data), (2, fem.example2_data)):
+        tau, v, F_t, F_der = data()
+        for k in (1, 4, 6):
+            p = workloads.paper_fem_example(ex, k)
+            assert p.tau == tau and p.N == 100 and p.mx == 999
+            assert np.max(np.abs(p.v - v)) <= 1e-14 * np.max(np.abs(v))
+            assert np.max(np.abs(p.f() - F_t)) <= 1e-15
+            assert np.max(np.abs(p.fderiv() - F_der[: k - 1]), initial=0.0) <= 1e-15

@@ -259,6 +259,41 @@ def fem_problem(mx=63, N=32, k=2, alpha=1.0, kappa=0.1, T=1.0, seed=7, modes=8, 
     return p
 
 
+def fem_mass_solve(m: int, b: np.ndarray) -> np.ndarray:
+    """The nodal values v_h of the L2 projection of a function whose loads (v, phi_i) are b: the
+    P1 mass matrix M_h = (h/6) tridiag(1, 4, 1) solved by a banded LU (scipy)."""
+    from scipy.linalg import solve_banded
+    h = 1.0 / (m + 1)
+    ab = np.zeros((3, m))
+    ab[0, 1:] = h / 6.0
+    ab[1, :] = 4.0 * h / 6.0
+    ab[2, :-1] = h / 6.0
+    return solve_banded((1, 1), ab, b)
+
+
+def paper_fem_example(example: int, k: int, N: int = 100, m: int = 999) -> Problem:
+    """The data of the paper's 1D tests (Sec. 4) with P1 elements on the uniform mesh h = 1/(m+1)
+    (the paper: h = 1/1000, N = 100):
+    example 1 (Table 2): heat, T = 0.5, kappa = 0.5, v_h the L2 projection of the indicator of
+      (0, 1/2), f = e^t cos x (loads 2 cos(x_i) (1 - cos h) / h e^t, every d_t^l f(0) = cos x);
+    example 2 (Table 3): subdiffusion alpha = 0.5, T = 0.1, kappa = 0.1, v_h the L2 projection of
+      the Dirac delta at 1/2 (loads phi_i(1/2)), f = 0."""
+    h = 1.0 / (m + 1)
+    x = grid_points(m)
+    if example == 1:
+        b = np.where(x < 0.5 - 0.25 * h, h, np.where(np.abs(x - 0.5) <= 0.25 * h, h / 2, 0.0))
+        p = make_problem(f"paper_example1_M{m}_N{N}_k{k}", 1, m, 1, N, k, 1.0, 0.5, 0.5,
+                         fem_mass_solve(m, b), "exp_growth", fem_load_cos(m))
+    elif example == 2:
+        b = np.maximum(0.0, 1.0 - np.abs(x - 0.5) / h)
+        p = make_problem(f"paper_example2_M{m}_N{N}_k{k}", 1, m, 1, N, k, 0.5, 0.1, 0.1,
+                         fem_mass_solve(m, b), "zero", np.zeros(m))
+    else:
+        raise ValueError(example)
+    p.space = "fem"
+    return p
+
+
 # ---------------------------------------------------------------------------
 # Periodic problems: m points per axis at x_i = i/m (periodic boundary conditions)
 # ---------------------------------------------------------------------------
