@@ -111,9 +111,13 @@ typedef struct {
   pint_precision precision;
   pint_eig_variant eig;
   int ysolve;             /* 2D y-direction solver of the shifted systems: 0 or 1 = sine transform
-                             (default), 2 = tridiagonal (FP32 inner solves only; FP64 uses 1),
-                             3 = whichever of 1 and 2 runs faster on this GPU, timed at plan
-                             creation (cached per shape). The sine transform is the default: its
+                             (default), 2 = tridiagonal by a thread-per-line recurrence (for
+                             batches of many lines), 4 = tridiagonal by parallel cyclic reduction
+                             (parallel within a line: one warp per line up to 32 rows, the whole
+                             CTA on a line up to 1024 rows, for batches of few lines; my <= 1024,
+                             else 1), 3 = whichever of 1, 2 and 4 runs fastest on this GPU, timed
+                             at plan creation (cached per shape). 2 and 4 apply to FP32 inner
+                             solves only (FP64 uses 1). The sine transform is the default: its
                              FP32 inner solves are more accurate (the tridiagonal recurrences
                              amplify rounding with the condition of the line systems), which
                              saves a sweep at tol 1e-8 on a 255 x 255, N = 256 heat problem */

@@ -22,11 +22,21 @@ namespace pint {
 // stencil centre need error-free products.
 // ---------------------------------------------------------------------------
 
-// level groups of a residual tile: up to kThreads / 2C, each with at least 4 levels
+// level groups of a residual tile: up to kThreads / 2C, each with at least 4 levels, and a divisor
+// of N (N = 2^a 5^b: a power of two up to 2^a)
 __host__ __device__ inline int resid_groups(int N, int C) {
   int g = kThreads / (2 * C);
-  while (g > 1 && N / g < 4) g >>= 1;
+  while (g > 1 && (N / g < 4 || N % g != 0)) g >>= 1;
   return g;
+}
+
+// A += g b with the product's rounding error kept: exact by itself when g is a power of two (the
+// stencil weights of grids with m + 1 = 2^a), otherwise the error (one fma) joins the low part.
+// `exact` is uniform over the launch.
+__device__ __forceinline__ void add_prod(ff_acc& A, float g, float b, bool exact) {
+  const float p = g * b;
+  A.add_hi(p);
+  if (!exact) A.sl += fmaf(g, b, -p);
 }
 
 size_t resid_fwd_smem(int N, int C) { return time_tile_bytes<float2>(N, C) + 16; }
@@ -192,6 +202,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
       }
     }
     const float gx = a.gx_hi, gy = a.gy_hi, gz = a.gz_hi;
+    const bool gexact = a.g_pow2 != 0;
     // reaction term w c_i U_i^n (1D, the linearised operator of Algorithm 3): one coefficient per point
     const bool react = DIM == 1 && a.react != nullptr;
     const ff rc = (react && valid) ? ff_from_double(a.react[m]) : ff{0.f, 0.f};
@@ -221,11 +232,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
 #pragma unroll
         for (int t = 1; t <= K; ++t) A.fma_term(ff{a.c_hi[t], a.c_lo[t]}, h[t - 1], -1.f);
         // stiffness centre 2/h and neighbours 1/h: powers of two, exact
-        A.add_hi(-2.f * gx * c.uh);
+        add_prod(A, -2.f * gx, c.uh, gexact);
         A.sl = fmaf(-2.f * gx, c.ul, A.sl);
         float bx, ex;
         two_sum(wh, eh, bx, ex);
-        A.add_hi(gx * bx);
+        add_prod(A, gx, bx, gexact);
         A.sl += gx * (ex + (wl + el));
       } else {
         cur = ff{c.uh, c.ul};
@@ -237,18 +248,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
         // neighbours: exact sums, exact power-of-two scaling
         float bx, ex;
         two_sum(wh, eh, bx, ex);
-        A.add_hi(gx * bx);
+        add_prod(A, gx, bx, gexact);
         float lo = gx * (ex + (wl + el));
         if constexpr (DIM >= 2) {
           float by, ey;
           two_sum(c.sh, c.nh, by, ey);
-          A.add_hi(gy * by);
+          add_prod(A, gy, by, gexact);
           lo = fmaf(gy, ey + (c.sl + c.nl), lo);
         }
         if constexpr (DIM == 3) {
           float bz, ez;
           two_sum(c.bh, c.th, bz, ez);
-          A.add_hi(gz * bz);
+          add_prod(A, gz, bz, gexact);
           lo = fmaf(gz, ez + (c.bl + c.tl), lo);
         }
         A.sl += lo;
@@ -303,15 +314,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_v0(ResidFwdArgs a) {
   const ff vw = hasW ? ff_from_double(a.v[m + dW]) : ff{0.f, 0.f};
   const ff ve = hasE ? ff_from_double(a.v[m + dE]) : ff{0.f, 0.f};
   const float gx = a.gx_hi;
+  const bool gexact = a.g_pow2 != 0;
   ff_acc Av;
   Av.init(ff{0.f, 0.f});
   // centre: 2 gx + 2 gy + 2 gz (FD), 2/h (P1 stiffness) -- exact multiples of powers of two
   {
     float b0, e0;
     two_sum(vw.hi, ve.hi, b0, e0);
-    Av.add_hi(2.f * gx * vc.hi);
+    add_prod(Av, 2.f * gx, vc.hi, gexact);
     Av.sl = fmaf(2.f * gx, vc.lo, Av.sl);
-    Av.add_hi(-gx * b0);
+    add_prod(Av, -gx, b0, gexact);
     Av.sl -= gx * (e0 + (vw.lo + ve.lo));
   }
   if constexpr (DIM >= 2) {
@@ -320,9 +332,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_v0(ResidFwdArgs a) {
     const ff vn = hasN ? ff_from_double(a.v[m + dN]) : ff{0.f, 0.f};
     float b1, e1;
     two_sum(vs.hi, vn.hi, b1, e1);
-    Av.add_hi(2.f * gy * vc.hi);
+    add_prod(Av, 2.f * gy, vc.hi, gexact);
     Av.sl = fmaf(2.f * gy, vc.lo, Av.sl);
-    Av.add_hi(-gy * b1);
+    add_prod(Av, -gy, b1, gexact);
     Av.sl -= gy * (e1 + (vs.lo + vn.lo));
   }
   if constexpr (DIM == 3) {
@@ -331,9 +343,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_v0(ResidFwdArgs a) {
     const ff vt = hasT ? ff_from_double(a.v[m + mxy]) : ff{0.f, 0.f};
     float b2, e2;
     two_sum(vb.hi, vt.hi, b2, e2);
-    Av.add_hi(2.f * gz * vc.hi);
+    add_prod(Av, 2.f * gz, vc.hi, gexact);
     Av.sl = fmaf(2.f * gz, vc.lo, Av.sl);
-    Av.add_hi(-gz * b2);
+    add_prod(Av, -gz, b2, gexact);
     Av.sl -= gz * (e2 + (vb.lo + vt.lo));
   }
   if (DIM == 1 && a.react && valid) Av.fma_term(ff_from_double(a.react[m]), vc, 1.f);

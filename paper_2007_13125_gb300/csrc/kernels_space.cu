@@ -654,6 +654,185 @@ cudaError_t launch_tri(const TriArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// k_pcr -- the same constant-coefficient tridiagonal systems along y by parallel cyclic reduction:
+// parallel within a system, for batches of few systems (small grids and few frequencies), where
+// one thread per system leaves the GPU idle. Divided by g, row i is
+//   a_i q_{i-1} + b_i q_i + c_i q_{i+1} = d_i,  a_i = -1 (i > 0), c_i = -1 (i < n-1), b_i = 2 + e,
+// e = (s_j + lambda_p^x) / g. A reduction step of stride s eliminates q_{i-s} and q_{i+s} with rows
+// i - s and i + s (k1 = a_i / b_{i-s}, k2 = c_i / b_{i+s}):
+//   a_i' = -a_{i-s} k1,  c_i' = -c_{i+s} k2,  b_i' = b_i - c_{i-s} k1 - a_{i+s} k2,
+//   d_i' = d_i - d_{i-s} k1 - d_{i+s} k2,
+// rows outside 0..n-1 acting as the identity (a = c = d = 0, b = 1). After the steps s = 1, 2, 4, ...
+// < n every row is decoupled: q_i = d_i / b_i. No pivoting: the rows are those of sigma_j + A_h
+// restricted to one sine mode in x, nonsingular for every frequency.
+// Lines of at most 32 rows: one warp per line, one row per lane, neighbours by warp shuffles. Longer
+// lines (up to 1024 rows): the whole CTA on one line, E rows per thread (row tid + 256 e), neighbours
+// through one shared-memory copy of the coefficients (read, barrier, write, barrier per step).
+// Lines are staged through a [n][C] tile for coalesced loads and stores, as in k_tri.
+// ---------------------------------------------------------------------------
+struct PcrRow { float2 a, b, c, d; };
+
+__device__ __forceinline__ float2 crcp_mul(float2 a, float2 b) {  // a / b
+  const float inv = __frcp_rn(b.x * b.x + b.y * b.y);
+  return make_float2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
+}
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return cfma(a, b, make_float2(0.f, 0.f)); }
+__device__ __forceinline__ float2 csubf(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+__device__ __forceinline__ PcrRow pcr_step(const PcrRow& r, const PcrRow& m, const PcrRow& p) {
+  const float2 k1 = crcp_mul(r.a, m.b), k2 = crcp_mul(r.c, p.b);
+  PcrRow o;
+  o.a = cmulf(make_float2(-m.a.x, -m.a.y), k1);
+  o.c = cmulf(make_float2(-p.c.x, -p.c.y), k2);
+  o.b = csubf(csubf(r.b, cmulf(m.c, k1)), cmulf(p.a, k2));
+  o.d = csubf(csubf(r.d, cmulf(m.d, k1)), cmulf(p.d, k2));
+  return o;
+}
+
+__device__ __forceinline__ PcrRow pcr_identity() {
+  PcrRow r;
+  r.a = r.c = r.d = make_float2(0.f, 0.f);
+  r.b = make_float2(1.f, 0.f);
+  return r;
+}
+
+__device__ __forceinline__ float2 shfl_up2(float2 v, int s) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, s), __shfl_up_sync(0xffffffffu, v.y, s));
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v, int s) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, s), __shfl_down_sync(0xffffffffu, v.y, s));
+}
+
+size_t pcr_smem(int n, int C) {
+  const int E = n <= 32 ? 0 : (n + kThreads - 1) / kThreads;
+  return sizeof(float2) * (size_t)n * C + 2 * sizeof(int) * C + sizeof(PcrRow) * (size_t)kThreads * E;
+}
+
+template <int E>
+__global__ void __launch_bounds__(kThreads) k_pcr(TriArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int n = a.n, C = a.C, logC = a.logC;
+  float2* X = reinterpret_cast<float2*>(smraw);   // [n][C]
+  int* lj = reinterpret_cast<int*>(X + (size_t)n * C);
+  int* lp = lj + C;
+  PcrRow* R = reinterpret_cast<PcrRow*>(lp + C);   // E > 0: [kThreads * E] rows of the current line
+  const int line0 = blockIdx.x * C;
+  for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+    const int line = line0 + cc;
+    lj[cc] = line / a.P;
+    lp[cc] = line - lj[cc] * a.P;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < (n << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), i = it >> logC;
+    float2 v = make_float2(0.f, 0.f);
+    if (line0 + cc < a.lines) v = a.S[((size_t)lj[cc] * n + i) * a.P + lp[cc]];
+    X[(size_t)i * C + cc] = v;
+  }
+  __syncthreads();
+  const float ig = 1.f / a.g;
+  if constexpr (E == 0) {
+    // one warp per line, row = lane
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int cc = warp; cc < C; cc += nwarp) {
+      if (line0 + cc >= a.lines) break;  // warp-uniform
+      const float2 sg = a.sigma[lj[cc]];
+      const float2 b0 = make_float2(2.f + (sg.x + a.lam_x[lp[cc]]) * ig, sg.y * ig);
+      PcrRow r = pcr_identity();
+      if (lane < n) {
+        r.a = make_float2(lane > 0 ? -1.f : 0.f, 0.f);
+        r.c = make_float2(lane < n - 1 ? -1.f : 0.f, 0.f);
+        r.b = b0;
+        r.d = X[(size_t)lane * C + cc];
+      }
+      for (int st = 1; st < n; st <<= 1) {
+        PcrRow m, p;
+        m.a = shfl_up2(r.a, st); m.b = shfl_up2(r.b, st); m.c = shfl_up2(r.c, st); m.d = shfl_up2(r.d, st);
+        p.a = shfl_down2(r.a, st); p.b = shfl_down2(r.b, st); p.c = shfl_down2(r.c, st); p.d = shfl_down2(r.d, st);
+        if (lane < st) m = pcr_identity();
+        if (lane + st >= 32) p = pcr_identity();
+        r = pcr_step(r, m, p);
+      }
+      if (lane < n) {
+        const float2 q = crcp_mul(r.d, r.b);
+        const float f = ig * a.scale;
+        X[(size_t)lane * C + cc] = make_float2(q.x * f, q.y * f);
+      }
+    }
+  } else {
+    const int NR = kThreads * E;  // rows of the buffer; rows >= n are the identity
+    for (int cc = 0; cc < C; ++cc) {
+      if (line0 + cc >= a.lines) break;
+      const float2 sg = a.sigma[lj[cc]];
+      const float2 b0 = make_float2(2.f + (sg.x + a.lam_x[lp[cc]]) * ig, sg.y * ig);
+      PcrRow r[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = threadIdx.x + kThreads * e;
+        r[e] = pcr_identity();
+        if (i < n) {
+          r[e].a = make_float2(i > 0 ? -1.f : 0.f, 0.f);
+          r[e].c = make_float2(i < n - 1 ? -1.f : 0.f, 0.f);
+          r[e].b = b0;
+          r[e].d = X[(size_t)i * C + cc];
+        }
+        R[i] = r[e];
+      }
+      __syncthreads();
+      for (int st = 1; st < n; st <<= 1) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = threadIdx.x + kThreads * e;
+          const PcrRow m = i - st >= 0 ? R[i - st] : pcr_identity();
+          const PcrRow p = i + st < NR ? R[i + st] : pcr_identity();
+          r[e] = pcr_step(r[e], m, p);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) R[threadIdx.x + kThreads * e] = r[e];
+        __syncthreads();
+      }
+      const float f = ig * a.scale;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = threadIdx.x + kThreads * e;
+        if (i < n) {
+          const float2 q = crcp_mul(r[e].d, r[e].b);
+          X[(size_t)i * C + cc] = make_float2(q.x * f, q.y * f);
+        }
+      }
+      // (the next line rewrites R only after the barrier that ends its first row set-up)
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < (n << logC); it += blockDim.x) {
+    const int cc = it & (C - 1), i = it >> logC;
+    if (line0 + cc < a.lines) a.S[((size_t)lj[cc] * n + i) * a.P + lp[cc]] = X[(size_t)i * C + cc];
+  }
+}
+
+cudaError_t launch_pcr(const TriArgs& a, cudaStream_t st) {
+  const size_t sm = pcr_smem(a.n, a.C);
+  const int blocks = (a.lines + a.C - 1) / a.C;
+  auto go = [&](auto kern) -> cudaError_t {
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    prof_begin("pcr_y_f32", st);
+    kern<<<blocks, kThreads, sm, st>>>(a);
+    prof_end(st);
+    return cudaGetLastError();
+  };
+  if (a.n <= 32) return go(k_pcr<0>);
+  if (a.n <= kThreads) return go(k_pcr<1>);
+  if (a.n <= 2 * kThreads) return go(k_pcr<2>);
+  if (a.n <= 4 * kThreads) return go(k_pcr<4>);
+  return cudaErrorInvalidValue;
+}
+
 // ---- variable-coefficient tridiagonal systems ----
 template <typename T> struct cx_ops;
 template <> struct cx_ops<float> {

@@ -22,12 +22,13 @@ __host__ __device__ constexpr size_t inv_upd_smem_ring(int N, int C, int ring) {
   return sizeof(float2) * ((size_t)N * C + N) + sizeof(unsigned short) * (size_t)N + 16 +
          2 * sizeof(float2) * (size_t)C + 16 + inv_ring_bytes(C, ring);
 }
-// ring depth: as many levels (a power of two, at most 64) as fit next to the tile with three
-// CTAs per SM, at least one round of kThreads / 2C levels and at most N
+// ring depth: as many levels (a power of two, at most 64: slots are taken modulo the depth) as fit
+// next to the tile with three CTAs per SM, at least one round of kThreads / 2C levels, and no more
+// than N unless one round is longer
 __host__ __device__ constexpr int inv_ring_levels(int N, int C) {
   int ring = 64;
   while (ring > kThreads / (2 * C) && inv_upd_smem_ring(N, C, ring) > 72 * 1024) ring >>= 1;
-  if (ring > N) ring = N;
+  while (ring > N && ring > kThreads / (2 * C)) ring >>= 1;
   if (ring < kThreads / (2 * C)) ring = kThreads / (2 * C);
   return ring;
 }

@@ -27,6 +27,7 @@ struct ResidFwdArgs {
   int fem;                                 // P1 FEM (1D): time terms act on M_h U, centre 2/h
   float m_hi, m_lo;                        // P1 FEM: h/6 (mass matrix off-diagonal)
   int periodic;                            // periodic boundary conditions: neighbours wrap around
+  int g_pow2;                              // gx, gy, gz all powers of two (their products are exact)
   const double* react;                     // 1D: [M] weighted reaction coefficient w c_i; the
                                            // residual loses w c_i U_i^n (null: no reaction term)
   // first sweep from U_0^n = v (k_resid_v0): r_0^n = F_hat_n - beta_n M v - A v
@@ -170,6 +171,8 @@ template <typename T> cudaError_t launch_axis(const AxisArgs<T>& a, cudaStream_t
 // periodic lines (complex FFT of n points): op 0 forward, 1 shifted solve, 2 inverse
 template <typename T> cudaError_t launch_axis_per(const AxisArgs<T>& a, cudaStream_t st);
 cudaError_t launch_tri(const TriArgs& a, cudaStream_t st);
+// the same systems by parallel cyclic reduction (n <= 1024 rows)
+cudaError_t launch_pcr(const TriArgs& a, cudaStream_t st);
 template <typename T> cudaError_t launch_trivar_factor(const TriVarArgs<T>& a, cudaStream_t st);
 template <typename T> cudaError_t launch_trivar_solve(const TriVarArgs<T>& a, cudaStream_t st);
 size_t tri_smem(int n, int C);

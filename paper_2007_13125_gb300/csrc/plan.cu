@@ -483,7 +483,7 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   if (d->eig != PINT_EIG_TRUNC_DFT && d->eig != PINT_EIG_CLOSED_FORM) return fail(PINT_EINVAL, "bad eig variant");
   if (d->eig == PINT_EIG_CLOSED_FORM && d->alpha != 1.0 && d->precision != PINT_MIXED)
     return fail(PINT_EINVAL, "CLOSED_FORM eigenvalues with alpha < 1 need the residual form (PINT_MIXED)");
-  if (d->ysolve < 0 || d->ysolve > 3) return fail(PINT_EINVAL, "bad ysolve variant");
+  if (d->ysolve < 0 || d->ysolve > 4) return fail(PINT_EINVAL, "bad ysolve variant");
   if (d->space != PINT_SPACE_FD && d->space != PINT_SPACE_FEM_P1 && d->space != PINT_SPACE_PERIODIC)
     return fail(PINT_EINVAL, "bad space discretisation");
   if (d->space == PINT_SPACE_FEM_P1 && d->grid.dim != 1)
@@ -507,10 +507,11 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   const double hx = p->periodic ? 1.0 / p->mx : 1.0 / (p->mx + 1);
   const double hy = p->periodic ? 1.0 / p->my : 1.0 / (p->my + 1);
   // off-diagonal weight of the discrete Laplacian: 1/h^2 (FD stencil), 1/h (P1 stiffness)
-  p->gx = p->fem ? 1.0 / hx : 1.0 / (hx * hx);
-  p->gy = p->dim >= 2 ? 1.0 / (hy * hy) : 0.0;
-  const double hz = 1.0 / (p->mz + 1);
-  p->gz = p->dim == 3 ? 1.0 / (hz * hz) : 0.0;
+  // (as the integers 1/h and 1/h^2, below 2^24: exact in FP32 as well)
+  const double ix = p->periodic ? p->mx : p->mx + 1, iy = p->periodic ? p->my : p->my + 1;
+  p->gx = p->fem ? ix : ix * ix;
+  p->gy = p->dim >= 2 ? iy * iy : 0.0;
+  p->gz = p->dim == 3 ? (double)(p->mz + 1) * (p->mz + 1) : 0.0;
 
   auto bail = [&](pint_status st) { destroy_plan(p); return st; };
 
@@ -644,6 +645,7 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   p->ysolve = 1;
   if (p->dim == 2 && p->prec != PINT_FP64 && !p->periodic) {
     if (d->ysolve == 2) p->ysolve = 2;
+    else if (d->ysolve == 4 && p->my <= 1024) p->ysolve = 4;
     else if (d->ysolve == 3 && (s = autotune_ysolve(p)) != PINT_OK) return bail(s);
   }
   {
@@ -819,7 +821,7 @@ void split_ff(double x, float& hi, float& lo) {
   lo = (float)(x - (double)hi);
 }
 
-template <typename T> bool ysolve_tri(pint_plan p) { return sizeof(T) == 4 && p->ysolve == 2; }
+template <typename T> bool ysolve_tri(pint_plan p) { return sizeof(T) == 4 && (p->ysolve == 2 || p->ysolve == 4); }
 
 // spatial step on the half spectrum for T (float: MIXED/FP32, double: FP64)
 // mass and stiffness rows (diagonal, off-diagonal) of a 1D plan: finite differences (1, 0) and
@@ -908,7 +910,7 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
     tr.sigma = reinterpret_cast<const float2*>(t.sigma); tr.lam_x = reinterpret_cast<const float*>(t.lam_x);
     tr.g = (float)p->gy; tr.scale = (float)(-0.5 / (p->mx + 1));
     tr.C = p->Ctri; tr.logC = ilog2c(p->Ctri);
-    e = launch_tri(tr, st);
+    e = p->ysolve == 4 ? launch_pcr(tr, st) : launch_tri(tr, st);
   } else {
     AxisArgs<T> ay{};
     ay.S = p->S; ay.n = p->my; ay.lines = J * p->mx; ay.mode = 1; ay.P = p->mx; ay.op = 1;
@@ -921,8 +923,9 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
   return launch_axis(ax, st);
 }
 
-// Time the two y-direction solvers (sine transform vs tridiagonal) on this plan's workspace
-// and keep the faster; the choice is cached per (N, mx, my, precision) for the process.
+// Time the y-direction solvers (sine transform, thread-per-line recurrence, parallel cyclic
+// reduction) on this plan's workspace and keep the fastest; the choice is cached per
+// (N, mx, my, precision) for the process.
 pint_status autotune_ysolve(pint_plan p) {
   static std::mutex mu;
   static std::vector<std::pair<long long, int>> cache;
@@ -941,7 +944,8 @@ pint_status autotune_ysolve(pint_plan p) {
   int bestv = 1;
   const bool prof = g_prof_on;
   g_prof_on = false;
-  for (int v = 1; v <= 2; ++v) {
+  for (int v : {1, 2, 4}) {
+    if (v == 4 && p->my > 1024) continue;
     p->ysolve = v;
     cudaError_t e = spatial<float>(p, p->tf, st);
     cudaEventRecord(e0, st);
@@ -977,6 +981,13 @@ cudaError_t mixed_toeplitz(pint_plan p, cudaStream_t st) {
   return launch_toeplitz_ff(ta, st);
 }
 
+// The off-diagonal stencil weights are powers of two (m + 1 = 2^a per axis), so products with
+// them are exact in FP32.
+int stencil_pow2(pint_plan p) {
+  auto p2 = [](double g) { return g == 0.0 || pow2((long)g); };
+  return p2(p->gx) && p2(p->gy) && p2(p->gz) ? 1 : 0;
+}
+
 cudaError_t mixed_resid(pint_plan p, const double* Fhat, cudaStream_t st) {
   const int N = p->N, M = p->M;
   float* yhi = reinterpret_cast<float*>(p->z);
@@ -1005,6 +1016,7 @@ cudaError_t mixed_resid(pint_plan p, const double* Fhat, cudaStream_t st) {
   split_ff(p->gx, r.gx_hi, r.gx_lo);
   split_ff(p->gy, r.gy_hi, r.gy_lo);
   split_ff(p->gz, r.gz_hi, r.gz_lo);
+  r.g_pow2 = stencil_pow2(p);
   r.my = p->my;
   r.react = p->react_on ? p->react : nullptr;
   return launch_resid_fwd(r, st);
@@ -1121,6 +1133,7 @@ pint_status sweep_mixed_v0(pint_plan p, const double* Fhat, const double* v, cud
   split_ff(p->gx, r.gx_hi, r.gx_lo);
   split_ff(p->gy, r.gy_hi, r.gy_lo);
   split_ff(p->gz, r.gz_hi, r.gz_lo);
+  r.g_pow2 = stencil_pow2(p);
   r.my = p->my;
   r.react = p->react_on ? p->react : nullptr;
   cudaError_t e = launch_resid_v0(r, st);

@@ -167,9 +167,13 @@ def test_closed_form_eigenvalues_converge_to_same_solution():
         Plan.for_problem(p, "fp64", eig=1)
 
 
-@pytest.mark.parametrize("ysolve", [1, 2])
-@pytest.mark.parametrize("case", [(2, 31, 32, 4, 1.0, 0.05), (2, 63, 16, 2, 0.5, 0.1), (2, 7, 64, 6, 1.0, 0.1)])
+@pytest.mark.parametrize("ysolve", [1, 2, 3, 4])
+@pytest.mark.parametrize("case", [(2, 31, 32, 4, 1.0, 0.05), (2, 63, 16, 2, 0.5, 0.1), (2, 7, 64, 6, 1.0, 0.1),
+                                  (2, 15, 8, 3, 1.0, 0.1), (2, 255, 16, 2, 1.0, 0.1), (2, 511, 8, 2, 1.0, 0.1),
+                                  (2, 99, 20, 3, 1.0, 0.1)])
 def test_ysolve_variants(case, ysolve):
+    # 1: sine transform along y; 2: thread-per-line recurrence; 4: parallel cyclic reduction (a warp
+    # per line up to 32 rows, the CTA on a line beyond); 3: the fastest of them, timed at plan creation
     torch = torch_cuda()
     p = _p(*case)
     ref = oracle_solution(p)
