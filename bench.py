@@ -69,6 +69,7 @@ def algo_bytes(name: str, N: int, M: int) -> float:
         "cvt_d2f": 12 * NM,                     # read FP64, write FP32
         "cvt_f2d": 12 * NM,
         "tri_y_f32": 16 * JM,                   # read + write spectrum (complex float)
+        "pcr_y_f32": 16 * JM,                   # the same systems by parallel cyclic reduction
         "axis_solve_per_f32": 16 * JM,
         "fft_per_f32": 16 * JM,
         "axis_solve_per_f64": 32 * JM,
