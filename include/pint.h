@@ -231,6 +231,24 @@ pint_status pint_solve_v_async(pint_plan plan, const double* Fhat, const double*
 pint_status pint_solve_async(pint_plan plan, const double* Fhat, double* U, double tol, int max_sweeps,
                              void* stream);
 
+/* End-to-end solve through host buffers: copies v [M], f [N][M] and fderiv [k-1][M] (NULL when
+ * k = 1) from host memory into device buffers the plan owns, forms F_hat (pint_form_rhs), solves
+ * from U_0^n = v (pint_solve_v, tol and max_sweeps as there) and copies the solution into the host
+ * array U_out [N][M]; everything is enqueued without waiting. The device work runs on `stream`;
+ * the copies run on two streams of the plan, and the plan keeps two sets of staging buffers, so
+ * consecutive calls overlap their transfers with the neighbouring solves (the inputs of call i+1
+ * are copied in, and the solution of call i-1 is copied out, while call i solves).
+ * pint_solve_host_join makes a stream wait for every copy-out issued so far: once that stream has
+ * completed, every U_out is filled; pint_solve_result then reports the last solve. Host arrays must
+ * stay valid, and the inputs unchanged, until then; page-locked host memory (cudaHostAlloc) makes
+ * the copies asynchronous, pageable memory works with the driver's staging. The staging buffers
+ * (two sets of v, f, d^l f(0) and U, and one F_hat: 5 N M + 2 k M doubles) are allocated on the
+ * first call (PINT_ENOMEM if they cannot be) and freed with the plan. A plan runs one call at a
+ * time per stream ordering: calls on different streams must not overlap. */
+pint_status pint_solve_host(pint_plan plan, const double* v, const double* f, const double* fderiv,
+                            double* U_out, double tol, int max_sweeps, void* stream);
+pint_status pint_solve_host_join(pint_plan plan, void* stream);
+
 /* Outcome of the plan's most recent graph-launched solve: sweeps, final relative update, and
  * PINT_OK if it met tol, PINT_ENOTCONV if it stopped at max_sweeps. Valid once the stream has
  * completed that solve; the next solve on the plan overwrites it. */

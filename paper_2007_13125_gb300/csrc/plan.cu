@@ -445,6 +445,7 @@ pint_status validate(int k, double alpha, double kappa, double tau, int N, const
 
 void destroy_plan(pint_plan p) {
   if (!p) return;
+  host_stage_free(p);
   for (SolveGraph& c : p->sg)
     if (c.exec) cudaGraphExecDestroy(c.exec);
   if (p->cap) cudaStreamDestroy(p->cap);

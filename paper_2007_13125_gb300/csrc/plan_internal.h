@@ -28,6 +28,10 @@ template <typename T> struct DevTables {
 
 // Source of a plan's device memory: cudaMalloc by default, or a sub-allocator (the server's
 // budgeted arena). alloc returns nullptr on failure.
+struct HostStage;
+// frees the staging of pint_solve_host (host_io.cu); called by plan destruction
+void host_stage_free(pint_plan p);
+
 struct DevAllocator {
   virtual void* alloc(size_t bytes) = 0;
   virtual void release(void* p) = 0;
@@ -75,6 +79,7 @@ struct pint_plan_s {
   pint::DevAllocator* alloc = nullptr;   // null: cudaMalloc / cudaFree
   std::vector<void*> allocs;
   std::vector<size_t> alloc_sizes;
+  pint::HostStage* hstage = nullptr;      // staging of pint_solve_host (host_io.cu), on first use
   size_t bytes = 0;
   pint::DevTables<float> tf;
   pint::DevTables<double> td;

@@ -102,6 +102,8 @@ def lib():
         "pint_solve_v": (_I, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
         "pint_solve_v_async": (_I, [_P, _P, _P, _P, _D, _I, _P]),
         "pint_solve_result": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+        "pint_solve_host": (_I, [_P, _P, _P, _P, _P, _D, _I, _P]),
+        "pint_solve_host_join": (_I, [_P, _P]),
         "pint_time_weights": (_I, [_I, _D, _I, ctypes.POINTER(_D)]),
         "pint_correction_coefficients": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
         "pint_circulant_eigenvalues": (_I, [_I, _D, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -380,6 +382,31 @@ class Plan:
             raise PintError(st, last_error())
         n = info.steps
         return st, list(info.sweeps[:n]), list(info.upd[:n])
+
+    def solve_host(self, v, f, fderiv, U_out, tol=1e-10, max_sweeps=50, stream=None):
+        """End-to-end solve through host buffers (pint_solve_host): v [M], f [N][M], fderiv [k-1][M]
+        and U_out [N][M] are host float64 arrays (numpy, or CPU tensors, preferably pinned) that
+        must stay alive until the work is complete (solve_host_join, then a sync of the stream)."""
+        def hp(x, n):
+            if x is None:
+                return None
+            if hasattr(x, "is_cuda"):
+                if x.is_cuda or x.dtype.itemsize != 8 or not x.dtype.is_floating_point or not x.is_contiguous():
+                    raise ValueError("expected a contiguous float64 host tensor")
+                if x.numel() != n:
+                    raise ValueError(f"expected {n} elements, got {x.numel()}")
+                return ctypes.c_void_p(x.data_ptr())
+            if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"] or x.size != n:
+                raise ValueError(f"expected a C-contiguous float64 array of {n} elements")
+            return ctypes.c_void_p(x.ctypes.data)
+        NM, M = self.N * self.M, self.M
+        fdp = hp(fderiv, (self.k - 1) * M) if self.k > 1 else None
+        check(lib().pint_solve_host(self.handle, hp(v, M), hp(f, NM), fdp, hp(U_out, NM), float(tol),
+                                    int(max_sweeps), _stream(stream)))
+
+    def solve_host_join(self, stream=None):
+        """Make `stream` wait for every copy-out of solve_host issued so far (pint_solve_host_join)."""
+        check(lib().pint_solve_host_join(self.handle, _stream(stream)))
 
     def solve_result(self, raise_on_notconv=True):
         """(status, sweeps, update) of the last graph-launched solve, once its stream completed it."""
