@@ -315,17 +315,17 @@ __global__ void __launch_bounds__(kThreads) k_toeplitz(ToepArgs a) {
 // pipes (~48-bit significand; GB300's FP64 pipe is ~70x slower than its FP32 pipes), in the
 // lazy form (ffz: renormalised once per pass, when a value is stored).
 // ---------------------------------------------------------------------------
-// Shared memory holds only the [2N][C] tile: the double-float twiddles (16 B each, 64 KB at
-// N = 2048) are read through the L1 cache, which every CTA on the SM shares, so a tile of one or two
-// columns leaves room for three CTAs per SM (with the table in shared memory a 4096-point tile ran
-// one CTA, eight warps, per SM).
-size_t toep_ff_smem(int N, int C) { return sizeof(ffz) * (size_t)(2 * N) * C; }
+size_t toep_ff_smem(int N, int C) { return time_tile_bytes<ffc>(2 * N, C); }
 
 __global__ void __launch_bounds__(kThreads) k_toeplitz_ff(ToepFFArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = a.N, C = a.C, M = a.M, L = 2 * a.N, logC = a.logC;
   ffz* X = reinterpret_cast<ffz*>(smraw);
-  const ffz* tw = reinterpret_cast<const ffz*>(a.tw);
+  ffz* tw = X + (size_t)L * C;
+  unsigned short* perm = reinterpret_cast<unsigned short*>(tw + L);
+  const ffz* gtw = reinterpret_cast<const ffz*>(a.tw);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = gtw[i];
+  (void)perm;
   const int m0 = blockIdx.x * 2 * C;
   for (int it = threadIdx.x; it < (L << logC); it += blockDim.x) {
     const int cc = it & (C - 1), i = it >> logC;

@@ -623,8 +623,7 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   p->Cr = std::min(p->Ct, 16);
   p->Ci = p->Cr;
   p->Ctd = std::min(pick_cols((size_t)N * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2)), budget, 32, 1), occ);
-  // (CQ history tiles: at most ~72 KB, three CTAs per SM)
-  p->Cz = std::min(pick_cols((size_t)2 * N * sizeof(double2), 72 * 1024, 16, 1), occ);
+  p->Cz = std::min(pick_cols((size_t)2 * N * sizeof(double2), 160 * 1024, 16, 1), occ);
   const size_t ve = p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2);
   // sine-transform tiles: up to 64 KB of extended lines (16 lines of 512 FP32 complex points),
   // three CTAs per SM
