@@ -453,6 +453,7 @@ def run_mix(args) -> int:
                        "sweeps": {"min": min(sweeps), "max": max(sweeps), "mean": sum(sweeps) / len(sweeps)},
                        "status": st,
                        "solo_sum_ms": sum(solo), "batch_over_solo_speedup": sum(solo) / ms,
+                       "solo_ms": {p.name: round(t, 3) for p, t in zip(probs, solo)},
                        "solo_note": "each problem alone (one graph launch per solve, host wait after each); "
                                     "the batch runs them as independent branches of one graph",
                        "launch_mode": "one CUDA graph for all 64 solves (independent branches)",
