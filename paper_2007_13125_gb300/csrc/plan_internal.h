@@ -138,9 +138,10 @@ pint_status solve_enqueue(pint_plan p, const double* F, double* U, double tol, i
                           const double* v = nullptr);
 // Result of the last enqueued solve (valid once its stream work has completed).
 void solve_result(pint_plan p, int* sweeps, double* upd, bool* converged);
-// Add one solve (prologue, while-loop, epilogue) of plan p as independent nodes of graph g.
+// Add one solve (prologue, while-loop, epilogue, or the one-CTA solve) of plan p to graph g.
 // v: start from U_0^n = v (MIXED: the first sweep in the prologue; otherwise v is broadcast into U).
+// dep (optional): a node the solve's first node must follow; *last (optional): its final node.
 pint_status add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, double* U, double tol, int max_sweeps,
-                            const double* v = nullptr);
+                            const double* v, cudaGraphNode_t dep = nullptr, cudaGraphNode_t* last = nullptr);
 
 }  // namespace pint
