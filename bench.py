@@ -86,12 +86,11 @@ def algo_bytes(name: str, N: int, M: int) -> float:
 # the kernel's source is unchanged (sha1 of its translation unit); other workloads report null
 NCU_TRAFFIC = {
     "heat2d_255x255_N256_bdf4": {
-        "resid_fwd_ff": (316.93e6, "kernels_resid.cu", "b48ed6cac8d6424f3c0746711fca42871516c65a"),
-        "resid_v0_ff": (167.08e6, "kernels_resid.cu", "b48ed6cac8d6424f3c0746711fca42871516c65a"),
-        "inv_update_v0_ff": (141.95e6, "kernels_time.cu", "5394d4dd1afe55ae78ee7de2ccad83cad9d216cf"),
-        "inv_update_ff": (277.44e6, "kernels_time.cu", "5394d4dd1afe55ae78ee7de2ccad83cad9d216cf"),
-        "dst_f32": (76.13e6, "kernels_space.cu", "481cdea001d1c5629944d60849106b33e388ead1"),
-        "axis_solve_f32": (78.62e6, "kernels_space.cu", "481cdea001d1c5629944d60849106b33e388ead1"),
+        "resid_fwd_ff": (317.10e6, "kernels_resid.cu", "ea51c64f5e96cb1d0117a303ab55145454a99bd4"),
+        "inv_update_v0_ff": (142.02e6, "kernels_time.cu", "52a9807ae8c6d22bb1c383866a1efa3fc7e6abba"),
+        "inv_update_ff": (277.51e6, "kernels_time.cu", "52a9807ae8c6d22bb1c383866a1efa3fc7e6abba"),
+        "dst_f32": (76.13e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
+        "axis_solve_f32": (79.02e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
     },
 }
 
