@@ -453,6 +453,7 @@ def run_mix(args) -> int:
                        "status": st,
                        "solo_sum_ms": sum(solo), "batch_over_solo_speedup": sum(solo) / ms,
                        "solo_ms": {p.name: round(t, 3) for p, t in zip(probs, solo)},
+                       "tuning": {p.name: pl.tuning() for p, pl in zip(probs, plans)},
                        "solo_note": "each problem alone (one graph launch per solve, host wait after each); "
                                     "the batch runs them as independent branches of one graph",
                        "launch_mode": "one CUDA graph for all 64 solves (independent branches)",
@@ -965,6 +966,7 @@ def main():
             "launch_mode": "per-sweep launches" if args.per_sweep_launches else "one CUDA graph per solve (device-side convergence loop)",
             "parallelism": f"replicas x{world}",
             "kernels": per_kernel,
+            "tuning": plans["mixed"].tuning(),
         },
         "roofline": roofline,
         "cpu_baseline": cpu,

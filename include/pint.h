@@ -249,6 +249,14 @@ pint_status pint_solve_host(pint_plan plan, const double* v, const double* f, co
                             double* U_out, double tol, int max_sweeps, void* stream);
 pint_status pint_solve_host_join(pint_plan plan, void* stream);
 
+/* The plan's tuned choices: out[0] residual tile width (points / 2 per CTA), out[1] update tile
+ * width, out[2] CQ-history tile width, out[3] y-direction solver (1 sine transform, 2 recurrence,
+ * 4 parallel cyclic reduction), out[4] / out[5] largest FFT radix of the residual / update time
+ * transforms (16 for the compiled shapes; 8 or 16 as timed for runtime shapes; 0 when not MIXED),
+ * out[6] 1 if the whole solve runs as one CTA. Fills min(n, 7) entries and returns 7 (-1 for a
+ * NULL plan or out). Host-only. */
+int pint_plan_tuning(pint_plan plan, int* out, int n);
+
 /* Outcome of the plan's most recent graph-launched solve: sweeps, final relative update, and
  * PINT_OK if it met tol, PINT_ENOTCONV if it stopped at max_sweeps. Valid once the stream has
  * completed that solve; the next solve on the plan overwrites it. */

@@ -444,6 +444,19 @@ __device__ void fft_inverse(V* X, int ld, int logC, int L, const V* tw) {
   }
 }
 
+// The runtime-shape transforms with the radix bound chosen at run time (maxlog 3: radix <= 8,
+// otherwise radix <= 16); the position table of the same schedule is fft_perm_table(perm, L, maxlog).
+template <typename V, typename TW>
+__device__ __forceinline__ void fft_forward_ml(V* X, int ld, int logC, int L, const TW tw, int maxlog) {
+  if (maxlog == 3) fft_forward<3>(X, ld, logC, L, tw);
+  else fft_forward<4>(X, ld, logC, L, tw);
+}
+template <typename V, typename TW>
+__device__ __forceinline__ void fft_inverse_ml(V* X, int ld, int logC, int L, const TW tw, int maxlog) {
+  if (maxlog == 3) fft_inverse<3>(X, ld, logC, L, tw);
+  else fft_inverse<4>(X, ld, logC, L, tw);
+}
+
 // ---- compile-time variant: L = 2^LOGL, C = 2^LOGC columns, pitch LD, all known to the
 // compiler, so every shared-memory address is a base register plus an immediate and the
 // twiddle indices need no masks. Same radix schedule (and output order) as above.

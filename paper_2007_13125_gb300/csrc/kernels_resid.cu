@@ -63,19 +63,21 @@ struct ResidLevel {
 // instances keep constant neighbour offsets).
 // CTF: the tile shape (N, C) is one of the compiled transforms; otherwise the runtime-shape one.
 // Keeping the two apart keeps the compiled instances within 64 registers without spill code.
-__host__ __device__ inline bool compiled_time_fft(int N, int C) {
-  return (N == 128 && C == 16) || (N == 256 && C == 16) || (N == 512 && C == 16) || (N == 1024 && C == 8);
-}
+__host__ __device__ inline bool compiled_time_fft(int N, int C) { return compiled_time_fft_shape(N, C); }
 template <bool CTF>
-__device__ __forceinline__ void resid_time_fft(float2* X, int C, int logC, int N, const float2* tw) {
+__device__ __forceinline__ void resid_time_fft(float2* X, int C, int logC, int N, const float2* tw, int maxlog) {
   if constexpr (CTF) {
     if (N == 128) fft_forward_ct<7, 4, 16>(X, tw);
     else if (N == 256) fft_forward_ct<8, 4, 16>(X, tw);
     else if (N == 512) fft_forward_ct<9, 4, 16>(X, tw);
     else fft_forward_ct<10, 3, 8>(X, tw);
   } else {
-    fft_forward(X, C, logC, N, tw);
+    fft_forward_ml(X, C, logC, N, tw, maxlog);
   }
+}
+// radix bound of the tile's transform: the compiled shapes use radix <= 16
+template <bool CTF> __device__ __forceinline__ int resid_maxlog(const ResidFwdArgs& a) {
+  return CTF ? 4 : (a.maxlog == 3 ? 3 : 4);
 }
 
 template <int K, bool CQ, int DIM, bool FEM, bool PER, bool CTF>
@@ -84,7 +86,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
   const int N = a.N, C = a.C, M = a.M, logC = a.logC, mx = a.mx;
   float2 *X, *tw;
   unsigned short* perm;
-  time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
+  const int ml = resid_maxlog<CTF>(a);
+  time_tile_setup(smraw, N, C, a.tw, X, tw, perm, ml);
 
   const int P2 = 2 * C, logP2 = logC + 1;
   const int G = resid_groups(N, C), NL = N / G;
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
     }
   }
   __syncthreads();
-  resid_time_fft<CTF>(X, C, logC, N, tw);
+  resid_time_fft<CTF>(X, C, logC, N, tw, ml);
   store_half_spectrum(X, perm, a.S, N, M, C, logC, (int)blockIdx.x * P2);
 }
 
@@ -292,7 +295,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_v0(ResidFwdArgs a) {
   const int N = a.N, C = a.C, M = a.M, logC = a.logC, mx = a.mx;
   float2 *X, *tw;
   unsigned short* perm;
-  time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
+  const int ml = resid_maxlog<CTF>(a);
+  time_tile_setup(smraw, N, C, a.tw, X, tw, perm, ml);
   const int P2 = 2 * C, logP2 = logC + 1;
   const int G = resid_groups(N, C), NL = N / G;
   const int q = threadIdx.x & (P2 - 1), g = threadIdx.x >> logP2;
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_v0(ResidFwdArgs a) {
     }
   }
   __syncthreads();
-  resid_time_fft<CTF>(X, C, logC, N, tw);
+  resid_time_fft<CTF>(X, C, logC, N, tw, ml);
   store_half_spectrum(X, perm, a.S, N, M, C, logC, (int)blockIdx.x * P2);
 }
 

@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_upd(InvUpdArgs a) {
   const int C = CT ? (1 << LOGC) : a.C, logC = CT ? LOGC : a.logC;
   float2 *X, *tw;
   unsigned short* perm;
-  time_tile_setup(smraw, N, C, a.tw, X, tw, perm);
+  const int ml = CT ? 4 : (a.maxlog == 3 ? 3 : 4);
+  time_tile_setup(smraw, N, C, a.tw, X, tw, perm, ml);
   float2* B0 = reinterpret_cast<float2*>(((size_t)(perm + N) + 15) & ~(size_t)15);  // [2][C]
   // U staging ring: RING levels x 2C points of (hi, lo) pairs
   float2* ring = reinterpret_cast<float2*>(((size_t)(B0 + 2 * C) + 15) & ~(size_t)15);
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_upd(InvUpdArgs a) {
   }
   __syncthreads();
   if constexpr (CT) fft_inverse_ct<LOGN, LOGC, (1 << LOGC)>(X, tw);
-  else fft_inverse(X, C, logC, N, tw);
+  else fft_inverse_ml(X, C, logC, N, tw, ml);
 
   // 4. U += c, level by level through the ring
   float sc = 0.f, su = 0.f;  // per-thread partial norms (FP32: the FP64 pipe is ~1/70 rate)

@@ -12,6 +12,15 @@ constexpr int kMaxK = 6;
 // ---- time-axis kernels (kernels_time.cu) ----
 
 // MIXED: r = F_hat - K U in double-float, times kappa^{i/N}, real -> half-complex DFT.
+// Time-tile shapes (N, tile width) with a compiled time FFT: the residual kernels' and the update
+// kernel's (the launchers pick those instances; every other shape runs the runtime-shape transform).
+__host__ __device__ inline bool compiled_time_fft_shape(int N, int C) {
+  return (N == 128 && C == 16) || (N == 256 && C == 16) || (N == 512 && C == 16) || (N == 1024 && C == 8);
+}
+__host__ __device__ inline bool compiled_update_shape(int N, int C) {
+  return compiled_time_fft_shape(N, C) || (N == 2048 && C == 4) || (N == 4096 && C == 2);
+}
+
 struct ResidFwdArgs {
   const float2* U;                         // iterate U [N][M] (double-float pairs: hi, lo)
   const double* F;                         // F_hat [N][M] (FP64, split to double-float on load)
@@ -28,6 +37,7 @@ struct ResidFwdArgs {
   float m_hi, m_lo;                        // P1 FEM: h/6 (mass matrix off-diagonal)
   int periodic;                            // periodic boundary conditions: neighbours wrap around
   int g_pow2;                              // gx, gy, gz all powers of two (their products are exact)
+  int maxlog;                              // runtime-shape time FFT: radix <= 2^maxlog (3 or 4; 0: 4)
   const double* react;                     // 1D: [M] weighted reaction coefficient w c_i; the
                                            // residual loses w c_i U_i^n (null: no reaction term)
   // first sweep from U_0^n = v (k_resid_v0): r_0^n = F_hat_n - beta_n M v - A v
@@ -42,6 +52,7 @@ struct InvUpdArgs {
   int N, M, C, logC;
   double* norms;                           // [0] += sum c^2, [1] += sum U^2
   int ring;                                // levels in the U staging ring (set by the launcher)
+  int maxlog;                              // runtime-shape time FFT: radix <= 2^maxlog (3 or 4; 0: 4)
   const double* v;                         // first sweep from U_0^n = v: U = v + c ([M]), else null
 };
 

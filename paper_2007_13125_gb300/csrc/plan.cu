@@ -470,6 +470,7 @@ void destroy_plan(pint_plan p) {
 namespace {
 pint_status autotune_ysolve(pint_plan p);
 pint_status tune_time_tiles(pint_plan p, int cmax_t, int cmax_z);
+pint_status tune_radix(pint_plan p);
 }
 
 extern "C" pint_status pint_plan_create_desc(const pint_plan_desc* d, pint_plan* out) {
@@ -701,6 +702,11 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
     // (below 2^18 space-time unknowns launch latency dominates and the timings carry no signal)
     if (!A && p->prec == PINT_MIXED && occ < cmax_t && (size_t)N * M >= ((size_t)1 << 18) &&
         (s = tune_time_tiles(p, cmax_t, cmax_z)) != PINT_OK)
+      return bail(s);
+    // the radix schedule of time FFTs without a compiled shape (at the widths now fixed)
+    if (!A && p->prec == PINT_MIXED && (size_t)N * M >= ((size_t)1 << 18) &&
+        (!compiled_time_fft_shape(N, p->Cr) || !compiled_update_shape(N, p->Ci)) &&
+        (s = tune_radix(p)) != PINT_OK)
       return bail(s);
   }
   {
@@ -1018,6 +1024,7 @@ cudaError_t mixed_resid(pint_plan p, const double* Fhat, cudaStream_t st) {
   split_ff(p->gy, r.gy_hi, r.gy_lo);
   split_ff(p->gz, r.gz_hi, r.gz_lo);
   r.g_pow2 = stencil_pow2(p);
+  r.maxlog = p->rml;
   r.my = p->my;
   r.react = p->react_on ? p->react : nullptr;
   return launch_resid_fwd(r, st);
@@ -1028,6 +1035,7 @@ cudaError_t mixed_update(pint_plan p, const double* v, cudaStream_t st) {
   u.S = reinterpret_cast<const float2*>(p->S); u.U = p->Uff;
   u.inv_s = p->tf.inv_s; u.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
   u.N = p->N; u.M = p->M; u.C = p->Ci; u.logC = ilog2c(p->Ci); u.norms = p->norms; u.v = v;
+  u.maxlog = p->uml;
   return launch_inv_upd(u, st);
 }
 
@@ -1117,6 +1125,75 @@ pint_status tune_time_tiles(pint_plan p, int cmax_t, int cmax_z) {
   return PINT_OK;
 }
 
+// Radix bound of the runtime-shape time FFTs (shapes without a compiled transform, e.g. N = 2048 or
+// N = 100): the residual and the update kernel are each timed with radix <= 8 and radix <= 16
+// passes on the plan's workspaces at their chosen widths, and each keeps its faster schedule (the
+// forward and the inverse transform need not match: the half spectrum is stored in natural order).
+// Cached per problem shape and widths for the process.
+pint_status tune_radix(pint_plan p) {
+  static std::mutex mu;
+  struct Entry { long long key[4]; int rml, uml; };
+  static std::vector<Entry> cache;
+  const long long key[4] = {(long long)p->N * 8192 + p->k, ((long long)p->mx * 4096 + p->my) * 4096 + p->mz,
+                            (long long)p->dim * 16 + (p->cq ? 8 : 0) + (p->fem ? 4 : 0) + (p->periodic ? 2 : 0),
+                            (long long)p->Cr * 4096 + p->Ci};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry& c : cache)
+      if (std::equal(key, key + 4, c.key)) { p->rml = c.rml; p->uml = c.uml; return PINT_OK; }
+  }
+  const size_t NM = (size_t)p->N * p->M;
+  double* F = nullptr;
+  {
+    void* q = nullptr;
+    const cudaError_t ea = lib_malloc(&q, NM * sizeof(double));
+    if (ea != cudaSuccess) return fail(PINT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(ea));
+    F = (double*)q;
+  }
+  cudaStream_t st;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { lib_free(F, NM * sizeof(double)); return cuda_fail(e, "radix tuning"); }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bool prof = g_prof_on;
+  g_prof_on = false;
+  if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, NM * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->Uff, 0, NM * sizeof(float2), st);
+  if (e == cudaSuccess && p->cq) e = cudaMemsetAsync(p->z, 0, NM * sizeof(double), st);
+  int* ml[2] = {&p->rml, &p->uml};
+  for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
+    float best = 1e30f;
+    int bestl = 4;
+    for (int l = 3; l <= 4 && e == cudaSuccess; ++l) {
+      *ml[kind] = l;
+      auto run = [&]() { return kind == 0 ? mixed_resid(p, F, st) : mixed_update(p, nullptr, st); };
+      e = run();
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = run();
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) { best = ms; bestl = l; }
+    }
+    *ml[kind] = bestl;
+  }
+  g_prof_on = prof;
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  lib_free(F, NM * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(e, "radix tuning");
+  std::lock_guard<std::mutex> lk(mu);
+  Entry en;
+  std::copy(key, key + 4, en.key);
+  en.rml = p->rml; en.uml = p->uml;
+  cache.push_back(en);
+  return PINT_OK;
+}
+
 // MIXED first sweep from U_0^n = v (Theorem 2.7): r_0 = F_hat - beta_n M v - A v in one pass over
 // F_hat (no U read; for CQ no history product), the spatial solves, and U_1 = v + c written as
 // the double-float iterate
@@ -1135,6 +1212,7 @@ pint_status sweep_mixed_v0(pint_plan p, const double* Fhat, const double* v, cud
   split_ff(p->gy, r.gy_hi, r.gy_lo);
   split_ff(p->gz, r.gz_hi, r.gz_lo);
   r.g_pow2 = stencil_pow2(p);
+  r.maxlog = p->rml;
   r.my = p->my;
   r.react = p->react_on ? p->react : nullptr;
   cudaError_t e = launch_resid_v0(r, st);
@@ -1446,6 +1524,20 @@ extern "C" pint_status pint_solve_v_async(pint_plan p, const double* Fhat, const
   if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
   if (g_prof_on) return fail(PINT_EINVAL, "pint_solve_v_async: not available while per-kernel profiling is on");
   return solve_enqueue(p, Fhat, U, tol, max_sweeps, (cudaStream_t)stream, v);
+}
+
+extern "C" int pint_plan_tuning(pint_plan p, int* out, int n) {
+  if (!p || !out || n < 0) {
+    set_last_error("NULL argument");
+    return -1;
+  }
+  const bool mixed = p->prec == PINT_MIXED;
+  const int v[7] = {p->Cr, p->Ci, p->Cz, p->ysolve,
+                    mixed ? (compiled_time_fft_shape(p->N, p->Cr) ? 16 : 1 << p->rml) : 0,
+                    mixed ? (compiled_update_shape(p->N, p->Ci) ? 16 : 1 << p->uml) : 0, p->small ? 1 : 0};
+  const int k = n < 7 ? n : 7;
+  for (int i = 0; i < k; ++i) out[i] = v[i];
+  return 7;
 }
 
 extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* upd_rel_out) {

@@ -104,7 +104,9 @@ struct pint_plan_s {
   // tiles
   int Ct, Cr, Ci, Ctd, Cz, Cx, Cy, Czl, Ctri;  // columns per CTA: time (float), residual, update, time (T),
                                              // toeplitz, x, y, z lines, tri
-  int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal
+  int ysolve;                       // 2D y direction: 1 sine transform, 2 tridiagonal, 4 PCR
+  int rml = 4, uml = 4;             // radix bound (log2) of the runtime-shape time FFTs of the
+                                    // MIXED residual and update kernels (tuned: 3 or 4)
   double q_floor;                   // predicted floor of the per-sweep contraction (inner precision)
   // reaction term (1D, Dirichlet): the spatial operator A + w diag(c) of the linear solves
   // (pint_set_reaction; the linearised operator of Algorithm 3)

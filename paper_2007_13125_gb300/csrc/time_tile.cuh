@@ -72,14 +72,15 @@ template <typename V> __host__ __device__ inline size_t time_tile_bytes(int N, i
   return sizeof(V) * ((size_t)N * C + N) + sizeof(unsigned short) * (size_t)N;
 }
 
+// (maxlog: the radix bound of the transform the tile will use, for its position table)
 template <typename V>
 __device__ __forceinline__ void time_tile_setup(unsigned char* raw, int N, int C, const V* gtw, V*& X,
-                                                V*& tw, unsigned short*& perm) {
+                                                V*& tw, unsigned short*& perm, int maxlog = 4) {
   X = reinterpret_cast<V*>(raw);
   tw = X + (size_t)N * C;
   perm = reinterpret_cast<unsigned short*>(tw + N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = gtw[i];
-  fft_perm_table(perm, N);
+  fft_perm_table(perm, N, maxlog);
 }
 
 // Separate the spectra of the two real columns packed in complex column cc and store the

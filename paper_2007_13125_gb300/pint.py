@@ -104,6 +104,7 @@ def lib():
         "pint_solve_result": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
         "pint_solve_host": (_I, [_P, _P, _P, _P, _P, _D, _I, _P]),
         "pint_solve_host_join": (_I, [_P, _P]),
+        "pint_plan_tuning": (_I, [_P, ctypes.POINTER(_I), _I]),
         "pint_time_weights": (_I, [_I, _D, _I, ctypes.POINTER(_D)]),
         "pint_correction_coefficients": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
         "pint_circulant_eigenvalues": (_I, [_I, _D, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -304,6 +305,15 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def tuning(self) -> dict:
+        """The plan's tuned choices (pint_plan_tuning): tile widths, y solver, FFT radix bounds."""
+        out = (_I * 7)()
+        if lib().pint_plan_tuning(self.handle, out, 7) < 0:
+            raise PintError(PINT_EINVAL, last_error())
+        keys = ["resid_width", "update_width", "history_width", "ysolve", "resid_max_radix",
+                "update_max_radix", "one_cta"]
+        return {k: int(out[i]) for i, k in enumerate(keys)}
 
     def workspace_bytes(self) -> int:
         """Device bytes the plan owns (pint_plan_workspace_bytes)."""

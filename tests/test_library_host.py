@@ -166,3 +166,7 @@ def test_noalloc_wrapper_checks_buffer_sizes_without_a_gpu(pint):
         pint.kappa_solve_noalloc(2, 0.1, 1.0 / 64, 64, 63, R, Q)
     with pytest.raises(ValueError):
         pint.kappa_solve_noalloc(2, 0.1, 1.0 / 64, 64, 63, R, R)
+
+
+def test_plan_tuning_query_rejects_null(pint):
+    assert pint.lib().pint_plan_tuning(None, None, 0) == -1
