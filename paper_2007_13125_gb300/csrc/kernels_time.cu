@@ -17,11 +17,7 @@ namespace pint {
 // MIXED: inverse DFT + unscale + U += c (double-float) + norms
 // ---------------------------------------------------------------------------
 // U staging ring of the update: RING levels x 2C points, hi and lo
-// (compiled shapes stream U with bulk copies of 2C points plus 16 bytes per level, into slots of
-// 16 C + 16 bytes, with one 8-byte barrier per stage: at most 64 stages)
-__host__ __device__ constexpr size_t inv_ring_bytes(int C, int ring) {
-  return (size_t)ring * (16 * (size_t)C + 16) + 8 * 64 + 16;
-}
+__host__ __device__ constexpr size_t inv_ring_bytes(int C, int ring) { return 2 * sizeof(float) * (size_t)ring * 2 * C; }
 __host__ __device__ constexpr size_t inv_upd_smem_ring(int N, int C, int ring) {
   return sizeof(float2) * ((size_t)N * C + N) + sizeof(unsigned short) * (size_t)N + 16 +
          2 * sizeof(float2) * (size_t)C + 16 + inv_ring_bytes(C, ring);
@@ -67,43 +63,6 @@ __device__ __forceinline__ void cp_async_wait_pending(int n) {
   }
 }
 
-// ---- bulk copies completing on shared-memory barriers (the update kernel's U stream) ----
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
-// one arrival that also announces `bytes` of copies completing on the barrier
-__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
-               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for phase `parity` of the barrier to complete, giving up after ~2^22 polls (well over the
-// time any copy takes; a wait that gives up is reported through the solve's error flag).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
-    if (mbar_test(bar, parity)) return true;
-    __nanosleep(32);
-  }
-  return false;
-}
-// order this thread's earlier generic-proxy accesses to shared memory before later bulk copies
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-
 // Inverse time DFT of the tile, unscaling, and U += c with the norms of c and U.
 // Thread (q, r) of the update owns point q and the levels i = r (mod kThreads / 2C). Its U values
 // stream through a per-thread ring of shared-memory slots filled by asynchronous copies: the
@@ -112,21 +71,11 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // arithmetic and the stores. A thread reads only slots it filled itself (no block barrier).
 // LOGN > 0: compiled for N = 2^LOGN levels and 2^LOGC columns; LOGN = 0: any shape.
 // V0: the first sweep from U_0^n = v: U = v + c, v read once per point (no U stream, no ring)
-// Compiled shapes (BULK): the U rows of a round of levels come in as one stage of bulk copies
-// (cp.async.bulk, one per level row of the tile: the 2C points, started at the 16-byte boundary at
-// or below the row's first point, 16C + 16 bytes) that complete on the stage's shared-memory
-// barrier; thread 0 issues them, every thread waits on the barrier (bounded), reads its value, and
-// after a block barrier thread 0 refills the stage with the round RING levels further on.
 template <int LOGN, int LOGC, bool V0>
 __global__ void __launch_bounds__(kThreads, 4) k_inv_upd(InvUpdArgs a) {
   constexpr bool CT = LOGN > 0;
   constexpr int CT_RING = CT ? inv_ring_levels(1 << LOGN, 1 << LOGC) : 1;
   constexpr int CT_DEPTH = CT ? CT_RING / (kThreads >> (LOGC + 1)) : 1;
-  constexpr bool BULK = CT && !V0;
-  constexpr int ROWB = 16 * (1 << LOGC) + 16;  // bytes of one level slot (BULK)
-  static_assert(!BULK || (CT_DEPTH & (CT_DEPTH - 1)) == 0, "stages: a power of two");
-  static_assert(!BULK || CT_DEPTH <= 64, "stages: at most 64 barriers");
-  __shared__ int s_err;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = CT ? (1 << LOGN) : a.N, M = a.M;
   const int C = CT ? (1 << LOGC) : a.C, logC = CT ? LOGC : a.logC;
@@ -145,31 +94,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_upd(InvUpdArgs a) {
   const int depth = CT ? CT_DEPTH : RING / LPR;  // rounds in flight
   const int m = m0 + q;
   const bool valid = m < M;
-  unsigned char* ringb = reinterpret_cast<unsigned char*>(ring);
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ringb + (size_t)CT_RING * ROWB);
-  if constexpr (BULK) {
-    if (threadIdx.x == 0) {
-      s_err = 0;
-      for (int d = 0; d < CT_DEPTH; ++d) mbar_init(bars + d, 1);
-      mbar_fence_init();
-    }
-  }
-  __syncthreads();  // perm (and the barriers)
-  // stage d: the level rows d LPR .. d LPR + LPR - 1 into their ring slots (BULK; thread 0)
-  auto issue_stage = [&](int d) {
-    unsigned long long* bar = bars + (d & (CT_DEPTH - 1));
-    mbar_arrive_expect(bar, (unsigned)(LPR * ROWB));
-    for (int l = 0; l < LPR; ++l) {
-      const int i = d * LPR + l;
-      const size_t byte = ((size_t)i * M + m0) * sizeof(float2);
-      bulk_g2s(ringb + (size_t)(i & (RING - 1)) * ROWB,
-               reinterpret_cast<const unsigned char*>(a.U) + (byte & ~(size_t)15), (unsigned)ROWB, bar);
-    }
-  };
-  if constexpr (BULK) {
-    if (threadIdx.x == 0)
-      for (int d = 0; d < CT_DEPTH; ++d) issue_stage(d);
-  }
+  __syncthreads();  // perm
 
   // 1. the half spectra straight into the FFT's permuted rows: A_j (real-part point) into row
   //    perm[j], B_j (imaginary-part point) into row perm[N-j]; B_0 and B_{N/2}, whose partner
@@ -187,9 +112,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_upd(InvUpdArgs a) {
   cp_async_commit();
   // 2. the first rounds of U into the ring (one group per round)
   const float2* u_src = a.U + m;
-  if constexpr (BULK) {
-    cp_async_wait_all();
-  } else if constexpr (!V0) {
+  if constexpr (!V0) {
     for (int d = 0; d < depth; ++d) {
       const int i = d * LPR + r0;  // < RING
       if (valid && i < N) cp_async8(ring + (i << logP2) + q, u_src + (size_t)i * M);
@@ -234,42 +157,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_inv_upd(InvUpdArgs a) {
         sc = fmaf(cval, cval, sc);
         su = fmaf(u.hi, u.hi, su);
       }
-    }
-    block_reduce_add2f(sc, su, a.norms);
-    return;
-  }
-  if constexpr (BULK) {
-    const int NR = N / LPR;
-    int d = 0;
-    for (; d < NR; ++d) {
-      const int i = d * LPR + r0;
-      if (!mbar_wait_bounded(bars + (d & (CT_DEPTH - 1)), (unsigned)((d / CT_DEPTH) & 1))) s_err = 1;
-      const float cval = Xf[(size_t)2 * i * C] * __ldg(a.inv_s + i);
-      const size_t row = (size_t)i * M;
-      if (valid) {
-        const size_t off = ((row + m0) * sizeof(float2)) & 15;
-        const float2 r = *reinterpret_cast<const float2*>(ringb + (size_t)(i & (RING - 1)) * ROWB + off +
-                                                          (size_t)q * sizeof(float2));
-        const ff u = ff_add_f(ff{r.x, r.y}, cval);
-        u_dst[row] = make_float2(u.hi, u.lo);
-        sc = fmaf(cval, cval, sc);
-        su = fmaf(u.hi, u.hi, su);
-      }
-      __syncthreads();  // every thread has read its value of stage d
-      if (s_err) break;
-      if (threadIdx.x == 0 && d + CT_DEPTH < NR) {
-        fence_proxy_async_smem();
-        issue_stage(d + CT_DEPTH);
-      }
-    }
-    if (s_err) {
-      // a wait gave up: let the copies in flight land (bounded), report, skip the norms
-      if (threadIdx.x == 0) {
-        for (int e = d; e < NR && e < d + CT_DEPTH; ++e)
-          mbar_wait_bounded(bars + (e & (CT_DEPTH - 1)), (unsigned)((e / CT_DEPTH) & 1));
-        if (a.err) atomicExch(a.err, kDeviceWaitTimeout);
-      }
-      return;
     }
     block_reduce_add2f(sc, su, a.norms);
     return;
@@ -630,7 +517,6 @@ __global__ void k_ctl_init(SolveCtl* c, double tol, double q_floor, int max_swee
     c->max_sweeps = max_sweeps;
     c->m = 0;
     c->done = 0;
-    c->err = 0;
   }
 }
 
@@ -639,13 +525,12 @@ __global__ void k_converge(const double* norms, SolveCtl* c, cudaGraphConditiona
   const double c2 = norms[0], u2 = norms[1];
   const double upd = u2 > 0.0 ? sqrt(c2 / u2) : sqrt(c2);
   const int m = c->m + 1;
-  // a sweep whose device-side wait gave up has no valid update: stop (the host reports it)
-  const bool done = c->err == 0 && stop_decision(m, upd, c->prev, c->tol, c->q_floor);
+  const bool done = stop_decision(m, upd, c->prev, c->tol, c->q_floor);
   c->m = m;
   c->prev = upd;
   c->upd = upd;
   c->done = done ? 1 : 0;
-  cudaGraphSetConditional(h, (!done && m < c->max_sweeps && c->err == 0) ? 1u : 0u);
+  cudaGraphSetConditional(h, (!done && m < c->max_sweeps) ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------

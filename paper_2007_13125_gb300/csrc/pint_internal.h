@@ -53,7 +53,6 @@ struct InvUpdArgs {
   double* norms;                           // [0] += sum c^2, [1] += sum U^2
   int ring;                                // levels in the U staging ring (set by the launcher)
   int maxlog;                              // runtime-shape time FFT: radix <= 2^maxlog (3 or 4; 0: 4)
-  int* err;                                // set to kDeviceWaitTimeout if a bounded wait gives up
   const double* v;                         // first sweep from U_0^n = v: U = v + c ([M]), else null
 };
 
@@ -220,10 +219,8 @@ cudaError_t launch_window_rhs(const double* f, const double* Up, double* F, int 
 // ---- convergence control (shared by the host loop and the graph's device-side check) ----
 struct SolveCtl {
   double tol, q_floor, prev, upd;
-  int max_sweeps, m, done;
-  int err;  // nonzero: a bounded device-side wait gave up (kDeviceWaitTimeout); the solve stops
+  int max_sweeps, m, done, pad;
 };
-constexpr int kDeviceWaitTimeout = 1;
 
 // Whole MIXED solve of a small 1D problem in one CTA (kernels_small.cu): finite differences,
 // Dirichlet, BDF-k, no reaction term; tables as for the multi-kernel sweep (float).

@@ -587,9 +587,7 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   // workspaces
   const size_t NM = (size_t)N * M, JM = (size_t)(N / 2 + 1) * M;
   if (p->prec == PINT_MIXED) {
-    // (+128 pairs: the update kernel's bulk copies start rows at the 16-byte boundary below them
-    // and run 16 C + 16 bytes, past the last row's end by at most that much)
-    if ((s = dalloc(p, &p->Uff, NM + 128)) != PINT_OK) return bail(s);
+    if ((s = dalloc(p, &p->Uff, NM)) != PINT_OK) return bail(s);
   } else if (p->prec == PINT_FP32) {
     if ((s = dalloc(p, &p->Uhi, NM)) != PINT_OK) return bail(s);
     if ((s = dalloc(p, &p->Fhi, NM)) != PINT_OK) return bail(s);
@@ -602,7 +600,6 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   }
   if ((s = dalloc(p, &p->norms, 2)) != PINT_OK) return bail(s);
   if ((s = dalloc(p, &p->ctl, 1)) != PINT_OK) return bail(s);
-  PINT_CUDA_B(cudaMemset(p->ctl, 0, sizeof(SolveCtl)));
   if (p->alloc) {
     p->h_norms = (double*)p->alloc->host_alloc(2 * sizeof(double));
     p->h_ctl = (SolveCtl*)p->alloc->host_alloc(sizeof(SolveCtl));
@@ -1039,7 +1036,6 @@ cudaError_t mixed_update(pint_plan p, const double* v, cudaStream_t st) {
   u.inv_s = p->tf.inv_s; u.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
   u.N = p->N; u.M = p->M; u.C = p->Ci; u.logC = ilog2c(p->Ci); u.norms = p->norms; u.v = v;
   u.maxlog = p->uml;
-  u.err = &p->ctl->err;
   return launch_inv_upd(u, st);
 }
 
@@ -1264,12 +1260,7 @@ pint_status sweep_direct(pint_plan p, const DevTables<T>& t, const T* F, const T
 
 pint_status read_norms(pint_plan p, cudaStream_t st, double* upd) {
   PINT_CUDA(cudaMemcpyAsync(p->h_norms, p->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  PINT_CUDA(cudaMemcpyAsync(&p->h_ctl->err, &p->ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   PINT_CUDA(cudaStreamSynchronize(st));
-  if (p->h_ctl->err) {
-    PINT_CUDA(cudaMemsetAsync(&p->ctl->err, 0, sizeof(int), st));
-    return fail(PINT_ECUDA, "a device-side wait of the sweep gave up (bounded wait)");
-  }
   const double c2 = p->h_norms[0], u2 = p->h_norms[1];
   *upd = u2 > 0.0 ? std::sqrt(c2 / u2) : std::sqrt(c2);
   return PINT_OK;
@@ -1488,8 +1479,6 @@ pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double 
   return PINT_OK;
 }
 
-bool pint::solve_wait_gave_up(pint_plan p) { return p->h_ctl->err != 0; }
-
 void pint::solve_result(pint_plan p, int* sweeps, double* upd, bool* converged) {
   if (sweeps) *sweeps = p->h_ctl->m;
   if (upd) *upd = p->h_ctl->upd;
@@ -1559,7 +1548,6 @@ extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* u
   solve_result(p, &m, &upd, &done);
   if (sweeps_out) *sweeps_out = m;
   if (upd_rel_out) *upd_rel_out = upd;
-  if (solve_wait_gave_up(p)) return fail(PINT_ECUDA, "a device-side wait of the solve gave up (bounded wait)");
   if (!done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
   return PINT_OK;
 }
@@ -1581,7 +1569,6 @@ pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double*
     solve_result(p, &m, &upd, &done);
     if (sweeps_out) *sweeps_out = m;
     if (upd_rel_out) *upd_rel_out = upd;
-    if (solve_wait_gave_up(p)) return fail(PINT_ECUDA, "a device-side wait of the solve gave up (bounded wait)");
     if (!done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
     return PINT_OK;
   }
@@ -1721,8 +1708,6 @@ pint_status batch_impl(pint_plan* plans, int n, const double* const* Fhat, const
     if (sweeps_out) sweeps_out[i] = m;
     if (upd_out) upd_out[i] = upd;
     all = all && done;
-    if (solve_wait_gave_up(plans[i]))
-      return fail(PINT_ECUDA, "a device-side wait of a batch solve gave up (bounded wait)");
   }
   if (!all) return fail(PINT_ENOTCONV, "some problems reached max_sweeps above tol");
   return PINT_OK;

@@ -140,8 +140,6 @@ pint_status solve_enqueue(pint_plan p, const double* F, double* U, double tol, i
                           const double* v = nullptr);
 // Result of the last enqueued solve (valid once its stream work has completed).
 void solve_result(pint_plan p, int* sweeps, double* upd, bool* converged);
-// True if the last enqueued solve stopped because a bounded device-side wait gave up.
-bool solve_wait_gave_up(pint_plan p);
 // Add one solve (prologue, while-loop, epilogue, or the one-CTA solve) of plan p to graph g.
 // v: start from U_0^n = v (MIXED: the first sweep in the prologue; otherwise v is broadcast into U).
 // dep (optional): a node the solve's first node must follow; *last (optional): its final node.
