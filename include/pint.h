@@ -208,6 +208,21 @@ pint_status pint_wr_sweep(pint_plan plan, const double* Fhat, const double* U_pr
 pint_status pint_solve(pint_plan plan, const double* Fhat, double* U, double tol, int max_sweeps,
                        int* sweeps_out, double* upd_rel_out, void* stream);
 
+/* Resume a preempted solve (checkpoint / restart). U [N][M] device holds the iterate U_m left by an
+ * earlier solve of the same problem after sweeps_done sweeps -- for example what pint_solve or
+ * pint_solve_v left in U when it returned PINT_ENOTCONV at max_sweeps = m, saved by the caller and
+ * written back, possibly into another plan with the same description or in another process -- and
+ * upd_last that solve's last relative update (its upd_rel_out). The WR iteration is a stationary
+ * fixed-point iteration (eq. (2.5) / eq. (3.10)), so any iterate is a valid restart point; with the
+ * stopping rule's history restored (the sweep count and the last update) the resumed solve takes
+ * the same sweeps and the same stopping decision as a solve that was not interrupted (PINT_FP64:
+ * bit-identical iterates; PINT_MIXED: the FP64 iterate re-split into double-float differs from the
+ * uninterrupted one by its last bits). max_sweeps bounds the total count (done + new); sweeps_out
+ * reports the total. Sweeps are launched one by one from the host (no graph); the call waits for
+ * `stream`. PINT_EINVAL unless 0 <= sweeps_done <= max_sweeps and upd_last >= 0. */
+pint_status pint_solve_resume(pint_plan plan, const double* Fhat, double* U, int sweeps_done, double upd_last,
+                              double tol, int max_sweeps, int* sweeps_out, double* upd_rel_out, void* stream);
+
 /* pint_solve from the initial guess U_0^n = v of Theorem 2.7 (every level equal to the initial
  * value), without materialising it: for that iterate K U_0 = beta_n M v + A v with
  * beta_n = tau^-alpha sum_{j<n} omega_j (BDF and CQ alike), so the first residual is

@@ -1553,6 +1553,9 @@ extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* u
 }
 
 namespace {
+pint_status solve_sweeps(pint_plan p, const double* Fhat, const double* v, double* U, double tol, int max_sweeps,
+                         int m0, double prev0, int* sweeps_out, double* upd_rel_out, cudaStream_t st);
+
 // pint_solve (v null: from the content of U) and pint_solve_v (from U_0^n = v)
 pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double* U, double tol, int max_sweeps,
                        int* sweeps_out, double* upd_rel_out, cudaStream_t st) {
@@ -1572,7 +1575,6 @@ pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double*
     if (!done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
     return PINT_OK;
   }
-  const size_t NM = (size_t)p->N * p->M;
   cudaError_t e;
   if (use_small(p)) {
     // the one-CTA solve is one launch in either mode (its kernel appears in the profile)
@@ -1585,8 +1587,18 @@ pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double*
     if (!p->h_ctl->done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
     return PINT_OK;
   }
-  double prev = -1.0, upd = 0.0;
-  int m = 0;
+  return solve_sweeps(p, Fhat, v, U, tol, max_sweeps, 0, -1.0, sweeps_out, upd_rel_out, st);
+}
+
+// The sweeps of a solve launched one by one from the host, starting after m0 sweeps whose last
+// relative update was prev0 (m0 = 0, prev0 < 0: a fresh solve; otherwise a resumed one, whose
+// stopping decisions then match those of the uninterrupted solve).
+pint_status solve_sweeps(pint_plan p, const double* Fhat, const double* v, double* U, double tol, int max_sweeps,
+                         int m0, double prev0, int* sweeps_out, double* upd_rel_out, cudaStream_t st) {
+  const size_t NM = (size_t)p->N * p->M;
+  cudaError_t e;
+  double prev = prev0, upd = prev0 > 0.0 ? prev0 : 0.0;
+  int m = m0;
   bool done = false;
   pint_status s = PINT_OK;
   if (v && p->prec != PINT_MIXED && (e = launch_bcast_d(v, U, p->N, p->M, st)) != cudaSuccess)
@@ -1627,6 +1639,16 @@ pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double*
   return PINT_OK;
 }
 }  // namespace
+
+extern "C" pint_status pint_solve_resume(pint_plan p, const double* Fhat, double* U, int sweeps_done,
+                                         double upd_last, double tol, int max_sweeps, int* sweeps_out,
+                                         double* upd_rel_out, void* stream) {
+  if (!p || !Fhat || !U) return fail(PINT_EINVAL, "NULL argument");
+  if (!(tol > 0.0) || max_sweeps < 1 || sweeps_done < 0 || sweeps_done > max_sweeps || !(upd_last >= 0.0))
+    return fail(PINT_EINVAL, "tol > 0, 0 <= sweeps_done <= max_sweeps and upd_last >= 0 are required");
+  return solve_sweeps(p, Fhat, nullptr, U, tol, max_sweeps, sweeps_done, sweeps_done > 0 ? upd_last : -1.0,
+                      sweeps_out, upd_rel_out, (cudaStream_t)stream);
+}
 
 extern "C" pint_status pint_solve(pint_plan p, const double* Fhat, double* U, double tol, int max_sweeps,
                                   int* sweeps_out, double* upd_rel_out, void* stream) {

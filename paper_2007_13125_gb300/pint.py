@@ -103,6 +103,7 @@ def lib():
         "pint_solve_v_async": (_I, [_P, _P, _P, _P, _D, _I, _P]),
         "pint_solve_result": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
         "pint_solve_host": (_I, [_P, _P, _P, _P, _P, _D, _I, _P]),
+        "pint_solve_resume": (_I, [_P, _P, _P, _I, _D, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
         "pint_solve_host_join": (_I, [_P, _P]),
         "pint_plan_tuning": (_I, [_P, ctypes.POINTER(_I), _I]),
         "pint_time_weights": (_I, [_I, _D, _I, ctypes.POINTER(_D)]),
@@ -345,6 +346,17 @@ class Plan:
         upd = _D(0.0)
         st = lib().pint_solve(self.handle, _ptr(Fhat), _ptr(U), float(tol), int(max_sweeps),
                               ctypes.byref(sweeps), ctypes.byref(upd), _stream(stream))
+        if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
+            raise PintError(st, last_error())
+        return st, sweeps.value, upd.value
+
+    def solve_resume(self, Fhat, U, sweeps_done, upd_last, tol=1e-10, max_sweeps=50, stream=None,
+                     raise_on_notconv=True):
+        """Resume a preempted solve from the iterate in U (pint_solve_resume): (status, total sweeps, update)."""
+        sweeps = _I(0)
+        upd = _D(0.0)
+        st = lib().pint_solve_resume(self.handle, _ptr(Fhat), _ptr(U), int(sweeps_done), float(upd_last), float(tol),
+                                     int(max_sweeps), ctypes.byref(sweeps), ctypes.byref(upd), _stream(stream))
         if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
             raise PintError(st, last_error())
         return st, sweeps.value, upd.value
