@@ -41,7 +41,8 @@ def test_resume_matches_the_uninterrupted_solve(kw, prec, tol):
     got, want = U2.cpu().numpy(), U_full.cpu().numpy()
     if prec == "fp64":
         assert np.array_equal(got, want)
-        assert upd_res == upd_full
+        # (the update norm is formed on the device in the graph and on the host here: last bit)
+        assert upd_res == pytest.approx(upd_full, rel=1e-12)
     else:
         assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
     assert rel_l2(got, oracle_solution(p)) <= (1e-10 if prec == "fp64" else 1e-8)
