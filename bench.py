@@ -86,11 +86,12 @@ def algo_bytes(name: str, N: int, M: int) -> float:
 # the kernel's source is unchanged (sha1 of its translation unit); other workloads report null
 NCU_TRAFFIC = {
     "heat2d_255x255_N256_bdf4": {
-        "resid_fwd_ff": (317.10e6, "kernels_resid.cu", "ea51c64f5e96cb1d0117a303ab55145454a99bd4"),
-        "inv_update_v0_ff": (142.02e6, "kernels_time.cu", "52a9807ae8c6d22bb1c383866a1efa3fc7e6abba"),
-        "inv_update_ff": (277.51e6, "kernels_time.cu", "52a9807ae8c6d22bb1c383866a1efa3fc7e6abba"),
-        "dst_f32": (76.13e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
-        "axis_solve_f32": (79.02e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
+        "resid_fwd_ff": (316.92e6, "kernels_resid.cu", "5af68bdb7ccbe5814ceb45b90e186c0227840d7e"),
+        "resid_v0_ff": (167.22e6, "kernels_resid.cu", "5af68bdb7ccbe5814ceb45b90e186c0227840d7e"),
+        "inv_update_v0_ff": (142.00e6, "kernels_time.cu", "1cbdbcdf85d37f489baf91b9682d42622ef022f4"),
+        "inv_update_ff": (277.49e6, "kernels_time.cu", "1cbdbcdf85d37f489baf91b9682d42622ef022f4"),
+        "dst_f32": (76.07e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
+        "axis_solve_f32": (78.60e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
     },
 }
 
