@@ -47,6 +47,7 @@ def algo_bytes(name: str, N: int, M: int) -> float:
         "inv_update_v0_ff": 8 * JM + 8 * NM,    # first sweep: read spectrum; write U (double-float)
         "inv_update_ff": 8 * JM + 16 * NM,      # read spectrum; read + write U (double-float)
         "dst_f32": 16 * JM,                     # read + write spectrum (complex float)
+        "dst_tc_f32": 16 * JM,                  # the same transform as tensor-core products
         "axis_solve_f32": 16 * JM,
         "rhs_f64": 16 * NM,                     # read f, write F_hat
         "cvt_d2ff": 16 * NM,

@@ -122,6 +122,15 @@ typedef struct {
                              amplify rounding with the condition of the line systems), which
                              saves a sweep at tol 1e-8 on a 255 x 255, N = 256 heat problem */
   int space;              /* pint_space (0 = FD, the default when the struct is zeroed) */
+  int xdst;               /* x-direction sine transforms of the FP32 inner solves (Algorithm 1 / 2,
+                             step 2; 2D and 3D finite differences, Dirichlet): 1 = odd-sequence FFT;
+                             2 = a dense product with the sine matrix on the tensor cores (tcgen05;
+                             FP16 operands split in two, three products per term, the accuracy of
+                             the FP32 FFT) where the lines have 255 points, else 1; 3 = whichever
+                             of 1 and 2 runs faster, timed at plan creation (cached per shape);
+                             0 (default) = 2 when the lines have 255 points and there are at least
+                             16384 of them ((N/2 + 1) my mz), else 1. PINT_FP64 plans use 1.
+                             The tensor-core form holds 128 KB of tables on the device. */
 } pint_plan_desc;
 
 /* Build a plan: FP64 constant tables (BDF / CQ weights omega_j of eq. (2.2) / eq. (3.2) --
@@ -268,7 +277,8 @@ pint_status pint_solve_host_join(pint_plan plan, void* stream);
  * width, out[2] CQ-history tile width, out[3] y-direction solver (1 sine transform, 2 recurrence,
  * 4 parallel cyclic reduction), out[4] / out[5] largest FFT radix of the residual / update time
  * transforms (16 for the compiled shapes; 8 or 16 as timed for runtime shapes; 0 when not MIXED),
- * out[6] 1 if the whole solve runs as one CTA. Fills min(n, 7) entries and returns 7 (-1 for a
+ * out[6] 1 if the whole solve runs as one CTA, out[7] x sine transform of the FP32 inner solves
+ * (1 odd-sequence FFT, 2 tensor-core products). Fills min(n, 8) entries and returns 8 (-1 for a
  * NULL plan or out). Host-only. */
 int pint_plan_tuning(pint_plan plan, int* out, int n);
 

@@ -16,7 +16,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libpint.so")
 SOURCES = ["kernels_time.cu", "kernels_resid.cu", "kernels_space.cu", "kernels_nl.cu", "kernels_small.cu", "plan.cu",
-           "server.cu", "noalloc.cu", "host_io.cu"]
+           "server.cu", "noalloc.cu", "host_io.cu", "kernels_dst_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

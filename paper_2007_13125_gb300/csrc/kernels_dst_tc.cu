@@ -1,0 +1,539 @@
+// Sine transform along x of lines of n = 255 points as tensor-core products (tcgen05, sm_103a).
+//
+// The x-direction step of the shifted spatial solves (Algorithm 1 / 2, step 2: A is diagonal on
+// the sine modes, Sec. 2.2) transforms every line of the half spectrum,
+//   Y_k = -2i sum_{x=1}^{255} X_x sin(pi k x / 256),   k = 1..255,
+// the same output as the odd-sequence FFT (k_axis, op 0). Here it is a dense contraction against
+// the sine matrix, folded once: with e_x = X_x - X_{256-x} and o_x = X_x + X_{256-x},
+//   Y_{2k'}   = -2i sum_{x=1}^{127} e_x sin(pi k' x / 128)            (k' = 1..127)
+//   Y_{2k'+1} = -2i sum_{x=1}^{128} o_x sin(pi (2k'+1) x / 256)       (o_128 = X_128, k' = 0..127)
+// (sin(pi k (256 - x) / 256) = -/+ sin(pi k x / 256) for even / odd k). Each half is a 128 x 128
+// matrix times the lines' real and imaginary parts: D = S B^T with M = 128 outputs, K = 128 inputs
+// and N = 64 real rows (32 complex lines per tile).
+//
+// Precision: FP16 operands split in two (v = hi + lo: hi of 11 significant bits by Veltkamp's
+// splitting, lo = v - hi), three products per term (hi hi + hi lo + lo hi, FP32 accumulation in
+// tensor memory): ~22 significant bits per operand, the accuracy of the FP32 FFT it replaces. Every
+// line is scaled by a power of two (its largest |re|, |im| brought to [2^13, 2^14)) so that the
+// FP16 range holds it; the matrices are scaled by 16 (their low parts stay normal numbers). Both
+// scalings are exact and undone in the epilogue.
+//
+// Roles (one CTA per SM, persistent over tiles of 32 lines; the resident matrices fill most of its
+// shared memory):
+//   * load warp: one thread copies each tile's lines (contiguous, 65 KB) into a raw buffer with
+//     bulk asynchronous copies (cp.async.bulk, complete_tx on a shared-memory barrier), as soon as
+//     the staging threads have taken the previous tile out of it;
+//   * 8 staging warps: read their share of the raw tile into registers (then release the buffer),
+//     reduce each line's largest magnitude, fold, scale and split the lines into K-chunks of 32
+//     inputs in the canonical K-major layout (8-row x 16-byte core matrices, no swizzle) in a ring
+//     of two stage slots, and signal each chunk on the slot's "full" barrier; after staging a tile
+//     they run the previous tile's epilogue, so that a tile's MMAs overlap it;
+//   * MMA warp: one thread copies the four matrix operands (hi / lo of both halves, 128 KB, a
+//     precomputed image of their shared-memory layout) once by bulk copies, then for each chunk
+//     waits "full", issues the 12 MMAs (M 128, N 64, K 16) and commits them to the slot's "empty"
+//     barrier; after a tile's last chunk it commits the tile to its accumulator buffer's barrier.
+// Accumulators are double-buffered in tensor memory (2 x 128 columns: D_even and D_odd, 64
+// columns each); the epilogue reads them with tcgen05.ld (one output per lane: TMEM lane = output
+// index), releases the buffer, unscales, applies -2i and writes the lines in place (every read of
+// a tile precedes its writes).
+//
+// Every wait is bounded: a barrier that does not complete within ~2^31 clock cycles sets a shared
+// abort flag (all roles then stop at their next wait or tile) and *err; before the CTA exits, the
+// MMA thread waits (bounded) for every MMA it issued and the load thread for its last copy, and
+// tensor memory is freed.
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "pint_internal.h"
+
+namespace pint {
+namespace {
+
+constexpr int kTcLines = 32;                   // complex lines per tile
+constexpr int kTcN = 2 * kTcLines;             // MMA N: real rows (re 0..31, im 32..63)
+constexpr int kTcChunk = 32;                   // K inputs per stage buffer
+constexpr int kTcChunks = 128 / kTcChunk;      // stage buffers (one tile)
+constexpr int kTcStageThreads = 256;           // staging / epilogue warps
+constexpr int kTcItems = 512 / kTcStageThreads;  // items (line, pair of inputs) per staging thread
+constexpr int kTcLinesPerWarp = kTcLines * 128 / kTcStageThreads;  // epilogue lines per warp
+constexpr int kTcThreads = kTcStageThreads + 64;  // + the MMA warp and the load warp
+constexpr int kTcMatBytes = 128 * 128 * 2;     // one 128 x 128 FP16 operand
+constexpr int kTcABytes = 4 * kTcMatBytes;     // even hi, even lo, odd hi, odd lo
+constexpr int kTcOpBytes = kTcN * kTcChunk * 2;  // one B operand of one stage
+constexpr int kTcStageBytes = 4 * kTcOpBytes;
+constexpr int kTcSlots = 2;                    // stage slots (ring of K-chunks)
+constexpr int kTcLineBytes = 255 * 8;          // one line of complex FP32 values
+constexpr int kTcRawOff = kTcABytes + kTcSlots * kTcStageBytes;    // the tile's lines as read
+constexpr int kTcMiscOff = kTcRawOff + 65536;
+constexpr int kTcSmemBytes = kTcMiscOff + 1536;
+constexpr int kTcTmemCols = 256;                // two accumulator buffers of 128 columns
+constexpr long long kTcWaitCycles = 1ll << 31;
+
+// instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B FP16 (formats 0), both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+struct TcMisc {
+  unsigned long long bar_a;                 // matrix image copied
+  unsigned long long full[kTcSlots];        // stage slot written (the staging threads arrive)
+  unsigned long long empty[kTcSlots];       // stage slot's MMAs done (tcgen05.commit)
+  unsigned long long raw_full;              // the tile's lines copied (bulk copies complete)
+  unsigned long long raw_empty;             // the tile's lines read out (the staging threads arrive)
+  unsigned long long acc_full[2];           // accumulator buffer complete (tcgen05.commit)
+  unsigned long long acc_empty[2];          // accumulator buffer read out (256 threads arrive)
+  unsigned long long fin;                   // every MMA done (tcgen05.commit, at exit)
+  float pmax[4][kTcLines];                  // per line and group of inputs: largest |re|, |im|
+  float unscale[2][kTcLines];               // per accumulator buffer and line: 2 / (16 * 2^s)
+  uint32_t tmem;                            // tensor-memory base address
+  uint32_t abort;                           // a wait gave up: every role stops
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start >> 4, leading (K-direction) core-matrix stride >> 4,
+// stride (M/N-direction) core-matrix stride >> 4, descriptor version 1 (bit 46), no swizzle
+__device__ __forceinline__ uint64_t mat_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// wait for the phase of the given parity to complete, for at most kTcWaitCycles; gives up at
+// once when *abort (a shared flag, if given) is set
+__device__ bool bar_wait(uint32_t bar, uint32_t parity, const uint32_t* abort) {
+  const long long t0 = clock64();
+  while (!bar_try(bar, parity)) {
+    if (abort && *reinterpret_cast<const volatile uint32_t*>(abort)) return false;
+    if (clock64() - t0 > kTcWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of (row, k) in a K-major operand of `rows` rows: core matrices of 8 rows x 8 FP16,
+// rows of a core matrix 16 bytes apart, core matrices along rows 128 bytes apart (SBO), along K
+// rows / 8 * 128 bytes apart (LBO)
+__device__ __forceinline__ uint32_t kmajor_off(int row, int k, int rows) {
+  return (uint32_t)((k >> 3) * (rows / 8) * 128 + (row >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// two FP16 values packed in 32 bits (a in the low half), rounded to nearest
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+
+// v = hi + lo with hi of 11 significant bits (Veltkamp's splitting with the factor 2^13 + 1; the
+// products and sums are rounded separately, never fused), lo = v - hi exactly; both then as FP16
+// (hi exactly for |v| >= 2^-14, lo rounded: ~2^-24 |v|). Returns the hi pair, *lo the lo pair.
+__device__ __forceinline__ uint32_t split2(float a, float b, uint32_t* lo) {
+  const float ca = __fmul_rn(a, 8193.f), cb = __fmul_rn(b, 8193.f);
+  const float ha = __fsub_rn(ca, __fsub_rn(ca, a)), hb = __fsub_rn(cb, __fsub_rn(cb, b));
+  *lo = pack_f16x2(__fsub_rn(a, ha), __fsub_rn(b, hb));
+  return pack_f16x2(ha, hb);
+}
+
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_dst255_tc(DstTcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  TcMisc& ms = *reinterpret_cast<TcMisc*>(smem + kTcMiscOff);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t sA = smem_u32(smem), sB = sA + kTcABytes;
+  const int tiles = (a.lines + kTcLines - 1) / kTcLines;
+  const uint32_t* abort = reinterpret_cast<const uint32_t*>(&ms.abort);
+
+  if (tid == 0) {
+    auto init = [](unsigned long long* b, int count) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+    };
+    init(&ms.bar_a, 1);
+    for (int c = 0; c < kTcSlots; ++c) {
+      init(&ms.full[c], kTcStageThreads);
+      init(&ms.empty[c], 1);
+    }
+    init(&ms.raw_full, 1);
+    init(&ms.raw_empty, kTcStageThreads);
+    for (int b2 = 0; b2 < 2; ++b2) {
+      init(&ms.acc_full[b2], 1);
+      init(&ms.acc_empty[b2], kTcStageThreads);
+    }
+    init(&ms.fin, 1);
+    ms.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ms.tmem)),
+                 "r"(kTcTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = ms.tmem;
+
+  if (warp == kTcStageThreads / 32) {
+    // ---- MMA warp: one thread issues every MMA of the CTA ----
+    if (lane == 0) {
+      const uint32_t ba = smem_u32(&ms.bar_a);
+      // the four matrix operands: one image, copied in four bulk copies of 32 KB
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ba), "r"(kTcABytes) : "memory");
+      for (int i = 0; i < 4; ++i)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                sA + i * kTcMatBytes),
+            "l"(reinterpret_cast<const unsigned char*>(a.tab) + (size_t)i * kTcMatBytes), "r"(kTcMatBytes),
+            "r"(ba)
+            : "memory");
+      bool ok = bar_wait(ba, 0u, abort);
+      // descriptors of the first K step; a later step adds its byte offset >> 4 to the start field
+      const uint64_t dA[4] = {mat_desc(sA + 0 * kTcMatBytes, 16 * 128, 128), mat_desc(sA + 1 * kTcMatBytes, 16 * 128, 128),
+                              mat_desc(sA + 2 * kTcMatBytes, 16 * 128, 128), mat_desc(sA + 3 * kTcMatBytes, 16 * 128, 128)};
+      int i = 0;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+        const int b2 = i & 1;
+        if (i >= 2) ok = bar_wait(smem_u32(&ms.acc_empty[b2]), (uint32_t)(((i >> 1) - 1) & 1), abort);
+        tc_after_sync();
+        const uint32_t dacc = tmem + (uint32_t)(b2 * 2 * kTcN);
+        for (int c = 0; c < kTcChunks && ok; ++c) {
+          const int u = 2 * i + (c >> 1);  // use of the chunk's slot (c & 1)
+          ok = bar_wait(smem_u32(&ms.full[c & 1]), (uint32_t)(u & 1), abort);
+          if (!ok) break;
+          tc_after_sync();
+          const uint32_t stage = sB + (c & 1) * kTcStageBytes;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t d = dacc + (uint32_t)(h * kTcN);
+            const uint64_t dbh0 = mat_desc(stage + (2 * h) * kTcOpBytes, (kTcN / 8) * 128, 128);
+            const uint64_t dbl0 = mat_desc(stage + (2 * h + 1) * kTcOpBytes, (kTcN / 8) * 128, 128);
+#pragma unroll
+            for (int ks = 0; ks < kTcChunk / 16; ++ks) {
+              const int kg = c * (kTcChunk / 16) + ks;  // 16-input step within the 128 inputs
+              const uint64_t aoff = (uint64_t)(kg * 2 * 16 * 128) >> 4;  // two core matrices along K
+              const uint64_t boff = (uint64_t)(ks * 2 * (kTcN / 8) * 128) >> 4;
+              mma_f16(d, dA[2 * h] + aoff, dbh0 + boff, (c | ks) ? 1u : 0u);
+              mma_f16(d, dA[2 * h] + aoff, dbl0 + boff, 1u);
+              mma_f16(d, dA[2 * h + 1] + aoff, dbh0 + boff, 1u);
+            }
+          }
+          mma_commit(smem_u32(&ms.empty[c & 1]));  // the slot is free once these MMAs are done
+        }
+        if (ok) mma_commit(smem_u32(&ms.acc_full[b2]));  // the tile's accumulators are complete
+      }
+      if (!ok) {
+        atomicExch(&ms.abort, 1u);
+        atomicExch(a.err, 1);
+      }
+      // the matrix image has landed and every MMA issued by this thread has completed before the
+      // CTA exits and tensor memory is freed (bounded)
+      bar_wait(ba, 0u, nullptr);
+      const uint32_t fin = smem_u32(&ms.fin);
+      mma_commit(fin);
+      bar_wait(fin, 0u, nullptr);
+    }
+  } else if (warp == kTcStageThreads / 32 + 1) {
+    // ---- load warp: one thread copies each tile's lines (contiguous) into the raw buffer as soon
+    // as the staging threads have read the previous tile's out of it ----
+    if (lane == 0) {
+      const uint32_t rf = smem_u32(&ms.raw_full), sraw = sA + kTcRawOff;
+      bool ok = true;
+      int i = 0;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+        if (i >= 1) ok = bar_wait(smem_u32(&ms.raw_empty), (uint32_t)((i - 1) & 1), abort);
+        if (!ok) break;
+        const long long first = (long long)t * kTcLines;
+        const int n = (int)(a.lines - first < kTcLines ? a.lines - first : kTcLines);
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(a.S + first * 255);
+        // bulk copies move multiples of 16 bytes: an odd count of lines leaves the last value
+        // of the last line (8 bytes) to a plain copy, written before the arrive that publishes it
+        const uint32_t bytes = (uint32_t)n * kTcLineBytes - ((n & 1) ? 8u : 0u);
+        if (n & 1) {
+          const float2 v = *reinterpret_cast<const float2*>(src + bytes);
+          asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(sraw + bytes), "f"(v.x), "f"(v.y) : "memory");
+        }
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(rf), "r"(bytes) : "memory");
+        for (uint32_t off = 0; off < bytes; off += 16384u) {
+          const uint32_t len = bytes - off < 16384u ? bytes - off : 16384u;
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                           sraw + off),
+                       "l"(src + off), "r"(len), "r"(rf)
+                       : "memory");
+        }
+      }
+      if (!ok) atomicExch(&ms.abort, 1u);
+      // the last copies have landed before the CTA exits (bounded)
+      if (i > 0) bar_wait(rf, (uint32_t)((i - 1) & 1), nullptr);
+    }
+  } else {
+    // ---- staging / epilogue warps ----
+    // barrier of the staging threads that also returns, to all of them, whether any saw the
+    // abort flag set (one decision for all, so that they leave the loop together)
+    auto ssync_abort = [&]() -> bool {
+      const uint32_t f = *reinterpret_cast<volatile uint32_t*>(&ms.abort);
+      uint32_t any;
+      asm volatile(
+          "{\n\t.reg .pred q, p;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+          "bar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+          : "=r"(any)
+          : "r"(f), "r"(kTcStageThreads)
+          : "memory");
+      return any != 0;
+    };
+    // item (line l, pair q, group g8) of a tile, item = tid + j * threads: for each chunk c,
+    // X_x, X_{x+1}, X_{256-x}, X_{255-x} with x = 32 c + 8 g8 + 2 q + 1 (32 lines x 16 pairs of
+    // inputs = 512 items)
+    int il[kTcItems], ikl[kTcItems];
+    uint32_t iore[kTcItems], ioim[kTcItems];
+#pragma unroll
+    for (int j = 0; j < kTcItems; ++j) {
+      const int item = tid + j * kTcStageThreads;
+      const int q = item & 3, rl = (item >> 2) & 7, g8 = (item >> 5) & 3, rh = (item >> 7) & 3;
+      il[j] = rh * 8 + rl;
+      ikl[j] = g8 * 8 + 2 * q;  // K index within a chunk (even)
+      iore[j] = kmajor_off(il[j], ikl[j], kTcN);
+      ioim[j] = kmajor_off(kTcLines + il[j], ikl[j], kTcN);
+    }
+    const float2* raw = reinterpret_cast<const float2*>(smem + kTcRawOff);
+    // epilogue of the j-th tile of this CTA (tile index tj): lanes 32 (warp % 4) .. + 31 of tensor
+    // memory hold output index m; each group of four warps takes kTcLinesPerWarp lines
+    auto epilogue = [&](int j, int tj) {
+      const int b2 = j & 1;
+      if (!bar_wait(smem_u32(&ms.acc_full[b2]), (uint32_t)((j >> 1) & 1), abort)) atomicExch(&ms.abort, 1u);
+      tc_after_sync();
+      const int m = 32 * (warp & 3) + lane;
+      const int l0 = kTcLinesPerWarp * (warp >> 2);
+      const uint32_t tl = tmem + (uint32_t)(b2 * 2 * kTcN) + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll
+      for (int h8 = 0; h8 < kTcLinesPerWarp; h8 += 8) {
+        float ere[8], eim[8], orr[8], oim8[8];
+        tmem_ld8(tl + (uint32_t)(0 * kTcN + l0 + h8), ere);
+        tmem_ld8(tl + (uint32_t)(0 * kTcN + kTcLines + l0 + h8), eim);
+        tmem_ld8(tl + (uint32_t)(1 * kTcN + l0 + h8), orr);
+        tmem_ld8(tl + (uint32_t)(1 * kTcN + kTcLines + l0 + h8), oim8);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (h8 + 8 == kTcLinesPerWarp) {
+          tc_before_sync();
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.acc_empty[b2])) : "memory");
+        }
+        if (!*reinterpret_cast<volatile uint32_t*>(&ms.abort)) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int lu = l0 + h8 + u;
+            const long long line = (long long)tj * kTcLines + lu;
+            if (line >= a.lines) break;
+            const float us = ms.unscale[b2][lu];
+            float2* row = a.S + line * 255;
+            // -2i z = (2 Im z, -2 Re z); index 2m: k = 2m + 1 (odd half), 2m + 1: k = 2m + 2 (even half)
+            const float2 yo = make_float2(oim8[u] * us, -orr[u] * us);
+            const float2 ye = make_float2(eim[u] * us, -ere[u] * us);
+            if ((line & 1) == 0 && m < 127) {
+              // even lines start on a 16-byte boundary (255 values of 8 bytes per line)
+              *reinterpret_cast<float4*>(row + 2 * m) = make_float4(yo.x, yo.y, ye.x, ye.y);
+            } else {
+              row[2 * m] = yo;
+              if (m < 127) row[2 * m + 1] = ye;
+            }
+          }
+        }
+      }
+    };
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+      const int b2 = i & 1;
+      // the tile's inputs, from the raw buffer into registers; then the buffer is released
+      if (!bar_wait(smem_u32(&ms.raw_full), (uint32_t)(i & 1), abort)) atomicExch(&ms.abort, 1u);
+      float2 in[kTcItems][kTcChunks][4];
+#pragma unroll
+      for (int j = 0; j < kTcItems; ++j) {
+        const bool okl = (long long)t * kTcLines + il[j] < a.lines;
+        const float2* row = raw + il[j] * 255;
+#pragma unroll
+        for (int c = 0; c < kTcChunks; ++c) {
+          const int x = c * kTcChunk + ikl[j] + 1;
+          const float2 z = make_float2(0.f, 0.f);
+          in[j][c][0] = okl ? row[x - 1] : z;
+          in[j][c][1] = okl ? row[x] : z;
+          in[j][c][2] = okl ? row[255 - x] : z;
+          in[j][c][3] = okl ? row[254 - x] : z;
+        }
+      }
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.raw_empty)) : "memory");
+      // largest |re|, |im| of each line: over the item, its four lanes (q), the four warps
+      // holding the line's groups (g8)
+#pragma unroll
+      for (int j = 0; j < kTcItems; ++j) {
+        float m = 0.f;
+#pragma unroll
+        for (int c = 0; c < kTcChunks; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) m = fmaxf(m, fmaxf(fabsf(in[j][c][k].x), fabsf(in[j][c][k].y)));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        if ((ikl[j] & 7) == 0) ms.pmax[ikl[j] >> 3][il[j]] = m;
+      }
+      if (ssync_abort()) break;
+      float sc[kTcItems];
+#pragma unroll
+      for (int j = 0; j < kTcItems; ++j) {
+        const int l = il[j];
+        const float m = fmaxf(fmaxf(ms.pmax[0][l], ms.pmax[1][l]), fmaxf(ms.pmax[2][l], ms.pmax[3][l]));
+        // m = f 2^E, f in [0.5, 1): the scale 2^(14 - E) brings m to [2^13, 2^14)
+        const int E = m > 0.f ? (int)((__float_as_uint(m) >> 23) & 0xff) - 126 : 14;
+        int sh = 14 - E;
+        sh = sh > 100 ? 100 : (sh < -100 ? -100 : sh);
+        sc[j] = __uint_as_float((uint32_t)(127 + sh) << 23);
+        if (ikl[j] == 0) ms.unscale[b2][l] = __uint_as_float((uint32_t)(127 - sh - 3) << 23);  // 2/(16 2^sh)
+      }
+      // fold, scale and split chunk by chunk into the stage slots (each free once the MMAs of
+      // its previous chunk are done), then signal the MMA warp
+#pragma unroll
+      for (int c = 0; c < kTcChunks; ++c) {
+        const int u = 2 * i + (c >> 1);  // use of the chunk's slot (c & 1)
+        if (u >= 1 && !bar_wait(smem_u32(&ms.empty[c & 1]), (uint32_t)((u - 1) & 1), abort))
+          atomicExch(&ms.abort, 1u);
+        const uint32_t stage = sB + (c & 1) * kTcStageBytes;
+#pragma unroll
+        for (int j = 0; j < kTcItems; ++j) {
+          const float2 a0 = in[j][c][0], a1 = in[j][c][1], b0 = in[j][c][2], b1 = in[j][c][3];
+          const float f = sc[j];
+          const float2 e0 = make_float2((a0.x - b0.x) * f, (a0.y - b0.y) * f);
+          const float2 e1 = make_float2((a1.x - b1.x) * f, (a1.y - b1.y) * f);
+          const float2 o0 = make_float2((a0.x + b0.x) * f, (a0.y + b0.y) * f);
+          const float2 o1 = make_float2((a1.x + b1.x) * f, (a1.y + b1.y) * f);
+          uint32_t lo;
+          uint32_t hi = split2(e0.x, e1.x, &lo);
+          sts32(stage + 0 * kTcOpBytes + iore[j], hi);
+          sts32(stage + 1 * kTcOpBytes + iore[j], lo);
+          hi = split2(e0.y, e1.y, &lo);
+          sts32(stage + 0 * kTcOpBytes + ioim[j], hi);
+          sts32(stage + 1 * kTcOpBytes + ioim[j], lo);
+          hi = split2(o0.x, o1.x, &lo);
+          sts32(stage + 2 * kTcOpBytes + iore[j], hi);
+          sts32(stage + 3 * kTcOpBytes + iore[j], lo);
+          hi = split2(o0.y, o1.y, &lo);
+          sts32(stage + 2 * kTcOpBytes + ioim[j], hi);
+          sts32(stage + 3 * kTcOpBytes + ioim[j], lo);
+        }
+        fence_async_smem();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.full[c & 1])) : "memory");
+      }
+      // the previous tile's epilogue runs now, while this tile's MMAs execute
+      if (i >= 1) epilogue(i - 1, t - (int)gridDim.x);
+    }
+    if (i >= 1 && !*reinterpret_cast<volatile uint32_t*>(&ms.abort)) epilogue(i - 1, blockIdx.x + (i - 1) * (int)gridDim.x);
+    if (tid == 0 && *reinterpret_cast<volatile uint32_t*>(&ms.abort)) atomicExch(a.err, 1);
+  }
+  tc_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+  }
+}
+
+static_assert(sizeof(TcMisc) <= 1536, "barrier block");
+static_assert(kTcLines * kTcLineBytes <= 65536, "raw tile");
+static_assert(kTcSmemBytes <= 227 * 1024, "shared memory");
+
+}  // namespace
+
+size_t dst_tc_table_bytes() { return (size_t)kTcABytes; }
+
+// The matrix image in its shared-memory layout: [even hi | even lo | odd hi | odd lo], each
+// 128 x 128 FP16 K-major (row = output, K = input x - 1), scaled by 16.
+//   even: row r -> k' = r + 1, column q -> x = q + 1: 16 sin(pi k' x / 128) (zero for k' = 128
+//         or x = 128)
+//   odd:  row r -> k' = r,     column q -> x = q + 1: 16 sin(pi (2k'+1) x / 256), halved at
+//         x = 128 (the folded input there is 2 X_128)
+void dst_tc_table(unsigned short* img) {
+  const double pi = 3.14159265358979323846;
+  for (int h = 0; h < 2; ++h)
+    for (int r = 0; r < 128; ++r)
+      for (int q = 0; q < 128; ++q) {
+        const int x = q + 1;
+        double v;
+        if (h == 0) {
+          const int kp = r + 1;
+          v = (kp == 128 || x == 128) ? 0.0 : 16.0 * std::sin(pi * (double)((kp * x) % 256) / 128.0);
+        } else {
+          v = 16.0 * std::sin(pi * (double)(((2 * r + 1) * x) % 512) / 256.0);
+          if (x == 128) v *= 0.5;
+        }
+        const __half hi = __double2half(v);
+        const __half lo = __double2half(v - (double)__half2float(hi));
+        const int off = ((q >> 3) * 16 * 128 + (r >> 3) * 128 + (r & 7) * 16 + (q & 7) * 2) / 2;
+        img[(2 * h) * (kTcMatBytes / 2) + off] = __half_as_ushort(hi);
+        img[(2 * h + 1) * (kTcMatBytes / 2) + off] = __half_as_ushort(lo);
+      }
+}
+
+cudaError_t launch_dst_tc(const DstTcArgs& a, cudaStream_t st) {
+  static int sms = 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_dst255_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (a.lines <= 0) return cudaSuccess;
+  const int tiles = (a.lines + kTcLines - 1) / kTcLines;
+  const int grid = tiles < sms ? tiles : sms;
+  prof_begin("dst_tc_f32", st);
+  k_dst255_tc<<<grid, kTcThreads, kTcSmemBytes, st>>>(a);
+  prof_end(st);
+  return cudaGetLastError();
+}
+
+}  // namespace pint

@@ -517,6 +517,7 @@ __global__ void k_ctl_init(SolveCtl* c, double tol, double q_floor, int max_swee
     c->max_sweeps = max_sweeps;
     c->m = 0;
     c->done = 0;
+    c->err = 0;
   }
 }
 
@@ -525,12 +526,12 @@ __global__ void k_converge(const double* norms, SolveCtl* c, cudaGraphConditiona
   const double c2 = norms[0], u2 = norms[1];
   const double upd = u2 > 0.0 ? sqrt(c2 / u2) : sqrt(c2);
   const int m = c->m + 1;
-  const bool done = stop_decision(m, upd, c->prev, c->tol, c->q_floor);
+  const bool done = c->err == 0 && stop_decision(m, upd, c->prev, c->tol, c->q_floor);
   c->m = m;
   c->prev = upd;
   c->upd = upd;
   c->done = done ? 1 : 0;
-  cudaGraphSetConditional(h, (!done && m < c->max_sweeps) ? 1u : 0u);
+  cudaGraphSetConditional(h, (!done && m < c->max_sweeps && c->err == 0) ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------

@@ -128,6 +128,19 @@ template <typename T> struct AxisArgs {
   int C, logC, ld;
 };
 
+// Sine transform along x of lines of 255 points as tensor-core products (kernels_dst_tc.cu): the
+// output of AxisArgs op 0 (Y_k = -2i sum_x X_x sin(pi k x / 256)), in place on `lines`
+// consecutive lines of 255 complex values.
+struct DstTcArgs {
+  float2* S;                               // lines [lines][255] (in place)
+  const void* tab;                         // matrix image, dst_tc_table_bytes() (16-byte aligned)
+  int lines;
+  int* err;                                // set to 1 if a bounded wait of the kernel gave up
+};
+size_t dst_tc_table_bytes();
+void dst_tc_table(unsigned short* img);    // host: fills the image (dst_tc_table_bytes() / 2 halves)
+cudaError_t launch_dst_tc(const DstTcArgs& a, cudaStream_t st);
+
 // Toeplitz tridiagonal solve along y (2D, after the x sine transform): for each line (j, p),
 // (s_j + lambda_p^x + 2 g) q_y - g (q_{y-1} + q_{y+1}) = b_y, g = 1/h_y^2, through the
 // factorisation T = (g/r)(I - r Z)(I - r Z^T) + g r e_0 e_0^T, r + 1/r = d/g, |r| < 1.
@@ -219,7 +232,8 @@ cudaError_t launch_window_rhs(const double* f, const double* Up, double* F, int 
 // ---- convergence control (shared by the host loop and the graph's device-side check) ----
 struct SolveCtl {
   double tol, q_floor, prev, upd;
-  int max_sweeps, m, done, pad;
+  int max_sweeps, m, done;
+  int err;  // nonzero: a bounded device-side wait gave up; the solve stops and reports PINT_ECUDA
 };
 
 // Whole MIXED solve of a small 1D problem in one CTA (kernels_small.cu): finite differences,

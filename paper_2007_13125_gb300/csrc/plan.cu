@@ -469,6 +469,12 @@ void destroy_plan(pint_plan p) {
 
 namespace {
 pint_status autotune_ysolve(pint_plan p);
+pint_status autotune_xdst(pint_plan p);
+// the tensor-core x sine transform serves lines of 255 points of FP32 inner solves (2D / 3D,
+// Dirichlet finite differences)
+bool dst_tc_applies(pint_plan p) {
+  return p->mx == 255 && (p->dim == 2 || p->dim == 3) && !p->periodic && !p->fem && p->prec != PINT_FP64;
+}
 pint_status tune_time_tiles(pint_plan p, int cmax_t, int cmax_z);
 pint_status tune_radix(pint_plan p);
 }
@@ -486,6 +492,7 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   if (d->eig == PINT_EIG_CLOSED_FORM && d->alpha != 1.0 && d->precision != PINT_MIXED)
     return fail(PINT_EINVAL, "CLOSED_FORM eigenvalues with alpha < 1 need the residual form (PINT_MIXED)");
   if (d->ysolve < 0 || d->ysolve > 4) return fail(PINT_EINVAL, "bad ysolve variant");
+  if (d->xdst < 0 || d->xdst > 3) return fail(PINT_EINVAL, "bad xdst variant");
   if (d->space != PINT_SPACE_FD && d->space != PINT_SPACE_FEM_P1 && d->space != PINT_SPACE_PERIODIC)
     return fail(PINT_EINVAL, "bad space discretisation");
   if (d->space == PINT_SPACE_FEM_P1 && d->grid.dim != 1)
@@ -644,6 +651,19 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   p->Czl = pick_cols((size_t)2 * (p->mz + 1) * ve, 64 * 1024, 16, 1);
   p->Ctri = pick_cols((size_t)p->my * sizeof(float2), 72 * 1024, 32, 1);
   PINT_CUDA_B(cudaMemset(p->S, 0, JM * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2))));
+  PINT_CUDA_B(cudaMemset(p->ctl, 0, sizeof(SolveCtl)));
+  p->xdst = 1;
+  // default (0): the tensor-core transform where it applies and the lines fill the GPU (at least
+  // 16384 lines, ~3.4 tiles of 32 per SM; below that the FFT's four CTAs per SM keep it ahead)
+  const long long xlines = (long long)(N / 2 + 1) * p->my * p->mz;
+  const bool tc_default = d->xdst == 0 && xlines >= 16384;
+  if (dst_tc_applies(p) && (d->xdst >= 2 || tc_default)) {
+    std::vector<unsigned short> img(dst_tc_table_bytes() / 2);
+    dst_tc_table(img.data());
+    if ((s = upload(p, &p->dst_tab, img)) != PINT_OK) return bail(s);
+    p->xdst = 2;
+    if (d->xdst == 3 && (s = autotune_xdst(p)) != PINT_OK) return bail(s);
+  }
   p->ysolve = 1;
   if (p->dim == 2 && p->prec != PINT_FP64 && !p->periodic) {
     if (d->ysolve == 2) p->ysolve = 2;
@@ -830,6 +850,20 @@ void split_ff(double x, float& hi, float& lo) {
 
 template <typename T> bool ysolve_tri(pint_plan p) { return sizeof(T) == 4 && (p->ysolve == 2 || p->ysolve == 4); }
 
+// x sine transform (AxisArgs op 0) of `lines` lines: the odd-sequence FFT, or for FP32 lines of
+// 255 points on a plan that selected it, the tensor-core products
+template <typename T> cudaError_t xform_x(pint_plan p, const AxisArgs<T>& ax, cudaStream_t st) {
+  if (sizeof(T) == 4 && p->xdst == 2) {
+    DstTcArgs g{};
+    g.S = reinterpret_cast<float2*>(ax.S);
+    g.tab = p->dst_tab;
+    g.lines = ax.lines;
+    g.err = &p->ctl->err;
+    return launch_dst_tc(g, st);
+  }
+  return launch_axis(ax, st);
+}
+
 // spatial step on the half spectrum for T (float: MIXED/FP32, double: FP64)
 // mass and stiffness rows (diagonal, off-diagonal) of a 1D plan: finite differences (1, 0) and
 // (2/h^2, -1/h^2); P1 elements (4h/6, h/6) and (2/h, -1/h)
@@ -892,11 +926,11 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
     az.scale = (T)(8.0 * (p->mx + 1) * (double)(p->my + 1) * (double)(p->mz + 1));
     az.lines_per_j = p->mx * p->my; az.tw = t.tw_z; az.C = p->Czl; az.logC = ilog2c(p->Czl); az.ld = p->Czl + 1;
     cudaError_t e;
-    if ((e = launch_axis(ax, st)) != cudaSuccess) return e;
+    if ((e = xform_x(p, ax, st)) != cudaSuccess) return e;
     if ((e = launch_axis(ay, st)) != cudaSuccess) return e;
     if ((e = launch_axis(az, st)) != cudaSuccess) return e;
     if ((e = launch_axis(ay, st)) != cudaSuccess) return e;
-    return launch_axis(ax, st);
+    return xform_x(p, ax, st);
   }
   if (p->dim == 1) {
     AxisArgs<T> a{};
@@ -909,7 +943,7 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
   AxisArgs<T> ax{};
   ax.S = p->S; ax.n = p->mx; ax.lines = J * p->my; ax.mode = 0; ax.P = 1; ax.op = 0;
   ax.lines_per_j = p->my; ax.tw = t.tw_x; ax.C = p->Cx; ax.logC = ilog2c(p->Cx); ax.ld = p->Cx + 1;
-  cudaError_t e = launch_axis(ax, st);
+  cudaError_t e = xform_x(p, ax, st);
   if (e != cudaSuccess) return e;
   if (ysolve_tri<T>(p)) {
     TriArgs tr{};
@@ -927,7 +961,62 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
     e = launch_axis(ay, st);
   }
   if (e != cudaSuccess) return e;
-  return launch_axis(ax, st);
+  return xform_x(p, ax, st);
+}
+
+// Time the x sine transforms (odd-sequence FFT, tensor-core products) on this plan's workspace and
+// keep the faster; cached per (N, my, mz, dim) for the process.
+pint_status autotune_xdst(pint_plan p) {
+  static std::mutex mu;
+  static std::vector<std::pair<long long, int>> cache;
+  const long long key = (((long long)p->N * 4096 + p->my) * 4096 + p->mz) * 4 + p->dim;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& kv : cache)
+      if (kv.first == key) { p->xdst = kv.second; return PINT_OK; }
+  }
+  cudaStream_t st;
+  PINT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  AxisArgs<float> ax{};
+  ax.S = p->S; ax.n = p->mx; ax.lines = (p->N / 2 + 1) * p->my * p->mz; ax.mode = 0; ax.P = 1; ax.op = 0;
+  ax.lines_per_j = p->my * p->mz; ax.tw = p->tf.tw_x; ax.C = p->Cx; ax.logC = ilog2c(p->Cx); ax.ld = p->Cx + 1;
+  float best = 1e30f;
+  int bestv = 1;
+  const bool prof = g_prof_on;
+  g_prof_on = false;
+  for (int v : {1, 2}) {
+    p->xdst = v;
+    cudaError_t e = xform_x<float>(p, ax, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 4 && e == cudaSuccess; ++r) e = xform_x<float>(p, ax, st);
+    cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      g_prof_on = prof;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaStreamDestroy(st);
+      return cuda_fail(e, "x sine transform tuning");
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; bestv = v; }
+  }
+  g_prof_on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  p->xdst = bestv;
+  // the timing ran on the zeroed workspace; the device error flag must still be clear
+  int err = 0;
+  PINT_CUDA(cudaMemcpy(&err, &p->ctl->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) return fail(PINT_ECUDA, "x sine transform tuning: a device-side wait gave up");
+  std::lock_guard<std::mutex> lk(mu);
+  cache.emplace_back(key, bestv);
+  return PINT_OK;
 }
 
 // Time the y-direction solvers (sine transform, thread-per-line recurrence, parallel cyclic
@@ -1260,7 +1349,12 @@ pint_status sweep_direct(pint_plan p, const DevTables<T>& t, const T* F, const T
 
 pint_status read_norms(pint_plan p, cudaStream_t st, double* upd) {
   PINT_CUDA(cudaMemcpyAsync(p->h_norms, p->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PINT_CUDA(cudaMemcpyAsync(&p->h_ctl->err, &p->ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   PINT_CUDA(cudaStreamSynchronize(st));
+  if (p->h_ctl->err) {
+    PINT_CUDA(cudaMemsetAsync(&p->ctl->err, 0, sizeof(int), st));
+    return fail(PINT_ECUDA, "a device-side wait of the sweep gave up (bounded wait)");
+  }
   const double c2 = p->h_norms[0], u2 = p->h_norms[1];
   *upd = u2 > 0.0 ? std::sqrt(c2 / u2) : std::sqrt(c2);
   return PINT_OK;
@@ -1479,6 +1573,8 @@ pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double 
   return PINT_OK;
 }
 
+bool pint::solve_wait_gave_up(pint_plan p) { return p->h_ctl->err != 0; }
+
 void pint::solve_result(pint_plan p, int* sweeps, double* upd, bool* converged) {
   if (sweeps) *sweeps = p->h_ctl->m;
   if (upd) *upd = p->h_ctl->upd;
@@ -1497,6 +1593,7 @@ size_t pint::plan_bytes_estimate(const pint_plan_desc* d) {
   else b += 16 * JM;
   if (d->alpha != 1.0) b += 8 * NM;
   b += 64 * (N + d->grid.mx + d->grid.my) + 65536;  // tables, alignment slack
+  if (d->xdst != 1 && d->grid.mx == 255 && d->grid.dim >= 2) b += dst_tc_table_bytes();
   return b;
 }
 
@@ -1532,12 +1629,13 @@ extern "C" int pint_plan_tuning(pint_plan p, int* out, int n) {
     return -1;
   }
   const bool mixed = p->prec == PINT_MIXED;
-  const int v[7] = {p->Cr, p->Ci, p->Cz, p->ysolve,
+  const int v[8] = {p->Cr, p->Ci, p->Cz, p->ysolve,
                     mixed ? (compiled_time_fft_shape(p->N, p->Cr) ? 16 : 1 << p->rml) : 0,
-                    mixed ? (compiled_update_shape(p->N, p->Ci) ? 16 : 1 << p->uml) : 0, p->small ? 1 : 0};
-  const int k = n < 7 ? n : 7;
+                    mixed ? (compiled_update_shape(p->N, p->Ci) ? 16 : 1 << p->uml) : 0, p->small ? 1 : 0,
+                    p->xdst};
+  const int k = n < 8 ? n : 8;
   for (int i = 0; i < k; ++i) out[i] = v[i];
-  return 7;
+  return 8;
 }
 
 extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* upd_rel_out) {
@@ -1548,6 +1646,7 @@ extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* u
   solve_result(p, &m, &upd, &done);
   if (sweeps_out) *sweeps_out = m;
   if (upd_rel_out) *upd_rel_out = upd;
+  if (solve_wait_gave_up(p)) return fail(PINT_ECUDA, "a device-side wait of the solve gave up (bounded wait)");
   if (!done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
   return PINT_OK;
 }
@@ -1572,6 +1671,7 @@ pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double*
     solve_result(p, &m, &upd, &done);
     if (sweeps_out) *sweeps_out = m;
     if (upd_rel_out) *upd_rel_out = upd;
+    if (solve_wait_gave_up(p)) return fail(PINT_ECUDA, "a device-side wait of the solve gave up (bounded wait)");
     if (!done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
     return PINT_OK;
   }
@@ -1730,6 +1830,8 @@ pint_status batch_impl(pint_plan* plans, int n, const double* const* Fhat, const
     if (sweeps_out) sweeps_out[i] = m;
     if (upd_out) upd_out[i] = upd;
     all = all && done;
+    if (solve_wait_gave_up(plans[i]))
+      return fail(PINT_ECUDA, "a device-side wait of a batch solve gave up (bounded wait)");
   }
   if (!all) return fail(PINT_ENOTCONV, "some problems reached max_sweeps above tol");
   return PINT_OK;

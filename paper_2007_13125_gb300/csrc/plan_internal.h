@@ -91,6 +91,9 @@ struct pint_plan_s {
   float4* what_ff = nullptr;        // MIXED CQ: [2N] double-float complex, radix-8 permuted, * tau^-alpha / 2N
   float4* tw_ff = nullptr;          // MIXED CQ: [2N] double-float complex exp(-2 pi i m / 2N)
   float2* Uff = nullptr;            // MIXED: U as double-float pairs (hi, lo) [N][M]
+  int xdst = 1;                     // x sine transforms of FP32 inner solves: 1 odd-sequence FFT,
+                                    // 2 tensor-core products (mx = 255)
+  unsigned short* dst_tab = nullptr;  // xdst 2: the sine-matrix image (FP16 hi / lo)
   float *Uhi = nullptr, *Fhi = nullptr;  // FP32: U, F_hat
   void* S = nullptr;                // spectrum
   double* z = nullptr;              // CQ Toeplitz output [N][M]
@@ -140,6 +143,7 @@ pint_status solve_enqueue(pint_plan p, const double* F, double* U, double tol, i
                           const double* v = nullptr);
 // Result of the last enqueued solve (valid once its stream work has completed).
 void solve_result(pint_plan p, int* sweeps, double* upd, bool* converged);
+bool solve_wait_gave_up(pint_plan p);  // the last solve's device-side wait gave up (after it completed)
 // Add one solve (prologue, while-loop, epilogue, or the one-CTA solve) of plan p to graph g.
 // v: start from U_0^n = v (MIXED: the first sweep in the prologue; otherwise v is broadcast into U).
 // dep (optional): a node the solve's first node must follow; *last (optional): its final node.

@@ -375,7 +375,7 @@ void worker_loop(pint_server_s* s) {
         // the solution stays on the device until it is polled (or moved to the host when its
         // memory is needed for queued requests); everything else returns to the budget now
         solve_result(r->plan, &r->sweeps, &r->upd, &conv);
-        r->status = conv ? PINT_OK : PINT_ENOTCONV;
+        r->status = solve_wait_gave_up(r->plan) ? PINT_ECUDA : (conv ? PINT_OK : PINT_ENOTCONV);
         release_request_inputs(s, r);
       } else {
         r->status = PINT_ECUDA;

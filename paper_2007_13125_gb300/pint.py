@@ -41,7 +41,7 @@ class _Desc(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("alpha", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("tau", ctypes.c_double), ("N", ctypes.c_int), ("grid", _Grid),
                 ("precision", ctypes.c_int), ("eig", ctypes.c_int), ("ysolve", ctypes.c_int),
-                ("space", ctypes.c_int)]
+                ("space", ctypes.c_int), ("xdst", ctypes.c_int)]
 
 
 class _Req(ctypes.Structure):
@@ -269,11 +269,12 @@ class Plan:
     """Owns a pint_plan handle."""
 
     def __init__(self, k, alpha, kappa, tau, N, dim, mx, my=1, precision="mixed",
-                 eig=PINT_EIG_TRUNC_DFT, ysolve=0, space="fd", mz=1):
+                 eig=PINT_EIG_TRUNC_DFT, ysolve=0, space="fd", mz=1, xdst=0):
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         spc = SPACES[space] if isinstance(space, str) else int(space)
         d = _Desc(k, float(alpha), float(kappa), float(tau), int(N),
-                  _Grid(dim, mx, my if dim >= 2 else 1, mz if dim == 3 else 1), prec, eig, int(ysolve), spc)
+                  _Grid(dim, mx, my if dim >= 2 else 1, mz if dim == 3 else 1), prec, eig, int(ysolve), spc,
+                  int(xdst))
         h = _P()
         check(lib().pint_plan_create_desc(ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
@@ -284,10 +285,10 @@ class Plan:
         self.precision = prec
 
     @classmethod
-    def for_problem(cls, p, precision="mixed", eig=PINT_EIG_TRUNC_DFT, ysolve=0):
+    def for_problem(cls, p, precision="mixed", eig=PINT_EIG_TRUNC_DFT, ysolve=0, xdst=0):
         """Plan for a workloads.Problem (its k, alpha, kappa, tau, N, grid and space)."""
         return cls(p.k, p.alpha, p.kappa, p.tau, p.N, p.dim, p.mx, p.my, precision, eig, ysolve,
-                   getattr(p, "space", "fd"), getattr(p, "mz", 1))
+                   getattr(p, "space", "fd"), getattr(p, "mz", 1), xdst)
 
     def close(self):
         """Destroy the plan (pint_plan_destroy); idempotent."""
@@ -308,12 +309,13 @@ class Plan:
             pass
 
     def tuning(self) -> dict:
-        """The plan's tuned choices (pint_plan_tuning): tile widths, y solver, FFT radix bounds."""
-        out = (_I * 7)()
-        if lib().pint_plan_tuning(self.handle, out, 7) < 0:
+        """The plan's tuned choices (pint_plan_tuning): tile widths, y solver, FFT radix bounds,
+        x sine transform."""
+        out = (_I * 8)()
+        if lib().pint_plan_tuning(self.handle, out, 8) < 0:
             raise PintError(PINT_EINVAL, last_error())
         keys = ["resid_width", "update_width", "history_width", "ysolve", "resid_max_radix",
-                "update_max_radix", "one_cta"]
+                "update_max_radix", "one_cta", "xdst"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
 
     def workspace_bytes(self) -> int:

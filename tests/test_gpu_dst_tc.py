@@ -1,0 +1,118 @@
+"""The x sine transform as tensor-core products (tcgen05; xdst = 2) against the odd-sequence FFT
+(xdst = 1) and the oracle.
+
+Both compute the x-direction step of the shifted spatial solves (Algorithm 1 / 2, step 2: A is
+diagonal on the sine modes, Sec. 2.2) in FP32-class arithmetic, so one sweep from U = 0 (one
+application of P^-1 to F_hat) agrees to the FP32 inner-solve level, and a solve reaches the oracle's
+solution to the mixed path's bar with the same number of sweeps. Line counts cover one partial
+tile, odd and even last tiles, ragged tails over many tiles, 3D and both FP32 precisions."""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import device_inputs, oracle_solution, rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+# one sweep from U = 0: the two transforms differ only by FP32 rounding (measured 1.1e-6 -
+# 2.5e-6, amplified from ~1e-7 in the transform by the spread of the shifted spectrum)
+SWEEP_BAR = 1e-5
+
+
+def _sweep(p, torch, precision, xdst):
+    from paper_2007_13125_gb300 import Plan
+    v, f, fd = device_inputs(p, torch)
+    with Plan.for_problem(p, precision, xdst=xdst) as plan:
+        used = plan.tuning()["xdst"]
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        plan.form_rhs(v, f, fd, F)
+        U0 = torch.zeros_like(F)
+        U1 = torch.empty_like(F)
+        plan.wr_sweep(F, U0, U1)
+        torch.cuda.synchronize()
+    return used, U1.cpu().numpy()
+
+
+def _solve(p, torch, xdst, tol=1e-10):
+    from paper_2007_13125_gb300 import Plan
+    v, f, fd = device_inputs(p, torch)
+    with Plan.for_problem(p, "mixed", xdst=xdst) as plan:
+        used = plan.tuning()["xdst"]
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        plan.form_rhs(v, f, fd, F)
+        U = torch.empty_like(F)
+        st, sweeps, upd = plan.solve_v(F, v, U, tol=tol)
+        torch.cuda.synchronize()
+    return used, U.cpu().numpy(), st, sweeps
+
+
+CASES = [
+    ("2d_255x3_N8", dict(dim=2, mx=255, my=3, N=8, k=2)),           # 15 lines: one partial tile, odd
+    ("2d_255x3_N10", dict(dim=2, mx=255, my=3, N=10, k=3)),         # 18 lines: one partial tile, even
+    ("2d_255x15_N64", dict(dim=2, mx=255, my=15, N=64, k=4)),       # 495 lines: 15 tiles + 15
+    ("2d_255x255_N16", dict(dim=2, mx=255, my=255, N=16, k=4, kappa=0.05)),  # 2295: 71 tiles + 23
+]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+@pytest.mark.parametrize("name,kw", CASES)
+def test_sweep_matches_fft_transform(name, kw, precision):
+    torch = torch_cuda()
+    p = workloads.small_problem(**kw)
+    u1, a = _sweep(p, torch, precision, 1)
+    u2, b = _sweep(p, torch, precision, 2)
+    assert (u1, u2) == (1, 2)
+    assert np.all(np.isfinite(b))
+    assert rel_l2(b, a) <= SWEEP_BAR, name
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_sweep_matches_fft_transform_3d(precision):
+    torch = torch_cuda()
+    p = workloads.heat3d_problem(m=255, N=16, my=7, mz=3)            # 189 lines: 5 tiles + 29
+    u1, a = _sweep(p, torch, precision, 1)
+    u2, b = _sweep(p, torch, precision, 2)
+    assert (u1, u2) == (1, 2)
+    assert rel_l2(b, a) <= SWEEP_BAR
+
+
+def test_solve_reaches_the_oracle_with_the_same_sweeps():
+    torch = torch_cuda()
+    p = workloads.small_problem(dim=2, mx=255, my=255, N=32, k=4, kappa=0.05)
+    ref = oracle_solution(p)
+    _, Ua, sta, swa = _solve(p, torch, 1)
+    _, Ub, stb, swb = _solve(p, torch, 2)
+    assert sta == 0 and stb == 0
+    assert swb == swa
+    assert rel_l2(Ub, ref) <= 1e-8
+    lev = np.linalg.norm(Ub - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1),
+                                                        np.sqrt(np.mean(np.sum(ref ** 2, axis=1))))
+    assert lev.max() <= 1e-7
+
+
+def test_heat2d_full_size_both_transforms():
+    """2D heat 255x255, N = 256, BDF4, kappa = 0.05 (32895 x lines: the tensor-core transform is
+    the default there): both transforms meet the mixed path's bar with the same sweeps."""
+    torch = torch_cuda()
+    p = workloads.c2_heat2d()
+    ref = oracle_solution(p)
+    used0, U0, st0, sw0 = _solve(p, torch, 0, tol=1e-8)
+    used1, U1, st1, sw1 = _solve(p, torch, 1, tol=1e-8)
+    assert (used0, used1) == (2, 1)
+    assert st0 == 0 and st1 == 0 and sw0 == sw1
+    assert rel_l2(U0, ref) <= 1e-8 and rel_l2(U1, ref) <= 1e-8
+
+
+def test_variant_selection():
+    torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    small = workloads.small_problem(dim=2, mx=255, my=255, N=16, k=2)    # 2295 lines: FFT by default
+    other = workloads.small_problem(dim=2, mx=127, my=127, N=64, k=2)    # lines of 127 points
+    with Plan.for_problem(small, "mixed") as plan:
+        assert plan.tuning()["xdst"] == 1
+    with Plan.for_problem(small, "fp64", xdst=2) as plan:                 # FP64 inner solves
+        assert plan.tuning()["xdst"] == 1
+    with Plan.for_problem(other, "mixed", xdst=2) as plan:
+        assert plan.tuning()["xdst"] == 1
+    with Plan.for_problem(workloads.c2_heat2d(), "mixed", xdst=3) as plan:   # timed choice
+        assert plan.tuning()["xdst"] in (1, 2)

@@ -68,6 +68,13 @@ def test_invalid_plans_rejected_before_device_use(pint):
     assert "status" in pint.status_string(1) or pint.status_string(1) == "PINT_EINVAL"
 
 
+def test_invalid_x_transform_variant_rejected_before_device_use(pint):
+    for xdst in (-1, 4):
+        with pytest.raises(pint.PintError) as e:
+            pint.Plan(2, 1.0, 0.1, 0.01, 64, 2, 255, 255, xdst=xdst)
+        assert e.value.status == pint.PINT_EINVAL
+
+
 def test_invalid_fem_plans_rejected_before_device_use(pint):
     # P1 finite elements: 1D only (every precision), mx + 1 of the form 2^a 5^b; an unknown
     # space code is rejected too
