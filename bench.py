@@ -92,6 +92,7 @@ NCU_TRAFFIC = {
         "inv_update_v0_ff": (142.00e6, "kernels_time.cu", "1cbdbcdf85d37f489baf91b9682d42622ef022f4"),
         "inv_update_ff": (277.49e6, "kernels_time.cu", "1cbdbcdf85d37f489baf91b9682d42622ef022f4"),
         "dst_f32": (76.07e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
+        "dst_tc_f32": (75.08e6, "kernels_dst_tc.cu", "8dabcec6d0070781383f1f35bedce20e28ba6bd9"),
         "axis_solve_f32": (78.60e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
     },
 }
