@@ -658,8 +658,13 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   const long long xlines = (long long)(N / 2 + 1) * p->my * p->mz;
   const bool tc_default = d->xdst == 0 && xlines >= 16384;
   if (dst_tc_applies(p) && (d->xdst >= 2 || tc_default)) {
-    std::vector<unsigned short> img(dst_tc_table_bytes() / 2);
-    dst_tc_table(img.data());
+    // the matrix image is the same for every plan: built once per process
+    static std::once_flag once;
+    static std::vector<unsigned short> img;
+    std::call_once(once, [] {
+      img.resize(dst_tc_table_bytes() / 2);
+      dst_tc_table(img.data());
+    });
     if ((s = upload(p, &p->dst_tab, img)) != PINT_OK) return bail(s);
     p->xdst = 2;
     if (d->xdst == 3 && (s = autotune_xdst(p)) != PINT_OK) return bail(s);
