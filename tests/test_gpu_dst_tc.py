@@ -116,3 +116,50 @@ def test_variant_selection():
         assert plan.tuning()["xdst"] == 1
     with Plan.for_problem(workloads.c2_heat2d(), "mixed", xdst=3) as plan:   # timed choice
         assert plan.tuning()["xdst"] in (1, 2)
+
+
+@pytest.mark.parametrize("ysolve", [2, 4])
+def test_tensor_core_x_with_the_tridiagonal_y_solvers(ysolve):
+    """The x transforms on the tensor cores around the recurrence (2) and PCR (4) y solvers."""
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = workloads.small_problem(dim=2, mx=255, my=63, N=32, k=3, kappa=0.05)
+    ref = oracle_solution(p)
+    v, f, fd = device_inputs(p, torch)
+    with Plan.for_problem(p, "mixed", ysolve=ysolve, xdst=2) as plan:
+        t = plan.tuning()
+        assert t["xdst"] == 2 and t["ysolve"] == ysolve
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+        plan.form_rhs(v, f, fd, F)
+        U = torch.empty_like(F)
+        st, sweeps, upd = plan.solve_v(F, v, U, tol=1e-10)
+        torch.cuda.synchronize()
+    assert st == 0 and rel_l2(U.cpu().numpy(), ref) <= 1e-8
+
+
+def test_tensor_core_plans_in_a_batch_graph_beside_fft_plans():
+    """Solves with the tensor-core x transform run as concurrent branches of one batch graph next
+    to problems that use the FFT transforms; each result meets its oracle bar."""
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan, pint
+    dev = torch.device("cuda:0")
+    probs = [workloads.small_problem(dim=2, mx=255, my=255, N=16, k=2, kappa=0.1, seed=61),
+             workloads.small_problem(dim=2, mx=255, my=127, N=32, k=4, kappa=0.05, seed=62),
+             workloads.small_problem(dim=2, mx=63, my=63, N=64, k=3, kappa=0.1, seed=63),
+             workloads.small_problem(dim=1, mx=255, N=128, k=2, alpha=0.6, kappa=0.1, seed=64)]
+    xdst = [2, 2, 0, 0]
+    plans, Fs, Us = [], [], []
+    for p, x in zip(probs, xdst):
+        pl = Plan.for_problem(p, "mixed", xdst=x)
+        v = torch.tensor(p.v, device=dev); f = torch.tensor(p.f(), device=dev); fd = torch.tensor(p.fderiv(), device=dev)
+        F = torch.empty((p.N, p.M), dtype=torch.float64, device=dev)
+        U = torch.empty_like(F)
+        pl.form_rhs(v, f, fd, F)
+        pl.initial_guess(v, U)
+        plans.append(pl); Fs.append(F); Us.append(U)
+    assert [pl.tuning()["xdst"] for pl in plans] == [2, 2, 1, 1]
+    st, sweeps, upd = pint.batch_solve(plans, Fs, Us, tol=1e-10)
+    for p, U, s in zip(probs, Us, sweeps):
+        assert rel_l2(U.cpu().numpy(), oracle_solution(p)) <= 1e-8, (p.name, s)
+    for pl in plans:
+        pl.close()
