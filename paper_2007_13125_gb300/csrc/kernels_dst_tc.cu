@@ -43,6 +43,7 @@
 // tensor memory is freed.
 #include <cuda_fp16.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 
@@ -516,20 +517,24 @@ void dst_tc_table(unsigned short* img) {
 }
 
 cudaError_t launch_dst_tc(const DstTcArgs& a, cudaStream_t st) {
-  static int sms = 0;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_dst255_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   if (a.lines <= 0) return cudaSuccess;
+  // the shared-memory attribute applies to the current device: set on every launch, as the other
+  // launchers do; the SM count is queried once per device
+  static std::atomic<int> sms[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int n = sms[dev].load(std::memory_order_relaxed);
+  if (n == 0) {
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    sms[dev].store(n, std::memory_order_relaxed);
+  }
+  e = cudaFuncSetAttribute(k_dst255_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+  if (e != cudaSuccess) return e;
   const int tiles = (a.lines + kTcLines - 1) / kTcLines;
-  const int grid = tiles < sms ? tiles : sms;
+  const int grid = tiles < n ? tiles : n;
   prof_begin("dst_tc_f32", st);
   k_dst255_tc<<<grid, kTcThreads, kTcSmemBytes, st>>>(a);
   prof_end(st);
