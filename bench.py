@@ -39,7 +39,7 @@ UNIT = "DOF/s"
 TOL = 1e-8
 
 # algorithmic bytes per launch of each kernel, as a function of (N, M)
-def algo_bytes(name: str, N: int, M: int) -> float:
+def algo_bytes(name: str, N: int, M: int, K: int = 1) -> float:
     NM, JM = N * M, (N // 2 + 1) * M
     table = {
         "resid_fwd_ff": 16 * NM + 8 * JM,       # read U, F_hat (double-float); write half spectrum
@@ -50,6 +50,7 @@ def algo_bytes(name: str, N: int, M: int) -> float:
         "dst_tc_f32": 16 * JM,                  # the same transform as tensor-core products
         "axis_solve_f32": 16 * JM,
         "rhs_f64": 16 * NM,                     # read f, write F_hat
+        "rhs_head_f64": 16 * K * M,             # F_hat's first k levels: read f, write
         "cvt_d2ff": 16 * NM,
         "cvt_ff2d": 16 * NM,
         "initial_guess": 8 * NM,
@@ -636,17 +637,17 @@ def run_nl(args) -> int:
     tot_all = sum(t for _, t in kstats.values()) or 1.0
     for name, (n, tot) in kstats.items():
         avg_ms = tot / max(n, 1)
-        b = algo_bytes(name, N, M)
+        b = algo_bytes(name, N, M, p.k)
         per_kernel[name] = {"launches": n, "avg_us": round(1e3 * avg_ms, 2), "share": round(tot / tot_all, 3),
                             "algo_GBps": round(b / (avg_ms * 1e-3) / 1e9, 1) if b else None}
     roofline = None
     if kstats:
         name, (n, tot) = max(kstats.items(), key=lambda kv: kv[1][1])
-        ach = algo_bytes(name, N, M) / (tot / n * 1e-3) / 1e9
+        ach = algo_bytes(name, N, M, p.k) / (tot / n * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(ach / hbm_peak, 4), "traffic": traffic_for(name, p.name),
                     "peak_source": peak_src + " hbm_gbs (STREAM-style copy)",
-                    "algo_bytes_per_launch": algo_bytes(name, N, M),
+                    "algo_bytes_per_launch": algo_bytes(name, N, M, p.k),
                     "note": f"1D problem of {N * M * 8 / 1e6:.1f} MB per FP64 array: latency-bound, no bandwidth claim"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -704,8 +705,7 @@ def run_once(precision: str) -> int:
             st, sweeps, upd = plan.nl_solve(p.g, F, U, newton_tol=NL_NEWTON_TOL, max_steps=20, tol=NL_TOL,
                                             max_sweeps=40)
         else:
-            plan.form_rhs(v, f, fd, F)
-            st, sweeps, upd = plan.solve_v(F, v, U, tol=TOL, max_sweeps=30)
+            st, sweeps, upd = plan.solve_fv(v, f, fd, U, tol=TOL, max_sweeps=30)
         torch.cuda.synchronize()
     print(json.dumps({"once": precision, "workload": p.name, "sweeps": sweeps, "final_update": upd}))
     return 0
@@ -781,9 +781,10 @@ def main():
     last = {}
 
     def step(prec):
+        # from the problem data to U: pint_solve_fv (MIXED BDF: F_hat never materialised, the
+        # residual kernels read f; otherwise F_hat formed in the plan's workspace, then the solve)
         plan = plans[prec]
-        plan.form_rhs(v, f, fd, F, stream)
-        st, sweeps, upd = plan.solve_v(F, v, U, tol=TOL, max_sweeps=30, stream=stream)
+        st, sweeps, upd = plan.solve_fv(v, f, fd, U, tol=TOL, max_sweeps=30, stream=stream)
         last[prec] = (sweeps, upd)
 
     def barrier():
@@ -896,18 +897,18 @@ def main():
     per_kernel = {}
     for name, (n, tot) in kstats.items():
         avg_ms = tot / max(n, 1)
-        b = algo_bytes(name, N, M)
+        b = algo_bytes(name, N, M, p.k)
         per_kernel[name] = {"launches": n, "avg_us": round(1e3 * avg_ms, 2),
                             "share": round(tot / sum(t for _, t in kstats.values()), 3),
                             "algo_GBps": round(b / (avg_ms * 1e-3) / 1e9, 1) if b else None}
     if top:
         name, (n, tot) = top
         avg_s = tot / n * 1e-3
-        ach = algo_bytes(name, N, M) / avg_s / 1e9
+        ach = algo_bytes(name, N, M, p.k) / avg_s / 1e9
         roofline = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": hbm_peak,
                     "unit": "GB/s", "frac": round(ach / hbm_peak, 3), "traffic": traffic_for(name, p.name),
                     "peak_source": peak_src + " hbm_gbs (STREAM-style copy)",
-                    "algo_bytes_per_launch": algo_bytes(name, N, M)}
+                    "algo_bytes_per_launch": algo_bytes(name, N, M, p.k)}
 
     dof_total = job_units(pg, p.dof, dev)
     value = dof_total / (ms_mixed * 1e-3)

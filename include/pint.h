@@ -243,6 +243,18 @@ pint_status pint_solve_resume(pint_plan plan, const double* Fhat, double* U, int
 pint_status pint_solve_v(pint_plan plan, const double* Fhat, const double* v, double* U, double tol,
                          int max_sweeps, int* sweeps_out, double* upd_rel_out, void* stream);
 
+/* pint_form_rhs followed by pint_solve_v, from the problem data (v, f, the derivatives of f at 0,
+ * laid out as for pint_form_rhs; device FP64) to U (device, output only), with the same iterates,
+ * stopping rule, results and errors. For PINT_MIXED BDF plans (alpha = 1, no reaction term) F_hat
+ * is not materialised: F_hat_n = f(t_n) exactly beyond the first k levels (the starting
+ * corrections of eq. (2.7) act on levels n <= k - 1 and beta_n = 0 from level k + 1 on), so the
+ * residual kernels read the first k levels of F_hat from a k x M block of the plan (formed by the
+ * right-hand-side kernel) and f for the others; the results are those of the unfused path. Other
+ * plans form F_hat into a plan workspace of N M doubles, allocated on the first call (PINT_ENOMEM
+ * if it cannot be) and freed with the plan. Waits for `stream`. */
+pint_status pint_solve_fv(pint_plan plan, const double* v, const double* f, const double* fderiv, double* U,
+                          double tol, int max_sweeps, int* sweeps_out, double* upd_rel_out, void* stream);
+
 /* pint_solve_v enqueued without waiting (as pint_solve_async; result by pint_solve_result). */
 pint_status pint_solve_v_async(pint_plan plan, const double* Fhat, const double* v, double* U, double tol,
                                int max_sweeps, void* stream);

@@ -140,9 +140,16 @@ extern "C" pint_status pint_solve_host(pint_plan p, const double* v, const doubl
   if (e != cudaSuccess) return cerr(e, "stream order");
   h->used[s] = true;
   h->next ^= 1;
-  st = pint_form_rhs(p, h->v[s], h->f[s], p->k > 1 ? h->fd[s] : nullptr, h->F, stream);
-  if (st != PINT_OK) return st;
-  st = pint_solve_v_async(p, h->F, h->v[s], h->U[s], tol, max_sweeps, stream);
+  if (fused_rhs_ok(p)) {
+    // F_hat not materialised: the residual kernels read f and the correction of the first levels
+    // (graph-launched like pint_solve_v_async, hence not while per-kernel profiling is on)
+    if (profiling_on()) return hs_fail(PINT_EINVAL, "pint_solve_host: not available while per-kernel profiling is on");
+    st = form_rhs_corr(p, h->v[s], h->f[s], p->k > 1 ? h->fd[s] : nullptr, cs);
+    if (st == PINT_OK) st = solve_enqueue(p, h->f[s], h->U[s], tol, max_sweeps, cs, h->v[s], p->fcorr);
+  } else {
+    st = pint_form_rhs(p, h->v[s], h->f[s], p->k > 1 ? h->fd[s] : nullptr, h->F, stream);
+    if (st == PINT_OK) st = pint_solve_v_async(p, h->F, h->v[s], h->U[s], tol, max_sweeps, stream);
+  }
   if (st != PINT_OK) return st;
   e = cudaEventRecord(h->comp_done[s], cs);
   // 3. the solution back to the host on the copy-out stream

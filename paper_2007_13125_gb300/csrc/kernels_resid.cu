@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_fwd(ResidFwdArgs a) {
     } else {
       v.ywh = v.ywl = v.yeh = v.yel = 0.f;
     }
-    v.f = valid ? a.F[idx] : 0.0;
+    const double* Fb = i < a.kc ? a.Fh : a.F;  // F_hat's first levels, then f (= F_hat there)
+    v.f = valid ? Fb[idx] : 0.0;
     v.s = __ldg(a.s + i);
     return v;
   };
@@ -371,7 +372,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_resid_v0(ResidFwdArgs a) {
     for (int b = i0; b < i1; b += 8) {
       double f[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) f[t] = (valid && b + t < i1) ? Fp[(size_t)(b + t) * M] : 0.0;
+      for (int t = 0; t < 8; ++t) {
+        // F_hat's first levels from their own block, then f (= F_hat there)
+        const double* Fb = b + t < a.kc ? a.Fh + m : Fp;
+        f[t] = (valid && b + t < i1) ? Fb[(size_t)(b + t) * M] : 0.0;
+      }
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int i = b + t;

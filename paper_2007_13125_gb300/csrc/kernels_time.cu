@@ -637,7 +637,7 @@ cudaError_t launch_toeplitz_ff(const ToepFFArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_rhs(const RhsArgs& a, cudaStream_t st) {
-  prof_begin("rhs_f64", st);
+  prof_begin(a.head ? "rhs_head_f64" : "rhs_f64", st);
   k_rhs<<<grid_pts(a.M, a.N), kThreads, 0, st>>>(a);
   prof_end(st);
   return cudaGetLastError();

@@ -23,7 +23,9 @@ __host__ __device__ inline bool compiled_update_shape(int N, int C) {
 
 struct ResidFwdArgs {
   const float2* U;                         // iterate U [N][M] (double-float pairs: hi, lo)
-  const double* F;                         // F_hat [N][M] (FP64, split to double-float on load)
+  const double* F;                         // F_hat [N][M] (FP64, split to double-float on load), or f
+  const double* Fh;                        // with f: F_hat on levels < kc ([kc][M]; beyond them
+  int kc;                                  // F_hat = f exactly: BDF-k), else null
   const float* yhi; const float* ylo;      // CQ: tau^-alpha (L_omega U) [N][M] double-float, else null
   float2* S;                               // half spectrum [(N/2+1)][M]
   const float* s;                          // kappa^{i/N}, i < N
@@ -106,6 +108,7 @@ struct RhsArgs {
   int fem;                                 // P1 FEM: A v -> K_h v, v -> M_h v in the beta term
   double mass6;                            // h/6
   int periodic;                            // periodic boundary conditions: neighbours wrap around
+  int head;                                // the first N levels of a longer F_hat only (profiling label)
 };
 
 // ---- spatial kernels (kernels_space.cu) ----

@@ -595,6 +595,12 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   const size_t NM = (size_t)N * M, JM = (size_t)(N / 2 + 1) * M;
   if (p->prec == PINT_MIXED) {
     if ((s = dalloc(p, &p->Uff, NM)) != PINT_OK) return bail(s);
+    if (p->alpha == 1.0) {
+      // BDF-k: F_hat = f exactly beyond the first k levels (the corrections act on levels < k - 1
+      // and beta_n = 0 from level k on), so a solve from f needs F_hat itself on k levels only
+      p->kc = p->k < N ? p->k : N;
+      if ((s = dalloc(p, &p->fcorr, (size_t)p->kc * M)) != PINT_OK) return bail(s);
+    }
   } else if (p->prec == PINT_FP32) {
     if ((s = dalloc(p, &p->Uhi, NM)) != PINT_OK) return bail(s);
     if ((s = dalloc(p, &p->Fhi, NM)) != PINT_OK) return bail(s);
@@ -791,8 +797,9 @@ double react_weight(pint_plan p);
 // F_hat with the starting correction a_n (f(0) - A v - w c v - w g(v)): the reaction term when one
 // is installed, the nonlinearity when g is given (the rows of fderiv are then copied with f(0)
 // replaced first)
+// head_levels > 0: Fhat receives the first head_levels levels of F_hat only (pitch M)
 pint_status form_rhs(pint_plan p, const double* v, const double* f, const double* fderiv, double* Fhat,
-                     cudaStream_t st, const NlPoly* g) {
+                     cudaStream_t st, const NlPoly* g, int head_levels = 0) {
   if (!p || !v || !f || !Fhat) return fail(PINT_EINVAL, "NULL argument");
   if (p->k >= 2 && !fderiv) return fail(PINT_EINVAL, "fderiv is required for k >= 2");
   if (p->k >= 2 && (g || p->react_on)) {
@@ -814,6 +821,10 @@ pint_status form_rhs(pint_plan p, const double* v, const double* f, const double
   for (int n = 0; n < kMaxK - 1; ++n) {
     a.a[n] = n < 5 ? p->a[n] : 0.0;
     for (int l = 1; l <= 4; ++l) a.bt[l][n] = p->b[l - 1][n] * std::pow(p->tau, l);
+  }
+  if (head_levels > 0) {
+    a.N = head_levels;
+    a.head = 1;
   }
   cudaError_t e = launch_rhs(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "rhs kernel");
@@ -1089,11 +1100,13 @@ int stencil_pow2(pint_plan p) {
   return p2(p->gx) && p2(p->gy) && p2(p->gz) ? 1 : 0;
 }
 
-cudaError_t mixed_resid(pint_plan p, const double* Fhat, cudaStream_t st) {
+// Fc: Fhat is f, and F_hat's first kc levels are in Fc (BDF: F_hat = f beyond them; the fused
+// right-hand side), else null
+cudaError_t mixed_resid(pint_plan p, const double* Fhat, cudaStream_t st, const double* Fc = nullptr) {
   const int N = p->N, M = p->M;
   float* yhi = reinterpret_cast<float*>(p->z);
   ResidFwdArgs r{};
-  r.U = p->Uff; r.F = Fhat;
+  r.U = p->Uff; r.F = Fhat; r.Fh = Fc; r.kc = Fc ? p->kc : 0;
   r.yhi = p->cq ? yhi : nullptr;
   r.ylo = p->cq ? yhi + (size_t)N * M : nullptr;
   r.S = reinterpret_cast<float2*>(p->S);
@@ -1134,11 +1147,11 @@ cudaError_t mixed_update(pint_plan p, const double* v, cudaStream_t st) {
 }
 
 // MIXED sweep on the plan's double-float iterate (Uff); F_hat read in FP64
-pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st) {
+pint_status sweep_mixed(pint_plan p, const double* Fhat, cudaStream_t st, const double* Fc = nullptr) {
   cudaError_t e;
   if (p->cq && (e = mixed_toeplitz(p, st)) != cudaSuccess) return cuda_fail(e, "toeplitz kernel");
   PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
-  if ((e = mixed_resid(p, Fhat, st)) != cudaSuccess) return cuda_fail(e, "residual kernel");
+  if ((e = mixed_resid(p, Fhat, st, Fc)) != cudaSuccess) return cuda_fail(e, "residual kernel");
   if ((e = spatial<float>(p, p->tf, st)) != cudaSuccess) return cuda_fail(e, "spatial kernel");
   if ((e = mixed_update(p, nullptr, st)) != cudaSuccess) return cuda_fail(e, "update kernel");
   return PINT_OK;
@@ -1291,11 +1304,12 @@ pint_status tune_radix(pint_plan p) {
 // MIXED first sweep from U_0^n = v (Theorem 2.7): r_0 = F_hat - beta_n M v - A v in one pass over
 // F_hat (no U read; for CQ no history product), the spatial solves, and U_1 = v + c written as
 // the double-float iterate
-pint_status sweep_mixed_v0(pint_plan p, const double* Fhat, const double* v, cudaStream_t st) {
+pint_status sweep_mixed_v0(pint_plan p, const double* Fhat, const double* v, cudaStream_t st,
+                           const double* Fc = nullptr) {
   const int N = p->N, M = p->M;
   PINT_CUDA(cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), st));
   ResidFwdArgs r{};
-  r.F = Fhat; r.v = v; r.beta_ff = p->beta_ff;
+  r.F = Fhat; r.v = v; r.beta_ff = p->beta_ff; r.Fh = Fc; r.kc = Fc ? p->kc : 0;
   r.S = reinterpret_cast<float2*>(p->S);
   r.s = p->tf.s; r.tw = reinterpret_cast<const float2*>(p->tf.tw_time);
   r.N = N; r.M = M; r.mx = p->mx; r.dim = p->dim; r.C = p->Cr; r.logC = ilog2c(p->Cr);
@@ -1431,8 +1445,8 @@ SmallArgs small_args(pint_plan p, const double* F, double* U, const double* v, d
   return a;
 }
 
-pint_status sweep_body(pint_plan p, const double* F, double* U, cudaStream_t st) {
-  if (p->prec == PINT_MIXED) return sweep_mixed(p, F, st);
+pint_status sweep_body(pint_plan p, const double* F, double* U, cudaStream_t st, const double* Fc = nullptr) {
+  if (p->prec == PINT_MIXED) return sweep_mixed(p, F, st, Fc);
   if (p->prec == PINT_FP64) return sweep_direct<double>(p, p->td, F, U, U, st);
   return sweep_direct<float>(p, p->tf, p->Fhi, p->Uhi, p->Uhi, st);
 }
@@ -1440,7 +1454,8 @@ pint_status sweep_body(pint_plan p, const double* F, double* U, cudaStream_t st)
 }  // namespace
 
 pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, double* U, double tol,
-                                  int max_sweeps, const double* v, cudaGraphNode_t dep, cudaGraphNode_t* last) {
+                                  int max_sweeps, const double* v, cudaGraphNode_t dep, cudaGraphNode_t* last,
+                                  const double* Fc) {
   const cudaGraphNode_t* deps = dep ? &dep : nullptr;
   const size_t ndeps = dep ? 1 : 0;
   const size_t NM = (size_t)p->N * p->M;
@@ -1483,7 +1498,7 @@ pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, d
       if (e1 == cudaSuccess && v && p->prec != PINT_MIXED) e1 = launch_bcast_d(v, U, p->N, p->M, p->cap);
       if (e1 == cudaSuccess && p->prec == PINT_MIXED) {
         if (v) {
-          b = sweep_mixed_v0(p, F, v, p->cap);
+          b = sweep_mixed_v0(p, F, v, p->cap, Fc);
           if (b == PINT_OK) e1 = launch_converge(p->norms, p->ctl, h, p->cap);
         } else {
           e1 = launch_d2ff(U, p->Uff, NM, p->cap);
@@ -1510,7 +1525,7 @@ pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, d
     body = cp.conditional.phGraph_out[0];
     if ((s = capture_begin(p, body)) != PINT_OK) break;
     {
-      pint_status b = sweep_body(p, F, U, p->cap);
+      pint_status b = sweep_body(p, F, U, p->cap, Fc);
       if (b == PINT_OK) {
         cudaError_t e2 = launch_converge(p->norms, p->ctl, h, p->cap);
         if (e2 != cudaSuccess) b = cuda_fail(e2, "convergence kernel");
@@ -1541,10 +1556,10 @@ pint_status pint::add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, d
 }
 
 pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double tol, int max_sweeps,
-                                cudaStream_t st, const double* v) {
+                                cudaStream_t st, const double* v, const double* Fc) {
   SolveGraph* hit = nullptr;
   for (SolveGraph& c : p->sg)
-    if (c.exec && c.F == F && c.U == U && c.v == v && c.tol == tol && c.max_sweeps == max_sweeps &&
+    if (c.exec && c.F == F && c.Fc == Fc && c.U == U && c.v == v && c.tol == tol && c.max_sweeps == max_sweeps &&
         c.react == p->react_on)
       hit = &c;
   if (!hit) {
@@ -1561,7 +1576,7 @@ pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double 
     }
     cudaGraph_t g;
     PINT_CUDA(cudaGraphCreate(&g, 0));
-    pint_status s = add_solve_nodes(p, g, F, U, tol, max_sweeps, v);
+    pint_status s = add_solve_nodes(p, g, F, U, tol, max_sweeps, v, nullptr, nullptr, Fc);
     if (s == PINT_OK) {
       cudaError_t e = cudaGraphInstantiate(&sg.exec, g, 0);
       if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphInstantiate");
@@ -1571,7 +1586,7 @@ pint_status pint::solve_enqueue(pint_plan p, const double* F, double* U, double 
       sg.exec = nullptr;
       return s;
     }
-    sg.F = F; sg.U = U; sg.v = v; sg.tol = tol; sg.max_sweeps = max_sweeps; sg.react = p->react_on;
+    sg.F = F; sg.Fc = Fc; sg.U = U; sg.v = v; sg.tol = tol; sg.max_sweeps = max_sweeps; sg.react = p->react_on;
   }
   hit->last_use = ++p->sg_clock;
   PINT_CUDA(cudaGraphLaunch(hit->exec, st));
@@ -1593,7 +1608,7 @@ size_t pint::plan_bytes_estimate(const pint_plan_desc* d) {
                                  (d->grid.dim == 3 ? d->grid.mz : 1);
   const size_t NM = N * M, JM = (N / 2 + 1) * M;
   size_t b = 0;
-  if (d->precision == PINT_MIXED) b += 8 * NM + 8 * JM;
+  if (d->precision == PINT_MIXED) b += 8 * NM + 8 * JM + (d->alpha == 1.0 ? 8 * (size_t)d->k * M : 0);
   else if (d->precision == PINT_FP32) b += 8 * NM + 8 * JM;
   else b += 16 * JM;
   if (d->alpha != 1.0) b += 8 * NM;
@@ -1658,16 +1673,18 @@ extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* u
 
 namespace {
 pint_status solve_sweeps(pint_plan p, const double* Fhat, const double* v, double* U, double tol, int max_sweeps,
-                         int m0, double prev0, int* sweeps_out, double* upd_rel_out, cudaStream_t st);
+                         int m0, double prev0, int* sweeps_out, double* upd_rel_out, cudaStream_t st,
+                         const double* Fc = nullptr);
 
-// pint_solve (v null: from the content of U) and pint_solve_v (from U_0^n = v)
+// pint_solve (v null: from the content of U) and pint_solve_v (from U_0^n = v); with Fc, Fhat is f
+// and F_hat's first kc levels are in Fc (the fused right-hand side of pint_solve_fv)
 pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double* U, double tol, int max_sweeps,
-                       int* sweeps_out, double* upd_rel_out, cudaStream_t st) {
+                       int* sweeps_out, double* upd_rel_out, cudaStream_t st, const double* Fc = nullptr) {
   if (!p || !Fhat || !U) return fail(PINT_EINVAL, "NULL argument");
   if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
   if (!g_prof_on) {
     // one graph launch runs every sweep; the host waits once for the result
-    pint_status gs = solve_enqueue(p, Fhat, U, tol, max_sweeps, st, v);
+    pint_status gs = solve_enqueue(p, Fhat, U, tol, max_sweeps, st, v, Fc);
     if (gs != PINT_OK) return gs;
     PINT_CUDA(cudaStreamSynchronize(st));
     int m = 0;
@@ -1692,14 +1709,15 @@ pint_status solve_impl(pint_plan p, const double* Fhat, const double* v, double*
     if (!p->h_ctl->done) return fail(PINT_ENOTCONV, "max_sweeps reached above tol");
     return PINT_OK;
   }
-  return solve_sweeps(p, Fhat, v, U, tol, max_sweeps, 0, -1.0, sweeps_out, upd_rel_out, st);
+  return solve_sweeps(p, Fhat, v, U, tol, max_sweeps, 0, -1.0, sweeps_out, upd_rel_out, st, Fc);
 }
 
 // The sweeps of a solve launched one by one from the host, starting after m0 sweeps whose last
 // relative update was prev0 (m0 = 0, prev0 < 0: a fresh solve; otherwise a resumed one, whose
 // stopping decisions then match those of the uninterrupted solve).
 pint_status solve_sweeps(pint_plan p, const double* Fhat, const double* v, double* U, double tol, int max_sweeps,
-                         int m0, double prev0, int* sweeps_out, double* upd_rel_out, cudaStream_t st) {
+                         int m0, double prev0, int* sweeps_out, double* upd_rel_out, cudaStream_t st,
+                         const double* Fc) {
   const size_t NM = (size_t)p->N * p->M;
   cudaError_t e;
   double prev = prev0, upd = prev0 > 0.0 ? prev0 : 0.0;
@@ -1711,7 +1729,7 @@ pint_status solve_sweeps(pint_plan p, const double* Fhat, const double* v, doubl
   if (p->prec == PINT_MIXED) {
     if (v) {
       // first sweep from U_0^n = v
-      if ((s = sweep_mixed_v0(p, Fhat, v, st)) != PINT_OK) return s;
+      if ((s = sweep_mixed_v0(p, Fhat, v, st, Fc)) != PINT_OK) return s;
       m = 1;
       if ((s = read_norms(p, st, &upd)) != PINT_OK) return s;
       done = stop_decision(m, upd, prev, tol, p->q_floor);
@@ -1724,7 +1742,7 @@ pint_status solve_sweeps(pint_plan p, const double* Fhat, const double* v, doubl
     if ((e = launch_d2f(U, p->Uhi, NM, st)) != cudaSuccess) return cuda_fail(e, "convert");
   }
   while (m < max_sweeps && !done) {
-    if (p->prec == PINT_MIXED) s = sweep_mixed(p, Fhat, st);
+    if (p->prec == PINT_MIXED) s = sweep_mixed(p, Fhat, st, Fc);
     else if (p->prec == PINT_FP64) s = sweep_direct<double>(p, p->td, Fhat, U, U, st);
     else s = sweep_direct<float>(p, p->tf, p->Fhi, p->Uhi, p->Uhi, st);
     if (s != PINT_OK) return s;
@@ -1764,6 +1782,34 @@ extern "C" pint_status pint_solve_v(pint_plan p, const double* Fhat, const doubl
                                     int max_sweeps, int* sweeps_out, double* upd_rel_out, void* stream) {
   if (!v) return fail(PINT_EINVAL, "NULL argument");
   return solve_impl(p, Fhat, v, U, tol, max_sweeps, sweeps_out, upd_rel_out, (cudaStream_t)stream);
+}
+
+bool pint::profiling_on() { return g_prof_on; }
+
+bool pint::fused_rhs_ok(pint_plan p) {
+  return p->prec == PINT_MIXED && p->fcorr && !p->react_on && !use_small(p);
+}
+
+pint_status pint::form_rhs_corr(pint_plan p, const double* v, const double* f, const double* fderiv, cudaStream_t st) {
+  return form_rhs(p, v, f, fderiv, p->fcorr, st, nullptr, p->kc);
+}
+
+extern "C" pint_status pint_solve_fv(pint_plan p, const double* v, const double* f, const double* fderiv, double* U,
+                                     double tol, int max_sweeps, int* sweeps_out, double* upd_rel_out,
+                                     void* stream) {
+  if (!p || !v || !f || !U) return fail(PINT_EINVAL, "NULL argument");
+  if (p->k >= 2 && !fderiv) return fail(PINT_EINVAL, "fderiv is required for k >= 2");
+  if (!(tol > 0.0) || max_sweeps < 1) return fail(PINT_EINVAL, "tol must be > 0 and max_sweeps >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  pint_status s;
+  if (fused_rhs_ok(p)) {
+    // fused: the residual kernels read F_hat's first kc levels from the plan's block, then f
+    if ((s = form_rhs_corr(p, v, f, fderiv, st)) != PINT_OK) return s;
+    return solve_impl(p, f, v, U, tol, max_sweeps, sweeps_out, upd_rel_out, st, p->fcorr);
+  }
+  if (!p->Fws && (s = dalloc(p, &p->Fws, (size_t)p->N * p->M)) != PINT_OK) return s;
+  if ((s = form_rhs(p, v, f, fderiv, p->Fws, st, nullptr)) != PINT_OK) return s;
+  return solve_impl(p, p->Fws, v, U, tol, max_sweeps, sweeps_out, upd_rel_out, st);
 }
 
 namespace {

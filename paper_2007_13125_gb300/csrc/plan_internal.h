@@ -49,6 +49,7 @@ struct DevAllocator {
 struct SolveGraph {
   cudaGraphExec_t exec = nullptr;
   const double* F = nullptr;
+  const double* Fc = nullptr;       // F is f, F_hat's first kc levels in Fc (null: F is F_hat)
   double* U = nullptr;
   const double* v = nullptr;        // solve from U_0^n = v (null: from the content of U)
   double tol = 0.0;
@@ -91,6 +92,9 @@ struct pint_plan_s {
   float4* what_ff = nullptr;        // MIXED CQ: [2N] double-float complex, radix-8 permuted, * tau^-alpha / 2N
   float4* tw_ff = nullptr;          // MIXED CQ: [2N] double-float complex exp(-2 pi i m / 2N)
   float2* Uff = nullptr;            // MIXED: U as double-float pairs (hi, lo) [N][M]
+  double* fcorr = nullptr;          // MIXED BDF: F_hat's first kc levels [kc][M] (pint_solve_fv)
+  int kc = 0;
+  double* Fws = nullptr;            // pint_solve_fv without the fused form: F_hat [N][M] (on first use)
   int xdst = 1;                     // x sine transforms of FP32 inner solves: 1 odd-sequence FFT,
                                     // 2 tensor-core products (mx = 255)
   unsigned short* dst_tab = nullptr;  // xdst 2: the sine-matrix image (FP16 hi / lo)
@@ -140,14 +144,21 @@ size_t plan_bytes_estimate(const pint_plan_desc* d);
 // Enqueue one whole solve on `st` as a single graph launch (building or reusing the cached graph);
 // the graph ends with a copy of the convergence state into pinned host memory.
 pint_status solve_enqueue(pint_plan p, const double* F, double* U, double tol, int max_sweeps, cudaStream_t st,
-                          const double* v = nullptr);
+                          const double* v = nullptr, const double* Fc = nullptr);
 // Result of the last enqueued solve (valid once its stream work has completed).
 void solve_result(pint_plan p, int* sweeps, double* upd, bool* converged);
-bool solve_wait_gave_up(pint_plan p);  // the last solve's device-side wait gave up (after it completed)
+bool solve_wait_gave_up(pint_plan p);
+// The fused right-hand side (MIXED BDF plans without a reaction term, not the one-CTA solve): a
+// solve from f with F_hat's first kc levels formed into the plan's block (form_rhs_corr) and
+// passed to solve_enqueue as Fc.
+bool fused_rhs_ok(pint_plan p);
+bool profiling_on();  // pint_set_profiling is on (sweeps launched one by one, no graphs)
+pint_status form_rhs_corr(pint_plan p, const double* v, const double* f, const double* fderiv, cudaStream_t st);  // the last solve's device-side wait gave up (after it completed)
 // Add one solve (prologue, while-loop, epilogue, or the one-CTA solve) of plan p to graph g.
 // v: start from U_0^n = v (MIXED: the first sweep in the prologue; otherwise v is broadcast into U).
 // dep (optional): a node the solve's first node must follow; *last (optional): its final node.
 pint_status add_solve_nodes(pint_plan p, cudaGraph_t g, const double* F, double* U, double tol, int max_sweeps,
-                            const double* v, cudaGraphNode_t dep = nullptr, cudaGraphNode_t* last = nullptr);
+                            const double* v, cudaGraphNode_t dep = nullptr, cudaGraphNode_t* last = nullptr,
+                            const double* Fc = nullptr);
 
 }  // namespace pint

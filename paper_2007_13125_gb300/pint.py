@@ -100,6 +100,7 @@ def lib():
         "pint_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
         "pint_solve_async": (_I, [_P, _P, _P, _D, _I, _P]),
         "pint_solve_v": (_I, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+        "pint_solve_fv": (_I, [_P, _P, _P, _P, _P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
         "pint_solve_v_async": (_I, [_P, _P, _P, _P, _D, _I, _P]),
         "pint_solve_result": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
         "pint_solve_host": (_I, [_P, _P, _P, _P, _P, _D, _I, _P]),
@@ -369,6 +370,18 @@ class Plan:
         upd = _D(0.0)
         st = lib().pint_solve_v(self.handle, _ptr(Fhat), _ptr(v), _ptr(U), float(tol), int(max_sweeps),
                                 ctypes.byref(sweeps), ctypes.byref(upd), _stream(stream))
+        if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
+            raise PintError(st, last_error())
+        return st, sweeps.value, upd.value
+
+    def solve_fv(self, v, f, fderiv, U, tol=1e-10, max_sweeps=50, stream=None, raise_on_notconv=True):
+        """From the problem data to U (pint_solve_fv): pint_form_rhs + pint_solve_v, with F_hat
+        never materialised for MIXED BDF plans; (status, sweeps, update)."""
+        sweeps = _I(0)
+        upd = _D(0.0)
+        fd = _ptr(fderiv) if fderiv is not None and fderiv.numel() else None
+        st = lib().pint_solve_fv(self.handle, _ptr(v), _ptr(f), fd, _ptr(U), float(tol), int(max_sweeps),
+                                 ctypes.byref(sweeps), ctypes.byref(upd), _stream(stream))
         if st != PINT_OK and not (st == PINT_ENOTCONV and not raise_on_notconv):
             raise PintError(st, last_error())
         return st, sweeps.value, upd.value

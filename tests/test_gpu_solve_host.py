@@ -1,7 +1,9 @@
 """pint_solve_host: end-to-end solves through host buffers (inputs copied in, solution copied out
 by the library), several calls in a row on one plan so that the two staging sets and copy streams
-are both exercised and reused. Each solution must be bit-identical to the device-buffer path
-(pint_form_rhs + pint_solve_v on the same plan) and within the MIXED bar of the oracle."""
+are both exercised and reused. Each solution must be bit-identical to the device-buffer paths
+(pint_solve_fv, and pint_form_rhs + pint_solve_v, on the same plan: the library reads the same
+F_hat values whether it forms the whole of it or only its first levels) and within the MIXED bar of
+the oracle."""
 import numpy as np
 import pytest
 
@@ -32,8 +34,11 @@ def test_solve_host_matches_device_path_and_oracle(dim, mx, N, k, alpha):
             plan.form_rhs(v, f, fd if k > 1 else None, F)
             U = torch.empty_like(F)
             plan.solve_v(F, v, U, tol=1e-10)
+            Ufv = torch.empty_like(F)
+            plan.solve_fv(v, f, fd if k > 1 else None, Ufv, tol=1e-10)
             torch.cuda.synchronize()
             got = out.numpy()
+            assert np.array_equal(got, Ufv.cpu().numpy())
             assert np.array_equal(got, U.cpu().numpy())
             assert rel_l2(got, oracle_solution(p)) <= 1e-8
 

@@ -127,6 +127,7 @@ def test_reaction_and_semilinear_entry_points_reject_null_plans(pint):
     g = pint._poly((0.0, -1.0, 0.0, 1.0))
     assert L.pint_set_reaction(None, None, None) == pint.PINT_EINVAL
     assert L.pint_form_rhs_window(None, None, None, None, None) == pint.PINT_EINVAL
+    assert L.pint_solve_fv(None, None, None, None, None, 1e-8, 10, None, None, None) == pint.PINT_EINVAL
     assert L.pint_nl_form_rhs(None, ctypes.byref(g), None, None, None, None, None) == pint.PINT_EINVAL
     assert L.pint_nl_solve(None, ctypes.byref(g), None, None, 1e-8, 10, 1e-10, 20, None, None) == pint.PINT_EINVAL
     with pytest.raises(ValueError):
