@@ -88,12 +88,12 @@ def algo_bytes(name: str, N: int, M: int, K: int = 1) -> float:
 # the kernel's source is unchanged (sha1 of its translation unit); other workloads report null
 NCU_TRAFFIC = {
     "heat2d_255x255_N256_bdf4": {
-        "resid_fwd_ff": (316.92e6, "kernels_resid.cu", "5af68bdb7ccbe5814ceb45b90e186c0227840d7e"),
-        "resid_v0_ff": (167.22e6, "kernels_resid.cu", "5af68bdb7ccbe5814ceb45b90e186c0227840d7e"),
-        "inv_update_v0_ff": (142.00e6, "kernels_time.cu", "1cbdbcdf85d37f489baf91b9682d42622ef022f4"),
-        "inv_update_ff": (277.49e6, "kernels_time.cu", "1cbdbcdf85d37f489baf91b9682d42622ef022f4"),
+        "resid_fwd_ff": (317.82e6, "kernels_resid.cu", "bef7a9dcb9ea6525c6c50e53b5f4b76293ad46a2"),
+        "resid_v0_ff": (167.23e6, "kernels_resid.cu", "bef7a9dcb9ea6525c6c50e53b5f4b76293ad46a2"),
+        "inv_update_v0_ff": (141.95e6, "kernels_time.cu", "4f1bc2da689b12f51d0599e98cff88feff864466"),
+        "inv_update_ff": (277.48e6, "kernels_time.cu", "4f1bc2da689b12f51d0599e98cff88feff864466"),
         "dst_f32": (76.07e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
-        "dst_tc_f32": (75.08e6, "kernels_dst_tc.cu", "8dabcec6d0070781383f1f35bedce20e28ba6bd9"),
+        "dst_tc_f32": (75.25e6, "kernels_dst_tc.cu", "9f23cb73856c30b4679802786ab447cb7cc404c1"),
         "axis_solve_f32": (78.60e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
     },
 }
