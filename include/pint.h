@@ -404,7 +404,8 @@ pint_status pint_server_create(size_t hbm_budget_bytes, int max_active, pint_ser
 /* Finishes admitted work, frees everything (unpolled results are dropped). NULL is accepted. */
 pint_status pint_server_destroy(pint_server s);
 /* v [M], f [N][M], fderiv [k-1][M] (NULL when k = 1): host arrays copied before returning, or
- * device arrays (req->inputs_on_device = 1) that are read when the request is admitted. */
+ * device arrays (req->inputs_on_device = 1) that are read while the request runs (from its
+ * admission until it is done; PINT_MIXED BDF requests read f during the solve). */
 pint_status pint_submit(pint_server s, const pint_request* req, const double* v, const double* f,
                         const double* fderiv, uint64_t* ticket);
 /* Wait up to timeout_us for the result: PINT_EAGAIN (timeout_us == 0) or PINT_ETIMEOUT if not

@@ -172,9 +172,12 @@ size_t request_bytes(const pint_request& r) {
   const pint_plan_desc& d = r.desc;
   const size_t M = (size_t)d.grid.mx * (d.grid.dim == 2 ? d.grid.my : 1);
   const size_t NM = (size_t)d.N * M;
-  // F_hat and U on the device, plus copies of f, v and d^l f(0) when the inputs come from the host
+  // U on the device and F_hat unless the solve reads f directly (MIXED BDF, not the one-CTA solve,
+  // which only takes problems of up to 4096 unknowns), plus copies of f, v and d^l f(0) when the
+  // inputs come from the host
+  const bool fused = d.precision == PINT_MIXED && d.alpha == 1.0 && NM > 4096;
   const size_t inputs = r.inputs_on_device ? 0 : 8 * NM + 8 * M * (size_t)(d.k + 1);
-  return plan_bytes_estimate(&d) + 2 * 8 * NM + inputs + 8 * 256;
+  return plan_bytes_estimate(&d) + (fused ? 1 : 2) * 8 * NM + inputs + 8 * 256;
 }
 
 // everything but the solution U
@@ -249,7 +252,9 @@ void start_request(pint_server_s* s, Request* r) {
     take(&r->df, NM);
     if (d.k >= 2) take(&r->dfd, (size_t)(d.k - 1) * M);
   }
-  take(&r->dF, NM);
+  // MIXED BDF: F_hat is not materialised (the residual reads f and F_hat's first k levels)
+  const bool fused = status == PINT_OK && fused_rhs_ok(r->plan);
+  if (!fused) take(&r->dF, NM);
   take(&r->dU, NM);
   cudaError_t e = cudaSuccess;
   const double* in_v = dev_in ? r->uv : r->dv;
@@ -262,9 +267,15 @@ void start_request(pint_server_s* s, Request* r) {
       e = cudaMemcpyAsync(r->dfd, r->fd.data(), (size_t)(d.k - 1) * M * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) status = PINT_ECUDA;
   }
-  if (status == PINT_OK) status = pint_form_rhs(r->plan, in_v, in_f, in_fd, r->dF, st);
   // the whole solve from U_0^n = v (the first sweep reads v; U_0 is never written)
-  if (status == PINT_OK) status = solve_enqueue(r->plan, r->dF, r->dU, r->req.tol, r->req.max_sweeps, st, in_v);
+  if (fused) {
+    if (status == PINT_OK) status = form_rhs_corr(r->plan, in_v, in_f, in_fd, st);
+    if (status == PINT_OK)
+      status = solve_enqueue(r->plan, in_f, r->dU, r->req.tol, r->req.max_sweeps, st, in_v, r->plan->fcorr);
+  } else {
+    if (status == PINT_OK) status = pint_form_rhs(r->plan, in_v, in_f, in_fd, r->dF, st);
+    if (status == PINT_OK) status = solve_enqueue(r->plan, r->dF, r->dU, r->req.tol, r->req.max_sweeps, st, in_v);
+  }
   if (status == PINT_OK) {
     e = cudaEventRecord(s->events[r->slot], st);
     if (e != cudaSuccess) status = PINT_ECUDA;
