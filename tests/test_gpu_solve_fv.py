@@ -32,6 +32,8 @@ CASES = [
     ("cq1d_255_N128_a0.5", lambda: workloads.small_problem(dim=1, mx=255, N=128, k=3, alpha=0.5), "mixed"),
     ("2d_63_N64_bdf4_fp64", lambda: workloads.small_problem(dim=2, mx=63, N=64, k=4), "fp64"),
     ("1d_31_N32_small", lambda: workloads.small_problem(dim=1, mx=31, N=32, k=2), "mixed"),
+    ("1d_127_N64_bdf1", lambda: workloads.small_problem(dim=1, mx=127, N=64, k=1), "mixed"),   # one head level, no d^l f(0)
+    ("2d_63_N32_bdf3_fp32", lambda: workloads.small_problem(dim=2, mx=63, N=32, k=3), "fp32"),
 ]
 
 
@@ -41,17 +43,18 @@ def test_solve_fv_matches_form_rhs_and_solve_v(name, make, precision):
     from paper_2007_13125_gb300 import Plan
     p = make()
     v, f, fd = device_inputs(p, torch)
-    bar = 1e-8 if precision == "mixed" else 1e-10
+    bar = {"mixed": 1e-8, "fp64": 1e-10, "fp32": 1e-4}[precision]
+    tol = 1e-5 if precision == "fp32" else 1e-10
     with Plan.for_problem(p, precision) as plan:
         F = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
         plan.form_rhs(v, f, fd, F)
         U1 = torch.empty_like(F)
-        st1, sw1, _ = plan.solve_v(F, v, U1, tol=1e-10)
+        st1, sw1, _ = plan.solve_v(F, v, U1, tol=tol)
         U2 = torch.empty_like(F)
-        st2, sw2, _ = plan.solve_fv(v, f, fd, U2, tol=1e-10)
+        st2, sw2, _ = plan.solve_fv(v, f, fd, U2, tol=tol)
         # a second call reuses the plan's state (correction block or F_hat workspace, graphs)
         U3 = torch.empty_like(F)
-        st3, sw3, _ = plan.solve_fv(v, f, fd, U3, tol=1e-10)
+        st3, sw3, _ = plan.solve_fv(v, f, fd, U3, tol=tol)
         torch.cuda.synchronize()
     a, b, c = U1.cpu().numpy(), U2.cpu().numpy(), U3.cpu().numpy()
     assert st1 == st2 == st3 == 0 and sw1 == sw2 == sw3, (sw1, sw2, sw3)
