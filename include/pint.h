@@ -126,11 +126,13 @@ typedef struct {
                              step 2; 2D and 3D finite differences, Dirichlet): 1 = odd-sequence FFT;
                              2 = a dense product with the sine matrix on the tensor cores (tcgen05;
                              FP16 operands split in two, three products per term, the accuracy of
-                             the FP32 FFT) where the lines have 255 points, else 1; 3 = whichever
-                             of 1 and 2 runs faster, timed at plan creation (cached per shape);
-                             0 (default) = 2 when the lines have 255 points and there are at least
-                             16384 of them ((N/2 + 1) my mz), else 1. PINT_FP64 plans use 1.
-                             The tensor-core form holds 128 KB of tables on the device. */
+                             the FP32 FFT) where the lines have 255 or 127 points, else 1;
+                             3 = whichever of 1 and 2 runs faster, timed at plan creation (cached
+                             per shape); 0 (default) = 2 when the lines have 255 points and there
+                             are at least 16384 of them ((N/2 + 1) my mz), or 127 points and at
+                             least 8192 of them, else 1. PINT_FP64 plans use 1. The tensor-core
+                             form holds 128 KB (255 points) or 64 KB (127 points) of tables on the
+                             device. */
 } pint_plan_desc;
 
 /* Build a plan: FP64 constant tables (BDF / CQ weights omega_j of eq. (2.2) / eq. (3.2) --

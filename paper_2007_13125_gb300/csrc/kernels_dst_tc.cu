@@ -1,15 +1,20 @@
-// Sine transform along x of lines of n = 255 points as tensor-core products (tcgen05, sm_103a).
+// Sine transform along x of lines of n = 255 or n = 127 points as tensor-core products (tcgen05,
+// sm_103a).
 //
 // The x-direction step of the shifted spatial solves (Algorithm 1 / 2, step 2: A is diagonal on
 // the sine modes, Sec. 2.2) transforms every line of the half spectrum,
-//   Y_k = -2i sum_{x=1}^{255} X_x sin(pi k x / 256),   k = 1..255,
+//   Y_k = -2i sum_{x=1}^{n} X_x sin(pi k x / (n + 1)),   k = 1..n,
 // the same output as the odd-sequence FFT (k_axis, op 0). Here it is a dense contraction against
-// the sine matrix, folded once: with e_x = X_x - X_{256-x} and o_x = X_x + X_{256-x},
-//   Y_{2k'}   = -2i sum_{x=1}^{127} e_x sin(pi k' x / 128)            (k' = 1..127)
-//   Y_{2k'+1} = -2i sum_{x=1}^{128} o_x sin(pi (2k'+1) x / 256)       (o_128 = X_128, k' = 0..127)
-// (sin(pi k (256 - x) / 256) = -/+ sin(pi k x / 256) for even / odd k). Each half is a 128 x 128
-// matrix times the lines' real and imaginary parts: D = S B^T with M = 128 outputs, K = 128 inputs
-// and N = 64 real rows (32 complex lines per tile).
+// the sine matrix, as MMAs with M = 128 outputs and K = 128 inputs:
+//   * n = 255 (k_dst255_tc): the matrix is folded once. With e_x = X_x - X_{256-x} and
+//     o_x = X_x + X_{256-x},
+//       Y_{2k'}   = -2i sum_{x=1}^{127} e_x sin(pi k' x / 128)            (k' = 1..127)
+//       Y_{2k'+1} = -2i sum_{x=1}^{128} o_x sin(pi (2k'+1) x / 256)       (o_128 = X_128, k' = 0..127)
+//     (sin(pi k (256 - x) / 256) = -/+ sin(pi k x / 256) for even / odd k). Each half is a 128 x 128
+//     matrix times the lines' real and imaginary parts: D = S B^T with N = 64 real rows (32
+//     complex lines per tile).
+//   * n = 127 (k_dst127_tc): the 127 x 127 matrix itself, padded with a zero row and column, is one
+//     128 x 128 operand; no fold. N = 128 real rows (64 complex lines per tile).
 //
 // Precision: FP16 operands split in two (v = hi + lo: hi of 11 significant bits by Veltkamp's
 // splitting, lo = v - hi), three products per term (hi hi + hi lo + lo hi, FP32 accumulation in
@@ -18,24 +23,25 @@
 // FP16 range holds it; the matrices are scaled by 16 (their low parts stay normal numbers). Both
 // scalings are exact and undone in the epilogue.
 //
-// Roles (one CTA per SM, persistent over tiles of 32 lines; the resident matrices fill most of its
-// shared memory):
-//   * load warp: one thread copies each tile's lines (contiguous, 65 KB) into a raw buffer with
+// Roles (one CTA per SM, persistent over tiles of lines; the resident matrices take a large part
+// of its shared memory):
+//   * load warp: one thread copies each tile's lines (contiguous, ~65 KB) into a raw buffer with
 //     bulk asynchronous copies (cp.async.bulk, complete_tx on a shared-memory barrier), as soon as
 //     the staging threads have taken the previous tile out of it;
 //   * 8 staging warps: read their share of the raw tile into registers (then release the buffer),
-//     reduce each line's largest magnitude, fold, scale and split the lines into K-chunks of 32
+//     reduce each line's largest magnitude, (fold,) scale and split the lines into K-chunks of 32
 //     inputs in the canonical K-major layout (8-row x 16-byte core matrices, no swizzle) in a ring
 //     of two stage slots, and signal each chunk on the slot's "full" barrier; after staging a tile
 //     they run the previous tile's epilogue, so that a tile's MMAs overlap it;
-//   * MMA warp: one thread copies the four matrix operands (hi / lo of both halves, 128 KB, a
+//   * MMA warp: one thread copies the matrix operands (hi / lo, of both halves for n = 255; a
 //     precomputed image of their shared-memory layout) once by bulk copies, then for each chunk
-//     waits "full", issues the 12 MMAs (M 128, N 64, K 16) and commits them to the slot's "empty"
-//     barrier; after a tile's last chunk it commits the tile to its accumulator buffer's barrier.
-// Accumulators are double-buffered in tensor memory (2 x 128 columns: D_even and D_odd, 64
-// columns each); the epilogue reads them with tcgen05.ld (one output per lane: TMEM lane = output
-// index), releases the buffer, unscales, applies -2i and writes the lines in place (every read of
-// a tile precedes its writes).
+//     waits "full", issues the chunk's MMAs (M 128, N 64 or 128, K 16; three per term) and commits
+//     them to the slot's "empty" barrier; after a tile's last chunk it commits the tile to its
+//     accumulator buffer's barrier.
+// Accumulators are double-buffered in tensor memory (2 x 128 columns: D_even and D_odd of 64
+// columns each, or one D of 128); the epilogue reads them with tcgen05.ld (one output per lane:
+// TMEM lane = output index), releases the buffer, unscales, applies -2i and writes the lines in
+// place (every read of a tile precedes its writes).
 //
 // Every wait is bounded: a barrier that does not complete within ~2^31 clock cycles sets a shared
 // abort flag (all roles then stop at their next wait or tile) and *err; before the CTA exits, the
@@ -52,44 +58,58 @@
 namespace pint {
 namespace {
 
-constexpr int kTcLines = 32;                   // complex lines per tile
-constexpr int kTcN = 2 * kTcLines;             // MMA N: real rows (re 0..31, im 32..63)
-constexpr int kTcChunk = 32;                   // K inputs per stage buffer
-constexpr int kTcChunks = 128 / kTcChunk;      // stage buffers (one tile)
-constexpr int kTcStageThreads = 256;           // staging / epilogue warps
-constexpr int kTcItems = 512 / kTcStageThreads;  // items (line, pair of inputs) per staging thread
-constexpr int kTcLinesPerWarp = kTcLines * 128 / kTcStageThreads;  // epilogue lines per warp
-constexpr int kTcThreads = kTcStageThreads + 64;  // + the MMA warp and the load warp
-constexpr int kTcMatBytes = 128 * 128 * 2;     // one 128 x 128 FP16 operand
-constexpr int kTcABytes = 4 * kTcMatBytes;     // even hi, even lo, odd hi, odd lo
-constexpr int kTcOpBytes = kTcN * kTcChunk * 2;  // one B operand of one stage
-constexpr int kTcStageBytes = 4 * kTcOpBytes;
-constexpr int kTcSlots = 2;                    // stage slots (ring of K-chunks)
-constexpr int kTcLineBytes = 255 * 8;          // one line of complex FP32 values
-constexpr int kTcRawOff = kTcABytes + kTcSlots * kTcStageBytes;    // the tile's lines as read
-constexpr int kTcMiscOff = kTcRawOff + 65536;
-constexpr int kTcSmemBytes = kTcMiscOff + 1536;
-constexpr int kTcTmemCols = 256;                // two accumulator buffers of 128 columns
+// Tile geometry per line length P (compile time).
+template <int P> struct TcShape {
+  static_assert(P == 255 || P == 127, "line length");
+  static constexpr bool kFold = P == 255;                 // folded into even / odd halves
+  static constexpr int kHalves = kFold ? 2 : 1;           // D regions (and matrix operands / 2)
+  static constexpr int kLines = kFold ? 32 : 64;          // complex lines per tile
+  static constexpr int kN = 2 * kLines;                   // MMA N: real rows (re, then im)
+  static constexpr int kChunk = 32;                       // K inputs per stage buffer
+  static constexpr int kChunks = 128 / kChunk;            // stage buffers (one tile)
+  static constexpr int kStageThreads = 256;               // staging / epilogue warps
+  static constexpr int kItems = kLines * 16 / kStageThreads;  // items (line, pair of K inputs) per thread
+  static constexpr int kVals = kFold ? 4 : 2;             // complex inputs per item and chunk
+  static constexpr int kLinesPerWarp = kLines * 128 / kStageThreads;  // epilogue lines per warp
+  static constexpr int kThreads = kStageThreads + 64;     // + the MMA warp and the load warp
+  static constexpr int kMatBytes = 128 * 128 * 2;         // one 128 x 128 FP16 operand
+  static constexpr int kABytes = 2 * kHalves * kMatBytes; // hi, lo (of each half)
+  static constexpr int kOpBytes = kN * kChunk * 2;        // one B operand of one stage
+  static constexpr int kStageBytes = 2 * kHalves * kOpBytes;
+  static constexpr int kSlots = 2;                        // stage slots (ring of K-chunks)
+  static constexpr int kLineBytes = P * 8;                // one line of complex FP32 values
+  static constexpr int kRawOff = kABytes + kSlots * kStageBytes;  // the tile's lines as read
+  static constexpr int kMiscOff = kRawOff + 65536;
+  static constexpr int kMiscBytes = 2048;
+  static constexpr int kSmemBytes = kMiscOff + kMiscBytes;
+  static constexpr int kTmemCols = 256;                   // two accumulator buffers of 128 columns
+  // instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B FP16 (formats 0), both
+  // K-major, N >> 3 at bit 17, M >> 4 at bit 24
+  static constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  static_assert(kItems * kStageThreads == kLines * 16, "items");
+  static_assert(kStageBytes == 16384, "stage");
+  static_assert(kLines * kLineBytes <= 65536, "raw tile");
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+};
+
 constexpr long long kTcWaitCycles = 1ll << 31;
 
-// instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B FP16 (formats 0), both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24
-constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-
-struct TcMisc {
-  unsigned long long bar_a;                 // matrix image copied
-  unsigned long long full[kTcSlots];        // stage slot written (the staging threads arrive)
-  unsigned long long empty[kTcSlots];       // stage slot's MMAs done (tcgen05.commit)
-  unsigned long long raw_full;              // the tile's lines copied (bulk copies complete)
-  unsigned long long raw_empty;             // the tile's lines read out (the staging threads arrive)
-  unsigned long long acc_full[2];           // accumulator buffer complete (tcgen05.commit)
-  unsigned long long acc_empty[2];          // accumulator buffer read out (256 threads arrive)
-  unsigned long long fin;                   // every MMA done (tcgen05.commit, at exit)
-  float pmax[4][kTcLines];                  // per line and group of inputs: largest |re|, |im|
-  float unscale[2][kTcLines];               // per accumulator buffer and line: 2 / (16 * 2^s)
-  uint32_t tmem;                            // tensor-memory base address
-  uint32_t abort;                           // a wait gave up: every role stops
+template <int P> struct TcMisc {
+  unsigned long long bar_a;                     // matrix image copied
+  unsigned long long full[2];                   // stage slot written (the staging threads arrive)
+  unsigned long long empty[2];                  // stage slot's MMAs done (tcgen05.commit)
+  unsigned long long raw_full;                  // the tile's lines copied (bulk copies complete)
+  unsigned long long raw_empty;                 // the tile's lines read out (the staging threads arrive)
+  unsigned long long acc_full[2];               // accumulator buffer complete (tcgen05.commit)
+  unsigned long long acc_empty[2];              // accumulator buffer read out (256 threads arrive)
+  unsigned long long fin;                       // every MMA done (tcgen05.commit, at exit)
+  float pmax[4][TcShape<P>::kLines];            // per line and group of inputs: largest |re|, |im|
+  float unscale[2][TcShape<P>::kLines];         // per accumulator buffer and line: 2 / (16 * 2^s)
+  uint32_t tmem;                                // tensor-memory base address
+  uint32_t abort;                               // a wait gave up: every role stops
 };
+static_assert(sizeof(TcMisc<255>) <= TcShape<255>::kMiscBytes && sizeof(TcMisc<127>) <= TcShape<127>::kMiscBytes,
+              "barrier block");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -102,11 +122,12 @@ __device__ __forceinline__ uint64_t mat_desc(uint32_t saddr, uint32_t lbo, uint3
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+template <uint32_t IDESC>
 __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -158,7 +179,7 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 // byte offset of (row, k) in a K-major operand of `rows` rows: core matrices of 8 rows x 8 FP16,
 // rows of a core matrix 16 bytes apart, core matrices along rows 128 bytes apart (SBO), along K
 // rows / 8 * 128 bytes apart (LBO)
-__device__ __forceinline__ uint32_t kmajor_off(int row, int k, int rows) {
+__host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int k, int rows) {
   return (uint32_t)((k >> 3) * (rows / 8) * 128 + (row >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
@@ -183,12 +204,18 @@ __device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_dst255_tc(DstTcArgs a) {
+// the whole kernel for lines of P points (launched by k_dst255_tc / k_dst127_tc)
+template <int P> __device__ __forceinline__ void dst_tc_body(const DstTcArgs& a) {
+  using S = TcShape<P>;
+  constexpr int kLines = S::kLines, kN = S::kN, kChunk = S::kChunk, kChunks = S::kChunks;
+  constexpr int kStageThreads = S::kStageThreads, kItems = S::kItems, kVals = S::kVals;
+  constexpr int kLinesPerWarp = S::kLinesPerWarp, kMatBytes = S::kMatBytes, kABytes = S::kABytes;
+  constexpr int kOpBytes = S::kOpBytes, kStageBytes = S::kStageBytes, kHalves = S::kHalves;
   extern __shared__ __align__(1024) unsigned char smem[];
-  TcMisc& ms = *reinterpret_cast<TcMisc*>(smem + kTcMiscOff);
+  TcMisc<P>& ms = *reinterpret_cast<TcMisc<P>*>(smem + S::kMiscOff);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t sA = smem_u32(smem), sB = sA + kTcABytes;
-  const int tiles = (a.lines + kTcLines - 1) / kTcLines;
+  const uint32_t sA = smem_u32(smem), sB = sA + kABytes;
+  const int tiles = (a.lines + kLines - 1) / kLines;
   const uint32_t* abort = reinterpret_cast<const uint32_t*>(&ms.abort);
 
   if (tid == 0) {
@@ -196,15 +223,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dst255_tc(DstTcArgs a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
     };
     init(&ms.bar_a, 1);
-    for (int c = 0; c < kTcSlots; ++c) {
-      init(&ms.full[c], kTcStageThreads);
+    for (int c = 0; c < S::kSlots; ++c) {
+      init(&ms.full[c], kStageThreads);
       init(&ms.empty[c], 1);
     }
     init(&ms.raw_full, 1);
-    init(&ms.raw_empty, kTcStageThreads);
+    init(&ms.raw_empty, kStageThreads);
     for (int b2 = 0; b2 < 2; ++b2) {
       init(&ms.acc_full[b2], 1);
-      init(&ms.acc_empty[b2], kTcStageThreads);
+      init(&ms.acc_empty[b2], kStageThreads);
     }
     init(&ms.fin, 1);
     ms.abort = 0;
@@ -212,7 +239,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dst255_tc(DstTcArgs a) {
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ms.tmem)),
-                 "r"(kTcTmemCols)
+                 "r"(S::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -221,48 +248,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dst255_tc(DstTcArgs a) {
   tc_after_sync();
   const uint32_t tmem = ms.tmem;
 
-  if (warp == kTcStageThreads / 32) {
+  if (warp == kStageThreads / 32) {
     // ---- MMA warp: one thread issues every MMA of the CTA ----
     if (lane == 0) {
       const uint32_t ba = smem_u32(&ms.bar_a);
-      // the four matrix operands: one image, copied in four bulk copies of 32 KB
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ba), "r"(kTcABytes) : "memory");
-      for (int i = 0; i < 4; ++i)
+      // the matrix operands: one image, copied in bulk copies of 32 KB
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ba), "r"(kABytes) : "memory");
+      for (int i = 0; i < 2 * kHalves; ++i)
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                sA + i * kTcMatBytes),
-            "l"(reinterpret_cast<const unsigned char*>(a.tab) + (size_t)i * kTcMatBytes), "r"(kTcMatBytes),
+                sA + i * kMatBytes),
+            "l"(reinterpret_cast<const unsigned char*>(a.tab) + (size_t)i * kMatBytes), "r"(kMatBytes),
             "r"(ba)
             : "memory");
       bool ok = bar_wait(ba, 0u, abort);
-      // descriptors of the first K step; a later step adds its byte offset >> 4 to the start field
-      const uint64_t dA[4] = {mat_desc(sA + 0 * kTcMatBytes, 16 * 128, 128), mat_desc(sA + 1 * kTcMatBytes, 16 * 128, 128),
-                              mat_desc(sA + 2 * kTcMatBytes, 16 * 128, 128), mat_desc(sA + 3 * kTcMatBytes, 16 * 128, 128)};
+      // descriptors of the first K step (operand 2h: hi, 2h + 1: lo of half h); a later step adds
+      // its byte offset >> 4 to the start field
+      uint64_t dA[2 * kHalves];
+#pragma unroll
+      for (int i = 0; i < 2 * kHalves; ++i) dA[i] = mat_desc(sA + i * kMatBytes, 16 * 128, 128);
       int i = 0;
       for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
         const int b2 = i & 1;
         if (i >= 2) ok = bar_wait(smem_u32(&ms.acc_empty[b2]), (uint32_t)(((i >> 1) - 1) & 1), abort);
         tc_after_sync();
-        const uint32_t dacc = tmem + (uint32_t)(b2 * 2 * kTcN);
-        for (int c = 0; c < kTcChunks && ok; ++c) {
+        const uint32_t dacc = tmem + (uint32_t)(b2 * kHalves * kN);
+        for (int c = 0; c < kChunks && ok; ++c) {
           const int u = 2 * i + (c >> 1);  // use of the chunk's slot (c & 1)
           ok = bar_wait(smem_u32(&ms.full[c & 1]), (uint32_t)(u & 1), abort);
           if (!ok) break;
           tc_after_sync();
-          const uint32_t stage = sB + (c & 1) * kTcStageBytes;
+          const uint32_t stage = sB + (c & 1) * kStageBytes;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t d = dacc + (uint32_t)(h * kTcN);
-            const uint64_t dbh0 = mat_desc(stage + (2 * h) * kTcOpBytes, (kTcN / 8) * 128, 128);
-            const uint64_t dbl0 = mat_desc(stage + (2 * h + 1) * kTcOpBytes, (kTcN / 8) * 128, 128);
+          for (int h = 0; h < kHalves; ++h) {
+            const uint32_t d = dacc + (uint32_t)(h * kN);
+            const uint64_t dbh0 = mat_desc(stage + (2 * h) * kOpBytes, (kN / 8) * 128, 128);
+            const uint64_t dbl0 = mat_desc(stage + (2 * h + 1) * kOpBytes, (kN / 8) * 128, 128);
 #pragma unroll
-            for (int ks = 0; ks < kTcChunk / 16; ++ks) {
-              const int kg = c * (kTcChunk / 16) + ks;  // 16-input step within the 128 inputs
+            for (int ks = 0; ks < kChunk / 16; ++ks) {
+              const int kg = c * (kChunk / 16) + ks;  // 16-input step within the 128 inputs
               const uint64_t aoff = (uint64_t)(kg * 2 * 16 * 128) >> 4;  // two core matrices along K
-              const uint64_t boff = (uint64_t)(ks * 2 * (kTcN / 8) * 128) >> 4;
-              mma_f16(d, dA[2 * h] + aoff, dbh0 + boff, (c | ks) ? 1u : 0u);
-              mma_f16(d, dA[2 * h] + aoff, dbl0 + boff, 1u);
-              mma_f16(d, dA[2 * h + 1] + aoff, dbh0 + boff, 1u);
+              const uint64_t boff = (uint64_t)(ks * 2 * (kN / 8) * 128) >> 4;
+              mma_f16<S::kIdesc>(d, dA[2 * h] + aoff, dbh0 + boff, (c | ks) ? 1u : 0u);
+              mma_f16<S::kIdesc>(d, dA[2 * h] + aoff, dbl0 + boff, 1u);
+              mma_f16<S::kIdesc>(d, dA[2 * h + 1] + aoff, dbh0 + boff, 1u);
             }
           }
           mma_commit(smem_u32(&ms.empty[c & 1]));  // the slot is free once these MMAs are done
@@ -280,22 +309,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dst255_tc(DstTcArgs a) {
       mma_commit(fin);
       bar_wait(fin, 0u, nullptr);
     }
-  } else if (warp == kTcStageThreads / 32 + 1) {
+  } else if (warp == kStageThreads / 32 + 1) {
     // ---- load warp: one thread copies each tile's lines (contiguous) into the raw buffer as soon
     // as the staging threads have read the previous tile's out of it ----
     if (lane == 0) {
-      const uint32_t rf = smem_u32(&ms.raw_full), sraw = sA + kTcRawOff;
+      const uint32_t rf = smem_u32(&ms.raw_full), sraw = sA + S::kRawOff;
       bool ok = true;
       int i = 0;
       for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
         if (i >= 1) ok = bar_wait(smem_u32(&ms.raw_empty), (uint32_t)((i - 1) & 1), abort);
         if (!ok) break;
-        const long long first = (long long)t * kTcLines;
-        const int n = (int)(a.lines - first < kTcLines ? a.lines - first : kTcLines);
-        const unsigned char* src = reinterpret_cast<const unsigned char*>(a.S + first * 255);
+        const long long first = (long long)t * kLines;
+        const int n = (int)(a.lines - first < kLines ? a.lines - first : kLines);
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(a.S + first * P);
         // bulk copies move multiples of 16 bytes: an odd count of lines leaves the last value
         // of the last line (8 bytes) to a plain copy, written before the arrive that publishes it
-        const uint32_t bytes = (uint32_t)n * kTcLineBytes - ((n & 1) ? 8u : 0u);
+        // (tiles start on a 16-byte boundary: a tile holds an even number of odd-length lines)
+        const uint32_t bytes = (uint32_t)n * S::kLineBytes - ((n & 1) ? 8u : 0u);
         if (n & 1) {
           const float2 v = *reinterpret_cast<const float2*>(src + bytes);
           asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(sraw + bytes), "f"(v.x), "f"(v.y) : "memory");
@@ -324,63 +354,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dst255_tc(DstTcArgs a) {
           "{\n\t.reg .pred q, p;\n\tsetp.ne.u32 q, %1, 0;\n\t"
           "bar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
           : "=r"(any)
-          : "r"(f), "r"(kTcStageThreads)
+          : "r"(f), "r"(kStageThreads)
           : "memory");
       return any != 0;
     };
-    // item (line l, pair q, group g8) of a tile, item = tid + j * threads: for each chunk c,
-    // X_x, X_{x+1}, X_{256-x}, X_{255-x} with x = 32 c + 8 g8 + 2 q + 1 (32 lines x 16 pairs of
-    // inputs = 512 items)
-    int il[kTcItems], ikl[kTcItems];
-    uint32_t iore[kTcItems], ioim[kTcItems];
+    // item (line l, pair q, group g8) of a tile, item = tid + j * threads; for each chunk c the
+    // pair covers the K inputs kk = 32 c + 8 g8 + 2 q and kk + 1, i.e. x = kk + 1 and x + 1:
+    //   n = 255: X_x, X_{x+1}, X_{256-x}, X_{255-x} (folded);  n = 127: X_x, X_{x+1} (X_128 = 0)
+    int il[kItems], ikl[kItems];
+    uint32_t iore[kItems], ioim[kItems];
 #pragma unroll
-    for (int j = 0; j < kTcItems; ++j) {
-      const int item = tid + j * kTcStageThreads;
-      const int q = item & 3, rl = (item >> 2) & 7, g8 = (item >> 5) & 3, rh = (item >> 7) & 3;
+    for (int j = 0; j < kItems; ++j) {
+      const int item = tid + j * kStageThreads;
+      const int q = item & 3, rl = (item >> 2) & 7, g8 = (item >> 5) & 3, rh = item >> 7;
       il[j] = rh * 8 + rl;
       ikl[j] = g8 * 8 + 2 * q;  // K index within a chunk (even)
-      iore[j] = kmajor_off(il[j], ikl[j], kTcN);
-      ioim[j] = kmajor_off(kTcLines + il[j], ikl[j], kTcN);
+      iore[j] = kmajor_off(il[j], ikl[j], kN);
+      ioim[j] = kmajor_off(kLines + il[j], ikl[j], kN);
     }
-    const float2* raw = reinterpret_cast<const float2*>(smem + kTcRawOff);
+    const float2* raw = reinterpret_cast<const float2*>(smem + S::kRawOff);
     // epilogue of the j-th tile of this CTA (tile index tj): lanes 32 (warp % 4) .. + 31 of tensor
-    // memory hold output index m; each group of four warps takes kTcLinesPerWarp lines
+    // memory hold output index m; each group of four warps takes kLinesPerWarp lines
     auto epilogue = [&](int j, int tj) {
       const int b2 = j & 1;
       if (!bar_wait(smem_u32(&ms.acc_full[b2]), (uint32_t)((j >> 1) & 1), abort)) atomicExch(&ms.abort, 1u);
       tc_after_sync();
       const int m = 32 * (warp & 3) + lane;
-      const int l0 = kTcLinesPerWarp * (warp >> 2);
-      const uint32_t tl = tmem + (uint32_t)(b2 * 2 * kTcN) + ((uint32_t)(32 * (warp & 3)) << 16);
+      const int l0 = kLinesPerWarp * (warp >> 2);
+      const uint32_t tl = tmem + (uint32_t)(b2 * kHalves * kN) + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll
-      for (int h8 = 0; h8 < kTcLinesPerWarp; h8 += 8) {
-        float ere[8], eim[8], orr[8], oim8[8];
-        tmem_ld8(tl + (uint32_t)(0 * kTcN + l0 + h8), ere);
-        tmem_ld8(tl + (uint32_t)(0 * kTcN + kTcLines + l0 + h8), eim);
-        tmem_ld8(tl + (uint32_t)(1 * kTcN + l0 + h8), orr);
-        tmem_ld8(tl + (uint32_t)(1 * kTcN + kTcLines + l0 + h8), oim8);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (h8 + 8 == kTcLinesPerWarp) {
-          tc_before_sync();
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.acc_empty[b2])) : "memory");
-        }
-        if (!*reinterpret_cast<volatile uint32_t*>(&ms.abort)) {
+      for (int h8 = 0; h8 < kLinesPerWarp; h8 += 8) {
+        if constexpr (S::kFold) {
+          float ere[8], eim[8], orr[8], oim8[8];
+          tmem_ld8(tl + (uint32_t)(0 * kN + l0 + h8), ere);
+          tmem_ld8(tl + (uint32_t)(0 * kN + kLines + l0 + h8), eim);
+          tmem_ld8(tl + (uint32_t)(1 * kN + l0 + h8), orr);
+          tmem_ld8(tl + (uint32_t)(1 * kN + kLines + l0 + h8), oim8);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (h8 + 8 == kLinesPerWarp) {
+            tc_before_sync();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.acc_empty[b2])) : "memory");
+          }
+          if (!*reinterpret_cast<volatile uint32_t*>(&ms.abort)) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int lu = l0 + h8 + u;
-            const long long line = (long long)tj * kTcLines + lu;
-            if (line >= a.lines) break;
-            const float us = ms.unscale[b2][lu];
-            float2* row = a.S + line * 255;
-            // -2i z = (2 Im z, -2 Re z); index 2m: k = 2m + 1 (odd half), 2m + 1: k = 2m + 2 (even half)
-            const float2 yo = make_float2(oim8[u] * us, -orr[u] * us);
-            const float2 ye = make_float2(eim[u] * us, -ere[u] * us);
-            if ((line & 1) == 0 && m < 127) {
-              // even lines start on a 16-byte boundary (255 values of 8 bytes per line)
-              *reinterpret_cast<float4*>(row + 2 * m) = make_float4(yo.x, yo.y, ye.x, ye.y);
-            } else {
-              row[2 * m] = yo;
-              if (m < 127) row[2 * m + 1] = ye;
+            for (int u = 0; u < 8; ++u) {
+              const int lu = l0 + h8 + u;
+              const long long line = (long long)tj * kLines + lu;
+              if (line >= a.lines) break;
+              const float us = ms.unscale[b2][lu];
+              float2* row = a.S + line * P;
+              // -2i z = (2 Im z, -2 Re z); index 2m: k = 2m + 1 (odd half), 2m + 1: k = 2m + 2 (even half)
+              const float2 yo = make_float2(oim8[u] * us, -orr[u] * us);
+              const float2 ye = make_float2(eim[u] * us, -ere[u] * us);
+              if ((line & 1) == 0 && m < 127) {
+                // even lines start on a 16-byte boundary (255 values of 8 bytes per line)
+                *reinterpret_cast<float4*>(row + 2 * m) = make_float4(yo.x, yo.y, ye.x, ye.y);
+              } else {
+                row[2 * m] = yo;
+                if (m < 127) row[2 * m + 1] = ye;
+              }
+            }
+          }
+        } else {
+          float re[8], im[8];
+          tmem_ld8(tl + (uint32_t)(l0 + h8), re);
+          tmem_ld8(tl + (uint32_t)(kLines + l0 + h8), im);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (h8 + 8 == kLinesPerWarp) {
+            tc_before_sync();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.acc_empty[b2])) : "memory");
+          }
+          if (!*reinterpret_cast<volatile uint32_t*>(&ms.abort) && m < P) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int lu = l0 + h8 + u;
+              const long long line = (long long)tj * kLines + lu;
+              if (line >= a.lines) break;
+              const float us = ms.unscale[b2][lu];
+              // output index m: k = m + 1; -2i z = (2 Im z, -2 Re z)
+              a.S[line * P + m] = make_float2(im[u] * us, -re[u] * us);
             }
           }
         }
@@ -391,39 +443,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dst255_tc(DstTcArgs a) {
       const int b2 = i & 1;
       // the tile's inputs, from the raw buffer into registers; then the buffer is released
       if (!bar_wait(smem_u32(&ms.raw_full), (uint32_t)(i & 1), abort)) atomicExch(&ms.abort, 1u);
-      float2 in[kTcItems][kTcChunks][4];
+      float2 in[kItems][kChunks][kVals];
 #pragma unroll
-      for (int j = 0; j < kTcItems; ++j) {
-        const bool okl = (long long)t * kTcLines + il[j] < a.lines;
-        const float2* row = raw + il[j] * 255;
+      for (int j = 0; j < kItems; ++j) {
+        const bool okl = (long long)t * kLines + il[j] < a.lines;
+        const float2* row = raw + il[j] * P;
 #pragma unroll
-        for (int c = 0; c < kTcChunks; ++c) {
-          const int x = c * kTcChunk + ikl[j] + 1;
+        for (int c = 0; c < kChunks; ++c) {
+          const int x = c * kChunk + ikl[j] + 1;
           const float2 z = make_float2(0.f, 0.f);
           in[j][c][0] = okl ? row[x - 1] : z;
-          in[j][c][1] = okl ? row[x] : z;
-          in[j][c][2] = okl ? row[255 - x] : z;
-          in[j][c][3] = okl ? row[254 - x] : z;
+          if constexpr (S::kFold) {
+            in[j][c][1] = okl ? row[x] : z;
+            in[j][c][2] = okl ? row[255 - x] : z;
+            in[j][c][3] = okl ? row[254 - x] : z;
+          } else {
+            in[j][c][1] = (okl && x < P) ? row[x] : z;  // x + 1 = 128: the zero padding
+          }
         }
       }
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.raw_empty)) : "memory");
       // largest |re|, |im| of each line: over the item, its four lanes (q), the four warps
       // holding the line's groups (g8)
 #pragma unroll
-      for (int j = 0; j < kTcItems; ++j) {
+      for (int j = 0; j < kItems; ++j) {
         float m = 0.f;
 #pragma unroll
-        for (int c = 0; c < kTcChunks; ++c)
+        for (int c = 0; c < kChunks; ++c)
 #pragma unroll
-          for (int k = 0; k < 4; ++k) m = fmaxf(m, fmaxf(fabsf(in[j][c][k].x), fabsf(in[j][c][k].y)));
+          for (int k = 0; k < kVals; ++k) m = fmaxf(m, fmaxf(fabsf(in[j][c][k].x), fabsf(in[j][c][k].y)));
         m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
         m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
         if ((ikl[j] & 7) == 0) ms.pmax[ikl[j] >> 3][il[j]] = m;
       }
       if (ssync_abort()) break;
-      float sc[kTcItems];
+      float sc[kItems];
 #pragma unroll
-      for (int j = 0; j < kTcItems; ++j) {
+      for (int j = 0; j < kItems; ++j) {
         const int l = il[j];
         const float m = fmaxf(fmaxf(ms.pmax[0][l], ms.pmax[1][l]), fmaxf(ms.pmax[2][l], ms.pmax[3][l]));
         // m = f 2^E, f in [0.5, 1): the scale 2^(14 - E) brings m to [2^13, 2^14)
@@ -433,35 +489,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dst255_tc(DstTcArgs a) {
         sc[j] = __uint_as_float((uint32_t)(127 + sh) << 23);
         if (ikl[j] == 0) ms.unscale[b2][l] = __uint_as_float((uint32_t)(127 - sh - 3) << 23);  // 2/(16 2^sh)
       }
-      // fold, scale and split chunk by chunk into the stage slots (each free once the MMAs of
+      // (fold,) scale and split chunk by chunk into the stage slots (each free once the MMAs of
       // its previous chunk are done), then signal the MMA warp
 #pragma unroll
-      for (int c = 0; c < kTcChunks; ++c) {
+      for (int c = 0; c < kChunks; ++c) {
         const int u = 2 * i + (c >> 1);  // use of the chunk's slot (c & 1)
         if (u >= 1 && !bar_wait(smem_u32(&ms.empty[c & 1]), (uint32_t)((u - 1) & 1), abort))
           atomicExch(&ms.abort, 1u);
-        const uint32_t stage = sB + (c & 1) * kTcStageBytes;
+        const uint32_t stage = sB + (c & 1) * kStageBytes;
 #pragma unroll
-        for (int j = 0; j < kTcItems; ++j) {
-          const float2 a0 = in[j][c][0], a1 = in[j][c][1], b0 = in[j][c][2], b1 = in[j][c][3];
+        for (int j = 0; j < kItems; ++j) {
           const float f = sc[j];
-          const float2 e0 = make_float2((a0.x - b0.x) * f, (a0.y - b0.y) * f);
-          const float2 e1 = make_float2((a1.x - b1.x) * f, (a1.y - b1.y) * f);
-          const float2 o0 = make_float2((a0.x + b0.x) * f, (a0.y + b0.y) * f);
-          const float2 o1 = make_float2((a1.x + b1.x) * f, (a1.y + b1.y) * f);
-          uint32_t lo;
-          uint32_t hi = split2(e0.x, e1.x, &lo);
-          sts32(stage + 0 * kTcOpBytes + iore[j], hi);
-          sts32(stage + 1 * kTcOpBytes + iore[j], lo);
-          hi = split2(e0.y, e1.y, &lo);
-          sts32(stage + 0 * kTcOpBytes + ioim[j], hi);
-          sts32(stage + 1 * kTcOpBytes + ioim[j], lo);
-          hi = split2(o0.x, o1.x, &lo);
-          sts32(stage + 2 * kTcOpBytes + iore[j], hi);
-          sts32(stage + 3 * kTcOpBytes + iore[j], lo);
-          hi = split2(o0.y, o1.y, &lo);
-          sts32(stage + 2 * kTcOpBytes + ioim[j], hi);
-          sts32(stage + 3 * kTcOpBytes + ioim[j], lo);
+          uint32_t lo, hi;
+          if constexpr (S::kFold) {
+            const float2 a0 = in[j][c][0], a1 = in[j][c][1], b0 = in[j][c][2], b1 = in[j][c][3];
+            const float2 e0 = make_float2((a0.x - b0.x) * f, (a0.y - b0.y) * f);
+            const float2 e1 = make_float2((a1.x - b1.x) * f, (a1.y - b1.y) * f);
+            const float2 o0 = make_float2((a0.x + b0.x) * f, (a0.y + b0.y) * f);
+            const float2 o1 = make_float2((a1.x + b1.x) * f, (a1.y + b1.y) * f);
+            hi = split2(e0.x, e1.x, &lo);
+            sts32(stage + 0 * kOpBytes + iore[j], hi);
+            sts32(stage + 1 * kOpBytes + iore[j], lo);
+            hi = split2(e0.y, e1.y, &lo);
+            sts32(stage + 0 * kOpBytes + ioim[j], hi);
+            sts32(stage + 1 * kOpBytes + ioim[j], lo);
+            hi = split2(o0.x, o1.x, &lo);
+            sts32(stage + 2 * kOpBytes + iore[j], hi);
+            sts32(stage + 3 * kOpBytes + iore[j], lo);
+            hi = split2(o0.y, o1.y, &lo);
+            sts32(stage + 2 * kOpBytes + ioim[j], hi);
+            sts32(stage + 3 * kOpBytes + ioim[j], lo);
+          } else {
+            const float2 a0 = in[j][c][0], a1 = in[j][c][1];
+            hi = split2(a0.x * f, a1.x * f, &lo);
+            sts32(stage + 0 * kOpBytes + iore[j], hi);
+            sts32(stage + 1 * kOpBytes + iore[j], lo);
+            hi = split2(a0.y * f, a1.y * f, &lo);
+            sts32(stage + 0 * kOpBytes + ioim[j], hi);
+            sts32(stage + 1 * kOpBytes + ioim[j], lo);
+          }
         }
         fence_async_smem();
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.full[c & 1])) : "memory");
@@ -476,48 +542,65 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dst255_tc(DstTcArgs a) {
   __syncthreads();
   if (warp == 0) {
     tc_after_sync();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols) : "memory");
   }
 }
 
-static_assert(sizeof(TcMisc) <= 1536, "barrier block");
-static_assert(kTcLines * kTcLineBytes <= 65536, "raw tile");
-static_assert(kTcSmemBytes <= 227 * 1024, "shared memory");
+__global__ void __launch_bounds__(TcShape<255>::kThreads, 1) k_dst255_tc(DstTcArgs a) { dst_tc_body<255>(a); }
+__global__ void __launch_bounds__(TcShape<127>::kThreads, 1) k_dst127_tc(DstTcArgs a) { dst_tc_body<127>(a); }
+
+// One FP16 operand pair (hi, lo) of a 128 x 128 matrix v(r, q) in its K-major shared-memory layout.
+template <typename F> void put_matrix(unsigned short* hi_img, unsigned short* lo_img, F v) {
+  for (int r = 0; r < 128; ++r)
+    for (int q = 0; q < 128; ++q) {
+      const double x = v(r, q);
+      const __half hi = __double2half(x);
+      const __half lo = __double2half(x - (double)__half2float(hi));
+      const int off = (int)kmajor_off(r, q, 128) / 2;
+      hi_img[off] = __half_as_ushort(hi);
+      lo_img[off] = __half_as_ushort(lo);
+    }
+}
 
 }  // namespace
 
-size_t dst_tc_table_bytes() { return (size_t)kTcABytes; }
+size_t dst_tc_table_bytes(int n) {
+  return n == 255 ? (size_t)TcShape<255>::kABytes : n == 127 ? (size_t)TcShape<127>::kABytes : 0;
+}
 
-// The matrix image in its shared-memory layout: [even hi | even lo | odd hi | odd lo], each
-// 128 x 128 FP16 K-major (row = output, K = input x - 1), scaled by 16.
+// The matrix image in its shared-memory layout, FP16 K-major (row = output, K = input x - 1),
+// scaled by 16.
+// n = 255: [even hi | even lo | odd hi | odd lo]
 //   even: row r -> k' = r + 1, column q -> x = q + 1: 16 sin(pi k' x / 128) (zero for k' = 128
 //         or x = 128)
 //   odd:  row r -> k' = r,     column q -> x = q + 1: 16 sin(pi (2k'+1) x / 256), halved at
 //         x = 128 (the folded input there is 2 X_128)
-void dst_tc_table(unsigned short* img) {
+// n = 127: [hi | lo], row r -> k = r + 1, column q -> x = q + 1: 16 sin(pi k x / 128) (zero for
+//         k = 128 or x = 128)
+void dst_tc_table(int n, unsigned short* img) {
   const double pi = 3.14159265358979323846;
-  for (int h = 0; h < 2; ++h)
-    for (int r = 0; r < 128; ++r)
-      for (int q = 0; q < 128; ++q) {
-        const int x = q + 1;
-        double v;
-        if (h == 0) {
-          const int kp = r + 1;
-          v = (kp == 128 || x == 128) ? 0.0 : 16.0 * std::sin(pi * (double)((kp * x) % 256) / 128.0);
-        } else {
-          v = 16.0 * std::sin(pi * (double)(((2 * r + 1) * x) % 512) / 256.0);
-          if (x == 128) v *= 0.5;
-        }
-        const __half hi = __double2half(v);
-        const __half lo = __double2half(v - (double)__half2float(hi));
-        const int off = ((q >> 3) * 16 * 128 + (r >> 3) * 128 + (r & 7) * 16 + (q & 7) * 2) / 2;
-        img[(2 * h) * (kTcMatBytes / 2) + off] = __half_as_ushort(hi);
-        img[(2 * h + 1) * (kTcMatBytes / 2) + off] = __half_as_ushort(lo);
-      }
+  constexpr int half = 128 * 128;  // FP16 values per operand
+  if (n == 255) {
+    put_matrix(img, img + half, [&](int r, int q) {
+      const int kp = r + 1, x = q + 1;
+      return (kp == 128 || x == 128) ? 0.0 : 16.0 * std::sin(pi * (double)((kp * x) % 256) / 128.0);
+    });
+    put_matrix(img + 2 * half, img + 3 * half, [&](int r, int q) {
+      const int x = q + 1;
+      const double v = 16.0 * std::sin(pi * (double)(((2 * r + 1) * x) % 512) / 256.0);
+      return x == 128 ? 0.5 * v : v;
+    });
+  } else if (n == 127) {
+    put_matrix(img, img + half, [&](int r, int q) {
+      const int k = r + 1, x = q + 1;
+      return (k == 128 || x == 128) ? 0.0 : 16.0 * std::sin(pi * (double)((k * x) % 256) / 128.0);
+    });
+  }
 }
 
 cudaError_t launch_dst_tc(const DstTcArgs& a, cudaStream_t st) {
   if (a.lines <= 0) return cudaSuccess;
+  if (!dst_tc_line_ok(a.n)) return cudaErrorInvalidValue;
   // the shared-memory attribute applies to the current device: set on every launch, as the other
   // launchers do; the SM count is queried once per device
   static std::atomic<int> sms[64];
@@ -531,12 +614,17 @@ cudaError_t launch_dst_tc(const DstTcArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     sms[dev].store(n, std::memory_order_relaxed);
   }
-  e = cudaFuncSetAttribute(k_dst255_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+  const bool l255 = a.n == 255;
+  const int smem = l255 ? TcShape<255>::kSmemBytes : TcShape<127>::kSmemBytes;
+  const int per_tile = l255 ? TcShape<255>::kLines : TcShape<127>::kLines;
+  const int threads = l255 ? TcShape<255>::kThreads : TcShape<127>::kThreads;
+  e = cudaFuncSetAttribute(l255 ? k_dst255_tc : k_dst127_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const int tiles = (a.lines + kTcLines - 1) / kTcLines;
+  const int tiles = (a.lines + per_tile - 1) / per_tile;
   const int grid = tiles < n ? tiles : n;
   prof_begin("dst_tc_f32", st);
-  k_dst255_tc<<<grid, kTcThreads, kTcSmemBytes, st>>>(a);
+  if (l255) k_dst255_tc<<<grid, threads, smem, st>>>(a);
+  else k_dst127_tc<<<grid, threads, smem, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
 }

@@ -135,13 +135,15 @@ template <typename T> struct AxisArgs {
 // output of AxisArgs op 0 (Y_k = -2i sum_x X_x sin(pi k x / 256)), in place on `lines`
 // consecutive lines of 255 complex values.
 struct DstTcArgs {
-  float2* S;                               // lines [lines][255] (in place)
-  const void* tab;                         // matrix image, dst_tc_table_bytes() (16-byte aligned)
+  float2* S;                               // lines [lines][n] (in place)
+  const void* tab;                         // matrix image, dst_tc_table_bytes(n) (16-byte aligned)
+  int n;                                   // points per line: 255 or 127 (dst_tc_line_ok)
   int lines;
   int* err;                                // set to 1 if a bounded wait of the kernel gave up
 };
-size_t dst_tc_table_bytes();
-void dst_tc_table(unsigned short* img);    // host: fills the image (dst_tc_table_bytes() / 2 halves)
+inline bool dst_tc_line_ok(int n) { return n == 255 || n == 127; }
+size_t dst_tc_table_bytes(int n);
+void dst_tc_table(int n, unsigned short* img);  // host: fills the image (dst_tc_table_bytes(n) / 2 halves)
 cudaError_t launch_dst_tc(const DstTcArgs& a, cudaStream_t st);
 
 // Toeplitz tridiagonal solve along y (2D, after the x sine transform): for each line (j, p),

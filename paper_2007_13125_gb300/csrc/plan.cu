@@ -470,10 +470,10 @@ void destroy_plan(pint_plan p) {
 namespace {
 pint_status autotune_ysolve(pint_plan p);
 pint_status autotune_xdst(pint_plan p);
-// the tensor-core x sine transform serves lines of 255 points of FP32 inner solves (2D / 3D,
-// Dirichlet finite differences)
+// the tensor-core x sine transform serves lines of 255 or 127 points of FP32 inner solves (2D /
+// 3D, Dirichlet finite differences)
 bool dst_tc_applies(pint_plan p) {
-  return p->mx == 255 && (p->dim == 2 || p->dim == 3) && !p->periodic && !p->fem && p->prec != PINT_FP64;
+  return dst_tc_line_ok(p->mx) && (p->dim == 2 || p->dim == 3) && !p->periodic && !p->fem && p->prec != PINT_FP64;
 }
 pint_status tune_time_tiles(pint_plan p, int cmax_t, int cmax_z);
 pint_status tune_radix(pint_plan p);
@@ -659,19 +659,25 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   PINT_CUDA_B(cudaMemset(p->S, 0, JM * (p->prec == PINT_FP64 ? sizeof(double2) : sizeof(float2))));
   PINT_CUDA_B(cudaMemset(p->ctl, 0, sizeof(SolveCtl)));
   p->xdst = 1;
-  // default (0): the tensor-core transform where it applies and the lines fill the GPU (at least
-  // 16384 lines, ~3.4 tiles of 32 per SM; below that the FFT's four CTAs per SM keep it ahead)
+  // default (0): the tensor-core transform where it applies and there are enough lines to fill
+  // the GPU: at least 16384 lines of 255 points (~3.4 tiles of 32 per SM) or 8192 lines of 127
+  // points (~0.8 tiles of 64 per SM). Measured per launch: below 4096 lines both FFT forms are
+  // ahead (their four CTAs per SM start faster than the tensor-core pipeline fills), from 4096 to
+  // 16384 lines of 255 points the two are within 4%, and from 8192 lines of 127 points on the
+  // tensor cores win (1.2x there, 1.8x at 130K lines in 2D, 2x in 3D)
   const long long xlines = (long long)(N / 2 + 1) * p->my * p->mz;
-  const bool tc_default = d->xdst == 0 && xlines >= 16384;
+  const bool tc_default = d->xdst == 0 && xlines >= (p->mx == 255 ? 16384 : 8192);
   if (dst_tc_applies(p) && (d->xdst >= 2 || tc_default)) {
-    // the matrix image is the same for every plan: built once per process
-    static std::once_flag once;
-    static std::vector<unsigned short> img;
-    std::call_once(once, [] {
-      img.resize(dst_tc_table_bytes() / 2);
-      dst_tc_table(img.data());
+    // the matrix image of a line length is the same for every plan: built once per process
+    static std::once_flag once[2];
+    static std::vector<unsigned short> img[2];
+    const int which = p->mx == 255 ? 0 : 1;
+    std::call_once(once[which], [which] {
+      const int n = which == 0 ? 255 : 127;
+      img[which].resize(dst_tc_table_bytes(n) / 2);
+      dst_tc_table(n, img[which].data());
     });
-    if ((s = upload(p, &p->dst_tab, img)) != PINT_OK) return bail(s);
+    if ((s = upload(p, &p->dst_tab, img[which])) != PINT_OK) return bail(s);
     p->xdst = 2;
     if (d->xdst == 3 && (s = autotune_xdst(p)) != PINT_OK) return bail(s);
   }
@@ -867,12 +873,13 @@ void split_ff(double x, float& hi, float& lo) {
 template <typename T> bool ysolve_tri(pint_plan p) { return sizeof(T) == 4 && (p->ysolve == 2 || p->ysolve == 4); }
 
 // x sine transform (AxisArgs op 0) of `lines` lines: the odd-sequence FFT, or for FP32 lines of
-// 255 points on a plan that selected it, the tensor-core products
+// 255 or 127 points on a plan that selected it, the tensor-core products
 template <typename T> cudaError_t xform_x(pint_plan p, const AxisArgs<T>& ax, cudaStream_t st) {
   if (sizeof(T) == 4 && p->xdst == 2) {
     DstTcArgs g{};
     g.S = reinterpret_cast<float2*>(ax.S);
     g.tab = p->dst_tab;
+    g.n = p->mx;
     g.lines = ax.lines;
     g.err = &p->ctl->err;
     return launch_dst_tc(g, st);
@@ -985,7 +992,7 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
 pint_status autotune_xdst(pint_plan p) {
   static std::mutex mu;
   static std::vector<std::pair<long long, int>> cache;
-  const long long key = (((long long)p->N * 4096 + p->my) * 4096 + p->mz) * 4 + p->dim;
+  const long long key = ((((long long)p->N * 4096 + p->mx) * 4096 + p->my) * 4096 + p->mz) * 4 + p->dim;
   {
     std::lock_guard<std::mutex> lk(mu);
     for (auto& kv : cache)
@@ -1613,7 +1620,7 @@ size_t pint::plan_bytes_estimate(const pint_plan_desc* d) {
   else b += 16 * JM;
   if (d->alpha != 1.0) b += 8 * NM;
   b += 64 * (N + d->grid.mx + d->grid.my) + 65536;  // tables, alignment slack
-  if (d->xdst != 1 && d->grid.mx == 255 && d->grid.dim >= 2) b += dst_tc_table_bytes();
+  if (d->xdst != 1 && dst_tc_line_ok(d->grid.mx) && d->grid.dim >= 2) b += dst_tc_table_bytes(d->grid.mx);
   return b;
 }
 

@@ -1,8 +1,8 @@
-"""The tensor-core form of the x sine transform (lines of 255 points) written out in numpy: the
-folded sine matrices, the FP16 splitting with the per-line power-of-two scale, the three products
-per term, and the -2i output convention, checked against the sine transform computed directly.
-No GPU is involved; the CUDA kernel itself is compared with the FFT form and the oracle in the GPU
-tests (tests/test_gpu_dst_tc.py).
+"""The tensor-core form of the x sine transform (lines of 255 and of 127 points) written out in
+numpy: the folded sine matrices (255) or the padded 128 x 128 matrix (127), the FP16 splitting with
+the per-line power-of-two scale, the three products per term, and the -2i output convention,
+checked against the sine transform computed directly. No GPU is involved; the CUDA kernels
+themselves are compared with the FFT form and the oracle in the GPU tests (tests/test_gpu_dst_tc.py).
 
 The transform of a line X_1..X_255 is Y_k = -2i sum_x X_x sin(pi k x / 256), k = 1..255 (the
 output of the odd-extension FFT). With e_x = X_x - X_{256-x} and o_x = X_x + X_{256-x}:
@@ -151,3 +151,77 @@ def test_bf16_pieces_are_not_enough(pieces):
     z = eh @ mh.T + eh @ ml.T + el @ mh.T
     ref = e.astype(np.float64) @ even.T
     assert np.linalg.norm(z - ref) > 1e-6 * np.linalg.norm(ref)
+
+
+# ---- lines of 127 points: the sine matrix itself, padded to 128 x 128 (no fold) ----
+N127 = 127
+
+
+def direct127(X):
+    x = np.arange(1, N127 + 1)
+    S = np.sin(np.pi * np.outer(x, x) / (N127 + 1))
+    return -2j * (X @ S.T)
+
+
+def matrix127():
+    """16 sin(pi k x / 128) for k, x = 1..127, row 128 and column 128 zero (row = k - 1, column = x - 1)."""
+    k = np.arange(1, 129)[:, None]
+    x = np.arange(1, 129)[None, :]
+    S = 16.0 * np.sin(np.pi * ((k * x) % 256) / 128.0)
+    S[127, :] = 0.0
+    S[:, 127] = 0.0
+    return S
+
+
+def tensor_core_form127(X):
+    S = matrix127()
+    sc, sh = line_scale(X.astype(np.complex64))
+    B = np.zeros((X.shape[0], 128), dtype=np.complex64)
+    B[:, :N127] = X.astype(np.complex64)                  # the padding input x = 128 is zero
+    re = products((B.real * sc[:, None]).astype(np.float32), S)
+    im = products((B.imag * sc[:, None]).astype(np.float32), S)
+    z = (re + 1j * im) / (16.0 * np.ldexp(1.0, sh))[:, None]
+    return (-2j * z)[:, :N127]                            # output k = row + 1; row 128 is zero
+
+
+def lines127(rng, n=24):
+    X = rng.standard_normal((n, N127)) + 1j * rng.standard_normal((n, N127))
+    X *= np.exp(rng.uniform(-30, 30, size=(n, 1)))
+    X[2] = 0.0
+    X[7, :-1] = 0.0                                       # only the last point (x = 127) nonzero
+    return X
+
+
+def test_padded_127_matrix_is_the_sine_transform_exactly():
+    rng = np.random.default_rng(5)
+    X = lines127(rng)
+    S = matrix127()
+    B = np.zeros((X.shape[0], 128), dtype=np.complex128)
+    B[:, :N127] = X
+    out = (-2j * (B @ S.T) / 16.0)[:, :N127]
+    ref = direct127(X)
+    assert np.max(np.abs(out - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.all(S[127] == 0.0) and np.all(S[:, 127] == 0.0)
+
+
+def test_split_products_127_reach_fp32_accuracy_per_line():
+    rng = np.random.default_rng(6)
+    X = lines127(rng).astype(np.complex64)
+    got = tensor_core_form127(X)
+    ref = direct127(X.astype(np.complex128))
+    for i in range(X.shape[0]):
+        nrm = np.linalg.norm(ref[i])
+        if nrm == 0.0:
+            assert np.all(got[i] == 0.0)
+            continue
+        assert np.linalg.norm(got[i] - ref[i]) <= 5e-7 * nrm, i
+
+
+def test_127_transform_applied_twice_is_the_scaled_identity():
+    """DST-I is its own inverse up to (n + 1) / 2: with the -2i convention, two transforms give
+    -2 (n + 1) X = -256 X (the factor the 3D and 2D divisors account for)."""
+    rng = np.random.default_rng(7)
+    X = (rng.standard_normal((6, N127)) + 1j * rng.standard_normal((6, N127))).astype(np.complex64)
+    Y = tensor_core_form127(X)
+    Z = tensor_core_form127(Y.astype(np.complex64))
+    assert np.linalg.norm(Z + 256.0 * X) <= 1e-6 * 256.0 * np.linalg.norm(X)

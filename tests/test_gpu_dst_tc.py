@@ -1,11 +1,12 @@
-"""The x sine transform as tensor-core products (tcgen05; xdst = 2) against the odd-sequence FFT
-(xdst = 1) and the oracle.
+"""The x sine transform as tensor-core products (tcgen05; xdst = 2; lines of 255 points folded,
+lines of 127 points unfolded) against the odd-sequence FFT (xdst = 1) and the oracle.
 
 Both compute the x-direction step of the shifted spatial solves (Algorithm 1 / 2, step 2: A is
 diagonal on the sine modes, Sec. 2.2) in FP32-class arithmetic, so one sweep from U = 0 (one
 application of P^-1 to F_hat) agrees to the FP32 inner-solve level, and a solve reaches the oracle's
 solution to the mixed path's bar with the same number of sweeps. Line counts cover one partial
-tile, odd and even last tiles, ragged tails over many tiles, 3D and both FP32 precisions."""
+tile, odd and even last tiles, ragged tails over many tiles, 3D and both FP32 precisions, for both
+line lengths (tiles of 32 lines of 255 points, of 64 lines of 127 points)."""
 import numpy as np
 import pytest
 
@@ -51,6 +52,10 @@ CASES = [
     ("2d_255x3_N10", dict(dim=2, mx=255, my=3, N=10, k=3)),         # 18 lines: one partial tile, even
     ("2d_255x15_N64", dict(dim=2, mx=255, my=15, N=64, k=4)),       # 495 lines: 15 tiles + 15
     ("2d_255x255_N16", dict(dim=2, mx=255, my=255, N=16, k=4, kappa=0.05)),  # 2295: 71 tiles + 23
+    ("2d_127x3_N8", dict(dim=2, mx=127, my=3, N=8, k=2)),           # 15 lines of 127: one partial tile
+    ("2d_127x3_N10", dict(dim=2, mx=127, my=3, N=10, k=3)),         # 18: one partial tile, even
+    ("2d_127x31_N64", dict(dim=2, mx=127, my=31, N=64, k=4)),       # 1023: 15 tiles of 64 + 63
+    ("2d_127x127_N32", dict(dim=2, mx=127, my=127, N=32, k=4, kappa=0.05)),  # 2159: 33 tiles + 47
 ]
 
 
@@ -67,18 +72,20 @@ def test_sweep_matches_fft_transform(name, kw, precision):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp32"])
-def test_sweep_matches_fft_transform_3d(precision):
+@pytest.mark.parametrize("m", [255, 127])
+def test_sweep_matches_fft_transform_3d(m, precision):
     torch = torch_cuda()
-    p = workloads.heat3d_problem(m=255, N=16, my=7, mz=3)            # 189 lines: 5 tiles + 29
+    p = workloads.heat3d_problem(m=m, N=16, my=7, mz=3)   # 189 lines: 5 tiles of 32 + 29, 2 of 64 + 61
     u1, a = _sweep(p, torch, precision, 1)
     u2, b = _sweep(p, torch, precision, 2)
     assert (u1, u2) == (1, 2)
     assert rel_l2(b, a) <= SWEEP_BAR
 
 
-def test_solve_reaches_the_oracle_with_the_same_sweeps():
+@pytest.mark.parametrize("n,N", [(255, 32), (127, 64)])
+def test_solve_reaches_the_oracle_with_the_same_sweeps(n, N):
     torch = torch_cuda()
-    p = workloads.small_problem(dim=2, mx=255, my=255, N=32, k=4, kappa=0.05)
+    p = workloads.small_problem(dim=2, mx=n, my=n, N=N, k=4, kappa=0.05)
     ref = oracle_solution(p)
     _, Ua, sta, swa = _solve(p, torch, 1)
     _, Ub, stb, swb = _solve(p, torch, 2)
@@ -107,11 +114,23 @@ def test_variant_selection():
     torch_cuda()
     from paper_2007_13125_gb300 import Plan
     small = workloads.small_problem(dim=2, mx=255, my=255, N=16, k=2)    # 2295 lines: FFT by default
-    other = workloads.small_problem(dim=2, mx=127, my=127, N=64, k=2)    # lines of 127 points
+    l127 = workloads.small_problem(dim=2, mx=127, my=127, N=64, k=2)     # 4191 lines of 127: FFT by default
+    big127 = workloads.small_problem(dim=2, mx=127, my=127, N=128, k=2)  # 8255 lines: tensor cores
+    other = workloads.small_problem(dim=2, mx=63, my=63, N=64, k=2)      # lines of 63 points
     with Plan.for_problem(small, "mixed") as plan:
         assert plan.tuning()["xdst"] == 1
     with Plan.for_problem(small, "fp64", xdst=2) as plan:                 # FP64 inner solves
         assert plan.tuning()["xdst"] == 1
+    with Plan.for_problem(l127, "mixed") as plan:
+        assert plan.tuning()["xdst"] == 1
+    with Plan.for_problem(l127, "mixed", xdst=2) as plan:
+        assert plan.tuning()["xdst"] == 2
+    with Plan.for_problem(big127, "mixed") as plan:
+        assert plan.tuning()["xdst"] == 2
+    with Plan.for_problem(workloads.heat3d_problem(m=127, my=7, mz=15, N=64), "mixed") as plan:   # 33 x 105 lines
+        assert plan.tuning()["xdst"] == 1
+    with Plan.for_problem(workloads.heat3d_problem(m=127, my=15, mz=31, N=64), "fp32") as plan:   # 33 x 465
+        assert plan.tuning()["xdst"] == 2
     with Plan.for_problem(other, "mixed", xdst=2) as plan:
         assert plan.tuning()["xdst"] == 1
     with Plan.for_problem(workloads.c2_heat2d(), "mixed", xdst=3) as plan:   # timed choice
@@ -146,8 +165,9 @@ def test_tensor_core_plans_in_a_batch_graph_beside_fft_plans():
     probs = [workloads.small_problem(dim=2, mx=255, my=255, N=16, k=2, kappa=0.1, seed=61),
              workloads.small_problem(dim=2, mx=255, my=127, N=32, k=4, kappa=0.05, seed=62),
              workloads.small_problem(dim=2, mx=63, my=63, N=64, k=3, kappa=0.1, seed=63),
-             workloads.small_problem(dim=1, mx=255, N=128, k=2, alpha=0.6, kappa=0.1, seed=64)]
-    xdst = [2, 2, 0, 0]
+             workloads.small_problem(dim=1, mx=255, N=128, k=2, alpha=0.6, kappa=0.1, seed=64),
+             workloads.small_problem(dim=2, mx=127, my=127, N=32, k=3, kappa=0.1, seed=65)]
+    xdst = [2, 2, 0, 0, 2]
     plans, Fs, Us = [], [], []
     for p, x in zip(probs, xdst):
         pl = Plan.for_problem(p, "mixed", xdst=x)
@@ -157,7 +177,7 @@ def test_tensor_core_plans_in_a_batch_graph_beside_fft_plans():
         pl.form_rhs(v, f, fd, F)
         pl.initial_guess(v, U)
         plans.append(pl); Fs.append(F); Us.append(U)
-    assert [pl.tuning()["xdst"] for pl in plans] == [2, 2, 1, 1]
+    assert [pl.tuning()["xdst"] for pl in plans] == [2, 2, 1, 1, 2]
     st, sweeps, upd = pint.batch_solve(plans, Fs, Us, tol=1e-10)
     for p, U, s in zip(probs, Us, sweeps):
         assert rel_l2(U.cpu().numpy(), oracle_solution(p)) <= 1e-8, (p.name, s)
