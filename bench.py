@@ -48,6 +48,7 @@ def algo_bytes(name: str, N: int, M: int, K: int = 1) -> float:
         "inv_update_ff": 8 * JM + 16 * NM,      # read spectrum; read + write U (double-float)
         "dst_f32": 16 * JM,                     # read + write spectrum (complex float)
         "dst_tc_f32": 16 * JM,                  # the same transform as tensor-core products
+        "dst_tc_y_f32": 16 * JM,                # the y transform of 3D grids, the same way
         "axis_solve_f32": 16 * JM,
         "rhs_f64": 16 * NM,                     # read f, write F_hat
         "rhs_head_f64": 16 * K * M,             # F_hat's first k levels: read f, write

@@ -132,7 +132,9 @@ typedef struct {
                              are at least 16384 of them ((N/2 + 1) my mz), or 127 points and at
                              least 8192 of them, else 1. PINT_FP64 plans use 1. The tensor-core
                              form holds 128 KB (255 points) or 64 KB (127 points) of tables on the
-                             device. */
+                             device. The y-direction transforms of 3D grids with my = 127 follow
+                             the same switch (tensor cores for 2, and for 0 and 3 from 8192 lines
+                             (N/2 + 1) mx mz; 64 KB more of tables; pint_plan_tuning out[8]). */
 } pint_plan_desc;
 
 /* Build a plan: FP64 constant tables (BDF / CQ weights omega_j of eq. (2.2) / eq. (3.2) --
@@ -292,8 +294,8 @@ pint_status pint_solve_host_join(pint_plan plan, void* stream);
  * 4 parallel cyclic reduction), out[4] / out[5] largest FFT radix of the residual / update time
  * transforms (16 for the compiled shapes; 8 or 16 as timed for runtime shapes; 0 when not MIXED),
  * out[6] 1 if the whole solve runs as one CTA, out[7] x sine transform of the FP32 inner solves
- * (1 odd-sequence FFT, 2 tensor-core products). Fills min(n, 8) entries and returns 8 (-1 for a
- * NULL plan or out). Host-only. */
+ * (1 odd-sequence FFT, 2 tensor-core products), out[8] y sine transform of 3D plans (the same
+ * codes). Fills min(n, 9) entries and returns 9 (-1 for a NULL plan or out). Host-only. */
 int pint_plan_tuning(pint_plan plan, int* out, int n);
 
 /* Outcome of the plan's most recent graph-launched solve: sweeps, final relative update, and

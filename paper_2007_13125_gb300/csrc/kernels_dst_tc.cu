@@ -1,5 +1,5 @@
-// Sine transform along x of lines of n = 255 or n = 127 points as tensor-core products (tcgen05,
-// sm_103a).
+// Sine transform along x of lines of n = 255 or n = 127 points (and along y of 3D grids with
+// my = 127) as tensor-core products (tcgen05, sm_103a).
 //
 // The x-direction step of the shifted spatial solves (Algorithm 1 / 2, step 2: A is diagonal on
 // the sine modes, Sec. 2.2) transforms every line of the half spectrum,
@@ -15,6 +15,9 @@
 //     complex lines per tile).
 //   * n = 127 (k_dst127_tc): the 127 x 127 matrix itself, padded with a zero row and column, is one
 //     128 x 128 operand; no fold. N = 128 real rows (64 complex lines per tile).
+//   * n = 127, strided lines (k_dst127s_tc): the y-direction transforms of 3D grids (my = 127),
+//     whose lines are the columns of the (j, z) planes of my rows x mx points; a tile is up to 64
+//     consecutive columns of one plane, read and written row by row (contiguous along x).
 //
 // Precision: FP16 operands split in two (v = hi + lo: hi of 11 significant bits by Veltkamp's
 // splitting, lo = v - hi), three products per term (hi hi + hi lo + lo hi, FP32 accumulation in
@@ -27,8 +30,9 @@
 // of its shared memory):
 //   * load warp: one thread copies each tile's lines (contiguous, ~65 KB) into a raw buffer with
 //     bulk asynchronous copies (cp.async.bulk, complete_tx on a shared-memory barrier), as soon as
-//     the staging threads have taken the previous tile out of it;
-//   * 8 staging warps: read their share of the raw tile into registers (then release the buffer),
+//     the staging threads have taken the previous tile out of it (strided lines: idle);
+//   * 8 staging warps: read their share of the raw tile into registers (then release the buffer;
+//     strided lines: straight from global memory, coalesced along the rows),
 //     reduce each line's largest magnitude, (fold,) scale and split the lines into K-chunks of 32
 //     inputs in the canonical K-major layout (8-row x 16-byte core matrices, no swizzle) in a ring
 //     of two stage slots, and signal each chunk on the slot's "full" barrier; after staging a tile
@@ -79,8 +83,14 @@ template <int P> struct TcShape {
   static constexpr int kSlots = 2;                        // stage slots (ring of K-chunks)
   static constexpr int kLineBytes = P * 8;                // one line of complex FP32 values
   static constexpr int kRawOff = kABytes + kSlots * kStageBytes;  // the tile's lines as read
-  static constexpr int kMiscOff = kRawOff + 65536;
-  static constexpr int kMiscBytes = 2048;
+  // strided lines (P = 127): the raw buffer, unused for its lines, holds the tile's outputs on
+  // their way to global memory, P rows of up to kLines columns (pitch kOutPitch float2). (The
+  // smaller the shared memory, the larger the L1 that the strided kernel's global loads go through.)
+  static constexpr int kOutPitch = kLines + 1;
+  static constexpr int kRawBytes = kFold ? 65536 : ((P * kOutPitch * 8 + 15) / 16) * 16;
+  static constexpr int kOutOff = kRawOff;
+  static constexpr int kMiscOff = kRawOff + kRawBytes;
+  static constexpr int kMiscBytes = kFold ? 2048 : 1664;
   static constexpr int kSmemBytes = kMiscOff + kMiscBytes;
   static constexpr int kTmemCols = 256;                   // two accumulator buffers of 128 columns
   // instruction descriptor (kind::f16): D FP32 (bits 4-5 = 1), A and B FP16 (formats 0), both
@@ -88,7 +98,7 @@ template <int P> struct TcShape {
   static constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   static_assert(kItems * kStageThreads == kLines * 16, "items");
   static_assert(kStageBytes == 16384, "stage");
-  static_assert(kLines * kLineBytes <= 65536, "raw tile");
+  static_assert(kLines * kLineBytes <= kRawBytes, "raw tile");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 };
 
@@ -204,9 +214,13 @@ __device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-// the whole kernel for lines of P points (launched by k_dst255_tc / k_dst127_tc)
-template <int P> __device__ __forceinline__ void dst_tc_body(const DstTcArgs& a) {
+// the whole kernel for lines of P points (launched by k_dst255_tc / k_dst127_tc / k_dst127s_tc).
+// STRIDED (P = 127): the lines are the columns of planes of P rows (a.stride points per row); a
+// tile is up to 64 consecutive columns of one plane, which the staging warps read straight from
+// global memory (each row's columns are contiguous) instead of through the load warp's raw buffer.
+template <int P, bool STRIDED> __device__ __forceinline__ void dst_tc_body(const DstTcArgs& a) {
   using S = TcShape<P>;
+  static_assert(!STRIDED || P == 127, "strided lines: 127 points");
   constexpr int kLines = S::kLines, kN = S::kN, kChunk = S::kChunk, kChunks = S::kChunks;
   constexpr int kStageThreads = S::kStageThreads, kItems = S::kItems, kVals = S::kVals;
   constexpr int kLinesPerWarp = S::kLinesPerWarp, kMatBytes = S::kMatBytes, kABytes = S::kABytes;
@@ -215,8 +229,30 @@ template <int P> __device__ __forceinline__ void dst_tc_body(const DstTcArgs& a)
   TcMisc<P>& ms = *reinterpret_cast<TcMisc<P>*>(smem + S::kMiscOff);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t sA = smem_u32(smem), sB = sA + kABytes;
-  const int tiles = (a.lines + kLines - 1) / kLines;
+  // strided: tiles per plane and the tile count (lines = planes * stride)
+  const int tpp = STRIDED ? (a.stride + kLines - 1) / kLines : 1;
+  const int tiles = STRIDED ? (a.lines / a.stride) * tpp : (a.lines + kLines - 1) / kLines;
   const uint32_t* abort = reinterpret_cast<const uint32_t*>(&ms.abort);
+  // tile tt: its first element, the element steps between lines (ls) and between points (ps) of a
+  // line, and its number of lines
+  struct TileGeo { float2* base; size_t ls, ps; int nl; };
+  auto geo = [&](int tt) -> TileGeo {
+    TileGeo g;
+    if constexpr (STRIDED) {
+      const int q = tt / tpp, x0 = (tt - q * tpp) * kLines;
+      g.base = a.S + (size_t)q * P * a.stride + x0;
+      g.ls = 1;
+      g.ps = (size_t)a.stride;
+      g.nl = a.stride - x0 < kLines ? a.stride - x0 : kLines;
+    } else {
+      const long long first = (long long)tt * kLines;
+      g.base = a.S + first * P;
+      g.ls = P;
+      g.ps = 1;
+      g.nl = (int)(a.lines - first < kLines ? a.lines - first : kLines);
+    }
+    return g;
+  };
 
   if (tid == 0) {
     auto init = [](unsigned long long* b, int count) {
@@ -311,8 +347,8 @@ template <int P> __device__ __forceinline__ void dst_tc_body(const DstTcArgs& a)
     }
   } else if (warp == kStageThreads / 32 + 1) {
     // ---- load warp: one thread copies each tile's lines (contiguous) into the raw buffer as soon
-    // as the staging threads have read the previous tile's out of it ----
-    if (lane == 0) {
+    // as the staging threads have read the previous tile's out of it (idle for strided lines) ----
+    if (!STRIDED && lane == 0) {
       const uint32_t rf = smem_u32(&ms.raw_full), sraw = sA + S::kRawOff;
       bool ok = true;
       int i = 0;
@@ -424,45 +460,93 @@ template <int P> __device__ __forceinline__ void dst_tc_body(const DstTcArgs& a)
             tc_before_sync();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.acc_empty[b2])) : "memory");
           }
-          if (!*reinterpret_cast<volatile uint32_t*>(&ms.abort) && m < P) {
+          if constexpr (STRIDED) {
+            // output index m of the 8 lines into the transposition buffer (row m, column lu)
+            if (m < P) {
+              float2* so = reinterpret_cast<float2*>(smem + S::kOutOff) + m * S::kOutPitch + l0 + h8;
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const float us = ms.unscale[b2][l0 + h8 + u];
+                so[u] = make_float2(im[u] * us, -re[u] * us);
+              }
+            }
+          } else if (!*reinterpret_cast<volatile uint32_t*>(&ms.abort) && m < P) {
+            const TileGeo g = geo(tj);
+            float2* out = g.base + (size_t)m * g.ps;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               const int lu = l0 + h8 + u;
-              const long long line = (long long)tj * kLines + lu;
-              if (line >= a.lines) break;
+              if (lu >= g.nl) break;
               const float us = ms.unscale[b2][lu];
               // output index m: k = m + 1; -2i z = (2 Im z, -2 Re z)
-              a.S[line * P + m] = make_float2(im[u] * us, -re[u] * us);
+              out[(size_t)lu * g.ls] = make_float2(im[u] * us, -re[u] * us);
             }
           }
         }
       }
-    };
-    int i = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
-      const int b2 = i & 1;
-      // the tile's inputs, from the raw buffer into registers; then the buffer is released
-      if (!bar_wait(smem_u32(&ms.raw_full), (uint32_t)(i & 1), abort)) atomicExch(&ms.abort, 1u);
-      float2 in[kItems][kChunks][kVals];
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        const bool okl = (long long)t * kLines + il[j] < a.lines;
-        const float2* row = raw + il[j] * P;
-#pragma unroll
-        for (int c = 0; c < kChunks; ++c) {
-          const int x = c * kChunk + ikl[j] + 1;
-          const float2 z = make_float2(0.f, 0.f);
-          in[j][c][0] = okl ? row[x - 1] : z;
-          if constexpr (S::kFold) {
-            in[j][c][1] = okl ? row[x] : z;
-            in[j][c][2] = okl ? row[255 - x] : z;
-            in[j][c][3] = okl ? row[254 - x] : z;
-          } else {
-            in[j][c][1] = (okl && x < P) ? row[x] : z;  // x + 1 = 128: the zero padding
+      if constexpr (STRIDED) {
+        // the buffer complete (the staging threads only), then row by row to global memory: a
+        // warp stores 32 consecutive columns of a row. (The next tile's writes into the buffer
+        // follow the staging threads' barrier of the next tile.)
+        asm volatile("bar.sync 2, %0;" ::"r"(kStageThreads) : "memory");
+        if (!*reinterpret_cast<volatile uint32_t*>(&ms.abort)) {
+          const TileGeo g = geo(tj);
+          const float2* so = reinterpret_cast<const float2*>(smem + S::kOutOff);
+          for (int idx = tid; idx < P * kLines; idx += kStageThreads) {
+            const int r = idx / kLines, col = idx - r * kLines;
+            if (col < g.nl) g.base[(size_t)r * g.ps + col] = so[r * S::kOutPitch + col];
           }
         }
       }
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.raw_empty)) : "memory");
+    };
+    // strided lines: a tile's inputs straight from global memory into registers, point x of line
+    // l at base[(x - 1) ps + l] (a warp's lanes read 8 consecutive columns of 4 rows); issued one
+    // tile ahead, so that they are in flight during the previous tile's epilogue
+    float2 in[kItems][kChunks][kVals];
+    auto load_strided = [&](int tt) {
+      if constexpr (STRIDED) {
+        const TileGeo g = geo(tt);
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+          const bool okl = il[j] < g.nl;
+          const float2* col = g.base + il[j];
+#pragma unroll
+          for (int c = 0; c < kChunks; ++c) {
+            const int x = c * kChunk + ikl[j] + 1;
+            const float2 z = make_float2(0.f, 0.f);
+            in[j][c][0] = okl ? col[(size_t)(x - 1) * g.ps] : z;
+            in[j][c][1] = (okl && x < P) ? col[(size_t)x * g.ps] : z;  // x + 1 = 128: the zero padding
+          }
+        }
+      }
+    };
+    if (STRIDED && blockIdx.x < tiles) load_strided(blockIdx.x);
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+      const int b2 = i & 1;
+      if constexpr (!STRIDED) {
+        // the tile's inputs, from the raw buffer into registers; then the buffer is released
+        if (!bar_wait(smem_u32(&ms.raw_full), (uint32_t)(i & 1), abort)) atomicExch(&ms.abort, 1u);
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+          const bool okl = (long long)t * kLines + il[j] < a.lines;
+          const float2* row = raw + il[j] * P;
+#pragma unroll
+          for (int c = 0; c < kChunks; ++c) {
+            const int x = c * kChunk + ikl[j] + 1;
+            const float2 z = make_float2(0.f, 0.f);
+            in[j][c][0] = okl ? row[x - 1] : z;
+            if constexpr (S::kFold) {
+              in[j][c][1] = okl ? row[x] : z;
+              in[j][c][2] = okl ? row[255 - x] : z;
+              in[j][c][3] = okl ? row[254 - x] : z;
+            } else {
+              in[j][c][1] = (okl && x < P) ? row[x] : z;  // x + 1 = 128: the zero padding
+            }
+          }
+        }
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.raw_empty)) : "memory");
+      }
       // largest |re|, |im| of each line: over the item, its four lanes (q), the four warps
       // holding the line's groups (g8)
 #pragma unroll
@@ -532,10 +616,15 @@ template <int P> __device__ __forceinline__ void dst_tc_body(const DstTcArgs& a)
         fence_async_smem();
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.full[c & 1])) : "memory");
       }
+      // strided lines: the next tile's loads (the registers are free again)
+      if (STRIDED && t + (int)gridDim.x < tiles) load_strided(t + (int)gridDim.x);
       // the previous tile's epilogue runs now, while this tile's MMAs execute
       if (i >= 1) epilogue(i - 1, t - (int)gridDim.x);
     }
-    if (i >= 1 && !*reinterpret_cast<volatile uint32_t*>(&ms.abort)) epilogue(i - 1, blockIdx.x + (i - 1) * (int)gridDim.x);
+    // the last tile's epilogue, decided once for all staging threads (the strided epilogue holds a
+    // barrier of theirs)
+    const bool stop = ssync_abort();
+    if (i >= 1 && !stop) epilogue(i - 1, blockIdx.x + (i - 1) * (int)gridDim.x);
     if (tid == 0 && *reinterpret_cast<volatile uint32_t*>(&ms.abort)) atomicExch(a.err, 1);
   }
   tc_before_sync();
@@ -546,8 +635,9 @@ template <int P> __device__ __forceinline__ void dst_tc_body(const DstTcArgs& a)
   }
 }
 
-__global__ void __launch_bounds__(TcShape<255>::kThreads, 1) k_dst255_tc(DstTcArgs a) { dst_tc_body<255>(a); }
-__global__ void __launch_bounds__(TcShape<127>::kThreads, 1) k_dst127_tc(DstTcArgs a) { dst_tc_body<127>(a); }
+__global__ void __launch_bounds__(TcShape<255>::kThreads, 1) k_dst255_tc(DstTcArgs a) { dst_tc_body<255, false>(a); }
+__global__ void __launch_bounds__(TcShape<127>::kThreads, 1) k_dst127_tc(DstTcArgs a) { dst_tc_body<127, false>(a); }
+__global__ void __launch_bounds__(TcShape<127>::kThreads, 1) k_dst127s_tc(DstTcArgs a) { dst_tc_body<127, true>(a); }
 
 // One FP16 operand pair (hi, lo) of a 128 x 128 matrix v(r, q) in its K-major shared-memory layout.
 template <typename F> void put_matrix(unsigned short* hi_img, unsigned short* lo_img, F v) {
@@ -600,7 +690,9 @@ void dst_tc_table(int n, unsigned short* img) {
 
 cudaError_t launch_dst_tc(const DstTcArgs& a, cudaStream_t st) {
   if (a.lines <= 0) return cudaSuccess;
-  if (!dst_tc_line_ok(a.n)) return cudaErrorInvalidValue;
+  if (!dst_tc_line_ok(a.n) || a.stride < 1) return cudaErrorInvalidValue;
+  const bool strided = a.stride > 1;
+  if (strided && (a.n != 127 || a.lines % a.stride != 0)) return cudaErrorInvalidValue;
   // the shared-memory attribute applies to the current device: set on every launch, as the other
   // launchers do; the SM count is queried once per device
   static std::atomic<int> sms[64];
@@ -618,13 +710,14 @@ cudaError_t launch_dst_tc(const DstTcArgs& a, cudaStream_t st) {
   const int smem = l255 ? TcShape<255>::kSmemBytes : TcShape<127>::kSmemBytes;
   const int per_tile = l255 ? TcShape<255>::kLines : TcShape<127>::kLines;
   const int threads = l255 ? TcShape<255>::kThreads : TcShape<127>::kThreads;
-  e = cudaFuncSetAttribute(l255 ? k_dst255_tc : k_dst127_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  auto* kern = l255 ? k_dst255_tc : (strided ? k_dst127s_tc : k_dst127_tc);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const int tiles = (a.lines + per_tile - 1) / per_tile;
-  const int grid = tiles < n ? tiles : n;
-  prof_begin("dst_tc_f32", st);
-  if (l255) k_dst255_tc<<<grid, threads, smem, st>>>(a);
-  else k_dst127_tc<<<grid, threads, smem, st>>>(a);
+  const long long tiles = strided ? (long long)(a.lines / a.stride) * ((a.stride + per_tile - 1) / per_tile)
+                                  : (a.lines + per_tile - 1) / per_tile;
+  const int grid = tiles < n ? (int)tiles : n;
+  prof_begin(strided ? "dst_tc_y_f32" : "dst_tc_f32", st);
+  kern<<<grid, threads, smem, st>>>(a);
   prof_end(st);
   return cudaGetLastError();
 }

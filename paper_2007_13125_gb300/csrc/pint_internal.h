@@ -135,10 +135,14 @@ template <typename T> struct AxisArgs {
 // output of AxisArgs op 0 (Y_k = -2i sum_x X_x sin(pi k x / 256)), in place on `lines`
 // consecutive lines of 255 complex values.
 struct DstTcArgs {
-  float2* S;                               // lines [lines][n] (in place)
+  float2* S;                               // the lines (in place)
   const void* tab;                         // matrix image, dst_tc_table_bytes(n) (16-byte aligned)
   int n;                                   // points per line: 255 or 127 (dst_tc_line_ok)
   int lines;
+  // 1: lines stored one after another ([lines][n]); > 1 (n = 127 only): point i of line
+  // l = q * stride + x at S[(q * n + i) * stride + x], i.e. planes of n rows of `stride` points, a
+  // line per column (lines = planes * stride)
+  int stride;
   int* err;                                // set to 1 if a bounded wait of the kernel gave up
 };
 inline bool dst_tc_line_ok(int n) { return n == 255 || n == 127; }

@@ -475,6 +475,23 @@ pint_status autotune_xdst(pint_plan p);
 bool dst_tc_applies(pint_plan p) {
   return dst_tc_line_ok(p->mx) && (p->dim == 2 || p->dim == 3) && !p->periodic && !p->fem && p->prec != PINT_FP64;
 }
+// ... and the y sine transforms of 3D grids with lines of 127 points (strided: the columns of
+// the (j, z) planes)
+bool dst_tc_y_applies(pint_plan p) {
+  return p->dim == 3 && p->my == 127 && !p->periodic && !p->fem && p->prec != PINT_FP64;
+}
+// the matrix image of a line length (255 or 127), built once per process
+const std::vector<unsigned short>& dst_tc_image(int n) {
+  static std::once_flag once[2];
+  static std::vector<unsigned short> img[2];
+  const int which = n == 255 ? 0 : 1;
+  std::call_once(once[which], [which] {
+    const int len = which == 0 ? 255 : 127;
+    img[which].resize(dst_tc_table_bytes(len) / 2);
+    dst_tc_table(len, img[which].data());
+  });
+  return img[which];
+}
 pint_status tune_time_tiles(pint_plan p, int cmax_t, int cmax_z);
 pint_status tune_radix(pint_plan p);
 }
@@ -668,18 +685,17 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
   const long long xlines = (long long)(N / 2 + 1) * p->my * p->mz;
   const bool tc_default = d->xdst == 0 && xlines >= (p->mx == 255 ? 16384 : 8192);
   if (dst_tc_applies(p) && (d->xdst >= 2 || tc_default)) {
-    // the matrix image of a line length is the same for every plan: built once per process
-    static std::once_flag once[2];
-    static std::vector<unsigned short> img[2];
-    const int which = p->mx == 255 ? 0 : 1;
-    std::call_once(once[which], [which] {
-      const int n = which == 0 ? 255 : 127;
-      img[which].resize(dst_tc_table_bytes(n) / 2);
-      dst_tc_table(n, img[which].data());
-    });
-    if ((s = upload(p, &p->dst_tab, img[which])) != PINT_OK) return bail(s);
+    if ((s = upload(p, &p->dst_tab, dst_tc_image(p->mx))) != PINT_OK) return bail(s);
     p->xdst = 2;
     if (d->xdst == 3 && (s = autotune_xdst(p)) != PINT_OK) return bail(s);
+  }
+  // the y transforms of 3D grids (my = 127) on the tensor cores under the same switch: 2 always,
+  // 0 and 3 from 8192 lines ((N/2 + 1) mx mz), 1 never
+  p->ydst = 1;
+  const long long ylines = (long long)(N / 2 + 1) * p->mx * p->mz;
+  if (dst_tc_y_applies(p) && d->xdst != 1 && (d->xdst == 2 || ylines >= 8192)) {
+    if ((s = upload(p, &p->dst_tab_y, dst_tc_image(127))) != PINT_OK) return bail(s);
+    p->ydst = 2;
   }
   p->ysolve = 1;
   if (p->dim == 2 && p->prec != PINT_FP64 && !p->periodic) {
@@ -881,10 +897,27 @@ template <typename T> cudaError_t xform_x(pint_plan p, const AxisArgs<T>& ax, cu
     g.tab = p->dst_tab;
     g.n = p->mx;
     g.lines = ax.lines;
+    g.stride = 1;
     g.err = &p->ctl->err;
     return launch_dst_tc(g, st);
   }
   return launch_axis(ax, st);
+}
+
+// y sine transform (AxisArgs op 0, strided) of 3D grids: the odd-sequence FFT, or for FP32 lines of
+// 127 points on a plan that selected it, the tensor-core products
+template <typename T> cudaError_t xform_y3(pint_plan p, const AxisArgs<T>& ay, cudaStream_t st) {
+  if (sizeof(T) == 4 && p->ydst == 2) {
+    DstTcArgs g{};
+    g.S = reinterpret_cast<float2*>(ay.S);
+    g.tab = p->dst_tab_y;
+    g.n = 127;
+    g.lines = ay.lines;
+    g.stride = ay.P;
+    g.err = &p->ctl->err;
+    return launch_dst_tc(g, st);
+  }
+  return launch_axis(ay, st);
 }
 
 // spatial step on the half spectrum for T (float: MIXED/FP32, double: FP64)
@@ -950,9 +983,9 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
     az.lines_per_j = p->mx * p->my; az.tw = t.tw_z; az.C = p->Czl; az.logC = ilog2c(p->Czl); az.ld = p->Czl + 1;
     cudaError_t e;
     if ((e = xform_x(p, ax, st)) != cudaSuccess) return e;
-    if ((e = launch_axis(ay, st)) != cudaSuccess) return e;
+    if ((e = xform_y3(p, ay, st)) != cudaSuccess) return e;
     if ((e = launch_axis(az, st)) != cudaSuccess) return e;
-    if ((e = launch_axis(ay, st)) != cudaSuccess) return e;
+    if ((e = xform_y3(p, ay, st)) != cudaSuccess) return e;
     return xform_x(p, ax, st);
   }
   if (p->dim == 1) {
@@ -1621,6 +1654,7 @@ size_t pint::plan_bytes_estimate(const pint_plan_desc* d) {
   if (d->alpha != 1.0) b += 8 * NM;
   b += 64 * (N + d->grid.mx + d->grid.my) + 65536;  // tables, alignment slack
   if (d->xdst != 1 && dst_tc_line_ok(d->grid.mx) && d->grid.dim >= 2) b += dst_tc_table_bytes(d->grid.mx);
+  if (d->xdst != 1 && d->grid.dim == 3 && d->grid.my == 127) b += dst_tc_table_bytes(127);
   return b;
 }
 
@@ -1656,13 +1690,13 @@ extern "C" int pint_plan_tuning(pint_plan p, int* out, int n) {
     return -1;
   }
   const bool mixed = p->prec == PINT_MIXED;
-  const int v[8] = {p->Cr, p->Ci, p->Cz, p->ysolve,
+  const int v[9] = {p->Cr, p->Ci, p->Cz, p->ysolve,
                     mixed ? (compiled_time_fft_shape(p->N, p->Cr) ? 16 : 1 << p->rml) : 0,
                     mixed ? (compiled_update_shape(p->N, p->Ci) ? 16 : 1 << p->uml) : 0, p->small ? 1 : 0,
-                    p->xdst};
-  const int k = n < 8 ? n : 8;
+                    p->xdst, p->ydst};
+  const int k = n < 9 ? n : 9;
   for (int i = 0; i < k; ++i) out[i] = v[i];
-  return 8;
+  return 9;
 }
 
 extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* upd_rel_out) {

@@ -96,8 +96,11 @@ struct pint_plan_s {
   int kc = 0;
   double* Fws = nullptr;            // pint_solve_fv without the fused form: F_hat [N][M] (on first use)
   int xdst = 1;                     // x sine transforms of FP32 inner solves: 1 odd-sequence FFT,
-                                    // 2 tensor-core products (mx = 255)
+                                    // 2 tensor-core products (mx = 255 or 127)
   unsigned short* dst_tab = nullptr;  // xdst 2: the sine-matrix image (FP16 hi / lo)
+  int ydst = 1;                     // y sine transforms of 3D FP32 inner solves: 1 odd-sequence FFT,
+                                    // 2 tensor-core products (lines of 127 points, strided)
+  unsigned short* dst_tab_y = nullptr;  // ydst 2: the 127-point sine-matrix image
   float *Uhi = nullptr, *Fhi = nullptr;  // FP32: U, F_hat
   void* S = nullptr;                // spectrum
   double* z = nullptr;              // CQ Toeplitz output [N][M]

@@ -183,3 +183,63 @@ def test_tensor_core_plans_in_a_batch_graph_beside_fft_plans():
         assert rel_l2(U.cpu().numpy(), oracle_solution(p)) <= 1e-8, (p.name, s)
     for pl in plans:
         pl.close()
+
+
+# ---- the y transforms of 3D grids with my = 127: strided lines, tiles of up to 64 columns of a
+# (j, z) plane (k_dst127s_tc) ----
+Y3_CASES = [
+    ("3d_31x127x3_N8", dict(m=31, my=127, mz=3, N=8, k=2)),      # rows of 31: one partial tile per plane
+    ("3d_127x127x7_N16", dict(m=127, my=127, mz=7, N=16, k=3)),  # 64 + 63 columns; x on the tensor cores too
+    ("3d_255x127x3_N8", dict(m=255, my=127, mz=3, N=8, k=2)),    # 3 x 64 + 63; x: the folded 255-point kernel
+    ("3d_63x127x7_N16", dict(m=63, my=127, mz=7, N=16, k=4)),
+]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+@pytest.mark.parametrize("name,kw", Y3_CASES)
+def test_sweep_matches_fft_transform_3d_y(name, kw, precision):
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = workloads.heat3d_problem(**kw)
+    with Plan.for_problem(p, precision, xdst=1) as plan:
+        assert plan.tuning()["ydst"] == 1
+    with Plan.for_problem(p, precision, xdst=2) as plan:
+        assert plan.tuning()["ydst"] == 2
+    u1, a = _sweep(p, torch, precision, 1)
+    u2, b = _sweep(p, torch, precision, 2)
+    assert np.all(np.isfinite(b))
+    assert rel_l2(b, a) <= SWEEP_BAR, name
+
+
+def test_solve_3d_y_reaches_the_oracle_with_the_same_sweeps():
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = workloads.heat3d_problem(m=63, my=127, mz=7, N=16, k=4, kappa=0.05)
+    ref = oracle_solution(p)
+    res = []
+    for x in (1, 2):
+        v, f, fd = device_inputs(p, torch)
+        with Plan.for_problem(p, "mixed", xdst=x) as plan:
+            assert plan.tuning()["ydst"] == x
+            U = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+            st, sweeps, upd = plan.solve_fv(v, f, fd, U, tol=1e-10)
+            torch.cuda.synchronize()
+        res.append((st, sweeps, U.cpu().numpy()))
+    assert res[0][0] == 0 and res[1][0] == 0 and res[0][1] == res[1][1]
+    assert rel_l2(res[1][2], ref) <= 1e-8
+
+
+def test_3d_y_variant_selection():
+    torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    few = workloads.heat3d_problem(m=31, my=127, mz=7, N=32)      # 17 x 31 x 7 = 3689 y lines: FFT
+    many = workloads.heat3d_problem(m=63, my=127, mz=15, N=16)    # 9 x 63 x 15 = 8505: tensor cores
+    other = workloads.heat3d_problem(m=127, my=63, mz=15, N=32)   # y lines of 63 points
+    with Plan.for_problem(few, "mixed") as plan:
+        assert plan.tuning()["ydst"] == 1
+    with Plan.for_problem(many, "mixed") as plan:
+        assert plan.tuning()["ydst"] == 2
+    with Plan.for_problem(many, "fp64") as plan:
+        assert plan.tuning()["ydst"] == 1
+    with Plan.for_problem(other, "mixed", xdst=2) as plan:
+        assert plan.tuning()["ydst"] == 1
