@@ -94,11 +94,11 @@ NCU_TRAFFIC = {
         "inv_update_v0_ff": (141.95e6, "kernels_time.cu", "4f1bc2da689b12f51d0599e98cff88feff864466"),
         "inv_update_ff": (277.48e6, "kernels_time.cu", "4f1bc2da689b12f51d0599e98cff88feff864466"),
         "dst_f32": (76.07e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
-        "dst_tc_f32": (75.41e6, "kernels_dst_tc.cu", "a7a4737520aeb28b4889590b53b66a6b6fa736a1"),
+        "dst_tc_f32": (74.98e6, "kernels_dst_tc.cu", "ecf55e88d35fcc7c612f9c05c2e89a4fe91fe57f"),
         "axis_solve_f32": (78.60e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
     },
     "heat3d_127x127x63_N32_k4_a1.0": {
-        "dst_tc_f32": (217.65e6, "kernels_dst_tc.cu", "a7a4737520aeb28b4889590b53b66a6b6fa736a1"),
+        "dst_tc_y_f32": (217.40e6, "kernels_dst_tc.cu", "ecf55e88d35fcc7c612f9c05c2e89a4fe91fe57f"),
     },
 }
 
