@@ -49,6 +49,7 @@ def algo_bytes(name: str, N: int, M: int, K: int = 1) -> float:
         "dst_f32": 16 * JM,                     # read + write spectrum (complex float)
         "dst_tc_f32": 16 * JM,                  # the same transform as tensor-core products
         "dst_tc_y_f32": 16 * JM,                # the y transform of 3D grids, the same way
+        "axis_solve_tc_f32": 16 * JM,           # the z solve of 3D grids, two tensor-core passes
         "axis_solve_f32": 16 * JM,
         "rhs_f64": 16 * NM,                     # read f, write F_hat
         "rhs_head_f64": 16 * K * M,             # F_hat's first k levels: read f, write
@@ -94,11 +95,11 @@ NCU_TRAFFIC = {
         "inv_update_v0_ff": (141.95e6, "kernels_time.cu", "4f1bc2da689b12f51d0599e98cff88feff864466"),
         "inv_update_ff": (277.48e6, "kernels_time.cu", "4f1bc2da689b12f51d0599e98cff88feff864466"),
         "dst_f32": (76.07e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
-        "dst_tc_f32": (74.98e6, "kernels_dst_tc.cu", "ecf55e88d35fcc7c612f9c05c2e89a4fe91fe57f"),
+        "dst_tc_f32": (75.21e6, "kernels_dst_tc.cu", "cc4217510b4500885aa87744fecb930383c9a098"),
         "axis_solve_f32": (78.60e6, "kernels_space.cu", "75607f77d5b73a2e1fbb1c5ca20a86e16298a900"),
     },
     "heat3d_127x127x63_N32_k4_a1.0": {
-        "dst_tc_y_f32": (217.40e6, "kernels_dst_tc.cu", "ecf55e88d35fcc7c612f9c05c2e89a4fe91fe57f"),
+        "dst_tc_y_f32": (217.41e6, "kernels_dst_tc.cu", "cc4217510b4500885aa87744fecb930383c9a098"),
     },
 }
 

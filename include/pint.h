@@ -134,7 +134,10 @@ typedef struct {
                              form holds 128 KB (255 points) or 64 KB (127 points) of tables on the
                              device. The y-direction transforms of 3D grids with my = 127 follow
                              the same switch (tensor cores for 2, and for 0 and 3 from 8192 lines
-                             (N/2 + 1) mx mz; 64 KB more of tables; pint_plan_tuning out[8]). */
+                             (N/2 + 1) mx mz; 64 KB more of tables; pint_plan_tuning out[8]); the
+                             z solves of 3D grids with mz = 127 take two tensor-core passes
+                             around the divide for 2 only (slower than the FFT form on the
+                             grids measured; the same table; out[9]). */
 } pint_plan_desc;
 
 /* Build a plan: FP64 constant tables (BDF / CQ weights omega_j of eq. (2.2) / eq. (3.2) --
@@ -295,7 +298,9 @@ pint_status pint_solve_host_join(pint_plan plan, void* stream);
  * transforms (16 for the compiled shapes; 8 or 16 as timed for runtime shapes; 0 when not MIXED),
  * out[6] 1 if the whole solve runs as one CTA, out[7] x sine transform of the FP32 inner solves
  * (1 odd-sequence FFT, 2 tensor-core products), out[8] y sine transform of 3D plans (the same
- * codes). Fills min(n, 9) entries and returns 9 (-1 for a NULL plan or out). Host-only. */
+ * codes), out[9] z solve of 3D plans (1 odd-sequence FFTs around the divide, 2 two tensor-core
+ * passes around it). Fills min(n, 10) entries and returns 10 (-1 for a NULL plan or out).
+ * Host-only. */
 int pint_plan_tuning(pint_plan plan, int* out, int n);
 
 /* Outcome of the plan's most recent graph-launched solve: sweeps, final relative update, and

@@ -18,6 +18,9 @@
 //   * n = 127, strided lines (k_dst127s_tc): the y-direction transforms of 3D grids (my = 127),
 //     whose lines are the columns of the (j, z) planes of my rows x mx points; a tile is up to 64
 //     consecutive columns of one plane, read and written row by row (contiguous along x).
+//   * n = 127, strided lines, solve (k_dst127z_tc): the z-direction solve of 3D grids (mz = 127:
+//     DST-z, divide by the shifted eigenvalues, DST-z back, AxisArgs op 1) as two passes per tile,
+//     the divided spectrum held in shared memory between them.
 //
 // Precision: FP16 operands split in two (v = hi + lo: hi of 11 significant bits by Veltkamp's
 // splitting, lo = v - hi), three products per term (hi hi + hi lo + lo hi, FP32 accumulation in
@@ -218,8 +221,11 @@ __device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
 // STRIDED (P = 127): the lines are the columns of planes of P rows (a.stride points per row); a
 // tile is up to 64 consecutive columns of one plane, which the staging warps read straight from
 // global memory (each row's columns are contiguous) instead of through the load warp's raw buffer.
-template <int P, bool STRIDED> __device__ __forceinline__ void dst_tc_body(const DstTcArgs& a) {
+// SOLVE (strided, P = 127): per tile, the transform (pass A), the divide of AxisArgs op 1 in the
+// epilogue, and the transform back (pass B, +2i) from the divided spectrum in shared memory.
+template <int P, int MODE> __device__ __forceinline__ void dst_tc_body(const DstTcArgs& a) {
   using S = TcShape<P>;
+  constexpr bool STRIDED = MODE >= 1, SOLVE = MODE == 2;
   static_assert(!STRIDED || P == 127, "strided lines: 127 points");
   constexpr int kLines = S::kLines, kN = S::kN, kChunk = S::kChunk, kChunks = S::kChunks;
   constexpr int kStageThreads = S::kStageThreads, kItems = S::kItems, kVals = S::kVals;
@@ -303,14 +309,21 @@ template <int P, bool STRIDED> __device__ __forceinline__ void dst_tc_body(const
       uint64_t dA[2 * kHalves];
 #pragma unroll
       for (int i = 0; i < 2 * kHalves; ++i) dA[i] = mat_desc(sA + i * kMatBytes, 16 * 128, 128);
+      // units: the tiles, or for SOLVE their two passes (accumulator buffer = pass, used once per
+      // tile; otherwise buffer i & 1, used every other tile)
+      constexpr int U = SOLVE ? 2 : 1;
       int i = 0;
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
-        const int b2 = i & 1;
-        if (i >= 2) ok = bar_wait(smem_u32(&ms.acc_empty[b2]), (uint32_t)(((i >> 1) - 1) & 1), abort);
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i)
+      for (int pass = 0; pass < U && ok; ++pass) {
+        const int ui = i * U + pass;
+        const int b2 = SOLVE ? pass : (i & 1);
+        if (SOLVE ? i >= 1 : i >= 2)
+          ok = bar_wait(smem_u32(&ms.acc_empty[b2]), SOLVE ? (uint32_t)((i - 1) & 1) : (uint32_t)(((i >> 1) - 1) & 1),
+                        abort);
         tc_after_sync();
         const uint32_t dacc = tmem + (uint32_t)(b2 * kHalves * kN);
         for (int c = 0; c < kChunks && ok; ++c) {
-          const int u = 2 * i + (c >> 1);  // use of the chunk's slot (c & 1)
+          const int u = 2 * ui + (c >> 1);  // use of the chunk's slot (c & 1)
           ok = bar_wait(smem_u32(&ms.full[c & 1]), (uint32_t)(u & 1), abort);
           if (!ok) break;
           tc_after_sync();
@@ -411,9 +424,10 @@ template <int P, bool STRIDED> __device__ __forceinline__ void dst_tc_body(const
     const float2* raw = reinterpret_cast<const float2*>(smem + S::kRawOff);
     // epilogue of the j-th tile of this CTA (tile index tj): lanes 32 (warp % 4) .. + 31 of tensor
     // memory hold output index m; each group of four warps takes kLinesPerWarp lines
-    auto epilogue = [&](int j, int tj) {
-      const int b2 = j & 1;
-      if (!bar_wait(smem_u32(&ms.acc_full[b2]), (uint32_t)((j >> 1) & 1), abort)) atomicExch(&ms.abort, 1u);
+    // kind 0: the transform's output (-2i); SOLVE: kind 1 the divided spectrum (-2i, then / d) into
+    // the shared buffer only, kind 2 the solution (+2i)
+    auto epilogue = [&](int b2, uint32_t ph, int tj, int kind) {
+      if (!bar_wait(smem_u32(&ms.acc_full[b2]), ph, abort)) atomicExch(&ms.abort, 1u);
       tc_after_sync();
       const int m = 32 * (warp & 3) + lane;
       const int l0 = kLinesPerWarp * (warp >> 2);
@@ -464,10 +478,33 @@ template <int P, bool STRIDED> __device__ __forceinline__ void dst_tc_body(const
             // output index m of the 8 lines into the transposition buffer (row m, column lu)
             if (m < P) {
               float2* so = reinterpret_cast<float2*>(smem + S::kOutOff) + m * S::kOutPitch + l0 + h8;
+              if (SOLVE && kind == 1) {
+                // / scale (sigma_j + lambda_other + lambda_k), k = m + 1 (as AxisArgs op 1)
+                const int q = tj / tpp, x0 = (tj - q * tpp) * kLines, nl = geo(tj).nl;
+                const float2 sg = a.sigma[q];
+                const float lz = a.lam_axis[m];
 #pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const float us = ms.unscale[b2][l0 + h8 + u];
-                so[u] = make_float2(im[u] * us, -re[u] * us);
+                for (int u = 0; u < 8; ++u) {
+                  const int lu = l0 + h8 + u;
+                  const float us = ms.unscale[b2][lu];
+                  const float yx = im[u] * us, yy = -re[u] * us;
+                  const float lo = lu < nl ? a.lam_other[x0 + lu] : 0.f;
+                  const float dx = (sg.x + lo + lz) * a.scale, dy = sg.y * a.scale;
+                  const float inv = 1.f / (dx * dx + dy * dy);
+                  so[u] = make_float2((yx * dx + yy * dy) * inv, (yy * dx - yx * dy) * inv);
+                }
+              } else if (SOLVE && kind == 2) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                  const float us = ms.unscale[b2][l0 + h8 + u];
+                  so[u] = make_float2(-im[u] * us, re[u] * us);  // +2i z
+                }
+              } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                  const float us = ms.unscale[b2][l0 + h8 + u];
+                  so[u] = make_float2(im[u] * us, -re[u] * us);
+                }
               }
             }
           } else if (!*reinterpret_cast<volatile uint32_t*>(&ms.abort) && m < P) {
@@ -489,7 +526,7 @@ template <int P, bool STRIDED> __device__ __forceinline__ void dst_tc_body(const
         // warp stores 32 consecutive columns of a row. (The next tile's writes into the buffer
         // follow the staging threads' barrier of the next tile.)
         asm volatile("bar.sync 2, %0;" ::"r"(kStageThreads) : "memory");
-        if (!*reinterpret_cast<volatile uint32_t*>(&ms.abort)) {
+        if (kind != 1 && !*reinterpret_cast<volatile uint32_t*>(&ms.abort)) {
           const TileGeo g = geo(tj);
           const float2* so = reinterpret_cast<const float2*>(smem + S::kOutOff);
           for (int idx = tid; idx < P * kLines; idx += kStageThreads) {
@@ -520,6 +557,82 @@ template <int P, bool STRIDED> __device__ __forceinline__ void dst_tc_body(const
         }
       }
     };
+    // one unit (a tile, or a pass of a SOLVE tile) from `in`: the line maxima, the scales (unscale
+    // buffer ubuf), then (fold,) scale and split chunk by chunk into the stage slots (each free once
+    // the MMAs of its previous chunk are done), signalling the MMA warp; true if the CTA aborts
+    // (decided for all staging threads together)
+    auto stage_unit = [&](int ui, int ubuf) -> bool {
+        // largest |re|, |im| of each line: over the item, its four lanes (q), the four warps
+        // holding the line's groups (g8)
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+          float m = 0.f;
+#pragma unroll
+          for (int c = 0; c < kChunks; ++c)
+#pragma unroll
+            for (int k = 0; k < kVals; ++k) m = fmaxf(m, fmaxf(fabsf(in[j][c][k].x), fabsf(in[j][c][k].y)));
+          m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+          m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+          if ((ikl[j] & 7) == 0) ms.pmax[ikl[j] >> 3][il[j]] = m;
+        }
+        if (ssync_abort()) return true;
+        float sc[kItems];
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+          const int l = il[j];
+          const float m = fmaxf(fmaxf(ms.pmax[0][l], ms.pmax[1][l]), fmaxf(ms.pmax[2][l], ms.pmax[3][l]));
+          // m = f 2^E, f in [0.5, 1): the scale 2^(14 - E) brings m to [2^13, 2^14)
+          const int E = m > 0.f ? (int)((__float_as_uint(m) >> 23) & 0xff) - 126 : 14;
+          int sh = 14 - E;
+          sh = sh > 100 ? 100 : (sh < -100 ? -100 : sh);
+          sc[j] = __uint_as_float((uint32_t)(127 + sh) << 23);
+          if (ikl[j] == 0) ms.unscale[ubuf][l] = __uint_as_float((uint32_t)(127 - sh - 3) << 23);  // 2/(16 2^sh)
+        }
+        // (fold,) scale and split chunk by chunk into the stage slots (each free once the MMAs of
+        // its previous chunk are done), then signal the MMA warp
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c) {
+          const int u = 2 * ui + (c >> 1);  // use of the chunk's slot (c & 1)
+          if (u >= 1 && !bar_wait(smem_u32(&ms.empty[c & 1]), (uint32_t)((u - 1) & 1), abort))
+            atomicExch(&ms.abort, 1u);
+          const uint32_t stage = sB + (c & 1) * kStageBytes;
+#pragma unroll
+          for (int j = 0; j < kItems; ++j) {
+            const float f = sc[j];
+            uint32_t lo, hi;
+            if constexpr (S::kFold) {
+              const float2 a0 = in[j][c][0], a1 = in[j][c][1], b0 = in[j][c][2], b1 = in[j][c][3];
+              const float2 e0 = make_float2((a0.x - b0.x) * f, (a0.y - b0.y) * f);
+              const float2 e1 = make_float2((a1.x - b1.x) * f, (a1.y - b1.y) * f);
+              const float2 o0 = make_float2((a0.x + b0.x) * f, (a0.y + b0.y) * f);
+              const float2 o1 = make_float2((a1.x + b1.x) * f, (a1.y + b1.y) * f);
+              hi = split2(e0.x, e1.x, &lo);
+              sts32(stage + 0 * kOpBytes + iore[j], hi);
+              sts32(stage + 1 * kOpBytes + iore[j], lo);
+              hi = split2(e0.y, e1.y, &lo);
+              sts32(stage + 0 * kOpBytes + ioim[j], hi);
+              sts32(stage + 1 * kOpBytes + ioim[j], lo);
+              hi = split2(o0.x, o1.x, &lo);
+              sts32(stage + 2 * kOpBytes + iore[j], hi);
+              sts32(stage + 3 * kOpBytes + iore[j], lo);
+              hi = split2(o0.y, o1.y, &lo);
+              sts32(stage + 2 * kOpBytes + ioim[j], hi);
+              sts32(stage + 3 * kOpBytes + ioim[j], lo);
+            } else {
+              const float2 a0 = in[j][c][0], a1 = in[j][c][1];
+              hi = split2(a0.x * f, a1.x * f, &lo);
+              sts32(stage + 0 * kOpBytes + iore[j], hi);
+              sts32(stage + 1 * kOpBytes + iore[j], lo);
+              hi = split2(a0.y * f, a1.y * f, &lo);
+              sts32(stage + 0 * kOpBytes + ioim[j], hi);
+              sts32(stage + 1 * kOpBytes + ioim[j], lo);
+            }
+          }
+          fence_async_smem();
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.full[c & 1])) : "memory");
+        }
+      return false;
+    };
     if (STRIDED && blockIdx.x < tiles) load_strided(blockIdx.x);
     int i = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
@@ -547,84 +660,40 @@ template <int P, bool STRIDED> __device__ __forceinline__ void dst_tc_body(const
         }
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.raw_empty)) : "memory");
       }
-      // largest |re|, |im| of each line: over the item, its four lanes (q), the four warps
-      // holding the line's groups (g8)
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        float m = 0.f;
-#pragma unroll
-        for (int c = 0; c < kChunks; ++c)
-#pragma unroll
-          for (int k = 0; k < kVals; ++k) m = fmaxf(m, fmaxf(fabsf(in[j][c][k].x), fabsf(in[j][c][k].y)));
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-        if ((ikl[j] & 7) == 0) ms.pmax[ikl[j] >> 3][il[j]] = m;
-      }
-      if (ssync_abort()) break;
-      float sc[kItems];
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        const int l = il[j];
-        const float m = fmaxf(fmaxf(ms.pmax[0][l], ms.pmax[1][l]), fmaxf(ms.pmax[2][l], ms.pmax[3][l]));
-        // m = f 2^E, f in [0.5, 1): the scale 2^(14 - E) brings m to [2^13, 2^14)
-        const int E = m > 0.f ? (int)((__float_as_uint(m) >> 23) & 0xff) - 126 : 14;
-        int sh = 14 - E;
-        sh = sh > 100 ? 100 : (sh < -100 ? -100 : sh);
-        sc[j] = __uint_as_float((uint32_t)(127 + sh) << 23);
-        if (ikl[j] == 0) ms.unscale[b2][l] = __uint_as_float((uint32_t)(127 - sh - 3) << 23);  // 2/(16 2^sh)
-      }
-      // (fold,) scale and split chunk by chunk into the stage slots (each free once the MMAs of
-      // its previous chunk are done), then signal the MMA warp
-#pragma unroll
-      for (int c = 0; c < kChunks; ++c) {
-        const int u = 2 * i + (c >> 1);  // use of the chunk's slot (c & 1)
-        if (u >= 1 && !bar_wait(smem_u32(&ms.empty[c & 1]), (uint32_t)((u - 1) & 1), abort))
-          atomicExch(&ms.abort, 1u);
-        const uint32_t stage = sB + (c & 1) * kStageBytes;
+      if constexpr (SOLVE) {
+        // pass A from the tile's rows; the divided spectrum into the shared buffer; pass B from it
+        if (stage_unit(2 * i, 0)) break;
+        epilogue(0, (uint32_t)(i & 1), t, 1);
+        const float2* zs = reinterpret_cast<const float2*>(smem + S::kOutOff);
+        const int nl = geo(t).nl;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
-          const float f = sc[j];
-          uint32_t lo, hi;
-          if constexpr (S::kFold) {
-            const float2 a0 = in[j][c][0], a1 = in[j][c][1], b0 = in[j][c][2], b1 = in[j][c][3];
-            const float2 e0 = make_float2((a0.x - b0.x) * f, (a0.y - b0.y) * f);
-            const float2 e1 = make_float2((a1.x - b1.x) * f, (a1.y - b1.y) * f);
-            const float2 o0 = make_float2((a0.x + b0.x) * f, (a0.y + b0.y) * f);
-            const float2 o1 = make_float2((a1.x + b1.x) * f, (a1.y + b1.y) * f);
-            hi = split2(e0.x, e1.x, &lo);
-            sts32(stage + 0 * kOpBytes + iore[j], hi);
-            sts32(stage + 1 * kOpBytes + iore[j], lo);
-            hi = split2(e0.y, e1.y, &lo);
-            sts32(stage + 0 * kOpBytes + ioim[j], hi);
-            sts32(stage + 1 * kOpBytes + ioim[j], lo);
-            hi = split2(o0.x, o1.x, &lo);
-            sts32(stage + 2 * kOpBytes + iore[j], hi);
-            sts32(stage + 3 * kOpBytes + iore[j], lo);
-            hi = split2(o0.y, o1.y, &lo);
-            sts32(stage + 2 * kOpBytes + ioim[j], hi);
-            sts32(stage + 3 * kOpBytes + ioim[j], lo);
-          } else {
-            const float2 a0 = in[j][c][0], a1 = in[j][c][1];
-            hi = split2(a0.x * f, a1.x * f, &lo);
-            sts32(stage + 0 * kOpBytes + iore[j], hi);
-            sts32(stage + 1 * kOpBytes + iore[j], lo);
-            hi = split2(a0.y * f, a1.y * f, &lo);
-            sts32(stage + 0 * kOpBytes + ioim[j], hi);
-            sts32(stage + 1 * kOpBytes + ioim[j], lo);
+          const bool okl = il[j] < nl;
+#pragma unroll
+          for (int c = 0; c < kChunks; ++c) {
+            const int x = c * kChunk + ikl[j] + 1;
+            const float2 z = make_float2(0.f, 0.f);
+            in[j][c][0] = okl ? zs[(x - 1) * S::kOutPitch + il[j]] : z;
+            in[j][c][1] = (okl && x < P) ? zs[x * S::kOutPitch + il[j]] : z;
           }
         }
-        fence_async_smem();
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ms.full[c & 1])) : "memory");
+        // (the unit's barrier orders these reads before the buffer's next writes)
+        if (stage_unit(2 * i + 1, 1)) break;
+        if (t + (int)gridDim.x < tiles) load_strided(t + (int)gridDim.x);
+        epilogue(1, (uint32_t)(i & 1), t, 2);
+        continue;
       }
+      if (stage_unit(i, b2)) break;
       // strided lines: the next tile's loads (the registers are free again)
       if (STRIDED && t + (int)gridDim.x < tiles) load_strided(t + (int)gridDim.x);
       // the previous tile's epilogue runs now, while this tile's MMAs execute
-      if (i >= 1) epilogue(i - 1, t - (int)gridDim.x);
+      if (i >= 1) epilogue((i - 1) & 1, (uint32_t)(((i - 1) >> 1) & 1), t - (int)gridDim.x, 0);
     }
     // the last tile's epilogue, decided once for all staging threads (the strided epilogue holds a
     // barrier of theirs)
     const bool stop = ssync_abort();
-    if (i >= 1 && !stop) epilogue(i - 1, blockIdx.x + (i - 1) * (int)gridDim.x);
+    if (!SOLVE && i >= 1 && !stop)
+      epilogue((i - 1) & 1, (uint32_t)(((i - 1) >> 1) & 1), blockIdx.x + (i - 1) * (int)gridDim.x, 0);
     if (tid == 0 && *reinterpret_cast<volatile uint32_t*>(&ms.abort)) atomicExch(a.err, 1);
   }
   tc_before_sync();
@@ -635,9 +704,10 @@ template <int P, bool STRIDED> __device__ __forceinline__ void dst_tc_body(const
   }
 }
 
-__global__ void __launch_bounds__(TcShape<255>::kThreads, 1) k_dst255_tc(DstTcArgs a) { dst_tc_body<255, false>(a); }
-__global__ void __launch_bounds__(TcShape<127>::kThreads, 1) k_dst127_tc(DstTcArgs a) { dst_tc_body<127, false>(a); }
-__global__ void __launch_bounds__(TcShape<127>::kThreads, 1) k_dst127s_tc(DstTcArgs a) { dst_tc_body<127, true>(a); }
+__global__ void __launch_bounds__(TcShape<255>::kThreads, 1) k_dst255_tc(DstTcArgs a) { dst_tc_body<255, 0>(a); }
+__global__ void __launch_bounds__(TcShape<127>::kThreads, 1) k_dst127_tc(DstTcArgs a) { dst_tc_body<127, 0>(a); }
+__global__ void __launch_bounds__(TcShape<127>::kThreads, 1) k_dst127s_tc(DstTcArgs a) { dst_tc_body<127, 1>(a); }
+__global__ void __launch_bounds__(TcShape<127>::kThreads, 1) k_dst127z_tc(DstTcArgs a) { dst_tc_body<127, 2>(a); }
 
 // One FP16 operand pair (hi, lo) of a 128 x 128 matrix v(r, q) in its K-major shared-memory layout.
 template <typename F> void put_matrix(unsigned short* hi_img, unsigned short* lo_img, F v) {
@@ -691,8 +761,9 @@ void dst_tc_table(int n, unsigned short* img) {
 cudaError_t launch_dst_tc(const DstTcArgs& a, cudaStream_t st) {
   if (a.lines <= 0) return cudaSuccess;
   if (!dst_tc_line_ok(a.n) || a.stride < 1) return cudaErrorInvalidValue;
-  const bool strided = a.stride > 1;
+  const bool strided = a.stride > 1, solve = a.sigma != nullptr;
   if (strided && (a.n != 127 || a.lines % a.stride != 0)) return cudaErrorInvalidValue;
+  if (solve && (!strided || !a.lam_other || !a.lam_axis)) return cudaErrorInvalidValue;
   // the shared-memory attribute applies to the current device: set on every launch, as the other
   // launchers do; the SM count is queried once per device
   static std::atomic<int> sms[64];
@@ -710,13 +781,13 @@ cudaError_t launch_dst_tc(const DstTcArgs& a, cudaStream_t st) {
   const int smem = l255 ? TcShape<255>::kSmemBytes : TcShape<127>::kSmemBytes;
   const int per_tile = l255 ? TcShape<255>::kLines : TcShape<127>::kLines;
   const int threads = l255 ? TcShape<255>::kThreads : TcShape<127>::kThreads;
-  auto* kern = l255 ? k_dst255_tc : (strided ? k_dst127s_tc : k_dst127_tc);
+  auto* kern = l255 ? k_dst255_tc : (solve ? k_dst127z_tc : (strided ? k_dst127s_tc : k_dst127_tc));
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const long long tiles = strided ? (long long)(a.lines / a.stride) * ((a.stride + per_tile - 1) / per_tile)
                                   : (a.lines + per_tile - 1) / per_tile;
   const int grid = tiles < n ? (int)tiles : n;
-  prof_begin(strided ? "dst_tc_y_f32" : "dst_tc_f32", st);
+  prof_begin(solve ? "axis_solve_tc_f32" : (strided ? "dst_tc_y_f32" : "dst_tc_f32"), st);
   kern<<<grid, threads, smem, st>>>(a);
   prof_end(st);
   return cudaGetLastError();

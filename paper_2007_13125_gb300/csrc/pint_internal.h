@@ -144,6 +144,13 @@ struct DstTcArgs {
   // line per column (lines = planes * stride)
   int stride;
   int* err;                                // set to 1 if a bounded wait of the kernel gave up
+  // strided lines with sigma set: the solve of AxisArgs op 1 instead of the transform -- forward
+  // transform, divide line (q, x) at frequency k by scale (sigma[q] + lam_other[x] +
+  // lam_axis[k - 1]), transform back (+2i)
+  const float2* sigma;
+  const float* lam_other;
+  const float* lam_axis;
+  float scale;
 };
 inline bool dst_tc_line_ok(int n) { return n == 255 || n == 127; }
 size_t dst_tc_table_bytes(int n);

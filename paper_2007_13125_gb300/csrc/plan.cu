@@ -480,6 +480,10 @@ bool dst_tc_applies(pint_plan p) {
 bool dst_tc_y_applies(pint_plan p) {
   return p->dim == 3 && p->my == 127 && !p->periodic && !p->fem && p->prec != PINT_FP64;
 }
+// ... and the z solves of 3D grids with lines of 127 points (mz = 127)
+bool dst_tc_z_applies(pint_plan p) {
+  return p->dim == 3 && p->mz == 127 && !p->periodic && !p->fem && p->prec != PINT_FP64;
+}
 // the matrix image of a line length (255 or 127), built once per process
 const std::vector<unsigned short>& dst_tc_image(int n) {
   static std::once_flag once[2];
@@ -697,6 +701,14 @@ pint_status pint::plan_create_internal(const pint_plan_desc* d, DevAllocator* A,
     if ((s = upload(p, &p->dst_tab_y, dst_tc_image(127))) != PINT_OK) return bail(s);
     p->ydst = 2;
   }
+  // the z solves (mz = 127) on the tensor cores only when asked for (xdst = 2): two passes per tile
+  // around the divide measured slower than the FFT form on a 127^3, N = 128 grid (1283 against
+  // 1181 us per launch); one image for y and z
+  p->zsolve = 1;
+  if (dst_tc_z_applies(p) && d->xdst == 2) {
+    if (!p->dst_tab_y && (s = upload(p, &p->dst_tab_y, dst_tc_image(127))) != PINT_OK) return bail(s);
+    p->zsolve = 2;
+  }
   p->ysolve = 1;
   if (p->dim == 2 && p->prec != PINT_FP64 && !p->periodic) {
     if (d->ysolve == 2) p->ysolve = 2;
@@ -904,6 +916,26 @@ template <typename T> cudaError_t xform_x(pint_plan p, const AxisArgs<T>& ax, cu
   return launch_axis(ax, st);
 }
 
+// z solve (AxisArgs op 1, strided) of 3D grids: the odd-sequence FFTs around the divide, or for
+// FP32 lines of 127 points on a plan that selected it, two tensor-core passes around it
+template <typename T> cudaError_t solve_z3(pint_plan p, const AxisArgs<T>& az, cudaStream_t st) {
+  if (sizeof(T) == 4 && p->zsolve == 2) {
+    DstTcArgs g{};
+    g.S = reinterpret_cast<float2*>(az.S);
+    g.tab = p->dst_tab_y;
+    g.n = 127;
+    g.lines = az.lines;
+    g.stride = az.P;
+    g.err = &p->ctl->err;
+    g.sigma = reinterpret_cast<const float2*>(az.sigma);
+    g.lam_other = reinterpret_cast<const float*>(az.lam_other);
+    g.lam_axis = reinterpret_cast<const float*>(az.lam_axis);
+    g.scale = (float)az.scale;
+    return launch_dst_tc(g, st);
+  }
+  return launch_axis(az, st);
+}
+
 // y sine transform (AxisArgs op 0, strided) of 3D grids: the odd-sequence FFT, or for FP32 lines of
 // 127 points on a plan that selected it, the tensor-core products
 template <typename T> cudaError_t xform_y3(pint_plan p, const AxisArgs<T>& ay, cudaStream_t st) {
@@ -984,7 +1016,7 @@ cudaError_t spatial(pint_plan p, const DevTables<T>& t, cudaStream_t st) {
     cudaError_t e;
     if ((e = xform_x(p, ax, st)) != cudaSuccess) return e;
     if ((e = xform_y3(p, ay, st)) != cudaSuccess) return e;
-    if ((e = launch_axis(az, st)) != cudaSuccess) return e;
+    if ((e = solve_z3(p, az, st)) != cudaSuccess) return e;
     if ((e = xform_y3(p, ay, st)) != cudaSuccess) return e;
     return xform_x(p, ax, st);
   }
@@ -1654,7 +1686,7 @@ size_t pint::plan_bytes_estimate(const pint_plan_desc* d) {
   if (d->alpha != 1.0) b += 8 * NM;
   b += 64 * (N + d->grid.mx + d->grid.my) + 65536;  // tables, alignment slack
   if (d->xdst != 1 && dst_tc_line_ok(d->grid.mx) && d->grid.dim >= 2) b += dst_tc_table_bytes(d->grid.mx);
-  if (d->xdst != 1 && d->grid.dim == 3 && d->grid.my == 127) b += dst_tc_table_bytes(127);
+  if (d->xdst != 1 && d->grid.dim == 3 && (d->grid.my == 127 || d->grid.mz == 127)) b += dst_tc_table_bytes(127);
   return b;
 }
 
@@ -1690,13 +1722,13 @@ extern "C" int pint_plan_tuning(pint_plan p, int* out, int n) {
     return -1;
   }
   const bool mixed = p->prec == PINT_MIXED;
-  const int v[9] = {p->Cr, p->Ci, p->Cz, p->ysolve,
+  const int v[10] = {p->Cr, p->Ci, p->Cz, p->ysolve,
                     mixed ? (compiled_time_fft_shape(p->N, p->Cr) ? 16 : 1 << p->rml) : 0,
                     mixed ? (compiled_update_shape(p->N, p->Ci) ? 16 : 1 << p->uml) : 0, p->small ? 1 : 0,
-                    p->xdst, p->ydst};
-  const int k = n < 9 ? n : 9;
+                    p->xdst, p->ydst, p->zsolve};
+  const int k = n < 10 ? n : 10;
   for (int i = 0; i < k; ++i) out[i] = v[i];
-  return 9;
+  return 10;
 }
 
 extern "C" pint_status pint_solve_result(pint_plan p, int* sweeps_out, double* upd_rel_out) {

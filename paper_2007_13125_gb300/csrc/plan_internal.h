@@ -100,7 +100,9 @@ struct pint_plan_s {
   unsigned short* dst_tab = nullptr;  // xdst 2: the sine-matrix image (FP16 hi / lo)
   int ydst = 1;                     // y sine transforms of 3D FP32 inner solves: 1 odd-sequence FFT,
                                     // 2 tensor-core products (lines of 127 points, strided)
-  unsigned short* dst_tab_y = nullptr;  // ydst 2: the 127-point sine-matrix image
+  unsigned short* dst_tab_y = nullptr;  // ydst / zsolve 2: the 127-point sine-matrix image
+  int zsolve = 1;                   // z solve of 3D FP32 inner solves: 1 odd-sequence FFT (k_axis op 1),
+                                    // 2 two tensor-core passes around the divide (mz = 127)
   float *Uhi = nullptr, *Fhi = nullptr;  // FP32: U, F_hat
   void* S = nullptr;                // spectrum
   double* z = nullptr;              // CQ Toeplitz output [N][M]

@@ -311,12 +311,12 @@ class Plan:
 
     def tuning(self) -> dict:
         """The plan's tuned choices (pint_plan_tuning): tile widths, y solver, FFT radix bounds,
-        x sine transform, y sine transform of 3D plans."""
-        out = (_I * 9)()
-        if lib().pint_plan_tuning(self.handle, out, 9) < 0:
+        x sine transform, y sine transform and z solve of 3D plans."""
+        out = (_I * 10)()
+        if lib().pint_plan_tuning(self.handle, out, 10) < 0:
             raise PintError(PINT_EINVAL, last_error())
         keys = ["resid_width", "update_width", "history_width", "ysolve", "resid_max_radix",
-                "update_max_radix", "one_cta", "xdst", "ydst"]
+                "update_max_radix", "one_cta", "xdst", "ydst", "zsolve"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
 
     def workspace_bytes(self) -> int:

@@ -39,7 +39,8 @@ def test_heat3d_full_size_mixed_against_fp64():
     transforms run on the tensor cores by default: the MIXED solve against the FP64 direct form on
     the same GPU (the oracle's sparse LU of 2M unknowns per level is beyond a test; the FP64 path
     meets the oracle to 1e-10 in the cases above), space-time and per level, and with the FFT
-    transforms (xdst = 1) in the same number of sweeps."""
+    transforms (xdst = 1) and with the z solve on the tensor cores too (xdst = 2) in the same number
+    of sweeps."""
     import numpy as np
     torch = torch_cuda()
     from paper_2007_13125_gb300 import Plan
@@ -48,13 +49,15 @@ def test_heat3d_full_size_mixed_against_fp64():
     v, f, fd = device_inputs(p, torch)
     out = {}
     for name, prec, kw, tol in (("fp64", "fp64", {}, 1e-11), ("tc", "mixed", {}, 1e-8),
-                                ("fft", "mixed", {"xdst": 1}, 1e-8)):
+                                ("fft", "mixed", {"xdst": 1}, 1e-8), ("tcz", "mixed", {"xdst": 2}, 1e-8)):
         with Plan.for_problem(p, prec, **kw) as plan:
             t = plan.tuning()
             if name == "tc":
-                assert t["xdst"] == 2 and t["ydst"] == 2, t
+                assert t["xdst"] == 2 and t["ydst"] == 2 and t["zsolve"] == 1, t
             if name == "fft":
-                assert t["xdst"] == 1 and t["ydst"] == 1, t
+                assert t["xdst"] == 1 and t["ydst"] == 1 and t["zsolve"] == 1, t
+            if name == "tcz":
+                assert t["xdst"] == 2 and t["ydst"] == 2 and t["zsolve"] == 2, t
             U = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
             st, sweeps, upd = plan.solve_fv(v, f, fd, U, tol=tol)
             torch.cuda.synchronize()
@@ -62,10 +65,10 @@ def test_heat3d_full_size_mixed_against_fp64():
             out[name] = (sweeps, U)
     ref = out["fp64"][1]
     rms = float(torch.linalg.norm(ref)) / np.sqrt(p.N)
-    for name in ("tc", "fft"):
+    for name in ("tc", "fft", "tcz"):
         U = out[name][1]
         err = float(torch.linalg.norm(U - ref) / torch.linalg.norm(ref))
         lev = (torch.linalg.norm(U - ref, dim=1) / torch.clamp(torch.linalg.norm(ref, dim=1), min=rms)).max().item()
         assert err <= 1e-8, (name, err)
         assert lev <= 1e-7, (name, lev)
-    assert out["tc"][0] == out["fft"][0]
+    assert out["tc"][0] == out["fft"][0] == out["tcz"][0]

@@ -243,3 +243,71 @@ def test_3d_y_variant_selection():
         assert plan.tuning()["ydst"] == 1
     with Plan.for_problem(other, "mixed", xdst=2) as plan:
         assert plan.tuning()["ydst"] == 1
+
+
+# ---- the z solves of 3D grids with mz = 127 (DST-z, divide, DST-z back) as two tensor-core passes
+# per tile (k_dst127z_tc) ----
+Z3_CASES = [
+    ("3d_31x31x127_N8", dict(m=31, my=31, mz=127, N=8, k=2)),    # planes of 961 columns: 15 tiles + 1 column
+    ("3d_15x7x127_N16", dict(m=15, my=7, mz=127, N=16, k=3)),    # planes of 105: 64 + 41
+]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+@pytest.mark.parametrize("name,kw", Z3_CASES)
+def test_sweep_matches_fft_solve_3d_z(name, kw, precision):
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = workloads.heat3d_problem(**kw)
+    with Plan.for_problem(p, precision, xdst=1) as plan:
+        assert plan.tuning()["zsolve"] == 1
+    with Plan.for_problem(p, precision, xdst=2) as plan:
+        assert plan.tuning()["zsolve"] == 2
+    u1, a = _sweep(p, torch, precision, 1)
+    u2, b = _sweep(p, torch, precision, 2)
+    assert np.all(np.isfinite(b))
+    assert rel_l2(b, a) <= SWEEP_BAR, name
+
+
+@pytest.mark.parametrize("tol", [1e-8, 1e-10])
+def test_solve_3d_z_reaches_the_oracle(tol):
+    """At the metric's tolerance (1e-8) the same sweeps as the FFT form. At 1e-10 the stopping
+    rule's rounding floor decides: the FFT form stops after 3 sweeps (last update ~3e-8, ~1e-10 from
+    the oracle), the tensor-core form's slightly larger last update takes it to a 4th sweep (~2e-13
+    from the oracle); both meet the bar, at most one sweep apart."""
+    torch = torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    p = workloads.heat3d_problem(m=15, my=15, mz=127, N=16, k=4, kappa=0.05)
+    ref = oracle_solution(p)
+    res = []
+    for x in (1, 2):
+        v, f, fd = device_inputs(p, torch)
+        with Plan.for_problem(p, "mixed", xdst=x) as plan:
+            assert plan.tuning()["zsolve"] == x
+            U = torch.empty((p.N, p.M), dtype=torch.float64, device="cuda:0")
+            st, sweeps, upd = plan.solve_fv(v, f, fd, U, tol=tol)
+            torch.cuda.synchronize()
+        res.append((st, sweeps, U.cpu().numpy()))
+    assert res[0][0] == 0 and res[1][0] == 0
+    if tol == 1e-8:
+        assert res[0][1] == res[1][1]
+    else:
+        assert 0 <= res[1][1] - res[0][1] <= 1
+    assert rel_l2(res[1][2], ref) <= 1e-8 and rel_l2(res[0][2], ref) <= 1e-8
+
+
+def test_3d_z_variant_selection():
+    """The tensor-core z solve only when asked for (xdst = 2); the FFT form by default at any size."""
+    torch_cuda()
+    from paper_2007_13125_gb300 import Plan
+    many = workloads.heat3d_problem(m=31, my=15, mz=127, N=64)    # 33 x 465 = 15345 z lines
+    with Plan.for_problem(many, "mixed") as plan:
+        assert plan.tuning()["zsolve"] == 1
+    with Plan.for_problem(many, "mixed", xdst=3) as plan:
+        assert plan.tuning()["zsolve"] == 1
+    with Plan.for_problem(many, "mixed", xdst=2) as plan:
+        assert plan.tuning()["zsolve"] == 2
+    with Plan.for_problem(many, "fp64", xdst=2) as plan:
+        assert plan.tuning()["zsolve"] == 1
+    with Plan.for_problem(workloads.heat3d_problem(m=31, my=31, mz=63, N=64), "mixed", xdst=2) as plan:
+        assert plan.tuning()["zsolve"] == 1                       # z lines of 63 points
